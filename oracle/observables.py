@@ -1,0 +1,65 @@
+"""Observables on link configurations and Monte Carlo error analysis.
+
+* Plaquette Wilson loop (Sec. 2.3): the diagonal value of the plaquette
+  operator is the trace of the oriented product of the four link group
+  elements; for Z2 that is g1 g2 g3 g4, for U(1) cos(theta1 + theta2 -
+  theta3 - theta4) (real part of the U(1) character).  The plaquette at site
+  s uses link (s, x), link (s + e_x, y), link (s + e_y, x) reversed and
+  link (s, y) reversed.  <W> = sum_G p(G) W(G) (Sec. 5.1).
+* Integrated autocorrelation time with the automatic window of Madras &
+  Sokal (J. Stat. Phys. 50, 1988): tau(W) = 1/2 + sum_{t=1..W} rho(t),
+  smallest W with W >= c tau(W), c = 5.
+
+Pinned (tests/test_oracle_observables.py): plaquette against a loop-by-loop
+product on hand-built configurations, tau_int against the closed form
+(1 + a) / (2 (1 - a)) of an AR(1) series.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+Z2, U1 = 0, 1
+
+
+def plaquette_links(L: int):
+    """(V, 4) link ids: +l1, +l2, -l3, -l4 around each plaquette."""
+    out = []
+    for s in range(L * L):
+        x, y = s % L, s // L
+        sx = y * L + (x + 1) % L
+        sy = ((y + 1) % L) * L + x
+        out.append((2 * s + 0, 2 * sx + 1, 2 * sy + 0, 2 * s + 1))
+    return np.array(out, dtype=np.int64)
+
+
+def plaquette_values(group: int, L: int, links: np.ndarray) -> np.ndarray:
+    """(n_cfg, V) plaquette values."""
+    links = np.atleast_2d(links)
+    pl = plaquette_links(L)
+    if group == Z2:
+        g = links.astype(np.int64)
+        return (g[:, pl[:, 0]] * g[:, pl[:, 1]] * g[:, pl[:, 2]] * g[:, pl[:, 3]]).astype(np.float64)
+    th = links.astype(np.float64)
+    return np.cos(th[:, pl[:, 0]] + th[:, pl[:, 1]] - th[:, pl[:, 2]] - th[:, pl[:, 3]])
+
+
+def plaquette_mean(group: int, L: int, links: np.ndarray) -> np.ndarray:
+    return plaquette_values(group, L, links).mean(axis=1)
+
+
+def tau_int(series: np.ndarray, c: float = 5.0):
+    """Integrated autocorrelation time of (n_chains, T) series (chains pooled
+    after removing the grand mean).  Returns (tau, window)."""
+    x = np.atleast_2d(np.asarray(series, dtype=np.float64))
+    x = x - x.mean()
+    T = x.shape[1]
+    var = np.mean(x * x)
+    if var == 0.0 or T < 2:
+        return 0.5, 0
+    tau = 0.5
+    for t in range(1, T):
+        rho = np.mean(x[:, :-t] * x[:, t:]) / var
+        tau += rho
+        if t >= c * tau:
+            return float(tau), t
+    return float(tau), T - 1
