@@ -1,0 +1,165 @@
+/* ggf.h - C ABI of libggf, a GB300 (sm_103a) sampler for gauged
+ * superpositions of Gaussian fermionic PEPS (arXiv 2412.01737).
+ *
+ * The library samples gauge-link configurations G of an L x L periodic
+ * lattice with probability p(G) = N(G) / N (Sec. 5.1), where
+ *     N(G) = sum_nm lambda_n^* lambda_m N_nm(G)            (Sec. 5)
+ * and N_nm(G) = <psi_n(G)|psi_m(G)>, psi_n(G) = <B_n| U(G) |A> (Sec. 4).
+ * Each N_nm(G) is a constant times the Pfaffian of the virtual-mode matrix
+ *     M_nm(G) = D + O(G) Gamma_{X_nm} O(G)^T,
+ * D the direct sum of the sites' virtual covariance blocks, Gamma_{X_nm}
+ * the link-local covariance of |B_n><B_m| / <B_m|B_n>, O(G) the gauge twist
+ * on the source-end virtual Majoranas (Sec. 3.1, Sec. 5).
+ *
+ * Input conventions (all arrays row-major, all indices 0-based):
+ *   site s = y*L + x; link l = 2*s + d joins the +d end of s (source end,
+ *   carries the twist) to the -d end of s + e_d (d = 0: x, 1: y).
+ *   Site Majorana layout [phys(2) | end -x | end +x | end -y | end +y], each
+ *   end 2*n_v Majoranas, m_s = 2 + 8 n_v.  Bond layout per link
+ *   [source end (2 n_v) | target end (2 n_v)], r = 4 n_v.
+ *   Majoranas c_{2i} = psi_i + psi_i^dag, c_{2i+1} = -i (psi_i - psi_i^dag);
+ *   covariance Gamma_ab = (i/2) <[c_a, c_b]> (Sec. 3.2).
+ *   Z2 links: int8 values +1 / -1.  U(1) links: double angles in [0, 2 pi);
+ *   a source-end mode of charge q is twisted by exp(i q theta n).
+ *
+ * Memory: every entry point that takes array arguments also takes `mem`:
+ * GGF_MEM_DEVICE (device pointers, borrowed until the stream work ends) or
+ * GGF_MEM_HOST (host pointers; the call copies in and out and returns after
+ * synchronising the stream).  The caller owns every buffer it passes; the
+ * library owns its internal state (inverses, workspaces).  No exception
+ * crosses the ABI; every call returns a ggf_status and leaves a message for
+ * ggf_last_error.  Calls on one context are not thread safe.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef GGF_H
+#define GGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GGF_Z2 0
+#define GGF_U1 1
+#define GGF_FP64 0
+#define GGF_FP32 1
+#define GGF_MEM_DEVICE 0
+#define GGF_MEM_HOST 1
+#define GGF_N_OBS 3 /* per sweep and chain: plaquette mean, log N(G), acceptance */
+#define GGF_OBS_PLAQUETTE 0
+
+typedef enum {
+    GGF_OK = 0,
+    GGF_EINVAL = 1,     /* bad argument or size */
+    GGF_ENOMEM = 2,     /* device allocation failed */
+    GGF_ECUDA = 3,      /* a CUDA call failed */
+    GGF_ESINGULAR = 4,  /* a matrix M(G) was singular (N(G) = 0) */
+    GGF_ETIMEOUT = 5,   /* a bounded device wait ran out */
+    GGF_EDRIFT = 6,     /* tracked log-weights drifted past tolerance */
+    GGF_ESTATE = 7,     /* call out of order (e.g. sample before init) */
+    GGF_EIO = 8         /* checkpoint file error */
+} ggf_status;
+
+typedef struct ggf_ctx ggf_ctx;
+
+/* Create a context on CUDA device `device`.  *out is NULL on failure. */
+ggf_status ggf_create(ggf_ctx** out, int device);
+/* Free the context and everything it owns.  NULL is accepted. */
+void ggf_destroy(ggf_ctx* ctx);
+/* Message for the last failing call on ctx (valid until the next call). */
+const char* ggf_last_error(const ggf_ctx* ctx);
+
+/* Periodic L x L lattice, L >= 1 (Sec. 3: PEPS on a square lattice).
+ * Resets groups, Gaussians and chains. */
+ggf_status ggf_init_lattice(ggf_ctx* ctx, int L);
+
+/* Gauge group (GGF_Z2 or GGF_U1, Sec. 2.1-2.2) and n_v in {1, 2} virtual
+ * complex modes per link end.  q_src[n_v]: U(1) charges of the source-end
+ * modes (ignored for Z2, may be NULL then). */
+ggf_status ggf_init_group(ggf_ctx* ctx, int group, int n_v, const int* q_src);
+
+/* Variational parameters of the Ansatz (Sec. 4-5), host pointers:
+ *   gamma_site [V][m_s][m_s]  pure site covariances Gamma_A (one per site),
+ *   gamma_bond [K][2V][r][r]  pure bond covariances Gamma_{B_n} per link,
+ *   lambda     [K][2]         complex weights lambda_n (re, im).
+ * Builds the link-local covariances of |B_n><B_m|/<B_m|B_n>, the constants
+ * <B_m|B_n> with the reference-state phase convention <B_n|B_0> > 0, B_0 :=
+ * B_1 (Sec. 5), and the virtual blocks D.  1 <= K <= 8.  Host work only. */
+ggf_status ggf_init_gaussians(ggf_ctx* ctx, const double* gamma_site, int K,
+                              const double* gamma_bond, const double* lambda);
+
+/* Introspection of the per-pair constants, P = K(K+1)/2 pairs ordered
+ * (0,0)..(K-1,K-1) then (n,m), n<m, row by row.  log_c[2P]: complex log of the
+ * constant c_nm in N_nm(G) = c_nm Pf(M_nm(G)) (diagonal pairs: log|c_nn|);
+ * pairs[2P]: (n, m).  Either pointer may be NULL.  Host pointers. */
+ggf_status ggf_get_constants(const ggf_ctx* ctx, int* n_pairs, double* log_c, int* pairs);
+
+/* log N(G) for n_cfg configurations (Sec. 5): assemble M_nm(G) for every
+ * pair, factor it (FP64 Parlett-Reid Pfaffian on the GPU) and combine.
+ *   links  [n_cfg][2V]  int8 (Z2) or double (U(1))
+ *   logN   [n_cfg]      log N(G) (unnormalised; -inf if N(G) <= 0)
+ *   ell    [n_cfg][P][2] optional (NULL): log Pf(M_nm(G)) as (log|Pf|, arg);
+ *                       diagonal pairs report (log|Pf|, 0). */
+ggf_status ggf_logweight(ggf_ctx* ctx, int n_cfg, const void* links, double* logN,
+                         double* ell, int mem, void* stream);
+
+/* Wilson-loop observables from links alone (Sec. 2.3, Sec. 5.1).
+ * which = GGF_OBS_PLAQUETTE: out[n_cfg] = mean over the V plaquettes of the
+ * trace of the oriented plaquette product (Z2: product of signs; U(1): cos of
+ * theta1 + theta2 - theta3 - theta4). */
+ggf_status ggf_observable(ggf_ctx* ctx, int which, int n_cfg, const void* links,
+                          double* out, int mem, void* stream);
+
+typedef struct {
+    int precision;      /* GGF_FP64, or GGF_FP32 (inverse and updates in FP32,
+                           ratios, log-weights and refresh in FP64) */
+    int refresh_every;  /* full FP64 refresh of a chain after this many accepts */
+    double width;       /* U(1) proposal: theta += width * (u - 1/2) */
+    uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = chain index) */
+} ggf_chain_opts;
+
+/* Create n_chains Markov chains starting at links [n_chains][2V] and build
+ * their inverses W_nm = M_nm^{-1} and log-weights (full FP64 factorisation;
+ * identical starting configurations are factored once).  Resets the sweep
+ * counter to 0. */
+ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links,
+                           const ggf_chain_opts* opts, int mem, void* stream);
+
+/* Run n_sweeps Metropolis sweeps on every chain (Sec. 5.1).  A sweep
+ * proposes links l = 0 .. 2V-1 in order (Z2 flip; U(1) theta += width (u -
+ * 1/2) wrapped into [0, 2 pi)), scores each proposal by the low-rank Pfaffian
+ * ratio on the cached inverse, accepts iff u < N(G')/N(G) and applies the
+ * rank-r Sherman-Morrison-Woodbury update.  Random numbers: Philox4x64-10 with
+ * counter (sweep, link, 0, 0), key (seed, chain); word 0 -> u_accept, word 1
+ * -> u_propose, u = (word >> 11) 2^-53.
+ *   obs [n_sweeps][n_chains][GGF_N_OBS] (may be NULL) */
+ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* stream);
+
+/* Current links of all chains, [n_chains][2V]. */
+ggf_status ggf_chains_links(ggf_ctx* ctx, void* links, int mem, void* stream);
+
+/* Tracked log Pf(M_nm) of all chains, [n_chains][P][2] as (log|Pf|, arg). */
+ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
+
+typedef struct {
+    uint64_t proposals, accepts, refreshes, sweeps;
+    double max_drift;   /* max |l_tracked - l_refresh| over refreshes so far */
+    int n_chains, n_pairs;
+} ggf_chain_stats;
+
+ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out);
+
+/* Write / read the chain state (links, sweep counter, options, log-weights,
+ * counters).  Inverses are rebuilt on resume by a full refresh, so resumed
+ * chains make the same decisions as uninterrupted ones. */
+ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path);
+ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
+
+/* Wait for the context's work on `stream` and report device-side errors. */
+ggf_status ggf_sync(ggf_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

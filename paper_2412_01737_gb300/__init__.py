@@ -1,0 +1,8 @@
+"""GB300-native sampler for gauged superpositions of Gaussian fermionic PEPS.
+
+The compute path is libggf.so (hand-written CUDA for sm_103a behind a C ABI,
+include/ggf.h); this package only builds it and marshals arguments.  There is
+no CPU fallback: importing the binding fails loudly when the library is
+missing.
+"""
+from .ggf import GGF, GGFError, Z2, U1, FP64, FP32, lib_path  # noqa: F401

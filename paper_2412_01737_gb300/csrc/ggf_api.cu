@@ -1,0 +1,635 @@
+// C ABI entry points of libggf (see include/ggf.h for the contract).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+#include "ggf_ctx.h"
+
+size_t ggf_factor_tmp_bytes(int n, int batch);
+ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st);
+ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st);
+ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st);
+
+ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+ggf_status ggf_cuda(ggf_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return ggf_fail(ctx, GGF_ENOMEM, m);
+    return ggf_fail(ctx, GGF_ECUDA, m);
+}
+
+ggf_status ggf_workspace(ggf_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->work_bytes) return GGF_OK;
+    if (ctx->work) cudaFree(ctx->work);
+    ctx->work = nullptr;
+    ctx->work_bytes = 0;
+    GGF_CK(cudaMalloc(&ctx->work, bytes));
+    ctx->work_bytes = bytes;
+    return GGF_OK;
+}
+
+void ggf_free_chains(ggf_ctx* ctx) {
+    Chains& c = ctx->ch;
+    void* ptrs[] = {c.links, c.Wr, c.Wc, c.ell, c.zbuf, c.ybuf, c.accept, c.since_refresh,
+                    c.sweep_acc, c.counters, c.drift, c.refresh_list};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    ggf_chain_opts o = c.opts;
+    c = Chains();
+    c.opts = o;
+}
+
+void ggf_free_consts(ggf_ctx* ctx) {
+    void* ptrs[] = {ctx->d_D, ctx->d_Gr, ctx->d_Gc, ctx->d_logc, ctx->d_w};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    ctx->d_D = nullptr; ctx->d_Gr = nullptr; ctx->d_Gc = nullptr; ctx->d_logc = nullptr; ctx->d_w = nullptr;
+    ctx->have_gauss = false;
+}
+
+namespace {
+
+size_t link_bytes(const Geometry& g) { return g.group == GGF_Z2 ? 1 : sizeof(double); }
+
+// scoped device buffer
+struct DBuf {
+    void* p = nullptr;
+    ~DBuf() { if (p) cudaFree(p); }
+};
+
+ggf_status dalloc(ggf_ctx* ctx, DBuf& b, size_t bytes) {
+    GGF_CK(cudaMalloc(&b.p, std::max<size_t>(bytes, 16)));
+    return GGF_OK;
+}
+
+size_t budget_bytes() {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    size_t cap = (size_t)8 << 30;
+    return std::max<size_t>(std::min(cap, fr / 2), (size_t)64 << 20);
+}
+
+__global__ void write_ell_kernel(int n_items, int fam_pairs, int pair_off, int P, bool cplx, const cxd* logpf,
+                                 const cxd* phase, cxd* ell) {
+    int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    int cfg = it / fam_pairs, p = it % fam_pairs;
+    cxd v = {logpf[it].x, 0.0};
+    if (cplx) v.y = atan2(phase[it].y, phase[it].x);
+    ell[(size_t)cfg * P + pair_off + p] = v;
+}
+
+// W[chain][p] <- convert(A[item]) and log-weight bookkeeping after a factorisation
+template <class TD>
+__global__ void scatter_kernel(int N, int fam_pairs, const int* item_chain, const int* item_pair, const void* A,
+                               bool cplx, TD* W) {
+    int it = blockIdx.y;
+    size_t NN = (size_t)N * N;
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NN) return;
+    int c = item_chain[it], p = item_pair[it];
+    cxd v = cplx ? ((const cxd*)A)[(size_t)it * NN + e] : cxd{((const double*)A)[(size_t)it * NN + e], 0.0};
+    W[((size_t)c * fam_pairs + p) * NN + e] = Sc<TD>::from(v);
+}
+
+__global__ void ell_update_kernel(int n_items, int pair_off, int P, bool cplx, bool init, const int* item_chain,
+                                  const int* item_pair, const cxd* logdet, const cxd* logpf, const cxd* phase,
+                                  cxd* ell, double* drift, int* since, unsigned long long* counters) {
+    int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    int c = item_chain[it], p = pair_off + item_pair[it];
+    cxd& el = ell[(size_t)c * P + p];
+    if (!isfinite(logdet[it].x)) atomicAdd(&counters[3], 1ULL);
+    if (init) {
+        cxd v = {logpf[it].x, 0.0};
+        if (cplx) v.y = atan2(phase[it].y, phase[it].x);
+        el = v;
+    } else {
+        double la = 0.5 * logdet[it].x;
+        double d = 0.0;
+        if (!cplx) {
+            d = fabs(la - el.x);
+            el = {la, 0.0};
+        } else {
+            double ph = 0.5 * logdet[it].y;
+            double best = 0.0, bestd = 1e300;
+            for (int k = 0; k < 2; ++k) {
+                double cand = ph + k * M_PI;
+                double dd = remainder(cand - el.y, 2 * M_PI);
+                if (fabs(dd) < bestd) { bestd = fabs(dd); best = cand; }
+            }
+            best = remainder(best, 2 * M_PI);
+            d = fabs(la - el.x) + bestd;
+            el = {la, best};
+        }
+        if (d > drift[c]) drift[c] = d;
+    }
+    since[c] = 0;
+}
+
+// Factor the FP64 M_nm(G) of the listed chains: W <- M^{-1}; log-weights from
+// the Pfaffian (init) or from det with the branch nearest the tracked value.
+ggf_status factor_chains(ggf_ctx* ctx, const std::vector<int>& chains, bool init, cudaStream_t st) {
+    if (chains.empty()) return GGF_OK;
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    const int N = g.N;
+    const size_t NN = (size_t)N * N;
+    const bool fp64 = ch.opts.precision == GGF_FP64;
+    for (int fam = 0; fam < 2; ++fam) {
+        const bool cplx = fam == 1;
+        const int npf = cplx ? ctx->Kc : ctx->K;
+        if (npf == 0) continue;
+        const size_t elem = cplx ? sizeof(cxd) : sizeof(double);
+        const size_t per_item = NN * elem * (init ? 2 : 1);
+        size_t budget = budget_bytes();
+        int chunk_chains = (int)std::max<size_t>(1, budget / (per_item * npf));
+        chunk_chains = std::min<int>(chunk_chains, (int)chains.size());
+        const int max_items = chunk_chains * npf;
+        const size_t tmp = ggf_factor_tmp_bytes(N, max_items);
+        const size_t small = (size_t)max_items * (2 * sizeof(int) + 3 * sizeof(cxd)) + 256;
+        GGF_TRY(ggf_workspace(ctx, per_item * max_items + tmp + small + 1024));
+        unsigned char* base = (unsigned char*)ctx->work;
+        void* A = base;
+        void* A2 = init ? base + NN * elem * max_items : nullptr;
+        unsigned char* q = base + per_item * max_items;
+        void* ftmp = q;
+        q += (tmp + 255) / 256 * 256;
+        int* d_chain = (int*)q; q += (size_t)max_items * sizeof(int);
+        int* d_pair = (int*)q; q += (size_t)max_items * sizeof(int);
+        q = (unsigned char*)(((uintptr_t)q + 15) / 16 * 16);
+        cxd* d_logdet = (cxd*)q; q += (size_t)max_items * sizeof(cxd);
+        cxd* d_logpf = (cxd*)q; q += (size_t)max_items * sizeof(cxd);
+        cxd* d_phase = (cxd*)q;
+        std::vector<int> hc, hp;
+        for (size_t c0 = 0; c0 < chains.size(); c0 += chunk_chains) {
+            int nc = (int)std::min<size_t>(chunk_chains, chains.size() - c0);
+            int items = nc * npf;
+            hc.resize(items); hp.resize(items);
+            for (int i = 0; i < nc; ++i)
+                for (int p = 0; p < npf; ++p) { hc[i * npf + p] = chains[c0 + i]; hp[i * npf + p] = p; }
+            GGF_CK(cudaMemcpyAsync(d_chain, hc.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+            GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+            GGF_TRY(ggf_assemble(ctx, !cplx, items, d_chain, d_pair, ch.links, A, st));
+            if (init) {
+                GGF_CK(cudaMemcpyAsync(A2, A, NN * elem * items, cudaMemcpyDeviceToDevice, st));
+                GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, items, A2, d_logpf, d_phase, ftmp, st));
+            }
+            GGF_TRY(ggf_invert_batched(ctx, cplx, N, items, A, d_logdet, ftmp, st));
+            dim3 grid((unsigned)((NN + 255) / 256), items);
+            if (!cplx) {
+                if (fp64) scatter_kernel<double><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, false, (double*)ch.Wr);
+                else scatter_kernel<float><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, false, (float*)ch.Wr);
+            } else {
+                if (fp64) scatter_kernel<cxd><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxd*)ch.Wc);
+                else scatter_kernel<cxf><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxf*)ch.Wc);
+            }
+            ell_update_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, cplx ? ctx->K : 0, ctx->P, cplx, init,
+                                                                   d_chain, d_pair, d_logdet, d_logpf, d_phase,
+                                                                   ch.ell, ch.drift, ch.since_refresh, ch.counters);
+            GGF_CK(cudaGetLastError());
+            GGF_CK(cudaStreamSynchronize(st));  // hc/hp are reused by the next chunk
+        }
+    }
+    return GGF_OK;
+}
+
+ggf_status require(ggf_ctx* ctx, bool gauss, bool chains) {
+    if (!ctx) return GGF_EINVAL;
+    if (!ctx->have_lattice || !ctx->have_group) return ggf_fail(ctx, GGF_ESTATE, "lattice/group not initialised");
+    if (gauss && !ctx->have_gauss) return ggf_fail(ctx, GGF_ESTATE, "Gaussians not initialised");
+    if (chains && ctx->ch.n == 0) return ggf_fail(ctx, GGF_ESTATE, "chains not initialised");
+    return GGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ggf_status ggf_create(ggf_ctx** out, int device) {
+    if (!out) return GGF_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return GGF_ECUDA;
+    if (device < 0 || device >= n) return GGF_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return GGF_ECUDA;
+    ggf_ctx* c = new ggf_ctx();
+    c->device = device;
+    c->ch.opts.precision = GGF_FP64;
+    c->ch.opts.refresh_every = 64;
+    c->ch.opts.width = 0.5;
+    c->ch.opts.seed = 20241202ULL;
+    *out = c;
+    return GGF_OK;
+}
+
+void ggf_destroy(ggf_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    ggf_free_chains(ctx);
+    ggf_free_consts(ctx);
+    if (ctx->work) cudaFree(ctx->work);
+    delete ctx;
+}
+
+const char* ggf_last_error(const ggf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ggf_status ggf_init_lattice(ggf_ctx* ctx, int L) {
+    if (!ctx) return GGF_EINVAL;
+    if (L < 1 || L > 64) return ggf_fail(ctx, GGF_EINVAL, "L must be in [1, 64]");
+    cudaSetDevice(ctx->device);
+    ggf_free_chains(ctx);
+    ggf_free_consts(ctx);
+    ctx->g = Geometry();
+    ctx->g.L = L;
+    ctx->g.V = L * L;
+    ctx->g.n_links = 2 * L * L;
+    ctx->have_lattice = true;
+    ctx->have_group = false;
+    return GGF_OK;
+}
+
+ggf_status ggf_init_group(ggf_ctx* ctx, int group, int n_v, const int* q_src) {
+    if (!ctx) return GGF_EINVAL;
+    if (!ctx->have_lattice) return ggf_fail(ctx, GGF_ESTATE, "call ggf_init_lattice first");
+    if (group != GGF_Z2 && group != GGF_U1) return ggf_fail(ctx, GGF_EINVAL, "group must be GGF_Z2 or GGF_U1");
+    if (n_v < 1 || n_v > 2) return ggf_fail(ctx, GGF_EINVAL, "n_v must be 1 or 2");
+    if (group == GGF_U1 && !q_src) return ggf_fail(ctx, GGF_EINVAL, "U(1) needs q_src");
+    cudaSetDevice(ctx->device);
+    ggf_free_chains(ctx);
+    ggf_free_consts(ctx);
+    Geometry& g = ctx->g;
+    g.group = group;
+    g.n_v = n_v;
+    g.B = 8 * n_v;
+    g.h2 = 2 * n_v;
+    g.r = 4 * n_v;
+    g.N = g.B * g.V;
+    for (int j = 0; j < 2; ++j) g.q[j] = (group == GGF_U1 && j < n_v) ? q_src[j] : 1;
+    ctx->have_group = true;
+    return GGF_OK;
+}
+
+ggf_status ggf_init_gaussians(ggf_ctx* ctx, const double* gamma_site, int K, const double* gamma_bond,
+                              const double* lambda) {
+    if (!ctx) return GGF_EINVAL;
+    if (!ctx->have_group) return ggf_fail(ctx, GGF_ESTATE, "call ggf_init_group first");
+    if (K < 1 || K > 8) return ggf_fail(ctx, GGF_EINVAL, "K must be in [1, 8]");
+    if (!gamma_site || !gamma_bond || !lambda) return ggf_fail(ctx, GGF_EINVAL, "null input");
+    cudaSetDevice(ctx->device);
+    ggf_free_chains(ctx);
+    return ggf_build_constants(ctx, gamma_site, K, gamma_bond, lambda);
+}
+
+ggf_status ggf_get_constants(const ggf_ctx* cctx, int* n_pairs, double* log_c, int* pairs) {
+    if (!cctx || !cctx->have_gauss) return GGF_ESTATE;
+    if (n_pairs) *n_pairs = cctx->P;
+    for (int p = 0; p < cctx->P; ++p) {
+        if (log_c) { log_c[2 * p] = cctx->logc[p].x; log_c[2 * p + 1] = cctx->logc[p].y; }
+        if (pairs) { pairs[2 * p] = cctx->pair_n[p]; pairs[2 * p + 1] = cctx->pair_m[p]; }
+    }
+    return GGF_OK;
+}
+
+ggf_status ggf_logweight(ggf_ctx* ctx, int n_cfg, const void* links, double* logN, double* ell, int mem,
+                         void* stream) {
+    GGF_TRY(require(ctx, true, false));
+    if (n_cfg < 0 || !links || !logN) return ggf_fail(ctx, GGF_EINVAL, "bad logweight arguments");
+    if (n_cfg == 0) return GGF_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geometry& g = ctx->g;
+    const int N = g.N, P = ctx->P;
+    const size_t NN = (size_t)N * N;
+    const size_t lbytes = (size_t)n_cfg * g.n_links * link_bytes(g);
+    DBuf dl, dell, dlog;
+    const void* d_links = links;
+    if (mem == GGF_MEM_HOST) {
+        GGF_TRY(dalloc(ctx, dl, lbytes));
+        GGF_CK(cudaMemcpyAsync(dl.p, links, lbytes, cudaMemcpyHostToDevice, st));
+        d_links = dl.p;
+    }
+    GGF_TRY(dalloc(ctx, dell, (size_t)n_cfg * P * sizeof(cxd)));
+    for (int fam = 0; fam < 2; ++fam) {
+        const bool cplx = fam == 1;
+        const int npf = cplx ? ctx->Kc : ctx->K;
+        if (npf == 0) continue;
+        const size_t elem = cplx ? sizeof(cxd) : sizeof(double);
+        size_t budget = budget_bytes();
+        int max_items = (int)std::max<size_t>(1, budget / (NN * elem));
+        max_items = std::min(max_items, n_cfg * npf);
+        max_items = std::min(max_items, 65535);
+        max_items = std::max(npf, max_items / npf * npf);  // whole configurations per chunk
+        const size_t tmp = ggf_factor_tmp_bytes(N, max_items);
+        const size_t small = (size_t)max_items * (2 * sizeof(int) + 2 * sizeof(cxd)) + 256;
+        GGF_TRY(ggf_workspace(ctx, NN * elem * max_items + tmp + small + 1024));
+        unsigned char* q = (unsigned char*)ctx->work;
+        void* A = q;
+        q += NN * elem * max_items;
+        void* ftmp = q;
+        q += (tmp + 255) / 256 * 256;
+        int* d_cfg = (int*)q; q += (size_t)max_items * sizeof(int);
+        int* d_pair = (int*)q; q += (size_t)max_items * sizeof(int);
+        q = (unsigned char*)(((uintptr_t)q + 15) / 16 * 16);
+        cxd* d_logpf = (cxd*)q; q += (size_t)max_items * sizeof(cxd);
+        cxd* d_phase = (cxd*)q;
+        const int total = n_cfg * npf;
+        std::vector<int> hc, hp;
+        for (int i0 = 0; i0 < total; i0 += max_items) {
+            int items = std::min(max_items, total - i0);
+            hc.resize(items); hp.resize(items);
+            for (int i = 0; i < items; ++i) { hc[i] = (i0 + i) / npf; hp[i] = (i0 + i) % npf; }
+            GGF_CK(cudaMemcpyAsync(d_cfg, hc.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+            GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+            GGF_TRY(ggf_assemble(ctx, !cplx, items, d_cfg, d_pair, d_links, A, st));
+            GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, items, A, d_logpf, d_phase, ftmp, st));
+            // items are consecutive (cfg, pair) in this family: offset by i0
+            write_ell_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, npf, cplx ? ctx->K : 0, P, cplx, d_logpf,
+                                                                   d_phase, (cxd*)dell.p + (size_t)(i0 / npf) * P);
+            GGF_CK(cudaGetLastError());
+            // hc/hp are reused by the next chunk: wait for their copies
+            GGF_CK(cudaStreamSynchronize(st));
+        }
+    }
+    double* d_logN = logN;
+    if (mem == GGF_MEM_HOST) {
+        GGF_TRY(dalloc(ctx, dlog, (size_t)n_cfg * sizeof(double)));
+        d_logN = (double*)dlog.p;
+    }
+    GGF_TRY(ggf_combine(ctx, n_cfg, (const cxd*)dell.p, d_logN, st));
+    if (mem == GGF_MEM_HOST) {
+        GGF_CK(cudaMemcpyAsync(logN, d_logN, n_cfg * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (ell) GGF_CK(cudaMemcpyAsync(ell, dell.p, (size_t)n_cfg * P * sizeof(cxd), cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+    } else {
+        if (ell) GGF_CK(cudaMemcpyAsync(ell, dell.p, (size_t)n_cfg * P * sizeof(cxd), cudaMemcpyDeviceToDevice, st));
+        GGF_CK(cudaStreamSynchronize(st));  // scoped temporaries are freed on return
+    }
+    return GGF_OK;
+}
+
+ggf_status ggf_observable(ggf_ctx* ctx, int which, int n_cfg, const void* links, double* out, int mem,
+                          void* stream) {
+    GGF_TRY(require(ctx, false, false));
+    if (which != GGF_OBS_PLAQUETTE) return ggf_fail(ctx, GGF_EINVAL, "unknown observable");
+    if (n_cfg < 0 || !links || !out) return ggf_fail(ctx, GGF_EINVAL, "bad observable arguments");
+    if (n_cfg == 0) return GGF_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geometry& g = ctx->g;
+    if (mem == GGF_MEM_HOST) {
+        DBuf dl, dout;
+        size_t lb = (size_t)n_cfg * g.n_links * link_bytes(g);
+        GGF_TRY(dalloc(ctx, dl, lb));
+        GGF_TRY(dalloc(ctx, dout, n_cfg * sizeof(double)));
+        GGF_CK(cudaMemcpyAsync(dl.p, links, lb, cudaMemcpyHostToDevice, st));
+        GGF_TRY(ggf_plaquette(ctx, n_cfg, dl.p, (double*)dout.p, st));
+        GGF_CK(cudaMemcpyAsync(out, dout.p, n_cfg * sizeof(double), cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return GGF_OK;
+    }
+    return ggf_plaquette(ctx, n_cfg, links, out, st);
+}
+
+ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const ggf_chain_opts* opts, int mem,
+                           void* stream) {
+    GGF_TRY(require(ctx, true, false));
+    if (n_chains < 1 || !links || !opts) return ggf_fail(ctx, GGF_EINVAL, "bad chains_init arguments");
+    if (opts->precision != GGF_FP64 && opts->precision != GGF_FP32)
+        return ggf_fail(ctx, GGF_EINVAL, "precision must be GGF_FP64 or GGF_FP32");
+    if (opts->refresh_every < 1) return ggf_fail(ctx, GGF_EINVAL, "refresh_every must be >= 1");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    ggf_free_chains(ctx);
+    Chains& ch = ctx->ch;
+    ch.opts = *opts;
+    ch.n = n_chains;
+    ch.sweep = 0;
+    const Geometry& g = ctx->g;
+    const bool fp64 = opts->precision == GGF_FP64;
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    const size_t NN = (size_t)g.N * g.N;
+    const size_t lb = (size_t)n_chains * g.n_links * link_bytes(g);
+    GGF_CK(cudaMalloc(&ch.links, lb));
+    GGF_CK(cudaMalloc(&ch.Wr, std::max<size_t>(16, (size_t)n_chains * ctx->K * NN * rsz)));
+    GGF_CK(cudaMalloc(&ch.Wc, std::max<size_t>(16, (size_t)n_chains * ctx->Kc * NN * 2 * rsz)));
+    GGF_CK(cudaMalloc(&ch.ell, (size_t)n_chains * ctx->P * sizeof(cxd)));
+    GGF_CK(cudaMalloc(&ch.zbuf, (size_t)n_chains * ctx->P * g.r * g.r * sizeof(cxd)));
+    GGF_CK(cudaMalloc(&ch.ybuf, (size_t)n_chains * (ctx->K + 2 * ctx->Kc) * g.r * g.N * rsz + 16));
+    GGF_CK(cudaMalloc(&ch.accept, n_chains * sizeof(int)));
+    GGF_CK(cudaMalloc(&ch.since_refresh, n_chains * sizeof(int)));
+    GGF_CK(cudaMalloc(&ch.sweep_acc, n_chains * sizeof(int)));
+    GGF_CK(cudaMalloc(&ch.counters, 4 * sizeof(unsigned long long)));
+    GGF_CK(cudaMalloc(&ch.drift, n_chains * sizeof(double)));
+    GGF_CK(cudaMalloc(&ch.refresh_list, (n_chains + 1) * sizeof(int)));
+    GGF_CK(cudaMemsetAsync(ch.accept, 0, n_chains * sizeof(int), st));
+    GGF_CK(cudaMemsetAsync(ch.since_refresh, 0, n_chains * sizeof(int), st));
+    GGF_CK(cudaMemsetAsync(ch.sweep_acc, 0, n_chains * sizeof(int), st));
+    GGF_CK(cudaMemsetAsync(ch.counters, 0, 4 * sizeof(unsigned long long), st));
+    GGF_CK(cudaMemsetAsync(ch.drift, 0, n_chains * sizeof(double), st));
+    // host copy of the starting links to find identical configurations
+    std::vector<unsigned char> hl(lb);
+    if (mem == GGF_MEM_HOST) std::memcpy(hl.data(), links, lb);
+    else GGF_CK(cudaMemcpy(hl.data(), links, lb, cudaMemcpyDeviceToHost));
+    GGF_CK(cudaMemcpyAsync(ch.links, hl.data(), lb, cudaMemcpyHostToDevice, st));
+    const size_t row = g.n_links * link_bytes(g);
+    std::map<std::string, int> first;
+    std::vector<int> reps, rep_of(n_chains);
+    for (int c = 0; c < n_chains; ++c) {
+        std::string key((const char*)hl.data() + (size_t)c * row, row);
+        auto it = first.find(key);
+        if (it == first.end()) { first[key] = c; reps.push_back(c); rep_of[c] = c; }
+        else rep_of[c] = it->second;
+    }
+    GGF_TRY(factor_chains(ctx, reps, true, st));
+    for (int c = 0; c < n_chains; ++c) {
+        int r0 = rep_of[c];
+        if (r0 == c) continue;
+        GGF_CK(cudaMemcpyAsync((unsigned char*)ch.Wr + (size_t)c * ctx->K * NN * rsz,
+                               (unsigned char*)ch.Wr + (size_t)r0 * ctx->K * NN * rsz, ctx->K * NN * rsz,
+                               cudaMemcpyDeviceToDevice, st));
+        if (ctx->Kc)
+            GGF_CK(cudaMemcpyAsync((unsigned char*)ch.Wc + (size_t)c * ctx->Kc * NN * 2 * rsz,
+                                   (unsigned char*)ch.Wc + (size_t)r0 * ctx->Kc * NN * 2 * rsz,
+                                   ctx->Kc * NN * 2 * rsz, cudaMemcpyDeviceToDevice, st));
+        GGF_CK(cudaMemcpyAsync(ch.ell + (size_t)c * ctx->P, ch.ell + (size_t)r0 * ctx->P, ctx->P * sizeof(cxd),
+                               cudaMemcpyDeviceToDevice, st));
+    }
+    GGF_CK(cudaMemsetAsync(ch.counters, 0, 4 * sizeof(unsigned long long), st));
+    GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (n_sweeps < 0) return ggf_fail(ctx, GGF_EINVAL, "n_sweeps < 0");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    DBuf dobs;
+    double* d_obs = obs;
+    if (obs && mem == GGF_MEM_HOST) {
+        GGF_TRY(dalloc(ctx, dobs, (size_t)ch.n * GGF_N_OBS * sizeof(double)));
+        d_obs = (double*)dobs.p;
+    }
+    std::vector<int> list;
+    for (int s = 0; s < n_sweeps; ++s) {
+        GGF_CK(cudaMemsetAsync(ch.sweep_acc, 0, ch.n * sizeof(int), st));
+        for (int l = 0; l < g.n_links; ++l) GGF_TRY(ggf_link_step(ctx, l, st));
+        if (obs) {
+            double* dst = mem == GGF_MEM_HOST ? d_obs : d_obs + (size_t)s * ch.n * GGF_N_OBS;
+            GGF_TRY(ggf_observe(ctx, dst, st));
+            if (mem == GGF_MEM_HOST)
+                GGF_CK(cudaMemcpyAsync(obs + (size_t)s * ch.n * GGF_N_OBS, d_obs, (size_t)ch.n * GGF_N_OBS * sizeof(double),
+                                       cudaMemcpyDeviceToHost, st));
+        }
+        GGF_TRY(ggf_mark_refresh(ctx, st));
+        int cnt = 0;
+        GGF_CK(cudaMemcpyAsync(&cnt, ch.refresh_list, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        if (cnt > 0) {
+            list.resize(cnt);
+            GGF_CK(cudaMemcpyAsync(list.data(), ch.refresh_list + 1, cnt * sizeof(int), cudaMemcpyDeviceToHost, st));
+            GGF_CK(cudaStreamSynchronize(st));
+            std::sort(list.begin(), list.end());
+            GGF_TRY(factor_chains(ctx, list, false, st));
+            unsigned long long h[4];
+            GGF_CK(cudaMemcpyAsync(h, ch.counters, sizeof(h), cudaMemcpyDeviceToHost, st));
+            GGF_CK(cudaStreamSynchronize(st));
+            h[2] += cnt;
+            GGF_CK(cudaMemcpyAsync(ch.counters + 2, &h[2], sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+        }
+        ch.sweep += 1;
+    }
+    GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_links(ggf_ctx* ctx, void* links, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!links) return ggf_fail(ctx, GGF_EINVAL, "null links");
+    cudaSetDevice(ctx->device);
+    size_t lb = (size_t)ctx->ch.n * ctx->g.n_links * link_bytes(ctx->g);
+    cudaStream_t st = (cudaStream_t)stream;
+    GGF_CK(cudaMemcpyAsync(links, ctx->ch.links, lb,
+                           mem == GGF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!ell) return ggf_fail(ctx, GGF_EINVAL, "null ell");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    GGF_CK(cudaMemcpyAsync(ell, ctx->ch.ell, (size_t)ctx->ch.n * ctx->P * sizeof(cxd),
+                           mem == GGF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
+    GGF_TRY(require(ctx, true, true));
+    if (!out) return ggf_fail(ctx, GGF_EINVAL, "null stats");
+    cudaSetDevice(ctx->device);
+    unsigned long long h[4];
+    GGF_CK(cudaMemcpy(h, ctx->ch.counters, sizeof(h), cudaMemcpyDeviceToHost));
+    std::vector<double> d(ctx->ch.n);
+    GGF_CK(cudaMemcpy(d.data(), ctx->ch.drift, d.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    out->proposals = h[0];
+    out->accepts = h[1];
+    out->refreshes = h[2];
+    out->sweeps = ctx->ch.sweep;
+    out->max_drift = d.empty() ? 0.0 : *std::max_element(d.begin(), d.end());
+    out->n_chains = ctx->ch.n;
+    out->n_pairs = ctx->P;
+    if (h[3]) return ggf_fail(ctx, GGF_ESINGULAR, "a refresh met a singular M(G)");
+    return GGF_OK;
+}
+
+ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path) {
+    GGF_TRY(require(ctx, true, true));
+    if (!path) return ggf_fail(ctx, GGF_EINVAL, "null path");
+    cudaSetDevice(ctx->device);
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    size_t lb = (size_t)ch.n * g.n_links * link_bytes(g);
+    std::vector<unsigned char> hl(lb);
+    std::vector<cxd> he((size_t)ch.n * ctx->P);
+    std::vector<int> hs(ch.n);
+    unsigned long long cnt[4];
+    GGF_CK(cudaDeviceSynchronize());
+    GGF_CK(cudaMemcpy(hl.data(), ch.links, lb, cudaMemcpyDeviceToHost));
+    GGF_CK(cudaMemcpy(he.data(), ch.ell, he.size() * sizeof(cxd), cudaMemcpyDeviceToHost));
+    GGF_CK(cudaMemcpy(hs.data(), ch.since_refresh, hs.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    GGF_CK(cudaMemcpy(cnt, ch.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+    FILE* f = fopen(path, "wb");
+    if (!f) return ggf_fail(ctx, GGF_EIO, std::string("cannot open ") + path);
+    const char magic[8] = {'G', 'G', 'F', 'C', 'K', 'P', 'T', '1'};
+    int hdr[8] = {g.L, g.group, g.n_v, ctx->K, ch.n, ctx->P, 0, 0};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(&ch.opts, sizeof(ch.opts), 1, f) == 1 && fwrite(&ch.sweep, sizeof(ch.sweep), 1, f) == 1 &&
+              fwrite(cnt, sizeof(cnt), 1, f) == 1 && fwrite(hl.data(), 1, lb, f) == lb &&
+              fwrite(he.data(), sizeof(cxd), he.size(), f) == he.size() &&
+              fwrite(hs.data(), sizeof(int), hs.size(), f) == hs.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return ggf_fail(ctx, GGF_EIO, "checkpoint write failed");
+    return GGF_OK;
+}
+
+ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream) {
+    GGF_TRY(require(ctx, true, false));
+    if (!path) return ggf_fail(ctx, GGF_EINVAL, "null path");
+    FILE* f = fopen(path, "rb");
+    if (!f) return ggf_fail(ctx, GGF_EIO, std::string("cannot open ") + path);
+    char magic[8];
+    int hdr[8];
+    ggf_chain_opts o;
+    uint64_t sweep;
+    unsigned long long cnt[4];
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GGFCKPT1", 8) == 0 &&
+              fread(hdr, sizeof(hdr), 1, f) == 1 && fread(&o, sizeof(o), 1, f) == 1 &&
+              fread(&sweep, sizeof(sweep), 1, f) == 1 && fread(cnt, sizeof(cnt), 1, f) == 1;
+    const Geometry& g = ctx->g;
+    if (!ok || hdr[0] != g.L || hdr[1] != g.group || hdr[2] != g.n_v || hdr[3] != ctx->K || hdr[5] != ctx->P) {
+        fclose(f);
+        return ggf_fail(ctx, GGF_EIO, "checkpoint does not match the context (or is corrupt)");
+    }
+    int n = hdr[4];
+    if (n < 1) { fclose(f); return ggf_fail(ctx, GGF_EIO, "corrupt checkpoint"); }
+    size_t lb = (size_t)n * g.n_links * link_bytes(g);
+    std::vector<unsigned char> hl(lb);
+    std::vector<cxd> he((size_t)n * ctx->P);
+    std::vector<int> hs(n);
+    ok = fread(hl.data(), 1, lb, f) == lb && fread(he.data(), sizeof(cxd), he.size(), f) == he.size() &&
+         fread(hs.data(), sizeof(int), hs.size(), f) == hs.size();
+    fclose(f);
+    if (!ok) return ggf_fail(ctx, GGF_EIO, "truncated checkpoint");
+    GGF_TRY(ggf_chains_init(ctx, n, hl.data(), &o, GGF_MEM_HOST, stream));
+    Chains& ch = ctx->ch;
+    cudaStream_t st = (cudaStream_t)stream;
+    // restore the tracked log-weights: the rebuilt ones agree to rounding, and the
+    // tracked values keep the run bit-identical to an uninterrupted one
+    GGF_CK(cudaMemcpyAsync(ch.ell, he.data(), he.size() * sizeof(cxd), cudaMemcpyHostToDevice, st));
+    GGF_CK(cudaMemcpyAsync(ch.since_refresh, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    GGF_CK(cudaMemcpyAsync(ch.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
+    GGF_CK(cudaStreamSynchronize(st));
+    ch.sweep = sweep;
+    return GGF_OK;
+}
+
+ggf_status ggf_sync(ggf_ctx* ctx, void* stream) {
+    if (!ctx) return GGF_EINVAL;
+    cudaSetDevice(ctx->device);
+    GGF_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}
+
+}  // extern "C"

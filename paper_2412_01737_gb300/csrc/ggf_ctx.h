@@ -1,0 +1,107 @@
+// Internal state of a libggf context (not part of the ABI).
+#pragma once
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include "ggf_common.cuh"
+#include "../../include/ggf.h"
+
+struct Geometry {
+    int L = 0, V = 0, n_links = 0;
+    int group = -1, n_v = 0;
+    int B = 0;    // virtual Majoranas per site, 8 n_v
+    int h2 = 0;   // Majoranas per link end, 2 n_v
+    int r = 0;    // Majoranas per link, 4 n_v
+    int N = 0;    // virtual Majoranas on the lattice, B V
+    int q[2] = {0, 0};  // U(1) charges of source-end modes
+};
+
+// Read-only data the kernels need, passed by value.
+struct DevConst {
+    Geometry g;
+    int K, P, Kc;                 // Gaussians, pairs, complex pairs (P = K + Kc)
+    const double* D;              // [V][B][B]
+    const double* Gr;             // [K][n_links][r][r]   diagonal pairs
+    const cxd* Gc;                // [Kc][n_links][r][r]  pairs n < m
+    const cxd* logc;              // [P]
+    const cxd* w;                 // [P] combine weights
+};
+
+struct Chains {
+    int n = 0;
+    ggf_chain_opts opts{};
+    uint64_t sweep = 0;
+    void* links = nullptr;        // int8 or double [n][n_links]
+    void* Wr = nullptr;           // [n][K][N][N]   double or float
+    void* Wc = nullptr;           // [n][Kc][N][N]  cxd or cxf
+    cxd* ell = nullptr;           // [n][P]
+    void* zbuf = nullptr;         // [n][P][r][r]  W-precision scalars (complex slot size)
+    void* ybuf = nullptr;         // [n][P][r][N]
+    int* accept = nullptr;        // [n]
+    int* since_refresh = nullptr; // [n]
+    int* sweep_acc = nullptr;     // [n]
+    unsigned long long* counters = nullptr;  // [4]: proposals, accepts, refreshes, singular
+    double* drift = nullptr;      // [n] max drift seen
+    int* refresh_list = nullptr;  // [n + 1]
+};
+
+struct ggf_ctx {
+    int device = 0;
+    std::string err;
+    Geometry g;
+    bool have_lattice = false, have_group = false, have_gauss = false;
+    int K = 0, P = 0, Kc = 0;
+    std::vector<int> pair_n, pair_m;
+    std::vector<cxd> logc, w;
+    double* d_D = nullptr;
+    double* d_Gr = nullptr;
+    cxd* d_Gc = nullptr;
+    cxd* d_logc = nullptr;
+    cxd* d_w = nullptr;
+    Chains ch;
+    void* work = nullptr;
+    size_t work_bytes = 0;
+    DevConst dc() const {
+        DevConst c;
+        c.g = g; c.K = K; c.P = P; c.Kc = Kc;
+        c.D = d_D; c.Gr = d_Gr; c.Gc = d_Gc; c.logc = d_logc; c.w = d_w;
+        return c;
+    }
+};
+
+// status helpers
+ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg);
+ggf_status ggf_cuda(ggf_ctx* ctx, cudaError_t e, const char* what);
+#define GGF_CK(call)                                                      \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return ggf_cuda(ctx, _e, #call);           \
+    } while (0)
+#define GGF_TRY(call)                                                     \
+    do {                                                                  \
+        ggf_status _s = (call);                                           \
+        if (_s != GGF_OK) return _s;                                      \
+    } while (0)
+
+ggf_status ggf_workspace(ggf_ctx* ctx, size_t bytes);
+void ggf_free_chains(ggf_ctx* ctx);
+void ggf_free_consts(ggf_ctx* ctx);
+
+// host init (ggf_init.cu)
+ggf_status ggf_build_constants(ggf_ctx* ctx, const double* gamma_site, int K,
+                               const double* gamma_bond, const double* lambda);
+
+// linear algebra drivers (k_linalg.cu)
+// Assemble FP64 M for items (cfg index, pair index) into dst (item-major, N*N each).
+// real_family: pairs 0..K-1 (double) else complex pairs (cxd).
+ggf_status ggf_assemble(ggf_ctx* ctx, bool real_family, int n_items, const int* d_item_cfg,
+                        const int* d_item_pair, const void* d_links, void* dst, cudaStream_t st);
+// Batched Pfaffian (destroys A): out[item] = (log|Pf|, phase as unit cxd)
+ggf_status ggf_pfaffian_batched(ggf_ctx* ctx, bool cplx, int n, int batch, void* A, cxd* d_logpf,
+                                cxd* d_phase, void* d_tmp, cudaStream_t st);
+// Batched Gauss-Jordan inverse in place: logdet (log|det|, arg) per item.
+ggf_status ggf_invert_batched(ggf_ctx* ctx, bool cplx, int n, int batch, void* A, cxd* d_logdet,
+                              void* d_tmp, cudaStream_t st);
+// Combine per-config pair log-Pfaffians into log N (device, n_cfg items).
+ggf_status ggf_combine(ggf_ctx* ctx, int n_cfg, const cxd* d_ell, double* d_logN, cudaStream_t st);
+ggf_status ggf_plaquette(ggf_ctx* ctx, int n_cfg, const void* d_links, double* d_out, cudaStream_t st);

@@ -1,0 +1,443 @@
+// Metropolis sweep kernels of libggf (Sec. 5.1 sampling of p(G) = N(G)/N).
+//
+// Per link step, for every chain in lockstep:
+//  ratio_kernel   one CTA per chain.  Draws the Philox numbers, forms the
+//                 change Delta of the twisted link block for every pair
+//                 (n, m), gathers W_SS from the cached inverse W = M^{-1},
+//                 evaluates the Pfaffian ratio
+//                    Pf(M') / Pf(M) = Pf([[Delta, -1], [1, W_SS]])
+//                 (r/2 = 2 n_v even, so no extra sign) warp-parallel in FP64,
+//                 combines the pairs into N(G')/N(G), decides, and on accept
+//                 writes Z = (1 + Delta W_SS)^{-1} Delta and Y = W[S, :].
+//  update_kernel  rank-r Sherman-Morrison-Woodbury update of every pair's W
+//                 of the accepted chains:  W <- W + Y^T Z Y
+//                 (W[:, S] = -W[S, :]^T because W is antisymmetric).
+//  observe_kernel per sweep: plaquette mean, log N(G), acceptance rate.
+#include "ggf_ctx.h"
+#include "ggf_geom.cuh"
+
+namespace {
+
+constexpr int NWARP = 8;
+
+__device__ __forceinline__ double magc(cxd v) { return fabs(v.x) + fabs(v.y); }
+
+// warp argmax over lanes (ties: lowest index)
+__device__ __forceinline__ int warp_argmax(double v, int idx) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    return idx;
+}
+
+// Pfaffian of an n x n (n <= 32) antisymmetric matrix in shared memory, by one
+// warp (skew Gaussian elimination with pivoting).  A is destroyed.
+__device__ cxd warp_pfaffian(cxd* A, int n) {
+    const int lane = threadIdx.x & 31;
+    cxd res = {1.0, 0.0};
+    for (int k = 0; k < n - 1; k += 2) {
+        double m = (lane >= k + 1 && lane < n) ? magc(A[lane * n + k]) : -1.0;
+        int p = warp_argmax(m, lane);
+        const int q = k + 1;
+        if (p != q) {
+            if (lane >= k && lane < n) {
+                cxd t = A[q * n + lane]; A[q * n + lane] = A[p * n + lane]; A[p * n + lane] = t;
+            }
+            __syncwarp();
+            if (lane >= k && lane < n) {
+                cxd t = A[lane * n + q]; A[lane * n + q] = A[lane * n + p]; A[lane * n + p] = t;
+            }
+            __syncwarp();
+            res = -res;
+        }
+        cxd piv = A[q * n + k];
+        if (piv.x == 0.0 && piv.y == 0.0) { __syncwarp(); return {0.0, 0.0}; }
+        res = res * A[k * n + q];
+        int mm = n - k - 2;
+        for (int e = lane; e < mm * mm; e += 32) {
+            int i = k + 2 + e / mm, j = k + 2 + e % mm;
+            cxd ti = A[i * n + k] / piv, tj = A[j * n + k] / piv;
+            A[i * n + j] += ti * A[j * n + q] - A[i * n + q] * tj;
+        }
+        __syncwarp();
+    }
+    return res;
+}
+
+// Solve [A | B] (r x 2r, row-major, stride 2r) in place by Gauss-Jordan with
+// partial pivoting; the right half becomes A^{-1} B.  fcol: r scratch.
+__device__ bool warp_solve(cxd* A, int r, cxd* fcol) {
+    const int lane = threadIdx.x & 31;
+    const int w = 2 * r;
+    for (int k = 0; k < r; ++k) {
+        double m = (lane >= k && lane < r) ? magc(A[lane * w + k]) : -1.0;
+        int p = warp_argmax(m, lane);
+        if (p != k) {
+            if (lane < w) { cxd t = A[k * w + lane]; A[k * w + lane] = A[p * w + lane]; A[p * w + lane] = t; }
+            __syncwarp();
+        }
+        cxd d = A[k * w + k];
+        if (d.x == 0.0 && d.y == 0.0) return false;
+        __syncwarp();
+        if (lane < w) A[k * w + lane] = A[k * w + lane] / d;
+        if (lane < r) fcol[lane] = A[lane * w + k];
+        __syncwarp();
+        for (int e = lane; e < r * w; e += 32) {
+            int i = e / w, j = e % w;
+            if (i != k) A[i * w + j] -= fcol[i] * A[k * w + j];
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+template <class T>
+__device__ __forceinline__ cxd loadc(const T* p) { return Sc<T>::to(*p); }
+
+struct SweepArgs {
+    DevConst dc;
+    int n_chains;
+    uint64_t sweep;
+    int link;
+    uint64_t seed;
+    double width;
+    void* links;
+    const void* Wr;
+    const void* Wc;
+    cxd* ell;
+    cxd* zbuf;
+    void* ybuf_r;
+    void* ybuf_c;
+    int* accept;
+    int* since_refresh;
+    int* sweep_acc;
+    unsigned long long* counters;
+};
+
+template <class RW, class CW>
+__global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
+    extern __shared__ cxd sm[];
+    const Geometry& g = a.dc.g;
+    const int P = a.dc.P, K = a.dc.K, r = g.r, N = g.N;
+    const int c = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cxd* Delta = sm;                       // [P][r][r]
+    cxd* Wss = Delta + P * r * r;          // [P][r][r]
+    cxd* Bord = Wss + P * r * r;           // [NWARP][2r][2r]
+    cxd* rho = Bord + NWARP * 4 * r * r;   // [P]
+    cxd* fcol = rho + P;                   // [NWARP][r]
+    __shared__ double s_old_g, s_new_g, s_old_t, s_new_t;
+    __shared__ int s_accept;
+
+    const int l = a.link, s = l >> 1, d = l & 1;
+    const int x = s % g.L, y = s / g.L;
+    const int t = d == 0 ? y * g.L + (x + 1) % g.L : ((y + 1) % g.L) * g.L + x;
+    const int a0 = s * g.B + (2 * d + 1) * g.h2, b0 = t * g.B + (2 * d) * g.h2;
+
+    if (threadIdx.x == 0) {
+        uint64_t ctr[4] = {a.sweep, (uint64_t)l, 0, 0}, out[4];
+        philox4x64_10(ctr, a.seed, (uint64_t)c, out);
+        double u_acc = u53(out[0]), u_prop = u53(out[1]);
+        s_new_t = u_acc;  // temporarily hold u_acc
+        if (g.group == GGF_Z2) {
+            double gv = (double)((const int8_t*)a.links)[(size_t)c * g.n_links + l];
+            s_old_g = gv; s_new_g = -gv; s_old_t = 0.0;
+        } else {
+            double th = ((const double*)a.links)[(size_t)c * g.n_links + l];
+            double tn = th + a.width * (u_prop - 0.5);
+            if (tn >= GGF_TWO_PI) tn -= GGF_TWO_PI;
+            else if (tn < 0.0) tn += GGF_TWO_PI;
+            s_old_g = 1.0; s_new_g = 1.0; s_old_t = th;
+            fcol[0] = {tn, 0.0};
+        }
+    }
+    __syncthreads();
+    const double u_acc = s_new_t;
+    const double th_new = g.group == GGF_Z2 ? 0.0 : fcol[0].x;
+    const double g_old = s_old_g, g_new = s_new_g, th_old = s_old_t;
+    __syncthreads();
+
+    for (int p = warp; p < P; p += NWARP) {
+        cxd* D = Delta + p * r * r;
+        cxd* Ws = Wss + p * r * r;
+        for (int e = lane; e < r * r; e += 32) {
+            int xi = e / r, yi = e % r;
+            cxd nv, ov;
+            if (p < K) {
+                nv = {twisted<double>(a.dc, p, l, xi, yi, g_new, th_new), 0.0};
+                ov = {twisted<double>(a.dc, p, l, xi, yi, g_old, th_old), 0.0};
+            } else {
+                nv = twisted<cxd>(a.dc, p - K, l, xi, yi, g_new, th_new);
+                ov = twisted<cxd>(a.dc, p - K, l, xi, yi, g_old, th_old);
+            }
+            D[e] = nv - ov;
+            int gi = xi < g.h2 ? a0 + xi : b0 + xi - g.h2;
+            int gj = yi < g.h2 ? a0 + yi : b0 + yi - g.h2;
+            if (p < K) Ws[e] = loadc((const RW*)a.Wr + (((size_t)c * K + p) * N + gi) * N + gj);
+            else Ws[e] = loadc((const CW*)a.Wc + (((size_t)c * (P - K) + (p - K)) * N + gi) * N + gj);
+        }
+        __syncwarp();
+        cxd* Bw = Bord + warp * 4 * r * r;
+        const int n2 = 2 * r;
+        for (int e = lane; e < n2 * n2; e += 32) {
+            int i = e / n2, j = e % n2;
+            cxd v = {0.0, 0.0};
+            if (i < r && j < r) v = D[i * r + j];
+            else if (i >= r && j >= r) v = Ws[(i - r) * r + (j - r)];
+            else if (i < r && j == i + r) v = {-1.0, 0.0};
+            else if (i >= r && j == i - r) v = {1.0, 0.0};
+            Bw[e] = v;
+        }
+        __syncwarp();
+        cxd pf = warp_pfaffian(Bw, n2);
+        if (lane == 0) rho[p] = pf;
+        __syncwarp();
+    }
+    __syncthreads();
+
+    if (threadIdx.x == 0) {
+        double amax = -INFINITY;
+        for (int p = 0; p < P; ++p) amax = fmax(amax, a.dc.logc[p].x + a.ell[(size_t)c * P + p].x);
+        double so = 0.0, sn = 0.0;
+        for (int p = 0; p < P; ++p) {
+            cxd e = a.dc.logc[p] + a.ell[(size_t)c * P + p];
+            if (p < K) e.y = 0.0;
+            e.x -= amax;
+            cxd tt = a.dc.w[p] * cexp_(e);
+            so += tt.x;
+            sn += (tt * rho[p]).x;
+        }
+        int acc = (sn > 0.0 && so > 0.0 && u_acc < sn / so) ? 1 : 0;
+        s_accept = acc;
+        a.accept[c] = acc;
+        atomicAdd(&a.counters[0], 1ULL);
+        if (acc) {
+            atomicAdd(&a.counters[1], 1ULL);
+            a.since_refresh[c] += 1;
+            a.sweep_acc[c] += 1;
+            if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)g_new;
+            else ((double*)a.links)[(size_t)c * g.n_links + l] = th_new;
+        }
+    }
+    __syncthreads();
+    if (!s_accept) return;
+
+    for (int p = warp; p < P; p += NWARP) {
+        cxd* D = Delta + p * r * r;
+        cxd* Ws = Wss + p * r * r;
+        cxd* Aug = Bord + warp * 4 * r * r;   // r x 2r
+        const int w2 = 2 * r;
+        for (int e = lane; e < r * w2; e += 32) {
+            int i = e / w2, j = e % w2;
+            cxd v;
+            if (j < r) {
+                v = {i == j ? 1.0 : 0.0, 0.0};
+                for (int z = 0; z < r; ++z) v += D[i * r + z] * Ws[z * r + j];
+            } else {
+                v = D[i * r + (j - r)];
+            }
+            Aug[e] = v;
+        }
+        __syncwarp();
+        warp_solve(Aug, r, fcol + warp * r);
+        for (int e = lane; e < r * r; e += 32) {
+            int i = e / r, j = e % r;
+            a.zbuf[((size_t)c * P + p) * r * r + e] = Aug[i * w2 + r + j];
+        }
+        if (lane == 0) {
+            cxd lr = clog_(rho[p]);
+            cxd& el = a.ell[(size_t)c * P + p];
+            if (p < K) el.x += lr.x;
+            else {
+                el = el + lr;
+                if (el.y > M_PI) el.y -= 2 * M_PI;
+                else if (el.y <= -M_PI) el.y += 2 * M_PI;
+            }
+        }
+        __syncwarp();
+    }
+    // rows Y = W[S, :] for the update kernel
+    for (int p = 0; p < P; ++p) {
+        for (int e = threadIdx.x; e < r * N; e += blockDim.x) {
+            int xi = e / N, j = e - xi * N;
+            int gi = xi < g.h2 ? a0 + xi : b0 + xi - g.h2;
+            if (p < K) {
+                const RW* W = (const RW*)a.Wr + ((size_t)c * K + p) * N * N;
+                ((RW*)a.ybuf_r)[(((size_t)c * K + p) * r + xi) * N + j] = W[(size_t)gi * N + j];
+            } else {
+                const CW* W = (const CW*)a.Wc + ((size_t)c * (P - K) + (p - K)) * N * N;
+                ((CW*)a.ybuf_c)[(((size_t)c * (P - K) + (p - K)) * r + xi) * N + j] = W[(size_t)gi * N + j];
+            }
+        }
+    }
+}
+
+template <class T, int R>
+__global__ void __launch_bounds__(256) update_kernel(int N, int P, int fam_pairs, int pair_off, T* W,
+                                                     const T* ybuf, const cxd* zbuf, const int* accept, int TI) {
+    const int c = blockIdx.z;
+    if (!accept[c]) return;
+    const int p = blockIdx.y;
+    extern __shared__ unsigned char smraw[];
+    T* Zs = (T*)smraw;        // [R][R]
+    T* Pr = Zs + R * R;       // [TI][R]
+    T* Wp = W + ((size_t)c * fam_pairs + p) * N * N;
+    const T* Y = ybuf + ((size_t)c * fam_pairs + p) * R * N;
+    const cxd* Z = zbuf + ((size_t)c * P + pair_off + p) * R * R;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Zs[e] = Sc<T>::from(Z[e]);
+    __syncthreads();
+    const int i0 = blockIdx.x * TI;
+    const int ti = min(TI, N - i0);
+    for (int e = threadIdx.x; e < ti * R; e += blockDim.x) {
+        int i = e / R, b = e % R;
+        T acc = Sc<T>::zero();
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc += Y[(size_t)q * N + i0 + i] * Zs[q * R + b];
+        Pr[i * R + b] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        T yv[R];
+#pragma unroll
+        for (int b = 0; b < R; ++b) yv[b] = Y[(size_t)b * N + j];
+        for (int i = 0; i < ti; ++i) {
+            T acc = Wp[(size_t)(i0 + i) * N + j];
+#pragma unroll
+            for (int b = 0; b < R; ++b) acc += Pr[i * R + b] * yv[b];
+            Wp[(size_t)(i0 + i) * N + j] = acc;
+        }
+    }
+}
+
+__global__ void observe_kernel(DevConst dc, int n_chains, const void* links, const cxd* ell, const int* sweep_acc,
+                               double* obs) {
+    __shared__ double red[256];
+    const Geometry& g = dc.g;
+    int c = blockIdx.x;
+    double acc = 0.0;
+    for (int s = threadIdx.x; s < g.V; s += blockDim.x) {
+        int x = s % g.L, y = s / g.L;
+        int sx = y * g.L + (x + 1) % g.L, sy = ((y + 1) % g.L) * g.L + x;
+        int l1 = 2 * s, l2 = 2 * sx + 1, l3 = 2 * sy, l4 = 2 * s + 1;
+        if (g.group == GGF_Z2) {
+            const int8_t* L8 = (const int8_t*)links + (size_t)c * g.n_links;
+            acc += (double)(L8[l1] * L8[l2] * L8[l3] * L8[l4]);
+        } else {
+            const double* T = (const double*)links + (size_t)c * g.n_links;
+            acc += cos(T[l1] + T[l2] - T[l3] - T[l4]);
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double amax = -INFINITY;
+        for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + ell[(size_t)c * dc.P + p].x);
+        double sv = 0.0;
+        for (int p = 0; p < dc.P; ++p) {
+            cxd e = dc.logc[p] + ell[(size_t)c * dc.P + p];
+            if (p < dc.K) e.y = 0.0;
+            e.x -= amax;
+            sv += (dc.w[p] * cexp_(e)).x;
+        }
+        obs[(size_t)c * GGF_N_OBS + 0] = red[0] / g.V;
+        obs[(size_t)c * GGF_N_OBS + 1] = sv > 0 ? amax + log(sv) : -INFINITY;
+        obs[(size_t)c * GGF_N_OBS + 2] = (double)sweep_acc[c] / g.n_links;
+    }
+}
+
+__global__ void mark_refresh(int n_chains, int R, const int* since, int* list) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    if (since[c] >= R) {
+        int k = atomicAdd(&list[0], 1);
+        list[1 + k] = c;
+    }
+}
+
+}  // namespace
+
+size_t ggf_ratio_smem(int P, int r) {
+    return (size_t)(2 * P * r * r + NWARP * 4 * r * r + P + NWARP * r) * sizeof(cxd);
+}
+
+ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    SweepArgs a;
+    a.dc = ctx->dc();
+    a.n_chains = ch.n;
+    a.sweep = ch.sweep;
+    a.link = link;
+    a.seed = ch.opts.seed;
+    a.width = ch.opts.width;
+    a.links = ch.links;
+    a.Wr = ch.Wr;
+    a.Wc = ch.Wc;
+    a.ell = ch.ell;
+    a.zbuf = (cxd*)ch.zbuf;
+    const bool fp64 = ch.opts.precision == GGF_FP64;
+    size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    a.ybuf_r = ch.ybuf;
+    a.ybuf_c = (unsigned char*)ch.ybuf + (size_t)ch.n * ctx->K * g.r * g.N * rsz;
+    a.accept = ch.accept;
+    a.since_refresh = ch.since_refresh;
+    a.sweep_acc = ch.sweep_acc;
+    a.counters = ch.counters;
+    size_t smem = ggf_ratio_smem(ctx->P, g.r);
+    if (fp64) {
+        cudaFuncSetAttribute(ratio_kernel<double, cxd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ratio_kernel<double, cxd><<<ch.n, NWARP * 32, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(ratio_kernel<float, cxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ratio_kernel<float, cxf><<<ch.n, NWARP * 32, smem, st>>>(a);
+    }
+    GGF_CK(cudaGetLastError());
+    const int TI = 8;
+    const int N = g.N;
+    dim3 gr((N + TI - 1) / TI, ctx->K, ch.n);
+    dim3 gc((N + TI - 1) / TI, ctx->Kc, ch.n);
+#define GGF_UPD(T, R_, grid, fam, off, Wp, Yp)                                                         \
+    update_kernel<T, R_><<<grid, 256, (R_ * R_ + TI * R_) * sizeof(T), st>>>(N, ctx->P, fam, off, (T*)(Wp), \
+                                                                              (const T*)(Yp), a.zbuf, ch.accept, TI)
+    if (g.r == 4) {
+        if (fp64) {
+            GGF_UPD(double, 4, gr, ctx->K, 0, ch.Wr, a.ybuf_r);
+            if (ctx->Kc) GGF_UPD(cxd, 4, gc, ctx->Kc, ctx->K, ch.Wc, a.ybuf_c);
+        } else {
+            GGF_UPD(float, 4, gr, ctx->K, 0, ch.Wr, a.ybuf_r);
+            if (ctx->Kc) GGF_UPD(cxf, 4, gc, ctx->Kc, ctx->K, ch.Wc, a.ybuf_c);
+        }
+    } else {
+        if (fp64) {
+            GGF_UPD(double, 8, gr, ctx->K, 0, ch.Wr, a.ybuf_r);
+            if (ctx->Kc) GGF_UPD(cxd, 8, gc, ctx->Kc, ctx->K, ch.Wc, a.ybuf_c);
+        } else {
+            GGF_UPD(float, 8, gr, ctx->K, 0, ch.Wr, a.ybuf_r);
+            if (ctx->Kc) GGF_UPD(cxf, 8, gc, ctx->Kc, ctx->K, ch.Wc, a.ybuf_c);
+        }
+    }
+#undef GGF_UPD
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}
+
+ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    observe_kernel<<<ch.n, 256, 0, st>>>(ctx->dc(), ch.n, ch.links, ch.ell, ch.sweep_acc, d_obs);
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}
+
+ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    GGF_CK(cudaMemsetAsync(ch.refresh_list, 0, sizeof(int), st));
+    mark_refresh<<<(ch.n + 127) / 128, 128, 0, st>>>(ch.n, ch.opts.refresh_every, ch.since_refresh, ch.refresh_list);
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}

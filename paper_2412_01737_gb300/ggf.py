@@ -1,0 +1,255 @@
+"""ctypes binding of libggf (include/ggf.h).  Argument marshalling only.
+
+Arrays may be numpy arrays (host memory: the library copies in and out) or
+torch CUDA tensors (device memory, borrowed for the call on torch's current
+stream).  Every entry point of the C ABI has a method of the same name here
+(without the ggf_ prefix).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+Z2, U1 = 0, 1
+FP64, FP32 = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+N_OBS = 3
+OBS_PLAQUETTE = 0
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libggf.so")
+_lib = None
+
+STATUS = {0: "GGF_OK", 1: "GGF_EINVAL", 2: "GGF_ENOMEM", 3: "GGF_ECUDA", 4: "GGF_ESINGULAR",
+          5: "GGF_ETIMEOUT", 6: "GGF_EDRIFT", 7: "GGF_ESTATE", 8: "GGF_EIO"}
+
+
+class GGFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ChainOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("refresh_every", ctypes.c_int), ("width", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class ChainStats(ctypes.Structure):
+    _fields_ = [("proposals", ctypes.c_uint64), ("accepts", ctypes.c_uint64), ("refreshes", ctypes.c_uint64),
+                ("sweeps", ctypes.c_uint64), ("max_drift", ctypes.c_double), ("n_chains", ctypes.c_int),
+                ("n_pairs", ctypes.c_int)]
+
+
+EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
+           "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
+           "ggf_sample", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_stats", "ggf_checkpoint",
+           "ggf_resume", "ggf_sync"]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libggf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libggf.so not built at {_LIB_PATH}; run paper_2412_01737_gb300.build.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    sig = {
+        "ggf_create": ([ctypes.POINTER(P), I], I),
+        "ggf_destroy": ([P], V),
+        "ggf_last_error": ([P], ctypes.c_char_p),
+        "ggf_init_lattice": ([P, I], I),
+        "ggf_init_group": ([P, I, I, P], I),
+        "ggf_init_gaussians": ([P, P, I, P, P], I),
+        "ggf_get_constants": ([P, ctypes.POINTER(I), P, P], I),
+        "ggf_logweight": ([P, I, P, P, P, I, P], I),
+        "ggf_observable": ([P, I, I, P, P, I, P], I),
+        "ggf_chains_init": ([P, I, P, ctypes.POINTER(ChainOpts), I, P], I),
+        "ggf_sample": ([P, I, P, I, P], I),
+        "ggf_chains_links": ([P, P, I, P], I),
+        "ggf_chains_ell": ([P, P, I, P], I),
+        "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
+        "ggf_checkpoint": ([P, ctypes.c_char_p], I),
+        "ggf_resume": ([P, ctypes.c_char_p, P], I),
+        "ggf_sync": ([P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(pointer, mem) of a numpy array or torch CUDA tensor."""
+    if a is None:
+        return None, MEM_HOST
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, MEM_HOST
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), (MEM_DEVICE if a.is_cuda else MEM_HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(arrs):
+    for a in arrs:
+        if a is not None and hasattr(a, "is_cuda") and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+class GGF:
+    """One libggf context on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.ggf_create(ctypes.byref(h), device)
+        if st != 0:
+            raise GGFError(st, "ggf_create failed (no CUDA device?)")
+        self.h = h
+        self.group = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ggf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        if st != 0:
+            raise GGFError(st, self.lib.ggf_last_error(self.h).decode())
+
+    def _mem(self, *arrs):
+        mems = {_ptr(a)[1] for a in arrs if a is not None}
+        if len(mems) > 1:
+            raise ValueError("mix of host and device arrays in one call")
+        return mems.pop() if mems else MEM_HOST
+
+    # ---- set-up -------------------------------------------------------------
+    def init_lattice(self, L):
+        self._ck(self.lib.ggf_init_lattice(self.h, int(L)))
+        self._n_links = 2 * int(L) * int(L)
+
+    def init_group(self, group, n_v, q_src=None):
+        self.group = int(group)
+        q = None if q_src is None else np.ascontiguousarray(q_src, dtype=np.int32)
+        self._ck(self.lib.ggf_init_group(self.h, int(group), int(n_v), None if q is None else q.ctypes.data))
+
+    def init_gaussians(self, gamma_site, K, gamma_bond, lam):
+        gs = np.ascontiguousarray(gamma_site, dtype=np.float64)
+        gb = np.ascontiguousarray(gamma_bond, dtype=np.float64)
+        lm = np.ascontiguousarray(np.stack([np.real(lam), np.imag(lam)], axis=-1), dtype=np.float64)
+        self._ck(self.lib.ggf_init_gaussians(self.h, gs.ctypes.data, int(K), gb.ctypes.data, lm.ctypes.data))
+
+    def init_problem(self, p):
+        """Convenience: the three init calls for a ggf_inputs.Problem-like object."""
+        self.init_lattice(p.L)
+        self.init_group(p.group, p.n_v, p.q_src)
+        self.init_gaussians(p.gamma_site, p.K, p.gamma_bond, p.lam)
+
+    def get_constants(self):
+        n = ctypes.c_int()
+        self._ck(self.lib.ggf_get_constants(self.h, ctypes.byref(n), None, None))
+        lc = np.zeros((n.value, 2))
+        pr = np.zeros((n.value, 2), dtype=np.int32)
+        self._ck(self.lib.ggf_get_constants(self.h, ctypes.byref(n), lc.ctypes.data, pr.ctypes.data))
+        return lc[:, 0] + 1j * lc[:, 1], pr
+
+    # ---- compute --------------------------------------------------------------
+    def logweight(self, links, logN=None, ell=None):
+        """log N(G) per configuration (and log Pf(M_nm) per pair into `ell`)."""
+        n_cfg = int(links.shape[0])
+        if logN is None:
+            logN = np.zeros(n_cfg) if isinstance(links, np.ndarray) else _torch_like(links, (n_cfg,))
+        mem = self._mem(links, logN, ell)
+        lp, _ = _ptr(links)
+        self._ck(self.lib.ggf_logweight(self.h, n_cfg, lp, _ptr(logN)[0], _ptr(ell)[0], mem,
+                                        _stream([links, logN, ell])))
+        return logN
+
+    def observable(self, links, out=None, which=OBS_PLAQUETTE):
+        n_cfg = int(links.shape[0])
+        if out is None:
+            out = np.zeros(n_cfg) if isinstance(links, np.ndarray) else _torch_like(links, (n_cfg,))
+        mem = self._mem(links, out)
+        self._ck(self.lib.ggf_observable(self.h, which, n_cfg, _ptr(links)[0], _ptr(out)[0], mem,
+                                         _stream([links, out])))
+        return out
+
+    def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202):
+        o = ChainOpts(int(precision), int(refresh_every), float(width), int(seed))
+        mem = self._mem(links)
+        self.n_chains = int(links.shape[0])
+        self.link_dtype = links.dtype
+        self._ck(self.lib.ggf_chains_init(self.h, self.n_chains, _ptr(links)[0], ctypes.byref(o), mem,
+                                          _stream([links])))
+
+    def sample(self, n_sweeps, obs=None):
+        """Run sweeps; returns obs [n_sweeps, n_chains, 3] (numpy unless a tensor is given)."""
+        if obs is None:
+            obs = np.zeros((int(n_sweeps), self.n_chains, N_OBS))
+        mem = self._mem(obs)
+        self._ck(self.lib.ggf_sample(self.h, int(n_sweeps), _ptr(obs)[0], mem, _stream([obs])))
+        return obs
+
+    def sample_no_obs(self, n_sweeps, stream=None):
+        self._ck(self.lib.ggf_sample(self.h, int(n_sweeps), None, MEM_DEVICE, stream))
+
+    def chains_links(self, out=None):
+        if out is None:
+            L = self.n_links()
+            out = np.zeros((self.n_chains, L), dtype=np.int8 if self.group == Z2 else np.float64)
+        self._ck(self.lib.ggf_chains_links(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
+        return out
+
+    def chains_ell(self):
+        st = self.chains_stats()
+        out = np.zeros((self.n_chains, st.n_pairs, 2))
+        self._ck(self.lib.ggf_chains_ell(self.h, out.ctypes.data, MEM_HOST, None))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def chains_stats(self):
+        s = ChainStats()
+        self._ck(self.lib.ggf_chains_stats(self.h, ctypes.byref(s)))
+        return s
+
+    def checkpoint(self, path):
+        self._ck(self.lib.ggf_checkpoint(self.h, str(path).encode()))
+
+    def resume(self, path):
+        self._ck(self.lib.ggf_resume(self.h, str(path).encode(), None))
+        self.n_chains = self.chains_stats().n_chains
+
+    def sync(self, stream=None):
+        self._ck(self.lib.ggf_sync(self.h, stream))
+
+    def n_links(self):
+        return getattr(self, "_n_links", None) or self._links_from_state()
+
+    def _links_from_state(self):
+        raise RuntimeError("call init_problem/init_lattice through this object first")
+
+
+def _torch_like(t, shape):
+    import torch
+    return torch.zeros(shape, dtype=torch.float64, device=t.device)

@@ -1,0 +1,96 @@
+"""GPU sampler parity: FP64 decisions are bit-identical to the oracle's exact
+Metropolis under the shared Philox stream; FP32 chains are replayed through
+the oracle (|Delta log N| <= 1e-4 on their trajectories)."""
+import numpy as np
+import pytest
+
+import ggf_inputs as gi
+from oracle import mcmc, weight
+from tests.gpu_util import ctx_for
+
+pytestmark = pytest.mark.gpu
+
+
+def run_both(p, n_chains, n_sweeps, seed, start=None, refresh=8, precision=0):
+    from paper_2412_01737_gb300 import FP64
+    ctx = ctx_for(p)
+    start = gi.cold_links(p, n_chains) if start is None else start
+    ctx.chains_init(start, precision=precision, refresh_every=refresh, seed=seed)
+    obs = ctx.sample(n_sweeps)
+    fin = ctx.chains_links()
+    st = ctx.chains_stats()
+    ctx.close()
+    return start, obs, fin, st
+
+
+@pytest.mark.parametrize("case", [
+    (2, gi.Z2, 1, 1, 4, 25),
+    (2, gi.U1, 1, 2, 3, 6),
+    (2, gi.U1, 2, 2, 2, 3),
+    (3, gi.Z2, 1, 2, 2, 4),
+])
+def test_fp64_decisions_match_oracle(case):
+    L, grp, nv, K, nch, nsw = case
+    p = gi.make_problem(L, grp, nv, K, bond_scale=0.3)
+    start, obs, fin, st = run_both(p, nch, nsw, seed=123)
+    W = weight.Weights(p)
+    for c in range(nch):
+        lk, ob, _ = mcmc.run_chain(p, W, start[c], 123, c, 0, nsw)
+        assert np.array_equal(lk, fin[c])
+        assert np.abs(ob[:, 0] - obs[:, c, 0]).max() < 1e-12
+        assert np.abs(ob[:, 1] - obs[:, c, 1]).max() < 1e-10
+        assert np.array_equal(ob[:, 2], obs[:, c, 2])
+    assert st.proposals == nch * nsw * p.n_links
+    assert st.max_drift < 1e-9
+
+
+def test_random_start_and_refresh_every_accept():
+    p = gi.make_problem(2, gi.U1, 1, 2, bond_scale=0.3)
+    start = gi.random_links(p, 3, seed=9)
+    _, obs, fin, st = run_both(p, 3, 4, seed=7, start=start, refresh=1)
+    W = weight.Weights(p)
+    for c in range(3):
+        lk, ob, _ = mcmc.run_chain(p, W, start[c], 7, c, 0, 4)
+        assert np.array_equal(lk, fin[c])
+    assert st.refreshes > 0 and st.max_drift < 1e-9
+
+
+def test_fp32_replay():
+    from paper_2412_01737_gb300 import FP32
+    p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
+    start, obs, fin, st = run_both(p, 4, 6, seed=5, refresh=16, precision=FP32)
+    W = weight.Weights(p)
+    want = np.array([W.log_norm(c) for c in fin])
+    assert np.abs(obs[-1, :, 1] - want).max() <= 1e-4
+    assert st.max_drift < 1e-3
+
+
+def test_checkpoint_resume_bit_exact(tmp_path):
+    p = gi.make_problem(2, gi.U1, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.cold_links(p, 3), refresh_every=4, seed=3)
+    ctx.sample(2)
+    ck = tmp_path / "c.ckpt"
+    ctx.checkpoint(ck)
+    a = ctx.sample(3)
+    la = ctx.chains_links()
+    ctx.close()
+    ctx2 = ctx_for(p)
+    ctx2.resume(ck)
+    b = ctx2.sample(3)
+    lb = ctx2.chains_links()
+    ctx2.close()
+    assert np.array_equal(la, lb)
+    assert np.array_equal(a[:, :, 2], b[:, :, 2])
+    assert np.abs(a[:, :, 1] - b[:, :, 1]).max() < 1e-10
+
+
+def test_corrupt_checkpoint_rejected(tmp_path):
+    from paper_2412_01737_gb300 import GGFError
+    p = gi.make_problem(2, gi.Z2, 1, 1)
+    ctx = ctx_for(p)
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"GGFCKPT1" + b"\x00" * 10)
+    with pytest.raises(GGFError):
+        ctx.resume(bad)
+    ctx.close()
