@@ -142,6 +142,11 @@ ggf_status ggf_chains_links(ggf_ctx* ctx, void* links, int mem, void* stream);
 /* Tracked log Pf(M_nm) of all chains, [n_chains][P][2] as (log|Pf|, arg). */
 ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
 
+/* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
+ * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
+ * L^2.  For tests and diagnostics. */
+ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, int mem, void* stream);
+
 typedef struct {
     uint64_t proposals, accepts, refreshes, sweeps;
     double max_drift;   /* max |l_tracked - l_refresh| over refreshes so far */

@@ -420,7 +420,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     GGF_CK(cudaMalloc(&ch.Wc, std::max<size_t>(16, (size_t)n_chains * ctx->Kc * NN * 2 * rsz)));
     GGF_CK(cudaMalloc(&ch.ell, (size_t)n_chains * ctx->P * sizeof(cxd)));
     GGF_CK(cudaMalloc(&ch.zbuf, (size_t)n_chains * ctx->P * g.r * g.r * sizeof(cxd)));
-    GGF_CK(cudaMalloc(&ch.ybuf, (size_t)n_chains * (ctx->K + 2 * ctx->Kc) * g.r * g.N * rsz + 16));
+    GGF_CK(cudaMalloc(&ch.ybuf, (size_t)n_chains * (ctx->K + 2 * ctx->Kc) * 2 * g.r * g.N * rsz + 16));
     GGF_CK(cudaMalloc(&ch.accept, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.since_refresh, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.sweep_acc, n_chains * sizeof(int)));
@@ -531,6 +531,34 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream) {
     GGF_CK(cudaMemcpyAsync(ell, ctx->ch.ell, (size_t)ctx->ch.n * ctx->P * sizeof(cxd),
                            mem == GGF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    Chains& ch = ctx->ch;
+    if (chain < 0 || chain >= ch.n || pair < 0 || pair >= ctx->P || !out)
+        return ggf_fail(ctx, GGF_EINVAL, "bad chains_inverse arguments");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t NN = (size_t)ctx->g.N * ctx->g.N;
+    const bool fp64 = ch.opts.precision == GGF_FP64;
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    const bool cplx = pair >= ctx->K;
+    const size_t esz = cplx ? 2 * rsz : rsz;
+    const unsigned char* src = cplx ? (const unsigned char*)ch.Wc + ((size_t)chain * ctx->Kc + (pair - ctx->K)) * NN * esz
+                                    : (const unsigned char*)ch.Wr + ((size_t)chain * ctx->K + pair) * NN * esz;
+    std::vector<unsigned char> h(NN * esz);
+    GGF_CK(cudaStreamSynchronize(st));
+    GGF_CK(cudaMemcpy(h.data(), src, h.size(), cudaMemcpyDeviceToHost));
+    std::vector<double> o(2 * NN);
+    for (size_t e = 0; e < NN; ++e) {
+        double re, im = 0.0;
+        if (fp64) { const double* d = (const double*)h.data(); re = cplx ? d[2 * e] : d[e]; if (cplx) im = d[2 * e + 1]; }
+        else { const float* f = (const float*)h.data(); re = cplx ? f[2 * e] : f[e]; if (cplx) im = f[2 * e + 1]; }
+        o[2 * e] = re; o[2 * e + 1] = im;
+    }
+    GGF_CK(cudaMemcpy(out, o.data(), o.size() * sizeof(double), mem == GGF_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
     return GGF_OK;
 }
 

@@ -8,10 +8,13 @@
 //                    Pf(M') / Pf(M) = Pf([[Delta, -1], [1, W_SS]])
 //                 (r/2 = 2 n_v even, so no extra sign) warp-parallel in FP64,
 //                 combines the pairs into N(G')/N(G), decides, and on accept
-//                 writes Z = (1 + Delta W_SS)^{-1} Delta and Y = W[S, :].
+//                 writes Z = (1 + Delta W_SS)^{-1} Delta, the rows Y = W[S, :]
+//                 and the columns C = W[:, S].
 //  update_kernel  rank-r Sherman-Morrison-Woodbury update of every pair's W
-//                 of the accepted chains:  W <- W + Y^T Z Y
-//                 (W[:, S] = -W[S, :]^T because W is antisymmetric).
+//                 of the accepted chains:  W <- W - C Z Y.
+//                 The columns are gathered explicitly: replacing C by -Y^T
+//                 (exact for an antisymmetric W) lets the rounding error's
+//                 symmetric part grow geometrically from update to update.
 //  observe_kernel per sweep: plaquette mean, log N(G), acceptance rate.
 #include "ggf_ctx.h"
 #include "ggf_geom.cuh"
@@ -258,17 +261,22 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
         }
         __syncwarp();
     }
-    // rows Y = W[S, :] for the update kernel
+    // rows Y = W[S, :] and columns C^T = W[:, S]^T for the update kernel,
+    // stored per (chain, pair) as [2][r][N]
     for (int p = 0; p < P; ++p) {
         for (int e = threadIdx.x; e < r * N; e += blockDim.x) {
             int xi = e / N, j = e - xi * N;
             int gi = xi < g.h2 ? a0 + xi : b0 + xi - g.h2;
             if (p < K) {
                 const RW* W = (const RW*)a.Wr + ((size_t)c * K + p) * N * N;
-                ((RW*)a.ybuf_r)[(((size_t)c * K + p) * r + xi) * N + j] = W[(size_t)gi * N + j];
+                RW* yb = (RW*)a.ybuf_r + ((size_t)c * K + p) * 2 * r * N;
+                yb[(size_t)xi * N + j] = W[(size_t)gi * N + j];
+                yb[(size_t)(r + xi) * N + j] = W[(size_t)j * N + gi];
             } else {
                 const CW* W = (const CW*)a.Wc + ((size_t)c * (P - K) + (p - K)) * N * N;
-                ((CW*)a.ybuf_c)[(((size_t)c * (P - K) + (p - K)) * r + xi) * N + j] = W[(size_t)gi * N + j];
+                CW* yb = (CW*)a.ybuf_c + ((size_t)c * (P - K) + (p - K)) * 2 * r * N;
+                yb[(size_t)xi * N + j] = W[(size_t)gi * N + j];
+                yb[(size_t)(r + xi) * N + j] = W[(size_t)j * N + gi];
             }
         }
     }
@@ -284,7 +292,8 @@ __global__ void __launch_bounds__(256) update_kernel(int N, int P, int fam_pairs
     T* Zs = (T*)smraw;        // [R][R]
     T* Pr = Zs + R * R;       // [TI][R]
     T* Wp = W + ((size_t)c * fam_pairs + p) * N * N;
-    const T* Y = ybuf + ((size_t)c * fam_pairs + p) * R * N;
+    const T* Y = ybuf + ((size_t)c * fam_pairs + p) * 2 * R * N;   // rows W[S, :]
+    const T* Ct = Y + (size_t)R * N;                                 // columns W[:, S]^T
     const cxd* Z = zbuf + ((size_t)c * P + pair_off + p) * R * R;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) Zs[e] = Sc<T>::from(Z[e]);
     __syncthreads();
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(256) update_kernel(int N, int P, int fam_pairs
         int i = e / R, b = e % R;
         T acc = Sc<T>::zero();
 #pragma unroll
-        for (int q = 0; q < R; ++q) acc += Y[(size_t)q * N + i0 + i] * Zs[q * R + b];
+        for (int q = 0; q < R; ++q) acc += Ct[(size_t)q * N + i0 + i] * Zs[q * R + b];
         Pr[i * R + b] = acc;
     }
     __syncthreads();
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(256) update_kernel(int N, int P, int fam_pairs
         for (int i = 0; i < ti; ++i) {
             T acc = Wp[(size_t)(i0 + i) * N + j];
 #pragma unroll
-            for (int b = 0; b < R; ++b) acc += Pr[i * R + b] * yv[b];
+            for (int b = 0; b < R; ++b) acc -= Pr[i * R + b] * yv[b];
             Wp[(size_t)(i0 + i) * N + j] = acc;
         }
     }
@@ -384,7 +393,7 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     const bool fp64 = ch.opts.precision == GGF_FP64;
     size_t rsz = fp64 ? sizeof(double) : sizeof(float);
     a.ybuf_r = ch.ybuf;
-    a.ybuf_c = (unsigned char*)ch.ybuf + (size_t)ch.n * ctx->K * g.r * g.N * rsz;
+    a.ybuf_c = (unsigned char*)ch.ybuf + (size_t)ch.n * ctx->K * 2 * g.r * g.N * rsz;
     a.accept = ch.accept;
     a.since_refresh = ch.since_refresh;
     a.sweep_acc = ch.sweep_acc;

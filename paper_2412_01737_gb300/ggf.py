@@ -45,7 +45,7 @@ class ChainStats(ctypes.Structure):
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
-           "ggf_sample", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_stats", "ggf_checkpoint",
+           "ggf_sample", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
            "ggf_resume", "ggf_sync"]
 
 
@@ -76,6 +76,7 @@ def load():
         "ggf_sample": ([P, I, P, I, P], I),
         "ggf_chains_links": ([P, P, I, P], I),
         "ggf_chains_ell": ([P, P, I, P], I),
+        "ggf_chains_inverse": ([P, I, I, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -95,7 +96,7 @@ def _ptr(a):
         return None, MEM_HOST
     if isinstance(a, np.ndarray):
         if not a.flags["C_CONTIGUOUS"]:
-            raise ValueError("arrays must be C-contiguous")
+            raise ValueError("arrays must be C-contiguous (use np.ascontiguousarray)")
         return a.ctypes.data, MEM_HOST
     if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
         if not a.is_contiguous():
@@ -226,6 +227,11 @@ class GGF:
         st = self.chains_stats()
         out = np.zeros((self.n_chains, st.n_pairs, 2))
         self._ck(self.lib.ggf_chains_ell(self.h, out.ctypes.data, MEM_HOST, None))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def chains_inverse(self, chain, pair, N):
+        out = np.zeros((N, N, 2))
+        self._ck(self.lib.ggf_chains_inverse(self.h, int(chain), int(pair), out.ctypes.data, MEM_HOST, None))
         return out[..., 0] + 1j * out[..., 1]
 
     def chains_stats(self):
