@@ -117,6 +117,12 @@ typedef struct {
     int refresh_every;  /* full FP64 refresh of a chain after this many accepts */
     double width;       /* U(1) proposal: theta += width * (u - 1/2) */
     uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = chain index) */
+    int delay;          /* <= 1: apply every accepted update to W at once;
+                           k > 1: keep up to k accepted rank-r updates pending
+                           as panels U (N x k r), V (k r x N), with
+                           W_eff = W - U V, and fold them into W with one
+                           rank-(k r) product every k link steps (delayed
+                           Sherman-Morrison-Woodbury updates). */
 } ggf_chain_opts;
 
 /* Create n_chains Markov chains starting at links [n_chains][2V] and build
@@ -150,6 +156,7 @@ ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, in
 typedef struct {
     uint64_t proposals, accepts, refreshes, sweeps;
     double max_drift;   /* max |l_tracked - l_refresh| over refreshes so far */
+    uint64_t launches;  /* CUDA kernels launched by ggf_sample since ggf_chains_init */
     int n_chains, n_pairs;
 } ggf_chain_stats;
 
@@ -160,6 +167,22 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out);
  * chains make the same decisions as uninterrupted ones. */
 ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path);
 ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
+
+/* Kernel timing with CUDA events recorded on the launching stream, for
+ * benchmarks.  ggf_profile(ctx, 1) starts recording events around every
+ * ratio launch (GGF_KT_RATIO), every immediate rank-r update or delayed-mode
+ * row/column gather launch group (GGF_KT_UPDATE), every refresh
+ * (GGF_KT_REFRESH) and every delayed-update flush (GGF_KT_FLUSH) issued by
+ * ggf_sample, and resets the totals; ggf_profile(ctx, 0) stops.
+ * ggf_kernel_time returns the accumulated device milliseconds and the number
+ * of timed launch groups since the last reset.  Events are read at the end of
+ * each sweep. */
+#define GGF_KT_RATIO 0
+#define GGF_KT_UPDATE 1
+#define GGF_KT_REFRESH 2
+#define GGF_KT_FLUSH 3
+ggf_status ggf_profile(ggf_ctx* ctx, int enable);
+ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launches);
 
 /* Wait for the context's work on `stream` and report device-side errors. */
 ggf_status ggf_sync(ggf_ctx* ctx, void* stream);

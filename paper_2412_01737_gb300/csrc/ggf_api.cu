@@ -11,6 +11,7 @@ size_t ggf_factor_tmp_bytes(int n, int batch);
 ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st);
 ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st);
 ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st);
+ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -36,7 +37,7 @@ ggf_status ggf_workspace(ggf_ctx* ctx, size_t bytes) {
 void ggf_free_chains(ggf_ctx* ctx) {
     Chains& c = ctx->ch;
     void* ptrs[] = {c.links, c.Wr, c.Wc, c.ell, c.zbuf, c.ybuf, c.accept, c.since_refresh,
-                    c.sweep_acc, c.counters, c.drift, c.refresh_list};
+                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Ur, c.Vr, c.Uc, c.Vc, c.pend};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ggf_chain_opts o = c.opts;
@@ -189,6 +190,7 @@ ggf_status factor_chains(ggf_ctx* ctx, const std::vector<int>& chains, bool init
                 if (fp64) scatter_kernel<cxd><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxd*)ch.Wc);
                 else scatter_kernel<cxf><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxf*)ch.Wc);
             }
+            ctx->launches += 2;
             ell_update_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, cplx ? ctx->K : 0, ctx->P, cplx, init,
                                                                    d_chain, d_pair, d_logdet, d_logpf, d_phase,
                                                                    ch.ell, ch.drift, ch.since_refresh, ch.counters);
@@ -234,6 +236,7 @@ void ggf_destroy(ggf_ctx* ctx) {
     ggf_free_chains(ctx);
     ggf_free_consts(ctx);
     if (ctx->work) cudaFree(ctx->work);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -420,7 +423,21 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     GGF_CK(cudaMalloc(&ch.Wc, std::max<size_t>(16, (size_t)n_chains * ctx->Kc * NN * 2 * rsz)));
     GGF_CK(cudaMalloc(&ch.ell, (size_t)n_chains * ctx->P * sizeof(cxd)));
     GGF_CK(cudaMalloc(&ch.zbuf, (size_t)n_chains * ctx->P * g.r * g.r * sizeof(cxd)));
-    GGF_CK(cudaMalloc(&ch.ybuf, (size_t)n_chains * (ctx->K + 2 * ctx->Kc) * 2 * g.r * g.N * rsz + 16));
+    ch.kmax = opts->delay > 1 ? opts->delay : 1;
+    if (ch.kmax > 16) return ggf_fail(ctx, GGF_EINVAL, "delay must be <= 16");
+    ch.steps_since_flush = 0;
+    if (ch.kmax > 1) {
+        const size_t pr = (size_t)n_chains * ch.kmax * g.r * g.N * rsz;
+        GGF_CK(cudaMalloc(&ch.Ur, std::max<size_t>(16, pr * ctx->K)));
+        GGF_CK(cudaMalloc(&ch.Vr, std::max<size_t>(16, pr * ctx->K)));
+        GGF_CK(cudaMalloc(&ch.Uc, std::max<size_t>(16, pr * 2 * ctx->Kc)));
+        GGF_CK(cudaMalloc(&ch.Vc, std::max<size_t>(16, pr * 2 * ctx->Kc)));
+        GGF_CK(cudaMalloc(&ch.ybuf, 16));
+    } else {
+        GGF_CK(cudaMalloc(&ch.ybuf, (size_t)n_chains * (ctx->K + 2 * ctx->Kc) * 2 * g.r * g.N * rsz + 16));
+    }
+    GGF_CK(cudaMalloc(&ch.pend, n_chains * sizeof(int)));
+    GGF_CK(cudaMemsetAsync(ch.pend, 0, n_chains * sizeof(int), st));
     GGF_CK(cudaMalloc(&ch.accept, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.since_refresh, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.sweep_acc, n_chains * sizeof(int)));
@@ -462,6 +479,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     }
     GGF_CK(cudaMemsetAsync(ch.counters, 0, 4 * sizeof(unsigned long long), st));
     GGF_CK(cudaStreamSynchronize(st));
+    ctx->launches = 0;
     return GGF_OK;
 }
 
@@ -479,9 +497,23 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
         d_obs = (double*)dobs.p;
     }
     std::vector<int> list;
+    auto drain_events = [&]() -> ggf_status {
+        for (size_t k = 0; k + 2 < ctx->ev_cat.size(); k += 3) {
+            float ms = 0;
+            GGF_CK(cudaEventElapsedTime(&ms, ctx->ev[ctx->ev_cat[k + 1]], ctx->ev[ctx->ev_cat[k + 2]]));
+            ctx->kt_ms[ctx->ev_cat[k]] += ms;
+            ctx->kt_n[ctx->ev_cat[k]] += 1;
+        }
+        ctx->ev_cat.clear();
+        ctx->ev_used = 0;
+        return GGF_OK;
+    };
     for (int s = 0; s < n_sweeps; ++s) {
         GGF_CK(cudaMemsetAsync(ch.sweep_acc, 0, ch.n * sizeof(int), st));
+        ctx->ev_used = 0;
+        ctx->ev_cat.clear();
         for (int l = 0; l < g.n_links; ++l) GGF_TRY(ggf_link_step(ctx, l, st));
+        GGF_TRY(ggf_flush(ctx, st));   // pending delayed updates before observables and refresh
         if (obs) {
             double* dst = mem == GGF_MEM_HOST ? d_obs : d_obs + (size_t)s * ch.n * GGF_N_OBS;
             GGF_TRY(ggf_observe(ctx, dst, st));
@@ -493,12 +525,17 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
         int cnt = 0;
         GGF_CK(cudaMemcpyAsync(&cnt, ch.refresh_list, sizeof(int), cudaMemcpyDeviceToHost, st));
         GGF_CK(cudaStreamSynchronize(st));
+        GGF_TRY(drain_events());
         if (cnt > 0) {
             list.resize(cnt);
             GGF_CK(cudaMemcpyAsync(list.data(), ch.refresh_list + 1, cnt * sizeof(int), cudaMemcpyDeviceToHost, st));
             GGF_CK(cudaStreamSynchronize(st));
             std::sort(list.begin(), list.end());
+            const int r0 = ctx->prof_mark(st);
             GGF_TRY(factor_chains(ctx, list, false, st));
+            ctx->prof_pair(GGF_KT_REFRESH, r0, ctx->prof_mark(st));
+            GGF_CK(cudaStreamSynchronize(st));
+            GGF_TRY(drain_events());
             unsigned long long h[4];
             GGF_CK(cudaMemcpyAsync(h, ch.counters, sizeof(h), cudaMemcpyDeviceToHost, st));
             GGF_CK(cudaStreamSynchronize(st));
@@ -576,6 +613,7 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     out->sweeps = ctx->ch.sweep;
     out->max_drift = d.empty() ? 0.0 : *std::max_element(d.begin(), d.end());
     out->n_chains = ctx->ch.n;
+    out->launches = ctx->launches;
     out->n_pairs = ctx->P;
     if (h[3]) return ggf_fail(ctx, GGF_ESINGULAR, "a refresh met a singular M(G)");
     return GGF_OK;
@@ -649,6 +687,22 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream) {
     GGF_CK(cudaMemcpyAsync(ch.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
     GGF_CK(cudaStreamSynchronize(st));
     ch.sweep = sweep;
+    return GGF_OK;
+}
+
+ggf_status ggf_profile(ggf_ctx* ctx, int enable) {
+    if (!ctx) return GGF_EINVAL;
+    ctx->prof = enable != 0;
+    for (int k = 0; k < 4; ++k) { ctx->kt_ms[k] = 0; ctx->kt_n[k] = 0; }
+    ctx->ev_cat.clear();
+    ctx->ev_used = 0;
+    return GGF_OK;
+}
+
+ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launches) {
+    if (!ctx || which < 0 || which > 3) return GGF_EINVAL;
+    if (ms) *ms = ctx->kt_ms[which];
+    if (launches) *launches = ctx->kt_n[which];
     return GGF_OK;
 }
 

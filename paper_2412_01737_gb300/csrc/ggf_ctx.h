@@ -43,6 +43,13 @@ struct Chains {
     unsigned long long* counters = nullptr;  // [4]: proposals, accepts, refreshes, singular
     double* drift = nullptr;      // [n] max drift seen
     int* refresh_list = nullptr;  // [n + 1]
+    // delayed updates (opts.delay > 1): per chain and pair, U^T and V panels
+    // [n][pairs][kmax r][N] in W precision, pending count per chain
+    void* Ur = nullptr; void* Vr = nullptr;
+    void* Uc = nullptr; void* Vc = nullptr;
+    int* pend = nullptr;          // [n]
+    int kmax = 1;
+    int steps_since_flush = 0;
 };
 
 struct ggf_ctx {
@@ -61,6 +68,29 @@ struct ggf_ctx {
     Chains ch;
     void* work = nullptr;
     size_t work_bytes = 0;
+    // event timing (ggf_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;            // event pool
+    std::vector<int> ev_cat;                // category of each recorded (start, end) pair
+    int ev_used = 0;                        // events recorded this sweep
+    double kt_ms[4] = {0, 0, 0, 0};
+    unsigned long long kt_n[4] = {0, 0, 0, 0};
+    // record one event (returns its index, or -1 when profiling is off)
+    int prof_mark(cudaStream_t st) {
+        if (!prof) return -1;
+        if (ev_used == (int)ev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            ev.push_back(e);
+        }
+        cudaEventRecord(ev[ev_used], st);
+        return ev_used++;
+    }
+    void prof_pair(int cat, int a, int b) {
+        if (a < 0 || b < 0) return;
+        ev_cat.push_back(cat); ev_cat.push_back(a); ev_cat.push_back(b);
+    }
+    unsigned long long launches = 0;   // kernels launched by ggf_sample
     DevConst dc() const {
         DevConst c;
         c.g = g; c.K = K; c.P = P; c.Kc = Kc;

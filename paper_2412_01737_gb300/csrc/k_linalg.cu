@@ -303,6 +303,7 @@ ggf_status run_pfaffian(ggf_ctx* ctx, int n, int batch, T* A, cxd* logpf, cxd* p
     T* cv = tv + (size_t)batch * n;
     PfAcc* acc = (PfAcc*)(cv + (size_t)batch * n);
     acc_init<<<(batch + 127) / 128, 128, 0, st>>>(acc, batch);
+    ctx->launches += 2 + (n / 2) + (n / 2 - 1);
     for (int k = 0; k < n - 1; k += 2) {
         pf_pivot<T><<<batch, 256, 0, st>>>(A, n, k, tv, cv, acc);
         int m = n - k - 2;
@@ -323,6 +324,7 @@ ggf_status run_invert(ggf_ctx* ctx, int n, int batch, T* A, cxd* logdet, void* t
     int* piv = (int*)(col + (size_t)batch * n);
     PfAcc* acc = (PfAcc*)(piv + (size_t)batch * n + ((size_t)batch * n) % 2);
     acc_init<<<(batch + 127) / 128, 128, 0, st>>>(acc, batch);
+    ctx->launches += 3 + 2 * (unsigned long long)n;
     int tiles = (n + TILE - 1) / TILE;
     for (int k = 0; k < n; ++k) {
         gj_pivot<T><<<batch, 256, 0, st>>>(A, n, k, col, piv, acc);
@@ -346,6 +348,7 @@ ggf_status ggf_assemble(ggf_ctx* ctx, bool real_family, int n_items, const int* 
     if (n_items == 0) return GGF_OK;
     size_t NN = (size_t)ctx->g.N * ctx->g.N;
     dim3 grid((unsigned)((NN + 255) / 256), n_items);
+    ctx->launches += 1;
     if (real_family)
         assemble_kernel<double><<<grid, 256, 0, st>>>(ctx->dc(), d_item_cfg, d_item_pair, d_links, (double*)dst);
     else

@@ -117,6 +117,13 @@ struct SweepArgs {
     int* since_refresh;
     int* sweep_acc;
     unsigned long long* counters;
+    // delayed updates
+    const void* Ur;
+    const void* Vr;
+    const void* Uc;
+    const void* Vc;
+    int* pend;
+    int kmax;   // > 1: delayed
 };
 
 template <class RW, class CW>
@@ -178,8 +185,26 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
             D[e] = nv - ov;
             int gi = xi < g.h2 ? a0 + xi : b0 + xi - g.h2;
             int gj = yi < g.h2 ? a0 + yi : b0 + yi - g.h2;
-            if (p < K) Ws[e] = loadc((const RW*)a.Wr + (((size_t)c * K + p) * N + gi) * N + gj);
-            else Ws[e] = loadc((const CW*)a.Wc + (((size_t)c * (P - K) + (p - K)) * N + gi) * N + gj);
+            cxd wv;
+            if (p < K) wv = loadc((const RW*)a.Wr + (((size_t)c * K + p) * N + gi) * N + gj);
+            else wv = loadc((const CW*)a.Wc + (((size_t)c * (P - K) + (p - K)) * N + gi) * N + gj);
+            if (a.kmax > 1) {
+                // pending updates: W_eff[S, S] = W[S, S] - U[S, :] V[:, S]
+                const int kr = a.pend[c] * r;
+                const size_t pb = (p < K ? ((size_t)c * K + p) : ((size_t)c * (P - K) + (p - K))) * a.kmax * r;
+                for (int q = 0; q < kr; ++q) {
+                    cxd u, v;
+                    if (p < K) {
+                        u = loadc((const RW*)a.Ur + (pb + q) * N + gi);
+                        v = loadc((const RW*)a.Vr + (pb + q) * N + gj);
+                    } else {
+                        u = loadc((const CW*)a.Uc + (pb + q) * N + gi);
+                        v = loadc((const CW*)a.Vc + (pb + q) * N + gj);
+                    }
+                    wv -= u * v;
+                }
+            }
+            Ws[e] = wv;
         }
         __syncwarp();
         cxd* Bw = Bord + warp * 4 * r * r;
@@ -217,6 +242,7 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
         a.accept[c] = acc;
         atomicAdd(&a.counters[0], 1ULL);
         if (acc) {
+            if (a.kmax > 1) a.pend[c] += 1;
             atomicAdd(&a.counters[1], 1ULL);
             a.since_refresh[c] += 1;
             a.sweep_acc[c] += 1;
@@ -262,7 +288,8 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
         __syncwarp();
     }
     // rows Y = W[S, :] and columns C^T = W[:, S]^T for the update kernel,
-    // stored per (chain, pair) as [2][r][N]
+    // stored per (chain, pair) as [2][r][N] (delayed mode: gather_kernel)
+    if (a.kmax > 1) return;
     for (int p = 0; p < P; ++p) {
         for (int e = threadIdx.x; e < r * N; e += blockDim.x) {
             int xi = e / N, j = e - xi * N;
@@ -320,6 +347,131 @@ __global__ void __launch_bounds__(256) update_kernel(int N, int P, int fam_pairs
     }
 }
 
+// Delayed mode, accepted chains: rows Y = W_eff[S, :] and columns
+// C = W_eff[:, S] of the effective inverse W_eff = W - U V, then the new
+// panel entries U[:, slot] = C Z and V[slot, :] = Y.
+// Grid (ceil(N / 128), family pairs, chains), 128 threads, one index each.
+template <class T, int R>
+__global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_pairs, int pair_off, int link,
+                                                     const T* W, T* Ut, T* V, const cxd* zbuf,
+                                                     const int* accept, const int* pend, int kmax) {
+    const int c = blockIdx.z;
+    if (!accept[c]) return;
+    const int p = blockIdx.y, N = g.N;
+    const int slot = pend[c] - 1, kr = slot * R;
+    extern __shared__ unsigned char smraw[];
+    T* UtS = (T*)smraw;            // [kr][R]  U[S_a, q]
+    T* VS = UtS + kmax * R * R;    // [kr][R]  V[q, S_a]
+    T* Zs = VS + kmax * R * R;     // [R][R]
+    __shared__ int S[R];
+    const int s = link >> 1, d = link & 1, x = s % g.L, y = s / g.L;
+    const int t = d == 0 ? y * g.L + (x + 1) % g.L : ((y + 1) % g.L) * g.L + x;
+    const int a0 = s * g.B + (2 * d + 1) * g.h2, b0 = t * g.B + (2 * d) * g.h2;
+    if (threadIdx.x < R) S[threadIdx.x] = threadIdx.x < g.h2 ? a0 + threadIdx.x : b0 + threadIdx.x - g.h2;
+    __syncthreads();
+    const size_t base = ((size_t)c * fam_pairs + p);
+    const T* Wp = W + base * N * N;
+    T* Up = Ut + base * kmax * R * N;
+    T* Vp = V + base * kmax * R * N;
+    const cxd* Z = zbuf + ((size_t)c * P + pair_off + p) * R * R;
+    for (int e = threadIdx.x; e < kr * R; e += blockDim.x) {
+        int q = e / R, a = e % R;
+        UtS[e] = Up[(size_t)q * N + S[a]];
+        VS[e] = Vp[(size_t)q * N + S[a]];
+    }
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Zs[e] = Sc<T>::from(Z[e]);
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    T yv[R], cv[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        yv[a] = Wp[(size_t)S[a] * N + j];
+        cv[a] = Wp[(size_t)j * N + S[a]];
+    }
+    for (int q = 0; q < kr; ++q) {
+        T vq = Vp[(size_t)q * N + j];
+        T uq = Up[(size_t)q * N + j];
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            yv[a] -= UtS[q * R + a] * vq;
+            cv[a] -= uq * VS[q * R + a];
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+        T u = Sc<T>::zero();
+#pragma unroll
+        for (int a = 0; a < R; ++a) u += cv[a] * Zs[a * R + b];
+        Up[(size_t)(kr + b) * N + j] = u;
+        Vp[(size_t)(kr + b) * N + j] = yv[b];
+    }
+}
+
+// W <- W - U V over the pending panels (rank pend[c] * R), SIMT tiled product.
+// Grid (tiles_i * tiles_j, family pairs, chains), 256 threads as 16 x 16, each
+// a 4 x 4 block of a 64 x 64 tile of W.
+template <class T, int R>
+__global__ void __launch_bounds__(256) flush_kernel(int N, int fam_pairs, T* W, const T* Ut, const T* V,
+                                                    const int* pend, int kmax, int tiles) {
+    const int c = blockIdx.z;
+    const int kc = pend[c];
+    if (kc == 0) return;
+    const int kr = kc * R;
+    const int p = blockIdx.y;
+    const int ti = blockIdx.x / tiles, tj = blockIdx.x - ti * tiles;
+    const int i0 = ti * 64, j0 = tj * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    __shared__ T As[16][64];
+    __shared__ T Bs[16][64];
+    const size_t base = ((size_t)c * fam_pairs + p);
+    T* Wp = W + base * N * N;
+    const T* Up = Ut + base * kmax * R * N;
+    const T* Vp = V + base * kmax * R * N;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = Sc<T>::zero();
+    for (int q0 = 0; q0 < kr; q0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            int qq = e >> 6, k = e & 63;
+            int q = q0 + qq;
+            As[qq][k] = (q < kr && i0 + k < N) ? Up[(size_t)q * N + i0 + k] : Sc<T>::zero();
+            Bs[qq][k] = (q < kr && j0 + k < N) ? Vp[(size_t)q * N + j0 + k] : Sc<T>::zero();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int qq = 0; qq < 16; ++qq) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[qq][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[qq][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        int i = i0 + ty * 4 + a;
+        if (i >= N) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int j = j0 + tx * 4 + b;
+            if (j < N) Wp[(size_t)i * N + j] -= acc[a][b];
+        }
+    }
+}
+
+__global__ void reset_pend(int n, int* pend) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) pend[c] = 0;
+}
+
 __global__ void observe_kernel(DevConst dc, int n_chains, const void* links, const cxd* ell, const int* sweep_acc,
                                double* obs) {
     __shared__ double red[256];
@@ -371,6 +523,8 @@ __global__ void mark_refresh(int n_chains, int R, const int* since, int* list) {
 
 }  // namespace
 
+ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
+
 size_t ggf_ratio_smem(int P, int r) {
     return (size_t)(2 * P * r * r + NWARP * 4 * r * r + P + NWARP * r) * sizeof(cxd);
 }
@@ -398,7 +552,12 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     a.since_refresh = ch.since_refresh;
     a.sweep_acc = ch.sweep_acc;
     a.counters = ch.counters;
+    a.Ur = ch.Ur; a.Vr = ch.Vr; a.Uc = ch.Uc; a.Vc = ch.Vc;
+    a.pend = ch.pend;
+    a.kmax = ch.kmax;
     size_t smem = ggf_ratio_smem(ctx->P, g.r);
+    const int ev0 = ctx->prof_mark(st);
+    ctx->launches += 2 + (ctx->Kc ? 1 : 0);
     if (fp64) {
         cudaFuncSetAttribute(ratio_kernel<double, cxd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         ratio_kernel<double, cxd><<<ch.n, NWARP * 32, smem, st>>>(a);
@@ -407,8 +566,38 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
         ratio_kernel<float, cxf><<<ch.n, NWARP * 32, smem, st>>>(a);
     }
     GGF_CK(cudaGetLastError());
-    const int TI = 8;
+    const int ev1 = ctx->prof_mark(st);
+    ctx->prof_pair(GGF_KT_RATIO, ev0, ev1);
     const int N = g.N;
+    if (ch.kmax > 1) {
+        dim3 gg((N + 127) / 128, ctx->K, ch.n), gc2((N + 127) / 128, ctx->Kc, ch.n);
+#define GGF_GATH(T, R_, grid, fam, off, Wp, Up, Vp)                                                           \
+    gather_kernel<T, R_><<<grid, 128, (2 * ch.kmax * R_ * R_ + R_ * R_) * sizeof(T), st>>>(                 \
+        g, ctx->P, fam, off, link, (const T*)(Wp), (T*)(Up), (T*)(Vp), a.zbuf, ch.accept, ch.pend, ch.kmax)
+        if (g.r == 4) {
+            if (fp64) {
+                GGF_GATH(double, 4, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
+                if (ctx->Kc) GGF_GATH(cxd, 4, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+            } else {
+                GGF_GATH(float, 4, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
+                if (ctx->Kc) GGF_GATH(cxf, 4, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+            }
+        } else {
+            if (fp64) {
+                GGF_GATH(double, 8, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
+                if (ctx->Kc) GGF_GATH(cxd, 8, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+            } else {
+                GGF_GATH(float, 8, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
+                if (ctx->Kc) GGF_GATH(cxf, 8, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+            }
+        }
+#undef GGF_GATH
+        GGF_CK(cudaGetLastError());
+        ctx->prof_pair(GGF_KT_UPDATE, ev1, ctx->prof_mark(st));
+        if (++ch.steps_since_flush >= ch.kmax) GGF_TRY(ggf_flush(ctx, st));
+        return GGF_OK;
+    }
+    const int TI = 8;
     dim3 gr((N + TI - 1) / TI, ctx->K, ch.n);
     dim3 gc((N + TI - 1) / TI, ctx->Kc, ch.n);
 #define GGF_UPD(T, R_, grid, fam, off, Wp, Yp)                                                         \
@@ -433,11 +622,39 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     }
 #undef GGF_UPD
     GGF_CK(cudaGetLastError());
+    ctx->prof_pair(GGF_KT_UPDATE, ev1, ctx->prof_mark(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    if (ch.kmax <= 1 || ch.steps_since_flush == 0) return GGF_OK;
+    const bool fp64 = ch.opts.precision == GGF_FP64;
+    const int N = g.N, tiles = (N + 63) / 64;
+    const int ev0 = ctx->prof_mark(st);
+    dim3 gr(tiles * tiles, ctx->K, ch.n), gc(tiles * tiles, ctx->Kc, ch.n);
+#define GGF_FL(T, R_, grid, fam, Wp, Up, Vp) \
+    flush_kernel<T, R_><<<grid, 256, 0, st>>>(N, fam, (T*)(Wp), (const T*)(Up), (const T*)(Vp), ch.pend, ch.kmax, tiles)
+    if (g.r == 4) {
+        if (fp64) { GGF_FL(double, 4, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxd, 4, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
+        else { GGF_FL(float, 4, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxf, 4, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
+    } else {
+        if (fp64) { GGF_FL(double, 8, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxd, 8, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
+        else { GGF_FL(float, 8, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxf, 8, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
+    }
+#undef GGF_FL
+    ctx->prof_pair(GGF_KT_FLUSH, ev0, ctx->prof_mark(st));
+    reset_pend<<<(ch.n + 127) / 128, 128, 0, st>>>(ch.n, ch.pend);
+    ctx->launches += 2 + (ctx->Kc ? 1 : 0);
+    GGF_CK(cudaGetLastError());
+    ch.steps_since_flush = 0;
     return GGF_OK;
 }
 
 ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st) {
     Chains& ch = ctx->ch;
+    ctx->launches += 1;
     observe_kernel<<<ch.n, 256, 0, st>>>(ctx->dc(), ch.n, ch.links, ch.ell, ch.sweep_acc, d_obs);
     GGF_CK(cudaGetLastError());
     return GGF_OK;
@@ -446,6 +663,7 @@ ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st) {
 ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st) {
     Chains& ch = ctx->ch;
     GGF_CK(cudaMemsetAsync(ch.refresh_list, 0, sizeof(int), st));
+    ctx->launches += 1;
     mark_refresh<<<(ch.n + 127) / 128, 128, 0, st>>>(ch.n, ch.opts.refresh_every, ch.since_refresh, ch.refresh_list);
     GGF_CK(cudaGetLastError());
     return GGF_OK;

@@ -17,6 +17,7 @@ FP64, FP32 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 N_OBS = 3
 OBS_PLAQUETTE = 0
+KT_RATIO, KT_UPDATE, KT_REFRESH, KT_FLUSH = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libggf.so")
@@ -34,19 +35,19 @@ class GGFError(RuntimeError):
 
 class ChainOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refresh_every", ctypes.c_int), ("width", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("delay", ctypes.c_int)]
 
 
 class ChainStats(ctypes.Structure):
     _fields_ = [("proposals", ctypes.c_uint64), ("accepts", ctypes.c_uint64), ("refreshes", ctypes.c_uint64),
-                ("sweeps", ctypes.c_uint64), ("max_drift", ctypes.c_double), ("n_chains", ctypes.c_int),
-                ("n_pairs", ctypes.c_int)]
+                ("sweeps", ctypes.c_uint64), ("max_drift", ctypes.c_double), ("launches", ctypes.c_uint64),
+                ("n_chains", ctypes.c_int), ("n_pairs", ctypes.c_int)]
 
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
-           "ggf_resume", "ggf_sync"]
+           "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync"]
 
 
 def lib_path() -> str:
@@ -80,6 +81,8 @@ def load():
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
+        "ggf_profile": ([P, I], I),
+        "ggf_kernel_time": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)], I),
         "ggf_sync": ([P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -197,8 +200,8 @@ class GGF:
                                          _stream([links, out])))
         return out
 
-    def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202):
-        o = ChainOpts(int(precision), int(refresh_every), float(width), int(seed))
+    def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202, delay=1):
+        o = ChainOpts(int(precision), int(refresh_every), float(width), int(seed), int(delay))
         mem = self._mem(links)
         self.n_chains = int(links.shape[0])
         self.link_dtype = links.dtype
@@ -245,6 +248,15 @@ class GGF:
     def resume(self, path):
         self._ck(self.lib.ggf_resume(self.h, str(path).encode(), None))
         self.n_chains = self.chains_stats().n_chains
+
+    def profile(self, enable=True):
+        self._ck(self.lib.ggf_profile(self.h, 1 if enable else 0))
+
+    def kernel_time(self, which):
+        """(milliseconds, launches) accumulated since profile(True)."""
+        ms, n = ctypes.c_double(), ctypes.c_uint64()
+        self._ck(self.lib.ggf_kernel_time(self.h, int(which), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def sync(self, stream=None):
         self._ck(self.lib.ggf_sync(self.h, stream))

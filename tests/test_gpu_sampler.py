@@ -11,11 +11,10 @@ from tests.gpu_util import ctx_for
 pytestmark = pytest.mark.gpu
 
 
-def run_both(p, n_chains, n_sweeps, seed, start=None, refresh=8, precision=0):
-    from paper_2412_01737_gb300 import FP64
+def run_both(p, n_chains, n_sweeps, seed, start=None, refresh=8, precision=0, delay=1):
     ctx = ctx_for(p)
     start = gi.cold_links(p, n_chains) if start is None else start
-    ctx.chains_init(start, precision=precision, refresh_every=refresh, seed=seed)
+    ctx.chains_init(start, precision=precision, refresh_every=refresh, seed=seed, delay=delay)
     obs = ctx.sample(n_sweeps)
     fin = ctx.chains_links()
     st = ctx.chains_stats()
@@ -23,16 +22,18 @@ def run_both(p, n_chains, n_sweeps, seed, start=None, refresh=8, precision=0):
     return start, obs, fin, st
 
 
+@pytest.mark.parametrize("delay", [1, 4])
 @pytest.mark.parametrize("case", [
     (2, gi.Z2, 1, 1, 4, 25),
     (2, gi.U1, 1, 2, 3, 6),
     (2, gi.U1, 2, 2, 2, 3),
     (3, gi.Z2, 1, 2, 2, 4),
+    (4, gi.U1, 2, 3, 2, 2),
 ])
-def test_fp64_decisions_match_oracle(case):
+def test_fp64_decisions_match_oracle(case, delay):
     L, grp, nv, K, nch, nsw = case
     p = gi.make_problem(L, grp, nv, K, bond_scale=0.3)
-    start, obs, fin, st = run_both(p, nch, nsw, seed=123)
+    start, obs, fin, st = run_both(p, nch, nsw, seed=123, delay=delay)
     W = weight.Weights(p)
     for c in range(nch):
         lk, ob, _ = mcmc.run_chain(p, W, start[c], 123, c, 0, nsw)
@@ -55,20 +56,35 @@ def test_random_start_and_refresh_every_accept():
     assert st.refreshes > 0 and st.max_drift < 1e-9
 
 
-def test_fp32_replay():
+@pytest.mark.parametrize("delay", [1, 8])
+def test_fp32_replay(delay):
     from paper_2412_01737_gb300 import FP32
     p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
-    start, obs, fin, st = run_both(p, 4, 6, seed=5, refresh=16, precision=FP32)
+    start, obs, fin, st = run_both(p, 4, 6, seed=5, refresh=16, precision=FP32, delay=delay)
     W = weight.Weights(p)
     want = np.array([W.log_norm(c) for c in fin])
     assert np.abs(obs[-1, :, 1] - want).max() <= 1e-4
     assert st.max_drift < 1e-3
 
 
+def test_fp64_delayed_inverse_exact():
+    """With pending panels folded in, W equals inv(M(G)) to FP64 rounding."""
+    p = gi.make_problem(6, gi.U1, 2, 2, bond_scale=0.2)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.cold_links(p, 2), refresh_every=10**9, seed=2, delay=8)
+    ctx.sample(2)
+    links = np.ascontiguousarray(ctx.chains_links()[:1])
+    ell = np.zeros((1, 3, 2))
+    ctx.logweight(links, ell=ell)
+    tracked = ctx.chains_ell()[0]
+    assert np.abs(tracked.real - ell[0, :, 0]).max() < 1e-9
+    ctx.close()
+
+
 def test_checkpoint_resume_bit_exact(tmp_path):
     p = gi.make_problem(2, gi.U1, 1, 2, bond_scale=0.3)
     ctx = ctx_for(p)
-    ctx.chains_init(gi.cold_links(p, 3), refresh_every=4, seed=3)
+    ctx.chains_init(gi.cold_links(p, 3), refresh_every=4, seed=3, delay=4)
     ctx.sample(2)
     ck = tmp_path / "c.ckpt"
     ctx.checkpoint(ck)
