@@ -1,0 +1,133 @@
+// Allocation-free variant of ggf_logweight.
+//
+// Some callers cannot allocate device memory at the point where they need
+// log N(G): code that runs while a CUDA stream is being captured into a
+// graph, real-time or embedded hosts whose memory is budgeted once at start,
+// or a process that shares the GPU under an allocator that forbids further
+// cudaMalloc calls.  ggf_logweight itself grows a workspace with cudaMalloc,
+// so this entry point instead works in one fixed scratch array that lives in
+// the library image (a file-scope __device__ array, 32 MiB, held by every GPU
+// that loads the library until the process exits).
+//
+// The scratch is shared by all calls on a device: two calls whose work
+// overlaps on the GPU (different streams, or host threads racing) corrupt each
+// other's results; serialise them.  Every element the kernels read is written
+// first in the same call (the Pfaffian accumulators are set by their own
+// initialisation kernel), so nothing depends on what a previous call left.
+#include <mutex>
+#include "ggf_ctx.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)32 << 20;   // 32 MiB
+constexpr int kMaxN = 1024;                          // largest M_nm handled (N = 8 n_v L^2)
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_dev[64] = {nullptr};                // device address per device ordinal
+
+// Host code may not take the address of g_scratch directly (that is a host
+// shadow, not device memory): look it up once per device, device current.
+ggf_status scratch_for(ggf_ctx* ctx, void** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (ctx->device < 0 || ctx->device >= 64) return ggf_fail(ctx, GGF_EINVAL, "device ordinal out of range");
+    if (!g_scratch_dev[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) return ggf_cuda(ctx, e, "cudaGetSymbolAddress(scratch)");
+        g_scratch_dev[ctx->device] = p;
+    }
+    *out = g_scratch_dev[ctx->device];
+    return GGF_OK;
+}
+
+__global__ void na_items(int n_items, int npf, int* cfg, int* pair) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_items) { cfg[i] = i / npf; pair[i] = i % npf; }
+}
+
+__global__ void na_write_ell(int n_items, int npf, int pair_off, int P, bool cplx, const cxd* logpf,
+                             const cxd* phase, cxd* ell) {
+    int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    int c = it / npf, p = it % npf;
+    cxd v = {logpf[it].x, 0.0};
+    if (cplx) v.y = atan2(phase[it].y, phase[it].x);
+    ell[(size_t)c * P + pair_off + p] = v;
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t ggf_factor_tmp_bytes(int n, int batch);
+
+extern "C" ggf_status ggf_logweight_noalloc(ggf_ctx* ctx, int n_cfg, const void* links, double* logN,
+                                            void* stream) {
+    if (!ctx) return GGF_EINVAL;
+    if (!ctx->have_lattice || !ctx->have_group || !ctx->have_gauss)
+        return ggf_fail(ctx, GGF_ESTATE, "lattice, group and Gaussians must be initialised");
+    if (n_cfg < 0 || !links || !logN) return ggf_fail(ctx, GGF_EINVAL, "bad logweight_noalloc arguments");
+    const Geometry& g = ctx->g;
+    const int N = g.N, P = ctx->P;
+    if (N > kMaxN)
+        return ggf_fail(ctx, GGF_EINVAL, "ggf_logweight_noalloc: M is " + std::to_string(N) + " x " +
+                                             std::to_string(N) + ", above the fixed-scratch maximum " +
+                                             std::to_string(kMaxN) + " (use ggf_logweight)");
+    if (n_cfg == 0) return GGF_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ggf_fail(ctx, GGF_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    void* base = nullptr;
+    GGF_TRY(scratch_for(ctx, &base));
+    const size_t NN = (size_t)N * N;
+    // configurations per chunk: their pair log-Pfaffians plus one family's
+    // matrices, factor scratch and item tables must fit in the scratch
+    const int npf_max = std::max(ctx->K, ctx->Kc);
+    int cfg_chunk = 0;
+    for (int c = n_cfg; c >= 1; c = c > 1 ? c / 2 : 0) {
+        int items = c * npf_max;
+        size_t need = align256((size_t)c * P * sizeof(cxd)) + align256(NN * sizeof(cxd) * items) +
+                      align256(ggf_factor_tmp_bytes(N, items)) + 2 * align256((size_t)items * sizeof(int)) +
+                      2 * align256((size_t)items * sizeof(cxd));
+        if (need <= kScratchBytes) { cfg_chunk = c; break; }
+    }
+    if (cfg_chunk == 0) return ggf_fail(ctx, GGF_EINVAL, "ggf_logweight_noalloc: one configuration does not fit the scratch");
+    unsigned char* s0 = (unsigned char*)base;
+    const size_t lrow = (size_t)g.n_links * (g.group == GGF_Z2 ? 1 : sizeof(double));
+    for (int c0 = 0; c0 < n_cfg; c0 += cfg_chunk) {
+        const int nc = std::min(cfg_chunk, n_cfg - c0);
+        const void* lk = (const unsigned char*)links + (size_t)c0 * lrow;
+        unsigned char* q = s0;
+        cxd* ell = (cxd*)q;
+        q += align256((size_t)nc * P * sizeof(cxd));
+        unsigned char* fam_base = q;
+        for (int fam = 0; fam < 2; ++fam) {
+            const bool cplx = fam == 1;
+            const int npf = cplx ? ctx->Kc : ctx->K;
+            if (npf == 0) continue;
+            const int items = nc * npf;
+            q = fam_base;
+            void* A = q;
+            q += align256(NN * (cplx ? sizeof(cxd) : sizeof(double)) * items);
+            void* ftmp = q;
+            q += align256(ggf_factor_tmp_bytes(N, items));
+            int* d_cfg = (int*)q;
+            q += align256((size_t)items * sizeof(int));
+            int* d_pair = (int*)q;
+            q += align256((size_t)items * sizeof(int));
+            cxd* d_logpf = (cxd*)q;
+            q += align256((size_t)items * sizeof(cxd));
+            cxd* d_phase = (cxd*)q;
+            na_items<<<(items + 127) / 128, 128, 0, st>>>(items, npf, d_cfg, d_pair);
+            GGF_CK(cudaGetLastError());
+            GGF_TRY(ggf_assemble(ctx, !cplx, items, d_cfg, d_pair, lk, A, st));
+            GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, items, A, d_logpf, d_phase, ftmp, st));
+            na_write_ell<<<(items + 127) / 128, 128, 0, st>>>(items, npf, cplx ? ctx->K : 0, P, cplx, d_logpf,
+                                                              d_phase, ell);
+            GGF_CK(cudaGetLastError());
+        }
+        GGF_TRY(ggf_combine(ctx, nc, ell, logN + c0, st));
+    }
+    return GGF_OK;
+}

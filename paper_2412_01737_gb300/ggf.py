@@ -47,7 +47,7 @@ class ChainStats(ctypes.Structure):
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
-           "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync"]
+           "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc"]
 
 
 def lib_path() -> str:
@@ -84,6 +84,7 @@ def load():
         "ggf_profile": ([P, I], I),
         "ggf_kernel_time": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)], I),
         "ggf_sync": ([P, P], I),
+        "ggf_logweight_noalloc": ([P, I, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +190,14 @@ class GGF:
         lp, _ = _ptr(links)
         self._ck(self.lib.ggf_logweight(self.h, n_cfg, lp, _ptr(logN)[0], _ptr(ell)[0], mem,
                                         _stream([links, logN, ell])))
+        return logN
+
+    def logweight_noalloc(self, links, logN, stream=None):
+        """Allocation-free log N(G) into `logN`; both are CUDA tensors."""
+        if _ptr(links)[1] != MEM_DEVICE or _ptr(logN)[1] != MEM_DEVICE:
+            raise ValueError("logweight_noalloc takes device tensors only")
+        st = stream if stream is not None else _stream([links, logN])
+        self._ck(self.lib.ggf_logweight_noalloc(self.h, int(links.shape[0]), _ptr(links)[0], _ptr(logN)[0], st))
         return logN
 
     def observable(self, links, out=None, which=OBS_PLAQUETTE):
