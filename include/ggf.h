@@ -199,6 +199,14 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
 ggf_status ggf_profile(ggf_ctx* ctx, int enable);
 ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launches);
 
+/* Self-test of the tensor-core delayed-update flush (W <- W - U V^T with
+ * FP32 data on tcgen05 TF32 tensor cores, three-product split): runs it on
+ * one N x N (cplx = 0) or complex N x N (cplx = 1) matrix with seeded data
+ * and a rank-`rank` panel (rank a multiple of 8, <= 128) and reports the
+ * largest error relative to the largest entry of an FP64 reference.  Needs
+ * only a context (allocates its own buffers).  Not part of the method. */
+ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank, double* max_rel_err);
+
 /* Wait for the context's work on `stream` and report device-side errors. */
 ggf_status ggf_sync(ggf_ctx* ctx, void* stream);
 

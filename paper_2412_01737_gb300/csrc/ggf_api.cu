@@ -37,7 +37,7 @@ ggf_status ggf_workspace(ggf_ctx* ctx, size_t bytes) {
 void ggf_free_chains(ggf_ctx* ctx) {
     Chains& c = ctx->ch;
     void* ptrs[] = {c.links, c.Wr, c.Wc, c.ell, c.zbuf, c.ybuf, c.accept, c.since_refresh,
-                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Ur, c.Vr, c.Uc, c.Vc, c.pend};
+                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ggf_chain_opts o = c.opts;
@@ -222,6 +222,10 @@ ggf_status ggf_create(ggf_ctx** out, int device) {
     if (cudaSetDevice(device) != cudaSuccess) return GGF_ECUDA;
     ggf_ctx* c = new ggf_ctx();
     c->device = device;
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        delete c;
+        return GGF_ENOMEM;
+    }
     c->ch.opts.precision = GGF_FP64;
     c->ch.opts.refresh_every = 64;
     c->ch.opts.width = 0.5;
@@ -236,6 +240,7 @@ void ggf_destroy(ggf_ctx* ctx) {
     ggf_free_chains(ctx);
     ggf_free_consts(ctx);
     if (ctx->work) cudaFree(ctx->work);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }
@@ -427,11 +432,9 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     if (ch.kmax > 16) return ggf_fail(ctx, GGF_EINVAL, "delay must be <= 16");
     ch.steps_since_flush = 0;
     if (ch.kmax > 1) {
-        const size_t pr = (size_t)n_chains * ch.kmax * g.r * g.N * rsz;
-        GGF_CK(cudaMalloc(&ch.Ur, std::max<size_t>(16, pr * ctx->K)));
-        GGF_CK(cudaMalloc(&ch.Vr, std::max<size_t>(16, pr * ctx->K)));
-        GGF_CK(cudaMalloc(&ch.Uc, std::max<size_t>(16, pr * 2 * ctx->Kc)));
-        GGF_CK(cudaMalloc(&ch.Vc, std::max<size_t>(16, pr * 2 * ctx->Kc)));
+        const size_t pr = (size_t)n_chains * ch.kmax * g.r * g.N * rsz;   // one plane per chain
+        GGF_CK(cudaMalloc(&ch.Pr, std::max<size_t>(16, pr * 2 * ctx->K)));
+        GGF_CK(cudaMalloc(&ch.Pc, std::max<size_t>(16, pr * 4 * ctx->Kc)));
         GGF_CK(cudaMalloc(&ch.ybuf, 16));
     } else {
         GGF_CK(cudaMalloc(&ch.ybuf, (size_t)n_chains * (ctx->K + 2 * ctx->Kc) * 2 * g.r * g.N * rsz + 16));
@@ -545,6 +548,9 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
         ch.sweep += 1;
     }
     GGF_CK(cudaStreamSynchronize(st));
+    int herr = 0;
+    GGF_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return ggf_fail(ctx, GGF_ETIMEOUT, "a bounded device wait ran out (tensor-core flush)");
     return GGF_OK;
 }
 
@@ -711,6 +717,9 @@ ggf_status ggf_sync(ggf_ctx* ctx, void* stream) {
     cudaSetDevice(ctx->device);
     GGF_CK(cudaStreamSynchronize((cudaStream_t)stream));
     GGF_CK(cudaGetLastError());
+    int herr = 0;
+    GGF_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return ggf_fail(ctx, GGF_ETIMEOUT, "a bounded device wait ran out (tensor-core flush)");
     return GGF_OK;
 }
 

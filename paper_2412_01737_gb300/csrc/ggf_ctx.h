@@ -45,8 +45,8 @@ struct Chains {
     int* refresh_list = nullptr;  // [n + 1]
     // delayed updates (opts.delay > 1): per chain and pair, U^T and V panels
     // [n][pairs][kmax r][N] in W precision, pending count per chain
-    void* Ur = nullptr; void* Vr = nullptr;
-    void* Uc = nullptr; void* Vc = nullptr;
+    void* Pr = nullptr;   // real-family panels [n][K][2][N][kmax r]
+    void* Pc = nullptr;   // complex-family panels [n][Kc][2][2][N][kmax r]
     int* pend = nullptr;          // [n]
     int kmax = 1;
     int steps_since_flush = 0;
@@ -57,6 +57,8 @@ struct ggf_ctx {
     std::string err;
     Geometry g;
     bool have_lattice = false, have_group = false, have_gauss = false;
+    bool use_tc = true;        // FP32 delayed flush on tcgen05 tensor cores
+    int* d_err = nullptr;      // device error word (bounded waits that ran out)
     int K = 0, P = 0, Kc = 0;
     std::vector<int> pair_n, pair_m;
     std::vector<cxd> logc, w;

@@ -99,6 +99,25 @@ __device__ bool warp_solve(cxd* A, int r, cxd* fcol) {
 template <class T>
 __device__ __forceinline__ cxd loadc(const T* p) { return Sc<T>::to(*p); }
 
+// Pending-update panels of one (chain, pair): U (N x KRM) followed by V^T
+// (N x KRM), K-major (row index first, rank index contiguous); complex
+// values are stored as a real plane followed by an imaginary plane, so a
+// (chain, pair) block holds 2 (real) or 4 (complex) planes of N * KRM.
+template <class T> struct PanelIO {
+    typedef typename Sc<T>::R R;
+    static constexpr int PLANES = Sc<T>::CPLX ? 2 : 1;
+    __device__ static T ld(const R* p, size_t plane, size_t idx);
+    __device__ static void st(R* p, size_t plane, size_t idx, T v);
+};
+template <> __device__ __forceinline__ double PanelIO<double>::ld(const double* p, size_t, size_t i) { return p[i]; }
+template <> __device__ __forceinline__ float PanelIO<float>::ld(const float* p, size_t, size_t i) { return p[i]; }
+template <> __device__ __forceinline__ cxd PanelIO<cxd>::ld(const double* p, size_t pl, size_t i) { return {p[i], p[pl + i]}; }
+template <> __device__ __forceinline__ cxf PanelIO<cxf>::ld(const float* p, size_t pl, size_t i) { return {p[i], p[pl + i]}; }
+template <> __device__ __forceinline__ void PanelIO<double>::st(double* p, size_t, size_t i, double v) { p[i] = v; }
+template <> __device__ __forceinline__ void PanelIO<float>::st(float* p, size_t, size_t i, float v) { p[i] = v; }
+template <> __device__ __forceinline__ void PanelIO<cxd>::st(double* p, size_t pl, size_t i, cxd v) { p[i] = v.x; p[pl + i] = v.y; }
+template <> __device__ __forceinline__ void PanelIO<cxf>::st(float* p, size_t pl, size_t i, cxf v) { p[i] = v.x; p[pl + i] = v.y; }
+
 struct SweepArgs {
     DevConst dc;
     int n_chains;
@@ -118,10 +137,8 @@ struct SweepArgs {
     int* sweep_acc;
     unsigned long long* counters;
     // delayed updates
-    const void* Ur;
-    const void* Vr;
-    const void* Uc;
-    const void* Vc;
+    const void* Pr;   // real-family panels  [n][K][2][N][KRM]
+    const void* Pc;   // complex-family panels [n][Kc][2][2][N][KRM]
     int* pend;
     int kmax;   // > 1: delayed
 };
@@ -191,17 +208,21 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
             if (a.kmax > 1) {
                 // pending updates: W_eff[S, S] = W[S, S] - U[S, :] V[:, S]
                 const int kr = a.pend[c] * r;
-                const size_t pb = (p < K ? ((size_t)c * K + p) : ((size_t)c * (P - K) + (p - K))) * a.kmax * r;
-                for (int q = 0; q < kr; ++q) {
-                    cxd u, v;
-                    if (p < K) {
-                        u = loadc((const RW*)a.Ur + (pb + q) * N + gi);
-                        v = loadc((const RW*)a.Vr + (pb + q) * N + gj);
-                    } else {
-                        u = loadc((const CW*)a.Uc + (pb + q) * N + gi);
-                        v = loadc((const CW*)a.Vc + (pb + q) * N + gj);
-                    }
-                    wv -= u * v;
+                const int KRM = a.kmax * r;
+                const size_t NK = (size_t)N * KRM;
+                typedef typename Sc<RW>::R R;
+                if (p < K) {
+                    const R* U = (const R*)a.Pr + ((size_t)c * K + p) * 2 * NK;
+                    const R* Vt = U + NK;
+                    for (int q = 0; q < kr; ++q)
+                        wv -= Sc<RW>::to(PanelIO<RW>::ld(U, NK, (size_t)gi * KRM + q)) *
+                              Sc<RW>::to(PanelIO<RW>::ld(Vt, NK, (size_t)gj * KRM + q));
+                } else {
+                    const R* U = (const R*)a.Pc + ((size_t)c * (P - K) + (p - K)) * 4 * NK;
+                    const R* Vt = U + 2 * NK;
+                    for (int q = 0; q < kr; ++q)
+                        wv -= Sc<CW>::to(PanelIO<CW>::ld(U, NK, (size_t)gi * KRM + q)) *
+                              Sc<CW>::to(PanelIO<CW>::ld(Vt, NK, (size_t)gj * KRM + q));
                 }
             }
             Ws[e] = wv;
@@ -349,16 +370,19 @@ __global__ void __launch_bounds__(256) update_kernel(int N, int P, int fam_pairs
 
 // Delayed mode, accepted chains: rows Y = W_eff[S, :] and columns
 // C = W_eff[:, S] of the effective inverse W_eff = W - U V, then the new
-// panel entries U[:, slot] = C Z and V[slot, :] = Y.
+// panel entries U[:, slot] = C Z and V[slot, :] = Y (stored as V^T rows).
 // Grid (ceil(N / 128), family pairs, chains), 128 threads, one index each.
 template <class T, int R>
 __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_pairs, int pair_off, int link,
-                                                     const T* W, T* Ut, T* V, const cxd* zbuf,
+                                                     const T* W, typename Sc<T>::R* Pan, const cxd* zbuf,
                                                      const int* accept, const int* pend, int kmax) {
+    typedef typename Sc<T>::R RR;
     const int c = blockIdx.z;
     if (!accept[c]) return;
     const int p = blockIdx.y, N = g.N;
     const int slot = pend[c] - 1, kr = slot * R;
+    const int KRM = kmax * R;
+    const size_t NK = (size_t)N * KRM;
     extern __shared__ unsigned char smraw[];
     T* UtS = (T*)smraw;            // [kr][R]  U[S_a, q]
     T* VS = UtS + kmax * R * R;    // [kr][R]  V[q, S_a]
@@ -371,13 +395,13 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
     __syncthreads();
     const size_t base = ((size_t)c * fam_pairs + p);
     const T* Wp = W + base * N * N;
-    T* Up = Ut + base * kmax * R * N;
-    T* Vp = V + base * kmax * R * N;
+    RR* U = Pan + base * 2 * PanelIO<T>::PLANES * NK;
+    RR* Vt = U + PanelIO<T>::PLANES * NK;
     const cxd* Z = zbuf + ((size_t)c * P + pair_off + p) * R * R;
     for (int e = threadIdx.x; e < kr * R; e += blockDim.x) {
         int q = e / R, a = e % R;
-        UtS[e] = Up[(size_t)q * N + S[a]];
-        VS[e] = Vp[(size_t)q * N + S[a]];
+        UtS[e] = PanelIO<T>::ld(U, NK, (size_t)S[a] * KRM + q);
+        VS[e] = PanelIO<T>::ld(Vt, NK, (size_t)S[a] * KRM + q);
     }
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) Zs[e] = Sc<T>::from(Z[e]);
     __syncthreads();
@@ -390,8 +414,8 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
         cv[a] = Wp[(size_t)j * N + S[a]];
     }
     for (int q = 0; q < kr; ++q) {
-        T vq = Vp[(size_t)q * N + j];
-        T uq = Up[(size_t)q * N + j];
+        T vq = PanelIO<T>::ld(Vt, NK, (size_t)j * KRM + q);
+        T uq = PanelIO<T>::ld(U, NK, (size_t)j * KRM + q);
 #pragma unroll
         for (int a = 0; a < R; ++a) {
             yv[a] -= UtS[q * R + a] * vq;
@@ -403,31 +427,34 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
         T u = Sc<T>::zero();
 #pragma unroll
         for (int a = 0; a < R; ++a) u += cv[a] * Zs[a * R + b];
-        Up[(size_t)(kr + b) * N + j] = u;
-        Vp[(size_t)(kr + b) * N + j] = yv[b];
+        PanelIO<T>::st(U, NK, (size_t)j * KRM + kr + b, u);
+        PanelIO<T>::st(Vt, NK, (size_t)j * KRM + kr + b, yv[b]);
     }
 }
 
-// W <- W - U V over the pending panels (rank pend[c] * R), SIMT tiled product.
+// W <- W - U V over the pending panels (rank pend[c] * R), SIMT tiled product
+// (FP64 chains, and FP32 when the tensor-core flush is not used).
 // Grid (tiles_i * tiles_j, family pairs, chains), 256 threads as 16 x 16, each
 // a 4 x 4 block of a 64 x 64 tile of W.
 template <class T, int R>
-__global__ void __launch_bounds__(256) flush_kernel(int N, int fam_pairs, T* W, const T* Ut, const T* V,
+__global__ void __launch_bounds__(256) flush_kernel(int N, int fam_pairs, T* W, const typename Sc<T>::R* Pan,
                                                     const int* pend, int kmax, int tiles) {
+    typedef typename Sc<T>::R RR;
     const int c = blockIdx.z;
     const int kc = pend[c];
     if (kc == 0) return;
-    const int kr = kc * R;
+    const int kr = kc * R, KRM = kmax * R;
+    const size_t NK = (size_t)N * KRM;
     const int p = blockIdx.y;
     const int ti = blockIdx.x / tiles, tj = blockIdx.x - ti * tiles;
     const int i0 = ti * 64, j0 = tj * 64;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    __shared__ T As[16][64];
-    __shared__ T Bs[16][64];
+    __shared__ T As[16][65];
+    __shared__ T Bs[16][65];
     const size_t base = ((size_t)c * fam_pairs + p);
     T* Wp = W + base * N * N;
-    const T* Up = Ut + base * kmax * R * N;
-    const T* Vp = V + base * kmax * R * N;
+    const RR* U = Pan + base * 2 * PanelIO<T>::PLANES * NK;
+    const RR* Vt = U + PanelIO<T>::PLANES * NK;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -435,10 +462,10 @@ __global__ void __launch_bounds__(256) flush_kernel(int N, int fam_pairs, T* W, 
         for (int b = 0; b < 4; ++b) acc[a][b] = Sc<T>::zero();
     for (int q0 = 0; q0 < kr; q0 += 16) {
         for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-            int qq = e >> 6, k = e & 63;
+            int k = e >> 4, qq = e & 15;      // consecutive threads walk the rank index
             int q = q0 + qq;
-            As[qq][k] = (q < kr && i0 + k < N) ? Up[(size_t)q * N + i0 + k] : Sc<T>::zero();
-            Bs[qq][k] = (q < kr && j0 + k < N) ? Vp[(size_t)q * N + j0 + k] : Sc<T>::zero();
+            As[qq][k] = (q < kr && i0 + k < N) ? PanelIO<T>::ld(U, NK, (size_t)(i0 + k) * KRM + q) : Sc<T>::zero();
+            Bs[qq][k] = (q < kr && j0 + k < N) ? PanelIO<T>::ld(Vt, NK, (size_t)(j0 + k) * KRM + q) : Sc<T>::zero();
         }
         __syncthreads();
 #pragma unroll
@@ -524,6 +551,7 @@ __global__ void mark_refresh(int n_chains, int R, const int* since, int* list) {
 }  // namespace
 
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
+ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st);
 
 size_t ggf_ratio_smem(int P, int r) {
     return (size_t)(2 * P * r * r + NWARP * 4 * r * r + P + NWARP * r) * sizeof(cxd);
@@ -552,7 +580,7 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     a.since_refresh = ch.since_refresh;
     a.sweep_acc = ch.sweep_acc;
     a.counters = ch.counters;
-    a.Ur = ch.Ur; a.Vr = ch.Vr; a.Uc = ch.Uc; a.Vc = ch.Vc;
+    a.Pr = ch.Pr; a.Pc = ch.Pc;
     a.pend = ch.pend;
     a.kmax = ch.kmax;
     size_t smem = ggf_ratio_smem(ctx->P, g.r);
@@ -571,24 +599,24 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     const int N = g.N;
     if (ch.kmax > 1) {
         dim3 gg((N + 127) / 128, ctx->K, ch.n), gc2((N + 127) / 128, ctx->Kc, ch.n);
-#define GGF_GATH(T, R_, grid, fam, off, Wp, Up, Vp)                                                           \
+#define GGF_GATH(T, R_, grid, fam, off, Wp, Pp)                                                               \
     gather_kernel<T, R_><<<grid, 128, (2 * ch.kmax * R_ * R_ + R_ * R_) * sizeof(T), st>>>(                 \
-        g, ctx->P, fam, off, link, (const T*)(Wp), (T*)(Up), (T*)(Vp), a.zbuf, ch.accept, ch.pend, ch.kmax)
+        g, ctx->P, fam, off, link, (const T*)(Wp), (typename Sc<T>::R*)(Pp), a.zbuf, ch.accept, ch.pend, ch.kmax)
         if (g.r == 4) {
             if (fp64) {
-                GGF_GATH(double, 4, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
-                if (ctx->Kc) GGF_GATH(cxd, 4, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+                GGF_GATH(double, 4, gg, ctx->K, 0, ch.Wr, ch.Pr);
+                if (ctx->Kc) GGF_GATH(cxd, 4, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Pc);
             } else {
-                GGF_GATH(float, 4, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
-                if (ctx->Kc) GGF_GATH(cxf, 4, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+                GGF_GATH(float, 4, gg, ctx->K, 0, ch.Wr, ch.Pr);
+                if (ctx->Kc) GGF_GATH(cxf, 4, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Pc);
             }
         } else {
             if (fp64) {
-                GGF_GATH(double, 8, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
-                if (ctx->Kc) GGF_GATH(cxd, 8, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+                GGF_GATH(double, 8, gg, ctx->K, 0, ch.Wr, ch.Pr);
+                if (ctx->Kc) GGF_GATH(cxd, 8, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Pc);
             } else {
-                GGF_GATH(float, 8, gg, ctx->K, 0, ch.Wr, ch.Ur, ch.Vr);
-                if (ctx->Kc) GGF_GATH(cxf, 8, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Uc, ch.Vc);
+                GGF_GATH(float, 8, gg, ctx->K, 0, ch.Wr, ch.Pr);
+                if (ctx->Kc) GGF_GATH(cxf, 8, gc2, ctx->Kc, ctx->K, ch.Wc, ch.Pc);
             }
         }
 #undef GGF_GATH
@@ -634,14 +662,16 @@ ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st) {
     const int N = g.N, tiles = (N + 63) / 64;
     const int ev0 = ctx->prof_mark(st);
     dim3 gr(tiles * tiles, ctx->K, ch.n), gc(tiles * tiles, ctx->Kc, ch.n);
-#define GGF_FL(T, R_, grid, fam, Wp, Up, Vp) \
-    flush_kernel<T, R_><<<grid, 256, 0, st>>>(N, fam, (T*)(Wp), (const T*)(Up), (const T*)(Vp), ch.pend, ch.kmax, tiles)
-    if (g.r == 4) {
-        if (fp64) { GGF_FL(double, 4, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxd, 4, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
-        else { GGF_FL(float, 4, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxf, 4, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
+#define GGF_FL(T, R_, grid, fam, Wp, Pp) \
+    flush_kernel<T, R_><<<grid, 256, 0, st>>>(N, fam, (T*)(Wp), (const typename Sc<T>::R*)(Pp), ch.pend, ch.kmax, tiles)
+    if (!fp64 && ctx->use_tc) {
+        GGF_TRY(ggf_flush_tc(ctx, st));
+    } else if (g.r == 4) {
+        if (fp64) { GGF_FL(double, 4, gr, ctx->K, ch.Wr, ch.Pr); if (ctx->Kc) GGF_FL(cxd, 4, gc, ctx->Kc, ch.Wc, ch.Pc); }
+        else { GGF_FL(float, 4, gr, ctx->K, ch.Wr, ch.Pr); if (ctx->Kc) GGF_FL(cxf, 4, gc, ctx->Kc, ch.Wc, ch.Pc); }
     } else {
-        if (fp64) { GGF_FL(double, 8, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxd, 8, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
-        else { GGF_FL(float, 8, gr, ctx->K, ch.Wr, ch.Ur, ch.Vr); if (ctx->Kc) GGF_FL(cxf, 8, gc, ctx->Kc, ch.Wc, ch.Uc, ch.Vc); }
+        if (fp64) { GGF_FL(double, 8, gr, ctx->K, ch.Wr, ch.Pr); if (ctx->Kc) GGF_FL(cxd, 8, gc, ctx->Kc, ch.Wc, ch.Pc); }
+        else { GGF_FL(float, 8, gr, ctx->K, ch.Wr, ch.Pr); if (ctx->Kc) GGF_FL(cxf, 8, gc, ctx->Kc, ch.Wc, ch.Pc); }
     }
 #undef GGF_FL
     ctx->prof_pair(GGF_KT_FLUSH, ev0, ctx->prof_mark(st));

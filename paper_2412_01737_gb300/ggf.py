@@ -47,7 +47,8 @@ class ChainStats(ctypes.Structure):
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
-           "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc"]
+           "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
+           "ggf_selftest_flush"]
 
 
 def lib_path() -> str:
@@ -85,6 +86,7 @@ def load():
         "ggf_kernel_time": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)], I),
         "ggf_sync": ([P, P], I),
         "ggf_logweight_noalloc": ([P, I, P, P, P], I),
+        "ggf_selftest_flush": ([P, I, I, I, ctypes.POINTER(ctypes.c_double)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -257,6 +259,12 @@ class GGF:
     def resume(self, path):
         self._ck(self.lib.ggf_resume(self.h, str(path).encode(), None))
         self.n_chains = self.chains_stats().n_chains
+
+    def selftest_flush(self, cplx, N, rank):
+        """Max relative error of the tensor-core flush against FP64."""
+        e = ctypes.c_double()
+        self._ck(self.lib.ggf_selftest_flush(self.h, int(cplx), int(N), int(rank), ctypes.byref(e)))
+        return e.value
 
     def profile(self, enable=True):
         self._ck(self.lib.ggf_profile(self.h, 1 if enable else 0))
