@@ -118,25 +118,47 @@ def unit_bytes(p, prec):
     return 2 * p.N * p.N * (p.K * b + p.K * (p.K - 1) // 2 * 2 * b)
 
 
+# Largest lattice on which the oracle times a proposal directly; bigger
+# workloads are timed on this lattice with the same group, n_v and K and the
+# per-proposal time scaled by the cube of the Pfaffian size.
+CPU_PROXY_L = {"cfg3": 6}
+
+
 def cpu_sample(name, budget_s=15.0, workers=None):
-    """Time the oracle's exact Metropolis on a bounded sample (spawned pool)."""
+    """Time the oracle's exact Metropolis on a bounded sample (spawned pool).
+    Returns (proposals per second of the full workload, wall seconds,
+    workers, description)."""
     import multiprocessing as mp
     workers = workers or min(16, os.cpu_count() or 1)
+    Lp = CPU_PROXY_L.get(name)
+    if Lp:
+        workers = min(workers, 8)
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        res = pool.starmap(_cpu_worker, [(name, w, budget_s) for w in range(workers)])
+        res = pool.starmap(_cpu_worker, [(name, w, budget_s, Lp) for w in range(workers)])
     props = sum(r[0] for r in res)
     secs = max(r[1] for r in res)
-    return props, secs, workers
+    rate = props / secs
+    p, *_ = problem_for(name)
+    desc = (f"{props} exact-Metropolis proposals over {workers} spawned chains in {secs:.1f}s "
+            f"(one full FP64 Pfaffian per pair per proposal)")
+    if Lp:
+        n_full, n_proxy = p.m_s * p.V, p.m_s * Lp * Lp
+        rate /= (n_full / n_proxy) ** 3
+        desc += (f" on the {Lp}x{Lp} lattice with the same group, n_v and K; rate scaled by "
+                 f"(Pfaffian size {n_full}/{n_proxy})^3 to the {p.L}x{p.L} workload")
+    return rate, secs, workers, desc
 
 
-def _cpu_worker(name, chain, budget_s):
+def _cpu_worker(name, chain, budget_s, proxy_L=None):
     sys.path.insert(0, ROOT)
     import ggf_inputs as gi
     from oracle import weight
     from oracle.mcmc import propose
     from oracle.philox import draws
     p, *_ = problem_for(name)
+    if proxy_L:
+        p = gi.make_problem(proxy_L, p.group, p.n_v, p.K, seed=BASE_SEED)
     W = weight.Weights(p)
     links = gi.cold_links(p)[0]
     logN = W.log_norm(links)
@@ -160,8 +182,9 @@ def run_reference(args):
         return
     p, chains, prec, refresh, delay, label = problem_for(args.workload)
     t0 = time.time()
-    props, secs, workers = cpu_sample(args.workload, budget_s=args.cpu_seconds)
-    sweeps_per_s = props / p.n_links / secs
+    rate, secs, workers, desc = cpu_sample(args.workload, budget_s=args.cpu_seconds)
+    props = rate * secs
+    sweeps_per_s = rate / p.n_links
     value = sweeps_per_s / (2 * 0.5)      # tau_int >= 1/2: upper bound for the oracle
     line = {"metric": "effective samples/sec/GPU", "value": value, "unit": "samples/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -169,9 +192,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": label, "chains": chains},
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
-                             "sample": f"{props} exact-Metropolis proposals ({workers} spawned chains, "
-                                       f"{secs:.1f}s each; full FP64 Pfaffian per proposal); ESS bound with "
-                                       f"tau_int = 1/2"},
+                             "sample": desc + "; ESS bound with tau_int = 1/2"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.time() - t0}
     print(json.dumps(line), flush=True)
@@ -221,12 +242,14 @@ def run_ggf(args):
     clocks.start()
     ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()     # ncu --profile-from-start off sees the timed sweeps only
     e0.record(stream)
     for _ in range(args.steps):
         ctx.sample(1, obs=dev_obs)
         obs_all.append(dev_obs[0].clone())
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     obs_all = [o.cpu().numpy() if hasattr(o, "cpu") else o for o in obs_all]
@@ -251,7 +274,6 @@ def run_ggf(args):
     shares = {k: v[0] for k, v in kt.items()}
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # SM count x FP32 lanes x FMA x max clock
     dom = max(shares, key=shares.get)
     wpairs = p.K + 4 * (p.K * (p.K - 1) // 2)             # real-MAC weight of all pairs
     if dom == "refresh":
@@ -262,12 +284,19 @@ def run_ggf(args):
                 "peak_source": "FP64 nominal 1.25 TFLOP/s from the profiling recipe (not in MEASURED_PEAKS)"}
     elif dom == "flush":
         fl = accepts * 2.0 * p.N ** 2 * p.r * wpairs      # every accepted rank-r update folded once
-        roof = {"kernel": "flush_kernel (W -= U V, delayed SMW)", "bound": "alu",
-                "achieved": fl / (kt["flush"][0] * 1e-3) / 1e12,
-                "peak": (1.0 if prec == 0 else 1.0) * (1.25 if prec == 0 else fp32_peak), "unit": "TFLOP/s",
-                "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz (recipe unit counts and clock)"
-                               if prec == 1 else "FP64 nominal 1.25 TFLOP/s (recipe)",
-                "bytes_per_flush_chain": unit_bytes(p, prec)}
+        t_fl = kt["flush"][0] * 1e-3
+        if prec == 1:
+            # tensor-core flush: W read + written once per flush call and chain
+            byts = kt["flush"][1] * chains * unit_bytes(p, prec)
+            roof = {"kernel": "flush_tc_kernel (tcgen05 TF32x3, W -= U V)", "bound": "hbm",
+                    "achieved": byts / t_fl / 1e9, "peak": hbm, "unit": "GB/s",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                    "algorithmic_bytes_per_launch_group": chains * unit_bytes(p, prec),
+                    "fp32_equivalent_tflops": fl / t_fl / 1e12}
+        else:
+            roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V)", "bound": "alu",
+                    "achieved": fl / t_fl / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                    "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe)"}
     elif dom == "update":
         upd_bytes = accepts * unit_bytes(p, prec)
         roof = {"kernel": "update_kernel (rank-r SMW)" if delay <= 1 else "gather_kernel", "bound": "hbm",
@@ -297,15 +326,13 @@ def run_ggf(args):
             "dlogp_vs_fp64_recompute": dlogp,
             "roofline": roof, "clocks": ck,
             "gpu_launches": int(st1.launches - st0.launches)}
+    ctx.close()                                   # frees the chains before the e2e run
     if rank == 0 and not args.no_cpu:
-        props, secs, workers = cpu_sample(args.workload, budget_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": props / p.n_links / secs / (2 * tau), "unit": "samples/s",
-                                "cores": workers, "kind": "oracle",
-                                "sample": f"{props} exact-Metropolis proposals over {workers} spawned chains "
-                                          f"in {secs:.1f}s (full FP64 Pfaffian per proposal), same tau_int"}
+        rate, secs, workers, desc = cpu_sample(args.workload, budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate / p.n_links / (2 * tau), "unit": "samples/s",
+                                "cores": workers, "kind": "oracle", "sample": desc + ", same tau_int"}
     if rank == 0 and not args.no_e2e:
         line["e2e"] = run_e2e(args, p, chains, prec, refresh, delay, local, tau)
-    ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -338,7 +365,7 @@ def run_e2e(args, p, chains, prec, refresh, delay, local, tau):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--burn", type=int, default=0, help="extra untimed sweeps before warm-up")
     ap.add_argument("--impl", default="ggf", choices=["ggf", "reference"])

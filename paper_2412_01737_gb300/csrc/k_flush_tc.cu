@@ -10,15 +10,16 @@
 // V^T, B operand: rows of U), so the TMEM lane is the output column and the
 // TMEM column the output row: in the epilogue a warp's 32 lanes hold 32
 // consecutive columns of W for every row it reads, and its loads and stores
-// of W are coalesced without staging.  Persistent CTAs of 128 threads (three
-// per SM for real pairs, two for complex) walk tiles of 128 columns x 128 rows
+// of W are coalesced without staging.  Persistent CTAs of 128 threads walk
+// tiles of 128 columns x 128 rows
 // (real) or 128 complex columns x 64 rows (complex: two 64-column
-// accumulators, re and im, in the 128 TMEM columns allocated once).  Per
-// 32-wide rank chunk the operands are loaded (float4, all loads in flight),
-// split into tf32 hi/lo and written in the no-swizzle K-major core-matrix
-// layout (8 rows x 16 bytes per core matrix, LBO = 128 B along K, SBO =
-// 1024 B between 8-row groups); one thread issues the MMAs (M = 128, K = 8
-// each) and commits them to an mbarrier.  Every wait on the mbarrier is bounded; on
+// accumulators, re and im, in the 128 TMEM columns allocated once); four
+// CTAs share an SM (all 512 TMEM columns) so that one CTA's loads overlap
+// another's MMAs and stores.  Per 16-wide rank chunk the operands are loaded
+// (float4, all loads in flight), split into tf32 hi/lo and written in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
+// LBO = 128 B along K, SBO = 512 B between 8-row groups); one thread issues
+// the MMAs (M = 128, K = 8 each) and commits them to an mbarrier.  Every wait on the mbarrier is bounded; on
 // expiry the kernel raises the device error word and frees its TMEM.
 #include <cstring>
 #include "ggf_ctx.h"
@@ -26,24 +27,26 @@
 namespace {
 
 constexpr int TC_THREADS = 128;
-constexpr int KCH = 32;                       // rank chunk (tf32 elements)
-constexpr int TILE_BYTES_128 = 128 * KCH * 4; // 16 KB per 128-row operand plane
-constexpr int smem_bytes(bool cplx) { return (cplx ? 96 : 64) * 1024 + 1024; }
+constexpr int KCH = 16;                       // rank chunk (tf32 elements)
+constexpr int SBO = KCH / 4 * 128;            // bytes between 8-row core-matrix groups
+constexpr int TILE_BYTES_128 = 128 * KCH * 4; // 8 KB per 128-row operand plane
+constexpr int CTAS_PER_SM = 4;                // 4 x 128 TMEM columns = all 512
+constexpr int smem_bytes(bool cplx) { return (cplx ? 48 : 32) * 1024 + 1024; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// byte offset of (row, k) inside a K-major no-swizzle operand tile (32 wide)
+// byte offset of (row, k) inside a K-major no-swizzle operand tile (KCH wide)
 __device__ __forceinline__ uint32_t cm_off(int row, int k) {
-    return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+    return (uint32_t)((row >> 3) * SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);              // start address
     d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;         // leading byte offset (K direction)
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;        // stride byte offset (8-row groups)
+    d |= (uint64_t)(((uint32_t)SBO >> 4) & 0x3FFFu) << 32; // stride byte offset (8-row groups)
     d |= (uint64_t)1 << 46;                               // descriptor version for sm_100 family
     return d;                                             // base offset 0, no swizzle
 }
@@ -90,18 +93,19 @@ template <int ROWS>
 __device__ __forceinline__ void stage_plane(const float* src, int KRM, int row0, int row_lim, int k0, int K,
                                             unsigned char* hi, unsigned char* lo) {
     constexpr int PER = ROWS * (KCH / 4) / TC_THREADS;   // float4 per thread
+    constexpr int Q4 = KCH / 4;                          // float4 per row
     float4 v[PER];
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         int idx = threadIdx.x + t * TC_THREADS;
-        int row = idx >> 3, q4 = idx & 7;
+        int row = idx / Q4, q4 = idx % Q4;
         int gr = row0 + row, gk = k0 + 4 * q4;
         v[t] = (gr < row_lim && gk < K) ? *(const float4*)(src + (size_t)gr * KRM + gk) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         int idx = threadIdx.x + t * TC_THREADS;
-        int row = idx >> 3, q4 = idx & 7;
+        int row = idx / Q4, q4 = idx % Q4;
         float4 h = make_float4(tf32_hi(v[t].x), tf32_hi(v[t].y), tf32_hi(v[t].z), tf32_hi(v[t].w));
         float4 l = make_float4(v[t].x - h.x, v[t].y - h.y, v[t].z - h.z, v[t].w - h.w);
         uint32_t o = cm_off(row, 4 * q4);
@@ -111,7 +115,7 @@ __device__ __forceinline__ void stage_plane(const float* src, int KRM, int row0,
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(TC_THREADS, CPLX ? 2 : 3)
+__global__ void __launch_bounds__(TC_THREADS, CTAS_PER_SM)
 flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, const int* pend, int R, int KRM,
                 int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -226,57 +230,52 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
         if (s_fail) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         // epilogue: lane = output column j, register k of block cb = output row
-        // i0 + 32 cb + k; a warp touches 32 consecutive columns (coalesced)
+        // i0 + 16 cb + k; a warp touches 32 consecutive columns (coalesced)
         {
             const int j = j0 + warp * 32 + lane;
             const uint32_t tl = tbase + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-            for (int cb = 0; cb < NROW / 32; ++cb) {
-                uint32_t v[32];
+            for (int cb = 0; cb < NROW / 16; ++cb) {
+                uint32_t v[16];
                 asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                    " [%16];"
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                       "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(tl + cb * 32));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                      "=r"(v[15])
+                    : "r"(tl + cb * 16));
                 if (!CPLX) {
-                    float w[32];
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float w[16];
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const int i = i0 + cb * 32 + k;
+                    for (int k = 0; k < 16; ++k) {
+                        const int i = i0 + cb * 16 + k;
                         w[k] = (i < N && j < N) ? Wp[(size_t)i * N + j] : 0.f;
                     }
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const int i = i0 + cb * 32 + k;
+                    for (int k = 0; k < 16; ++k) {
+                        const int i = i0 + cb * 16 + k;
                         if (i < N && j < N) Wp[(size_t)i * N + j] = w[k] - __uint_as_float(v[k]);
                     }
                 } else {
-                    uint32_t vi[32];
+                    uint32_t vi[16];
                     asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
                         : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
                           "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]),
-                          "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15]), "=r"(vi[16]), "=r"(vi[17]), "=r"(vi[18]),
-                          "=r"(vi[19]), "=r"(vi[20]), "=r"(vi[21]), "=r"(vi[22]), "=r"(vi[23]), "=r"(vi[24]),
-                          "=r"(vi[25]), "=r"(vi[26]), "=r"(vi[27]), "=r"(vi[28]), "=r"(vi[29]), "=r"(vi[30]),
-                          "=r"(vi[31])
-                        : "r"(tl + 64 + cb * 32));
+                          "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
+                        : "r"(tl + 64 + cb * 16));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    float2 w[32];
+                    float2 w[16];
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const int i = i0 + cb * 32 + k;
+                    for (int k = 0; k < 16; ++k) {
+                        const int i = i0 + cb * 16 + k;
                         w[k] = (i < N && j < N) ? *(const float2*)(Wp + (size_t)i * rowW + 2 * j) : make_float2(0.f, 0.f);
                     }
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const int i = i0 + cb * 32 + k;
+                    for (int k = 0; k < 16; ++k) {
+                        const int i = i0 + cb * 16 + k;
                         if (i < N && j < N)
                             *(float2*)(Wp + (size_t)i * rowW + 2 * j) =
                                 make_float2(w[k].x - __uint_as_float(v[k]), w[k].y - __uint_as_float(vi[k]));
@@ -303,7 +302,7 @@ ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long grid = std::min<long long>(total, (long long)sms * (cplx ? 2 : 3));
+    const long long grid = std::min<long long>(total, (long long)sms * CTAS_PER_SM);
     if (cplx) {
         GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(true)));
         flush_tc_kernel<true><<<(unsigned)grid, TC_THREADS, smem_bytes(true), st>>>(N, fam_pairs, n_chains, W, Pan,
