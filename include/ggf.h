@@ -138,6 +138,9 @@ typedef struct {
                            W_eff = W - U V, and fold them into W with one
                            rank-(k r) product every k link steps (delayed
                            Sherman-Morrison-Woodbury updates). */
+    int graph;          /* != 0: capture one sweep (all link steps, flushes,
+                           observables) into a CUDA graph on first use and
+                           replay it; 0: launch every kernel eagerly */
 } ggf_chain_opts;
 
 /* Create n_chains Markov chains starting at links [n_chains][2V] and build
@@ -156,6 +159,17 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links,
  * -> u_propose, u = (word >> 11) 2^-53.
  *   obs [n_sweeps][n_chains][GGF_N_OBS] (may be NULL) */
 ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* stream);
+
+/* Sweep several independent problems together (uneven lattices, groups,
+ * K, precisions): every context's captured sweep becomes a child of one
+ * parent CUDA graph, so each sweep of the whole batch is a single graph
+ * launch on the device.  All contexts must be on the same device, have chains
+ * initialised with opts.graph != 0, and appear once.  obs[k] (may be NULL)
+ * receives context k's observables as in ggf_sample.  Refreshes run per
+ * context between launches.  Per-kernel timing (ggf_profile) is not recorded
+ * in this mode. */
+ggf_status ggf_sample_group(ggf_ctx* const* ctxs, int n_ctx, int n_sweeps, double* const* obs, int mem,
+                            void* stream);
 
 /* Current links of all chains, [n_chains][2V]. */
 ggf_status ggf_chains_links(ggf_ctx* ctx, void* links, int mem, void* stream);

@@ -12,6 +12,9 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st);
 ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st);
 ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
+ggf_status ggf_prepare_sampler(ggf_ctx* ctx);
+ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx);
+ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -36,6 +39,12 @@ ggf_status ggf_workspace(ggf_ctx* ctx, size_t bytes) {
 
 void ggf_free_chains(ggf_ctx* ctx) {
     Chains& c = ctx->ch;
+    if (c.gexec) cudaGraphExecDestroy(c.gexec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    if (c.cs) cudaStreamDestroy(c.cs);
+    if (c.join) cudaEventDestroy(c.join);
+    if (c.d_sweep) cudaFree(c.d_sweep);
+    if (c.d_obs_stage) cudaFree(c.d_obs_stage);
     void* ptrs[] = {c.links, c.Wr, c.Wc, c.ell, c.zbuf, c.ybuf, c.accept, c.since_refresh,
                     c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend};
     for (void* p : ptrs)
@@ -222,6 +231,7 @@ ggf_status ggf_create(ggf_ctx** out, int device) {
     if (cudaSetDevice(device) != cudaSuccess) return GGF_ECUDA;
     ggf_ctx* c = new ggf_ctx();
     c->device = device;
+    cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
         delete c;
         return GGF_ENOMEM;
@@ -441,6 +451,13 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     }
     GGF_CK(cudaMalloc(&ch.pend, n_chains * sizeof(int)));
     GGF_CK(cudaMemsetAsync(ch.pend, 0, n_chains * sizeof(int), st));
+    GGF_CK(cudaMalloc(&ch.d_sweep, sizeof(unsigned long long)));
+    GGF_CK(cudaMemsetAsync(ch.d_sweep, 0, sizeof(unsigned long long), st));
+    GGF_CK(cudaMalloc(&ch.d_obs_stage, (size_t)n_chains * GGF_N_OBS * sizeof(double)));
+    GGF_CK(cudaStreamCreateWithFlags(&ch.cs, cudaStreamNonBlocking));
+    GGF_CK(cudaEventCreateWithFlags(&ch.join, cudaEventDisableTiming));
+    GGF_TRY(ggf_prepare_sampler(ctx));
+    if (!fp64) GGF_TRY(ggf_prepare_flush_tc(ctx));
     GGF_CK(cudaMalloc(&ch.accept, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.since_refresh, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.sweep_acc, n_chains * sizeof(int)));
@@ -486,72 +503,222 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     return GGF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One sweep of every chain: link steps, pending flush, observables, refresh
+// marks, sweep counter.  The same sequence is either launched eagerly or
+// captured once into a CUDA graph and replayed.
+ggf_status sweep_body(ggf_ctx* ctx, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    GGF_CK(cudaMemsetAsync(ch.sweep_acc, 0, ch.n * sizeof(int), st));
+    for (int l = 0; l < ctx->g.n_links; ++l) GGF_TRY(ggf_link_step(ctx, l, st));
+    GGF_TRY(ggf_flush(ctx, st));
+    GGF_TRY(ggf_observe(ctx, ch.d_obs_stage, st));
+    GGF_TRY(ggf_mark_refresh(ctx, st));
+    GGF_TRY(ggf_bump_sweep(ctx, st));
+    return GGF_OK;
+}
+
+void drop_graph(Chains& ch) {
+    if (ch.gexec) cudaGraphExecDestroy(ch.gexec);
+    if (ch.graph) cudaGraphDestroy(ch.graph);
+    ch.gexec = nullptr;
+    ch.graph = nullptr;
+    ch.gev_cat.clear();
+}
+
+ggf_status ensure_graph(ggf_ctx* ctx) {
+    Chains& ch = ctx->ch;
+    if (ch.gexec && ch.graph_prof == ctx->prof) return GGF_OK;
+    drop_graph(ch);
+    if (ctx->prof) {   // events must exist before capture
+        const int need = 3 * ctx->g.n_links + 2 * (ctx->g.n_links / std::max(1, ch.kmax) + 2) + 8;
+        while ((int)ctx->ev.size() < need) {
+            cudaEvent_t e;
+            GGF_CK(cudaEventCreate(&e));
+            ctx->ev.push_back(e);
+        }
+    }
+    ctx->ev_used = 0;
+    ctx->ev_cat.clear();
+    const unsigned long long l0 = ctx->launches;
+    GGF_CK(cudaStreamBeginCapture(ch.cs, cudaStreamCaptureModeThreadLocal));
+    ggf_status s = sweep_body(ctx, ch.cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ch.cs, &g);
+    if (s != GGF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return ggf_cuda(ctx, e, "cudaStreamEndCapture");
+    ch.graph = g;
+    GGF_CK(cudaGraphInstantiate(&ch.gexec, g, 0));
+    ch.graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    ch.gev_cat = ctx->ev_cat;
+    ctx->ev_cat.clear();
+    ctx->ev_used = 0;
+    ch.graph_prof = ctx->prof;
+    return GGF_OK;
+}
+
+ggf_status accumulate_events(ggf_ctx* ctx, const std::vector<int>& cat) {
+    for (size_t k = 0; k + 2 < cat.size(); k += 3) {
+        float ms = 0;
+        GGF_CK(cudaEventElapsedTime(&ms, ctx->ev[cat[k + 1]], ctx->ev[cat[k + 2]]));
+        ctx->kt_ms[cat[k]] += ms;
+        ctx->kt_n[cat[k]] += 1;
+    }
+    return GGF_OK;
+}
+
+// After a sweep's kernels: observables out, refresh of the marked chains.
+ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem) {
+    Chains& ch = ctx->ch;
+    cudaStream_t cs = ch.cs;
+    if (obs_dst)
+        GGF_CK(cudaMemcpyAsync(obs_dst, ch.d_obs_stage, (size_t)ch.n * GGF_N_OBS * sizeof(double),
+                               mem == GGF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, cs));
+    int cnt = 0;
+    GGF_CK(cudaMemcpyAsync(&cnt, ch.refresh_list, sizeof(int), cudaMemcpyDeviceToHost, cs));
+    GGF_CK(cudaStreamSynchronize(cs));
+    if (ctx->prof) {
+        GGF_TRY(accumulate_events(ctx, ch.opts.graph ? ch.gev_cat : ctx->ev_cat));
+        ctx->ev_cat.clear();
+        ctx->ev_used = 0;
+    }
+    if (cnt > 0) {
+        std::vector<int> list(cnt);
+        GGF_CK(cudaMemcpyAsync(list.data(), ch.refresh_list + 1, cnt * sizeof(int), cudaMemcpyDeviceToHost, cs));
+        GGF_CK(cudaStreamSynchronize(cs));
+        std::sort(list.begin(), list.end());
+        const int r0 = ctx->prof_mark(cs);
+        GGF_TRY(factor_chains(ctx, list, false, cs));
+        ctx->prof_pair(GGF_KT_REFRESH, r0, ctx->prof_mark(cs));
+        GGF_CK(cudaStreamSynchronize(cs));
+        if (ctx->prof) {
+            GGF_TRY(accumulate_events(ctx, ctx->ev_cat));
+            ctx->ev_cat.clear();
+            ctx->ev_used = 0;
+        }
+        unsigned long long h[4];
+        GGF_CK(cudaMemcpy(h, ch.counters, sizeof(h), cudaMemcpyDeviceToHost));
+        h[2] += cnt;
+        GGF_CK(cudaMemcpy(ch.counters + 2, &h[2], sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    }
+    ch.sweep += 1;
+    return GGF_OK;
+}
+
+ggf_status check_err_word(ggf_ctx* ctx) {
+    int herr = 0;
+    GGF_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return ggf_fail(ctx, GGF_ETIMEOUT, "a bounded device wait ran out (tensor-core flush)");
+    return GGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* stream) {
     GGF_TRY(require(ctx, true, true));
     if (n_sweeps < 0) return ggf_fail(ctx, GGF_EINVAL, "n_sweeps < 0");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     Chains& ch = ctx->ch;
-    const Geometry& g = ctx->g;
-    DBuf dobs;
-    double* d_obs = obs;
-    if (obs && mem == GGF_MEM_HOST) {
-        GGF_TRY(dalloc(ctx, dobs, (size_t)ch.n * GGF_N_OBS * sizeof(double)));
-        d_obs = (double*)dobs.p;
-    }
-    std::vector<int> list;
-    auto drain_events = [&]() -> ggf_status {
-        for (size_t k = 0; k + 2 < ctx->ev_cat.size(); k += 3) {
-            float ms = 0;
-            GGF_CK(cudaEventElapsedTime(&ms, ctx->ev[ctx->ev_cat[k + 1]], ctx->ev[ctx->ev_cat[k + 2]]));
-            ctx->kt_ms[ctx->ev_cat[k]] += ms;
-            ctx->kt_n[ctx->ev_cat[k]] += 1;
-        }
-        ctx->ev_cat.clear();
-        ctx->ev_used = 0;
-        return GGF_OK;
-    };
+    // the library stream waits for the caller's stream, and the caller's stream for it at the end
+    GGF_CK(cudaEventRecord(ch.join, st));
+    GGF_CK(cudaStreamWaitEvent(ch.cs, ch.join, 0));
     for (int s = 0; s < n_sweeps; ++s) {
-        GGF_CK(cudaMemsetAsync(ch.sweep_acc, 0, ch.n * sizeof(int), st));
-        ctx->ev_used = 0;
-        ctx->ev_cat.clear();
-        for (int l = 0; l < g.n_links; ++l) GGF_TRY(ggf_link_step(ctx, l, st));
-        GGF_TRY(ggf_flush(ctx, st));   // pending delayed updates before observables and refresh
-        if (obs) {
-            double* dst = mem == GGF_MEM_HOST ? d_obs : d_obs + (size_t)s * ch.n * GGF_N_OBS;
-            GGF_TRY(ggf_observe(ctx, dst, st));
-            if (mem == GGF_MEM_HOST)
-                GGF_CK(cudaMemcpyAsync(obs + (size_t)s * ch.n * GGF_N_OBS, d_obs, (size_t)ch.n * GGF_N_OBS * sizeof(double),
-                                       cudaMemcpyDeviceToHost, st));
+        if (ch.opts.graph) {
+            GGF_TRY(ensure_graph(ctx));
+            GGF_CK(cudaGraphLaunch(ch.gexec, ch.cs));
+            ctx->launches += ch.graph_launches;
+        } else {
+            ctx->ev_used = 0;
+            ctx->ev_cat.clear();
+            GGF_TRY(sweep_body(ctx, ch.cs));
         }
-        GGF_TRY(ggf_mark_refresh(ctx, st));
-        int cnt = 0;
-        GGF_CK(cudaMemcpyAsync(&cnt, ch.refresh_list, sizeof(int), cudaMemcpyDeviceToHost, st));
-        GGF_CK(cudaStreamSynchronize(st));
-        GGF_TRY(drain_events());
-        if (cnt > 0) {
-            list.resize(cnt);
-            GGF_CK(cudaMemcpyAsync(list.data(), ch.refresh_list + 1, cnt * sizeof(int), cudaMemcpyDeviceToHost, st));
-            GGF_CK(cudaStreamSynchronize(st));
-            std::sort(list.begin(), list.end());
-            const int r0 = ctx->prof_mark(st);
-            GGF_TRY(factor_chains(ctx, list, false, st));
-            ctx->prof_pair(GGF_KT_REFRESH, r0, ctx->prof_mark(st));
-            GGF_CK(cudaStreamSynchronize(st));
-            GGF_TRY(drain_events());
-            unsigned long long h[4];
-            GGF_CK(cudaMemcpyAsync(h, ch.counters, sizeof(h), cudaMemcpyDeviceToHost, st));
-            GGF_CK(cudaStreamSynchronize(st));
-            h[2] += cnt;
-            GGF_CK(cudaMemcpyAsync(ch.counters + 2, &h[2], sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
-        }
-        ch.sweep += 1;
+        GGF_TRY(finish_sweep(ctx, obs ? obs + (size_t)s * ch.n * GGF_N_OBS : nullptr, mem));
     }
+    GGF_CK(cudaEventRecord(ch.join, ch.cs));
+    GGF_CK(cudaStreamWaitEvent(st, ch.join, 0));
     GGF_CK(cudaStreamSynchronize(st));
-    int herr = 0;
-    GGF_CK(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr) return ggf_fail(ctx, GGF_ETIMEOUT, "a bounded device wait ran out (tensor-core flush)");
-    return GGF_OK;
+    return check_err_word(ctx);
+}
+
+ggf_status ggf_sample_group(ggf_ctx* const* ctxs, int n_ctx, int n_sweeps, double* const* obs, int mem,
+                            void* stream) {
+    if (!ctxs || n_ctx < 1 || n_sweeps < 0) return GGF_EINVAL;
+    for (int k = 0; k < n_ctx; ++k) {
+        GGF_TRY(require(ctxs[k], true, true));
+        if (ctxs[k]->device != ctxs[0]->device) return ggf_fail(ctxs[0], GGF_EINVAL, "contexts on different devices");
+        if (!ctxs[k]->ch.opts.graph) return ggf_fail(ctxs[k], GGF_EINVAL, "group sampling needs graph mode");
+        for (int m = 0; m < k; ++m)
+            if (ctxs[m] == ctxs[k]) return ggf_fail(ctxs[k], GGF_EINVAL, "context listed twice");
+    }
+    ggf_ctx* ctx = ctxs[0];
+    cudaSetDevice(ctx->device);
+    for (int k = 0; k < n_ctx; ++k) {
+        // children hold no event-record nodes: capture without profiling events
+        const bool prof = ctxs[k]->prof;
+        ctxs[k]->prof = false;
+        ggf_status s = ensure_graph(ctxs[k]);
+        ctxs[k]->prof = prof;
+        GGF_TRY(s);
+    }
+    // one parent graph whose independent children are the contexts' sweeps
+    cudaGraph_t pg = nullptr;
+    cudaGraphExec_t pexec = nullptr;
+    GGF_CK(cudaGraphCreate(&pg, 0));
+    for (int k = 0; k < n_ctx; ++k) {
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddChildGraphNode(&node, pg, nullptr, 0, ctxs[k]->ch.graph);
+        if (e != cudaSuccess) { cudaGraphDestroy(pg); return ggf_cuda(ctx, e, "cudaGraphAddChildGraphNode"); }
+    }
+    cudaError_t e = cudaGraphInstantiate(&pexec, pg, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(pg); return ggf_cuda(ctx, e, "cudaGraphInstantiate(group)"); }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t gs = ctx->ch.cs;
+    ggf_status rc = GGF_OK;
+    do {
+        if (cudaEventRecord(ctx->ch.join, st) != cudaSuccess || cudaStreamWaitEvent(gs, ctx->ch.join, 0) != cudaSuccess) {
+            rc = ggf_fail(ctx, GGF_ECUDA, "stream join failed");
+            break;
+        }
+        for (int s = 0; s < n_sweeps && rc == GGF_OK; ++s) {
+            e = cudaGraphLaunch(pexec, gs);
+            if (e != cudaSuccess) { rc = ggf_cuda(ctx, e, "cudaGraphLaunch(group)"); break; }
+            // the other contexts' streams see the group launch before their own copies and refreshes
+            if (cudaEventRecord(ctx->ch.join, gs) != cudaSuccess) { rc = ggf_fail(ctx, GGF_ECUDA, "event"); break; }
+            for (int k = 0; k < n_ctx && rc == GGF_OK; ++k) {
+                ggf_ctx* c = ctxs[k];
+                c->launches += c->ch.graph_launches;
+                if (k > 0) cudaStreamWaitEvent(c->ch.cs, ctx->ch.join, 0);
+                double* dst = (obs && obs[k]) ? obs[k] + (size_t)s * c->ch.n * GGF_N_OBS : nullptr;
+                bool prof = c->prof;
+                c->prof = false;       // per-kernel timing is not collected in group mode
+                rc = finish_sweep(c, dst, mem);
+                c->prof = prof;
+            }
+        }
+        if (rc == GGF_OK) {
+            cudaEventRecord(ctx->ch.join, gs);
+            cudaStreamWaitEvent(st, ctx->ch.join, 0);
+            if (cudaStreamSynchronize(st) != cudaSuccess) rc = ggf_fail(ctx, GGF_ECUDA, "group sync failed");
+        }
+    } while (0);
+    cudaGraphExecDestroy(pexec);
+    cudaGraphDestroy(pg);
+    for (int k = 0; k < n_ctx && rc == GGF_OK; ++k) {
+        // each context's later work must also see the group's last sweep
+        cudaStreamSynchronize(ctxs[k]->ch.cs);
+        rc = check_err_word(ctxs[k]);
+    }
+    return rc;
 }
 
 ggf_status ggf_chains_links(ggf_ctx* ctx, void* links, int mem, void* stream) {
@@ -643,7 +810,7 @@ ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path) {
     GGF_CK(cudaMemcpy(cnt, ch.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
     FILE* f = fopen(path, "wb");
     if (!f) return ggf_fail(ctx, GGF_EIO, std::string("cannot open ") + path);
-    const char magic[8] = {'G', 'G', 'F', 'C', 'K', 'P', 'T', '1'};
+    const char magic[8] = {'G', 'G', 'F', 'C', 'K', 'P', 'T', '2'};
     int hdr[8] = {g.L, g.group, g.n_v, ctx->K, ch.n, ctx->P, 0, 0};
     bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               fwrite(&ch.opts, sizeof(ch.opts), 1, f) == 1 && fwrite(&ch.sweep, sizeof(ch.sweep), 1, f) == 1 &&
@@ -665,7 +832,7 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream) {
     ggf_chain_opts o;
     uint64_t sweep;
     unsigned long long cnt[4];
-    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GGFCKPT1", 8) == 0 &&
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GGFCKPT2", 8) == 0 &&
               fread(hdr, sizeof(hdr), 1, f) == 1 && fread(&o, sizeof(o), 1, f) == 1 &&
               fread(&sweep, sizeof(sweep), 1, f) == 1 && fread(cnt, sizeof(cnt), 1, f) == 1;
     const Geometry& g = ctx->g;
@@ -691,6 +858,8 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream) {
     GGF_CK(cudaMemcpyAsync(ch.ell, he.data(), he.size() * sizeof(cxd), cudaMemcpyHostToDevice, st));
     GGF_CK(cudaMemcpyAsync(ch.since_refresh, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     GGF_CK(cudaMemcpyAsync(ch.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
+    unsigned long long sw = sweep;
+    GGF_CK(cudaMemcpyAsync(ch.d_sweep, &sw, sizeof(sw), cudaMemcpyHostToDevice, st));
     GGF_CK(cudaStreamSynchronize(st));
     ch.sweep = sweep;
     return GGF_OK;

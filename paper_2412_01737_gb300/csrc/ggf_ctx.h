@@ -50,6 +50,16 @@ struct Chains {
     int* pend = nullptr;          // [n]
     int kmax = 1;
     int steps_since_flush = 0;
+    // one sweep captured as a CUDA graph (opts.graph != 0)
+    unsigned long long* d_sweep = nullptr;   // device copy of the sweep counter
+    double* d_obs_stage = nullptr;           // [n][GGF_N_OBS] observables of the last sweep
+    cudaStream_t cs = nullptr;               // library stream the graph runs on
+    cudaEvent_t join = nullptr;              // stream-join event
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_prof = false;                 // graph holds event-record nodes
+    std::vector<int> gev_cat;                // (category, start, end) event triples of the graph
+    unsigned long long graph_launches = 0;   // kernels per replay
 };
 
 struct ggf_ctx {
@@ -93,6 +103,7 @@ struct ggf_ctx {
         ev_cat.push_back(cat); ev_cat.push_back(a); ev_cat.push_back(b);
     }
     unsigned long long launches = 0;   // kernels launched by ggf_sample
+    int n_sms = 0;
     DevConst dc() const {
         DevConst c;
         c.g = g; c.K = K; c.P = P; c.Kc = Kc;

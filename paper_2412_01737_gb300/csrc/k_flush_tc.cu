@@ -293,22 +293,34 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
     }
 }
 
+}  // namespace
+
+// Shared-memory attributes of the tensor-core flush, set once per process and
+// device ordinal outside any stream capture.
+ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx) {
+    static bool done[64] = {false};
+    if (ctx->device >= 0 && ctx->device < 64 && done[ctx->device]) return GGF_OK;
+    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(true)));
+    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false)));
+    if (ctx->device >= 0 && ctx->device < 64) done[ctx->device] = true;
+    return GGF_OK;
+}
+
+namespace {
+
 ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_chains, float* W, const float* Pan,
                            const int* pend, int R, int KRM, int* err, cudaStream_t st) {
     if (fam_pairs == 0 || n_chains == 0) return GGF_OK;
     const int rowW = cplx ? 2 * N : N;
     const long long total = (long long)n_chains * fam_pairs * ((N + (cplx ? 63 : 127)) / (cplx ? 64 : 128)) *
                             ((N + 127) / 128);
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int sms = ctx->n_sms > 0 ? ctx->n_sms : 152;
     const long long grid = std::min<long long>(total, (long long)sms * CTAS_PER_SM);
+    GGF_TRY(ggf_prepare_flush_tc(ctx));
     if (cplx) {
-        GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(true)));
         flush_tc_kernel<true><<<(unsigned)grid, TC_THREADS, smem_bytes(true), st>>>(N, fam_pairs, n_chains, W, Pan,
                                                                                     pend, R, KRM, err);
     } else {
-        GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false)));
         flush_tc_kernel<false><<<(unsigned)grid, TC_THREADS, smem_bytes(false), st>>>(N, fam_pairs, n_chains, W, Pan,
                                                                                       pend, R, KRM, err);
     }

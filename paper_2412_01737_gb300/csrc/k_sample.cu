@@ -121,7 +121,7 @@ template <> __device__ __forceinline__ void PanelIO<cxf>::st(float* p, size_t pl
 struct SweepArgs {
     DevConst dc;
     int n_chains;
-    uint64_t sweep;
+    const unsigned long long* d_sweep;   // sweep index (device, so captured sweeps replay)
     int link;
     uint64_t seed;
     double width;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
     const int a0 = s * g.B + (2 * d + 1) * g.h2, b0 = t * g.B + (2 * d) * g.h2;
 
     if (threadIdx.x == 0) {
-        uint64_t ctr[4] = {a.sweep, (uint64_t)l, 0, 0}, out[4];
+        uint64_t ctr[4] = {(uint64_t)*a.d_sweep, (uint64_t)l, 0, 0}, out[4];
         philox4x64_10(ctr, a.seed, (uint64_t)c, out);
         double u_acc = u53(out[0]), u_prop = u53(out[1]);
         s_new_t = u_acc;  // temporarily hold u_acc
@@ -563,7 +563,7 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     SweepArgs a;
     a.dc = ctx->dc();
     a.n_chains = ch.n;
-    a.sweep = ch.sweep;
+    a.d_sweep = ch.d_sweep;
     a.link = link;
     a.seed = ch.opts.seed;
     a.width = ch.opts.width;
@@ -586,13 +586,8 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     size_t smem = ggf_ratio_smem(ctx->P, g.r);
     const int ev0 = ctx->prof_mark(st);
     ctx->launches += 2 + (ctx->Kc ? 1 : 0);
-    if (fp64) {
-        cudaFuncSetAttribute(ratio_kernel<double, cxd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        ratio_kernel<double, cxd><<<ch.n, NWARP * 32, smem, st>>>(a);
-    } else {
-        cudaFuncSetAttribute(ratio_kernel<float, cxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        ratio_kernel<float, cxf><<<ch.n, NWARP * 32, smem, st>>>(a);
-    }
+    if (fp64) ratio_kernel<double, cxd><<<ch.n, NWARP * 32, smem, st>>>(a);
+    else ratio_kernel<float, cxf><<<ch.n, NWARP * 32, smem, st>>>(a);
     GGF_CK(cudaGetLastError());
     const int ev1 = ctx->prof_mark(st);
     ctx->prof_pair(GGF_KT_RATIO, ev0, ev1);
@@ -679,6 +674,24 @@ ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st) {
     ctx->launches += 2 + (ctx->Kc ? 1 : 0);
     GGF_CK(cudaGetLastError());
     ch.steps_since_flush = 0;
+    return GGF_OK;
+}
+
+__global__ void bump_sweep(unsigned long long* s) { *s += 1ULL; }
+
+// Kernel attributes are set once per context before any launch, so that no
+// attribute call happens while a sweep is being captured into a graph.
+ggf_status ggf_prepare_sampler(ggf_ctx* ctx) {
+    size_t smem = ggf_ratio_smem(ctx->P, ctx->g.r);
+    GGF_CK(cudaFuncSetAttribute(ratio_kernel<double, cxd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GGF_CK(cudaFuncSetAttribute(ratio_kernel<float, cxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return GGF_OK;
+}
+
+ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st) {
+    bump_sweep<<<1, 1, 0, st>>>(ctx->ch.d_sweep);
+    ctx->launches += 1;
+    GGF_CK(cudaGetLastError());
     return GGF_OK;
 }
 

@@ -35,7 +35,7 @@ class GGFError(RuntimeError):
 
 class ChainOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refresh_every", ctypes.c_int), ("width", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("delay", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("delay", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class ChainStats(ctypes.Structure):
@@ -46,7 +46,7 @@ class ChainStats(ctypes.Structure):
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
-           "ggf_sample", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
+           "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
            "ggf_selftest_flush"]
 
@@ -76,6 +76,7 @@ def load():
         "ggf_observable": ([P, I, I, P, P, I, P], I),
         "ggf_chains_init": ([P, I, P, ctypes.POINTER(ChainOpts), I, P], I),
         "ggf_sample": ([P, I, P, I, P], I),
+        "ggf_sample_group": ([P, I, I, P, I, P], I),
         "ggf_chains_links": ([P, P, I, P], I),
         "ggf_chains_ell": ([P, P, I, P], I),
         "ggf_chains_inverse": ([P, I, I, P, I, P], I),
@@ -211,8 +212,8 @@ class GGF:
                                          _stream([links, out])))
         return out
 
-    def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202, delay=1):
-        o = ChainOpts(int(precision), int(refresh_every), float(width), int(seed), int(delay))
+    def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202, delay=1, graph=1):
+        o = ChainOpts(int(precision), int(refresh_every), float(width), int(seed), int(delay), int(graph))
         mem = self._mem(links)
         self.n_chains = int(links.shape[0])
         self.link_dtype = links.dtype
@@ -283,6 +284,21 @@ class GGF:
 
     def _links_from_state(self):
         raise RuntimeError("call init_problem/init_lattice through this object first")
+
+
+def sample_group(ctxs, n_sweeps):
+    """Sweep several contexts as one graph launch per sweep; returns their
+    observables (numpy, [n_sweeps, n_chains, 3] each)."""
+    lib = load()
+    n = len(ctxs)
+    handles = (ctypes.c_void_p * n)(*[c.h.value for c in ctxs])
+    outs = [np.zeros((int(n_sweeps), c.n_chains, N_OBS)) for c in ctxs]
+    ptrs = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+    st = lib.ggf_sample_group(handles, n, int(n_sweeps), ptrs, MEM_HOST, None)
+    if st != 0:
+        msgs = "; ".join(lib.ggf_last_error(c.h).decode() for c in ctxs)
+        raise GGFError(st, msgs)
+    return outs
 
 
 def _torch_like(t, shape):
