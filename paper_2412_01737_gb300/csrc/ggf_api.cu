@@ -457,7 +457,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     GGF_CK(cudaStreamCreateWithFlags(&ch.cs, cudaStreamNonBlocking));
     GGF_CK(cudaEventCreateWithFlags(&ch.join, cudaEventDisableTiming));
     GGF_TRY(ggf_prepare_sampler(ctx));
-    if (!fp64) GGF_TRY(ggf_prepare_flush_tc(ctx));
+    GGF_TRY(ggf_prepare_flush_tc(ctx));
     GGF_CK(cudaMalloc(&ch.accept, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.since_refresh, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.sweep_acc, n_chains * sizeof(int)));

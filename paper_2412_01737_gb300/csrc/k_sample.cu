@@ -681,10 +681,32 @@ __global__ void bump_sweep(unsigned long long* s) { *s += 1ULL; }
 
 // Kernel attributes are set once per context before any launch, so that no
 // attribute call happens while a sweep is being captured into a graph.
+// The attribute is a per-function cap shared by every context in the
+// process, so it is raised once to the device's opt-in maximum.
 ggf_status ggf_prepare_sampler(ggf_ctx* ctx) {
-    size_t smem = ggf_ratio_smem(ctx->P, ctx->g.r);
-    GGF_CK(cudaFuncSetAttribute(ratio_kernel<double, cxd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GGF_CK(cudaFuncSetAttribute(ratio_kernel<float, cxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static bool done[64] = {false};
+    if (ctx->device >= 0 && ctx->device < 64 && done[ctx->device]) return GGF_OK;
+    int mx = 0;
+    GGF_CK(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (ggf_ratio_smem(36, 8) > (size_t)mx) return ggf_fail(ctx, GGF_EINVAL, "shared memory too small for K = 8");
+    // dynamic cap = opt-in limit minus the kernel's static shared memory
+    auto cap = [&](const void* fn) -> ggf_status {
+        cudaFuncAttributes fa;
+        GGF_CK(cudaFuncGetAttributes(&fa, fn));
+        GGF_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
+        return GGF_OK;
+    };
+    GGF_TRY(cap((const void*)ratio_kernel<double, cxd>));
+    GGF_TRY(cap((const void*)ratio_kernel<float, cxf>));
+    GGF_TRY(cap((const void*)gather_kernel<double, 4>));
+    GGF_TRY(cap((const void*)gather_kernel<double, 8>));
+    GGF_TRY(cap((const void*)gather_kernel<float, 4>));
+    GGF_TRY(cap((const void*)gather_kernel<float, 8>));
+    GGF_TRY(cap((const void*)gather_kernel<cxd, 4>));
+    GGF_TRY(cap((const void*)gather_kernel<cxd, 8>));
+    GGF_TRY(cap((const void*)gather_kernel<cxf, 4>));
+    GGF_TRY(cap((const void*)gather_kernel<cxf, 8>));
+    if (ctx->device >= 0 && ctx->device < 64) done[ctx->device] = true;
     return GGF_OK;
 }
 
