@@ -186,6 +186,7 @@ typedef struct {
     uint64_t proposals, accepts, refreshes, sweeps;
     double max_drift;   /* max |l_tracked - l_refresh| over refreshes so far */
     uint64_t launches;  /* CUDA kernels launched by ggf_sample since ggf_chains_init */
+    uint64_t block_proposals, block_accepts;   /* learned-proposal block moves */
     int n_chains, n_pairs;
 } ggf_chain_stats;
 
@@ -220,6 +221,52 @@ ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launch
  * largest error relative to the largest entry of an FP64 reference.  Needs
  * only a context (allocates its own buffers).  Not part of the method. */
 ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank, double* max_rel_err);
+
+/* ---- Learned block proposal ------------------------------------------------
+ * A small convolutional network proposes new angles for the 32 links of a
+ * 4 x 4 block of sites (U(1) only) from the links outside the block; block
+ * moves are accepted by exact Metropolis-Hastings against p(G) (Sec. 5.1),
+ * so the sampled distribution does not depend on how well it is trained.
+ * Architecture: per-site input channels (cos, sin of the site's x- and
+ * y-link angles; cos, sin of the plaquette angle; block flags of the two
+ * links) with the block's links and the plaquettes containing them zeroed;
+ * 3x3 circular convolutions 8 -> 64 -> 64 -> 64 -> 6 with ReLU between; per
+ * block link a wrapped Cauchy density with mu = atan2(b, a), rho = 0.95
+ * sigmoid(z) from the head.  BF16 weights and activations, FP32 accumulation,
+ * FP32 master weights trained with Adam on configurations the sampler made.
+ * Parameters: one FP32 array of GGF_NET_PARAMS, per layer W[co][ci][3][3]
+ * then bias[co]. */
+#define GGF_NET_PARAMS 81990
+typedef struct ggf_net ggf_net;
+ggf_status ggf_net_create(ggf_net** out, int device, int L, uint64_t seed);
+void ggf_net_destroy(ggf_net* net);
+const char* ggf_net_last_error(const ggf_net* net);
+ggf_status ggf_net_get_params(ggf_net* net, float* out /* host, GGF_NET_PARAMS */);
+ggf_status ggf_net_set_params(ggf_net* net, const float* in /* host; resets Adam */);
+/* log q of the block links of n configurations: theta [n][2L^2], blocks
+ * [n][2] origins (bx, by), logq [n]. */
+ggf_status ggf_net_logq(ggf_net* net, int n, const double* theta, const int* blocks, double* logq, int mem,
+                        void* stream);
+/* Training loss (mean over the n samples of -sum log f) and its gradient
+ * [GGF_NET_PARAMS]; host arrays. */
+ggf_status ggf_net_loss_grad(ggf_net* net, int n, const double* theta, const int* blocks, double* loss,
+                             float* grad);
+/* n_steps Adam steps (lr; betas 0.9, 0.999) on minibatches of `batch`
+ * samples: a configuration drawn from theta [n_cfg][2L^2] (DEVICE) and a block
+ * origin, both from Philox.  losses [n_steps] host, optional. */
+ggf_status ggf_net_train(ggf_net* net, int n_cfg, const double* theta, int batch, int n_steps, float lr,
+                         float* losses, void* stream);
+
+/* n_moves block moves of every chain of a U(1) context whose chains were
+ * initialised with delay >= 32 (see the steps in the section comment): block
+ * origin per chain from Philox (counter (move, 0, 21, 0), key (seed, chain)),
+ * proposal from `net` (same lattice size), the 32 link changes applied as
+ * tentative rank-r updates whose Pfaffian ratios multiply to the block ratio,
+ * and Metropolis-Hastings acceptance u < [N(G')/N(G)] q(old)/q(new)
+ * (u from counter (move, 0, 23, 0)).  obs [n_moves][n_chains][GGF_N_OBS] as in
+ * ggf_sample (acceptance column: 1 or 0 for the move).  No refresh runs inside
+ * this call. */
+ggf_status ggf_sample_blocks(ggf_ctx* ctx, ggf_net* net, int n_moves, double* obs, int mem, void* stream);
 
 /* Wait for the context's work on `stream` and report device-side errors. */
 ggf_status ggf_sync(ggf_ctx* ctx, void* stream);

@@ -29,8 +29,14 @@ Network (shared convention with the CUDA kernels, each side its own code):
 * Training loss: mean over the batch of -sum over the 32 block links of
   log f(theta_link).
 
+Optional `quant`: a rounding function applied where the GPU network stores
+BF16 values (input features, weights, hidden activations after ReLU), so
+that the GPU kernels can be compared with the same arithmetic up to FP32
+accumulation; `bf16` below rounds to nearest even through FP32.
+
 Pinned (tests/test_oracle_net.py): gradients against central finite
-differences; the density integrates to 1; samples follow the density.
+differences; the density integrates to 1; samples follow the density; the
+BF16 rounding against hand-made bit patterns.
 """
 from __future__ import annotations
 
@@ -42,6 +48,14 @@ C_OUT = 6
 LAYERS = [(C_IN, CH), (CH, CH), (CH, CH), (CH, C_OUT)]
 RHO_MAX = 0.95
 BLOCK = 4
+
+
+def bf16(x):
+    """Round to the nearest bfloat16 (ties to even), via FP32, as float64."""
+    a = np.asarray(x, dtype=np.float32).copy()
+    u = a.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def n_params() -> int:
@@ -118,14 +132,16 @@ def conv_backward(X, W, dOut):
     return dX, dW, dOut.sum(axis=(0, 2, 3))
 
 
-def forward(params, X):
+def forward(params, X, quant=None):
     """Head outputs (B, 6, L, L) and the per-layer activations."""
+    q = quant if quant is not None else (lambda v: v)
+    X = q(X)
     acts = [X]
     h = X
     layers = unpack(params)
     for k, (W, b) in enumerate(layers):
-        z = conv(h, W, b)
-        h = np.maximum(z, 0.0) if k < len(layers) - 1 else z
+        z = conv(h, q(W), b)
+        h = q(np.maximum(z, 0.0)) if k < len(layers) - 1 else z
         acts.append(h)
     return h, acts
 
@@ -152,20 +168,21 @@ def sample_wc(mu, rho, u):
     return np.mod(t, 2 * np.pi)
 
 
-def log_q(params, theta, L, bx, by) -> float:
+def log_q(params, theta, L, bx, by, quant=None) -> float:
     """log density of the block links of `theta` under the proposal."""
-    out, _ = forward(params, features(theta, L, bx, by)[None])
+    out, _ = forward(params, features(theta, L, bx, by)[None], quant)
     mu, rho = head_params(out[0], L, bx, by)
     t = theta[block_links(L, bx, by)]
     return float(np.sum(log_wc(t, mu, rho)))
 
 
-def loss_and_grad(params, thetas, blocks, L):
+def loss_and_grad(params, thetas, blocks, L, quant=None):
     """Mean over samples of -sum log f, and its gradient w.r.t. params.
     thetas: (B, 2L^2) angles; blocks: (B, 2) block origins."""
     B = len(thetas)
     X = np.stack([features(thetas[k], L, *blocks[k]) for k in range(B)])
-    out, acts = forward(params, X)
+    out, acts = forward(params, X, quant)
+    q = quant if quant is not None else (lambda v: v)
     dOut = np.zeros_like(out)
     loss = 0.0
     for k in range(B):
@@ -197,7 +214,7 @@ def loss_and_grad(params, thetas, blocks, L):
     g = dOut
     for li in range(len(layers) - 1, -1, -1):
         W, b = layers[li]
-        dX, dW, db = conv_backward(acts[li], W, g)
+        dX, dW, db = conv_backward(acts[li], q(W), g)
         grads.append((dW, db))
         if li > 0:
             g = dX * (acts[li] > 0.0)

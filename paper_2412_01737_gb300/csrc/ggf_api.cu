@@ -428,6 +428,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     ch.opts = *opts;
     ch.n = n_chains;
     ch.sweep = 0;
+    ch.block_moves = 0;
     const Geometry& g = ctx->g;
     const bool fp64 = opts->precision == GGF_FP64;
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
@@ -439,7 +440,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     GGF_CK(cudaMalloc(&ch.ell, (size_t)n_chains * ctx->P * sizeof(cxd)));
     GGF_CK(cudaMalloc(&ch.zbuf, (size_t)n_chains * ctx->P * g.r * g.r * sizeof(cxd)));
     ch.kmax = opts->delay > 1 ? opts->delay : 1;
-    if (ch.kmax > 16) return ggf_fail(ctx, GGF_EINVAL, "delay must be <= 16");
+    if (ch.kmax > 64) return ggf_fail(ctx, GGF_EINVAL, "delay must be <= 64");
     ch.steps_since_flush = 0;
     if (ch.kmax > 1) {
         const size_t pr = (size_t)n_chains * ch.kmax * g.r * g.N * rsz;   // one plane per chain
@@ -461,13 +462,13 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     GGF_CK(cudaMalloc(&ch.accept, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.since_refresh, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.sweep_acc, n_chains * sizeof(int)));
-    GGF_CK(cudaMalloc(&ch.counters, 4 * sizeof(unsigned long long)));
+    GGF_CK(cudaMalloc(&ch.counters, 6 * sizeof(unsigned long long)));
     GGF_CK(cudaMalloc(&ch.drift, n_chains * sizeof(double)));
     GGF_CK(cudaMalloc(&ch.refresh_list, (n_chains + 1) * sizeof(int)));
     GGF_CK(cudaMemsetAsync(ch.accept, 0, n_chains * sizeof(int), st));
     GGF_CK(cudaMemsetAsync(ch.since_refresh, 0, n_chains * sizeof(int), st));
     GGF_CK(cudaMemsetAsync(ch.sweep_acc, 0, n_chains * sizeof(int), st));
-    GGF_CK(cudaMemsetAsync(ch.counters, 0, 4 * sizeof(unsigned long long), st));
+    GGF_CK(cudaMemsetAsync(ch.counters, 0, 6 * sizeof(unsigned long long), st));
     GGF_CK(cudaMemsetAsync(ch.drift, 0, n_chains * sizeof(double), st));
     // host copy of the starting links to find identical configurations
     std::vector<unsigned char> hl(lb);
@@ -497,7 +498,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
         GGF_CK(cudaMemcpyAsync(ch.ell + (size_t)c * ctx->P, ch.ell + (size_t)r0 * ctx->P, ctx->P * sizeof(cxd),
                                cudaMemcpyDeviceToDevice, st));
     }
-    GGF_CK(cudaMemsetAsync(ch.counters, 0, 4 * sizeof(unsigned long long), st));
+    GGF_CK(cudaMemsetAsync(ch.counters, 0, 6 * sizeof(unsigned long long), st));
     GGF_CK(cudaStreamSynchronize(st));
     ctx->launches = 0;
     return GGF_OK;
@@ -776,7 +777,7 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     GGF_TRY(require(ctx, true, true));
     if (!out) return ggf_fail(ctx, GGF_EINVAL, "null stats");
     cudaSetDevice(ctx->device);
-    unsigned long long h[4];
+    unsigned long long h[6];
     GGF_CK(cudaMemcpy(h, ctx->ch.counters, sizeof(h), cudaMemcpyDeviceToHost));
     std::vector<double> d(ctx->ch.n);
     GGF_CK(cudaMemcpy(d.data(), ctx->ch.drift, d.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -787,6 +788,8 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     out->max_drift = d.empty() ? 0.0 : *std::max_element(d.begin(), d.end());
     out->n_chains = ctx->ch.n;
     out->launches = ctx->launches;
+    out->block_proposals = h[4];
+    out->block_accepts = h[5];
     out->n_pairs = ctx->P;
     if (h[3]) return ggf_fail(ctx, GGF_ESINGULAR, "a refresh met a singular M(G)");
     return GGF_OK;

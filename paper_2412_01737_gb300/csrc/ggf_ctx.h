@@ -40,7 +40,7 @@ struct Chains {
     int* accept = nullptr;        // [n]
     int* since_refresh = nullptr; // [n]
     int* sweep_acc = nullptr;     // [n]
-    unsigned long long* counters = nullptr;  // [4]: proposals, accepts, refreshes, singular
+    unsigned long long* counters = nullptr;  // [6]: proposals, accepts, refreshes, singular, block proposals, block accepts
     double* drift = nullptr;      // [n] max drift seen
     int* refresh_list = nullptr;  // [n + 1]
     // delayed updates (opts.delay > 1): per chain and pair, U^T and V panels
@@ -50,6 +50,7 @@ struct Chains {
     int* pend = nullptr;          // [n]
     int kmax = 1;
     int steps_since_flush = 0;
+    unsigned long long block_moves = 0;      // learned-proposal moves made (Philox counter)
     // one sweep captured as a CUDA graph (opts.graph != 0)
     unsigned long long* d_sweep = nullptr;   // device copy of the sweep counter
     double* d_obs_stage = nullptr;           // [n][GGF_N_OBS] observables of the last sweep
@@ -61,6 +62,8 @@ struct Chains {
     std::vector<int> gev_cat;                // (category, start, end) event triples of the graph
     unsigned long long graph_launches = 0;   // kernels per replay
 };
+
+struct ggf_net;
 
 struct ggf_ctx {
     int device = 0;

@@ -141,6 +141,11 @@ struct SweepArgs {
     const void* Pc;   // complex-family panels [n][Kc][2][2][N][KRM]
     int* pend;
     int kmax;   // > 1: delayed
+    // block moves: per-chain link, forced new angle prop[c][32] entry k, dead flags
+    const int* link_of_chain;
+    const double* forced;
+    int forced_k;
+    int* dead;
 };
 
 template <class RW, class CW>
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
     __shared__ double s_old_g, s_new_g, s_old_t, s_new_t;
     __shared__ int s_accept;
 
-    const int l = a.link, s = l >> 1, d = l & 1;
+    const int l = a.link_of_chain ? a.link_of_chain[c] : a.link, s = l >> 1, d = l & 1;
     const int x = s % g.L, y = s / g.L;
     const int t = d == 0 ? y * g.L + (x + 1) % g.L : ((y + 1) % g.L) * g.L + x;
     const int a0 = s * g.B + (2 * d + 1) * g.h2, b0 = t * g.B + (2 * d) * g.h2;
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
             double tn = th + a.width * (u_prop - 0.5);
             if (tn >= GGF_TWO_PI) tn -= GGF_TWO_PI;
             else if (tn < 0.0) tn += GGF_TWO_PI;
+            if (a.forced) tn = a.forced[(size_t)c * 32 + a.forced_k];   // block move: given angle
             s_old_g = 1.0; s_new_g = 1.0; s_old_t = th;
             fcol[0] = {tn, 0.0};
         }
@@ -258,15 +264,27 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
             so += tt.x;
             sn += (tt * rho[p]).x;
         }
-        int acc = (sn > 0.0 && so > 0.0 && u_acc < sn / so) ? 1 : 0;
+        int acc;
+        if (a.forced) {
+            // block move: every link of the block is taken tentatively; the move is
+            // decided once the whole block's ratio is known
+            bool ok = a.dead[c] == 0;
+            for (int p = 0; p < P; ++p) ok = ok && isfinite(rho[p].x) && isfinite(rho[p].y) && (rho[p].x != 0.0 || rho[p].y != 0.0);
+            if (!ok) a.dead[c] = 1;
+            acc = ok ? 1 : 0;
+        } else {
+            acc = (sn > 0.0 && so > 0.0 && u_acc < sn / so) ? 1 : 0;
+            atomicAdd(&a.counters[0], 1ULL);
+        }
         s_accept = acc;
         a.accept[c] = acc;
-        atomicAdd(&a.counters[0], 1ULL);
         if (acc) {
             if (a.kmax > 1) a.pend[c] += 1;
-            atomicAdd(&a.counters[1], 1ULL);
-            a.since_refresh[c] += 1;
-            a.sweep_acc[c] += 1;
+            if (!a.forced) {
+                atomicAdd(&a.counters[1], 1ULL);
+                a.since_refresh[c] += 1;
+                a.sweep_acc[c] += 1;
+            }
             if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)g_new;
             else ((double*)a.links)[(size_t)c * g.n_links + l] = th_new;
         }
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
             Aug[e] = v;
         }
         __syncwarp();
-        warp_solve(Aug, r, fcol + warp * r);
+        if (!warp_solve(Aug, r, fcol + warp * r) && a.forced && lane == 0) a.dead[c] = 1;
         for (int e = lane; e < r * r; e += 32) {
             int i = e / r, j = e % r;
             a.zbuf[((size_t)c * P + p) * r * r + e] = Aug[i * w2 + r + j];
@@ -373,8 +391,9 @@ __global__ void __launch_bounds__(256) update_kernel(int N, int P, int fam_pairs
 // panel entries U[:, slot] = C Z and V[slot, :] = Y (stored as V^T rows).
 // Grid (ceil(N / 128), family pairs, chains), 128 threads, one index each.
 template <class T, int R>
-__global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_pairs, int pair_off, int link,
-                                                     const T* W, typename Sc<T>::R* Pan, const cxd* zbuf,
+__global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_pairs, int pair_off, int link_all,
+                                                     const int* link_of_chain, const T* W,
+                                                     typename Sc<T>::R* Pan, const cxd* zbuf,
                                                      const int* accept, const int* pend, int kmax) {
     typedef typename Sc<T>::R RR;
     const int c = blockIdx.z;
@@ -388,6 +407,7 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
     T* VS = UtS + kmax * R * R;    // [kr][R]  V[q, S_a]
     T* Zs = VS + kmax * R * R;     // [R][R]
     __shared__ int S[R];
+    const int link = link_of_chain ? link_of_chain[c] : link_all;
     const int s = link >> 1, d = link & 1, x = s % g.L, y = s / g.L;
     const int t = d == 0 ? y * g.L + (x + 1) % g.L : ((y + 1) % g.L) * g.L + x;
     const int a0 = s * g.B + (2 * d + 1) * g.h2, b0 = t * g.B + (2 * d) * g.h2;
@@ -557,7 +577,18 @@ size_t ggf_ratio_smem(int P, int r) {
     return (size_t)(2 * P * r * r + NWARP * 4 * r * r + P + NWARP * r) * sizeof(cxd);
 }
 
+ggf_status ggf_link_step_ex(ggf_ctx* ctx, int link, cudaStream_t st, const int* link_of_chain, const double* forced,
+                            int forced_k, int* dead);
+
 ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
+    return ggf_link_step_ex(ctx, link, st, nullptr, nullptr, 0, nullptr);
+}
+
+// One proposal per chain.  Block moves pass a per-chain link, the proposed
+// angles (forced, slot forced_k) and dead flags; the flush cadence then stays
+// with the caller.
+ggf_status ggf_link_step_ex(ggf_ctx* ctx, int link, cudaStream_t st, const int* link_of_chain, const double* forced,
+                            int forced_k, int* dead) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
     SweepArgs a;
@@ -581,6 +612,10 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
     a.sweep_acc = ch.sweep_acc;
     a.counters = ch.counters;
     a.Pr = ch.Pr; a.Pc = ch.Pc;
+    a.link_of_chain = link_of_chain;
+    a.forced = forced;
+    a.forced_k = forced_k;
+    a.dead = dead;
     a.pend = ch.pend;
     a.kmax = ch.kmax;
     size_t smem = ggf_ratio_smem(ctx->P, g.r);
@@ -596,7 +631,8 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
         dim3 gg((N + 127) / 128, ctx->K, ch.n), gc2((N + 127) / 128, ctx->Kc, ch.n);
 #define GGF_GATH(T, R_, grid, fam, off, Wp, Pp)                                                               \
     gather_kernel<T, R_><<<grid, 128, (2 * ch.kmax * R_ * R_ + R_ * R_) * sizeof(T), st>>>(                 \
-        g, ctx->P, fam, off, link, (const T*)(Wp), (typename Sc<T>::R*)(Pp), a.zbuf, ch.accept, ch.pend, ch.kmax)
+        g, ctx->P, fam, off, link, link_of_chain, (const T*)(Wp), (typename Sc<T>::R*)(Pp), a.zbuf, ch.accept, \
+        ch.pend, ch.kmax)
         if (g.r == 4) {
             if (fp64) {
                 GGF_GATH(double, 4, gg, ctx->K, 0, ch.Wr, ch.Pr);
@@ -617,6 +653,7 @@ ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st) {
 #undef GGF_GATH
         GGF_CK(cudaGetLastError());
         ctx->prof_pair(GGF_KT_UPDATE, ev1, ctx->prof_mark(st));
+        if (forced) { ++ch.steps_since_flush; return GGF_OK; }
         if (++ch.steps_since_flush >= ch.kmax) GGF_TRY(ggf_flush(ctx, st));
         return GGF_OK;
     }

@@ -41,6 +41,7 @@ class ChainOpts(ctypes.Structure):
 class ChainStats(ctypes.Structure):
     _fields_ = [("proposals", ctypes.c_uint64), ("accepts", ctypes.c_uint64), ("refreshes", ctypes.c_uint64),
                 ("sweeps", ctypes.c_uint64), ("max_drift", ctypes.c_double), ("launches", ctypes.c_uint64),
+                ("block_proposals", ctypes.c_uint64), ("block_accepts", ctypes.c_uint64),
                 ("n_chains", ctypes.c_int), ("n_pairs", ctypes.c_int)]
 
 
@@ -48,7 +49,8 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
-           "ggf_selftest_flush"]
+           "ggf_selftest_flush", "ggf_net_create", "ggf_net_destroy", "ggf_net_last_error", "ggf_net_get_params",
+           "ggf_net_set_params", "ggf_net_logq", "ggf_net_loss_grad", "ggf_net_train", "ggf_sample_blocks"]
 
 
 def lib_path() -> str:
@@ -88,6 +90,15 @@ def load():
         "ggf_sync": ([P, P], I),
         "ggf_logweight_noalloc": ([P, I, P, P, P], I),
         "ggf_selftest_flush": ([P, I, I, I, ctypes.POINTER(ctypes.c_double)], I),
+        "ggf_net_create": ([ctypes.POINTER(P), I, I, ctypes.c_uint64], I),
+        "ggf_net_destroy": ([P], V),
+        "ggf_net_last_error": ([P], ctypes.c_char_p),
+        "ggf_net_get_params": ([P, P], I),
+        "ggf_net_set_params": ([P, P], I),
+        "ggf_net_logq": ([P, I, P, P, P, I, P], I),
+        "ggf_net_loss_grad": ([P, I, P, P, ctypes.POINTER(ctypes.c_double), P], I),
+        "ggf_net_train": ([P, I, P, I, I, ctypes.c_float, P, P], I),
+        "ggf_sample_blocks": ([P, P, I, P, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -231,6 +242,13 @@ class GGF:
     def sample_no_obs(self, n_sweeps, stream=None):
         self._ck(self.lib.ggf_sample(self.h, int(n_sweeps), None, MEM_DEVICE, stream))
 
+    def sample_blocks(self, net, n_moves, obs=None):
+        """Learned-proposal block moves; returns obs [n_moves, n_chains, 3]."""
+        if obs is None:
+            obs = np.zeros((int(n_moves), self.n_chains, N_OBS))
+        self._ck(self.lib.ggf_sample_blocks(self.h, net.h, int(n_moves), _ptr(obs)[0], self._mem(obs), _stream([obs])))
+        return obs
+
     def chains_links(self, out=None):
         if out is None:
             L = self.n_links()
@@ -284,6 +302,70 @@ class GGF:
 
     def _links_from_state(self):
         raise RuntimeError("call init_problem/init_lattice through this object first")
+
+
+NET_PARAMS = 81990
+
+
+class Net:
+    """The learned block-proposal network (ggf_net)."""
+
+    def __init__(self, device: int, L: int, seed: int = 1):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.ggf_net_create(ctypes.byref(h), int(device), int(L), int(seed))
+        if st != 0:
+            raise GGFError(st, "ggf_net_create failed")
+        self.h, self.L = h, int(L)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ggf_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        if st != 0:
+            raise GGFError(st, self.lib.ggf_net_last_error(self.h).decode())
+
+    def get_params(self):
+        out = np.zeros(NET_PARAMS, dtype=np.float32)
+        self._ck(self.lib.ggf_net_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._ck(self.lib.ggf_net_set_params(self.h, p.ctypes.data))
+
+    def logq(self, theta, blocks):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        bl = np.ascontiguousarray(blocks, dtype=np.int32)
+        out = np.zeros(len(th))
+        self._ck(self.lib.ggf_net_logq(self.h, len(th), th.ctypes.data, bl.ctypes.data, out.ctypes.data, MEM_HOST,
+                                       None))
+        return out
+
+    def loss_grad(self, theta, blocks):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        bl = np.ascontiguousarray(blocks, dtype=np.int32)
+        loss = ctypes.c_double()
+        g = np.zeros(NET_PARAMS, dtype=np.float32)
+        self._ck(self.lib.ggf_net_loss_grad(self.h, len(th), th.ctypes.data, bl.ctypes.data, ctypes.byref(loss),
+                                            g.ctypes.data))
+        return loss.value, g
+
+    def train(self, theta_dev, batch, n_steps, lr):
+        """Adam steps on a device tensor of configurations [n_cfg, 2L^2]."""
+        losses = np.zeros(int(n_steps), dtype=np.float32)
+        st = _stream([theta_dev])
+        self._ck(self.lib.ggf_net_train(self.h, int(theta_dev.shape[0]), _ptr(theta_dev)[0], int(batch), int(n_steps),
+                                        float(lr), losses.ctypes.data, st))
+        return losses
 
 
 def sample_group(ctxs, n_sweeps):

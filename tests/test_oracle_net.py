@@ -71,3 +71,27 @@ def test_wrapped_cauchy_density_and_sampler(mu, rho):
     cdf = lambda x: np.interp(x, t, np.concatenate([[0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(t))]))
     want = (cdf(edges[1:]) - cdf(edges[:-1])) * len(s)
     assert np.abs(hist - want).max() <= 3 + 0.002 * len(s) / 40 + 0.01 * want.max()
+
+
+def test_bf16_rounding():
+    assert net.bf16(1.0) == 1.0
+    assert net.bf16(1.0 + 2.0**-8) == 1.0                 # tie -> even (mantissa bit 0)
+    assert net.bf16(1.0 + 3 * 2.0**-8) == 1.0 + 2.0**-6   # tie -> even (rounds up)
+    assert net.bf16(1.0 + 2.0**-7) == 1.0 + 2.0**-7       # representable
+    assert net.bf16(-2.5) == -2.5
+    x = np.random.default_rng(0).normal(size=1000)
+    assert np.all(np.abs(net.bf16(x) - x) <= 2.0**-8 * np.abs(x) * 1.0001)   # half an ulp of 7 bits
+
+
+def test_quantised_network_is_the_plain_one_at_exact_values():
+    """quant = identity gives the plain network; with BF16 rounding the loss moves by
+    a rounding-sized amount only."""
+    L = 4
+    rng = np.random.default_rng(7)
+    params = small_params(2, 0.1)
+    th = rng.uniform(0, 2 * np.pi, (2, 2 * L * L))
+    a = net.loss_and_grad(params, th, [(0, 0), (1, 3)], L)
+    b = net.loss_and_grad(params, th, [(0, 0), (1, 3)], L, quant=lambda v: v)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    c = net.loss_and_grad(params, th, [(0, 0), (1, 3)], L, quant=net.bf16)
+    assert abs(c[0] - a[0]) < 1e-2 * abs(a[0])
