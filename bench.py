@@ -38,7 +38,11 @@ WORKLOADS = {
              "8x8 periodic Z2, K=1 (M 512x512), 1024 chains, FP32 rank-r updates, FP64 refresh every 64 accepts"),
     "cfg2_fp64": (8, 0, 1, 1, 1024, 0, 1024, 1,
                   "8x8 periodic Z2, K=1 (M 512x512), 1024 chains, plain FP64 local updates"),
+    "cfg4": (16, 1, 2, 4, 192, 1, 1 << 30, 32,
+             "16x16 periodic U(1), n_v=2, K=4 with the learned 4x4-block proposal (BF16 conv net trained on "
+             "plain-sampler configurations); step = 1 local sweep + 16 block moves; 192 resident chains"),
 }
+BLOCK_MOVES_PER_STEP = 16
 BASE_SEED = 20241202
 
 
@@ -121,7 +125,7 @@ def unit_bytes(p, prec):
 # Largest lattice on which the oracle times a proposal directly; bigger
 # workloads are timed on this lattice with the same group, n_v and K and the
 # per-proposal time scaled by the cube of the Pfaffian size.
-CPU_PROXY_L = {"cfg3": 6}
+CPU_PROXY_L = {"cfg3": 6, "cfg4": 6}
 
 
 def cpu_sample(name, budget_s=15.0, workers=None):
@@ -225,10 +229,36 @@ def run_ggf(args):
     obs_all = []
     dev_obs = torch.zeros((1, chains, 3), dtype=torch.float64, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
+    net, train_info = None, None
+    if args.workload == "cfg4":
+        # training data from the plain local sampler, then MLE training of the proposal
+        from paper_2412_01737_gb300 import Net
+        t_tr = time.time()
+        ctx.sample(args.burn_train)
+        data = []
+        for _ in range(args.train_sweeps):
+            ctx.sample(1)
+            data.append(ctx.chains_links())
+        data = torch.from_numpy(np.concatenate(data)).cuda()
+        t_gen = time.time() - t_tr
+        net = Net(local, p.L, seed)
+        t0n = time.time()
+        losses = net.train(data, 128, args.train_steps, 2e-3)
+        torch.cuda.synchronize()
+        train_info = {"configs": int(data.shape[0]), "data_s": t_gen, "train_s": time.time() - t0n,
+                      "train_steps": args.train_steps, "loss_first": float(losses[:10].mean()),
+                      "loss_last": float(losses[-10:].mean())}
+        blk_obs = torch.zeros((BLOCK_MOVES_PER_STEP, chains, 3), dtype=torch.float64, device=f"cuda:{local}")
+
+    def one_step():
+        ctx.sample(1, obs=dev_obs)
+        if net is not None:
+            ctx.sample_blocks(net, BLOCK_MOVES_PER_STEP, obs=blk_obs)
+            return blk_obs[-1]
+        return dev_obs[0]
 
     def sweep():
-        ctx.sample(1, obs=dev_obs)
-        obs_all.append(dev_obs[0].cpu().numpy().copy())
+        obs_all.append(one_step().cpu().numpy().copy())
 
     for _ in range(args.burn):
         sweep()
@@ -245,8 +275,7 @@ def run_ggf(args):
     torch.cuda.cudart().cudaProfilerStart()     # ncu --profile-from-start off sees the timed sweeps only
     e0.record(stream)
     for _ in range(args.steps):
-        ctx.sample(1, obs=dev_obs)
-        obs_all.append(dev_obs[0].clone())
+        obs_all.append(one_step().clone())
     e1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
@@ -326,6 +355,12 @@ def run_ggf(args):
             "dlogp_vs_fp64_recompute": dlogp,
             "roofline": roof, "clocks": ck,
             "gpu_launches": int(st1.launches - st0.launches)}
+    if train_info is not None:
+        nb = st1.block_proposals - st0.block_proposals
+        train_info["block_acceptance"] = (st1.block_accepts - st0.block_accepts) / max(1, nb)
+        line["config"]["learned_proposal"] = train_info
+        net.close()
+        args.no_e2e = True     # the end-to-end leg covers the plain sampler only
     ctx.close()                                   # frees the chains before the e2e run
     if rank == 0 and not args.no_cpu:
         rate, secs, workers, desc = cpu_sample(args.workload, budget_s=args.cpu_seconds)
@@ -374,6 +409,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--burn-train", type=int, default=4, help="cfg4: local sweeps before collecting training data")
+    ap.add_argument("--train-sweeps", type=int, default=6, help="cfg4: local sweeps whose configurations train the net")
+    ap.add_argument("--train-steps", type=int, default=300, help="cfg4: Adam steps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -206,7 +206,8 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
  * ggf_sample, and resets the totals; ggf_profile(ctx, 0) stops.
  * ggf_kernel_time returns the accumulated device milliseconds and the number
  * of timed launch groups since the last reset.  Events are read at the end of
- * each sweep. */
+ * each sweep.  While timing is on, sweeps launch eagerly instead of replaying
+ * their graph (the kernel sequence is the same). */
 #define GGF_KT_RATIO 0
 #define GGF_KT_UPDATE 1
 #define GGF_KT_REFRESH 2

@@ -527,28 +527,23 @@ void drop_graph(Chains& ch) {
     if (ch.graph) cudaGraphDestroy(ch.graph);
     ch.gexec = nullptr;
     ch.graph = nullptr;
-    ch.gev_cat.clear();
 }
 
 ggf_status ensure_graph(ggf_ctx* ctx) {
     Chains& ch = ctx->ch;
-    if (ch.gexec && ch.graph_prof == ctx->prof) return GGF_OK;
+    if (ch.gexec) return GGF_OK;
     drop_graph(ch);
-    if (ctx->prof) {   // events must exist before capture
-        const int need = 3 * ctx->g.n_links + 2 * (ctx->g.n_links / std::max(1, ch.kmax) + 2) + 8;
-        while ((int)ctx->ev.size() < need) {
-            cudaEvent_t e;
-            GGF_CK(cudaEventCreate(&e));
-            ctx->ev.push_back(e);
-        }
-    }
+    const bool prof = ctx->prof;
+    ctx->prof = false;   // captured graphs hold no timing events
     ctx->ev_used = 0;
     ctx->ev_cat.clear();
     const unsigned long long l0 = ctx->launches;
-    GGF_CK(cudaStreamBeginCapture(ch.cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t eb = cudaStreamBeginCapture(ch.cs, cudaStreamCaptureModeThreadLocal);
+    if (eb != cudaSuccess) { ctx->prof = prof; return ggf_cuda(ctx, eb, "cudaStreamBeginCapture"); }
     ggf_status s = sweep_body(ctx, ch.cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(ch.cs, &g);
+    ctx->prof = prof;
     if (s != GGF_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
@@ -558,17 +553,15 @@ ggf_status ensure_graph(ggf_ctx* ctx) {
     GGF_CK(cudaGraphInstantiate(&ch.gexec, g, 0));
     ch.graph_launches = ctx->launches - l0;
     ctx->launches = l0;
-    ch.gev_cat = ctx->ev_cat;
     ctx->ev_cat.clear();
     ctx->ev_used = 0;
-    ch.graph_prof = ctx->prof;
     return GGF_OK;
 }
 
-ggf_status accumulate_events(ggf_ctx* ctx, const std::vector<int>& cat) {
+ggf_status accumulate_events(ggf_ctx* ctx, const std::vector<int>& cat, const std::vector<cudaEvent_t>& pool) {
     for (size_t k = 0; k + 2 < cat.size(); k += 3) {
         float ms = 0;
-        GGF_CK(cudaEventElapsedTime(&ms, ctx->ev[cat[k + 1]], ctx->ev[cat[k + 2]]));
+        GGF_CK(cudaEventElapsedTime(&ms, pool[cat[k + 1]], pool[cat[k + 2]]));
         ctx->kt_ms[cat[k]] += ms;
         ctx->kt_n[cat[k]] += 1;
     }
@@ -576,7 +569,7 @@ ggf_status accumulate_events(ggf_ctx* ctx, const std::vector<int>& cat) {
 }
 
 // After a sweep's kernels: observables out, refresh of the marked chains.
-ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem) {
+ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem, bool graph_launched) {
     Chains& ch = ctx->ch;
     cudaStream_t cs = ch.cs;
     if (obs_dst)
@@ -586,7 +579,7 @@ ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem) {
     GGF_CK(cudaMemcpyAsync(&cnt, ch.refresh_list, sizeof(int), cudaMemcpyDeviceToHost, cs));
     GGF_CK(cudaStreamSynchronize(cs));
     if (ctx->prof) {
-        GGF_TRY(accumulate_events(ctx, ch.opts.graph ? ch.gev_cat : ctx->ev_cat));
+        if (!graph_launched) GGF_TRY(accumulate_events(ctx, ctx->ev_cat, ctx->ev));
         ctx->ev_cat.clear();
         ctx->ev_used = 0;
     }
@@ -600,7 +593,7 @@ ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem) {
         ctx->prof_pair(GGF_KT_REFRESH, r0, ctx->prof_mark(cs));
         GGF_CK(cudaStreamSynchronize(cs));
         if (ctx->prof) {
-            GGF_TRY(accumulate_events(ctx, ctx->ev_cat));
+            GGF_TRY(accumulate_events(ctx, ctx->ev_cat, ctx->ev));
             ctx->ev_cat.clear();
             ctx->ev_used = 0;
         }
@@ -633,8 +626,11 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
     // the library stream waits for the caller's stream, and the caller's stream for it at the end
     GGF_CK(cudaEventRecord(ch.join, st));
     GGF_CK(cudaStreamWaitEvent(ch.cs, ch.join, 0));
+    // with per-kernel timing on, sweeps launch eagerly (same kernel sequence as
+    // the graph) so that every launch is bracketed by events
+    const bool use_graph = ch.opts.graph && !ctx->prof;
     for (int s = 0; s < n_sweeps; ++s) {
-        if (ch.opts.graph) {
+        if (use_graph) {
             GGF_TRY(ensure_graph(ctx));
             GGF_CK(cudaGraphLaunch(ch.gexec, ch.cs));
             ctx->launches += ch.graph_launches;
@@ -643,7 +639,7 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
             ctx->ev_cat.clear();
             GGF_TRY(sweep_body(ctx, ch.cs));
         }
-        GGF_TRY(finish_sweep(ctx, obs ? obs + (size_t)s * ch.n * GGF_N_OBS : nullptr, mem));
+        GGF_TRY(finish_sweep(ctx, obs ? obs + (size_t)s * ch.n * GGF_N_OBS : nullptr, mem, use_graph));
     }
     GGF_CK(cudaEventRecord(ch.join, ch.cs));
     GGF_CK(cudaStreamWaitEvent(st, ch.join, 0));
@@ -663,14 +659,7 @@ ggf_status ggf_sample_group(ggf_ctx* const* ctxs, int n_ctx, int n_sweeps, doubl
     }
     ggf_ctx* ctx = ctxs[0];
     cudaSetDevice(ctx->device);
-    for (int k = 0; k < n_ctx; ++k) {
-        // children hold no event-record nodes: capture without profiling events
-        const bool prof = ctxs[k]->prof;
-        ctxs[k]->prof = false;
-        ggf_status s = ensure_graph(ctxs[k]);
-        ctxs[k]->prof = prof;
-        GGF_TRY(s);
-    }
+    for (int k = 0; k < n_ctx; ++k) GGF_TRY(ensure_graph(ctxs[k]));
     // one parent graph whose independent children are the contexts' sweeps
     cudaGraph_t pg = nullptr;
     cudaGraphExec_t pexec = nullptr;
@@ -700,10 +689,7 @@ ggf_status ggf_sample_group(ggf_ctx* const* ctxs, int n_ctx, int n_sweeps, doubl
                 c->launches += c->ch.graph_launches;
                 if (k > 0) cudaStreamWaitEvent(c->ch.cs, ctx->ch.join, 0);
                 double* dst = (obs && obs[k]) ? obs[k] + (size_t)s * c->ch.n * GGF_N_OBS : nullptr;
-                bool prof = c->prof;
-                c->prof = false;       // per-kernel timing is not collected in group mode
-                rc = finish_sweep(c, dst, mem);
-                c->prof = prof;
+                rc = finish_sweep(c, dst, mem, true);   // no per-kernel timing in group mode
             }
         }
         if (rc == GGF_OK) {

@@ -58,8 +58,6 @@ struct Chains {
     cudaEvent_t join = nullptr;              // stream-join event
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    bool graph_prof = false;                 // graph holds event-record nodes
-    std::vector<int> gev_cat;                // (category, start, end) event triples of the graph
     unsigned long long graph_launches = 0;   // kernels per replay
 };
 

@@ -153,6 +153,17 @@ extern "C" ggf_status ggf_sample_blocks(ggf_ctx* ctx, ggf_net* net, int n_moves,
         ch.block_moves += 1;
     }
     if (rc == GGF_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) fail_cuda(e, "sample_blocks sync");
+    if (rc == GGF_OK && ctx->prof) {   // timing of the tentative link steps and flushes
+        for (size_t k = 0; k + 2 < ctx->ev_cat.size(); k += 3) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, ctx->ev[ctx->ev_cat[k + 1]], ctx->ev[ctx->ev_cat[k + 2]]) == cudaSuccess) {
+                ctx->kt_ms[ctx->ev_cat[k]] += ms;
+                ctx->kt_n[ctx->ev_cat[k]] += 1;
+            }
+        }
+    }
+    ctx->ev_cat.clear();
+    ctx->ev_used = 0;
     void* ps[] = {blocks, link_k, dead, lq, prop, old_links, ell_save, dobs};
     for (void* q : ps) if (q) cudaFree(q);
     return rc;
