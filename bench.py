@@ -43,6 +43,86 @@ WORKLOADS = {
              "plain-sampler configurations); step = 1 local sweep + 16 block moves; 192 resident chains"),
 }
 BLOCK_MOVES_PER_STEP = 16
+
+# Uneven batch: every (lattice, group, K) cell below is one problem; all cells
+# sweep together, one parent CUDA graph launch per sweep.  Chains are spread
+# so that every cell holds about the same inverse memory (at least one chain).
+CFG5_CELLS = [(L, grp, K) for L in (8, 12, 16) for grp in (0, 1) for K in (1, 2, 4)]
+CFG5_CHAINS = 4096
+CFG5_BUDGET = 120 * 2**30
+
+
+def cfg5_cells():
+    import ggf_inputs as gi
+    cells = []
+    for (L, grp, K) in CFG5_CELLS:
+        nv = 1 if grp == 0 else 2
+        p = gi.make_problem(L, grp, nv, K, seed=BASE_SEED + 31 * len(cells))
+        mem = 4 * p.N * p.N * K * K                  # FP32 inverses of all K^2 pair entries
+        cells.append([p, mem])
+    inv = [1.0 / m for _, m in cells]
+    scale = CFG5_CHAINS / sum(inv)
+    out = []
+    for (p, mem), w in zip(cells, inv):
+        ch = max(1, int(round(w * scale)))
+        ch = max(1, min(ch, int(CFG5_BUDGET / len(cells) // mem)))
+        out.append((p, ch, mem))
+    return out
+
+
+def run_cfg5(args):
+    """Uneven batch of problems in one graph launch per sweep."""
+    import torch
+    import ggf_inputs as gi
+    from paper_2412_01737_gb300 import GGF
+    from paper_2412_01737_gb300.ggf import sample_group
+    from paper_2412_01737_gb300.tune import tune_delay
+    cells = cfg5_cells()
+    ctxs, tuned, t0 = [], [], time.time()
+    for k, (p, ch, mem) in enumerate(cells):
+        links = gi.cold_links(p, ch)
+        d, tim = tune_delay(p, links, 1, candidates=(4, 8, 16), use_cache=False, seed=BASE_SEED + k)
+        tuned.append({"L": p.L, "group": "Z2" if p.group == 0 else "U1", "K": p.K, "chains": ch, "delay": d,
+                      "ms_per_sweep": {str(a): round(b, 2) for a, b in tim.items()}})
+        c = GGF(0)
+        c.init_problem(p)
+        c.chains_init(links, precision=1, refresh_every=1 << 30, seed=BASE_SEED + k, delay=d, graph=1)
+        ctxs.append(c)
+    t_setup = time.time() - t0
+    obs = [[] for _ in ctxs]
+    for o, s in zip(sample_group(ctxs, args.warmup), obs):
+        s.append(o)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs = sample_group(ctxs, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ess, total_chains, launches = 0.0, 0, 0
+    for k, (c, o) in enumerate(zip(ctxs, outs)):
+        ser = np.concatenate([obs[k][0], o], axis=0).transpose(1, 0, 2)      # chains, sweeps, 3
+        keep = ser[:, max(1, ser.shape[1] // 4):, :]
+        tau = max(tau_int(keep[:, :, 0] - keep[:, :, 0].mean(axis=0, keepdims=True)),
+                  tau_int(keep[:, :, 1] - keep[:, :, 1].mean(axis=0, keepdims=True)), 0.5)
+        tuned[k]["tau_int"] = round(tau, 3)
+        ess += c.n_chains * args.steps / (2 * tau)
+        total_chains += c.n_chains
+        launches += c.chains_stats().launches
+        c.close()
+    line = {"metric": "effective samples/sec/GPU", "value": ess / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"uneven batch: {len(cells)} problems (L in 8,12,16; Z2 and U(1); K in 1,2,4), "
+                                   f"{total_chains} chains, one parent CUDA graph launch per sweep, autotuned delay",
+                       "cells": tuned, "setup_s": t_setup},
+            "roofline": None, "roofline_note": "per-kernel timing is not collected inside grouped graph launches",
+            "clocks": ck, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
 BASE_SEED = 20241202
 
 
@@ -326,11 +406,22 @@ def run_ggf(args):
             roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V)", "bound": "alu",
                     "achieved": fl / t_fl / 1e12, "peak": 1.25, "unit": "TFLOP/s",
                     "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe)"}
-    elif dom == "update":
+    elif dom == "update" and delay <= 1:
         upd_bytes = accepts * unit_bytes(p, prec)
-        roof = {"kernel": "update_kernel (rank-r SMW)" if delay <= 1 else "gather_kernel", "bound": "hbm",
+        roof = {"kernel": "update_kernel (rank-r SMW)", "bound": "hbm",
                 "achieved": upd_bytes / (kt["update"][0] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    elif dom == "update":
+        # gather: per tentative or accepted update and pair, panel rows U, V^T (2 N kr b) plus
+        # the rows/columns of W at S and the two new panel columns (4 N r b); kr taken at its
+        # mean over a flush interval.  The panels are mostly L2-resident: no HBM peak applies.
+        b = 8 if prec == 0 else 4
+        kr_mean = 0.5 * (delay - 1) * p.r
+        per = sum((2 if n == m else 4) * b * p.N * (kr_mean + 2 * p.r) for n in range(p.K) for m in range(n, p.K))
+        n_upd = accepts + 32 * ((st1.block_proposals - st0.block_proposals) if hasattr(st1, "block_proposals") else 0)
+        roof = {"kernel": "gather_kernel (delayed rows/columns)", "bound": "l2",
+                "achieved": n_upd * per / (kt["update"][0] * 1e-3) / 1e9, "peak": None, "unit": "GB/s",
+                "peak_source": "no measured L2 peak; reported for the record"}
     else:
         roof = {"kernel": "ratio_kernel", "bound": "alu", "achieved": None, "peak": None, "unit": None}
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") else None
@@ -404,7 +495,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--burn", type=int, default=0, help="extra untimed sweeps before warm-up")
     ap.add_argument("--impl", default="ggf", choices=["ggf", "reference"])
-    ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS) + ["cfg5"])
     ap.add_argument("--chains", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -417,6 +508,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cfg5":
+        run_cfg5(args)
     else:
         run_ggf(args)
 

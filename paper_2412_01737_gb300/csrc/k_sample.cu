@@ -403,9 +403,12 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
     const int KRM = kmax * R;
     const size_t NK = (size_t)N * KRM;
     extern __shared__ unsigned char smraw[];
+    constexpr int QC = 128 / sizeof(T);  // rank chunk staged per step
     T* UtS = (T*)smraw;            // [kr][R]  U[S_a, q]
     T* VS = UtS + kmax * R * R;    // [kr][R]  V[q, S_a]
     T* Zs = VS + kmax * R * R;     // [R][R]
+    T* Uc = Zs + R * R;            // [128][QC + 1] panel rows j0.., rank chunk
+    T* Vc = Uc + 128 * (QC + 1);
     __shared__ int S[R];
     const int link = link_of_chain ? link_of_chain[c] : link_all;
     const int s = link >> 1, d = link & 1, x = s % g.L, y = s / g.L;
@@ -425,23 +428,39 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
     }
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) Zs[e] = Sc<T>::from(Z[e]);
     __syncthreads();
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
+    const int j0 = blockIdx.x * blockDim.x;
+    const int j = j0 + threadIdx.x;
+    const bool live = j < N;
     T yv[R], cv[R];
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-        yv[a] = Wp[(size_t)S[a] * N + j];
-        cv[a] = Wp[(size_t)j * N + S[a]];
+        yv[a] = live ? Wp[(size_t)S[a] * N + j] : Sc<T>::zero();
+        cv[a] = live ? Wp[(size_t)j * N + S[a]] : Sc<T>::zero();
     }
-    for (int q = 0; q < kr; ++q) {
-        T vq = PanelIO<T>::ld(Vt, NK, (size_t)j * KRM + q);
-        T uq = PanelIO<T>::ld(U, NK, (size_t)j * KRM + q);
+    // panel rows j0 .. j0+127 staged chunk by chunk with coalesced loads
+    for (int q0 = 0; q0 < kr; q0 += QC) {
+        const int qn = min(QC, kr - q0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 128 * QC; e += blockDim.x) {
+            int row = e / QC, qq = e % QC;
+            bool ok = qq < qn && j0 + row < N;
+            size_t idx = (size_t)(j0 + row) * KRM + q0 + qq;
+            Uc[row * (QC + 1) + qq] = ok ? PanelIO<T>::ld(U, NK, idx) : Sc<T>::zero();
+            Vc[row * (QC + 1) + qq] = ok ? PanelIO<T>::ld(Vt, NK, idx) : Sc<T>::zero();
+        }
+        __syncthreads();
+        for (int qq = 0; qq < qn; ++qq) {
+            const T vq = Vc[threadIdx.x * (QC + 1) + qq];
+            const T uq = Uc[threadIdx.x * (QC + 1) + qq];
+            const int q = q0 + qq;
 #pragma unroll
-        for (int a = 0; a < R; ++a) {
-            yv[a] -= UtS[q * R + a] * vq;
-            cv[a] -= uq * VS[q * R + a];
+            for (int a = 0; a < R; ++a) {
+                yv[a] -= UtS[q * R + a] * vq;
+                cv[a] -= uq * VS[q * R + a];
+            }
         }
     }
+    if (!live) return;
 #pragma unroll
     for (int b = 0; b < R; ++b) {
         T u = Sc<T>::zero();
@@ -630,7 +649,7 @@ ggf_status ggf_link_step_ex(ggf_ctx* ctx, int link, cudaStream_t st, const int* 
     if (ch.kmax > 1) {
         dim3 gg((N + 127) / 128, ctx->K, ch.n), gc2((N + 127) / 128, ctx->Kc, ch.n);
 #define GGF_GATH(T, R_, grid, fam, off, Wp, Pp)                                                               \
-    gather_kernel<T, R_><<<grid, 128, (2 * ch.kmax * R_ * R_ + R_ * R_) * sizeof(T), st>>>(                 \
+    gather_kernel<T, R_><<<grid, 128, (2 * ch.kmax * R_ * R_ + R_ * R_ + 2 * 128 * (128 / sizeof(T) + 1)) * sizeof(T), st>>>( \
         g, ctx->P, fam, off, link, link_of_chain, (const T*)(Wp), (typename Sc<T>::R*)(Pp), a.zbuf, ch.accept, \
         ch.pend, ch.kmax)
         if (g.r == 4) {
