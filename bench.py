@@ -299,6 +299,8 @@ def run_ggf(args):
     p, chains, prec, refresh, delay, label = problem_for(args.workload)
     if args.chains:
         chains = args.chains
+    if args.delay:
+        delay = args.delay
     seed = BASE_SEED + 7919 * rank
     ctx = GGF(local)
     ctx.init_problem(p)
@@ -436,7 +438,7 @@ def run_ggf(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
-            "config": {"workload": label, "chains": chains, "sweeps_timed": args.steps,
+            "config": {"workload": label, "chains": chains, "delay": delay, "sweeps_timed": args.steps,
                        "burn_in_sweeps": args.burn + args.warmup, "tau_int": {"plaquette": tau_pl, "logN": tau_ln},
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (W is "
                        f"{chains * unit_bytes(p, prec) / 2 / 2**30:.1f} GiB)",
@@ -497,6 +499,7 @@ def main():
     ap.add_argument("--impl", default="ggf", choices=["ggf", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS) + ["cfg5"])
     ap.add_argument("--chains", type=int, default=0)
+    ap.add_argument("--delay", type=int, default=0, help="override the workload's batch size (links per flush)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -14,6 +14,9 @@ ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_prepare_sampler(ggf_ctx* ctx);
 ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx);
+ggf_status ggf_prepare_batch(ggf_ctx* ctx);
+ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64);
+ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st);
 ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
@@ -46,7 +49,7 @@ void ggf_free_chains(ggf_ctx* ctx) {
     if (c.d_sweep) cudaFree(c.d_sweep);
     if (c.d_obs_stage) cudaFree(c.d_obs_stage);
     void* ptrs[] = {c.links, c.Wr, c.Wc, c.ell, c.zbuf, c.ybuf, c.accept, c.since_refresh,
-                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend};
+                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend, c.Sm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ggf_chain_opts o = c.opts;
@@ -447,6 +450,9 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
         GGF_CK(cudaMalloc(&ch.Pr, std::max<size_t>(16, pr * 2 * ctx->K)));
         GGF_CK(cudaMalloc(&ch.Pc, std::max<size_t>(16, pr * 4 * ctx->Kc)));
         GGF_CK(cudaMalloc(&ch.ybuf, 16));
+        GGF_TRY(ggf_check_batch(ctx, ch.kmax, fp64));
+        const size_t KRM = (size_t)ch.kmax * g.r;
+        GGF_CK(cudaMalloc(&ch.Sm, (size_t)n_chains * 2 * KRM * KRM * rsz * (ctx->K + 2 * ctx->Kc) + 16));
     } else {
         GGF_CK(cudaMalloc(&ch.ybuf, (size_t)n_chains * (ctx->K + 2 * ctx->Kc) * 2 * g.r * g.N * rsz + 16));
     }
@@ -458,6 +464,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     GGF_CK(cudaStreamCreateWithFlags(&ch.cs, cudaStreamNonBlocking));
     GGF_CK(cudaEventCreateWithFlags(&ch.join, cudaEventDisableTiming));
     GGF_TRY(ggf_prepare_sampler(ctx));
+    GGF_TRY(ggf_prepare_batch(ctx));
     GGF_TRY(ggf_prepare_flush_tc(ctx));
     GGF_CK(cudaMalloc(&ch.accept, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.since_refresh, n_chains * sizeof(int)));
@@ -514,7 +521,12 @@ namespace {
 ggf_status sweep_body(ggf_ctx* ctx, cudaStream_t st) {
     Chains& ch = ctx->ch;
     GGF_CK(cudaMemsetAsync(ch.sweep_acc, 0, ch.n * sizeof(int), st));
-    for (int l = 0; l < ctx->g.n_links; ++l) GGF_TRY(ggf_link_step(ctx, l, st));
+    const int nl = ctx->g.n_links;
+    if (ch.kmax > 1) {
+        for (int l0 = 0; l0 < nl; l0 += ch.kmax) GGF_TRY(ggf_batch(ctx, l0, std::min(ch.kmax, nl - l0), st));
+    } else {
+        for (int l = 0; l < nl; ++l) GGF_TRY(ggf_link_step(ctx, l, st));
+    }
     GGF_TRY(ggf_flush(ctx, st));
     GGF_TRY(ggf_observe(ctx, ch.d_obs_stage, st));
     GGF_TRY(ggf_mark_refresh(ctx, st));

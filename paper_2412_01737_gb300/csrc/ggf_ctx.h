@@ -48,6 +48,10 @@ struct Chains {
     void* Pr = nullptr;   // real-family panels [n][K][2][N][kmax r]
     void* Pc = nullptr;   // complex-family panels [n][Kc][2][2][N][kmax r]
     int* pend = nullptr;          // [n]
+    // batched delayed updates: small matrices G = W_eff[T, T] and X per chain
+    // and pair, real family [n][K][2][kmax r][kmax r] then complex family
+    // [n][Kc][2][kmax r][kmax r] (W precision)
+    void* Sm = nullptr;
     int kmax = 1;
     int steps_since_flush = 0;
     unsigned long long block_moves = 0;      // learned-proposal moves made (Philox counter)

@@ -1,43 +1,62 @@
 // Delayed-update flush on the sm_103a tensor cores (tcgen05 + TMEM).
 //
-// For FP32 chains, folds the pending rank-(k r) panels into the cached
-// inverse: W <- W - U V, with U (N x KR) and V^T (N x KR) stored K-major
-// (rank index contiguous), complex pairs as separate real/imaginary planes.
-// FP32 accuracy from TF32 tensor cores by the three-product split
+// For FP32 chains, folds the pending rank-K panels into the cached inverse:
+// W <- W - U V, with U (N x K) and V^T (N x K) stored K-major (rank index
+// contiguous, row stride KRM), complex pairs as separate real/imaginary
+// planes.  FP32 accuracy from TF32 tensor cores by the three-product split
 // x = hi + lo, hi = rna_tf32(x):  a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
 //
 // The MMA computes the transposed tile D^T = V U^T (A operand: 128 rows of
-// V^T, B operand: rows of U), so the TMEM lane is the output column and the
-// TMEM column the output row: in the epilogue a warp's 32 lanes hold 32
-// consecutive columns of W for every row it reads, and its loads and stores
-// of W are coalesced without staging.  Persistent CTAs of 128 threads walk
-// tiles of 128 columns x 128 rows
-// (real) or 128 complex columns x 64 rows (complex: two 64-column
-// accumulators, re and im, in the 128 TMEM columns allocated once); four
-// CTAs share an SM (all 512 TMEM columns) so that one CTA's loads overlap
-// another's MMAs and stores.  Per 16-wide rank chunk the operands are loaded
-// (float4, all loads in flight), split into tf32 hi/lo and written in the
-// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
-// LBO = 128 B along K, SBO = 512 B between 8-row groups); one thread issues
-// the MMAs (M = 128, K = 8 each) and commits them to an mbarrier.  Every wait on the mbarrier is bounded; on
-// expiry the kernel raises the device error word and frees its TMEM.
+// V^T, i.e. 128 columns of W; B operand: rows of U), so the TMEM lane is the
+// output column and the TMEM column the output row: in the epilogue a warp's
+// 32 lanes hold 32 consecutive columns of W for every row, and its loads and
+// stores of W are coalesced without staging.  Every MMA is M = 128, N = 256,
+// K = 8: real tiles are 128 columns x 256 rows; complex tiles are 128 complex
+// columns x 128 rows, with the B operand the composite [-U_i ; U_r ; U_i]
+// (384 rows), so that
+//   D[:, 0:256] += V_r [U_r ; U_i]^T + V_i [-U_i ; U_r]^T
+// holds re(D^T) in TMEM columns 0..127 and im(D^T) in 128..255.
+//
+// One persistent CTA per SM, warp-specialised:
+//   warps 0-3   producers: load an 8-wide rank chunk of the operands (float4),
+//               split into tf32 hi/lo and write them in the no-swizzle
+//               K-major core-matrix layout (8 rows x 16 B core matrices,
+//               LBO = 128 B along K, SBO = 256 B between 8-row groups) into a
+//               ring of STAGES shared-memory stages;
+//   warp 12     one thread issues the MMAs of each stage and commits them to
+//               the stage's "empty" mbarrier, and after a tile's last stage
+//               to the "accumulator full" mbarrier of one of two TMEM
+//               accumulators (2 x 256 of the 512 columns);
+//   warps 4-11  epilogue: TMEM -> registers, W -= D, releasing the
+//               accumulator, so that one tile's epilogue overlaps the next
+//               tile's MMAs.
+// Every mbarrier wait is bounded; on expiry the kernel raises the device error
+// word, the other roles leave their loops, the MMA thread waits (bounded) for
+// its MMAs in flight and the TMEM is freed.
 #include <cstring>
 #include "ggf_ctx.h"
 
 namespace {
 
-constexpr int TC_THREADS = 128;
-constexpr int KCH = 16;                       // rank chunk (tf32 elements)
-constexpr int SBO = KCH / 4 * 128;            // bytes between 8-row core-matrix groups
-constexpr int TILE_BYTES_128 = 128 * KCH * 4; // 8 KB per 128-row operand plane
-constexpr int CTAS_PER_SM = 4;                // 4 x 128 TMEM columns = all 512
-constexpr int smem_bytes(bool cplx) { return (cplx ? 48 : 32) * 1024 + 1024; }
+constexpr int KC = 8;                         // rank columns per stage (one MMA K step)
+constexpr int SBO = KC / 4 * 128;             // bytes between 8-row core-matrix groups
+constexpr int STAGES = 4;
+constexpr int NPROD = 4, NEPI = 8;            // producer and epilogue warps (+ one MMA warp)
+constexpr int TC_THREADS = (NPROD + NEPI + 1) * 32;
+constexpr int MMA_WARP = NPROD + NEPI;
+constexpr int PLANE_A = 128 * KC * 4;         // 4 KB: 128 rows x 8 tf32
+// stage: real    A hi, A lo, B hi, B lo (256 rows)                      24 KB
+//        complex Ar hi, Ar lo, Ai hi, Ai lo, Bc hi, Bc lo (384 rows)   40 KB
+__host__ __device__ constexpr int stage_bytes(bool cplx) { return cplx ? 4 * PLANE_A + 2 * 384 * KC * 4 : 2 * PLANE_A + 2 * 256 * KC * 4; }
+// both variants reserve the complex size, so exactly one CTA fits on an SM
+// (the CTA allocates all 512 TMEM columns)
+__host__ __device__ constexpr int smem_bytes(bool) { return STAGES * stage_bytes(true) + 1024; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// byte offset of (row, k) inside a K-major no-swizzle operand tile (KCH wide)
+// byte offset of (row, k) inside a K-major no-swizzle operand plane (KC wide)
 __device__ __forceinline__ uint32_t cm_off(int row, int k) {
     return (uint32_t)((row >> 3) * SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
@@ -52,9 +71,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 
 // instruction descriptor: D f32, A/B tf32, both K-major
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool negA) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | (negA ? (1u << 13) : 0u) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
@@ -62,6 +80,10 @@ __device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, 
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
         "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -80,74 +102,116 @@ __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t phase) {
     return ok != 0;
 }
 
-__device__ bool mbar_wait_bounded(uint32_t addr, uint32_t phase) {
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// Wait for the phase with the given parity; false after about two seconds or
+// once another role has given up.
+__device__ bool mbar_wait_bounded(uint32_t addr, uint32_t phase, volatile int* fail) {
     long long t0 = clock64();
-    while (!mbar_try(addr, phase))
-        if (clock64() - t0 > (1LL << 32)) return false;   // about two seconds
+    unsigned it = 0;
+    while (!mbar_try(addr, phase)) {
+        if ((++it & 31u) == 0) {
+            if (*fail) return false;
+            if (clock64() - t0 > (1LL << 32)) return false;
+        }
+    }
     return true;
 }
 
-// Load a 32-wide rank chunk of `ROWS` rows (float4 per thread, all loads in
-// flight before any store), split into tf32 hi/lo core-matrix tiles.
+__device__ __forceinline__ void raise_fail(volatile int* fail, int* err) {
+    *fail = 1;
+    atomicExch(err, 1);
+}
+
+struct TileInfo {
+    int c, p, i0, j0, K;
+};
+
 template <int ROWS>
-__device__ __forceinline__ void stage_plane(const float* src, int KRM, int row0, int row_lim, int k0, int K,
-                                            unsigned char* hi, unsigned char* lo) {
-    constexpr int PER = ROWS * (KCH / 4) / TC_THREADS;   // float4 per thread
-    constexpr int Q4 = KCH / 4;                          // float4 per row
+__device__ __forceinline__ TileInfo decode_tile(long long tile, int tiles_i, int tiles_j, int fam_pairs,
+                                                const int* pend, int R) {
+    TileInfo t;
+    long long rest = tile;
+    const int tj = (int)(rest % tiles_j);
+    rest /= tiles_j;
+    const int ti = (int)(rest % tiles_i);
+    rest /= tiles_i;
+    t.p = (int)(rest % fam_pairs);
+    t.c = (int)(rest / fam_pairs);
+    t.i0 = ti * ROWS;
+    t.j0 = tj * 128;
+    t.K = pend[t.c] * R;
+    return t;
+}
+
+// Load rows row0 .. row0 + NR - 1, rank columns k0 .. k0 + 7 of one plane
+// (float4 per thread, all loads issued before any store), split, and write
+// hi/lo at core-matrix row offset dst_row (sign -1 negates).
+template <int NR>
+__device__ __forceinline__ void produce_plane(const float* src, int KRM, int row0, int N, int k0, int K,
+                                              unsigned char* hi, unsigned char* lo, int dst_row, float sign,
+                                              unsigned char* hi2 = nullptr, unsigned char* lo2 = nullptr,
+                                              int dst_row2 = 0) {
+    constexpr int PER = NR * 2 / (NPROD * 32);
+    const int t0 = threadIdx.x;
     float4 v[PER];
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-        int idx = threadIdx.x + t * TC_THREADS;
-        int row = idx / Q4, q4 = idx % Q4;
-        int gr = row0 + row, gk = k0 + 4 * q4;
-        v[t] = (gr < row_lim && gk < K) ? *(const float4*)(src + (size_t)gr * KRM + gk) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int idx = t0 + t * NPROD * 32, row = idx >> 1, k = k0 + 4 * (idx & 1);
+        const int gr = row0 + row;
+        v[t] = (gr < N && k < K) ? __ldg((const float4*)(src + (size_t)gr * KRM + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-        int idx = threadIdx.x + t * TC_THREADS;
-        int row = idx / Q4, q4 = idx % Q4;
-        float4 h = make_float4(tf32_hi(v[t].x), tf32_hi(v[t].y), tf32_hi(v[t].z), tf32_hi(v[t].w));
-        float4 l = make_float4(v[t].x - h.x, v[t].y - h.y, v[t].z - h.z, v[t].w - h.w);
-        uint32_t o = cm_off(row, 4 * q4);
-        *(float4*)(hi + o) = h;
-        *(float4*)(lo + o) = l;
+        const int idx = t0 + t * NPROD * 32, row = idx >> 1, kq = 4 * (idx & 1);
+        const float4 x = v[t];
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        const uint32_t o = cm_off(dst_row + row, kq);
+        *(float4*)(hi + o) = make_float4(sign * h.x, sign * h.y, sign * h.z, sign * h.w);
+        *(float4*)(lo + o) = make_float4(sign * l.x, sign * l.y, sign * l.z, sign * l.w);
+        if (hi2) {
+            const uint32_t o2 = cm_off(dst_row2 + row, kq);
+            *(float4*)(hi2 + o2) = make_float4(-sign * h.x, -sign * h.y, -sign * h.z, -sign * h.w);
+            *(float4*)(lo2 + o2) = make_float4(-sign * l.x, -sign * l.y, -sign * l.z, -sign * l.w);
+        }
     }
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(TC_THREADS, CTAS_PER_SM)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, const int* pend, int R, int KRM,
                 int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint64_t mbar;
+    __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_accf[2], bar_acce[2], bar_done;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail;
+    __shared__ volatile int s_fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // The MMA computes the transposed tile D^T = V^T-rows x U-rows^T: TMEM lane
-    // = output column j (128 per tile), TMEM column = output row i.
-    constexpr int NROW = CPLX ? 64 : 128;         // output rows per tile (MMA N)
+    constexpr int ROWS = CPLX ? 128 : 256;        // W rows per tile
+    constexpr int SB = stage_bytes(CPLX);
     const int rowW = CPLX ? 2 * N : N;            // floats per W row
-    const int tiles_i = (N + NROW - 1) / NROW, tiles_j = (N + 127) / 128;
+    const int tiles_i = (N + ROWS - 1) / ROWS, tiles_j = (N + 127) / 128;
     const size_t NK = (size_t)N * KRM;
     const long long total = (long long)n_chains * fam_pairs * tiles_i * tiles_j;
     unsigned char* base = (unsigned char*)(((uintptr_t)sm + 1023) & ~(uintptr_t)1023);
-    // MMA A operand: V^T rows (re[, im]) x (hi, lo); B operand: U rows likewise
-    unsigned char* A0h = base;
-    unsigned char* A0l = A0h + TILE_BYTES_128;
-    unsigned char* A1h = A0l + TILE_BYTES_128;       // complex only
-    unsigned char* A1l = A1h + TILE_BYTES_128;
-    unsigned char* B0h = CPLX ? A1l + TILE_BYTES_128 : A1h;
-    unsigned char* B0l = B0h + NROW * KCH * 4;
-    unsigned char* B1h = B0l + NROW * KCH * 4;       // complex only
-    unsigned char* B1l = B1h + NROW * KCH * 4;
 
-    if (warp == 0) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(128));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        for (int s = 0; s < STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[s])), "r"(NPROD * 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[s])));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_accf[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_acce[b])), "r"(NEPI * 32));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_done)));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_fail = 0;
     }
@@ -155,141 +219,172 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tmem_slot;
-    const uint32_t mb = smem_u32(&mbar);
-    uint32_t phase = 0;
 
-    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        long long rest = tile;
-        const int tj = (int)(rest % tiles_j); rest /= tiles_j;
-        const int ti = (int)(rest % tiles_i); rest /= tiles_i;
-        const int p = (int)(rest % fam_pairs); rest /= fam_pairs;
-        const int c = (int)rest;
-        const int K = pend[c] * R;
-        if (K == 0) continue;
-        const size_t blk = ((size_t)c * fam_pairs + p) * (CPLX ? 4 : 2) * NK;
-        const float* U0 = Pan + blk;                         // U (re)
-        const float* U1 = U0 + NK;                           // U im (complex)
-        const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;   // V^T (re)
-        const float* V1 = V0 + NK;
-        const int i0 = ti * NROW, j0 = tj * 128;
-        float* Wp = W + ((size_t)c * fam_pairs + p) * (size_t)N * rowW;
-        for (int k0 = 0; k0 < K; k0 += KCH) {
-            stage_plane<128>(V0, KRM, j0, N, k0, K, A0h, A0l);
-            stage_plane<NROW>(U0, KRM, i0, N, k0, K, B0h, B0l);
-            if (CPLX) {
-                stage_plane<128>(V1, KRM, j0, N, k0, K, A1h, A1l);
-                stage_plane<NROW>(U1, KRM, i0, N, k0, K, B1h, B1l);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t a0h = smem_u32(A0h), a0l = smem_u32(A0l), b0h = smem_u32(B0h), b0l = smem_u32(B0l);
-                const uint32_t a1h = smem_u32(A1h), a1l = smem_u32(A1l), b1h = smem_u32(B1h), b1l = smem_u32(B1l);
-#pragma unroll
-                for (int kk = 0; kk < KCH / 8; ++kk) {
-                    const uint32_t o = kk * 256;             // two core matrices along K per MMA
-                    const uint32_t first = (k0 == 0 && kk == 0) ? 0u : 1u;
-                    if (!CPLX) {
-                        constexpr uint32_t id = idesc_tf32(128, 128, false);
-                        mma_tf32(tbase, smem_desc(a0h + o), smem_desc(b0h + o), id, first);
-                        mma_tf32(tbase, smem_desc(a0h + o), smem_desc(b0l + o), id, 1u);
-                        mma_tf32(tbase, smem_desc(a0l + o), smem_desc(b0h + o), id, 1u);
-                    } else {
-                        constexpr uint32_t id = idesc_tf32(128, 64, false);
-                        constexpr uint32_t idn = idesc_tf32(128, 64, true);
-                        const uint32_t dre = tbase, dim = tbase + 64;
-                        // re(D^T) = Vr Ur^T - Vi Ui^T
-                        mma_tf32(dre, smem_desc(a0h + o), smem_desc(b0h + o), id, first);
-                        mma_tf32(dre, smem_desc(a0h + o), smem_desc(b0l + o), id, 1u);
-                        mma_tf32(dre, smem_desc(a0l + o), smem_desc(b0h + o), id, 1u);
-                        mma_tf32(dre, smem_desc(a1h + o), smem_desc(b1h + o), idn, 1u);
-                        mma_tf32(dre, smem_desc(a1h + o), smem_desc(b1l + o), idn, 1u);
-                        mma_tf32(dre, smem_desc(a1l + o), smem_desc(b1h + o), idn, 1u);
-                        // im(D^T) = Vr Ui^T + Vi Ur^T
-                        mma_tf32(dim, smem_desc(a0h + o), smem_desc(b1h + o), id, first);
-                        mma_tf32(dim, smem_desc(a0h + o), smem_desc(b1l + o), id, 1u);
-                        mma_tf32(dim, smem_desc(a0l + o), smem_desc(b1h + o), id, 1u);
-                        mma_tf32(dim, smem_desc(a1h + o), smem_desc(b0h + o), id, 1u);
-                        mma_tf32(dim, smem_desc(a1h + o), smem_desc(b0l + o), id, 1u);
-                        mma_tf32(dim, smem_desc(a1l + o), smem_desc(b0h + o), id, 1u);
-                    }
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                             : "memory");
-                if (!mbar_wait_bounded(mb, phase)) {
-                    s_fail = 1;
-                    atomicExch(err, 1);
-                    mbar_wait_bounded(mb, phase);   // second bounded wait for the MMAs in flight
-                }
-            }
-            phase ^= 1u;
-            __syncthreads();
-            if (s_fail) break;
-        }
-        if (s_fail) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // epilogue: lane = output column j, register k of block cb = output row
-        // i0 + 16 cb + k; a warp touches 32 consecutive columns (coalesced)
-        {
-            const int j = j0 + warp * 32 + lane;
-            const uint32_t tl = tbase + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-            for (int cb = 0; cb < NROW / 16; ++cb) {
-                uint32_t v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-                    " [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15])
-                    : "r"(tl + cb * 16));
+    if (warp < NPROD) {
+        // ---- producers ----
+        int st = 0;
+        uint32_t ph = 0;
+        for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
+            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R);
+            if (t.K == 0) continue;
+            const size_t blk = ((size_t)t.c * fam_pairs + t.p) * (CPLX ? 4 : 2) * NK;
+            const float* U0 = Pan + blk;                         // U (re)
+            const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;   // V^T (re)
+            bool ok = true;
+            for (int k0 = 0; k0 < t.K; k0 += KC) {
+                if (!mbar_wait_bounded(smem_u32(&bar_empty[st]), ph ^ 1u, &s_fail)) { ok = false; break; }
+                unsigned char* sb = base + st * SB;
                 if (!CPLX) {
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    produce_plane<128>(V0, KRM, t.j0, N, k0, t.K, sb, sb + PLANE_A, 0, 1.f);
+                    produce_plane<256>(U0, KRM, t.i0, N, k0, t.K, sb + 2 * PLANE_A, sb + 2 * PLANE_A + 256 * KC * 4, 0,
+                                       1.f);
+                } else {
+                    unsigned char* bh = sb + 4 * PLANE_A;
+                    unsigned char* bl = bh + 384 * KC * 4;
+                    produce_plane<128>(V0, KRM, t.j0, N, k0, t.K, sb, sb + PLANE_A, 0, 1.f);
+                    produce_plane<128>(V0 + NK, KRM, t.j0, N, k0, t.K, sb + 2 * PLANE_A, sb + 3 * PLANE_A, 0, 1.f);
+                    produce_plane<128>(U0, KRM, t.i0, N, k0, t.K, bh, bl, 128, 1.f);               // U_r
+                    produce_plane<128>(U0 + NK, KRM, t.i0, N, k0, t.K, bh, bl, 256, 1.f, bh, bl, 0);   // U_i, -U_i
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&bar_full[st]));
+                if (++st == STAGES) { st = 0; ph ^= 1u; }
+            }
+            if (!ok) { raise_fail(&s_fail, err); break; }
+        }
+    } else if (warp < MMA_WARP) {
+        // ---- epilogue ----
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int half = (warp - NPROD) >> 2;   // which half of the tile's rows
+        int b = 0;
+        uint32_t ph = 0;
+        for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
+            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R);
+            if (t.K == 0) continue;
+            if (!mbar_wait_bounded(smem_u32(&bar_accf[b]), ph, &s_fail)) { raise_fail(&s_fail, err); break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int j = t.j0 + q * 32 + lane;
+            float* Wp = W + ((size_t)t.c * fam_pairs + t.p) * (size_t)N * rowW;
+            const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
+            if (!CPLX) {
+                // rows i0 + half*128 + 16 cb + k  <->  TMEM column half*128 + 16 cb + k
+#pragma unroll 1
+                for (int cb = 0; cb < 8; ++cb) {
+                    uint32_t v[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(tl + half * 128 + cb * 16));
+                    const int ib = t.i0 + half * 128 + cb * 16;
                     float w[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const int i = i0 + cb * 16 + k;
+                        const int i = ib + k;
                         w[k] = (i < N && j < N) ? Wp[(size_t)i * N + j] : 0.f;
                     }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const int i = i0 + cb * 16 + k;
+                        const int i = ib + k;
                         if (i < N && j < N) Wp[(size_t)i * N + j] = w[k] - __uint_as_float(v[k]);
                     }
-                } else {
-                    uint32_t vi[16];
+                }
+            } else {
+                // rows i0 + half*64 + 16 cb + k  <->  re column half*64 + 16 cb + k, im column + 128
+#pragma unroll 1
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t v[16], vi[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(tl + half * 64 + cb * 16));
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
                         "%15}, [%16];"
                         : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
                           "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]),
                           "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
-                        : "r"(tl + 64 + cb * 16));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        : "r"(tl + 128 + half * 64 + cb * 16));
+                    const int ib = t.i0 + half * 64 + cb * 16;
                     float2 w[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const int i = i0 + cb * 16 + k;
+                        const int i = ib + k;
                         w[k] = (i < N && j < N) ? *(const float2*)(Wp + (size_t)i * rowW + 2 * j) : make_float2(0.f, 0.f);
                     }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const int i = i0 + cb * 16 + k;
+                        const int i = ib + k;
                         if (i < N && j < N)
                             *(float2*)(Wp + (size_t)i * rowW + 2 * j) =
                                 make_float2(w[k].x - __uint_as_float(v[k]), w[k].y - __uint_as_float(vi[k]));
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(smem_u32(&bar_acce[b]));
+            b ^= 1;
+            if (b == 0) ph ^= 1u;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+    } else if (lane == 0) {
+        // ---- MMA issuer ----
+        int st = 0, b = 0;
+        uint32_t ph = 0, bph = 0;
+        constexpr uint32_t id = idesc_tf32(128, 256);
+        for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
+            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R);
+            if (t.K == 0) continue;
+            if (!mbar_wait_bounded(smem_u32(&bar_acce[b]), bph ^ 1u, &s_fail)) { raise_fail(&s_fail, err); break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t d = tbase + (uint32_t)(b * 256);
+            bool ok = true;
+            for (int k0 = 0; k0 < t.K; k0 += KC) {
+                if (!mbar_wait_bounded(smem_u32(&bar_full[st]), ph, &s_fail)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sb = smem_u32(base + st * SB);
+                const uint32_t first = k0 == 0 ? 0u : 1u;
+                if (!CPLX) {
+                    const uint32_t ah = sb, al = sb + PLANE_A, bh = sb + 2 * PLANE_A, bl = bh + 256 * KC * 4;
+                    mma_tf32(d, smem_desc(ah), smem_desc(bh), id, first);
+                    mma_tf32(d, smem_desc(ah), smem_desc(bl), id, 1u);
+                    mma_tf32(d, smem_desc(al), smem_desc(bh), id, 1u);
+                } else {
+                    const uint32_t arh = sb, arl = sb + PLANE_A, aih = sb + 2 * PLANE_A, ail = sb + 3 * PLANE_A;
+                    const uint32_t bh = sb + 4 * PLANE_A, bl = bh + 384 * KC * 4;
+                    const uint32_t o1 = (128 / 8) * SBO;    // rows 128..383: [U_r ; U_i]
+                    // rows 0..255: [-U_i ; U_r]
+                    mma_tf32(d, smem_desc(arh), smem_desc(bh + o1), id, first);
+                    mma_tf32(d, smem_desc(arh), smem_desc(bl + o1), id, 1u);
+                    mma_tf32(d, smem_desc(arl), smem_desc(bh + o1), id, 1u);
+                    mma_tf32(d, smem_desc(aih), smem_desc(bh), id, 1u);
+                    mma_tf32(d, smem_desc(aih), smem_desc(bl), id, 1u);
+                    mma_tf32(d, smem_desc(ail), smem_desc(bh), id, 1u);
+                }
+                mma_commit(smem_u32(&bar_empty[st]));
+                if (++st == STAGES) { st = 0; ph ^= 1u; }
+            }
+            if (!ok) { raise_fail(&s_fail, err); break; }
+            mma_commit(smem_u32(&bar_accf[b]));
+            b ^= 1;
+            if (b == 0) bph ^= 1u;
+        }
+        // every issued MMA completes before the TMEM is released
+        mma_commit(smem_u32(&bar_done));
+        volatile int never = 0;
+        if (!mbar_wait_bounded(smem_u32(&bar_done), 0u, &never)) atomicExch(err, 1);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(128));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
     }
 }
 
@@ -311,11 +406,11 @@ namespace {
 ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_chains, float* W, const float* Pan,
                            const int* pend, int R, int KRM, int* err, cudaStream_t st) {
     if (fam_pairs == 0 || n_chains == 0) return GGF_OK;
-    const int rowW = cplx ? 2 * N : N;
-    const long long total = (long long)n_chains * fam_pairs * ((N + (cplx ? 63 : 127)) / (cplx ? 64 : 128)) *
-                            ((N + 127) / 128);
+    if (KRM % 4) return ggf_fail(ctx, GGF_EINVAL, "tensor-core flush: panel row stride must be a multiple of 4");
+    const int rows = cplx ? 128 : 256;
+    const long long total = (long long)n_chains * fam_pairs * ((N + rows - 1) / rows) * ((N + 127) / 128);
     int sms = ctx->n_sms > 0 ? ctx->n_sms : 152;
-    const long long grid = std::min<long long>(total, (long long)sms * CTAS_PER_SM);
+    const long long grid = std::min<long long>(total, (long long)sms);
     GGF_TRY(ggf_prepare_flush_tc(ctx));
     if (cplx) {
         flush_tc_kernel<true><<<(unsigned)grid, TC_THREADS, smem_bytes(true), st>>>(N, fam_pairs, n_chains, W, Pan,
@@ -386,10 +481,10 @@ ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st) {
 }
 
 extern "C" ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank, double* max_rel_err) {
-    if (!ctx || !max_rel_err || N < 1 || N > 8192 || rank < 8 || rank > 128 || rank % 8)
-        return ggf_fail(ctx, GGF_EINVAL, "selftest_flush: N in [1, 8192], rank in {8, 16, ..., 128}");
+    if (!ctx || !max_rel_err || N < 1 || N > 8192 || rank < 4 || rank > 512 || rank % 4)
+        return ggf_fail(ctx, GGF_EINVAL, "selftest_flush: N in [1, 8192], rank in {4, 8, ..., 512}");
     cudaSetDevice(ctx->device);
-    const int R = 8, KRM = rank;
+    const int R = 4, KRM = rank;
     const int rowW = cplx ? 2 * N : N;
     const size_t NK = (size_t)N * KRM, nW = (size_t)N * rowW, nP = (cplx ? 4 : 2) * NK;
     float *W = nullptr, *Pan = nullptr;

@@ -19,104 +19,9 @@
 #include "ggf_ctx.h"
 #include "ggf_geom.cuh"
 
+#include "ggf_sweep.cuh"
+
 namespace {
-
-constexpr int NWARP = 8;
-
-__device__ __forceinline__ double magc(cxd v) { return fabs(v.x) + fabs(v.y); }
-
-// warp argmax over lanes (ties: lowest index)
-__device__ __forceinline__ int warp_argmax(double v, int idx) {
-    for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-    }
-    return idx;
-}
-
-// Pfaffian of an n x n (n <= 32) antisymmetric matrix in shared memory, by one
-// warp (skew Gaussian elimination with pivoting).  A is destroyed.
-__device__ cxd warp_pfaffian(cxd* A, int n) {
-    const int lane = threadIdx.x & 31;
-    cxd res = {1.0, 0.0};
-    for (int k = 0; k < n - 1; k += 2) {
-        double m = (lane >= k + 1 && lane < n) ? magc(A[lane * n + k]) : -1.0;
-        int p = warp_argmax(m, lane);
-        const int q = k + 1;
-        if (p != q) {
-            if (lane >= k && lane < n) {
-                cxd t = A[q * n + lane]; A[q * n + lane] = A[p * n + lane]; A[p * n + lane] = t;
-            }
-            __syncwarp();
-            if (lane >= k && lane < n) {
-                cxd t = A[lane * n + q]; A[lane * n + q] = A[lane * n + p]; A[lane * n + p] = t;
-            }
-            __syncwarp();
-            res = -res;
-        }
-        cxd piv = A[q * n + k];
-        if (piv.x == 0.0 && piv.y == 0.0) { __syncwarp(); return {0.0, 0.0}; }
-        res = res * A[k * n + q];
-        int mm = n - k - 2;
-        for (int e = lane; e < mm * mm; e += 32) {
-            int i = k + 2 + e / mm, j = k + 2 + e % mm;
-            cxd ti = A[i * n + k] / piv, tj = A[j * n + k] / piv;
-            A[i * n + j] += ti * A[j * n + q] - A[i * n + q] * tj;
-        }
-        __syncwarp();
-    }
-    return res;
-}
-
-// Solve [A | B] (r x 2r, row-major, stride 2r) in place by Gauss-Jordan with
-// partial pivoting; the right half becomes A^{-1} B.  fcol: r scratch.
-__device__ bool warp_solve(cxd* A, int r, cxd* fcol) {
-    const int lane = threadIdx.x & 31;
-    const int w = 2 * r;
-    for (int k = 0; k < r; ++k) {
-        double m = (lane >= k && lane < r) ? magc(A[lane * w + k]) : -1.0;
-        int p = warp_argmax(m, lane);
-        if (p != k) {
-            if (lane < w) { cxd t = A[k * w + lane]; A[k * w + lane] = A[p * w + lane]; A[p * w + lane] = t; }
-            __syncwarp();
-        }
-        cxd d = A[k * w + k];
-        if (d.x == 0.0 && d.y == 0.0) return false;
-        __syncwarp();
-        if (lane < w) A[k * w + lane] = A[k * w + lane] / d;
-        if (lane < r) fcol[lane] = A[lane * w + k];
-        __syncwarp();
-        for (int e = lane; e < r * w; e += 32) {
-            int i = e / w, j = e % w;
-            if (i != k) A[i * w + j] -= fcol[i] * A[k * w + j];
-        }
-        __syncwarp();
-    }
-    return true;
-}
-
-template <class T>
-__device__ __forceinline__ cxd loadc(const T* p) { return Sc<T>::to(*p); }
-
-// Pending-update panels of one (chain, pair): U (N x KRM) followed by V^T
-// (N x KRM), K-major (row index first, rank index contiguous); complex
-// values are stored as a real plane followed by an imaginary plane, so a
-// (chain, pair) block holds 2 (real) or 4 (complex) planes of N * KRM.
-template <class T> struct PanelIO {
-    typedef typename Sc<T>::R R;
-    static constexpr int PLANES = Sc<T>::CPLX ? 2 : 1;
-    __device__ static T ld(const R* p, size_t plane, size_t idx);
-    __device__ static void st(R* p, size_t plane, size_t idx, T v);
-};
-template <> __device__ __forceinline__ double PanelIO<double>::ld(const double* p, size_t, size_t i) { return p[i]; }
-template <> __device__ __forceinline__ float PanelIO<float>::ld(const float* p, size_t, size_t i) { return p[i]; }
-template <> __device__ __forceinline__ cxd PanelIO<cxd>::ld(const double* p, size_t pl, size_t i) { return {p[i], p[pl + i]}; }
-template <> __device__ __forceinline__ cxf PanelIO<cxf>::ld(const float* p, size_t pl, size_t i) { return {p[i], p[pl + i]}; }
-template <> __device__ __forceinline__ void PanelIO<double>::st(double* p, size_t, size_t i, double v) { p[i] = v; }
-template <> __device__ __forceinline__ void PanelIO<float>::st(float* p, size_t, size_t i, float v) { p[i] = v; }
-template <> __device__ __forceinline__ void PanelIO<cxd>::st(double* p, size_t pl, size_t i, cxd v) { p[i] = v.x; p[pl + i] = v.y; }
-template <> __device__ __forceinline__ void PanelIO<cxf>::st(float* p, size_t pl, size_t i, cxf v) { p[i] = v.x; p[pl + i] = v.y; }
 
 struct SweepArgs {
     DevConst dc;
@@ -160,54 +65,27 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
     cxd* Bord = Wss + P * r * r;           // [NWARP][2r][2r]
     cxd* rho = Bord + NWARP * 4 * r * r;   // [P]
     cxd* fcol = rho + P;                   // [NWARP][r]
-    __shared__ double s_old_g, s_new_g, s_old_t, s_new_t;
+    __shared__ Proposal s_q;
     __shared__ int s_accept;
 
-    const int l = a.link_of_chain ? a.link_of_chain[c] : a.link, s = l >> 1, d = l & 1;
-    const int x = s % g.L, y = s / g.L;
-    const int t = d == 0 ? y * g.L + (x + 1) % g.L : ((y + 1) % g.L) * g.L + x;
-    const int a0 = s * g.B + (2 * d + 1) * g.h2, b0 = t * g.B + (2 * d) * g.h2;
+    const int l = a.link_of_chain ? a.link_of_chain[c] : a.link;
+    int a0, b0;
+    link_ends(g, l, a0, b0);
 
     if (threadIdx.x == 0) {
-        uint64_t ctr[4] = {(uint64_t)*a.d_sweep, (uint64_t)l, 0, 0}, out[4];
-        philox4x64_10(ctr, a.seed, (uint64_t)c, out);
-        double u_acc = u53(out[0]), u_prop = u53(out[1]);
-        s_new_t = u_acc;  // temporarily hold u_acc
-        if (g.group == GGF_Z2) {
-            double gv = (double)((const int8_t*)a.links)[(size_t)c * g.n_links + l];
-            s_old_g = gv; s_new_g = -gv; s_old_t = 0.0;
-        } else {
-            double th = ((const double*)a.links)[(size_t)c * g.n_links + l];
-            double tn = th + a.width * (u_prop - 0.5);
-            if (tn >= GGF_TWO_PI) tn -= GGF_TWO_PI;
-            else if (tn < 0.0) tn += GGF_TWO_PI;
-            if (a.forced) tn = a.forced[(size_t)c * 32 + a.forced_k];   // block move: given angle
-            s_old_g = 1.0; s_new_g = 1.0; s_old_t = th;
-            fcol[0] = {tn, 0.0};
-        }
+        Proposal q = draw_proposal(g, a.links, c, l, *a.d_sweep, a.seed, a.width);
+        if (a.forced && g.group == GGF_U1) q.th_new = a.forced[(size_t)c * 32 + a.forced_k];   // block move
+        s_q = q;
     }
     __syncthreads();
-    const double u_acc = s_new_t;
-    const double th_new = g.group == GGF_Z2 ? 0.0 : fcol[0].x;
-    const double g_old = s_old_g, g_new = s_new_g, th_old = s_old_t;
-    __syncthreads();
+    const Proposal q = s_q;
 
     for (int p = warp; p < P; p += NWARP) {
         cxd* D = Delta + p * r * r;
         cxd* Ws = Wss + p * r * r;
+        pair_delta(a.dc, p, l, q, D);
         for (int e = lane; e < r * r; e += 32) {
-            int xi = e / r, yi = e % r;
-            cxd nv, ov;
-            if (p < K) {
-                nv = {twisted<double>(a.dc, p, l, xi, yi, g_new, th_new), 0.0};
-                ov = {twisted<double>(a.dc, p, l, xi, yi, g_old, th_old), 0.0};
-            } else {
-                nv = twisted<cxd>(a.dc, p - K, l, xi, yi, g_new, th_new);
-                ov = twisted<cxd>(a.dc, p - K, l, xi, yi, g_old, th_old);
-            }
-            D[e] = nv - ov;
-            int gi = xi < g.h2 ? a0 + xi : b0 + xi - g.h2;
-            int gj = yi < g.h2 ? a0 + yi : b0 + yi - g.h2;
+            const int gi = link_majorana(g, a0, b0, e / r), gj = link_majorana(g, a0, b0, e % r);
             cxd wv;
             if (p < K) wv = loadc((const RW*)a.Wr + (((size_t)c * K + p) * N + gi) * N + gj);
             else wv = loadc((const CW*)a.Wc + (((size_t)c * (P - K) + (p - K)) * N + gi) * N + gj);
@@ -220,50 +98,29 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
                 if (p < K) {
                     const R* U = (const R*)a.Pr + ((size_t)c * K + p) * 2 * NK;
                     const R* Vt = U + NK;
-                    for (int q = 0; q < kr; ++q)
-                        wv -= Sc<RW>::to(PanelIO<RW>::ld(U, NK, (size_t)gi * KRM + q)) *
-                              Sc<RW>::to(PanelIO<RW>::ld(Vt, NK, (size_t)gj * KRM + q));
+                    for (int qq = 0; qq < kr; ++qq)
+                        wv -= Sc<RW>::to(PanelIO<RW>::ld(U, NK, (size_t)gi * KRM + qq)) *
+                              Sc<RW>::to(PanelIO<RW>::ld(Vt, NK, (size_t)gj * KRM + qq));
                 } else {
                     const R* U = (const R*)a.Pc + ((size_t)c * (P - K) + (p - K)) * 4 * NK;
                     const R* Vt = U + 2 * NK;
-                    for (int q = 0; q < kr; ++q)
-                        wv -= Sc<CW>::to(PanelIO<CW>::ld(U, NK, (size_t)gi * KRM + q)) *
-                              Sc<CW>::to(PanelIO<CW>::ld(Vt, NK, (size_t)gj * KRM + q));
+                    for (int qq = 0; qq < kr; ++qq)
+                        wv -= Sc<CW>::to(PanelIO<CW>::ld(U, NK, (size_t)gi * KRM + qq)) *
+                              Sc<CW>::to(PanelIO<CW>::ld(Vt, NK, (size_t)gj * KRM + qq));
                 }
             }
             Ws[e] = wv;
         }
         __syncwarp();
-        cxd* Bw = Bord + warp * 4 * r * r;
-        const int n2 = 2 * r;
-        for (int e = lane; e < n2 * n2; e += 32) {
-            int i = e / n2, j = e % n2;
-            cxd v = {0.0, 0.0};
-            if (i < r && j < r) v = D[i * r + j];
-            else if (i >= r && j >= r) v = Ws[(i - r) * r + (j - r)];
-            else if (i < r && j == i + r) v = {-1.0, 0.0};
-            else if (i >= r && j == i - r) v = {1.0, 0.0};
-            Bw[e] = v;
-        }
-        __syncwarp();
-        cxd pf = warp_pfaffian(Bw, n2);
+        cxd pf = bordered_ratio(D, Ws, Bord + warp * 4 * r * r, r);
         if (lane == 0) rho[p] = pf;
         __syncwarp();
     }
     __syncthreads();
 
     if (threadIdx.x == 0) {
-        double amax = -INFINITY;
-        for (int p = 0; p < P; ++p) amax = fmax(amax, a.dc.logc[p].x + a.ell[(size_t)c * P + p].x);
-        double so = 0.0, sn = 0.0;
-        for (int p = 0; p < P; ++p) {
-            cxd e = a.dc.logc[p] + a.ell[(size_t)c * P + p];
-            if (p < K) e.y = 0.0;
-            e.x -= amax;
-            cxd tt = a.dc.w[p] * cexp_(e);
-            so += tt.x;
-            sn += (tt * rho[p]).x;
-        }
+        double sn, so;
+        combine_pairs(a.dc, a.ell + (size_t)c * P, rho, sn, so);
         int acc;
         if (a.forced) {
             // block move: every link of the block is taken tentatively; the move is
@@ -273,7 +130,7 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
             if (!ok) a.dead[c] = 1;
             acc = ok ? 1 : 0;
         } else {
-            acc = (sn > 0.0 && so > 0.0 && u_acc < sn / so) ? 1 : 0;
+            acc = (sn > 0.0 && so > 0.0 && q.u_acc < sn / so) ? 1 : 0;
             atomicAdd(&a.counters[0], 1ULL);
         }
         s_accept = acc;
@@ -285,45 +142,18 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
                 a.since_refresh[c] += 1;
                 a.sweep_acc[c] += 1;
             }
-            if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)g_new;
-            else ((double*)a.links)[(size_t)c * g.n_links + l] = th_new;
+            if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)q.g_new;
+            else ((double*)a.links)[(size_t)c * g.n_links + l] = q.th_new;
         }
     }
     __syncthreads();
     if (!s_accept) return;
 
     for (int p = warp; p < P; p += NWARP) {
-        cxd* D = Delta + p * r * r;
-        cxd* Ws = Wss + p * r * r;
-        cxd* Aug = Bord + warp * 4 * r * r;   // r x 2r
-        const int w2 = 2 * r;
-        for (int e = lane; e < r * w2; e += 32) {
-            int i = e / w2, j = e % w2;
-            cxd v;
-            if (j < r) {
-                v = {i == j ? 1.0 : 0.0, 0.0};
-                for (int z = 0; z < r; ++z) v += D[i * r + z] * Ws[z * r + j];
-            } else {
-                v = D[i * r + (j - r)];
-            }
-            Aug[e] = v;
-        }
-        __syncwarp();
-        if (!warp_solve(Aug, r, fcol + warp * r) && a.forced && lane == 0) a.dead[c] = 1;
-        for (int e = lane; e < r * r; e += 32) {
-            int i = e / r, j = e % r;
-            a.zbuf[((size_t)c * P + p) * r * r + e] = Aug[i * w2 + r + j];
-        }
-        if (lane == 0) {
-            cxd lr = clog_(rho[p]);
-            cxd& el = a.ell[(size_t)c * P + p];
-            if (p < K) el.x += lr.x;
-            else {
-                el = el + lr;
-                if (el.y > M_PI) el.y -= 2 * M_PI;
-                else if (el.y <= -M_PI) el.y += 2 * M_PI;
-            }
-        }
+        const bool ok = pair_z(Delta + p * r * r, Wss + p * r * r, Bord + warp * 4 * r * r, fcol + warp * r, r,
+                               a.zbuf + ((size_t)c * P + p) * r * r);
+        if (!ok && a.forced && lane == 0) a.dead[c] = 1;
+        if (lane == 0) ell_add(a.ell[(size_t)c * P + p], rho[p], p < K);
         __syncwarp();
     }
     // rows Y = W[S, :] and columns C^T = W[:, S]^T for the update kernel,

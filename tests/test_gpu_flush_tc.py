@@ -1,15 +1,20 @@
 """The tcgen05 tensor-core flush of the delayed updates (TF32 three-product
-split) reproduces W - U V^T at FP32 accuracy against an FP64 reference."""
+split) reproduces W - U V^T at FP32 accuracy against an FP64 reference.
+
+The tensor core accumulates the rank-K sum in FP32 in TMEM, so the error
+grows with K: the bound is 2e-6 of the largest entry up to K = 128 and
+scales linearly beyond (3.3e-6 measured at K = 256, complex)."""
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("cplx", [0, 1])
-@pytest.mark.parametrize("N,rank", [(128, 8), (200, 32), (512, 64), (384, 72), (4096, 64)])
+@pytest.mark.parametrize("N,rank", [(128, 8), (200, 36), (512, 64), (384, 72), (1000, 132), (4096, 64),
+                                    (4096, 128), (777, 256), (300, 512)])
 def test_flush_tc_accuracy(cplx, N, rank):
     from paper_2412_01737_gb300 import GGF
     ctx = GGF(0)
     err = ctx.selftest_flush(cplx, N, rank)
     ctx.close()
-    assert err < 2e-6, err
+    assert err < 2e-6 * max(1.0, rank / 128), err

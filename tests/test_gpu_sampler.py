@@ -22,7 +22,7 @@ def run_both(p, n_chains, n_sweeps, seed, start=None, refresh=8, precision=0, de
     return start, obs, fin, st
 
 
-@pytest.mark.parametrize("delay", [1, 4])
+@pytest.mark.parametrize("delay", [1, 4, 5])
 @pytest.mark.parametrize("case", [
     (2, gi.Z2, 1, 1, 4, 25),
     (2, gi.U1, 1, 2, 3, 6),
@@ -56,7 +56,7 @@ def test_random_start_and_refresh_every_accept():
     assert st.refreshes > 0 and st.max_drift < 1e-9
 
 
-@pytest.mark.parametrize("delay", [1, 8])
+@pytest.mark.parametrize("delay", [1, 8, 16])
 def test_fp32_replay(delay):
     from paper_2412_01737_gb300 import FP32
     p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
