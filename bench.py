@@ -195,6 +195,13 @@ def problem_for(name):
     return p, chains, prec, refresh, delay, label
 
 
+def flush_bytes(p, prec):
+    """Algorithmic HBM bytes of one flush of one chain in the delayed and batched
+    modes: the upper triangle (N (N + 1) / 2 elements) of every pair's W read
+    and written once."""
+    return unit_bytes(p, prec) * (p.N + 1) / (2 * p.N)
+
+
 def unit_bytes(p, prec):
     """Algorithmic HBM bytes of one rank-r update of one chain: every pair's W
     read and written once (N^2 elements each)."""
@@ -294,7 +301,7 @@ def run_ggf(args):
     torch.cuda.set_device(local)
     import ggf_inputs as gi
     from paper_2412_01737_gb300 import GGF
-    from paper_2412_01737_gb300.ggf import KT_RATIO, KT_UPDATE, KT_REFRESH, KT_FLUSH
+    from paper_2412_01737_gb300.ggf import KT_RATIO, KT_UPDATE, KT_REFRESH, KT_FLUSH, KT_GATHER, KT_APPLY
 
     p, chains, prec, refresh, delay, label = problem_for(args.workload)
     if args.chains:
@@ -366,7 +373,8 @@ def run_ggf(args):
     obs_all = [o.cpu().numpy() if hasattr(o, "cpu") else o for o in obs_all]
     st1 = ctx.chains_stats()
     kt = {k: ctx.kernel_time(v) for k, v in (("ratio", KT_RATIO), ("update", KT_UPDATE),
-                                             ("refresh", KT_REFRESH), ("flush", KT_FLUSH))}
+                                             ("refresh", KT_REFRESH), ("flush", KT_FLUSH),
+                                             ("gather", KT_GATHER), ("apply", KT_APPLY))}
     ctx.profile(False)
     if dist:
         t = torch.tensor([ms], dtype=torch.float64)
@@ -397,16 +405,17 @@ def run_ggf(args):
         fl = accepts * 2.0 * p.N ** 2 * p.r * wpairs      # every accepted rank-r update folded once
         t_fl = kt["flush"][0] * 1e-3
         if prec == 1:
-            # tensor-core flush: W read + written once per flush call and chain
-            byts = kt["flush"][1] * chains * unit_bytes(p, prec)
-            roof = {"kernel": "flush_tc_kernel (tcgen05 TF32x3, W -= U V)", "bound": "hbm",
+            # tensor-core flush: the upper triangle of W (delayed and batched modes
+            # keep only i <= j) read and written once per flush call and chain
+            byts = kt["flush"][1] * chains * flush_bytes(p, prec)
+            roof = {"kernel": "flush_tc_kernel (tcgen05 TF32x3, W -= U V, upper triangle)", "bound": "hbm",
                     "achieved": byts / t_fl / 1e9, "peak": hbm, "unit": "GB/s",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                    "algorithmic_bytes_per_launch_group": chains * unit_bytes(p, prec),
-                    "fp32_equivalent_tflops": fl / t_fl / 1e12}
+                    "algorithmic_bytes_per_launch_group": chains * flush_bytes(p, prec),
+                    "fp32_equivalent_tflops": fl / 2 / t_fl / 1e12}
         else:
-            roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V)", "bound": "alu",
-                    "achieved": fl / t_fl / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+            roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V, upper triangle)", "bound": "alu",
+                    "achieved": fl / 2 / t_fl / 1e12, "peak": 1.25, "unit": "TFLOP/s",
                     "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe)"}
     elif dom == "update" and delay <= 1:
         upd_bytes = accepts * unit_bytes(p, prec)
@@ -414,21 +423,40 @@ def run_ggf(args):
                 "achieved": upd_bytes / (kt["update"][0] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     elif dom == "update":
-        # gather: per tentative or accepted update and pair, panel rows U, V^T (2 N kr b) plus
-        # the rows/columns of W at S and the two new panel columns (4 N r b); kr taken at its
-        # mean over a flush interval.  The panels are mostly L2-resident: no HBM peak applies.
+        # gather of the pending-panel path (block moves): per tentative update and pair,
+        # panel rows U, V^T (2 N kr b) plus the rows of W at S and the new panel columns
+        # (3 N r b), kr at its mean over a block.  Mostly L2-resident: no HBM peak applies.
         b = 8 if prec == 0 else 4
-        kr_mean = 0.5 * (delay - 1) * p.r
-        per = sum((2 if n == m else 4) * b * p.N * (kr_mean + 2 * p.r) for n in range(p.K) for m in range(n, p.K))
-        n_upd = accepts + 32 * ((st1.block_proposals - st0.block_proposals) if hasattr(st1, "block_proposals") else 0)
-        roof = {"kernel": "gather_kernel (delayed rows/columns)", "bound": "l2",
+        kr_mean = 0.5 * 31 * p.r
+        per = sum((2 if n == m else 4) * b * p.N * (kr_mean + 1.5 * p.r) for n in range(p.K) for m in range(n, p.K))
+        n_upd = 32 * ((st1.block_proposals - st0.block_proposals) if hasattr(st1, "block_proposals") else 0)
+        roof = {"kernel": "gather_kernel (pending-panel rows/columns)", "bound": "l2",
                 "achieved": n_upd * per / (kt["update"][0] * 1e-3) / 1e9, "peak": None, "unit": "GB/s",
                 "peak_source": "no measured L2 peak; reported for the record"}
+    elif dom == "ratio" and delay > 1:
+        props = st1.proposals - st0.proposals
+        roof = {"kernel": "batch_steps (link steps on W[T, T], FP64 ratios)", "bound": "latency",
+                "achieved": props / (kt["ratio"][0] * 1e-3), "peak": None, "unit": "link proposals/s",
+                "peak_source": "latency-bound (one CTA per chain, sequential links); no peak applies"}
     else:
         roof = {"kernel": "ratio_kernel", "bound": "alu", "achieved": None, "peak": None, "unit": None}
-    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") else None
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
     roof["traffic"] = None
     roof["share"] = {k: round(v / max(ms, 1e-9), 4) for k, v in shares.items()}
+    if delay > 1 and kt["gather"][1] > 0:
+        # batched mode: per batch and pair, the gather reads W[:, T] through the upper
+        # triangle (N kr b) and writes the U and V^T panels (2 N kr b); the X product
+        # reads and writes V^T (2 N kr b) and does N kr^2 MACs
+        b = 8 if prec == 0 else 4
+        kr = delay * p.r
+        per_b = sum((1 if n == m else 2) * b * p.N * kr for n in range(p.K) for m in range(n, p.K))
+        macs = sum((1 if n == m else 4) * p.N * kr * kr for n in range(p.K) for m in range(n, p.K))
+        n_b = kt["gather"][1]
+        roof["batch_kernels"] = {
+            "batch_gather_gbs": n_b * chains * 3 * per_b / (kt["gather"][0] * 1e-3) / 1e9,
+            "batch_apply_gbs": n_b * chains * 2 * per_b / (kt["apply"][0] * 1e-3) / 1e9,
+            "batch_apply_fp32_tflops": n_b * chains * 2 * macs / (kt["apply"][0] * 1e-3) / 1e12,
+            "note": "kr = delay r is the batch's rank; sizes per launch group over all chains"}
     # |Delta log N|: tracked FP32/FP64 values vs a fresh FP64 factorisation
     fin = ctx.chains_links()
     pick = np.ascontiguousarray(fin[: min(4, chains)])

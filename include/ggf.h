@@ -199,11 +199,17 @@ ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path);
 ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
 
 /* Kernel timing with CUDA events recorded on the launching stream, for
- * benchmarks.  ggf_profile(ctx, 1) starts recording events around every
- * ratio launch (GGF_KT_RATIO), every immediate rank-r update or delayed-mode
- * row/column gather launch group (GGF_KT_UPDATE), every refresh
- * (GGF_KT_REFRESH) and every delayed-update flush (GGF_KT_FLUSH) issued by
- * ggf_sample, and resets the totals; ggf_profile(ctx, 0) stops.
+ * benchmarks.  ggf_profile(ctx, 1) starts recording events around the launch
+ * groups issued by ggf_sample and ggf_sample_blocks and resets the totals;
+ * ggf_profile(ctx, 0) stops.  Categories:
+ *   GGF_KT_RATIO    link-step ratio launches (one link per launch), and the
+ *                   batched link steps on the small matrices (batch_steps)
+ *   GGF_KT_UPDATE   immediate rank-r updates; row/column gathers of the
+ *                   pending-panel path (block moves)
+ *   GGF_KT_REFRESH  full refreshes
+ *   GGF_KT_FLUSH    delayed-update flushes W <- W - U V
+ *   GGF_KT_GATHER   batched mode: W[:, T], W[T, :] and W[T, T] gathers
+ *   GGF_KT_APPLY    batched mode: V <- X V
  * ggf_kernel_time returns the accumulated device milliseconds and the number
  * of timed launch groups since the last reset.  Events are read at the end of
  * each sweep.  While timing is on, sweeps launch eagerly instead of replaying
@@ -212,6 +218,9 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
 #define GGF_KT_UPDATE 1
 #define GGF_KT_REFRESH 2
 #define GGF_KT_FLUSH 3
+#define GGF_KT_GATHER 4
+#define GGF_KT_APPLY 5
+#define GGF_KT_N 6
 ggf_status ggf_profile(ggf_ctx* ctx, int enable);
 ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launches);
 

@@ -767,6 +767,15 @@ ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, in
         else { const float* f = (const float*)h.data(); re = cplx ? f[2 * e] : f[e]; if (cplx) im = f[2 * e + 1]; }
         o[2 * e] = re; o[2 * e + 1] = im;
     }
+    if (ch.kmax > 1) {
+        // delayed and batched modes keep only the upper triangle current
+        const int N = ctx->g.N;
+        for (int i = 1; i < N; ++i)
+            for (int j = 0; j < i; ++j) {
+                o[2 * ((size_t)i * N + j)] = -o[2 * ((size_t)j * N + i)];
+                o[2 * ((size_t)i * N + j) + 1] = -o[2 * ((size_t)j * N + i) + 1];
+            }
+    }
     GGF_CK(cudaMemcpy(out, o.data(), o.size() * sizeof(double), mem == GGF_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
     return GGF_OK;
 }
@@ -869,14 +878,14 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream) {
 ggf_status ggf_profile(ggf_ctx* ctx, int enable) {
     if (!ctx) return GGF_EINVAL;
     ctx->prof = enable != 0;
-    for (int k = 0; k < 4; ++k) { ctx->kt_ms[k] = 0; ctx->kt_n[k] = 0; }
+    for (int k = 0; k < GGF_KT_N; ++k) { ctx->kt_ms[k] = 0; ctx->kt_n[k] = 0; }
     ctx->ev_cat.clear();
     ctx->ev_used = 0;
     return GGF_OK;
 }
 
 ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launches) {
-    if (!ctx || which < 0 || which > 3) return GGF_EINVAL;
+    if (!ctx || which < 0 || which >= GGF_KT_N) return GGF_EINVAL;
     if (ms) *ms = ctx->kt_ms[which];
     if (launches) *launches = ctx->kt_n[which];
     return GGF_OK;

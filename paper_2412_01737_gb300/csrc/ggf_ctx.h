@@ -90,8 +90,8 @@ struct ggf_ctx {
     std::vector<cudaEvent_t> ev;            // event pool
     std::vector<int> ev_cat;                // category of each recorded (start, end) pair
     int ev_used = 0;                        // events recorded this sweep
-    double kt_ms[4] = {0, 0, 0, 0};
-    unsigned long long kt_n[4] = {0, 0, 0, 0};
+    double kt_ms[GGF_KT_N] = {0, 0, 0, 0, 0, 0};
+    unsigned long long kt_n[GGF_KT_N] = {0, 0, 0, 0, 0, 0};
     // record one event (returns its index, or -1 when profiling is off)
     int prof_mark(cudaStream_t st) {
         if (!prof) return -1;

@@ -65,6 +65,29 @@ __device__ T twisted(const DevConst& dc, int pair, int link, int x, int y, doubl
     return v;
 }
 
+// Same element with the twist's cos/sin precomputed: cs[2 j], cs[2 j + 1] =
+// cos, sin of q_j theta for source-end mode j (U(1); unused for Z2).
+template <class T>
+__device__ T twisted_tab(const DevConst& dc, int pair, int link, int x, int y, double gval, const double* cs) {
+    const Geometry& g = dc.g;
+    double cx_ = 1, sx_ = 0, cy_ = 1, sy_ = 0;
+    if (g.group == GGF_U1) {
+        if (x < g.h2) { cx_ = cs[2 * (x >> 1)]; sx_ = cs[2 * (x >> 1) + 1]; }
+        if (y < g.h2) { cy_ = cs[2 * (y >> 1)]; sy_ = cs[2 * (y >> 1) + 1]; }
+    }
+    int a0, a1, b0, b1;
+    double ca0, ca1, cb0, cb1;
+    twist_row(g, x, gval, cx_, sx_, a0, ca0, a1, ca1);
+    twist_row(g, y, gval, cy_, sy_, b0, cb0, b1, cb1);
+    T v = mulc(ca0 * cb0, bond_elem<T>(dc, pair, link, a0, b0));
+    if (cb1 != 0.0) v += mulc(ca0 * cb1, bond_elem<T>(dc, pair, link, a0, b1));
+    if (ca1 != 0.0) {
+        v += mulc(ca1 * cb0, bond_elem<T>(dc, pair, link, a1, b0));
+        if (cb1 != 0.0) v += mulc(ca1 * cb1, bond_elem<T>(dc, pair, link, a1, b1));
+    }
+    return v;
+}
+
 template <class T>
 __device__ __forceinline__ void link_value(const DevConst& dc, const void* links, int cfg, int link,
                                            double& gval, double& theta) {

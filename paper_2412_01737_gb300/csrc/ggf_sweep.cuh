@@ -43,11 +43,15 @@ __device__ cxd warp_pfaffian(cxd* A, int n) {
         cxd piv = A[q * n + k];
         if (piv.x == 0.0 && piv.y == 0.0) { __syncwarp(); return {0.0, 0.0}; }
         res = res * A[k * n + q];
+        const cxd ipiv = cxd{1.0, 0.0} / piv;
         int mm = n - k - 2;
+        // multipliers l_i = A[i][k] / A[q][k], one per row, in column k
+        // (column k is not read again)
+        if (lane < mm) A[(k + 2 + lane) * n + k] = A[(k + 2 + lane) * n + k] * ipiv;
+        __syncwarp();
         for (int e = lane; e < mm * mm; e += 32) {
             int i = k + 2 + e / mm, j = k + 2 + e % mm;
-            cxd ti = A[i * n + k] / piv, tj = A[j * n + k] / piv;
-            A[i * n + j] += ti * A[j * n + q] - A[i * n + q] * tj;
+            A[i * n + j] += A[i * n + k] * A[j * n + q] - A[i * n + q] * A[j * n + k];
         }
         __syncwarp();
     }
@@ -103,6 +107,15 @@ template <> __device__ __forceinline__ void PanelIO<float>::st(float* p, size_t,
 template <> __device__ __forceinline__ void PanelIO<cxd>::st(double* p, size_t pl, size_t i, cxd v) { p[i] = v.x; p[pl + i] = v.y; }
 template <> __device__ __forceinline__ void PanelIO<cxf>::st(float* p, size_t pl, size_t i, cxf v) { p[i] = v.x; p[pl + i] = v.y; }
 
+// Element (i, j) of a chain's cached inverse W = M^{-1} (row-major N x N).
+// M is antisymmetric, so W is too; in the delayed and batched modes only the
+// upper triangle (i <= j) is kept current, and the lower entries are read as
+// -W[j][i].
+template <class T>
+__device__ __forceinline__ T w_upper(const T* W, int N, int i, int j) {
+    return i <= j ? W[(size_t)i * N + j] : -W[(size_t)j * N + i];
+}
+
 // Majorana offsets of the two ends of link l = 2 s + d: the source end (+d
 // end of site s, which carries the twist) and the target end (-d end of the
 // neighbour t).  Majorana xi < h2 of the link is a0 + xi, the others b0 + xi - h2.
@@ -146,19 +159,35 @@ __device__ __forceinline__ Proposal draw_proposal(const Geometry& g, const void*
 
 // Change of pair p's twisted link block, Delta = O' G O'^T - O G O^T on the
 // r Majoranas of link l (r x r, one warp).
-__device__ __forceinline__ void pair_delta(const DevConst& dc, int p, int l, const Proposal& q, cxd* D) {
+// cs: cos, sin of q_j theta for the old angle (cs[0 .. 2 n_v)) and the new
+// one (cs[4 ..]), from twist_table.
+__device__ __forceinline__ void pair_delta(const DevConst& dc, int p, int l, const Proposal& q, const double* cs,
+                                           cxd* D) {
     const int r = dc.g.r, lane = threadIdx.x & 31;
     for (int e = lane; e < r * r; e += 32) {
         int xi = e / r, yi = e % r;
         cxd nv, ov;
         if (p < dc.K) {
-            nv = {twisted<double>(dc, p, l, xi, yi, q.g_new, q.th_new), 0.0};
-            ov = {twisted<double>(dc, p, l, xi, yi, q.g_old, q.th_old), 0.0};
+            nv = {twisted_tab<double>(dc, p, l, xi, yi, q.g_new, cs + 4), 0.0};
+            ov = {twisted_tab<double>(dc, p, l, xi, yi, q.g_old, cs), 0.0};
         } else {
-            nv = twisted<cxd>(dc, p - dc.K, l, xi, yi, q.g_new, q.th_new);
-            ov = twisted<cxd>(dc, p - dc.K, l, xi, yi, q.g_old, q.th_old);
+            nv = twisted_tab<cxd>(dc, p - dc.K, l, xi, yi, q.g_new, cs + 4);
+            ov = twisted_tab<cxd>(dc, p - dc.K, l, xi, yi, q.g_old, cs);
         }
         D[e] = nv - ov;
+    }
+}
+
+// cos, sin of q_j theta for the old and the new angle of a U(1) proposal
+// (threads 0 .. 2 n_v - 1 of the block; cs holds 8 doubles).
+__device__ __forceinline__ void twist_table(const Geometry& g, const Proposal& q, double* cs) {
+    const int t = threadIdx.x;
+    if (g.group == GGF_U1 && t < 2 * g.n_v) {
+        const int j = t % g.n_v, nw = t / g.n_v;
+        double sv, cv;
+        sincos(g.q[j] * (nw ? q.th_new : q.th_old), &sv, &cv);
+        cs[4 * nw + 2 * j] = cv;
+        cs[4 * nw + 2 * j + 1] = sv;
     }
 }
 

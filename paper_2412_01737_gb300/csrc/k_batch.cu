@@ -8,7 +8,8 @@
 // j r + xi of T is Majorana xi of link l0 + j).  Every proposal of the batch
 // needs only the block of the current inverse on T.  With W the inverse at
 // the start of the batch, C = W[:, T], Y = W[T, :], G0 = W[T, T]:
-//   batch_gather  C -> U panel, Y^T -> V^T panel, G := G0, X := 0
+//   batch_gather  C -> U panel, Y^T -> V^T panel, G := G0, X := 0 (read
+//                 through the upper triangle of W, so C = -Y^T exactly)
 //   batch_steps   one CTA per chain runs the kb link steps on the small
 //                 matrices: ratio from G[S_j, S_j], decision, and on accept,
 //                 with Z = (1 + Delta G[S, S])^{-1} Delta,
@@ -19,7 +20,8 @@
 //                 (each step is the rank-r update W' = W - W[:, S] Z W[S, :]
 //                 with W[:, S] = C P and W[S, :] = Q Y).
 //   batch_apply   V^T <- V^T X^T  (V = X Y)
-// followed by the flush W <- W - U V (tcgen05 tensor cores for FP32 chains).
+// followed by the flush W <- W - U V on the upper triangle (tcgen05 tensor
+// cores for FP32 chains).
 // Per batch and pair this reads C and Y once (2 N kb r elements) instead of
 // two N-long panel products per accepted link, and folds kb links into one
 // pass over W.
@@ -52,31 +54,31 @@ __global__ void __launch_bounds__(256) batch_gather(Geometry g, int l0, int kb, 
     RR* Vt = U + PanelIO<T>::PLANES * NK;
     T* Gm = Sm + base * 2 * KRM * KRM;
     T* Xm = Gm + (size_t)KRM * KRM;
-    // V^T rows: tile[ii][q] = W[T_q][i0 + ii], read along rows of W
+    // Only the upper triangle of W is current (W is antisymmetric): with
+    // y = W[T_q][i] = -W[i][T_q], V^T[i][q] = y and U[i][q] = -y.
+    // Entries with T_q <= i come from row T_q of W, read along i:
     for (int e = threadIdx.x; e < kr * BR; e += blockDim.x) {
         int q = e / BR, ii = e - q * BR;
-        tile[ii * ld + q] = ii < nb ? Wp[(size_t)Tl[q] * N + i0 + ii] : Sc<T>::zero();
+        if (ii < nb && Tl[q] <= i0 + ii) tile[ii * ld + q] = Wp[(size_t)Tl[q] * N + i0 + ii];
+    }
+    // the others from column T_q, read along the rows i of the block:
+    for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
+        int ii = e / kr, q = e - ii * kr;
+        if (Tl[q] > i0 + ii) tile[ii * ld + q] = -Wp[(size_t)(i0 + ii) * N + Tl[q]];
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
         int ii = e / kr, q = e - ii * kr;
-        PanelIO<T>::st(Vt, NK, (size_t)(i0 + ii) * KRM + q, tile[ii * ld + q]);
+        const T y = tile[ii * ld + q];
+        PanelIO<T>::st(Vt, NK, (size_t)(i0 + ii) * KRM + q, y);
+        PanelIO<T>::st(U, NK, (size_t)(i0 + ii) * KRM + q, -y);
     }
-    __syncthreads();
-    // U rows: W[i0 + ii][T_q]
-    for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
-        int ii = e / kr, q = e - ii * kr;
-        T v = Wp[(size_t)(i0 + ii) * N + Tl[q]];
-        tile[ii * ld + q] = v;
-        PanelIO<T>::st(U, NK, (size_t)(i0 + ii) * KRM + q, v);
-    }
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int a = warp; a < kr; a += nw) {
         const int ii = Tl[a] - i0;
         if (ii < 0 || ii >= nb) continue;
         for (int q = lane; q < kr; q += 32) {
-            Gm[(size_t)a * KRM + q] = tile[ii * ld + q];
+            Gm[(size_t)a * KRM + q] = -tile[ii * ld + q];   // W[T_a][T_q] = U[T_a][q]
             Xm[(size_t)a * KRM + q] = Sc<T>::zero();
         }
     }
@@ -104,9 +106,9 @@ struct BatchArgs {
 // Rank-r update of one pair's small matrices after link j of the batch was
 // accepted (all threads of the CTA).  Gm, Xm: KRM x KRM; U: the pair's U
 // panel (planes of N x KRM); Z: r x r (FP64); st: 4 KRM r scratch scalars.
-template <class T>
-__device__ void small_update(T* Gm, T* Xm, const typename Sc<T>::R* U, size_t NK, const int* Tl, int j, int kb,
-                             int r, int KRM, const cxd* Z, T* st) {
+template <class T, int r>
+__device__ __forceinline__ void small_update(T* Gm, T* Xm, const typename Sc<T>::R* U, size_t NK, const int* Tl,
+                                             int j, int kb, int KRM, const cxd* Z, T* st) {
     const int jr = j * r, m = jr + r, kr = kb * r, nf = kr - m;
     T* A1 = st;                    // G[F, S] Z, later G0[0:jr, S], later P Z
     T* A2 = A1 + (size_t)KRM * r;  // G[S, F], later G0[S, 0:jr]
@@ -141,25 +143,39 @@ __device__ void small_update(T* Gm, T* Xm, const typename Sc<T>::R* U, size_t NK
         A2[b * jr + a] = PanelIO<T>::ld(U, NK, (size_t)Tl[jr + b] * KRM + a);   // G0[S_b][a]
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
-        int a = e / r, b = e - a * r;
-        T acc = Sc<T>::zero();
+    // P (m x r): rows a < jr are -X[a, 0:jr] G0[0:jr, S], rows jr.. the identity;
+    // Q (r x m): columns cc < jr are -G0[S, 0:jr] X[0:jr, cc], then the identity.
+    // One thread per row a of P (resp. column cc of Q) keeps its r outputs in
+    // registers, so every element of X is loaded once per product.
+    const T one = Sc<T>::from(cxd{1.0, 0.0});
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+        T acc[r];
+#pragma unroll
+        for (int b = 0; b < r; ++b) acc[b] = Sc<T>::zero();
         if (a < jr) {
-            for (int q = 0; q < jr; ++q) acc -= Xm[(size_t)a * KRM + q] * A1[q * r + b];
-        } else if (a - jr == b) {
-            acc = Sc<T>::from(cxd{1.0, 0.0});
+            const T* xr = Xm + (size_t)a * KRM;
+            for (int q = 0; q < jr; ++q) {
+                const T x = xr[q];
+#pragma unroll
+                for (int b = 0; b < r; ++b) acc[b] -= x * A1[q * r + b];
+            }
         }
-        A3[e] = acc;
+#pragma unroll
+        for (int b = 0; b < r; ++b) A3[a * r + b] = (a >= jr && b == a - jr) ? one : acc[b];
     }
-    for (int e = threadIdx.x; e < r * m; e += blockDim.x) {
-        int b = e / m, cc = e - b * m;
-        T acc = Sc<T>::zero();
+    for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
+        T acc[r];
+#pragma unroll
+        for (int b = 0; b < r; ++b) acc[b] = Sc<T>::zero();
         if (cc < jr) {
-            for (int q = 0; q < jr; ++q) acc -= A2[b * jr + q] * Xm[(size_t)q * KRM + cc];
-        } else if (cc - jr == b) {
-            acc = Sc<T>::from(cxd{1.0, 0.0});
+            for (int q = 0; q < jr; ++q) {
+                const T x = Xm[(size_t)q * KRM + cc];
+#pragma unroll
+                for (int b = 0; b < r; ++b) acc[b] -= A2[b * jr + q] * x;
+            }
         }
-        A4[e] = acc;
+#pragma unroll
+        for (int b = 0; b < r; ++b) A4[b * m + cc] = (cc >= jr && b == cc - jr) ? one : acc[b];
     }
     __syncthreads();
     for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
@@ -181,7 +197,7 @@ __device__ void small_update(T* Gm, T* Xm, const typename Sc<T>::R* U, size_t NK
 
 // One CTA (NWARP warps) per chain runs the batch's kb link steps in order.
 template <class RW, class CW>
-__global__ void __launch_bounds__(NWARP * 32) batch_steps(BatchArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
     extern __shared__ cxd sm[];
     const Geometry& g = a.dc.g;
     const int P = a.dc.P, K = a.dc.K, Kc = P - K, r = g.r, N = g.N, KRM = a.KRM;
@@ -200,6 +216,7 @@ __global__ void __launch_bounds__(NWARP * 32) batch_steps(BatchArgs a) {
     cxd* Zs = sm + front;                  // [P][r][r]
     int* Tl = (int*)(Zs + P * r * r);      // [kb r]
     __shared__ Proposal s_q;
+    __shared__ double s_cs[8];
     __shared__ int s_accept, s_any;
     typedef typename Sc<RW>::R RR;
     const size_t NK = (size_t)N * KRM, SS = (size_t)KRM * KRM;
@@ -218,10 +235,12 @@ __global__ void __launch_bounds__(NWARP * 32) batch_steps(BatchArgs a) {
         if (threadIdx.x == 0) s_q = draw_proposal(g, a.links, c, l, sweep, a.seed, a.width);
         __syncthreads();
         const Proposal q = s_q;
+        twist_table(g, q, s_cs);
+        __syncthreads();
         for (int p = warp; p < P; p += NWARP) {
             cxd* D = Delta + p * r * r;
             cxd* Ws = Wss + p * r * r;
-            pair_delta(a.dc, p, l, q, D);
+            pair_delta(a.dc, p, l, q, s_cs, D);
             for (int e = lane; e < r * r; e += 32) {
                 const size_t off = (size_t)(jr + e / r) * KRM + jr + e % r;
                 if (p < K) Ws[e] = loadc((const RW*)a.Sr + ((size_t)c * K + p) * 2 * SS + off);
@@ -259,12 +278,14 @@ __global__ void __launch_bounds__(NWARP * 32) batch_steps(BatchArgs a) {
         for (int p = 0; p < K; ++p) {
             RW* Gm = (RW*)a.Sr + ((size_t)c * K + p) * 2 * SS;
             const RR* U = (const RR*)a.Pr + ((size_t)c * K + p) * 2 * PanelIO<RW>::PLANES * NK;
-            small_update<RW>(Gm, Gm + SS, U, NK, Tl, j, a.kb, r, KRM, Zs + p * r * r, (RW*)sm);
+            if (r == 4) small_update<RW, 4>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + p * r * r, (RW*)sm);
+            else small_update<RW, 8>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + p * r * r, (RW*)sm);
         }
         for (int p = 0; p < Kc; ++p) {
             CW* Gm = (CW*)a.Sc_ + ((size_t)c * Kc + p) * 2 * SS;
             const RR* U = (const RR*)a.Pc + ((size_t)c * Kc + p) * 2 * PanelIO<CW>::PLANES * NK;
-            small_update<CW>(Gm, Gm + SS, U, NK, Tl, j, a.kb, r, KRM, Zs + (K + p) * r * r, (CW*)sm);
+            if (r == 4) small_update<CW, 4>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + (K + p) * r * r, (CW*)sm);
+            else small_update<CW, 8>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + (K + p) * r * r, (CW*)sm);
         }
     }
     if (threadIdx.x == 0) a.pend[c] = s_any ? a.kb : 0;
@@ -277,56 +298,75 @@ size_t steps_smem(int P, int r, int KRM, size_t cw_bytes) {
 }
 
 // ---- V^T <- V^T X^T -----------------------------------------------------------
-// Grid (ceil(N / 32), family pairs, chains), 256 threads; a CTA stages its 32
-// rows of V^T in shared memory and rewrites them in place.  Thread (ii, ag)
-// computes row ii's outputs ag*8 .. ag*8+7 of each 64-wide output chunk.
-template <class T>
+// Grid (ceil(N / RB), family pairs, chains) with RB = 16 RPT rows per CTA,
+// 256 threads as 16 x 16.  A CTA stages its RB rows of V^T in shared memory
+// and rewrites them in place; per 128-wide output chunk, thread (ty, tx)
+// accumulates rows ty RPT .. + RPT - 1 x outputs tx 8 .. tx 8 + 7 over the
+// rank, with X^T staged 16 columns at a time.
+constexpr int AP_LDX = 132;   // X^T stage row length (128 outputs + pad, 16-byte rows)
+
+template <class T, int RPT>
 __global__ void __launch_bounds__(256) batch_apply(int N, int fam_pairs, int KRM, int kr, typename Sc<T>::R* Pan,
                                                    const T* Sm, const int* pend) {
     typedef typename Sc<T>::R RR;
+    constexpr int RB = 16 * RPT;
     const int c = blockIdx.z;
     if (pend[c] == 0) return;
     const int p = blockIdx.y;
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int ld = kr + 1;
-    T* Vs = (T*)smraw;          // [32][kr + 1]
-    T* Xs = Vs + 32 * ld;       // [64][17]
+    T* Xs = (T*)smraw;           // [16][AP_LDX]  X^T chunk: Xs[bb][aa] = X[a0 + aa][b0 + bb]
+    T* Vs = Xs + 16 * AP_LDX;    // [RB][kr + 1]
     const size_t NK = (size_t)N * KRM, base = (size_t)c * fam_pairs + p;
     RR* Vt = Pan + base * 2 * PanelIO<T>::PLANES * NK + PanelIO<T>::PLANES * NK;
     const T* Xm = Sm + base * 2 * KRM * KRM + (size_t)KRM * KRM;
-    const int i0 = blockIdx.x * 32, nb = min(32, N - i0);
-    for (int e = threadIdx.x; e < 32 * kr; e += blockDim.x) {
+    const int i0 = blockIdx.x * RB, nb = min(RB, N - i0);
+    for (int e = threadIdx.x; e < RB * kr; e += blockDim.x) {
         int ii = e / kr, q = e - ii * kr;
         Vs[ii * ld + q] = ii < nb ? PanelIO<T>::ld(Vt, NK, (size_t)(i0 + ii) * KRM + q) : Sc<T>::zero();
     }
-    const int ii = threadIdx.x & 31, ag = threadIdx.x >> 5;
-    for (int a0 = 0; a0 < kr; a0 += 64) {
-        T acc[8];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int a0 = 0; a0 < kr; a0 += 128) {
+        T acc[RPT][8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = Sc<T>::zero();
+        for (int u = 0; u < RPT; ++u)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc[u][t] = Sc<T>::zero();
         for (int b0 = 0; b0 < kr; b0 += 16) {
             __syncthreads();
-            for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+            for (int e = threadIdx.x; e < 128 * 16; e += blockDim.x) {
                 int aa = e >> 4, bb = e & 15;
-                Xs[aa * 17 + bb] = (a0 + aa < kr && b0 + bb < kr) ? Xm[(size_t)(a0 + aa) * KRM + b0 + bb] : Sc<T>::zero();
+                Xs[bb * AP_LDX + aa] =
+                    (a0 + aa < kr && b0 + bb < kr) ? Xm[(size_t)(a0 + aa) * KRM + b0 + bb] : Sc<T>::zero();
             }
             __syncthreads();
             const int bn = min(16, kr - b0);
             for (int bb = 0; bb < bn; ++bb) {
-                const T v = Vs[ii * ld + b0 + bb];
+                T v[RPT], x[8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc[t] += v * Xs[(ag * 8 + t) * 17 + bb];
+                for (int u = 0; u < RPT; ++u) v[u] = Vs[(ty * RPT + u) * ld + b0 + bb];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) x[t] = Xs[bb * AP_LDX + tx * 8 + t];
+#pragma unroll
+                for (int u = 0; u < RPT; ++u)
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) acc[u][t] += v[u] * x[t];
             }
         }
-        if (ii < nb) {
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int ii = ty * RPT + u;
+            if (ii >= nb) continue;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const int aa = a0 + ag * 8 + t;
-                if (aa < kr) PanelIO<T>::st(Vt, NK, (size_t)(i0 + ii) * KRM + aa, acc[t]);
+                const int aa = a0 + tx * 8 + t;
+                if (aa < kr) PanelIO<T>::st(Vt, NK, (size_t)(i0 + ii) * KRM + aa, acc[u][t]);
             }
         }
     }
 }
+
+size_t apply_smem(int RPT, int kr, size_t tb) { return (16 * AP_LDX + (size_t)16 * RPT * (kr + 1)) * tb; }
 
 int gather_rows(int kr, size_t tb) {
     int br = 32;
@@ -357,10 +397,14 @@ ggf_status ggf_prepare_batch(ggf_ctx* ctx) {
     GGF_TRY(cap((const void*)batch_gather<cxf>));
     GGF_TRY(cap((const void*)batch_steps<double, cxd>));
     GGF_TRY(cap((const void*)batch_steps<float, cxf>));
-    GGF_TRY(cap((const void*)batch_apply<double>));
-    GGF_TRY(cap((const void*)batch_apply<float>));
-    GGF_TRY(cap((const void*)batch_apply<cxd>));
-    GGF_TRY(cap((const void*)batch_apply<cxf>));
+    GGF_TRY(cap((const void*)batch_apply<double, 4>));
+    GGF_TRY(cap((const void*)batch_apply<float, 4>));
+    GGF_TRY(cap((const void*)batch_apply<cxd, 4>));
+    GGF_TRY(cap((const void*)batch_apply<cxf, 4>));
+    GGF_TRY(cap((const void*)batch_apply<double, 2>));
+    GGF_TRY(cap((const void*)batch_apply<float, 2>));
+    GGF_TRY(cap((const void*)batch_apply<cxd, 2>));
+    GGF_TRY(cap((const void*)batch_apply<cxf, 2>));
     if (ctx->device >= 0 && ctx->device < 64) done[ctx->device] = true;
     return GGF_OK;
 }
@@ -373,7 +417,7 @@ ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64) {
     const int r = ctx->g.r, KRM = kmax * r;
     const size_t cw = fp64 ? sizeof(cxd) : sizeof(cxf);
     const size_t need_steps = steps_smem(ctx->P, r, KRM, cw) + 1024;
-    const size_t need_apply = (32 * (size_t)(KRM + 1) + 64 * 17) * cw + 1024;
+    const size_t need_apply = apply_smem(2, KRM, cw) + 1024;
     if (need_steps > (size_t)mx || need_apply > (size_t)mx)
         return ggf_fail(ctx, GGF_EINVAL, "delay too large: batch kernels need more shared memory than the device has");
     return GGF_OK;
@@ -411,7 +455,7 @@ ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st) {
         GGF_CK(cudaGetLastError());
     }
     const int ev1 = ctx->prof_mark(st);
-    ctx->prof_pair(GGF_KT_UPDATE, ev0, ev1);
+    ctx->prof_pair(GGF_KT_GATHER, ev0, ev1);
     {
         BatchArgs a;
         a.dc = ctx->dc();
@@ -439,18 +483,30 @@ ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st) {
     const int ev2 = ctx->prof_mark(st);
     ctx->prof_pair(GGF_KT_RATIO, ev1, ev2);
     {
-        dim3 gr((N + 31) / 32, ctx->K, ch.n), gc((N + 31) / 32, ctx->Kc, ch.n);
-        const size_t sr = (32 * (size_t)(kr + 1) + 64 * 17) * rsz, sc = 2 * sr;
+        int mx = 0;
+        GGF_CK(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        // 64-row blocks where they fit in shared memory, else 32
+        const int rpt_r = apply_smem(4, kr, rsz) + 1024 <= (size_t)mx ? 4 : 2;
+        const int rpt_c = apply_smem(4, kr, 2 * rsz) + 1024 <= (size_t)mx ? 4 : 2;
+        dim3 gr((N + 16 * rpt_r - 1) / (16 * rpt_r), ctx->K, ch.n), gc((N + 16 * rpt_c - 1) / (16 * rpt_c), ctx->Kc, ch.n);
+        const size_t sr = apply_smem(rpt_r, kr, rsz), sc = apply_smem(rpt_c, kr, 2 * rsz);
+#define GGF_APPLY(T, RPT, grid, smem, fam, Pp, Sp) \
+    batch_apply<T, RPT><<<grid, 256, smem, st>>>(N, fam, KRM, kr, (typename Sc<T>::R*)(Pp), (const T*)(Sp), ch.pend)
         if (fp64) {
-            batch_apply<double><<<gr, 256, sr, st>>>(N, ctx->K, KRM, kr, (double*)ch.Pr, (const double*)Sr, ch.pend);
-            if (ctx->Kc) batch_apply<cxd><<<gc, 256, sc, st>>>(N, ctx->Kc, KRM, kr, (double*)ch.Pc, (const cxd*)Sc_, ch.pend);
+            if (rpt_r == 4) GGF_APPLY(double, 4, gr, sr, ctx->K, ch.Pr, Sr); else GGF_APPLY(double, 2, gr, sr, ctx->K, ch.Pr, Sr);
+            if (ctx->Kc) {
+                if (rpt_c == 4) GGF_APPLY(cxd, 4, gc, sc, ctx->Kc, ch.Pc, Sc_); else GGF_APPLY(cxd, 2, gc, sc, ctx->Kc, ch.Pc, Sc_);
+            }
         } else {
-            batch_apply<float><<<gr, 256, sr, st>>>(N, ctx->K, KRM, kr, (float*)ch.Pr, (const float*)Sr, ch.pend);
-            if (ctx->Kc) batch_apply<cxf><<<gc, 256, sc, st>>>(N, ctx->Kc, KRM, kr, (float*)ch.Pc, (const cxf*)Sc_, ch.pend);
+            if (rpt_r == 4) GGF_APPLY(float, 4, gr, sr, ctx->K, ch.Pr, Sr); else GGF_APPLY(float, 2, gr, sr, ctx->K, ch.Pr, Sr);
+            if (ctx->Kc) {
+                if (rpt_c == 4) GGF_APPLY(cxf, 4, gc, sc, ctx->Kc, ch.Pc, Sc_); else GGF_APPLY(cxf, 2, gc, sc, ctx->Kc, ch.Pc, Sc_);
+            }
         }
+#undef GGF_APPLY
         GGF_CK(cudaGetLastError());
     }
-    ctx->prof_pair(GGF_KT_UPDATE, ev2, ctx->prof_mark(st));
+    ctx->prof_pair(GGF_KT_APPLY, ev2, ctx->prof_mark(st));
     ctx->launches += 1 + 2 * (1 + (ctx->Kc ? 1 : 0));
     ch.steps_since_flush = kb;
     return ggf_flush(ctx, st);

@@ -1,7 +1,9 @@
 // Delayed-update flush on the sm_103a tensor cores (tcgen05 + TMEM).
 //
 // For FP32 chains, folds the pending rank-K panels into the cached inverse:
-// W <- W - U V, with U (N x K) and V^T (N x K) stored K-major (rank index
+// W <- W - U V on the tiles that touch the upper triangle (W is
+// antisymmetric; the sampler keeps only i <= j current), with U (N x K) and
+// V^T (N x K) stored K-major (rank index
 // contiguous, row stride KRM), complex pairs as separate real/imaginary
 // planes.  FP32 accuracy from TF32 tensor cores by the three-product split
 // x = hi + lo, hi = rna_tf32(x):  a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
@@ -131,7 +133,7 @@ struct TileInfo {
 
 template <int ROWS>
 __device__ __forceinline__ TileInfo decode_tile(long long tile, int tiles_i, int tiles_j, int fam_pairs,
-                                                const int* pend, int R) {
+                                                const int* pend, int R, int upper) {
     TileInfo t;
     long long rest = tile;
     const int tj = (int)(rest % tiles_j);
@@ -142,7 +144,8 @@ __device__ __forceinline__ TileInfo decode_tile(long long tile, int tiles_i, int
     t.c = (int)(rest / fam_pairs);
     t.i0 = ti * ROWS;
     t.j0 = tj * 128;
-    t.K = pend[t.c] * R;
+    // upper != 0: tiles strictly below the diagonal are skipped (no work)
+    t.K = (upper && t.i0 > t.j0 + 127) ? 0 : pend[t.c] * R;
     return t;
 }
 
@@ -183,7 +186,7 @@ __device__ __forceinline__ void produce_plane(const float* src, int KRM, int row
 template <bool CPLX>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, const int* pend, int R, int KRM,
-                int* err) {
+                int upper, int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_accf[2], bar_acce[2], bar_done;
     __shared__ uint32_t tmem_slot;
@@ -225,7 +228,7 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
         int st = 0;
         uint32_t ph = 0;
         for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
-            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R);
+            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
             if (t.K == 0) continue;
             const size_t blk = ((size_t)t.c * fam_pairs + t.p) * (CPLX ? 4 : 2) * NK;
             const float* U0 = Pan + blk;                         // U (re)
@@ -259,7 +262,7 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
         int b = 0;
         uint32_t ph = 0;
         for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
-            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R);
+            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
             if (t.K == 0) continue;
             if (!mbar_wait_bounded(smem_u32(&bar_accf[b]), ph, &s_fail)) { raise_fail(&s_fail, err); break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -339,7 +342,7 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
         uint32_t ph = 0, bph = 0;
         constexpr uint32_t id = idesc_tf32(128, 256);
         for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
-            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R);
+            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
             if (t.K == 0) continue;
             if (!mbar_wait_bounded(smem_u32(&bar_acce[b]), bph ^ 1u, &s_fail)) { raise_fail(&s_fail, err); break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -404,7 +407,7 @@ ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx) {
 namespace {
 
 ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_chains, float* W, const float* Pan,
-                           const int* pend, int R, int KRM, int* err, cudaStream_t st) {
+                           const int* pend, int R, int KRM, bool upper, int* err, cudaStream_t st) {
     if (fam_pairs == 0 || n_chains == 0) return GGF_OK;
     if (KRM % 4) return ggf_fail(ctx, GGF_EINVAL, "tensor-core flush: panel row stride must be a multiple of 4");
     const int rows = cplx ? 128 : 256;
@@ -414,10 +417,10 @@ ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_
     GGF_TRY(ggf_prepare_flush_tc(ctx));
     if (cplx) {
         flush_tc_kernel<true><<<(unsigned)grid, TC_THREADS, smem_bytes(true), st>>>(N, fam_pairs, n_chains, W, Pan,
-                                                                                    pend, R, KRM, err);
+                                                                                    pend, R, KRM, upper ? 1 : 0, err);
     } else {
         flush_tc_kernel<false><<<(unsigned)grid, TC_THREADS, smem_bytes(false), st>>>(N, fam_pairs, n_chains, W, Pan,
-                                                                                      pend, R, KRM, err);
+                                                                                      pend, R, KRM, upper ? 1 : 0, err);
     }
     GGF_CK(cudaGetLastError());
     return GGF_OK;
@@ -474,9 +477,9 @@ ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st) {
     const Geometry& g = ctx->g;
     const int KRM = ch.kmax * g.r;
     GGF_TRY(launch_flush_tc(ctx, false, g.N, ctx->K, ch.n, (float*)ch.Wr, (const float*)ch.Pr, ch.pend, g.r, KRM,
-                            ctx->d_err, st));
+                            true, ctx->d_err, st));
     GGF_TRY(launch_flush_tc(ctx, true, g.N, ctx->Kc, ch.n, (float*)ch.Wc, (const float*)ch.Pc, ch.pend, g.r, KRM,
-                            ctx->d_err, st));
+                            true, ctx->d_err, st));
     return GGF_OK;
 }
 
@@ -511,7 +514,7 @@ extern "C" ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank
     st_fill<<<(unsigned)((nW + 255) / 256), 256>>>(W, nW, 1, 1.0f);
     st_fill<<<(unsigned)((nP + 255) / 256), 256>>>(Pan, nP, 2, 0.3f);
     st_reference<<<(unsigned)((nW + 255) / 256), 256>>>(cplx != 0, N, rank, KRM, W, Pan, ref);
-    rc = launch_flush_tc(ctx, cplx != 0, N, 1, 1, W, Pan, pend, R, KRM, ctx->d_err, 0);
+    rc = launch_flush_tc(ctx, cplx != 0, N, 1, 1, W, Pan, pend, R, KRM, false, ctx->d_err, 0);
     if (rc == GGF_OK) {
         st_maxerr<<<(unsigned)((nW + 255) / 256), 256>>>(nW, W, ref, mx);
         unsigned long long h[2] = {0, 0};

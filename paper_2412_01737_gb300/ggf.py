@@ -17,7 +17,7 @@ FP64, FP32 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 N_OBS = 3
 OBS_PLAQUETTE = 0
-KT_RATIO, KT_UPDATE, KT_REFRESH, KT_FLUSH = 0, 1, 2, 3
+KT_RATIO, KT_UPDATE, KT_REFRESH, KT_FLUSH, KT_GATHER, KT_APPLY = 0, 1, 2, 3, 4, 5
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libggf.so")
