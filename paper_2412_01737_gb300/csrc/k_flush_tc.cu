@@ -20,7 +20,9 @@
 // holds re(D^T) in TMEM columns 0..127 and im(D^T) in 128..255.
 //
 // One persistent CTA per SM, warp-specialised:
-//   warps 0-3   producers: load an 8-wide rank chunk of the operands (float4),
+//   warps 0-3   producers: load an 8-wide rank chunk of the operands
+//               (float4; the next stage's loads are issued before the
+//               current stage is written, so two stages are in flight),
 //               split into tf32 hi/lo and write them in the no-swizzle
 //               K-major core-matrix layout (8 rows x 16 B core matrices,
 //               LBO = 128 B along K, SBO = 256 B between 8-row groups) into a
@@ -44,6 +46,7 @@ constexpr int KC = 8;                         // rank columns per stage (one MMA
 constexpr int SBO = KC / 4 * 128;             // bytes between 8-row core-matrix groups
 constexpr int STAGES = 4;
 constexpr int NPROD = 4, NEPI = 8;            // producer and epilogue warps (+ one MMA warp)
+constexpr int PGROUP = NPROD * 32;
 constexpr int TC_THREADS = (NPROD + NEPI + 1) * 32;
 constexpr int MMA_WARP = NPROD + NEPI;
 constexpr int PLANE_A = 128 * KC * 4;         // 4 KB: 128 rows x 8 tf32
@@ -149,37 +152,78 @@ __device__ __forceinline__ TileInfo decode_tile(long long tile, int tiles_i, int
     return t;
 }
 
-// Load rows row0 .. row0 + NR - 1, rank columns k0 .. k0 + 7 of one plane
-// (float4 per thread, all loads issued before any store), split, and write
-// hi/lo at core-matrix row offset dst_row (sign -1 negates).
+// One stage's operands in the producer threads' registers: rank columns
+// k0 .. k0 + 7 of the tile's planes, float4 per (row, half of the chunk).
+// Real: V^T rows j0.. (2 per thread), U rows i0.. (4); complex: V_r, V_i,
+// U_r, U_i rows (2 each).
+struct StageRegs {
+    float4 v[8];
+};
+
 template <int NR>
-__device__ __forceinline__ void produce_plane(const float* src, int KRM, int row0, int N, int k0, int K,
-                                              unsigned char* hi, unsigned char* lo, int dst_row, float sign,
-                                              unsigned char* hi2 = nullptr, unsigned char* lo2 = nullptr,
-                                              int dst_row2 = 0) {
-    constexpr int PER = NR * 2 / (NPROD * 32);
-    const int t0 = threadIdx.x;
-    float4 v[PER];
+__device__ __forceinline__ void load_plane(const float* src, int KRM, int row0, int N, int k0, int K, float4* v) {
+    constexpr int PER = NR * 2 / PGROUP;
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-        const int idx = t0 + t * NPROD * 32, row = idx >> 1, k = k0 + 4 * (idx & 1);
+        const int idx = (int)threadIdx.x + t * PGROUP, row = idx >> 1, k = k0 + 4 * (idx & 1);
         const int gr = row0 + row;
         v[t] = (gr < N && k < K) ? __ldg((const float4*)(src + (size_t)gr * KRM + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+}
+
+// Split loaded values into tf32 hi/lo and write them at core-matrix row
+// offset dst_row (and negated at dst_row2 when hi2 is given).
+template <int NR>
+__device__ __forceinline__ void store_plane(const float4* v, unsigned char* hi, unsigned char* lo, int dst_row,
+                                            unsigned char* hi2 = nullptr, unsigned char* lo2 = nullptr,
+                                            int dst_row2 = 0) {
+    constexpr int PER = NR * 2 / PGROUP;
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-        const int idx = t0 + t * NPROD * 32, row = idx >> 1, kq = 4 * (idx & 1);
+        const int idx = (int)threadIdx.x + t * PGROUP, row = idx >> 1, kq = 4 * (idx & 1);
         const float4 x = v[t];
         const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
         const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
         const uint32_t o = cm_off(dst_row + row, kq);
-        *(float4*)(hi + o) = make_float4(sign * h.x, sign * h.y, sign * h.z, sign * h.w);
-        *(float4*)(lo + o) = make_float4(sign * l.x, sign * l.y, sign * l.z, sign * l.w);
+        *(float4*)(hi + o) = h;
+        *(float4*)(lo + o) = l;
         if (hi2) {
             const uint32_t o2 = cm_off(dst_row2 + row, kq);
-            *(float4*)(hi2 + o2) = make_float4(-sign * h.x, -sign * h.y, -sign * h.z, -sign * h.w);
-            *(float4*)(lo2 + o2) = make_float4(-sign * l.x, -sign * l.y, -sign * l.z, -sign * l.w);
+            *(float4*)(hi2 + o2) = make_float4(-h.x, -h.y, -h.z, -h.w);
+            *(float4*)(lo2 + o2) = make_float4(-l.x, -l.y, -l.z, -l.w);
         }
+    }
+}
+
+template <bool CPLX>
+__device__ __forceinline__ void load_stage(const float* Pan, size_t NK, int fam_pairs, int KRM, int N,
+                                           const TileInfo& t, int k0, StageRegs& r) {
+    const size_t blk = ((size_t)t.c * fam_pairs + t.p) * (CPLX ? 4 : 2) * NK;
+    const float* U0 = Pan + blk;                         // U (re)
+    const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;   // V^T (re)
+    if (!CPLX) {
+        load_plane<128>(V0, KRM, t.j0, N, k0, t.K, r.v);
+        load_plane<256>(U0, KRM, t.i0, N, k0, t.K, r.v + 2);
+    } else {
+        load_plane<128>(V0, KRM, t.j0, N, k0, t.K, r.v);
+        load_plane<128>(V0 + NK, KRM, t.j0, N, k0, t.K, r.v + 2);
+        load_plane<128>(U0, KRM, t.i0, N, k0, t.K, r.v + 4);
+        load_plane<128>(U0 + NK, KRM, t.i0, N, k0, t.K, r.v + 6);
+    }
+}
+
+template <bool CPLX>
+__device__ __forceinline__ void store_stage(const StageRegs& r, unsigned char* sb) {
+    if (!CPLX) {
+        store_plane<128>(r.v, sb, sb + PLANE_A, 0);
+        store_plane<256>(r.v + 2, sb + 2 * PLANE_A, sb + 2 * PLANE_A + 256 * KC * 4, 0);
+    } else {
+        unsigned char* bh = sb + 4 * PLANE_A;
+        unsigned char* bl = bh + 384 * KC * 4;
+        store_plane<128>(r.v, sb, sb + PLANE_A, 0);                        // V_r
+        store_plane<128>(r.v + 2, sb + 2 * PLANE_A, sb + 3 * PLANE_A, 0);  // V_i
+        store_plane<128>(r.v + 4, bh, bl, 128);                           // U_r
+        store_plane<128>(r.v + 6, bh, bl, 256, bh, bl, 0);                // U_i and -U_i
     }
 }
 
@@ -225,35 +269,42 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
 
     if (warp < NPROD) {
         // ---- producers ----
+        // The stage sequence runs over all (tile, rank chunk) pairs of this CTA;
+        // the loads of the next stage are issued before the current one is
+        // waited for and written.
         int st = 0;
         uint32_t ph = 0;
-        for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
-            const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
-            if (t.K == 0) continue;
-            const size_t blk = ((size_t)t.c * fam_pairs + t.p) * (CPLX ? 4 : 2) * NK;
-            const float* U0 = Pan + blk;                         // U (re)
-            const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;   // V^T (re)
-            bool ok = true;
-            for (int k0 = 0; k0 < t.K; k0 += KC) {
-                if (!mbar_wait_bounded(smem_u32(&bar_empty[st]), ph ^ 1u, &s_fail)) { ok = false; break; }
-                unsigned char* sb = base + st * SB;
-                if (!CPLX) {
-                    produce_plane<128>(V0, KRM, t.j0, N, k0, t.K, sb, sb + PLANE_A, 0, 1.f);
-                    produce_plane<256>(U0, KRM, t.i0, N, k0, t.K, sb + 2 * PLANE_A, sb + 2 * PLANE_A + 256 * KC * 4, 0,
-                                       1.f);
-                } else {
-                    unsigned char* bh = sb + 4 * PLANE_A;
-                    unsigned char* bl = bh + 384 * KC * 4;
-                    produce_plane<128>(V0, KRM, t.j0, N, k0, t.K, sb, sb + PLANE_A, 0, 1.f);
-                    produce_plane<128>(V0 + NK, KRM, t.j0, N, k0, t.K, sb + 2 * PLANE_A, sb + 3 * PLANE_A, 0, 1.f);
-                    produce_plane<128>(U0, KRM, t.i0, N, k0, t.K, bh, bl, 128, 1.f);               // U_r
-                    produce_plane<128>(U0 + NK, KRM, t.i0, N, k0, t.K, bh, bl, 256, 1.f, bh, bl, 0);   // U_i, -U_i
+        long long tile = blockIdx.x;
+        TileInfo t{};
+        int k0 = 0;
+        for (; tile < total; tile += gridDim.x) {   // first tile with work
+            t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+            if (t.K > 0) break;
+        }
+        StageRegs cur, nxt;
+        if (tile < total) load_stage<CPLX>(Pan, NK, fam_pairs, KRM, N, t, 0, cur);
+        while (tile < total && !s_fail) {
+            // the stage after (tile, k0)
+            long long tile_n = tile;
+            TileInfo tn = t;
+            int kn = k0 + KC;
+            if (kn >= t.K) {
+                kn = 0;
+                for (tile_n = tile + gridDim.x; tile_n < total; tile_n += gridDim.x) {
+                    tn = decode_tile<ROWS>(tile_n, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+                    if (tn.K > 0) break;
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(smem_u32(&bar_full[st]));
-                if (++st == STAGES) { st = 0; ph ^= 1u; }
             }
-            if (!ok) { raise_fail(&s_fail, err); break; }
+            if (tile_n < total) load_stage<CPLX>(Pan, NK, fam_pairs, KRM, N, tn, kn, nxt);
+            if (!mbar_wait_bounded(smem_u32(&bar_empty[st]), ph ^ 1u, &s_fail)) { raise_fail(&s_fail, err); break; }
+            store_stage<CPLX>(cur, base + st * SB);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&bar_full[st]));
+            if (++st == STAGES) { st = 0; ph ^= 1u; }
+            cur = nxt;
+            tile = tile_n;
+            t = tn;
+            k0 = kn;
         }
     } else if (warp < MMA_WARP) {
         // ---- epilogue ----
