@@ -332,14 +332,29 @@ __global__ void __launch_bounds__(256) batch_apply(int N, int fam_pairs, int KRM
         for (int u = 0; u < RPT; ++u)
 #pragma unroll
             for (int t = 0; t < 8; ++t) acc[u][t] = Sc<T>::zero();
+        // X chunks are loaded into registers one chunk ahead (8 values per
+        // thread), so their global loads overlap the previous chunk's products
+        T xn[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int e = threadIdx.x + w * 256, aa = e >> 4, bb = e & 15;
+            xn[w] = (a0 + aa < kr && bb < kr) ? Xm[(size_t)(a0 + aa) * KRM + bb] : Sc<T>::zero();
+        }
         for (int b0 = 0; b0 < kr; b0 += 16) {
             __syncthreads();
-            for (int e = threadIdx.x; e < 128 * 16; e += blockDim.x) {
-                int aa = e >> 4, bb = e & 15;
-                Xs[bb * AP_LDX + aa] =
-                    (a0 + aa < kr && b0 + bb < kr) ? Xm[(size_t)(a0 + aa) * KRM + b0 + bb] : Sc<T>::zero();
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const int e = threadIdx.x + w * 256;
+                Xs[(e & 15) * AP_LDX + (e >> 4)] = xn[w];
             }
             __syncthreads();
+            if (b0 + 16 < kr) {
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const int e = threadIdx.x + w * 256, aa = e >> 4, bb = b0 + 16 + (e & 15);
+                    xn[w] = (a0 + aa < kr && bb < kr) ? Xm[(size_t)(a0 + aa) * KRM + bb] : Sc<T>::zero();
+                }
+            }
             const int bn = min(16, kr - b0);
             for (int bb = 0; bb < bn; ++bb) {
                 T v[RPT], x[8];
