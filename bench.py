@@ -32,8 +32,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # name: (L, group, n_v, K, chains, precision, refresh_every, delay, label)
-    "cfg3": (16, 1, 2, 4, 256, 1, 1 << 30, 8,
-             "16x16 periodic U(1), n_v=2 (M 4096x4096 complex), K=4, 256 chains, FP32 delayed rank-8k updates"),
+    "cfg3": (16, 1, 2, 4, 256, 1, 1 << 30, 16,
+             "16x16 periodic U(1), n_v=2 (M 4096x4096 complex), K=4, 256 chains, FP32 batched updates "
+             "(16 links per batch, one rank-128 tensor-core flush per batch)"),
     "cfg2": (8, 0, 1, 1, 1024, 1, 64, 1,
              "8x8 periodic Z2, K=1 (M 512x512), 1024 chains, FP32 rank-r updates, FP64 refresh every 64 accepts"),
     "cfg2_fp64": (8, 0, 1, 1, 1024, 0, 1024, 1,

@@ -446,7 +446,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     if (ch.kmax > 64) return ggf_fail(ctx, GGF_EINVAL, "delay must be <= 64");
     ch.steps_since_flush = 0;
     if (ch.kmax > 1) {
-        const size_t pr = (size_t)n_chains * ch.kmax * g.r * g.N * rsz;   // one plane per chain
+        const size_t pr = (size_t)n_chains * panel_plane(g.N, ch.kmax * g.r) * rsz;   // one plane per chain
         GGF_CK(cudaMalloc(&ch.Pr, std::max<size_t>(16, pr * 2 * ctx->K)));
         GGF_CK(cudaMalloc(&ch.Pc, std::max<size_t>(16, pr * 4 * ctx->Kc)));
         GGF_CK(cudaMalloc(&ch.ybuf, 16));

@@ -126,3 +126,13 @@ GGF_HD void philox4x64_10(const uint64_t ctr[4], uint64_t k0, uint64_t k1, uint6
 GGF_HD double u53(uint64_t w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }
 
 #define GGF_TWO_PI 6.283185307179586
+
+// Delayed-update panels (U and V^T planes, N rows x KRM rank columns) are
+// stored chunk-major: element (row, q) at ((q / 8) NP + row) 8 + q % 8, with
+// NP = N rounded up to a multiple of 256 rows and the rank rounded up to a
+// multiple of 8, so that the 8 rank columns of a block of consecutive rows
+// (what one tensor-core stage reads) are one contiguous run.
+GGF_HD int panel_rows(int N) { return (N + 255) & ~255; }
+GGF_HD int panel_cols(int KRM) { return (KRM + 7) & ~7; }
+GGF_HD size_t panel_plane(int N, int KRM) { return (size_t)panel_rows(N) * panel_cols(KRM); }
+GGF_HD size_t pidx(int row, int q, int NP) { return ((size_t)(q >> 3) * NP + row) * 8 + (q & 7); }

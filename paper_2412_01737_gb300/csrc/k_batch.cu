@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(256) batch_gather(Geometry g, int l0, int kb, 
     }
     __syncthreads();
     const int i0 = blockIdx.x * BR, nb = min(BR, N - i0), ld = kr + 1;
-    const size_t NK = (size_t)N * KRM, base = (size_t)c * fam_pairs + p;
+    const size_t NK = panel_plane(N, KRM), base = (size_t)c * fam_pairs + p;
+    const int NP = panel_rows(N);
     const T* Wp = W + base * N * N;
     RR* U = Pan + base * 2 * PanelIO<T>::PLANES * NK;
     RR* Vt = U + PanelIO<T>::PLANES * NK;
@@ -70,8 +71,8 @@ __global__ void __launch_bounds__(256) batch_gather(Geometry g, int l0, int kb, 
     for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
         int ii = e / kr, q = e - ii * kr;
         const T y = tile[ii * ld + q];
-        PanelIO<T>::st(Vt, NK, (size_t)(i0 + ii) * KRM + q, y);
-        PanelIO<T>::st(U, NK, (size_t)(i0 + ii) * KRM + q, -y);
+        PanelIO<T>::st(Vt, NK, pidx(i0 + ii, q, NP), y);
+        PanelIO<T>::st(U, NK, pidx(i0 + ii, q, NP), -y);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int a = warp; a < kr; a += nw) {
@@ -107,8 +108,8 @@ struct BatchArgs {
 // accepted (all threads of the CTA).  Gm, Xm: KRM x KRM; U: the pair's U
 // panel (planes of N x KRM); Z: r x r (FP64); st: 4 KRM r scratch scalars.
 template <class T, int r>
-__device__ __forceinline__ void small_update(T* Gm, T* Xm, const typename Sc<T>::R* U, size_t NK, const int* Tl,
-                                             int j, int kb, int KRM, const cxd* Z, T* st) {
+__device__ __forceinline__ void small_update(T* Gm, T* Xm, const typename Sc<T>::R* U, size_t NK, int NP,
+                                             const int* Tl, int j, int kb, int KRM, const cxd* Z, T* st) {
     const int jr = j * r, m = jr + r, kr = kb * r, nf = kr - m;
     T* A1 = st;                    // G[F, S] Z, later G0[0:jr, S], later P Z
     T* A2 = A1 + (size_t)KRM * r;  // G[S, F], later G0[S, 0:jr]
@@ -139,8 +140,8 @@ __device__ __forceinline__ void small_update(T* Gm, T* Xm, const typename Sc<T>:
     // (b) X += P Z Q on the leading m x m block
     for (int e = threadIdx.x; e < jr * r; e += blockDim.x) {
         int a = e / r, b = e - a * r;
-        A1[e] = PanelIO<T>::ld(U, NK, (size_t)Tl[a] * KRM + jr + b);        // G0[a][S_b]
-        A2[b * jr + a] = PanelIO<T>::ld(U, NK, (size_t)Tl[jr + b] * KRM + a);   // G0[S_b][a]
+        A1[e] = PanelIO<T>::ld(U, NK, pidx(Tl[a], jr + b, NP));        // G0[a][S_b]
+        A2[b * jr + a] = PanelIO<T>::ld(U, NK, pidx(Tl[jr + b], a, NP));   // G0[S_b][a]
     }
     __syncthreads();
     // P (m x r): rows a < jr are -X[a, 0:jr] G0[0:jr, S], rows jr.. the identity;
@@ -219,7 +220,8 @@ __global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
     __shared__ double s_cs[8];
     __shared__ int s_accept, s_any;
     typedef typename Sc<RW>::R RR;
-    const size_t NK = (size_t)N * KRM, SS = (size_t)KRM * KRM;
+    const size_t NK = panel_plane(N, KRM), SS = (size_t)KRM * KRM;
+    const int NP = panel_rows(N);
     const int kr = a.kb * r;
     for (int q = threadIdx.x; q < kr; q += blockDim.x) {
         int a0, b0;
@@ -278,14 +280,14 @@ __global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
         for (int p = 0; p < K; ++p) {
             RW* Gm = (RW*)a.Sr + ((size_t)c * K + p) * 2 * SS;
             const RR* U = (const RR*)a.Pr + ((size_t)c * K + p) * 2 * PanelIO<RW>::PLANES * NK;
-            if (r == 4) small_update<RW, 4>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + p * r * r, (RW*)sm);
-            else small_update<RW, 8>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + p * r * r, (RW*)sm);
+            if (r == 4) small_update<RW, 4>(Gm, Gm + SS, U, NK, NP, Tl, j, a.kb, KRM, Zs + p * r * r, (RW*)sm);
+            else small_update<RW, 8>(Gm, Gm + SS, U, NK, NP, Tl, j, a.kb, KRM, Zs + p * r * r, (RW*)sm);
         }
         for (int p = 0; p < Kc; ++p) {
             CW* Gm = (CW*)a.Sc_ + ((size_t)c * Kc + p) * 2 * SS;
             const RR* U = (const RR*)a.Pc + ((size_t)c * Kc + p) * 2 * PanelIO<CW>::PLANES * NK;
-            if (r == 4) small_update<CW, 4>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + (K + p) * r * r, (CW*)sm);
-            else small_update<CW, 8>(Gm, Gm + SS, U, NK, Tl, j, a.kb, KRM, Zs + (K + p) * r * r, (CW*)sm);
+            if (r == 4) small_update<CW, 4>(Gm, Gm + SS, U, NK, NP, Tl, j, a.kb, KRM, Zs + (K + p) * r * r, (CW*)sm);
+            else small_update<CW, 8>(Gm, Gm + SS, U, NK, NP, Tl, j, a.kb, KRM, Zs + (K + p) * r * r, (CW*)sm);
         }
     }
     if (threadIdx.x == 0) a.pend[c] = s_any ? a.kb : 0;
@@ -317,13 +319,14 @@ __global__ void __launch_bounds__(256) batch_apply(int N, int fam_pairs, int KRM
     const int ld = kr + 1;
     T* Xs = (T*)smraw;           // [16][AP_LDX]  X^T chunk: Xs[bb][aa] = X[a0 + aa][b0 + bb]
     T* Vs = Xs + 16 * AP_LDX;    // [RB][kr + 1]
-    const size_t NK = (size_t)N * KRM, base = (size_t)c * fam_pairs + p;
+    const size_t NK = panel_plane(N, KRM), base = (size_t)c * fam_pairs + p;
+    const int NP = panel_rows(N);
     RR* Vt = Pan + base * 2 * PanelIO<T>::PLANES * NK + PanelIO<T>::PLANES * NK;
     const T* Xm = Sm + base * 2 * KRM * KRM + (size_t)KRM * KRM;
     const int i0 = blockIdx.x * RB, nb = min(RB, N - i0);
     for (int e = threadIdx.x; e < RB * kr; e += blockDim.x) {
         int ii = e / kr, q = e - ii * kr;
-        Vs[ii * ld + q] = ii < nb ? PanelIO<T>::ld(Vt, NK, (size_t)(i0 + ii) * KRM + q) : Sc<T>::zero();
+        Vs[ii * ld + q] = ii < nb ? PanelIO<T>::ld(Vt, NK, pidx(i0 + ii, q, NP)) : Sc<T>::zero();
     }
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     for (int a0 = 0; a0 < kr; a0 += 128) {
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(256) batch_apply(int N, int fam_pairs, int KRM
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const int aa = a0 + tx * 8 + t;
-                if (aa < kr) PanelIO<T>::st(Vt, NK, (size_t)(i0 + ii) * KRM + aa, acc[u][t]);
+                if (aa < kr) PanelIO<T>::st(Vt, NK, pidx(i0 + ii, aa, NP), acc[u][t]);
             }
         }
     }

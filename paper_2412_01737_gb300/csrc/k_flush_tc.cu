@@ -20,20 +20,23 @@
 // holds re(D^T) in TMEM columns 0..127 and im(D^T) in 128..255.
 //
 // One persistent CTA per SM, warp-specialised:
-//   warps 0-3   producers: load an 8-wide rank chunk of the operands
-//               (float4; the next stage's loads are issued before the
-//               current stage is written, so two stages are in flight),
-//               split into tf32 hi/lo and write them in the no-swizzle
+//   warps 0-7   producers: copy an 8-wide rank chunk of the operands into
+//               a private raw shared-memory slot with cp.async (16 bytes
+//               per copy, zero-filled outside the matrix; PD stages of
+//               copies in flight ahead), then split each thread's own
+//               values into tf32 hi/lo and write them in the no-swizzle
 //               K-major core-matrix layout (8 rows x 16 B core matrices,
 //               LBO = 128 B along K, SBO = 256 B between 8-row groups) into a
 //               ring of STAGES shared-memory stages;
-//   warp 12     one thread issues the MMAs of each stage and commits them to
+//   warp 16     one thread issues the MMAs of each stage and commits them to
 //               the stage's "empty" mbarrier, and after a tile's last stage
 //               to the "accumulator full" mbarrier of one of two TMEM
 //               accumulators (2 x 256 of the 512 columns);
-//   warps 4-11  epilogue: TMEM -> registers, W -= D, releasing the
+//   warps 8-15  epilogue (two per TMEM lane quarter, each half of the
+//               tile's rows): TMEM -> registers, W -= D, releasing the
 //               accumulator, so that one tile's epilogue overlaps the next
-//               tile's MMAs.
+//               tile's MMAs; meanwhile the next tile's rows of W are bulk-
+//               prefetched into L2.
 // Every mbarrier wait is bounded; on expiry the kernel raises the device error
 // word, the other roles leave their loops, the MMA thread waits (bounded) for
 // its MMAs in flight and the TMEM is freed.
@@ -44,8 +47,10 @@ namespace {
 
 constexpr int KC = 8;                         // rank columns per stage (one MMA K step)
 constexpr int SBO = KC / 4 * 128;             // bytes between 8-row core-matrix groups
-constexpr int STAGES = 4;
-constexpr int NPROD = 4, NEPI = 8;            // producer and epilogue warps (+ one MMA warp)
+constexpr int STAGES = 3;                     // split (MMA operand) stages
+constexpr int RAWS = 4, PD = 3;               // raw cp.async slots; stages of loads in flight ahead
+constexpr int NPROD = 8, NEPI = 8;            // producer and epilogue warps (+ one MMA warp)
+constexpr int EPI_PARTS = NEPI / 4;           // epilogue warps per TMEM lane quarter (row groups of a tile)
 constexpr int PGROUP = NPROD * 32;
 constexpr int TC_THREADS = (NPROD + NEPI + 1) * 32;
 constexpr int MMA_WARP = NPROD + NEPI;
@@ -53,9 +58,12 @@ constexpr int PLANE_A = 128 * KC * 4;         // 4 KB: 128 rows x 8 tf32
 // stage: real    A hi, A lo, B hi, B lo (256 rows)                      24 KB
 //        complex Ar hi, Ar lo, Ai hi, Ai lo, Bc hi, Bc lo (384 rows)   40 KB
 __host__ __device__ constexpr int stage_bytes(bool cplx) { return cplx ? 4 * PLANE_A + 2 * 384 * KC * 4 : 2 * PLANE_A + 2 * 256 * KC * 4; }
+// raw slot: one stage's operands as float4 copies (complex 1024, real 768),
+// copy t of producer thread x at position t * PGROUP + x
+constexpr int RAW_BYTES = 8 * 128 * 16;
 // both variants reserve the complex size, so exactly one CTA fits on an SM
 // (the CTA allocates all 512 TMEM columns)
-__host__ __device__ constexpr int smem_bytes(bool) { return STAGES * stage_bytes(true) + 1024; }
+__host__ __device__ constexpr int smem_bytes(bool) { return STAGES * stage_bytes(true) + RAWS * RAW_BYTES + 1024; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -134,6 +142,25 @@ struct TileInfo {
     int c, p, i0, j0, K;
 };
 
+__device__ __forceinline__ void prefetch_l2(const void* ptr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
+// Bulk L2 prefetch of row e of tile t's block of W (the columns j0 .. j0 + 127
+// of that row, one contiguous segment).  The bulk copy needs a 16-byte
+// aligned start and a length that is a multiple of 16 bytes; rows of other
+// widths (possible only in the self-test) are not prefetched.
+template <int ROWS, bool CPLX>
+__device__ __forceinline__ void prefetch_tile_row(const TileInfo& t, const float* W, int fam_pairs, int N, int rowW,
+                                                  int e) {
+    const int i = t.i0 + e;
+    if (e >= ROWS || i >= N) return;
+    const int ncol = min(128, N - t.j0);
+    if ((rowW & 3) || ((ncol * (CPLX ? 8 : 4)) & 15)) return;
+    const float* ptr = W + ((size_t)t.c * fam_pairs + t.p) * (size_t)N * rowW + (size_t)i * rowW + (CPLX ? 2 : 1) * t.j0;
+    prefetch_l2(ptr, (uint32_t)ncol * (CPLX ? 8u : 4u));
+}
+
 template <int ROWS>
 __device__ __forceinline__ TileInfo decode_tile(long long tile, int tiles_i, int tiles_j, int fam_pairs,
                                                 const int* pend, int R, int upper) {
@@ -152,36 +179,58 @@ __device__ __forceinline__ TileInfo decode_tile(long long tile, int tiles_i, int
     return t;
 }
 
-// One stage's operands in the producer threads' registers: rank columns
-// k0 .. k0 + 7 of the tile's planes, float4 per (row, half of the chunk).
-// Real: V^T rows j0.. (2 per thread), U rows i0.. (4); complex: V_r, V_i,
-// U_r, U_i rows (2 each).
-struct StageRegs {
-    float4 v[8];
-};
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
+// Copies of one plane's rows row0 .. row0 + NR - 1, rank columns k0 .. k0 + 7
+// into raw slot positions slot0 .. (float4 units, this thread's only).  Rows
+// or columns outside the matrix are zero-filled (source size 0, source
+// address clamped to the plane's start).
 template <int NR>
-__device__ __forceinline__ void load_plane(const float* src, int KRM, int row0, int N, int k0, int K, float4* v) {
+__device__ __forceinline__ void copy_plane(const float* src, int NP, int row0, int N, int k0, int K, uint32_t raw,
+                                           int slot0) {
     constexpr int PER = NR * 2 / PGROUP;
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         const int idx = (int)threadIdx.x + t * PGROUP, row = idx >> 1, k = k0 + 4 * (idx & 1);
         const int gr = row0 + row;
-        v[t] = (gr < N && k < K) ? __ldg((const float4*)(src + (size_t)gr * KRM + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool in = gr < N && k < K;
+        const float* p = in ? src + pidx(gr, k, NP) : src;
+        cp_async16(raw + (uint32_t)((slot0 + t) * PGROUP + threadIdx.x) * 16u, p, in ? 16u : 0u);
     }
 }
 
-// Split loaded values into tf32 hi/lo and write them at core-matrix row
-// offset dst_row (and negated at dst_row2 when hi2 is given).
+template <bool CPLX>
+__device__ __forceinline__ void copy_stage(const float* Pan, size_t NK, int fam_pairs, int NP, int N,
+                                           const TileInfo& t, int k0, uint32_t raw) {
+    const size_t blk = ((size_t)t.c * fam_pairs + t.p) * (CPLX ? 4 : 2) * NK;
+    const float* U0 = Pan + blk;                         // U (re)
+    const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;   // V^T (re)
+    constexpr int S1 = 256 / PGROUP;   // float4 slots per thread of a 128-row plane
+    if (!CPLX) {
+        copy_plane<128>(V0, NP, t.j0, N, k0, t.K, raw, 0);
+        copy_plane<256>(U0, NP, t.i0, N, k0, t.K, raw, S1);
+    } else {
+        copy_plane<128>(V0, NP, t.j0, N, k0, t.K, raw, 0);
+        copy_plane<128>(V0 + NK, NP, t.j0, N, k0, t.K, raw, S1);
+        copy_plane<128>(U0, NP, t.i0, N, k0, t.K, raw, 2 * S1);
+        copy_plane<128>(U0 + NK, NP, t.i0, N, k0, t.K, raw, 3 * S1);
+    }
+}
+
+// Split this thread's raw values of one plane into tf32 hi/lo and write them
+// at core-matrix row offset dst_row (and negated at dst_row2 when hi2 is given).
 template <int NR>
-__device__ __forceinline__ void store_plane(const float4* v, unsigned char* hi, unsigned char* lo, int dst_row,
-                                            unsigned char* hi2 = nullptr, unsigned char* lo2 = nullptr,
+__device__ __forceinline__ void split_plane(const unsigned char* raw, int slot0, unsigned char* hi, unsigned char* lo,
+                                            int dst_row, unsigned char* hi2 = nullptr, unsigned char* lo2 = nullptr,
                                             int dst_row2 = 0) {
     constexpr int PER = NR * 2 / PGROUP;
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         const int idx = (int)threadIdx.x + t * PGROUP, row = idx >> 1, kq = 4 * (idx & 1);
-        const float4 x = v[t];
+        const float4 x = *(const float4*)(raw + ((slot0 + t) * PGROUP + threadIdx.x) * 16);
         const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
         const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
         const uint32_t o = cm_off(dst_row + row, kq);
@@ -196,34 +245,48 @@ __device__ __forceinline__ void store_plane(const float4* v, unsigned char* hi, 
 }
 
 template <bool CPLX>
-__device__ __forceinline__ void load_stage(const float* Pan, size_t NK, int fam_pairs, int KRM, int N,
-                                           const TileInfo& t, int k0, StageRegs& r) {
-    const size_t blk = ((size_t)t.c * fam_pairs + t.p) * (CPLX ? 4 : 2) * NK;
-    const float* U0 = Pan + blk;                         // U (re)
-    const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;   // V^T (re)
+__device__ __forceinline__ void split_stage(const unsigned char* raw, unsigned char* sb) {
+    constexpr int S1 = 256 / PGROUP;   // float4 slots per thread of a 128-row plane
     if (!CPLX) {
-        load_plane<128>(V0, KRM, t.j0, N, k0, t.K, r.v);
-        load_plane<256>(U0, KRM, t.i0, N, k0, t.K, r.v + 2);
-    } else {
-        load_plane<128>(V0, KRM, t.j0, N, k0, t.K, r.v);
-        load_plane<128>(V0 + NK, KRM, t.j0, N, k0, t.K, r.v + 2);
-        load_plane<128>(U0, KRM, t.i0, N, k0, t.K, r.v + 4);
-        load_plane<128>(U0 + NK, KRM, t.i0, N, k0, t.K, r.v + 6);
-    }
-}
-
-template <bool CPLX>
-__device__ __forceinline__ void store_stage(const StageRegs& r, unsigned char* sb) {
-    if (!CPLX) {
-        store_plane<128>(r.v, sb, sb + PLANE_A, 0);
-        store_plane<256>(r.v + 2, sb + 2 * PLANE_A, sb + 2 * PLANE_A + 256 * KC * 4, 0);
+        split_plane<128>(raw, 0, sb, sb + PLANE_A, 0);
+        split_plane<256>(raw, S1, sb + 2 * PLANE_A, sb + 2 * PLANE_A + 256 * KC * 4, 0);
     } else {
         unsigned char* bh = sb + 4 * PLANE_A;
         unsigned char* bl = bh + 384 * KC * 4;
-        store_plane<128>(r.v, sb, sb + PLANE_A, 0);                        // V_r
-        store_plane<128>(r.v + 2, sb + 2 * PLANE_A, sb + 3 * PLANE_A, 0);  // V_i
-        store_plane<128>(r.v + 4, bh, bl, 128);                           // U_r
-        store_plane<128>(r.v + 6, bh, bl, 256, bh, bl, 0);                // U_i and -U_i
+        split_plane<128>(raw, 0, sb, sb + PLANE_A, 0);                        // V_r
+        split_plane<128>(raw, S1, sb + 2 * PLANE_A, sb + 3 * PLANE_A, 0);     // V_i
+        split_plane<128>(raw, 2 * S1, bh, bl, 128);                           // U_r
+        split_plane<128>(raw, 3 * S1, bh, bl, 256, bh, bl, 0);                // U_i and -U_i
+    }
+}
+
+// Iterator over this CTA's stages: (tile, rank chunk) pairs with work.
+struct StageIter {
+    long long tile;
+    TileInfo t;
+    int k0;
+};
+
+template <int ROWS>
+__device__ __forceinline__ void stage_first(StageIter& it, long long total, int tiles_i, int tiles_j, int fam_pairs,
+                                            const int* pend, int R, int upper) {
+    it.k0 = 0;
+    for (it.tile = blockIdx.x; it.tile < total; it.tile += gridDim.x) {
+        it.t = decode_tile<ROWS>(it.tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+        if (it.t.K > 0) return;
+    }
+}
+
+template <int ROWS>
+__device__ __forceinline__ void stage_next(StageIter& it, long long total, int tiles_i, int tiles_j, int fam_pairs,
+                                           const int* pend, int R, int upper) {
+    if (it.tile >= total) return;
+    it.k0 += KC;
+    if (it.k0 < it.t.K) return;
+    it.k0 = 0;
+    for (it.tile += gridDim.x; it.tile < total; it.tile += gridDim.x) {
+        it.t = decode_tile<ROWS>(it.tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+        if (it.t.K > 0) return;
     }
 }
 
@@ -240,7 +303,8 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
     constexpr int SB = stage_bytes(CPLX);
     const int rowW = CPLX ? 2 * N : N;            // floats per W row
     const int tiles_i = (N + ROWS - 1) / ROWS, tiles_j = (N + 127) / 128;
-    const size_t NK = (size_t)N * KRM;
+    const size_t NK = panel_plane(N, KRM);
+    const int NP = panel_rows(N);
     const long long total = (long long)n_chains * fam_pairs * tiles_i * tiles_j;
     unsigned char* base = (unsigned char*)(((uintptr_t)sm + 1023) & ~(uintptr_t)1023);
 
@@ -269,61 +333,70 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
 
     if (warp < NPROD) {
         // ---- producers ----
-        // The stage sequence runs over all (tile, rank chunk) pairs of this CTA;
-        // the loads of the next stage are issued before the current one is
-        // waited for and written.
+        // Stage s's copies are issued PD stages before it is split; every
+        // stage (even a missing one past the end) commits one cp.async group,
+        // so "wait_group PD" leaves exactly stage s's copies complete.
+        unsigned char* raw = base + STAGES * SB;
+        const uint32_t raw_u = smem_u32(raw);
+        StageIter ahead, cur;
+        stage_first<ROWS>(ahead, total, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+        cur = ahead;
+        for (int d = 0; d < PD; ++d) {
+            if (ahead.tile < total)
+                copy_stage<CPLX>(Pan, NK, fam_pairs, NP, N, ahead.t, ahead.k0, raw_u + (uint32_t)(d % RAWS) * RAW_BYTES);
+            cp_async_commit();
+            stage_next<ROWS>(ahead, total, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+        }
         int st = 0;
         uint32_t ph = 0;
-        long long tile = blockIdx.x;
-        TileInfo t{};
-        int k0 = 0;
-        for (; tile < total; tile += gridDim.x) {   // first tile with work
-            t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
-            if (t.K > 0) break;
-        }
-        StageRegs cur, nxt;
-        if (tile < total) load_stage<CPLX>(Pan, NK, fam_pairs, KRM, N, t, 0, cur);
-        while (tile < total && !s_fail) {
-            // the stage after (tile, k0)
-            long long tile_n = tile;
-            TileInfo tn = t;
-            int kn = k0 + KC;
-            if (kn >= t.K) {
-                kn = 0;
-                for (tile_n = tile + gridDim.x; tile_n < total; tile_n += gridDim.x) {
-                    tn = decode_tile<ROWS>(tile_n, tiles_i, tiles_j, fam_pairs, pend, R, upper);
-                    if (tn.K > 0) break;
-                }
-            }
-            if (tile_n < total) load_stage<CPLX>(Pan, NK, fam_pairs, KRM, N, tn, kn, nxt);
+        for (long long sidx = 0; cur.tile < total && !s_fail; ++sidx) {
+            if (ahead.tile < total)
+                copy_stage<CPLX>(Pan, NK, fam_pairs, NP, N, ahead.t, ahead.k0,
+                                 raw_u + (uint32_t)((sidx + PD) % RAWS) * RAW_BYTES);
+            cp_async_commit();
+            stage_next<ROWS>(ahead, total, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+            asm volatile("cp.async.wait_group %0;" ::"n"(PD) : "memory");
             if (!mbar_wait_bounded(smem_u32(&bar_empty[st]), ph ^ 1u, &s_fail)) { raise_fail(&s_fail, err); break; }
-            store_stage<CPLX>(cur, base + st * SB);
+            split_stage<CPLX>(raw + (size_t)(sidx % RAWS) * RAW_BYTES, base + st * SB);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&bar_full[st]));
             if (++st == STAGES) { st = 0; ph ^= 1u; }
-            cur = nxt;
-            tile = tile_n;
-            t = tn;
-            k0 = kn;
+            stage_next<ROWS>(cur, total, tiles_i, tiles_j, fam_pairs, pend, R, upper);
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp < MMA_WARP) {
         // ---- epilogue ----
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int half = (warp - NPROD) >> 2;   // which half of the tile's rows
+        const int half = (warp - NPROD) >> 2;   // which row group of the tile
         int b = 0;
         uint32_t ph = 0;
+        // While a tile is drained, its successor's rows of W are prefetched into
+        // L2 (one row per epilogue thread), so that the epilogue's loads, which
+        // registers limit to 16 per thread in flight, hit L2 instead of DRAM.
+        const int e_row = (int)threadIdx.x - NPROD * 32;
+        bool first = true;
         for (long long tile = blockIdx.x; tile < total && !s_fail; tile += gridDim.x) {
             const TileInfo t = decode_tile<ROWS>(tile, tiles_i, tiles_j, fam_pairs, pend, R, upper);
             if (t.K == 0) continue;
+            if (first) {
+                prefetch_tile_row<ROWS, CPLX>(t, W, fam_pairs, N, rowW, e_row);
+                first = false;
+            }
+            for (long long tn = tile + gridDim.x; tn < total; tn += gridDim.x) {
+                const TileInfo u = decode_tile<ROWS>(tn, tiles_i, tiles_j, fam_pairs, pend, R, upper);
+                if (u.K == 0) continue;
+                prefetch_tile_row<ROWS, CPLX>(u, W, fam_pairs, N, rowW, e_row);
+                break;
+            }
             if (!mbar_wait_bounded(smem_u32(&bar_accf[b]), ph, &s_fail)) { raise_fail(&s_fail, err); break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int j = t.j0 + q * 32 + lane;
             float* Wp = W + ((size_t)t.c * fam_pairs + t.p) * (size_t)N * rowW;
             const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
             if (!CPLX) {
-                // rows i0 + half*128 + 16 cb + k  <->  TMEM column half*128 + 16 cb + k
+                // rows i0 + half*RG + 16 cb + k  <->  TMEM column half*RG + 16 cb + k (RG = 256 / EPI_PARTS)
 #pragma unroll 1
-                for (int cb = 0; cb < 8; ++cb) {
+                for (int cb = 0; cb < 256 / EPI_PARTS / 16; ++cb) {
                     uint32_t v[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -331,8 +404,8 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
                           "=r"(v[14]), "=r"(v[15])
-                        : "r"(tl + half * 128 + cb * 16));
-                    const int ib = t.i0 + half * 128 + cb * 16;
+                        : "r"(tl + half * (256 / EPI_PARTS) + cb * 16));
+                    const int ib = t.i0 + half * (256 / EPI_PARTS) + cb * 16;
                     float w[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
@@ -347,9 +420,10 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
                     }
                 }
             } else {
-                // rows i0 + half*64 + 16 cb + k  <->  re column half*64 + 16 cb + k, im column + 128
+                // rows i0 + half*RG + 16 cb + k  <->  re column half*RG + 16 cb + k, im column + 128
+                // (RG = 128 / EPI_PARTS)
 #pragma unroll 1
-                for (int cb = 0; cb < 4; ++cb) {
+                for (int cb = 0; cb < 128 / EPI_PARTS / 16; ++cb) {
                     uint32_t v[16], vi[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -357,15 +431,15 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
                           "=r"(v[14]), "=r"(v[15])
-                        : "r"(tl + half * 64 + cb * 16));
+                        : "r"(tl + half * (128 / EPI_PARTS) + cb * 16));
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
                         "%15}, [%16];"
                         : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
                           "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]),
                           "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
-                        : "r"(tl + 128 + half * 64 + cb * 16));
-                    const int ib = t.i0 + half * 64 + cb * 16;
+                        : "r"(tl + 128 + half * (128 / EPI_PARTS) + cb * 16));
+                    const int ib = t.i0 + half * (128 / EPI_PARTS) + cb * 16;
                     float2 w[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
@@ -460,7 +534,7 @@ namespace {
 ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_chains, float* W, const float* Pan,
                            const int* pend, int R, int KRM, bool upper, int* err, cudaStream_t st) {
     if (fam_pairs == 0 || n_chains == 0) return GGF_OK;
-    if (KRM % 4) return ggf_fail(ctx, GGF_EINVAL, "tensor-core flush: panel row stride must be a multiple of 4");
+    if (KRM < 1) return ggf_fail(ctx, GGF_EINVAL, "tensor-core flush: empty panel");
     const int rows = cplx ? 128 : 256;
     const long long total = (long long)n_chains * fam_pairs * ((N + rows - 1) / rows) * ((N + 127) / 128);
     int sms = ctx->n_sms > 0 ? ctx->n_sms : 152;
@@ -493,18 +567,19 @@ __global__ void st_reference(bool cplx, int N, int K, int KRM, const float* W0, 
     const int rowW = cplx ? 2 * N : N;
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)N * rowW) return;
-    const size_t NK = (size_t)N * KRM;
+    const size_t NK = panel_plane(N, KRM);
+    const int NP = panel_rows(N);
     int i = (int)(e / rowW), f = (int)(e % rowW);
     if (!cplx) {
         double s = 0.0;
-        for (int q = 0; q < K; ++q) s += (double)Pan[(size_t)i * KRM + q] * (double)Pan[NK + (size_t)f * KRM + q];
+        for (int q = 0; q < K; ++q) s += (double)Pan[pidx(i, q, NP)] * (double)Pan[NK + pidx(f, q, NP)];
         ref[e] = (double)W0[e] - s;
     } else {
         int j = f >> 1, part = f & 1;
         double sr = 0.0, si = 0.0;
         for (int q = 0; q < K; ++q) {
-            double ur = Pan[(size_t)i * KRM + q], ui = Pan[NK + (size_t)i * KRM + q];
-            double vr = Pan[2 * NK + (size_t)j * KRM + q], vi = Pan[3 * NK + (size_t)j * KRM + q];
+            double ur = Pan[pidx(i, q, NP)], ui = Pan[NK + pidx(i, q, NP)];
+            double vr = Pan[2 * NK + pidx(j, q, NP)], vi = Pan[3 * NK + pidx(j, q, NP)];
             sr += ur * vr - ui * vi;
             si += ur * vi + ui * vr;
         }
@@ -540,7 +615,7 @@ extern "C" ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank
     cudaSetDevice(ctx->device);
     const int R = 4, KRM = rank;
     const int rowW = cplx ? 2 * N : N;
-    const size_t NK = (size_t)N * KRM, nW = (size_t)N * rowW, nP = (cplx ? 4 : 2) * NK;
+    const size_t NK = panel_plane(N, KRM), nW = (size_t)N * rowW, nP = (cplx ? 4 : 2) * NK;
     float *W = nullptr, *Pan = nullptr;
     double* ref = nullptr;
     int* pend = nullptr;

@@ -97,21 +97,21 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
             if (a.kmax > 1) {
                 // pending updates: W_eff[S, S] = W[S, S] - U[S, :] V[:, S]
                 const int kr = a.pend[c] * r;
-                const int KRM = a.kmax * r;
-                const size_t NK = (size_t)N * KRM;
+                const int KRM = a.kmax * r, NP = panel_rows(N);
+                const size_t NK = panel_plane(N, KRM);
                 typedef typename Sc<RW>::R R;
                 if (p < K) {
                     const R* U = (const R*)a.Pr + ((size_t)c * K + p) * 2 * NK;
                     const R* Vt = U + NK;
                     for (int qq = 0; qq < kr; ++qq)
-                        wv -= Sc<RW>::to(PanelIO<RW>::ld(U, NK, (size_t)gi * KRM + qq)) *
-                              Sc<RW>::to(PanelIO<RW>::ld(Vt, NK, (size_t)gj * KRM + qq));
+                        wv -= Sc<RW>::to(PanelIO<RW>::ld(U, NK, pidx(gi, qq, NP))) *
+                              Sc<RW>::to(PanelIO<RW>::ld(Vt, NK, pidx(gj, qq, NP)));
                 } else {
                     const R* U = (const R*)a.Pc + ((size_t)c * (P - K) + (p - K)) * 4 * NK;
                     const R* Vt = U + 2 * NK;
                     for (int qq = 0; qq < kr; ++qq)
-                        wv -= Sc<CW>::to(PanelIO<CW>::ld(U, NK, (size_t)gi * KRM + qq)) *
-                              Sc<CW>::to(PanelIO<CW>::ld(Vt, NK, (size_t)gj * KRM + qq));
+                        wv -= Sc<CW>::to(PanelIO<CW>::ld(U, NK, pidx(gi, qq, NP))) *
+                              Sc<CW>::to(PanelIO<CW>::ld(Vt, NK, pidx(gj, qq, NP)));
                 }
             }
             Ws[e] = wv;
@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
     if (!accept[c]) return;
     const int p = blockIdx.y, N = g.N;
     const int slot = pend[c] - 1, kr = slot * R;
-    const int KRM = kmax * R;
-    const size_t NK = (size_t)N * KRM;
+    const int KRM = kmax * R, NP = panel_rows(N);
+    const size_t NK = panel_plane(N, KRM);
     extern __shared__ unsigned char smraw[];
     constexpr int QC = 128 / sizeof(T);  // rank chunk staged per step
     T* UtS = (T*)smraw;            // [kr][R]  U[S_a, q]
@@ -258,8 +258,8 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
     const cxd* Z = zbuf + ((size_t)c * P + pair_off + p) * R * R;
     for (int e = threadIdx.x; e < kr * R; e += blockDim.x) {
         int q = e / R, a = e % R;
-        UtS[e] = PanelIO<T>::ld(U, NK, (size_t)S[a] * KRM + q);
-        VS[e] = PanelIO<T>::ld(Vt, NK, (size_t)S[a] * KRM + q);
+        UtS[e] = PanelIO<T>::ld(U, NK, pidx(S[a], q, NP));
+        VS[e] = PanelIO<T>::ld(Vt, NK, pidx(S[a], q, NP));
     }
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) Zs[e] = Sc<T>::from(Z[e]);
     __syncthreads();
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
         for (int e = threadIdx.x; e < 128 * QC; e += blockDim.x) {
             int row = e / QC, qq = e % QC;
             bool ok = qq < qn && j0 + row < N;
-            size_t idx = (size_t)(j0 + row) * KRM + q0 + qq;
+            size_t idx = pidx(j0 + row, q0 + qq, NP);
             Uc[row * (QC + 1) + qq] = ok ? PanelIO<T>::ld(U, NK, idx) : Sc<T>::zero();
             Vc[row * (QC + 1) + qq] = ok ? PanelIO<T>::ld(Vt, NK, idx) : Sc<T>::zero();
         }
@@ -301,8 +301,8 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
         T u = Sc<T>::zero();
 #pragma unroll
         for (int a = 0; a < R; ++a) u += cv[a] * Zs[a * R + b];
-        PanelIO<T>::st(U, NK, (size_t)j * KRM + kr + b, u);
-        PanelIO<T>::st(Vt, NK, (size_t)j * KRM + kr + b, yv[b]);
+        PanelIO<T>::st(U, NK, pidx(j, kr + b, NP), u);
+        PanelIO<T>::st(Vt, NK, pidx(j, kr + b, NP), yv[b]);
     }
 }
 
@@ -317,8 +317,8 @@ __global__ void __launch_bounds__(256) flush_kernel(int N, int fam_pairs, T* W, 
     const int c = blockIdx.z;
     const int kc = pend[c];
     if (kc == 0) return;
-    const int kr = kc * R, KRM = kmax * R;
-    const size_t NK = (size_t)N * KRM;
+    const int kr = kc * R, KRM = kmax * R, NP = panel_rows(N);
+    const size_t NK = panel_plane(N, KRM);
     const int p = blockIdx.y;
     const int ti = blockIdx.x / tiles, tj = blockIdx.x - ti * tiles;
     const int i0 = ti * 64, j0 = tj * 64;
@@ -339,8 +339,8 @@ __global__ void __launch_bounds__(256) flush_kernel(int N, int fam_pairs, T* W, 
         for (int e = threadIdx.x; e < 16 * 64; e += 256) {
             int k = e >> 4, qq = e & 15;      // consecutive threads walk the rank index
             int q = q0 + qq;
-            As[qq][k] = (q < kr && i0 + k < N) ? PanelIO<T>::ld(U, NK, (size_t)(i0 + k) * KRM + q) : Sc<T>::zero();
-            Bs[qq][k] = (q < kr && j0 + k < N) ? PanelIO<T>::ld(Vt, NK, (size_t)(j0 + k) * KRM + q) : Sc<T>::zero();
+            As[qq][k] = (q < kr && i0 + k < N) ? PanelIO<T>::ld(U, NK, pidx(i0 + k, q, NP)) : Sc<T>::zero();
+            Bs[qq][k] = (q < kr && j0 + k < N) ? PanelIO<T>::ld(Vt, NK, pidx(j0 + k, q, NP)) : Sc<T>::zero();
         }
         __syncthreads();
 #pragma unroll
