@@ -82,7 +82,10 @@ def run_cfg5(args):
     ctxs, tuned, t0 = [], [], time.time()
     for k, (p, ch, mem) in enumerate(cells):
         links = gi.cold_links(p, ch)
+        t_cell = time.time()
         d, tim = tune_delay(p, links, 1, candidates=(4, 8, 16), use_cache=False, seed=BASE_SEED + k)
+        print(f"cfg5 cell {k}: L={p.L} group={p.group} K={p.K} chains={ch} delay={d} "
+              f"tune {time.time() - t_cell:.1f}s {tim}", file=sys.stderr, flush=True)
         tuned.append({"L": p.L, "group": "Z2" if p.group == 0 else "U1", "K": p.K, "chains": ch, "delay": d,
                       "ms_per_sweep": {str(a): round(b, 2) for a, b in tim.items()}})
         c = GGF(0)

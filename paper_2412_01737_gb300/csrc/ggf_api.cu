@@ -587,9 +587,12 @@ ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem, bool graph_launc
     if (obs_dst)
         GGF_CK(cudaMemcpyAsync(obs_dst, ch.d_obs_stage, (size_t)ch.n * GGF_N_OBS * sizeof(double),
                                mem == GGF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, cs));
-    int cnt = 0;
+    int cnt = 0, derr = 0;
     GGF_CK(cudaMemcpyAsync(&cnt, ch.refresh_list, sizeof(int), cudaMemcpyDeviceToHost, cs));
+    GGF_CK(cudaMemcpyAsync(&derr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, cs));
     GGF_CK(cudaStreamSynchronize(cs));
+    // a bounded device wait that ran out ends the call after this sweep
+    if (derr) return ggf_fail(ctx, GGF_ETIMEOUT, "a bounded device wait ran out (tensor-core flush)");
     if (ctx->prof) {
         if (!graph_launched) GGF_TRY(accumulate_events(ctx, ctx->ev_cat, ctx->ev));
         ctx->ev_cat.clear();

@@ -298,6 +298,9 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
     __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_accf[2], bar_acce[2], bar_done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_fail;
+    // an earlier bounded wait of this context ran out: do nothing (the host
+    // reports GGF_ETIMEOUT after the sweep)
+    if (*(volatile int*)err) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int ROWS = CPLX ? 128 : 256;        // W rows per tile
     constexpr int SB = stage_bytes(CPLX);
