@@ -10,14 +10,16 @@ constexpr int NWARP = 8;
 
 __device__ __forceinline__ double magc(cxd v) { return fabs(v.x) + fabs(v.y); }
 
-// warp argmax over lanes (ties: lowest index)
+// warp argmax over lanes (ties: lowest index).  The result is taken from
+// lane 0 so that every lane follows the same pivot even when a NaN makes the
+// comparisons inconsistent (the callers branch on it around __syncwarp).
 __device__ __forceinline__ int warp_argmax(double v, int idx) {
     for (int o = 16; o > 0; o >>= 1) {
         double ov = __shfl_xor_sync(0xffffffffu, v, o);
         int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
     }
-    return idx;
+    return __shfl_sync(0xffffffffu, idx, 0);
 }
 
 // Pfaffian of an n x n (n <= 32) antisymmetric matrix in shared memory, by one
@@ -195,6 +197,12 @@ __device__ __forceinline__ void twist_table(const Geometry& g, const Proposal& q
 // sign), one warp; Bw is 2r x 2r scratch.
 __device__ __forceinline__ cxd bordered_ratio(const cxd* D, const cxd* Ws, cxd* Bw, int r) {
     const int lane = threadIdx.x & 31, n2 = 2 * r;
+    // a non-finite block (an inverse that overflowed) gives ratio 0: the
+    // proposal is rejected
+    bool fin = true;
+    for (int e = lane; e < r * r; e += 32)
+        fin = fin && isfinite(Ws[e].x) && isfinite(Ws[e].y) && isfinite(D[e].x) && isfinite(D[e].y);
+    if (!__all_sync(0xffffffffu, fin)) return {0.0, 0.0};
     for (int e = lane; e < n2 * n2; e += 32) {
         int i = e / n2, j = e % n2;
         cxd v = {0.0, 0.0};
