@@ -132,12 +132,20 @@ typedef struct {
     int refresh_every;  /* full FP64 refresh of a chain after this many accepts */
     double width;       /* U(1) proposal: theta += width * (u - 1/2) */
     uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = chain index) */
-    int delay;          /* <= 1: apply every accepted update to W at once;
-                           k > 1: keep up to k accepted rank-r updates pending
-                           as panels U (N x k r), V (k r x N), with
-                           W_eff = W - U V, and fold them into W with one
-                           rank-(k r) product every k link steps (delayed
-                           Sherman-Morrison-Woodbury updates). */
+    int delay;          /* <= 1: apply every accepted rank-r update to the
+                           whole W at once (true columns);
+                           k > 1 (at most 64): sweep in batches of k
+                           consecutive links.  Their Majorana sets are
+                           disjoint, so a batch needs only the k r x k r
+                           block of the inverse on their union T: the
+                           batch's proposals and accepted updates run on that
+                           block and the composed update W - W[:, T] X W[T, :]
+                           is folded into W with one rank-(k r) product
+                           (delayed Sherman-Morrison-Woodbury updates).  In
+                           this mode only the upper triangle of each W
+                           (i <= j) is kept current (M and W are
+                           antisymmetric); learned-proposal block moves need
+                           k >= 32. */
     int graph;          /* != 0: capture one sweep (all link steps, flushes,
                            observables) into a CUDA graph on first use and
                            replay it; 0: launch every kernel eagerly */
@@ -179,7 +187,8 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
 
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
- * L^2.  For tests and diagnostics. */
+ * L^2 (with delay > 1 the lower triangle is filled from the upper one as
+ * W[j][i] = -W[i][j]).  For tests and diagnostics. */
 ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, int mem, void* stream);
 
 typedef struct {
