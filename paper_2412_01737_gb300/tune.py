@@ -1,9 +1,10 @@
 """Autotuner for the sampler's launch shape.
 
-The tunable is the delayed-update depth k (`delay`): deeper panels fold more
-accepted updates into one tensor-core flush (fewer passes over W) but make
-every ratio and gather read longer panels and cost k r N of extra memory per
-pair and chain.  For a given problem and chain count the tuner times one
+The tunable is the batch size k (`delay`): larger batches fold more links
+into one tensor-core flush (fewer passes over W) but make the flush a
+higher-rank product (k r), the small-matrix work of every link step grow
+with (k r)^2, and the X application grow with N (k r)^2; the panels cost
+2 k r N and the small matrices 2 (k r)^2 of memory per pair and chain.  For a given problem and chain count the tuner times one
 sweep per candidate through the C ABI and keeps the fastest; results are
 cached in a JSON file keyed by (lattice, group, n_v, K, chains, precision).
 """
