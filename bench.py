@@ -199,13 +199,6 @@ def problem_for(name):
     return p, chains, prec, refresh, delay, label
 
 
-def flush_bytes(p, prec):
-    """Algorithmic HBM bytes of one flush of one chain in the delayed and batched
-    modes: the upper triangle (N (N + 1) / 2 elements) of every pair's W read
-    and written once."""
-    return unit_bytes(p, prec) * (p.N + 1) / (2 * p.N)
-
-
 def unit_bytes(p, prec):
     """Algorithmic HBM bytes of one rank-r update of one chain: every pair's W
     read and written once (N^2 elements each)."""
@@ -409,17 +402,16 @@ def run_ggf(args):
         fl = accepts * 2.0 * p.N ** 2 * p.r * wpairs      # every accepted rank-r update folded once
         t_fl = kt["flush"][0] * 1e-3
         if prec == 1:
-            # tensor-core flush: the upper triangle of W (delayed and batched modes
-            # keep only i <= j) read and written once per flush call and chain
-            byts = kt["flush"][1] * chains * flush_bytes(p, prec)
-            roof = {"kernel": "flush_tc_kernel (tcgen05 TF32x3, W -= U V, upper triangle)", "bound": "hbm",
+            # tensor-core flush: W read + written once per flush call and chain
+            byts = kt["flush"][1] * chains * unit_bytes(p, prec)
+            roof = {"kernel": "flush_tc_kernel (tcgen05 TF32x3, W -= U V)", "bound": "hbm",
                     "achieved": byts / t_fl / 1e9, "peak": hbm, "unit": "GB/s",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                    "algorithmic_bytes_per_launch_group": chains * flush_bytes(p, prec),
-                    "fp32_equivalent_tflops": fl / 2 / t_fl / 1e12}
+                    "algorithmic_bytes_per_launch_group": chains * unit_bytes(p, prec),
+                    "fp32_equivalent_tflops": fl / t_fl / 1e12}
         else:
-            roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V, upper triangle)", "bound": "alu",
-                    "achieved": fl / 2 / t_fl / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+            roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V)", "bound": "alu",
+                    "achieved": fl / t_fl / 1e12, "peak": 1.25, "unit": "TFLOP/s",
                     "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe)"}
     elif dom == "update" and delay <= 1:
         upd_bytes = accepts * unit_bytes(p, prec)
@@ -448,8 +440,8 @@ def run_ggf(args):
     roof["traffic"] = None
     roof["share"] = {k: round(v / max(ms, 1e-9), 4) for k, v in shares.items()}
     if delay > 1 and kt["gather"][1] > 0:
-        # batched mode: per batch and pair, the gather reads W[:, T] through the upper
-        # triangle (N kr b) and writes the U and V^T panels (2 N kr b); the X product
+        # batched mode: per batch and pair, the gather reads W[:, T] and W[T, :]
+        # (2 N kr b) and writes the U and V^T panels (2 N kr b); the X product
         # reads and writes V^T (2 N kr b) and does N kr^2 MACs
         b = 8 if prec == 0 else 4
         kr = delay * p.r
@@ -457,7 +449,7 @@ def run_ggf(args):
         macs = sum((1 if n == m else 4) * p.N * kr * kr for n in range(p.K) for m in range(n, p.K))
         n_b = kt["gather"][1]
         roof["batch_kernels"] = {
-            "batch_gather_gbs": n_b * chains * 3 * per_b / (kt["gather"][0] * 1e-3) / 1e9,
+            "batch_gather_gbs": n_b * chains * 4 * per_b / (kt["gather"][0] * 1e-3) / 1e9,
             "batch_apply_gbs": n_b * chains * 2 * per_b / (kt["apply"][0] * 1e-3) / 1e9,
             "batch_apply_fp32_tflops": n_b * chains * 2 * macs / (kt["apply"][0] * 1e-3) / 1e12,
             "note": "kr = delay r is the batch's rank; sizes per launch group over all chains"}

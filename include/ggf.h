@@ -141,11 +141,9 @@ typedef struct {
                            batch's proposals and accepted updates run on that
                            block and the composed update W - W[:, T] X W[T, :]
                            is folded into W with one rank-(k r) product
-                           (delayed Sherman-Morrison-Woodbury updates).  In
-                           this mode only the upper triangle of each W
-                           (i <= j) is kept current (M and W are
-                           antisymmetric); learned-proposal block moves need
-                           k >= 32. */
+                           (delayed Sherman-Morrison-Woodbury updates, with
+                           the true columns W[:, T]); learned-proposal block
+                           moves need k >= 32. */
     int graph;          /* != 0: capture one sweep (all link steps, flushes,
                            observables) into a CUDA graph on first use and
                            replay it; 0: launch every kernel eagerly */
@@ -187,8 +185,7 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
 
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
- * L^2 (with delay > 1 the lower triangle is filled from the upper one as
- * W[j][i] = -W[i][j]).  For tests and diagnostics. */
+ * L^2.  For tests and diagnostics. */
 ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, int mem, void* stream);
 
 typedef struct {

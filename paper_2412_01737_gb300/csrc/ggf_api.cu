@@ -770,15 +770,6 @@ ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, in
         else { const float* f = (const float*)h.data(); re = cplx ? f[2 * e] : f[e]; if (cplx) im = f[2 * e + 1]; }
         o[2 * e] = re; o[2 * e + 1] = im;
     }
-    if (ch.kmax > 1) {
-        // delayed and batched modes keep only the upper triangle current
-        const int N = ctx->g.N;
-        for (int i = 1; i < N; ++i)
-            for (int j = 0; j < i; ++j) {
-                o[2 * ((size_t)i * N + j)] = -o[2 * ((size_t)j * N + i)];
-                o[2 * ((size_t)i * N + j) + 1] = -o[2 * ((size_t)j * N + i) + 1];
-            }
-    }
     GGF_CK(cudaMemcpy(out, o.data(), o.size() * sizeof(double), mem == GGF_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
     return GGF_OK;
 }

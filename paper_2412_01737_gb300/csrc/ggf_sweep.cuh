@@ -109,15 +109,6 @@ template <> __device__ __forceinline__ void PanelIO<float>::st(float* p, size_t,
 template <> __device__ __forceinline__ void PanelIO<cxd>::st(double* p, size_t pl, size_t i, cxd v) { p[i] = v.x; p[pl + i] = v.y; }
 template <> __device__ __forceinline__ void PanelIO<cxf>::st(float* p, size_t pl, size_t i, cxf v) { p[i] = v.x; p[pl + i] = v.y; }
 
-// Element (i, j) of a chain's cached inverse W = M^{-1} (row-major N x N).
-// M is antisymmetric, so W is too; in the delayed and batched modes only the
-// upper triangle (i <= j) is kept current, and the lower entries are read as
-// -W[j][i].
-template <class T>
-__device__ __forceinline__ T w_upper(const T* W, int N, int i, int j) {
-    return i <= j ? W[(size_t)i * N + j] : -W[(size_t)j * N + i];
-}
-
 // Majorana offsets of the two ends of link l = 2 s + d: the source end (+d
 // end of site s, which carries the twist) and the target end (-d end of the
 // neighbour t).  Majorana xi < h2 of the link is a0 + xi, the others b0 + xi - h2.

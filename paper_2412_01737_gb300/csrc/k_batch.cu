@@ -8,8 +8,9 @@
 // j r + xi of T is Majorana xi of link l0 + j).  Every proposal of the batch
 // needs only the block of the current inverse on T.  With W the inverse at
 // the start of the batch, C = W[:, T], Y = W[T, :], G0 = W[T, T]:
-//   batch_gather  C -> U panel, Y^T -> V^T panel, G := G0, X := 0 (read
-//                 through the upper triangle of W, so C = -Y^T exactly)
+//   batch_gather  C -> U panel, Y^T -> V^T panel, G := G0, X := 0 (C read as
+//                 the true columns: -Y^T, equal in exact arithmetic, makes
+//                 the rounding error grow geometrically)
 //   batch_steps   one CTA per chain runs the kb link steps on the small
 //                 matrices: ratio from G[S_j, S_j], decision, and on accept,
 //                 with Z = (1 + Delta G[S, S])^{-1} Delta,
@@ -20,8 +21,7 @@
 //                 (each step is the rank-r update W' = W - W[:, S] Z W[S, :]
 //                 with W[:, S] = C P and W[S, :] = Q Y).
 //   batch_apply   V^T <- V^T X^T  (V = X Y)
-// followed by the flush W <- W - U V on the upper triangle (tcgen05 tensor
-// cores for FP32 chains).
+// followed by the flush W <- W - U V (tcgen05 tensor cores for FP32 chains).
 // Per batch and pair this reads C and Y once (2 N kb r elements) instead of
 // two N-long panel products per accepted link, and folds kb links into one
 // pass over W.
@@ -55,31 +55,33 @@ __global__ void __launch_bounds__(256) batch_gather(Geometry g, int l0, int kb, 
     RR* Vt = U + PanelIO<T>::PLANES * NK;
     T* Gm = Sm + base * 2 * KRM * KRM;
     T* Xm = Gm + (size_t)KRM * KRM;
-    // Only the upper triangle of W is current (W is antisymmetric): with
-    // y = W[T_q][i] = -W[i][T_q], V^T[i][q] = y and U[i][q] = -y.
-    // Entries with T_q <= i come from row T_q of W, read along i:
+    // V^T rows: tile[ii][q] = W[T_q][i0 + ii], read along rows of W
     for (int e = threadIdx.x; e < kr * BR; e += blockDim.x) {
         int q = e / BR, ii = e - q * BR;
-        if (ii < nb && Tl[q] <= i0 + ii) tile[ii * ld + q] = Wp[(size_t)Tl[q] * N + i0 + ii];
-    }
-    // the others from column T_q, read along the rows i of the block:
-    for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
-        int ii = e / kr, q = e - ii * kr;
-        if (Tl[q] > i0 + ii) tile[ii * ld + q] = -Wp[(size_t)(i0 + ii) * N + Tl[q]];
+        tile[ii * ld + q] = ii < nb ? Wp[(size_t)Tl[q] * N + i0 + ii] : Sc<T>::zero();
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
         int ii = e / kr, q = e - ii * kr;
-        const T y = tile[ii * ld + q];
-        PanelIO<T>::st(Vt, NK, pidx(i0 + ii, q, NP), y);
-        PanelIO<T>::st(U, NK, pidx(i0 + ii, q, NP), -y);
+        PanelIO<T>::st(Vt, NK, pidx(i0 + ii, q, NP), tile[ii * ld + q]);
     }
+    __syncthreads();
+    // U rows: the true columns W[i0 + ii][T_q].  Replacing them by -Y^T (equal
+    // for an exactly antisymmetric W) lets the rounding error grow
+    // geometrically from batch to batch.
+    for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
+        int ii = e / kr, q = e - ii * kr;
+        T v = Wp[(size_t)(i0 + ii) * N + Tl[q]];
+        tile[ii * ld + q] = v;
+        PanelIO<T>::st(U, NK, pidx(i0 + ii, q, NP), v);
+    }
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int a = warp; a < kr; a += nw) {
         const int ii = Tl[a] - i0;
         if (ii < 0 || ii >= nb) continue;
         for (int q = lane; q < kr; q += 32) {
-            Gm[(size_t)a * KRM + q] = -tile[ii * ld + q];   // W[T_a][T_q] = U[T_a][q]
+            Gm[(size_t)a * KRM + q] = tile[ii * ld + q];   // W[T_a][T_q] = U[T_a][q]
             Xm[(size_t)a * KRM + q] = Sc<T>::zero();
         }
     }

@@ -1,9 +1,9 @@
 // Delayed-update flush on the sm_103a tensor cores (tcgen05 + TMEM).
 //
 // For FP32 chains, folds the pending rank-K panels into the cached inverse:
-// W <- W - U V on the tiles that touch the upper triangle (W is
-// antisymmetric; the sampler keeps only i <= j current), with U (N x K) and
-// V^T (N x K) stored K-major (rank index
+// W <- W - U V (with `upper` set, only the tiles that touch the upper
+// triangle; the sampler updates the whole matrix), with U (N x K) and V^T
+// (N x K) panels (rank index
 // contiguous, row stride KRM), complex pairs as separate real/imaginary
 // planes.  FP32 accuracy from TF32 tensor cores by the three-product split
 // x = hi + lo, hi = rna_tf32(x):  a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
@@ -606,9 +606,9 @@ ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st) {
     const Geometry& g = ctx->g;
     const int KRM = ch.kmax * g.r;
     GGF_TRY(launch_flush_tc(ctx, false, g.N, ctx->K, ch.n, (float*)ch.Wr, (const float*)ch.Pr, ch.pend, g.r, KRM,
-                            true, ctx->d_err, st));
+                            false, ctx->d_err, st));
     GGF_TRY(launch_flush_tc(ctx, true, g.N, ctx->Kc, ch.n, (float*)ch.Wc, (const float*)ch.Pc, ch.pend, g.r, KRM,
-                            true, ctx->d_err, st));
+                            false, ctx->d_err, st));
     return GGF_OK;
 }
 

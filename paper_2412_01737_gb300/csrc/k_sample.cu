@@ -90,10 +90,8 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
         for (int e = lane; e < r * r; e += 32) {
             const int gi = link_majorana(g, a0, b0, e / r), gj = link_majorana(g, a0, b0, e % r);
             cxd wv;
-            const RW* Wr_p = (const RW*)a.Wr + ((size_t)c * K + p) * N * N;
-            const CW* Wc_p = (const CW*)a.Wc + ((size_t)c * (P - K) + (p - K)) * N * N;
-            if (a.kmax <= 1) wv = p < K ? loadc(Wr_p + (size_t)gi * N + gj) : loadc(Wc_p + (size_t)gi * N + gj);
-            else wv = p < K ? Sc<RW>::to(w_upper(Wr_p, N, gi, gj)) : Sc<CW>::to(w_upper(Wc_p, N, gi, gj));
+            if (p < K) wv = loadc((const RW*)a.Wr + (((size_t)c * K + p) * N + gi) * N + gj);
+            else wv = loadc((const CW*)a.Wc + (((size_t)c * (P - K) + (p - K)) * N + gi) * N + gj);
             if (a.kmax > 1) {
                 // pending updates: W_eff[S, S] = W[S, S] - U[S, :] V[:, S]
                 const int kr = a.pend[c] * r;
@@ -269,8 +267,8 @@ __global__ void __launch_bounds__(128) gather_kernel(Geometry g, int P, int fam_
     T yv[R], cv[R];
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-        yv[a] = live ? w_upper(Wp, N, S[a], j) : Sc<T>::zero();
-        cv[a] = -yv[a];   // W[j][S_a] = -W[S_a][j]: only the upper triangle is current
+        yv[a] = live ? Wp[(size_t)S[a] * N + j] : Sc<T>::zero();
+        cv[a] = live ? Wp[(size_t)j * N + S[a]] : Sc<T>::zero();
     }
     // panel rows j0 .. j0+127 staged chunk by chunk with coalesced loads
     for (int q0 = 0; q0 < kr; q0 += QC) {
@@ -322,7 +320,6 @@ __global__ void __launch_bounds__(256) flush_kernel(int N, int fam_pairs, T* W, 
     const int p = blockIdx.y;
     const int ti = blockIdx.x / tiles, tj = blockIdx.x - ti * tiles;
     const int i0 = ti * 64, j0 = tj * 64;
-    if (i0 > j0 + 63) return;   // strictly lower tile: only the upper triangle is kept
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     __shared__ T As[16][65];
     __shared__ T Bs[16][65];
