@@ -18,6 +18,8 @@ mcmc     Sequential-sweep Metropolis over link configurations (Sec. 5.1),
          full recomputation of N(G) for every proposal.
 observables  Plaquette Wilson loops (Sec. 2.3) and integrated
          autocorrelation times.
+electric The Z2 electric (link-flip) observable of Sec. 5.3: f_E(G) from
+         explicit vectors and from a Pfaffian of the composed covariance.
 
 Parity status per function is listed in each module's docstring; every
 function is pinned by a `-m "not gpu"` test except where a docstring says
