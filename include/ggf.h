@@ -183,6 +183,22 @@ ggf_status ggf_chains_links(ggf_ctx* ctx, void* links, int mem, void* stream);
 /* Tracked log Pf(M_nm) of all chains, [n_chains][P][2] as (log|Pf|, arg). */
 ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
 
+/* Electric (link-flip) observable of a Z2 gauge field (Sec. 5.3) at the
+ * current configuration G of every chain:
+ *     f_E(G)_l = sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(G^(l))> / N(G),
+ * G^(l) being G with link l flipped.  The mean of f_E over samples of p(G)
+ * estimates <X_l>, X_l the flip of link l (the Z2 electric term of a link is
+ * a linear function of X_l).  Computed from the cached inverses: flipping g_l
+ * multiplies the state by the parity of the link's source-end modes S, so
+ * each pair contributes (-1)^{n_v} Pf(Gamma_O[S, S]) with Gamma_O =
+ * i 1 - (1 + i D) W_nm (1 + i O Gamma_X O^T) (Wick's theorem; only the
+ * 8 n_v x 4 n_v block of W between the source site and the link is read).
+ * Pending delayed updates are folded into W first.
+ *   out [n_chains][2V][2] FP64 (re, im), caller-owned.
+ * GGF_EINVAL for U(1) chains (the integral over g of Sec. 5.3 is not built),
+ * GGF_ESTATE before ggf_chains_init. */
+ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream);
+
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
  * L^2.  For tests and diagnostics. */

@@ -30,7 +30,8 @@ Two routes:
    from oracle.weight.
 
 Pinned (tests/test_oracle_electric.py): the covariance route against the Fock
-route on 2x2 Z2 lattices (K = 1, 2; every link; random configurations);
+route on 2x2 Z2 lattices (K = 1, 2; every link; random configurations) and
+on the 1x1 torus with n_v = 2 (every configuration);
 gauge invariance of f_E; the exhaustive <X_l> on the 2x2 lattice is real and
 at most 1 in modulus.
 """

@@ -18,6 +18,7 @@ ggf_status ggf_prepare_batch(ggf_ctx* ctx);
 ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64);
 ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st);
 ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
+ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -743,6 +744,26 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream) {
     GGF_CK(cudaMemcpyAsync(ell, ctx->ch.ell, (size_t)ctx->ch.n * ctx->P * sizeof(cxd),
                            mem == GGF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!out) return ggf_fail(ctx, GGF_EINVAL, "null out");
+    if (ctx->g.group != GGF_Z2)
+        return ggf_fail(ctx, GGF_EINVAL, "the link-flip electric observable is defined for Z2 links");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)ctx->ch.n * ctx->g.n_links * sizeof(cxd);
+    if (mem == GGF_MEM_HOST) {
+        DBuf d;
+        GGF_TRY(dalloc(ctx, d, bytes));
+        GGF_TRY(ggf_electric(ctx, (cxd*)d.p, st));
+        GGF_CK(cudaMemcpyAsync(out, d.p, bytes, cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return check_err_word(ctx);
+    }
+    GGF_TRY(ggf_electric(ctx, (cxd*)out, st));
     return GGF_OK;
 }
 

@@ -1,0 +1,171 @@
+// Electric (link-flip) observable of a Z2 gauge field (Sec. 5.3), evaluated
+// for every chain and link from the inverses W_nm = M_nm(G)^{-1} the sampler
+// keeps.
+//
+// For Z2 the electric term of link l is a linear function of the flip
+// X_l |G> = |G^(l)>, and Sec. 5.3 needs
+//   f_E(G)_l = sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(G^(l))> / N(G).
+// Flipping g_l multiplies the twisted state by the parity of the source-end
+// modes of l (the end that carries the twist), a product of the 2 n_v
+// Majoranas S of that end.  Wick's theorem on the Gaussian operator composed
+// of the sites' virtual state and the bond operator X_nm then gives
+//   R_nm = <psi_n(G)|psi_m(G^(l))> / <psi_n(G)|psi_m(G)> = (-1)^{n_v} Pf(Gamma_O[S, S]),
+//   Gamma_O = i 1 - (1 + i D) W_nm (1 + i Gamma_tw),
+// with M_nm = D + Gamma_tw, D the sites' virtual blocks and Gamma_tw =
+// O(G) Gamma_X O(G)^T the twisted link blocks.  D is block diagonal by site
+// and Gamma_tw by link, so [(1 + i D) W (1 + i Gamma_tw)]_SS involves only the
+// B x r block of W between the source site's virtual Majoranas and the link's
+// r Majoranas.  D and the twist are real and Gamma_X of (m, n) is the complex
+// conjugate of that of (n, m), so M_mn = conj(M_nm): both orders of a pair
+// n < m come from its one stored inverse.  With N_nm = e^{logc + ell}
+// (N_mn = conj N_nm) and the pair weights of the sampler's combination,
+//   f_E(G)_l = sum_nm lambda_n^* lambda_m N_nm R_nm / sum_nm lambda_n^* lambda_m N_nm.
+#include "ggf_ctx.h"
+#include "ggf_sweep.cuh"
+
+namespace {
+
+constexpr int ETHREADS = 128;
+
+// Pfaffian of an H x H antisymmetric matrix (H = 2 n_v = 2 or 4), closed form.
+template <int H>
+__device__ __forceinline__ cxd small_pf(const cxd (&A)[H][H]);
+template <>
+__device__ __forceinline__ cxd small_pf<2>(const cxd (&A)[2][2]) { return A[0][1]; }
+template <>
+__device__ __forceinline__ cxd small_pf<4>(const cxd (&A)[4][4]) {
+    return A[0][1] * A[2][3] - A[0][2] * A[1][3] + A[0][3] * A[1][2];
+}
+
+__device__ __forceinline__ cxd times_i(cxd v) { return {-v.y, v.x}; }
+
+// R for both orders of pair p at link l: Rf from (W, Gamma_tw), Rr from their
+// conjugates.  W points at the pair's N x N inverse (row-major).
+template <class T, int H>
+__device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* W, int l, double gval, cxd& Rf,
+                            cxd& Rr) {
+    constexpr int R = 2 * H, B = 4 * H;
+    const Geometry& g = dc.g;
+    int a0, b0;
+    link_ends(g, l, a0, b0);
+    const int s0 = (l >> 1) * g.B;        // first virtual Majorana of the source site
+    const int loc0 = a0 - s0;             // position of S inside the site block
+    const double* Ds = dc.D + (size_t)(l >> 1) * B * B;
+    cxd Xf[H][H], Xr[H][H];
+#pragma unroll
+    for (int a = 0; a < H; ++a)
+#pragma unroll
+        for (int b = 0; b < H; ++b) Xf[a][b] = Xr[a][b] = cxd{0.0, 0.0};
+#pragma unroll
+    for (int b = 0; b < H; ++b) {
+        // column b of (1 + i Gamma_tw)[link, S] and of its conjugate
+        cxd cf[R], cr[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            cxd gt;
+            if (cplx_pair) gt = twisted<cxd>(dc, p - dc.K, l, j, b, gval, 0.0);
+            else gt = cxd{twisted<double>(dc, p, l, j, b, gval, 0.0), 0.0};
+            cf[j] = times_i(gt);
+            cr[j] = times_i(conjg(gt));
+            if (j == b) { cf[j].x += 1.0; cr[j].x += 1.0; }
+        }
+        for (int i = 0; i < B; ++i) {
+            const T* row = W + (size_t)(s0 + i) * g.N;
+            cxd yf = {0.0, 0.0}, yr = {0.0, 0.0};
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const cxd w = Sc<T>::to(row[link_majorana(g, a0, b0, j)]);
+                yf += w * cf[j];
+                yr += conjg(w) * cr[j];
+            }
+            // row a of (1 + i D)[S, site] at column i
+#pragma unroll
+            for (int a = 0; a < H; ++a) {
+                cxd dp = {0.0, Ds[(size_t)(loc0 + a) * B + i]};
+                if (loc0 + a == i) dp.x = 1.0;
+                Xf[a][b] += dp * yf;
+                Xr[a][b] += dp * yr;
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < H; ++a)
+#pragma unroll
+        for (int b = 0; b < H; ++b) {
+            Xf[a][b] = -Xf[a][b];
+            Xr[a][b] = -Xr[a][b];
+            if (a == b) { Xf[a][b].y += 1.0; Xr[a][b].y += 1.0; }
+        }
+    const double sg = (H / 2) % 2 ? -1.0 : 1.0;    // (-1)^{n_v}
+    Rf = sg * small_pf<H>(Xf);
+    Rr = sg * small_pf<H>(Xr);
+}
+
+// One thread per (chain, link); out[c][l] = f_E(G_c)_l.
+template <class RW, class CW, int H>
+__global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_chains, int blocks_per_chain,
+                                                            const int8_t* links, const RW* Wr, const CW* Wc,
+                                                            const cxd* ell, cxd* out) {
+    const Geometry& g = dc.g;
+    const int c = blockIdx.x / blocks_per_chain;
+    const int l = (blockIdx.x - c * blocks_per_chain) * ETHREADS + threadIdx.x;
+    if (c >= n_chains || l >= g.n_links) return;
+    const size_t NN = (size_t)g.N * g.N;
+    const double gval = (double)links[(size_t)c * g.n_links + l];
+    const cxd* el = ell + (size_t)c * dc.P;
+    double amax = -INFINITY;
+    for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
+    double den = 0.0;
+    cxd num = {0.0, 0.0};
+    for (int p = 0; p < dc.P; ++p) {
+        cxd e = dc.logc[p] + el[p];
+        const bool cplx = p >= dc.K;
+        if (!cplx) e.y = 0.0;
+        e.x -= amax;
+        const cxd E = dc.w[p] * cexp_(e);        // w_p N_p, scaled
+        den += E.x;
+        cxd Rf, Rr;
+        if (cplx) {
+            flip_ratios<CW, H>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, Rf, Rr);
+            // w_p = 2 lambda_n^* lambda_m: the (n, m) term takes E / 2, the (m, n) term its conjugate
+            num += 0.5 * (E * Rf) + 0.5 * (conjg(E) * Rr);
+        } else {
+            flip_ratios<RW, H>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, Rf, Rr);
+            num += E * Rf;
+        }
+    }
+    out[(size_t)c * g.n_links + l] = cxd{num.x / den, num.y / den};
+}
+
+}  // namespace
+
+ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
+
+// f_E for every chain and link into d_out [n_chains][n_links] (device).
+ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    if (g.group != GGF_Z2)
+        return ggf_fail(ctx, GGF_EINVAL, "the link-flip electric observable is defined for Z2 links");
+    // pending delayed updates first, so that W is the inverse at the current links
+    GGF_TRY(ggf_flush(ctx, st));
+    const int bpc = (g.n_links + ETHREADS - 1) / ETHREADS;
+    const long long blocks = (long long)bpc * ch.n;
+    if (blocks > 0x7fffffffLL) return ggf_fail(ctx, GGF_EINVAL, "too many chains for one launch");
+    const bool fp64 = ch.opts.precision == GGF_FP64;
+    const int8_t* lk = (const int8_t*)ch.links;
+#define GGF_EL(RW, CW, H)                                                                                \
+    electric_kernel<RW, CW, H><<<(unsigned)blocks, ETHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, lk,          \
+                                                                      (const RW*)ch.Wr, (const CW*)ch.Wc, \
+                                                                      ch.ell, d_out)
+    if (g.h2 == 2) {
+        if (fp64) GGF_EL(double, cxd, 2); else GGF_EL(float, cxf, 2);
+    } else if (g.h2 == 4) {
+        if (fp64) GGF_EL(double, cxd, 4); else GGF_EL(float, cxf, 4);
+    } else {
+        return ggf_fail(ctx, GGF_EINVAL, "n_v must be 1 or 2");
+    }
+#undef GGF_EL
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}

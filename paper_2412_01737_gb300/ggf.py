@@ -47,7 +47,8 @@ class ChainStats(ctypes.Structure):
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
-           "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_stats", "ggf_checkpoint",
+           "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_electric",
+           "ggf_chains_stats", "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
            "ggf_selftest_flush", "ggf_net_create", "ggf_net_destroy", "ggf_net_last_error", "ggf_net_get_params",
            "ggf_net_set_params", "ggf_net_logq", "ggf_net_loss_grad", "ggf_net_train", "ggf_sample_blocks"]
@@ -82,6 +83,7 @@ def load():
         "ggf_chains_links": ([P, P, I, P], I),
         "ggf_chains_ell": ([P, P, I, P], I),
         "ggf_chains_inverse": ([P, I, I, P, I, P], I),
+        "ggf_chains_electric": ([P, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -261,6 +263,17 @@ class GGF:
         out = np.zeros((self.n_chains, st.n_pairs, 2))
         self._ck(self.lib.ggf_chains_ell(self.h, out.ctypes.data, MEM_HOST, None))
         return out[..., 0] + 1j * out[..., 1]
+
+    def chains_electric(self, out=None):
+        """f_E(G)_l of every chain and link (Z2 link flip, Sec. 5.3): complex
+        numpy array (n_chains, 2V), or fills `out` (float64 [n_chains][2V][2],
+        numpy or CUDA tensor) and returns it."""
+        if out is None:
+            host = np.zeros((self.n_chains, self.n_links(), 2))
+            self._ck(self.lib.ggf_chains_electric(self.h, host.ctypes.data, MEM_HOST, None))
+            return host[..., 0] + 1j * host[..., 1]
+        self._ck(self.lib.ggf_chains_electric(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
+        return out
 
     def chains_inverse(self, chain, pair, N):
         out = np.zeros((N, N, 2))

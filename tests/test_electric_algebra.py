@@ -1,0 +1,92 @@
+"""The algebra of the GPU electric-observable kernel, in numpy.
+
+The kernel works on the reduced virtual-mode matrix with the twist on the
+bond side, M = D + O Gamma_X O^T, W = M^{-1}, and for link l with source-end
+Majoranas S computes
+    R_nm = (-1)^{n_v} Pf(Gamma_O[S, S]),
+    Gamma_O[S, S] = i 1 - (1 + i D)[S, site] W[site, link] (1 + i O Gamma_X O^T)[link, S]
+from the B x r block of W between the source site and the link only, with the
+(m, n) order of a pair n < m taken from conj(W_nm) and conj(Gamma_X^nm).
+These checks restate that recipe and compare it with the oracle's f_E (which
+has the twist on the site side and the full covariance route), and check the
+two facts it rests on: the block restriction and M_mn = conj(M_nm).
+"""
+import numpy as np
+import pytest
+
+import ggf_inputs as gi
+from oracle import electric, pfaffian, weight
+
+
+def _gpu_picture(p, links):
+    """Reduced D, per-pair twisted bond blocks and inverses, and link indices."""
+    virt = np.array([i for i in range(p.m_s * p.V) if i % p.m_s >= 2])
+    pos = -np.ones(p.m_s * p.V, dtype=int)
+    pos[virt] = np.arange(virt.size)
+    N, B, h2 = virt.size, 8 * p.n_v, 2 * p.n_v
+    D = np.zeros((N, N))
+    for s in range(p.V):
+        D[s * B:(s + 1) * B, s * B:(s + 1) * B] = p.gamma_site[s][2:, 2:]
+    idx = [pos[np.array(ix)] for ix in weight.link_majoranas(p)]
+    o = np.ones(N)
+    for l in range(p.n_links):
+        o[idx[l][:h2]] = links[l]          # the source end carries the twist
+    bd = weight.BondData(p)
+    tw = {nm: o[:, None] * bd.embedded(*nm)[np.ix_(virt, virt)] * o[None, :]
+          for nm in [(n, m) for n in range(p.K) for m in range(p.K)]}
+    return D, tw, idx, B, h2
+
+
+def _kernel_ratio(D, W, Gtw, S, site, lk, n_v):
+    h2 = S.size
+    left = np.eye(D.shape[0])[S][:, site] + 1j * D[np.ix_(S, site)]
+    right = np.eye(D.shape[0])[np.ix_(lk, S)] + 1j * Gtw[np.ix_(lk, S)]
+    X = left @ W[np.ix_(site, lk)] @ right
+    return (-1) ** n_v * pfaffian.pfaffian(1j * np.eye(h2) - X)
+
+
+@pytest.mark.parametrize("L,n_v,K", [(3, 1, 2), (2, 1, 3), (2, 2, 2)])
+def test_block_recipe_matches_oracle(L, n_v, K):
+    p = gi.make_problem(L, gi.Z2, n_v, K, bond_scale=0.3)
+    el, Wt = electric.Electric(p), weight.Weights(p)
+    for links in gi.random_links(p, 2, seed=17):
+        D, tw, idx, B, h2 = _gpu_picture(p, links)
+        lnm = Wt.log_n_matrix(links)
+        Nnm = np.exp(lnm - lnm.real.max())
+        f = np.zeros(p.n_links, dtype=complex)
+        for n in range(p.K):
+            for m in range(n, p.K):
+                Wnm = np.linalg.inv(D + tw[n, m])
+                if m > n:
+                    # the (m, n) order from the stored (n, m) inverse
+                    assert np.abs(np.linalg.inv(D + tw[m, n]) - Wnm.conj()).max() <= 1e-10 * np.abs(Wnm).max()
+                for l in range(p.n_links):
+                    s = l // 2
+                    site = np.arange(s * B, (s + 1) * B)
+                    S, lk = idx[l][:h2], idx[l]
+                    Rf = _kernel_ratio(D, Wnm, tw[n, m], S, site, lk, n_v)
+                    f[l] += np.conj(p.lam[n]) * p.lam[m] * Nnm[n, m] * Rf
+                    if m > n:
+                        Rr = _kernel_ratio(D, Wnm.conj(), tw[n, m].conj(), S, site, lk, n_v)
+                        f[l] += np.conj(p.lam[m]) * p.lam[n] * Nnm[m, n] * Rr
+        f /= np.einsum("n,m,nm->", np.conj(p.lam), p.lam, Nnm)
+        ref = el.f_electric(links)
+        assert np.abs(f - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_block_restriction_is_exact():
+    """(1 + i D) W (1 + i Gamma_tw) on S x S equals the full product: D is
+    block diagonal by site and Gamma_tw by link."""
+    p = gi.make_problem(3, gi.Z2, 1, 1, bond_scale=0.3)
+    links = gi.random_links(p, 1, seed=2)[0]
+    D, tw, idx, B, h2 = _gpu_picture(p, links)
+    W = np.linalg.inv(D + tw[0, 0])
+    one = np.eye(D.shape[0])
+    full = (one + 1j * D) @ W @ (one + 1j * tw[0, 0])
+    for l in range(p.n_links):
+        s = l // 2
+        site = np.arange(s * B, (s + 1) * B)
+        S, lk = idx[l][:h2], idx[l]
+        blk = (one[S][:, site] + 1j * D[np.ix_(S, site)]) @ W[np.ix_(site, lk)] @ \
+              (one[np.ix_(lk, S)] + 1j * tw[0, 0][np.ix_(lk, S)])
+        assert np.abs(blk - full[np.ix_(S, S)]).max() <= 1e-12 * np.abs(full).max()

@@ -32,6 +32,17 @@ def test_covariance_route_matches_fock_2x2(K, seed):
     assert np.abs(cov - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("K", [1, 2])
+def test_covariance_route_matches_fock_two_modes_per_end(K):
+    """n_v = 2 (four Majoranas per link end, (-1)^{n_v} = +1) on the 1x1
+    torus, every configuration."""
+    p = gi.make_problem(1, gi.Z2, 2, K, bond_scale=0.4)
+    fp, el = fock.FockPEPS(p), electric.Electric(p)
+    for G in gi.all_z2_configs(p):
+        ref = _fock_f(fp, G)
+        assert np.abs(el.f_electric(G) - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("K", [1, 2, 3])
 def test_exhaustive_expectation_matches_fock_1x1(K):
     """<X_l> = sum_G <psi(G)|psi(G^(l))> / sum_G <psi(G)|psi(G)> on the 1x1

@@ -1,0 +1,89 @@
+"""GPU parity of the Z2 electric (link-flip) observable of Sec. 5.3.
+
+ggf_chains_electric evaluates f_E(G)_l for every chain and link from the
+chains' cached inverses; the oracle evaluates it by the full covariance route
+(itself pinned to explicit Fock vectors).  FP64 chains agree to 1e-10
+relative, FP32 chains to 1e-4.
+"""
+import numpy as np
+import pytest
+
+import ggf_inputs as gi
+from oracle import electric
+from tests.gpu_util import ctx_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(p, ctx, links, tol):
+    got = ctx.chains_electric()
+    el = electric.Electric(p)
+    assert got.shape == (links.shape[0], p.n_links)
+    for c in range(links.shape[0]):
+        ref = el.f_electric(links[c])
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(got[c] - ref).max() <= tol * scale, (c, np.abs(got[c] - ref).max())
+
+
+@pytest.mark.parametrize("L,n_v,K,nch", [
+    (2, 1, 1, 3),
+    (2, 1, 3, 2),
+    (3, 1, 2, 3),
+    (2, 2, 2, 2),
+    (9, 1, 2, 2),      # 162 links: two thread blocks per chain, ragged tail
+])
+def test_fp64_initial_configurations(L, n_v, K, nch):
+    p = gi.make_problem(L, gi.Z2, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, nch, seed=31)
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=0, seed=5)
+    _check(p, ctx, links, 1e-10)
+    ctx.close()
+
+
+@pytest.mark.parametrize("delay", [1, 8])
+def test_fp64_after_sampling(delay):
+    """After sweeps (immediate and batched updates) the inverses the
+    observable reads are those of the chains' current links."""
+    p = gi.make_problem(4, gi.Z2, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 3, seed=4), precision=0, seed=11, delay=delay, refresh_every=1000)
+    ctx.sample(3)
+    links = ctx.chains_links()
+    _check(p, ctx, links, 1e-10)
+    ctx.close()
+
+
+@pytest.mark.parametrize("n_v", [1, 2])
+def test_fp32_chains(n_v):
+    p = gi.make_problem(4 if n_v == 1 else 2, gi.Z2, n_v, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=8), precision=1, seed=3, delay=8 if n_v == 1 else 1)
+    ctx.sample(2)
+    links = ctx.chains_links()
+    _check(p, ctx, links, 1e-4)
+    ctx.close()
+
+
+def test_device_output_matches_host():
+    torch = pytest.importorskip("torch")
+    p = gi.make_problem(3, gi.Z2, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=6), precision=0, seed=1)
+    host = ctx.chains_electric()
+    dev = torch.zeros((2, p.n_links, 2), dtype=torch.float64, device="cuda")
+    ctx.chains_electric(out=dev)
+    ctx.sync()
+    d = dev.cpu().numpy()
+    assert np.array_equal(d[..., 0] + 1j * d[..., 1], host)
+    ctx.close()
+
+
+def test_u1_is_rejected():
+    from paper_2412_01737_gb300 import GGFError
+    p = gi.make_problem(2, gi.U1, 1, 1)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.cold_links(p, 1), precision=0)
+    with pytest.raises(GGFError):
+        ctx.chains_electric()
+    ctx.close()
