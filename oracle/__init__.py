@@ -20,6 +20,9 @@ observables  Plaquette Wilson loops (Sec. 2.3) and integrated
          autocorrelation times.
 electric The Z2 electric (link-flip) observable of Sec. 5.3: f_E(G) from
          explicit vectors and from a Pfaffian of the composed covariance.
+fermionic  Majorana expectations of Sec. 5.2 (densities, link bilinears,
+         general monomials) from explicit vectors and from the physical
+         covariance A + B W B^T of each pair.
 
 Parity status per function is listed in each module's docstring; every
 function is pinned by a `-m "not gpu"` test except where a docstring says
