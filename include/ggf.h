@@ -199,6 +199,23 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
  * GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream);
 
+/* Fermionic observables (Sec. 5.2): Majorana bilinears on the physical
+ * modes (site s carries c_2s, c_2s+1) at the current configuration G of every
+ * chain,
+ *     site[s]              = sum_nm lambda_n^* lambda_m <psi_n|c_2s c_2s+1|psi_m> / N(G),
+ *     link[l][alpha][beta] = the same for c_{2s+alpha} c_{2t+beta}, l = (s -> t).
+ * Densities are n_s = (1 + i site[s]) / 2; hoppings psi_s^dag psi_t and
+ * pairings are linear in the link block; a gauge-invariant observable
+ * multiplies them by its string of link variables, which is diagonal in G
+ * (the per-sample product is the caller's).  Computed by Wick's theorem from
+ * the physical covariance A + B W_nm B^T of each pair (A, B the sites'
+ * physical and physical-virtual blocks; only the 8 n_v x 8 n_v block of W
+ * between the two sites is read).  Pending delayed updates are folded into W
+ * first.
+ *   site [n_chains][V][2], link [n_chains][2V][2][2][2], FP64 (re, im),
+ *   caller-owned; either may be NULL (not both). */
+ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem, void* stream);
+
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
  * L^2.  For tests and diagnostics. */

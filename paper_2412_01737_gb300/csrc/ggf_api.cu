@@ -19,6 +19,7 @@ ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64);
 ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st);
 ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
+ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -59,10 +60,10 @@ void ggf_free_chains(ggf_ctx* ctx) {
 }
 
 void ggf_free_consts(ggf_ctx* ctx) {
-    void* ptrs[] = {ctx->d_D, ctx->d_Gr, ctx->d_Gc, ctx->d_logc, ctx->d_w};
+    void* ptrs[] = {ctx->d_D, ctx->d_Gr, ctx->d_Gc, ctx->d_logc, ctx->d_w, ctx->d_Ap, ctx->d_Bp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    ctx->d_D = nullptr; ctx->d_Gr = nullptr; ctx->d_Gc = nullptr; ctx->d_logc = nullptr; ctx->d_w = nullptr;
+    ctx->d_D = nullptr; ctx->d_Ap = nullptr; ctx->d_Bp = nullptr; ctx->d_Gr = nullptr; ctx->d_Gc = nullptr; ctx->d_logc = nullptr; ctx->d_w = nullptr;
     ctx->have_gauss = false;
 }
 
@@ -764,6 +765,27 @@ ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream)
         return check_err_word(ctx);
     }
     GGF_TRY(ggf_electric(ctx, (cxd*)out, st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!site && !link) return ggf_fail(ctx, GGF_EINVAL, "site and link are both null");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t sb = (size_t)ctx->ch.n * ctx->g.V * sizeof(cxd);
+    const size_t lb = (size_t)ctx->ch.n * ctx->g.n_links * 4 * sizeof(cxd);
+    if (mem == GGF_MEM_HOST) {
+        DBuf ds, dl;
+        if (site) GGF_TRY(dalloc(ctx, ds, sb));
+        if (link) GGF_TRY(dalloc(ctx, dl, lb));
+        GGF_TRY(ggf_fermion(ctx, (cxd*)ds.p, (cxd*)dl.p, st));
+        if (site) GGF_CK(cudaMemcpyAsync(site, ds.p, sb, cudaMemcpyDeviceToHost, st));
+        if (link) GGF_CK(cudaMemcpyAsync(link, dl.p, lb, cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return check_err_word(ctx);
+    }
+    GGF_TRY(ggf_fermion(ctx, (cxd*)site, (cxd*)link, st));
     return GGF_OK;
 }
 

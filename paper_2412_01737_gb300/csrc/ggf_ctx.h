@@ -21,6 +21,8 @@ struct DevConst {
     Geometry g;
     int K, P, Kc;                 // Gaussians, pairs, complex pairs (P = K + Kc)
     const double* D;              // [V][B][B]
+    const double* Ap;             // [V][2][2]   physical block of each site
+    const double* Bp;             // [V][2][B]   physical-virtual coupling of each site
     const double* Gr;             // [K][n_links][r][r]   diagonal pairs
     const cxd* Gc;                // [Kc][n_links][r][r]  pairs n < m
     const cxd* logc;              // [P]
@@ -78,6 +80,8 @@ struct ggf_ctx {
     std::vector<int> pair_n, pair_m;
     std::vector<cxd> logc, w;
     double* d_D = nullptr;
+    double* d_Ap = nullptr;
+    double* d_Bp = nullptr;
     double* d_Gr = nullptr;
     cxd* d_Gc = nullptr;
     cxd* d_logc = nullptr;
@@ -112,7 +116,7 @@ struct ggf_ctx {
     DevConst dc() const {
         DevConst c;
         c.g = g; c.K = K; c.P = P; c.Kc = Kc;
-        c.D = d_D; c.Gr = d_Gr; c.Gc = d_Gc; c.logc = d_logc; c.w = d_w;
+        c.D = d_D; c.Ap = d_Ap; c.Bp = d_Bp; c.Gr = d_Gr; c.Gc = d_Gc; c.logc = d_logc; c.w = d_w;
         return c;
     }
 };

@@ -233,14 +233,27 @@ ggf_status ggf_build_constants(ggf_ctx* ctx, const double* gamma_site, int K,
             for (int j = 0; j < g.B; ++j)
                 D[((size_t)s * g.B + i) * g.B + j] = gamma_site[((size_t)s * m_s + 2 + i) * m_s + 2 + j];
     std::memcpy(Gr.data(), gamma_bond, Gr.size() * sizeof(double));
+    // physical block A_s (2 x 2) and physical-virtual coupling B_s (2 x B) of
+    // every site, for the fermionic observables
+    std::vector<double> Ap((size_t)g.V * 4), Bp((size_t)g.V * 2 * g.B);
+    for (int s = 0; s < g.V; ++s)
+        for (int a = 0; a < 2; ++a) {
+            for (int b = 0; b < 2; ++b) Ap[(size_t)s * 4 + a * 2 + b] = gamma_site[((size_t)s * m_s + a) * m_s + b];
+            for (int j = 0; j < g.B; ++j)
+                Bp[((size_t)s * 2 + a) * g.B + j] = gamma_site[((size_t)s * m_s + a) * m_s + 2 + j];
+        }
     GGF_CK(cudaMalloc(&ctx->d_D, D.size() * sizeof(double)));
     GGF_CK(cudaMalloc(&ctx->d_Gr, Gr.size() * sizeof(double)));
     GGF_CK(cudaMalloc(&ctx->d_Gc, Gc.size() * sizeof(cxd)));
+    GGF_CK(cudaMalloc(&ctx->d_Ap, Ap.size() * sizeof(double)));
+    GGF_CK(cudaMalloc(&ctx->d_Bp, Bp.size() * sizeof(double)));
     GGF_CK(cudaMalloc(&ctx->d_logc, P * sizeof(cxd)));
     GGF_CK(cudaMalloc(&ctx->d_w, P * sizeof(cxd)));
     GGF_CK(cudaMemcpy(ctx->d_D, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice));
     GGF_CK(cudaMemcpy(ctx->d_Gr, Gr.data(), Gr.size() * sizeof(double), cudaMemcpyHostToDevice));
     GGF_CK(cudaMemcpy(ctx->d_Gc, Gc.data(), Gc.size() * sizeof(cxd), cudaMemcpyHostToDevice));
+    GGF_CK(cudaMemcpy(ctx->d_Ap, Ap.data(), Ap.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GGF_CK(cudaMemcpy(ctx->d_Bp, Bp.data(), Bp.size() * sizeof(double), cudaMemcpyHostToDevice));
     GGF_CK(cudaMemcpy(ctx->d_logc, logc.data(), P * sizeof(cxd), cudaMemcpyHostToDevice));
     GGF_CK(cudaMemcpy(ctx->d_w, w.data(), P * sizeof(cxd), cudaMemcpyHostToDevice));
     ctx->logc = logc;

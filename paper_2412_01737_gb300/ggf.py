@@ -47,8 +47,8 @@ class ChainStats(ctypes.Structure):
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
-           "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse", "ggf_chains_electric",
-           "ggf_chains_stats", "ggf_checkpoint",
+           "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
+           "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_stats", "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
            "ggf_selftest_flush", "ggf_net_create", "ggf_net_destroy", "ggf_net_last_error", "ggf_net_get_params",
            "ggf_net_set_params", "ggf_net_logq", "ggf_net_loss_grad", "ggf_net_train", "ggf_sample_blocks"]
@@ -84,6 +84,7 @@ def load():
         "ggf_chains_ell": ([P, P, I, P], I),
         "ggf_chains_inverse": ([P, I, I, P, I, P], I),
         "ggf_chains_electric": ([P, P, I, P], I),
+        "ggf_chains_fermion": ([P, P, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -274,6 +275,21 @@ class GGF:
             return host[..., 0] + 1j * host[..., 1]
         self._ck(self.lib.ggf_chains_electric(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
         return out
+
+    def chains_fermion(self, site=None, link=None):
+        """Physical Majorana bilinears of every chain (Sec. 5.2): complex numpy
+        arrays site (n_chains, V) and link (n_chains, 2V, 2, 2); or fills the
+        given float64 buffers site [n][V][2] / link [n][2V][2][2][2] (numpy or
+        CUDA tensors, either may be None) and returns them."""
+        if site is None and link is None:
+            nl = self.n_links()
+            hs = np.zeros((self.n_chains, nl // 2, 2))
+            hl = np.zeros((self.n_chains, nl, 2, 2, 2))
+            self._ck(self.lib.ggf_chains_fermion(self.h, hs.ctypes.data, hl.ctypes.data, MEM_HOST, None))
+            return hs[..., 0] + 1j * hs[..., 1], hl[..., 0] + 1j * hl[..., 1]
+        self._ck(self.lib.ggf_chains_fermion(self.h, _ptr(site)[0], _ptr(link)[0], self._mem(site, link),
+                                             _stream([site, link])))
+        return site, link
 
     def chains_inverse(self, chain, pair, N):
         out = np.zeros((N, N, 2))

@@ -1,4 +1,6 @@
-"""The algebra of the GPU electric-observable kernel, in numpy.
+"""The algebra of the GPU observable kernels (electric, fermionic), in numpy.
+
+Electric (Z2 link flip, Sec. 5.3):
 
 The kernel works on the reduced virtual-mode matrix with the twist on the
 bond side, M = D + O Gamma_X O^T, W = M^{-1}, and for link l with source-end
@@ -10,6 +12,9 @@ from the B x r block of W between the source site and the link only, with the
 These checks restate that recipe and compare it with the oracle's f_E (which
 has the twist on the site side and the full covariance route), and check the
 two facts it rests on: the block restriction and M_mn = conj(M_nm).
+
+Fermionic (Sec. 5.2): the physical covariance A + B W B^T of each pair from
+the B x B block of W between two sites, A and B untwisted.
 """
 import numpy as np
 import pytest
@@ -90,3 +95,54 @@ def test_block_restriction_is_exact():
         blk = (one[S][:, site] + 1j * D[np.ix_(S, site)]) @ W[np.ix_(site, lk)] @ \
               (one[np.ix_(lk, S)] + 1j * tw[0, 0][np.ix_(lk, S)])
         assert np.abs(blk - full[np.ix_(S, S)]).max() <= 1e-12 * np.abs(full).max()
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", [(3, gi.Z2, 1, 2), (2, gi.U1, 1, 3), (2, gi.U1, 2, 2)])
+def test_fermion_block_recipe_matches_oracle(L, grp, n_v, K):
+    """The fermionic kernel's recipe: Gamma_eff^nm[a, b] = A_s (s = t) +
+    B_s W_nm[site s, site t] B_t^T with untwisted A, B and the bond-side twist;
+    the (m, n) order of a pair uses the conjugate of the same product."""
+    from oracle import fermionic
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    fe, Wt = fermionic.Fermionic(p), weight.Weights(p)
+    B = 8 * n_v
+    virt = np.array([i for i in range(p.m_s * p.V) if i % p.m_s >= 2])
+    for links in gi.random_links(p, 2, seed=23):
+        O = weight.twist_matrix(p, links)[np.ix_(virt, virt)]
+        D = np.zeros((B * p.V, B * p.V))
+        for s in range(p.V):
+            D[s * B:(s + 1) * B, s * B:(s + 1) * B] = p.gamma_site[s][2:, 2:]
+        lnm = Wt.log_n_matrix(links)
+        Nnm = np.exp(lnm - lnm.real.max())
+        acc = np.zeros((p.n_links, 2, 2), dtype=complex)
+        acc_site = np.zeros(p.V, dtype=complex)
+        den = 0.0
+        for n in range(p.K):
+            for m in range(n, p.K):
+                GX = Wt.GX[n, m][np.ix_(virt, virt)]
+                Wnm = np.linalg.inv(D + O @ GX @ O.T)
+                wnm = np.conj(p.lam[n]) * p.lam[m] * Nnm[n, m]
+
+                def X(s, t, Wm):
+                    Bs, Bt = p.gamma_site[s][:2, 2:], p.gamma_site[t][:2, 2:]
+                    return Bs @ Wm[s * B:(s + 1) * B, t * B:(t + 1) * B] @ Bt.T
+                terms = [(wnm, Wnm, False)] + ([(np.conj(wnm), Wnm, True)] if m > n else [])
+                for wt, Wm, cj in terms:
+                    den += wt.real
+                    for s in range(p.V):
+                        x = X(s, s, Wm)
+                        acc_site[s] += wt * (x.conj() if cj else x)[0, 1]
+                    for l in range(p.n_links):
+                        s, t = fermionic._link_sites(p, l)
+                        x = X(s, t, Wm)
+                        acc[l] += wt * (x.conj() if cj else x)
+        site = -1j * (acc_site / den + np.array([p.gamma_site[s][0, 1] for s in range(p.V)]))
+        link = -1j * acc / den
+        for l in range(p.n_links):
+            s, t = fermionic._link_sites(p, l)
+            if s == t:
+                link[l] += -1j * p.gamma_site[s][:2, :2]
+                link[l][0, 0] = link[l][1, 1] = 1.0
+        rs, rl = fe.bilinears(links)
+        assert np.abs(site - rs).max() <= 1e-11
+        assert np.abs(link - rl).max() <= 1e-11

@@ -1,7 +1,7 @@
-"""GPU parity of the Z2 electric (link-flip) observable of Sec. 5.3.
-
-ggf_chains_electric evaluates f_E(G)_l for every chain and link from the
-chains' cached inverses; the oracle evaluates it by the full covariance route
+"""GPU parity of the per-configuration observables computed from the chains'
+cached inverses: the Z2 electric (link-flip) observable of Sec. 5.3
+(ggf_chains_electric) and the fermionic bilinears of Sec. 5.2
+(ggf_chains_fermion).  The oracle evaluates both by the full covariance route
 (itself pinned to explicit Fock vectors).  FP64 chains agree to 1e-10
 relative, FP32 chains to 1e-4.
 """
@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import ggf_inputs as gi
-from oracle import electric
+from oracle import electric, fermionic
 from tests.gpu_util import ctx_for
 
 pytestmark = pytest.mark.gpu
@@ -86,4 +86,54 @@ def test_u1_is_rejected():
     ctx.chains_init(gi.cold_links(p, 1), precision=0)
     with pytest.raises(GGFError):
         ctx.chains_electric()
+    ctx.close()
+
+
+def _check_fermion(p, ctx, links, tol):
+    site, link = ctx.chains_fermion()
+    fe = fermionic.Fermionic(p)
+    assert site.shape == (links.shape[0], p.V) and link.shape == (links.shape[0], p.n_links, 2, 2)
+    for c in range(links.shape[0]):
+        rs, rl = fe.bilinears(links[c])
+        assert np.abs(site[c] - rs).max() <= tol, (c, np.abs(site[c] - rs).max())
+        assert np.abs(link[c] - rl).max() <= tol, (c, np.abs(link[c] - rl).max())
+
+
+@pytest.mark.parametrize("L,grp,n_v,K,nch", [
+    (2, gi.Z2, 1, 2, 2),
+    (3, gi.U1, 1, 3, 2),
+    (2, gi.U1, 2, 2, 2),
+    (1, gi.Z2, 1, 2, 2),     # self-links: both Majoranas of a link on one site
+    (9, gi.Z2, 1, 1, 2),     # 243 items: two thread blocks per chain, ragged tail
+])
+def test_fermion_fp64_initial_configurations(L, grp, n_v, K, nch):
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, nch, seed=41)
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=0, seed=5)
+    _check_fermion(p, ctx, links, 1e-10)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,delay,tol", [(0, 4, 1e-10), (1, 8, 1e-4)])
+def test_fermion_after_sampling(precision, delay, tol):
+    p = gi.make_problem(4, gi.U1, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=4), precision=precision, seed=13, delay=delay)
+    ctx.sample(2)
+    _check_fermion(p, ctx, ctx.chains_links(), tol)
+    ctx.close()
+
+
+def test_fermion_site_only_and_device_buffers():
+    torch = pytest.importorskip("torch")
+    p = gi.make_problem(3, gi.Z2, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=6), precision=0, seed=1)
+    hs, hl = ctx.chains_fermion()
+    ds = torch.zeros((2, p.V, 2), dtype=torch.float64, device="cuda")
+    ctx.chains_fermion(site=ds)
+    ctx.sync()
+    d = ds.cpu().numpy()
+    assert np.array_equal(d[..., 0] + 1j * d[..., 1], hs)
     ctx.close()
