@@ -183,19 +183,24 @@ ggf_status ggf_chains_links(ggf_ctx* ctx, void* links, int mem, void* stream);
 /* Tracked log Pf(M_nm) of all chains, [n_chains][P][2] as (log|Pf|, arg). */
 ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
 
-/* Electric (link-flip) observable of a Z2 gauge field (Sec. 5.3) at the
- * current configuration G of every chain:
- *     f_E(G)_l = sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(G^(l))> / N(G),
- * G^(l) being G with link l flipped.  The mean of f_E over samples of p(G)
- * estimates <X_l>, X_l the flip of link l (the Z2 electric term of a link is
- * a linear function of X_l).  Computed from the cached inverses: flipping g_l
- * multiplies the state by the parity of the link's source-end modes S, so
- * each pair contributes (-1)^{n_v} Pf(Gamma_O[S, S]) with Gamma_O =
- * i 1 - (1 + i D) W_nm (1 + i O Gamma_X O^T) (Wick's theorem; only the
- * 8 n_v x 4 n_v block of W between the source site and the link is read).
- * Pending delayed updates are folded into W first.
- *   out [n_chains][2V][2] FP64 (re, im), caller-owned.
- * GGF_EINVAL for U(1) chains (the integral over g of Sec. 5.3 is not built),
+/* Electric-field observables (Sec. 5.3) at the current configuration G of
+ * every chain: the per-configuration factor f_E(G)_l of the single-link
+ * integral, whose mean over samples of p(G) estimates the link's electric
+ * term:
+ *   Z2:   f_E(G)_l = sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(G^(l))> / N(G),
+ *         G^(l) = G with link l flipped: the flip X_l, of which the Z2
+ *         electric term is a linear function;
+ *   U(1): f_E(G)_l = -d^2/dtheta'^2 of sum_nm lambda_n^* lambda_m
+ *         <psi_n(G)|psi_m(theta'; G)> / N(G) at theta' = theta_l: the Casimir
+ *         J_l^2 (J = -i d/dtheta), i.e. the twist charge Q_l = sum_j q_j n_j
+ *         of the link's source-end modes squared, inserted on the ket.
+ * Computed from the cached inverses by Wick's theorem on the covariance
+ * Gamma_O = i 1 - (1 + i D) W_nm (1 + i O Gamma_X O^T) restricted to the
+ * source-end Majoranas S (Z2: (-1)^{n_v} Pf(Gamma_O[S, S]); U(1): <Q_l^2>
+ * from Gamma_O[S, S]); only the 8 n_v x 4 n_v block of W between the source
+ * site and the link is read.  Pending delayed updates are folded into W first.
+ *   out [n_chains][2V][2] FP64 (re, im), caller-owned.  A single
+ *   configuration's value is complex; its average over p(G) is real.
  * GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream);
 

@@ -1,39 +1,54 @@
-"""Electric-field observable of a Z2 gauge field (Sec. 5.3).
+"""Electric-field observables of Sec. 5.3: the Z2 link flip and the U(1)
+Casimir J_l^2.
 
-For Z2 the electric operator of link l acts in the group-element basis as the
-flip X_l |G> = |G^(l)>, G^(l) being G with g_l -> -g_l (the electric energy of
-the link is a linear function of X_l; its normalisation and sign belong to the
-Hamiltonian, not to the state).  Sec. 5.3 writes <X_l> = sum_G p(G) f_E(G) with
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-    f_E(G) = sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(G^(l))> / N(G),
+Sec. 5.3 writes <J_l^2> = sum_G p(G) f_E(G) with the single-link integral
+    f_E(G) = int dg <G|J_l^2|g; G> sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(g; G)> / N(G),
+|g; G> being G with link l set to g.
 
-a bra/ket-asymmetric overlap, since <G|X_l|G~> vanishes unless G~ = G^(l).
+Z2: the electric term of a link is a linear function of the flip X_l
+|G> = |G^(l)> (G^(l): g_l -> -g_l), so the integral has the diagonal term
+(value 1) and the flip term
+    f_X(G) = sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(G^(l))> / N(G),
+which is what this module returns for Z2 (the Hamiltonian's coefficients are
+left out).
+
+U(1): in the angle basis J = -i d/dtheta, so the integral is -d^2/dtheta'^2 of
+the ket's overlap at theta' = theta_l.  The ket depends on theta' only
+through the twist exp(i theta' Q_l) of the source-end modes,
+Q_l = sum_j q_j n_j, so the overlap is a trigonometric polynomial with
+frequencies |Q| <= n_v and
+    f_E(G) = sum_nm lambda_n^* lambda_m <psi_n(G)| Q_l^2 |psi_m(G)>_ket / N(G),
+Q_l^2 inserted on the ket's source-end modes before the contraction.
 
 Two routes:
 
-1. Fock (the definition, tiny lattices): explicit vectors psi_n(G) from
-   oracle.fock.
-2. Covariance: psi_m(G^(l)) = <B_m| U(G) P_l |A>, where P_l is the parity of
-   the modes of the source end of link l (the end that carries the twist),
-   P_l = prod_j (-i c_2j c_2j+1) over that end's n_v modes.  Hence
-       R_nm = <psi_n(G)|psi_m(G^(l))> / <psi_n(G)|psi_m(G)>
-   is the expectation of P_l (on the right) in the Gaussian operator
-   sigma_G X_nm, sigma_G the reduced state of the twisted sites on the virtual
-   modes (covariance D_G, the virtual block of Gamma_{A(G)}) and X_nm the bond
-   operator of covariance Gamma_X (as in oracle.weight).  By Wick's theorem,
-   with <c_a c_b> = delta_ab - i Gamma_ab,
-       R_nm = (-1)^{n_v} Pf(Gamma_O[S, S])
-   over the 2 n_v Majoranas S of that end, and composing the two Gaussian
-   operators (Gamma_X^2 = -1) gives
-       Gamma_O = i 1 - (1 + i D_G) W (1 + i Gamma_X),  W = (D_G + Gamma_X)^{-1}.
-   Then f_E(G) = sum_nm lambda_n^* lambda_m N_nm(G) R_nm / N(G) with N_nm(G)
-   from oracle.weight.
+1. Fock (the definition, tiny lattices): explicit vectors.  Z2: psi(G^(l)).
+   U(1): the single-link integral itself, by quadrature over theta' on a
+   grid of 8 angles, exact for frequencies |Q| <= 3.
+2. Covariance: the insertion acts on the source-end Majoranas S of link l
+   (the end that carries the twist).  Composing the sites' virtual state
+   (covariance D_G, the virtual block of Gamma_{A(G)}) with the bond operator
+   X_nm (covariance Gamma_X, Gamma_X^2 = -1) gives a Gaussian operator whose
+   normalised covariance is
+       Gamma_O = i 1 - (1 + i D_G) W (1 + i Gamma_X),  W = (D_G + Gamma_X)^{-1},
+   and Wick's theorem with <c_a c_b> = -i Gamma_O[a, b] (a != b) gives
+     Z2:   R_nm = (-1)^{n_v} Pf(Gamma_O[S, S])   (the parity of the end),
+     U(1): R_nm = <Q_l^2> = sum_j q_j^2 <n_j> + 2 sum_{j<k} q_j q_k <n_j n_k>,
+           <n_j> = (1 + G_{2j,2j+1}) / 2,
+           <n_j n_k> = (1 + G_{2j,2j+1} + G_{2k,2k+1} + Pf G[2j,2j+1,2k,2k+1]) / 4,
+   G = Gamma_O[S, S].  Then f = sum_nm lambda_n^* lambda_m N_nm(G) R_nm / N(G)
+   with N_nm(G) from oracle.weight.
 
-Pinned (tests/test_oracle_electric.py): the covariance route against the Fock
-route on 2x2 Z2 lattices (K = 1, 2; every link; random configurations) and
-on the 1x1 torus with n_v = 2 (every configuration);
-gauge invariance of f_E; the exhaustive <X_l> on the 2x2 lattice is real and
-at most 1 in modulus.
+Pinned (tests/test_oracle_electric.py): Z2: the covariance route against the
+Fock route on 2x2 lattices (K = 1, 2; every link; random configurations) and
+on the 1x1 torus with n_v = 2 (every configuration); gauge invariance; the
+exhaustive <X_l> on the 1x1 torus against explicit vectors, and on the 2x2
+lattice real and at most 1 in modulus.  U(1): the covariance route against
+the quadrature of the definition (2x2, K = 1, 2; 1x1, n_v = 2); gauge
+invariance; <J_l^2> over p(G) on the 1x1 torus (exact product quadrature) is
+real and non-negative.
 """
 from __future__ import annotations
 
@@ -42,7 +57,8 @@ import numpy as np
 from . import fock, weight
 from .pfaffian import pfaffian
 
-Z2 = 0
+Z2, U1 = 0, 1
+N_QUAD = 8
 
 
 def flipped(links: np.ndarray, l: int) -> np.ndarray:
@@ -59,12 +75,28 @@ def f_electric_fock(fp: fock.FockPEPS, links: np.ndarray, l: int) -> complex:
     return complex(np.vdot(v, w) / np.vdot(v, v))
 
 
+def f_electric_u1_fock(fp: fock.FockPEPS, links: np.ndarray, l: int) -> complex:
+    """U(1) f_E(G) for link l: the single-link integral of <G|J^2|g; G>
+    against the overlap, by quadrature over the ket's angle (the overlap is a
+    trigonometric polynomial of degree <= n_v <= 2, so 8 points are exact)."""
+    p = fp.p
+    lam = p.lam
+    v = (lam[:, None] * fp.psi(links)).sum(axis=0)
+    th = 2.0 * np.pi * np.arange(N_QUAD) / N_QUAD
+    phi = np.zeros(N_QUAD, dtype=complex)
+    for k, t in enumerate(th):
+        g = np.array(links, dtype=float).copy()
+        g[l] = t
+        phi[k] = np.vdot(v, (lam[:, None] * fp.psi(g)).sum(axis=0))
+    Q = np.fft.fftfreq(N_QUAD, 1.0 / N_QUAD)           # integer frequencies
+    c = np.fft.fft(phi) / N_QUAD                        # phi(t) = sum_Q c_Q e^{i Q t}
+    return complex(np.sum(Q ** 2 * c * np.exp(1j * Q * links[l])) / np.vdot(v, v))
+
+
 class Electric:
-    """Covariance route to f_E(G) for every link of a Z2 problem."""
+    """Covariance route to f_E(G) for every link (Z2 flip or U(1) J^2)."""
 
     def __init__(self, p):
-        if p.group != Z2:
-            raise ValueError("the link-flip observable is defined for Z2")
         self.p = p
         self.W = weight.Weights(p)
         m_s = p.m_s
@@ -76,7 +108,8 @@ class Electric:
         self.GX = {nm: g[np.ix_(self.virt, self.virt)] for nm, g in self.W.GX.items()}
 
     def ratios(self, links: np.ndarray) -> np.ndarray:
-        """R[n, m, l] = <psi_n(G)|psi_m(G^(l))> / <psi_n(G)|psi_m(G)>."""
+        """R[n, m, l]: the insertion's normalised expectation for pair (n, m);
+        Z2: <psi_n(G)|psi_m(G^(l))> / <psi_n(G)|psi_m(G)>."""
         p = self.p
         O = weight.twist_matrix(p, links)
         D = (O.T @ self.W.GA @ O)[np.ix_(self.virt, self.virt)]
@@ -89,8 +122,23 @@ class Electric:
                 GO = 1j * one - (one + 1j * D) @ Wi @ (one + 1j * GX)
                 for l in range(p.n_links):
                     s = self.S[l]
-                    out[n, m, l] = (-1) ** p.n_v * pfaffian(GO[np.ix_(s, s)])
+                    out[n, m, l] = self._insertion(GO[np.ix_(s, s)])
         return out
+
+    def _insertion(self, G) -> complex:
+        """Normalised expectation of the insertion on one source end."""
+        p = self.p
+        if p.group == Z2:
+            return (-1) ** p.n_v * pfaffian(G)
+        q = p.q_src
+        occ = [(1.0 + G[2 * j, 2 * j + 1]) / 2.0 for j in range(p.n_v)]
+        val = sum(q[j] ** 2 * occ[j] for j in range(p.n_v))
+        for j in range(p.n_v):
+            for k in range(j + 1, p.n_v):
+                ix = [2 * j, 2 * j + 1, 2 * k, 2 * k + 1]
+                pair = (1.0 + G[2 * j, 2 * j + 1] + G[2 * k, 2 * k + 1] + pfaffian(G[np.ix_(ix, ix)])) / 4.0
+                val = val + 2 * q[j] * q[k] * pair
+        return val
 
     def f_electric(self, links: np.ndarray) -> np.ndarray:
         """f_E(G) for every link (complex; its expectation over p(G) is real)."""
@@ -103,7 +151,8 @@ class Electric:
         return np.einsum("nm,nml->l", w, R) / w.sum()
 
     def expectation_exhaustive(self, configs: np.ndarray) -> np.ndarray:
-        """<X_l> = sum_G p(G) f_E(G) over an explicit list of configurations."""
+        """sum_G p(G) f_E(G) over an explicit list of configurations (Z2: all
+        of them; U(1): a product grid that integrates exactly)."""
         num = np.zeros(self.p.n_links, dtype=complex)
         logs, fs = [], []
         for G in configs:

@@ -751,8 +751,6 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream) {
 ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream) {
     GGF_TRY(require(ctx, true, true));
     if (!out) return ggf_fail(ctx, GGF_EINVAL, "null out");
-    if (ctx->g.group != GGF_Z2)
-        return ggf_fail(ctx, GGF_EINVAL, "the link-flip electric observable is defined for Z2 links");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)ctx->ch.n * ctx->g.n_links * sizeof(cxd);

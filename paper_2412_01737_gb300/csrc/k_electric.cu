@@ -1,16 +1,24 @@
-// Electric (link-flip) observable of a Z2 gauge field (Sec. 5.3), evaluated
-// for every chain and link from the inverses W_nm = M_nm(G)^{-1} the sampler
-// keeps.
-//
-// For Z2 the electric term of link l is a linear function of the flip
-// X_l |G> = |G^(l)>, and Sec. 5.3 needs
-//   f_E(G)_l = sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(G^(l))> / N(G).
-// Flipping g_l multiplies the twisted state by the parity of the source-end
-// modes of l (the end that carries the twist), a product of the 2 n_v
-// Majoranas S of that end.  Wick's theorem on the Gaussian operator composed
-// of the sites' virtual state and the bond operator X_nm then gives
-//   R_nm = <psi_n(G)|psi_m(G^(l))> / <psi_n(G)|psi_m(G)> = (-1)^{n_v} Pf(Gamma_O[S, S]),
-//   Gamma_O = i 1 - (1 + i D) W_nm (1 + i Gamma_tw),
+// Electric-field observables (Sec. 5.3), evaluated for every chain and link
+// from the inverses W_nm = M_nm(G)^{-1} the sampler keeps:
+//   f_E(G)_l = sum_nm lambda_n^* lambda_m <psi_n(G)| I_l |psi_m(G)>_ket / N(G),
+// with the insertion I_l acting on the ket's source-end modes of link l (the
+// end that carries the twist) before the contraction:
+//   Z2:   I_l = the parity of those modes, so that the ket becomes psi_m(G^(l))
+//         (the flip X_l of the link, of which the Z2 electric term is a
+//         linear function);
+//   U(1): I_l = Q_l^2, Q_l = sum_j q_j n_j the twist charge of those modes: the
+//         ket depends on its link angle through exp(i theta Q_l), so the
+//         single-link integral with <G|J^2|g; G> (J = -i d/dtheta) is
+//         -d^2/dtheta^2 of the overlap, i.e. the insertion of Q_l^2.
+// Wick's theorem on the Gaussian operator composed of the sites' virtual
+// state and the bond operator X_nm gives the insertion's normalised
+// expectation from the covariance of that operator on the end's 2 n_v
+// Majoranas S,
+//   Gamma_O = i 1 - (1 + i D) W_nm (1 + i Gamma_tw),   G = Gamma_O[S, S],
+//   Z2:   R_nm = (-1)^{n_v} Pf(G),
+//   U(1): R_nm = sum_j q_j^2 <n_j> + 2 sum_{j<k} q_j q_k <n_j n_k>,
+//         <n_j> = (1 + G_{2j,2j+1}) / 2,
+//         <n_j n_k> = (1 + G_{2j,2j+1} + G_{2k,2k+1} + Pf G[2j, 2j+1, 2k, 2k+1]) / 4,
 // with M_nm = D + Gamma_tw, D the sites' virtual blocks and Gamma_tw =
 // O(G) Gamma_X O(G)^T the twisted link blocks.  D is block diagonal by site
 // and Gamma_tw by link, so [(1 + i D) W (1 + i Gamma_tw)]_SS involves only the
@@ -39,11 +47,34 @@ __device__ __forceinline__ cxd small_pf<4>(const cxd (&A)[4][4]) {
 
 __device__ __forceinline__ cxd times_i(cxd v) { return {-v.y, v.x}; }
 
+// Normalised expectation of the insertion from G = Gamma_O[S, S].
+template <int H>
+__device__ __forceinline__ cxd insertion(const Geometry& g, const cxd (&G)[H][H]) {
+    if (g.group == GGF_Z2) {
+        const double sg = (H / 2) % 2 ? -1.0 : 1.0;    // (-1)^{n_v}
+        return sg * small_pf<H>(G);
+    }
+    cxd val = {0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < H / 2; ++j) {
+        const double qj = g.q[j];
+        cxd occ = G[2 * j][2 * j + 1];
+        occ.x += 1.0;
+        val += (0.5 * qj * qj) * occ;
+    }
+    if (H == 4) {
+        cxd pr = G[0][1] + G[2][3] + small_pf<H>(G);
+        pr.x += 1.0;
+        val += (0.5 * g.q[0] * g.q[1]) * pr;            // 2 q_0 q_1 <n_0 n_1>
+    }
+    return val;
+}
+
 // R for both orders of pair p at link l: Rf from (W, Gamma_tw), Rr from their
 // conjugates.  W points at the pair's N x N inverse (row-major).
 template <class T, int H>
-__device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* W, int l, double gval, cxd& Rf,
-                            cxd& Rr) {
+__device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* W, int l, double gval,
+                            double theta, cxd& Rf, cxd& Rr) {
     constexpr int R = 2 * H, B = 4 * H;
     const Geometry& g = dc.g;
     int a0, b0;
@@ -63,8 +94,8 @@ __device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* 
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             cxd gt;
-            if (cplx_pair) gt = twisted<cxd>(dc, p - dc.K, l, j, b, gval, 0.0);
-            else gt = cxd{twisted<double>(dc, p, l, j, b, gval, 0.0), 0.0};
+            if (cplx_pair) gt = twisted<cxd>(dc, p - dc.K, l, j, b, gval, theta);
+            else gt = cxd{twisted<double>(dc, p, l, j, b, gval, theta), 0.0};
             cf[j] = times_i(gt);
             cr[j] = times_i(conjg(gt));
             if (j == b) { cf[j].x += 1.0; cr[j].x += 1.0; }
@@ -96,22 +127,22 @@ __device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* 
             Xr[a][b] = -Xr[a][b];
             if (a == b) { Xf[a][b].y += 1.0; Xr[a][b].y += 1.0; }
         }
-    const double sg = (H / 2) % 2 ? -1.0 : 1.0;    // (-1)^{n_v}
-    Rf = sg * small_pf<H>(Xf);
-    Rr = sg * small_pf<H>(Xr);
+    Rf = insertion<H>(g, Xf);
+    Rr = insertion<H>(g, Xr);
 }
 
 // One thread per (chain, link); out[c][l] = f_E(G_c)_l.
 template <class RW, class CW, int H>
 __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_chains, int blocks_per_chain,
-                                                            const int8_t* links, const RW* Wr, const CW* Wc,
+                                                            const void* links, const RW* Wr, const CW* Wc,
                                                             const cxd* ell, cxd* out) {
     const Geometry& g = dc.g;
     const int c = blockIdx.x / blocks_per_chain;
     const int l = (blockIdx.x - c * blocks_per_chain) * ETHREADS + threadIdx.x;
     if (c >= n_chains || l >= g.n_links) return;
     const size_t NN = (size_t)g.N * g.N;
-    const double gval = (double)links[(size_t)c * g.n_links + l];
+    double gval, theta;
+    link_value<double>(dc, links, c, l, gval, theta);
     const cxd* el = ell + (size_t)c * dc.P;
     double amax = -INFINITY;
     for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
@@ -126,11 +157,11 @@ __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_c
         den += E.x;
         cxd Rf, Rr;
         if (cplx) {
-            flip_ratios<CW, H>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, Rf, Rr);
+            flip_ratios<CW, H>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, theta, Rf, Rr);
             // w_p = 2 lambda_n^* lambda_m: the (n, m) term takes E / 2, the (m, n) term its conjugate
             num += 0.5 * (E * Rf) + 0.5 * (conjg(E) * Rr);
         } else {
-            flip_ratios<RW, H>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, Rf, Rr);
+            flip_ratios<RW, H>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, theta, Rf, Rr);
             num += E * Rf;
         }
     }
@@ -141,19 +172,18 @@ __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_c
 
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
 
-// f_E for every chain and link into d_out [n_chains][n_links] (device).
+// f_E for every chain and link into d_out [n_chains][n_links] (device):
+// Z2 the flip, U(1) the Casimir J^2.
 ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
-    if (g.group != GGF_Z2)
-        return ggf_fail(ctx, GGF_EINVAL, "the link-flip electric observable is defined for Z2 links");
     // pending delayed updates first, so that W is the inverse at the current links
     GGF_TRY(ggf_flush(ctx, st));
     const int bpc = (g.n_links + ETHREADS - 1) / ETHREADS;
     const long long blocks = (long long)bpc * ch.n;
     if (blocks > 0x7fffffffLL) return ggf_fail(ctx, GGF_EINVAL, "too many chains for one launch");
     const bool fp64 = ch.opts.precision == GGF_FP64;
-    const int8_t* lk = (const int8_t*)ch.links;
+    const void* lk = ch.links;
 #define GGF_EL(RW, CW, H)                                                                                \
     electric_kernel<RW, CW, H><<<(unsigned)blocks, ETHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, lk,          \
                                                                       (const RW*)ch.Wr, (const CW*)ch.Wc, \

@@ -266,9 +266,9 @@ class GGF:
         return out[..., 0] + 1j * out[..., 1]
 
     def chains_electric(self, out=None):
-        """f_E(G)_l of every chain and link (Z2 link flip, Sec. 5.3): complex
-        numpy array (n_chains, 2V), or fills `out` (float64 [n_chains][2V][2],
-        numpy or CUDA tensor) and returns it."""
+        """f_E(G)_l of every chain and link (Sec. 5.3; Z2: the link flip,
+        U(1): the Casimir J^2): complex numpy array (n_chains, 2V), or fills
+        `out` (float64 [n_chains][2V][2], numpy or CUDA tensor) and returns it."""
         if out is None:
             host = np.zeros((self.n_chains, self.n_links(), 2))
             self._ck(self.lib.ggf_chains_electric(self.h, host.ctypes.data, MEM_HOST, None))

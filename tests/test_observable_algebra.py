@@ -1,12 +1,12 @@
 """The algebra of the GPU observable kernels (electric, fermionic), in numpy.
 
-Electric (Z2 link flip, Sec. 5.3):
+Electric (Sec. 5.3; Z2 link flip, U(1) Casimir):
 
 The kernel works on the reduced virtual-mode matrix with the twist on the
 bond side, M = D + O Gamma_X O^T, W = M^{-1}, and for link l with source-end
 Majoranas S computes
-    R_nm = (-1)^{n_v} Pf(Gamma_O[S, S]),
     Gamma_O[S, S] = i 1 - (1 + i D)[S, site] W[site, link] (1 + i O Gamma_X O^T)[link, S]
+and from it R_nm = (-1)^{n_v} Pf(Gamma_O[S, S]) (Z2) or <Q_l^2> (U(1)),
 from the B x r block of W between the source site and the link only, with the
 (m, n) order of a pair n < m taken from conj(W_nm) and conj(Gamma_X^nm).
 These checks restate that recipe and compare it with the oracle's f_E (which
@@ -33,26 +33,31 @@ def _gpu_picture(p, links):
     for s in range(p.V):
         D[s * B:(s + 1) * B, s * B:(s + 1) * B] = p.gamma_site[s][2:, 2:]
     idx = [pos[np.array(ix)] for ix in weight.link_majoranas(p)]
-    o = np.ones(N)
-    for l in range(p.n_links):
-        o[idx[l][:h2]] = links[l]          # the source end carries the twist
+    O = weight.twist_matrix(p, links)[np.ix_(virt, virt)]   # acts on source ends only
     bd = weight.BondData(p)
-    tw = {nm: o[:, None] * bd.embedded(*nm)[np.ix_(virt, virt)] * o[None, :]
+    tw = {nm: O @ bd.embedded(*nm)[np.ix_(virt, virt)] @ O.T
           for nm in [(n, m) for n in range(p.K) for m in range(p.K)]}
     return D, tw, idx, B, h2
 
 
-def _kernel_ratio(D, W, Gtw, S, site, lk, n_v):
+def _kernel_ratio(p, D, W, Gtw, S, site, lk):
     h2 = S.size
     left = np.eye(D.shape[0])[S][:, site] + 1j * D[np.ix_(S, site)]
     right = np.eye(D.shape[0])[np.ix_(lk, S)] + 1j * Gtw[np.ix_(lk, S)]
-    X = left @ W[np.ix_(site, lk)] @ right
-    return (-1) ** n_v * pfaffian.pfaffian(1j * np.eye(h2) - X)
+    G = 1j * np.eye(h2) - left @ W[np.ix_(site, lk)] @ right
+    if p.group == gi.Z2:
+        return (-1) ** p.n_v * pfaffian.pfaffian(G)
+    q = p.q_src
+    val = sum(q[j] ** 2 * (1 + G[2 * j, 2 * j + 1]) / 2 for j in range(p.n_v))
+    if p.n_v == 2:
+        val += 2 * q[0] * q[1] * (1 + G[0, 1] + G[2, 3] + pfaffian.pfaffian(G)) / 4
+    return val
 
 
-@pytest.mark.parametrize("L,n_v,K", [(3, 1, 2), (2, 1, 3), (2, 2, 2)])
-def test_block_recipe_matches_oracle(L, n_v, K):
-    p = gi.make_problem(L, gi.Z2, n_v, K, bond_scale=0.3)
+@pytest.mark.parametrize("L,grp,n_v,K", [(3, gi.Z2, 1, 2), (2, gi.Z2, 1, 3), (2, gi.Z2, 2, 2),
+                                         (3, gi.U1, 1, 2), (2, gi.U1, 2, 3)])
+def test_block_recipe_matches_oracle(L, grp, n_v, K):
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
     el, Wt = electric.Electric(p), weight.Weights(p)
     for links in gi.random_links(p, 2, seed=17):
         D, tw, idx, B, h2 = _gpu_picture(p, links)
@@ -69,10 +74,10 @@ def test_block_recipe_matches_oracle(L, n_v, K):
                     s = l // 2
                     site = np.arange(s * B, (s + 1) * B)
                     S, lk = idx[l][:h2], idx[l]
-                    Rf = _kernel_ratio(D, Wnm, tw[n, m], S, site, lk, n_v)
+                    Rf = _kernel_ratio(p, D, Wnm, tw[n, m], S, site, lk)
                     f[l] += np.conj(p.lam[n]) * p.lam[m] * Nnm[n, m] * Rf
                     if m > n:
-                        Rr = _kernel_ratio(D, Wnm.conj(), tw[n, m].conj(), S, site, lk, n_v)
+                        Rr = _kernel_ratio(p, D, Wnm.conj(), tw[n, m].conj(), S, site, lk)
                         f[l] += np.conj(p.lam[m]) * p.lam[n] * Nnm[m, n] * Rr
         f /= np.einsum("n,m,nm->", np.conj(p.lam), p.lam, Nnm)
         ref = el.f_electric(links)

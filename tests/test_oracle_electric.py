@@ -1,7 +1,9 @@
-"""Pins of the Z2 electric (link-flip) observable of Sec. 5.3 in the oracle.
+"""Pins of the electric observables of Sec. 5.3 in the oracle (Z2 link flip,
+U(1) Casimir).
 
-The covariance route (a Pfaffian of the composed covariance on one link end)
-is checked against explicit Fock-space vectors, which are the definition.
+The covariance route (Wick's theorem on the composed covariance of one link
+end) is checked against explicit Fock-space vectors, which are the
+definition (for U(1) the single-link integral itself, by exact quadrature).
 """
 import numpy as np
 import pytest
@@ -81,7 +83,34 @@ def test_gauge_invariance_and_bounds_2x2():
     assert np.abs(x.real).max() > 0.05
 
 
-def test_u1_rejected():
-    p = gi.make_problem(2, gi.U1, 1, 1)
-    with pytest.raises(ValueError):
-        electric.Electric(p)
+@pytest.mark.parametrize("L,n_v,K", [(2, 1, 1), (2, 1, 2), (1, 2, 1), (1, 2, 2)])
+def test_u1_covariance_route_matches_quadrature(L, n_v, K):
+    """U(1): <Q_l^2> from Gamma_O against the single-link integral of
+    <G|J^2|g; G> with the overlap, by exact quadrature on explicit vectors."""
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    fp, el = fock.FockPEPS(p), electric.Electric(p)
+    # on 2x2 an x link and a y link from each sublattice (each needs 8 contractions)
+    ls = [0, 3, 5, 6] if L == 2 else list(range(p.n_links))
+    for G in gi.random_links(p, 1 if L == 2 else 3, seed=5):
+        ref = np.array([electric.f_electric_u1_fock(fp, G, l) for l in ls])
+        assert np.abs(ref).max() > 0.1
+        assert np.abs(el.f_electric(G)[ls] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_u1_gauge_invariance_and_positive_casimir():
+    p = gi.make_problem(2, gi.U1, 1, 2, bond_scale=0.3)
+    el = electric.Electric(p)
+    G = gi.random_links(p, 2, seed=9)
+    alpha = np.array([0.3, -1.1, 2.0, 0.7])
+    for a, b in zip(G, gi.gauge_transform(p, G, alpha)):
+        fa, fb = el.f_electric(a), el.f_electric(b)
+        assert np.abs(fa - fb).max() <= 1e-12 * np.abs(fa).max()
+    # <J_l^2> over p(G) on the 1x1 torus: N(G) and N(G) f_E(G) are
+    # trigonometric polynomials of degree <= 2 n_v in each angle, so an 8 x 8
+    # product grid integrates both exactly
+    q = gi.make_problem(1, gi.U1, 1, 2, bond_scale=0.4)
+    th = 2 * np.pi * np.arange(8) / 8
+    grid = np.array([[a, b] for a in th for b in th])
+    x = electric.Electric(q).expectation_exhaustive(grid)
+    assert np.abs(x.imag).max() <= 1e-12
+    assert x.real.min() >= 0.0 and x.real.max() > 0.01

@@ -1,6 +1,6 @@
 """GPU parity of the per-configuration observables computed from the chains'
-cached inverses: the Z2 electric (link-flip) observable of Sec. 5.3
-(ggf_chains_electric) and the fermionic bilinears of Sec. 5.2
+cached inverses: the electric observables of Sec. 5.3 (Z2 link flip, U(1)
+Casimir; ggf_chains_electric) and the fermionic bilinears of Sec. 5.2
 (ggf_chains_fermion).  The oracle evaluates both by the full covariance route
 (itself pinned to explicit Fock vectors).  FP64 chains agree to 1e-10
 relative, FP32 chains to 1e-4.
@@ -79,13 +79,22 @@ def test_device_output_matches_host():
     ctx.close()
 
 
-def test_u1_is_rejected():
-    from paper_2412_01737_gb300 import GGFError
-    p = gi.make_problem(2, gi.U1, 1, 1)
+@pytest.mark.parametrize("L,n_v,K,nch", [(2, 1, 2, 2), (3, 1, 3, 2), (2, 2, 2, 2)])
+def test_u1_casimir_fp64(L, n_v, K, nch):
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, nch, seed=33)
     ctx = ctx_for(p)
-    ctx.chains_init(gi.cold_links(p, 1), precision=0)
-    with pytest.raises(GGFError):
-        ctx.chains_electric()
+    ctx.chains_init(links, precision=0, seed=5)
+    _check(p, ctx, links, 1e-10)
+    ctx.close()
+
+
+def test_u1_casimir_fp32_after_sampling():
+    p = gi.make_problem(4, gi.U1, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=14), precision=1, seed=3, delay=8)
+    ctx.sample(2)
+    _check(p, ctx, ctx.chains_links(), 1e-4)
     ctx.close()
 
 
