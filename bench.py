@@ -8,7 +8,7 @@ the plaquette and log N(G) series (Madras-Sokal window, c = 5), estimated
 from all sweeps run after burn-in.
 
   python bench.py [--gpus N --steps K --warmup W] [--workload cfg3|cfg2]
-                  [--impl ggf|reference]
+                  [--impl ggf|reference] [--observables]
 
 --impl reference times the FP64 CPU oracle (exact Metropolis, full Pfaffian
 recompute per proposal) on the host cores on a bounded sample.
@@ -514,6 +514,61 @@ def run_e2e(args, p, chains, prec, refresh, delay, local, tau):
             "includes": "context creation, parameter upload, FP64 chain set-up, sweeps, per-sweep host read-back"}
 
 
+def observable_bytes(p, prec):
+    """Algorithmic bytes of W that one call of the electric and of the
+    fermionic kernel reads per chain: per pair, the B x r block between each
+    link's source site and the link (electric) and the B x B block between the
+    two sites of each site or link item (fermionic); B = 8 n_v, r = 4 n_v."""
+    b = 8 if prec == 0 else 4
+    per_pair = p.K * b + p.K * (p.K - 1) // 2 * 2 * b
+    B, r = 8 * p.n_v, 4 * p.n_v
+    return p.n_links * B * r * per_pair, (p.V + p.n_links) * B * B * per_pair
+
+
+def run_observables(args):
+    """Time the per-configuration observables of Secs. 5.2 and 5.3 on the
+    workload's chains (not part of the sampling step): K calls each after W
+    warm-up calls, CUDA events on the launching stream, device buffers."""
+    import torch
+    import ggf_inputs as gi
+    from paper_2412_01737_gb300 import GGF
+    p, chains, prec, refresh, delay, label = problem_for(args.workload)
+    if args.chains:
+        chains = args.chains
+    ctx = GGF(0)
+    ctx.init_problem(p)
+    ctx.chains_init(gi.random_links(p, chains, seed=BASE_SEED), precision=prec, refresh_every=refresh,
+                    seed=BASE_SEED, delay=delay)
+    ctx.sample(1 + args.burn)
+    el = torch.zeros((chains, p.n_links, 2), dtype=torch.float64, device="cuda")
+    fs = torch.zeros((chains, p.V, 2), dtype=torch.float64, device="cuda")
+    fl = torch.zeros((chains, p.n_links, 2, 2, 2), dtype=torch.float64, device="cuda")
+    calls = {"electric": lambda: ctx.chains_electric(out=el),
+             "fermion": lambda: ctx.chains_fermion(site=fs, link=fl)}
+    eb, fb = observable_bytes(p, prec)
+    peak = load_peaks().get("hbm_gbs")
+    out = {"metric": "observable_kernel_time", "unit": "ms per call (all chains)", "workload": args.workload,
+           "config": {"workload": label, "chains": chains}, "steps": args.steps, "warmup": args.warmup}
+    stream = torch.cuda.current_stream()
+    for name, fn in calls.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / args.steps
+        byts = (eb if name == "electric" else fb) * chains
+        gbs = byts / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes": byts, "achieved_gbs": gbs, "peak_gbs": peak,
+                     "frac": gbs / peak if peak else None, "bound": "latency (scattered small blocks)"}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,11 +585,15 @@ def main():
     ap.add_argument("--burn-train", type=int, default=4, help="cfg4: local sweeps before collecting training data")
     ap.add_argument("--train-sweeps", type=int, default=6, help="cfg4: local sweeps whose configurations train the net")
     ap.add_argument("--train-steps", type=int, default=300, help="cfg4: Adam steps")
+    ap.add_argument("--observables", action="store_true",
+                    help="time the electric and fermionic observable kernels instead of sampling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.observables:
+        run_observables(args)
     elif args.workload == "cfg5":
         run_cfg5(args)
     else:
