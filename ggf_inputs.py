@@ -21,13 +21,25 @@ Conventions (shared input contract, restated in include/ggf.h):
   is [[0,-1],[1,0]] (the matrix J below).
 * Bond covariance per link, layout [source end (2 n_v) | target end (2 n_v)],
   r = 4 n_v Majoranas.
-* Group Z2 (link value g = +-1) or U(1) (link angle theta in [0, 2 pi)).
+* Group Z2 (link value g = +-1), U(1) (link angle theta in [0, 2 pi)) or
+  SU(2) (unit quaternion (a0, a1, a2, a3), the group element
+  a0 1 + i (a1 sigma_x + a2 sigma_y + a3 sigma_z); links stored as
+  (n_cfg, 2V, 4) float64).
   Under U(1) a mode of charge q picks up the phase exp(i q phi); in Majorana
   space that is the rotation [[cos q phi, sin q phi], [-sin q phi, cos q phi]].
   Charges: physical (-1)^(x+y) (staggered, Sec. 2.4); virtual mode j on a
   source end +1 (j even) / -1 (j odd), on a target end the opposite sign, so
   that every bond pair is neutral.  Under Z2 every mode is odd (the group acts
   as fermion parity) and any Gaussian state is symmetric.
+* SU(2) (n_v even): the n_v modes of a link end form n_v / 2 doublets
+  (modes 2k, 2k + 1).  A group element u acts on a doublet as
+  psi^dag_alpha -> sum_beta psi^dag_beta u_{beta alpha}; source ends carry u,
+  target ends its complex conjugate, and the physical mode is a singlet, so
+  every bond pair sum_alpha psi^dag_{a alpha} psi^dag_{b alpha} is invariant
+  and the site covariance lies in the commutant of that action.  A gauge
+  transformation h (one element per site) maps the link (s -> t) to
+  h_t^dag g h_s (on the U(1) subgroup exp(i theta sigma_z) this is
+  theta + alpha_s - alpha_t, as for U(1)).
 """
 from __future__ import annotations
 
@@ -35,7 +47,7 @@ import dataclasses
 import numpy as np
 import scipy.linalg
 
-Z2, U1 = 0, 1
+Z2, U1, SU2 = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -103,6 +115,81 @@ def _project_commutant(A, charges, n_phi=16):
     return out / n_phi
 
 
+def su2(q) -> np.ndarray:
+    """2 x 2 unitary of a unit quaternion (a0, a1, a2, a3)."""
+    a0, a1, a2, a3 = q
+    return np.array([[a0 + 1j * a3, 1j * a1 + a2], [1j * a1 - a2, a0 - 1j * a3]])
+
+
+def _quat_of(u) -> np.ndarray:
+    return np.array([u[0, 0].real, u[0, 1].imag, u[0, 1].real, u[0, 0].imag])
+
+
+def _majorana_rep(u) -> np.ndarray:
+    """Real 2n x 2n rotation R with U c_a U^dag = sum_b R_ab c_b for the
+    Gaussian unitary U with U psi^dag_j U^dag = sum_k psi^dag_k u_kj."""
+    n = u.shape[0]
+    R = np.zeros((2 * n, 2 * n))
+    for j in range(n):
+        for k in range(n):
+            R[2 * j, 2 * k], R[2 * j, 2 * k + 1] = u[k, j].real, u[k, j].imag
+            R[2 * j + 1, 2 * k], R[2 * j + 1, 2 * k + 1] = -u[k, j].imag, u[k, j].real
+    return R
+
+
+_PAULI = [np.array([[0, 1], [1, 0]], dtype=complex), np.array([[0, -1j], [1j, 0]]),
+          np.array([[1, 0], [0, -1]], dtype=complex)]
+
+
+def _su2_generators(slots):
+    """so(m) generators of the SU(2) action on a mode register; slots lists,
+    per doublet, (first Majorana, conjugate?) (other Majoranas untouched)."""
+    m = max(a for a, _ in slots) + 4
+    gens = []
+    for sig in _PAULI:
+        Xi = np.zeros((m, m))
+        for a, conj in slots:
+            # the Majorana representation is real-linear in u, so the
+            # generator of u = exp(i t sigma / 2) is the map applied to i sigma / 2
+            x = 0.5j * sig
+            Xi[a:a + 4, a:a + 4] = _majorana_rep(x.conj() if conj else x)
+        gens.append(Xi)
+    return gens
+
+
+def _project_commutant_su2(A, gens):
+    """Orthogonal projection of an antisymmetric A onto the antisymmetric
+    matrices that commute with every generator (the SU(2) commutant)."""
+    n = A.shape[0]
+    iu = np.triu_indices(n, 1)
+    basis = []
+    for a, b in zip(*iu):
+        E = np.zeros((n, n))
+        E[a, b], E[b, a] = 1.0, -1.0
+        basis.append(E)
+    M = np.array([np.concatenate([(Xi @ E - E @ Xi).ravel() for Xi in gens]) for E in basis]).T
+    _, sv, vt = np.linalg.svd(M)
+    null = vt[np.sum(sv > 1e-8 * sv.max()):]
+    coef = A[iu]
+    coef = null.T @ (null @ coef)
+    out = np.zeros((n, n))
+    out[iu] = coef
+    return out - out.T
+
+
+def _site_slots_su2(n_v):
+    """Doublet slots of one site (layout [phys(2) | -x | +x | -y | +y])."""
+    slots = []
+    for e in range(4):
+        for k in range(n_v // 2):
+            slots.append((2 + e * 2 * n_v + 4 * k, e % 2 == 0))   # target ends (-x, -y) conjugate
+    return slots
+
+
+def _bond_slots_su2(n_v):
+    return [(4 * k, False) for k in range(n_v // 2)] + [(2 * n_v + 4 * k, True) for k in range(n_v // 2)]
+
+
 def _rand_antisym(rng, n, scale):
     X = rng.normal(size=(n, n)) * scale
     return np.triu(X, 1) - np.triu(X, 1).T
@@ -131,6 +218,8 @@ def make_problem(L: int, group: int, n_v: int, K: int, seed: int = 20241202,
     or 'random' (independent per site).  bond_mode: 'uniform' (same bond on
     every link) or 'random' (independent per link).  With distinct_bonds
     False, every B_n equals B_1."""
+    if group == SU2 and n_v % 2:
+        raise ValueError("SU(2) needs n_v even (doublets)")
     rng = np.random.default_rng(seed)
     V = L * L
     m_s, r = 2 + 8 * n_v, 4 * n_v
@@ -141,6 +230,8 @@ def make_problem(L: int, group: int, n_v: int, K: int, seed: int = 20241202,
         A = _rand_antisym(rng, m_s, site_scale)
         if group == U1:
             A = _project_commutant(A, site_charges(n_v, qp))
+        elif group == SU2:
+            A = _project_commutant_su2(A, _su2_generators(_site_slots_su2(n_v)))
         O = scipy.linalg.expm(A)
         return O @ vacuum(m_s // 2) @ O.T
 
@@ -162,6 +253,8 @@ def make_problem(L: int, group: int, n_v: int, K: int, seed: int = 20241202,
         A = _rand_antisym(rng, r, bond_scale)
         if group == U1:
             A = _project_commutant(A, bond_q)
+        elif group == SU2:
+            A = _project_commutant_su2(A, _su2_generators(_bond_slots_su2(n_v)))
         O = scipy.linalg.expm(A)
         return O @ g1 @ O.T
 
@@ -181,13 +274,21 @@ def make_problem(L: int, group: int, n_v: int, K: int, seed: int = 20241202,
 def cold_links(p: Problem, n_cfg: int = 1) -> np.ndarray:
     if p.group == Z2:
         return np.ones((n_cfg, p.n_links), dtype=np.int8)
+    if p.group == SU2:
+        out = np.zeros((n_cfg, p.n_links, 4))
+        out[..., 0] = 1.0
+        return out
     return np.zeros((n_cfg, p.n_links), dtype=np.float64)
 
 
 def random_links(p: Problem, n_cfg: int, seed: int = 7) -> np.ndarray:
+    """Haar-random link values (SU(2): normalised Gaussian quaternions)."""
     rng = np.random.default_rng(seed)
     if p.group == Z2:
         return rng.choice(np.array([1, -1], dtype=np.int8), size=(n_cfg, p.n_links))
+    if p.group == SU2:
+        q = rng.normal(size=(n_cfg, p.n_links, 4))
+        return q / np.linalg.norm(q, axis=-1, keepdims=True)
     return rng.uniform(0.0, 2 * np.pi, size=(n_cfg, p.n_links))
 
 
@@ -201,8 +302,8 @@ def all_z2_configs(p: Problem) -> np.ndarray:
 
 def gauge_transform(p: Problem, links: np.ndarray, h: np.ndarray) -> np.ndarray:
     """Apply a site gauge transformation h (V,) to links (n, 2V): the link
-    from s to t = s + e_d becomes h_s g h_t^{-1} (Z2: product of signs;
-    U(1): theta + alpha_s - alpha_t)."""
+    from s to t = s + e_d becomes (Z2) h_s g h_t, (U(1)) theta + alpha_s -
+    alpha_t, (SU(2), h (V, 4) quaternions) h_t^dag g h_s."""
     L = p.L
     out = links.copy()
     for s in range(p.V):
@@ -212,6 +313,9 @@ def gauge_transform(p: Problem, links: np.ndarray, h: np.ndarray) -> np.ndarray:
             l = 2 * s + d
             if p.group == Z2:
                 out[:, l] = links[:, l] * h[s] * h[t]
+            elif p.group == SU2:
+                for c in range(links.shape[0]):
+                    out[c, l] = _quat_of(su2(h[t]).conj().T @ su2(links[c, l]) @ su2(h[s]))
             else:
                 out[:, l] = np.mod(links[:, l] + h[s] - h[t], 2 * np.pi)
     return out

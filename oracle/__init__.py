@@ -9,6 +9,7 @@ Philox generator, Pfaffian, Fock-space machinery and weight formulas.
 Modules
 -------
 philox   Philox4x64-10 counter generator (Salmon et al., SC'11).
+         Groups: Z2, U(1) and SU(2) (doublets on the link ends; oracle only).
 pfaffian Plain Parlett-Reid Pfaffian in C (complex and real FP64).
 fock     Brute-force Fock-space construction and contraction of the PEPS
          (Sec. 3, Sec. 4, App. C): the definition of psi_n(G) written out.

@@ -12,7 +12,10 @@ Everything here is the definition written out on explicit state vectors:
   Sec. 3.2) is the ground state of H = -(i/4) sum_ab Gamma_ab c_a c_b.
 * The gauge twist U(G) (Sec. 3.1) multiplies every basis state by
   exp(i theta_l sum_j q_j n_j) over the source-end modes of every link
-  (Z2: (-1)^(sum_j n_j) for g_l = -1).
+  (Z2: (-1)^(sum_j n_j) for g_l = -1).  SU(2) acts on each doublet of a
+  source end (modes 2k, 2k + 1) by exp(sum_{alpha beta} (log u)_{beta alpha}
+  psi^dag_beta psi_alpha), so that psi^dag_alpha -> sum_beta psi^dag_beta
+  u_{beta alpha} (Sec. 2, the Wigner matrix acting on the fermion modes).
 * psi_n(G) = <B_n| U(G) |A> (Sec. 4): |A> is the product of site states, <B_n|
   the product of link states, the contraction runs over the virtual modes;
   N_nm(G) = <psi_n(G)|psi_m(G)> and N(G) = || sum_n lambda_n psi_n(G) ||^2.
@@ -20,7 +23,8 @@ Everything here is the definition written out on explicit state vectors:
   B_0 := B_1 and the per-link factors each made real positive.
 
 Pinned (tests/test_oracle_fock.py): vacuum covariance, Gamma -> state ->
-Gamma round trip, the worked two-mode contraction of App. C, overlaps against
+Gamma round trip, the SU(2) twist's action on creators
+(tests/test_oracle_su2.py), the worked two-mode contraction of App. C, overlaps against
 |<a|b>|^2 computed from explicit vectors, fermionic reordering against
 explicit operator products.
 """
@@ -28,9 +32,11 @@ from __future__ import annotations
 
 import functools
 import numpy as np
+import scipy.linalg
 import scipy.sparse as sp
+import scipy.sparse.linalg
 
-Z2, U1 = 0, 1
+Z2, U1, SU2 = 0, 1, 2
 
 
 @functools.lru_cache(maxsize=32)
@@ -237,9 +243,25 @@ class FockPEPS:
             return 1.0 - 2.0 * (np.round(ang / np.pi).astype(np.int64) % 2)
         return np.exp(1j * ang)
 
+    def twisted_state(self, links: np.ndarray) -> np.ndarray:
+        """U(G) |A>."""
+        if self.p.group != SU2:
+            return self.twist_phase(links) * self.A
+        from .weight import su2_matrix
+        ann, cre = fermion_ops(self.lat.n_modes)
+        Phi = self.A.astype(complex)
+        for l in range(self.p.n_links):
+            a, _ = self.lat.link_modes(l)
+            lg = scipy.linalg.logm(su2_matrix(links[l]))
+            for k in range(self.p.n_v // 2):
+                m = (a[2 * k], a[2 * k + 1])
+                H = sum(lg[b, al] * (cre[m[b]] @ ann[m[al]]) for b in range(2) for al in range(2))
+                Phi = scipy.sparse.linalg.expm_multiply(sp.csr_matrix(H), Phi)
+        return Phi
+
     def psi(self, links: np.ndarray) -> np.ndarray:
         """(K, 2^V) physical amplitudes psi_n(G) = <B_n| U(G) |A>."""
-        Phi = self.twist_phase(links) * self.A
+        Phi = self.twisted_state(links)
         return np.array([contract(Phi, self.phys, self.virt, b) for b in self.B])
 
     def n_matrix(self, links: np.ndarray) -> np.ndarray:

@@ -5,20 +5,27 @@
   elements; for Z2 that is g1 g2 g3 g4, for U(1) cos(theta1 + theta2 -
   theta3 - theta4) (real part of the U(1) character).  The plaquette at site
   s uses link (s, x), link (s + e_x, y), link (s + e_y, x) reversed and
-  link (s, y) reversed.  <W> = sum_G p(G) W(G) (Sec. 5.1).
+  link (s, y) reversed.  SU(2): the link label g enters the twist as
+  psi^dag -> psi^dag D(g) (the right-regular action of App. A), under which
+  the weight is invariant for g_l -> h_t^dag g_l h_s, so the covariant link
+  matrix is g^dag and the plaquette is (1/2) tr(g1^dag g2^dag g3 g4) (real
+  for SU(2); cos(theta1 + theta2 - theta3 - theta4) on the U(1) subgroup
+  exp(i theta sigma_z)).  <W> = sum_G p(G) W(G) (Sec. 5.1).
 * Integrated autocorrelation time with the automatic window of Madras &
   Sokal (J. Stat. Phys. 50, 1988): tau(W) = 1/2 + sum_{t=1..W} rho(t),
   smallest W with W >= c tau(W), c = 5.
 
 Pinned (tests/test_oracle_observables.py): plaquette against a loop-by-loop
 product on hand-built configurations, tau_int against the closed form
-(1 + a) / (2 (1 - a)) of an AR(1) series.
+(1 + a) / (2 (1 - a)) of an AR(1) series.  SU(2) (tests/test_oracle_su2.py):
+cold configuration, a centre element on one link, the U(1) subgroup, gauge
+invariance.
 """
 from __future__ import annotations
 
 import numpy as np
 
-Z2, U1 = 0, 1
+Z2, U1, SU2 = 0, 1, 2
 
 
 def plaquette_links(L: int):
@@ -34,8 +41,19 @@ def plaquette_links(L: int):
 
 def plaquette_values(group: int, L: int, links: np.ndarray) -> np.ndarray:
     """(n_cfg, V) plaquette values."""
-    links = np.atleast_2d(links)
     pl = plaquette_links(L)
+    if group == SU2:
+        from .weight import su2_matrix
+        links = np.asarray(links, dtype=np.float64)
+        if links.ndim == 2:
+            links = links[None]
+        out = np.zeros((links.shape[0], L * L))
+        for c in range(links.shape[0]):
+            for s in range(L * L):
+                g = [su2_matrix(links[c, k]) for k in pl[s]]
+                out[c, s] = 0.5 * np.trace(g[0].conj().T @ g[1].conj().T @ g[2] @ g[3]).real
+        return out
+    links = np.atleast_2d(links)
     if group == Z2:
         g = links.astype(np.int64)
         return (g[:, pl[:, 0]] * g[:, pl[:, 1]] * g[:, pl[:, 2]] * g[:, pl[:, 3]]).astype(np.float64)

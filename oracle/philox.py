@@ -37,3 +37,10 @@ def draws(seed: int, chain: int, sweep: int, link: int):
     """(u_accept, u_propose) for one proposal."""
     w = philox4x64_10((sweep, link, 0, 0), (seed, chain))
     return uniform53(w[0]), uniform53(w[1])
+
+
+def draws4(seed: int, chain: int, sweep: int, link: int):
+    """All four words of one proposal's block as uniforms (u_accept,
+    u_propose, u_axis_z, u_axis_phi); the last two serve SU(2) proposals."""
+    w = philox4x64_10((sweep, link, 0, 0), (seed, chain))
+    return tuple(uniform53(x) for x in w)

@@ -8,7 +8,13 @@ Steps, in the paper's order and notation:
 2. O(G): identity except on the source-end Majoranas of every link, where
    Z2 gives g_l * 1 and U(1) gives, per mode of charge q, the rotation
    [[cos q theta, sin q theta], [-sin q theta, cos q theta]] (this is
-   U(G) c_a U(G)^dag = O_ab c_b for U(G) = prod exp(i theta q n)).
+   U(G) c_a U(G)^dag = O_ab c_b for U(G) = prod exp(i theta q n)).  SU(2)
+   acts on each doublet (modes 2k, 2k + 1) of the end by the Gaussian unitary
+   with U psi^dag_j U^dag = sum_k psi^dag_k u_kj, u the link's 2 x 2 matrix,
+   whose Majorana rotation has rows
+   c_2j -> sum_k Re u_kj c_2k + Im u_kj c_2k+1 and
+   c_2j+1 -> sum_k -Im u_kj c_2k + Re u_kj c_2k+1 (the U(1) rotation for a
+   diagonal u).
    Gamma_{A(G)} = O^T Gamma_A O  (Sec. 5).
 3. Numerator tr(rho_{A(G)} (1 x rho_{B_n})(1 x rho_{B_m})): the product of
    the two bond density matrices is Gaussian (Bravyi-Gosset),
@@ -33,8 +39,12 @@ contraction (oracle.fock) for Z2 and U(1), K = 1, 2, 3; invariants
 (N >= 0, Im N = 0, N_mn = conj N_nm, gauge invariance, lambda phase
 invariance, B_2 = B_1 => N = |lambda_1 + lambda_2|^2 N_11); exhaustive
 normalisation on the 2x2 Z2 lattice.
-The absolute U(1) normalisation sum_G N(G) (an integral over angles) is
-parity unpinned; only ratios and observables are compared for U(1).
+SU(2) (tests/test_oracle_su2.py): the doublet rotation against explicit
+Fock operators, N_nm against the Fock contraction on the 1x1 torus, the U(1)
+code on the subgroup exp(i theta sigma_z), gauge invariance under
+g_l -> h_t^dag g_l h_s.
+The absolute U(1) and SU(2) normalisations sum_G N(G) (integrals over the
+group) are parity unpinned; only ratios and observables are compared.
 """
 from __future__ import annotations
 
@@ -43,7 +53,24 @@ import numpy as np
 from . import fock
 from .pfaffian import log_pfaffian
 
-Z2, U1 = 0, 1
+Z2, U1, SU2 = 0, 1, 2
+
+
+def su2_matrix(q) -> np.ndarray:
+    """a0 1 + i (a1 sigma_x + a2 sigma_y + a3 sigma_z) for a unit quaternion."""
+    a0, a1, a2, a3 = (float(x) for x in q)
+    return np.array([[complex(a0, a3), complex(a2, a1)], [complex(-a2, a1), complex(a0, -a3)]])
+
+
+def doublet_rotation(u) -> np.ndarray:
+    """Majorana rotation (4 x 4) of the Gaussian unitary psi^dag -> psi^dag u
+    on one doublet."""
+    R = np.zeros((4, 4))
+    for j in range(2):
+        for k in range(2):
+            R[2 * j, 2 * k], R[2 * j, 2 * k + 1] = u[k, j].real, u[k, j].imag
+            R[2 * j + 1, 2 * k], R[2 * j + 1, 2 * k + 1] = -u[k, j].imag, u[k, j].real
+    return R
 
 
 def twist_matrix(p, links) -> np.ndarray:
@@ -54,6 +81,12 @@ def twist_matrix(p, links) -> np.ndarray:
     for l in range(p.n_links):
         s, d = l // 2, l % 2
         base = s * m_s + 2 + (2 * d + 1) * 2 * n_v
+        if p.group == SU2:
+            R = doublet_rotation(su2_matrix(links[l]))
+            for k in range(n_v // 2):
+                i0 = base + 4 * k
+                O[i0:i0 + 4, i0:i0 + 4] = R
+            continue
         for j in range(n_v):
             i0 = base + 2 * j
             if p.group == Z2:
