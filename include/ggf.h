@@ -21,6 +21,15 @@
  *   covariance Gamma_ab = (i/2) <[c_a, c_b]> (Sec. 3.2).
  *   Z2 links: int8 values +1 / -1.  U(1) links: double angles in [0, 2 pi);
  *   a source-end mode of charge q is twisted by exp(i q theta n).
+ *   SU(2) links (n_v = 2: one doublet per link end): four doubles per link,
+ *   a unit quaternion (a0, a1, a2, a3) for u = a0 1 + i (a1 sigma_x +
+ *   a2 sigma_y + a3 sigma_z); the source-end doublet is twisted by
+ *   psi^dag_j -> sum_k psi^dag_k u_kj (the right-regular action, App. A).
+ *   The weight is then invariant under u_l -> h_t^dag u_l h_s, and the
+ *   plaquette observable is (1/2) tr(u1^dag u2^dag u3 u4).  SU(2) chains use
+ *   immediate updates (delay <= 1); the proposal is u -> r u with
+ *   r = cos d + i sin d (n . sigma), d = width (u_prop - 1/2) and n uniform
+ *   on the sphere from Philox words 2 and 3 (z = 2 u - 1, phi = 2 pi u).
  *
  * Memory: every entry point that takes array arguments also takes `mem`:
  * GGF_MEM_DEVICE (device pointers, borrowed until the stream work ends) or
@@ -42,6 +51,7 @@ extern "C" {
 
 #define GGF_Z2 0
 #define GGF_U1 1
+#define GGF_SU2 2
 #define GGF_FP64 0
 #define GGF_FP32 1
 #define GGF_MEM_DEVICE 0
@@ -74,9 +84,10 @@ const char* ggf_last_error(const ggf_ctx* ctx);
  * Resets groups, Gaussians and chains. */
 ggf_status ggf_init_lattice(ggf_ctx* ctx, int L);
 
-/* Gauge group (GGF_Z2 or GGF_U1, Sec. 2.1-2.2) and n_v in {1, 2} virtual
- * complex modes per link end.  q_src[n_v]: U(1) charges of the source-end
- * modes (ignored for Z2, may be NULL then). */
+/* Gauge group (GGF_Z2, GGF_U1 or GGF_SU2, Sec. 2.1-2.2) and n_v in {1, 2}
+ * virtual complex modes per link end (SU(2): n_v = 2, one doublet).
+ * q_src[n_v]: U(1) charges of the source-end modes (ignored for Z2 and SU(2),
+ * may be NULL then). */
 ggf_status ggf_init_group(ggf_ctx* ctx, int group, int n_v, const int* q_src);
 
 /* Variational parameters of the Ansatz (Sec. 4-5), host pointers:
@@ -122,7 +133,7 @@ ggf_status ggf_logweight_noalloc(ggf_ctx* ctx, int n_cfg, const void* links, dou
 /* Wilson-loop observables from links alone (Sec. 2.3, Sec. 5.1).
  * which = GGF_OBS_PLAQUETTE: out[n_cfg] = mean over the V plaquettes of the
  * trace of the oriented plaquette product (Z2: product of signs; U(1): cos of
- * theta1 + theta2 - theta3 - theta4). */
+ * theta1 + theta2 - theta3 - theta4; SU(2): (1/2) tr(u1^dag u2^dag u3 u4)). */
 ggf_status ggf_observable(ggf_ctx* ctx, int which, int n_cfg, const void* links,
                           double* out, int mem, void* stream);
 
@@ -201,7 +212,7 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
  * site and the link is read.  Pending delayed updates are folded into W first.
  *   out [n_chains][2V][2] FP64 (re, im), caller-owned.  A single
  *   configuration's value is complex; its average over p(G) is real.
- * GGF_ESTATE before ggf_chains_init. */
+ * GGF_EINVAL for SU(2) chains (not built); GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream);
 
 /* Fermionic observables (Sec. 5.2): Majorana bilinears on the physical

@@ -5,4 +5,4 @@ include/ggf.h); this package only builds it and marshals arguments.  There is
 no CPU fallback: importing the binding fails loudly when the library is
 missing.
 """
-from .ggf import GGF, GGFError, Net, Z2, U1, FP64, FP32, lib_path, sample_group  # noqa: F401
+from .ggf import GGF, GGFError, Net, Z2, U1, SU2, FP64, FP32, lib_path, sample_group  # noqa: F401

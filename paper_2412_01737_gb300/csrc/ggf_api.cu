@@ -69,7 +69,10 @@ void ggf_free_consts(ggf_ctx* ctx) {
 
 namespace {
 
-size_t link_bytes(const Geometry& g) { return g.group == GGF_Z2 ? 1 : sizeof(double); }
+// Z2: int8 g; U(1): double theta; SU(2): four doubles (unit quaternion)
+size_t link_bytes(const Geometry& g) {
+    return g.group == GGF_Z2 ? 1 : g.group == GGF_SU2 ? 4 * sizeof(double) : sizeof(double);
+}
 
 // scoped device buffer
 struct DBuf {
@@ -280,7 +283,9 @@ ggf_status ggf_init_lattice(ggf_ctx* ctx, int L) {
 ggf_status ggf_init_group(ggf_ctx* ctx, int group, int n_v, const int* q_src) {
     if (!ctx) return GGF_EINVAL;
     if (!ctx->have_lattice) return ggf_fail(ctx, GGF_ESTATE, "call ggf_init_lattice first");
-    if (group != GGF_Z2 && group != GGF_U1) return ggf_fail(ctx, GGF_EINVAL, "group must be GGF_Z2 or GGF_U1");
+    if (group != GGF_Z2 && group != GGF_U1 && group != GGF_SU2)
+        return ggf_fail(ctx, GGF_EINVAL, "group must be GGF_Z2, GGF_U1 or GGF_SU2");
+    if (group == GGF_SU2 && n_v != 2) return ggf_fail(ctx, GGF_EINVAL, "SU(2) needs n_v = 2 (one doublet per link end)");
     if (n_v < 1 || n_v > 2) return ggf_fail(ctx, GGF_EINVAL, "n_v must be 1 or 2");
     if (group == GGF_U1 && !q_src) return ggf_fail(ctx, GGF_EINVAL, "U(1) needs q_src");
     cudaSetDevice(ctx->device);
@@ -426,6 +431,8 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     if (opts->precision != GGF_FP64 && opts->precision != GGF_FP32)
         return ggf_fail(ctx, GGF_EINVAL, "precision must be GGF_FP64 or GGF_FP32");
     if (opts->refresh_every < 1) return ggf_fail(ctx, GGF_EINVAL, "refresh_every must be >= 1");
+    if (ctx->g.group == GGF_SU2 && opts->delay > 1)
+        return ggf_fail(ctx, GGF_EINVAL, "SU(2) chains use immediate updates (delay <= 1)");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     ggf_free_chains(ctx);

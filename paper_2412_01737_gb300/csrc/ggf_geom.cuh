@@ -100,5 +100,67 @@ __device__ __forceinline__ void link_value(const DevConst& dc, const void* links
     }
 }
 
+// ---- SU(2) links ------------------------------------------------------------
+// A link value is a unit quaternion q = (a0, a1, a2, a3), the group element
+// u = a0 1 + i (a1 sigma_x + a2 sigma_y + a3 sigma_z).  The twist acts on the
+// source-end doublet by psi^dag_j -> sum_k psi^dag_k u_kj (the right-regular
+// action of App. A), whose Majorana rotation R (4 x 4, row-major) has rows
+//   c_2j   -> sum_k  Re u_kj c_2k + Im u_kj c_2k+1,
+//   c_2j+1 -> sum_k -Im u_kj c_2k + Re u_kj c_2k+1.
+
+__device__ __forceinline__ const double* link_quat(const Geometry& g, const void* links, int cfg, int link) {
+    return (const double*)links + ((size_t)cfg * g.n_links + link) * 4;
+}
+
+// (a0 + i a.s)(b0 + i b.s) = a0 b0 - a.b + i (a0 b + b0 a - a x b).s
+__device__ __forceinline__ void quat_mul(const double* a, const double* b, double* o) {
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + b[0] * a[1] - (a[2] * b[3] - a[3] * b[2]);
+    o[2] = a[0] * b[2] + b[0] * a[2] - (a[3] * b[1] - a[1] * b[3]);
+    o[3] = a[0] * b[3] + b[0] * a[3] - (a[1] * b[2] - a[2] * b[1]);
+}
+
+// (1/2) tr(u1^dag u2^dag u3 u4): the scalar part of conj(q1) conj(q2) q3 q4.
+// The weight is invariant under u_l -> h_t^dag u_l h_s, so the covariant link
+// matrix is u^dag and this is the oriented plaquette trace.
+__device__ __forceinline__ double plaquette_su2(const double* q1, const double* q2, const double* q3,
+                                                const double* q4) {
+    const double c1[4] = {q1[0], -q1[1], -q1[2], -q1[3]}, c2[4] = {q2[0], -q2[1], -q2[2], -q2[3]};
+    double a[4], b[4];
+    quat_mul(c1, c2, a);
+    quat_mul(q3, q4, b);
+    return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+__device__ __forceinline__ void doublet_rotation(const double* q, double* R) {
+    // u00 = a0 + i a3, u01 = a2 + i a1, u10 = -a2 + i a1, u11 = a0 - i a3
+    const double ure[2][2] = {{q[0], q[2]}, {-q[2], q[0]}};
+    const double uim[2][2] = {{q[3], q[1]}, {q[1], -q[3]}};
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) {
+            R[(2 * j) * 4 + 2 * k] = ure[k][j];
+            R[(2 * j) * 4 + 2 * k + 1] = uim[k][j];
+            R[(2 * j + 1) * 4 + 2 * k] = -uim[k][j];
+            R[(2 * j + 1) * 4 + 2 * k + 1] = ure[k][j];
+        }
+}
+
+// (O G O^T)[x][y] on one link (n_v = 2: the source end is one doublet at link
+// positions 0..3, rotated by R; the target end 4..7 is untouched).
+template <class T>
+__device__ T twisted_su2(const DevConst& dc, int pair, int link, int x, int y, const double* R) {
+    T v = T{};
+    if (x < 4 && y < 4) {
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) v += mulc(R[x * 4 + a] * R[y * 4 + b], bond_elem<T>(dc, pair, link, a, b));
+    } else if (x < 4) {
+        for (int a = 0; a < 4; ++a) v += mulc(R[x * 4 + a], bond_elem<T>(dc, pair, link, a, y));
+    } else if (y < 4) {
+        for (int b = 0; b < 4; ++b) v += mulc(R[y * 4 + b], bond_elem<T>(dc, pair, link, x, b));
+    } else {
+        v = bond_elem<T>(dc, pair, link, x, y);
+    }
+    return v;
+}
 
 }  // namespace

@@ -94,7 +94,7 @@ extern "C" ggf_status ggf_logweight_noalloc(ggf_ctx* ctx, int n_cfg, const void*
     }
     if (cfg_chunk == 0) return ggf_fail(ctx, GGF_EINVAL, "ggf_logweight_noalloc: one configuration does not fit the scratch");
     unsigned char* s0 = (unsigned char*)base;
-    const size_t lrow = (size_t)g.n_links * (g.group == GGF_Z2 ? 1 : sizeof(double));
+    const size_t lrow = (size_t)g.n_links * (g.group == GGF_Z2 ? 1 : g.group == GGF_SU2 ? 4 * sizeof(double) : sizeof(double));
     for (int c0 = 0; c0 < n_cfg; c0 += cfg_chunk) {
         const int nc = std::min(cfg_chunk, n_cfg - c0);
         const void* lk = (const unsigned char*)links + (size_t)c0 * lrow;

@@ -171,6 +171,55 @@ __device__ __forceinline__ void pair_delta(const DevConst& dc, int p, int l, con
     }
 }
 
+// SU(2) proposal (n_v = 2, one doublet per link end), thread-local: with
+// Philox words (u_acc, u_prop, u_z, u_phi) of counter (sweep, l, 0, 0) and
+// key (seed, chain), g -> r g with r = cos d + i sin d (n . sigma),
+// d = width (u_prop - 1/2), n = (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z),
+// z = 2 u_z - 1, phi = 2 pi u_phi, renormalised to a unit quaternion.  r and
+// r^dag are equally likely (a Haar-symmetric move).  Writes the new
+// quaternion and the old and new doublet rotations; returns u_acc.
+__device__ __forceinline__ double draw_su2(const Geometry& g, const void* links, int c, int l,
+                                           unsigned long long sweep, uint64_t seed, double width, double* qn,
+                                           double* Rold, double* Rnew) {
+    uint64_t ctr[4] = {(uint64_t)sweep, (uint64_t)l, 0, 0}, out[4];
+    philox4x64_10(ctr, seed, (uint64_t)c, out);
+    const double d = width * (u53(out[1]) - 0.5);
+    const double z = 2.0 * u53(out[2]) - 1.0;
+    const double rho = sqrt(fmax(0.0, 1.0 - z * z));
+    const double ph = GGF_TWO_PI * u53(out[3]);
+    double sd, cd, sp, cp;
+    sincos(d, &sd, &cd);
+    sincos(ph, &sp, &cp);
+    const double r[4] = {cd, sd * rho * cp, sd * rho * sp, sd * z};
+    const double* q = link_quat(g, links, c, l);
+    double t[4];
+    quat_mul(r, q, t);
+    const double nrm = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
+    for (int k = 0; k < 4; ++k) qn[k] = t[k] / nrm;
+    doublet_rotation(q, Rold);
+    doublet_rotation(qn, Rnew);
+    return u53(out[0]);
+}
+
+// Delta of pair p for an SU(2) proposal (rotations Rold, Rnew of the source
+// doublet), r x r, one warp.
+__device__ __forceinline__ void pair_delta_su2(const DevConst& dc, int p, int l, const double* Rold,
+                                               const double* Rnew, cxd* D) {
+    const int r = dc.g.r, lane = threadIdx.x & 31;
+    for (int e = lane; e < r * r; e += 32) {
+        int xi = e / r, yi = e % r;
+        cxd nv, ov;
+        if (p < dc.K) {
+            nv = {twisted_su2<double>(dc, p, l, xi, yi, Rnew), 0.0};
+            ov = {twisted_su2<double>(dc, p, l, xi, yi, Rold), 0.0};
+        } else {
+            nv = twisted_su2<cxd>(dc, p - dc.K, l, xi, yi, Rnew);
+            ov = twisted_su2<cxd>(dc, p - dc.K, l, xi, yi, Rold);
+        }
+        D[e] = nv - ov;
+    }
+}
+
 // cos, sin of q_j theta for the old and the new angle of a U(1) proposal
 // (threads 0 .. 2 n_v - 1 of the block; cs holds 8 doubles).
 __device__ __forceinline__ void twist_table(const Geometry& g, const Proposal& q, double* cs) {

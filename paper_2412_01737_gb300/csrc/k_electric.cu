@@ -177,6 +177,8 @@ ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
+    if (g.group == GGF_SU2)
+        return ggf_fail(ctx, GGF_EINVAL, "the SU(2) electric observable (the Casimir of the doublet twist) is not built");
     // pending delayed updates first, so that W is the inverse at the current links
     GGF_TRY(ggf_flush(ctx, st));
     const int bpc = (g.n_links + ETHREADS - 1) / ETHREADS;

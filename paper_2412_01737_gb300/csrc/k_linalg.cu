@@ -38,9 +38,15 @@ __global__ void assemble_kernel(DevConst dc, const int* item_cfg, const int* ite
     link_of(g, i, li, pi);
     link_of(g, j, lj, pj);
     if (li == lj) {
-        double gv, th;
-        link_value<T>(dc, links, cfg, li, gv, th);
-        v += twisted<T>(dc, pair, li, pi, pj, gv, th);
+        if (g.group == GGF_SU2) {
+            double R[16];
+            doublet_rotation(link_quat(g, links, cfg, li), R);
+            v += twisted_su2<T>(dc, pair, li, pi, pj, R);
+        } else {
+            double gv, th;
+            link_value<T>(dc, links, cfg, li, gv, th);
+            v += twisted<T>(dc, pair, li, pi, pj, gv, th);
+        }
     }
     dst[(size_t)item * NN + e] = v;
 }
@@ -282,6 +288,9 @@ __global__ void plaquette_kernel(Geometry g, int n_cfg, const void* links, doubl
         if (g.group == GGF_Z2) {
             const int8_t* L8 = (const int8_t*)links + (size_t)c * g.n_links;
             acc += (double)(L8[l1] * L8[l2] * L8[l3] * L8[l4]);
+        } else if (g.group == GGF_SU2) {
+            acc += plaquette_su2(link_quat(g, links, c, l1), link_quat(g, links, c, l2), link_quat(g, links, c, l3),
+                                 link_quat(g, links, c, l4));
         } else {
             const double* T = (const double*)links + (size_t)c * g.n_links;
             acc += cos(T[l1] + T[l2] - T[l3] - T[l4]);

@@ -53,7 +53,9 @@ struct SweepArgs {
     int* dead;
 };
 
-template <class RW, class CW>
+// SU2: SU(2) links (quaternion proposal and doublet twist); the Z2 and U(1)
+// instantiations (SU2 = false) do not contain that code.
+template <class RW, class CW, bool SU2>
 __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
     extern __shared__ cxd sm[];
     const Geometry& g = a.dc.g;
@@ -68,25 +70,36 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
     __shared__ Proposal s_q;
     __shared__ double s_cs[8];
     __shared__ int s_accept;
+    __shared__ double s_su2[36];          // SU2: new quaternion, old and new doublet rotations
 
     const int l = a.link_of_chain ? a.link_of_chain[c] : a.link;
     int a0, b0;
     link_ends(g, l, a0, b0);
 
-    if (threadIdx.x == 0) {
-        Proposal q = draw_proposal(g, a.links, c, l, *a.d_sweep, a.seed, a.width);
-        if (a.forced && g.group == GGF_U1) q.th_new = a.forced[(size_t)c * 32 + a.forced_k];   // block move
-        s_q = q;
+    if constexpr (SU2) {
+        if (threadIdx.x == 0) {
+            Proposal q{};
+            q.u_acc = draw_su2(g, a.links, c, l, *a.d_sweep, a.seed, a.width, s_su2, s_su2 + 4, s_su2 + 20);
+            s_q = q;
+        }
+        __syncthreads();
+    } else {
+        if (threadIdx.x == 0) {
+            Proposal q = draw_proposal(g, a.links, c, l, *a.d_sweep, a.seed, a.width);
+            if (a.forced && g.group == GGF_U1) q.th_new = a.forced[(size_t)c * 32 + a.forced_k];   // block move
+            s_q = q;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const Proposal q = s_q;
-    twist_table(g, q, s_cs);
+    if constexpr (!SU2) twist_table(g, q, s_cs);
     __syncthreads();
 
     for (int p = warp; p < P; p += NWARP) {
         cxd* D = Delta + p * r * r;
         cxd* Ws = Wss + p * r * r;
-        pair_delta(a.dc, p, l, q, s_cs, D);
+        if constexpr (SU2) pair_delta_su2(a.dc, p, l, s_su2 + 4, s_su2 + 20, D);
+        else pair_delta(a.dc, p, l, q, s_cs, D);
         for (int e = lane; e < r * r; e += 32) {
             const int gi = link_majorana(g, a0, b0, e / r), gj = link_majorana(g, a0, b0, e % r);
             cxd wv;
@@ -145,8 +158,13 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
                 a.since_refresh[c] += 1;
                 a.sweep_acc[c] += 1;
             }
-            if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)q.g_new;
-            else ((double*)a.links)[(size_t)c * g.n_links + l] = q.th_new;
+            if constexpr (SU2) {
+                double* dst = (double*)a.links + ((size_t)c * g.n_links + l) * 4;
+                for (int k = 0; k < 4; ++k) dst[k] = s_su2[k];
+            } else {
+                if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)q.g_new;
+                else ((double*)a.links)[(size_t)c * g.n_links + l] = q.th_new;
+            }
         }
     }
     __syncthreads();
@@ -384,6 +402,9 @@ __global__ void observe_kernel(DevConst dc, int n_chains, const void* links, con
         if (g.group == GGF_Z2) {
             const int8_t* L8 = (const int8_t*)links + (size_t)c * g.n_links;
             acc += (double)(L8[l1] * L8[l2] * L8[l3] * L8[l4]);
+        } else if (g.group == GGF_SU2) {
+            acc += plaquette_su2(link_quat(g, links, c, l1), link_quat(g, links, c, l2), link_quat(g, links, c, l3),
+                                 link_quat(g, links, c, l4));
         } else {
             const double* T = (const double*)links + (size_t)c * g.n_links;
             acc += cos(T[l1] + T[l2] - T[l3] - T[l4]);
@@ -473,8 +494,13 @@ ggf_status ggf_link_step_ex(ggf_ctx* ctx, int link, cudaStream_t st, const int* 
     size_t smem = ggf_ratio_smem(ctx->P, g.r);
     const int ev0 = ctx->prof_mark(st);
     ctx->launches += 2 + (ctx->Kc ? 1 : 0);
-    if (fp64) ratio_kernel<double, cxd><<<ch.n, NWARP * 32, smem, st>>>(a);
-    else ratio_kernel<float, cxf><<<ch.n, NWARP * 32, smem, st>>>(a);
+    if (g.group == GGF_SU2) {
+        if (fp64) ratio_kernel<double, cxd, true><<<ch.n, NWARP * 32, smem, st>>>(a);
+        else ratio_kernel<float, cxf, true><<<ch.n, NWARP * 32, smem, st>>>(a);
+    } else {
+        if (fp64) ratio_kernel<double, cxd, false><<<ch.n, NWARP * 32, smem, st>>>(a);
+        else ratio_kernel<float, cxf, false><<<ch.n, NWARP * 32, smem, st>>>(a);
+    }
     GGF_CK(cudaGetLastError());
     const int ev1 = ctx->prof_mark(st);
     ctx->prof_pair(GGF_KT_RATIO, ev0, ev1);
@@ -585,8 +611,10 @@ ggf_status ggf_prepare_sampler(ggf_ctx* ctx) {
         GGF_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
         return GGF_OK;
     };
-    GGF_TRY(cap((const void*)ratio_kernel<double, cxd>));
-    GGF_TRY(cap((const void*)ratio_kernel<float, cxf>));
+    GGF_TRY(cap((const void*)ratio_kernel<double, cxd, false>));
+    GGF_TRY(cap((const void*)ratio_kernel<float, cxf, false>));
+    GGF_TRY(cap((const void*)ratio_kernel<double, cxd, true>));
+    GGF_TRY(cap((const void*)ratio_kernel<float, cxf, true>));
     GGF_TRY(cap((const void*)gather_kernel<double, 4>));
     GGF_TRY(cap((const void*)gather_kernel<double, 8>));
     GGF_TRY(cap((const void*)gather_kernel<float, 4>));

@@ -12,7 +12,7 @@ import os
 
 import numpy as np
 
-Z2, U1 = 0, 1
+Z2, U1, SU2 = 0, 1, 2
 FP64, FP32 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 N_OBS = 3
@@ -255,7 +255,10 @@ class GGF:
     def chains_links(self, out=None):
         if out is None:
             L = self.n_links()
-            out = np.zeros((self.n_chains, L), dtype=np.int8 if self.group == Z2 else np.float64)
+            if self.group == SU2:
+                out = np.zeros((self.n_chains, L, 4))          # unit quaternions
+            else:
+                out = np.zeros((self.n_chains, L), dtype=np.int8 if self.group == Z2 else np.float64)
         self._ck(self.lib.ggf_chains_links(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
         return out
 

@@ -50,7 +50,7 @@ def header_defines():
 def test_binding_constants_match_header():
     from paper_2412_01737_gb300 import ggf
     defs, enum = header_defines()
-    pairs = {"GGF_Z2": ggf.Z2, "GGF_U1": ggf.U1, "GGF_FP64": ggf.FP64, "GGF_FP32": ggf.FP32,
+    pairs = {"GGF_Z2": ggf.Z2, "GGF_U1": ggf.U1, "GGF_SU2": ggf.SU2, "GGF_FP64": ggf.FP64, "GGF_FP32": ggf.FP32,
              "GGF_MEM_DEVICE": ggf.MEM_DEVICE, "GGF_MEM_HOST": ggf.MEM_HOST, "GGF_N_OBS": ggf.N_OBS,
              "GGF_OBS_PLAQUETTE": ggf.OBS_PLAQUETTE, "GGF_KT_RATIO": ggf.KT_RATIO,
              "GGF_KT_UPDATE": ggf.KT_UPDATE, "GGF_KT_REFRESH": ggf.KT_REFRESH, "GGF_KT_FLUSH": ggf.KT_FLUSH,

@@ -1,0 +1,86 @@
+"""GPU parity of the SU(2) path: log N(G) against the oracle's covariance
+route, plaquettes, gauge invariance, FP64 Metropolis decisions against the
+oracle's exact chain under the shared Philox stream, and FP32 chains
+replayed through the oracle.
+"""
+import numpy as np
+import pytest
+
+import ggf_inputs as gi
+from oracle import fermionic, mcmc, observables, weight
+from tests.gpu_util import ctx_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("L,K", [(1, 1), (2, 2), (3, 3), (4, 2)])
+def test_logweight_matches_oracle(L, K):
+    p = gi.make_problem(L, gi.SU2, 2, K, bond_scale=0.3)
+    links = np.ascontiguousarray(gi.random_links(p, 3, seed=21))
+    ctx = ctx_for(p)
+    got = ctx.logweight(links)
+    W = weight.Weights(p)
+    want = np.array([W.log_norm(G) for G in links])
+    assert np.abs(got - want).max() <= 1e-10
+    pl = ctx.observable(links)
+    assert np.abs(pl - observables.plaquette_mean(gi.SU2, L, links)).max() <= 1e-13
+    h = gi.random_links(gi.make_problem(L, gi.SU2, 2, 1), 1, seed=3)[0][:p.V]
+    hg = np.ascontiguousarray(gi.gauge_transform(p, links, h))
+    assert np.abs(ctx.logweight(hg) - got).max() <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("L,K,nch,nsw", [(2, 1, 3, 6), (2, 2, 2, 4), (3, 1, 2, 3)])
+def test_fp64_decisions_match_oracle(L, K, nch, nsw):
+    p = gi.make_problem(L, gi.SU2, 2, K, bond_scale=0.3)
+    start = gi.random_links(p, nch, seed=9)
+    ctx = ctx_for(p)
+    ctx.chains_init(np.ascontiguousarray(start), precision=0, refresh_every=8, seed=77, width=1.0)
+    obs = ctx.sample(nsw)
+    fin = ctx.chains_links()
+    st = ctx.chains_stats()
+    ctx.close()
+    W = weight.Weights(p)
+    for c in range(nch):
+        lk, ob, _ = mcmc.run_chain(p, W, start[c], 77, c, 0, nsw, width=1.0)
+        assert np.array_equal(ob[:, 2], obs[:, c, 2])
+        assert np.abs(lk - fin[c]).max() <= 1e-12
+        assert np.abs(ob[:, 0] - obs[:, c, 0]).max() <= 1e-12
+        assert np.abs(ob[:, 1] - obs[:, c, 1]).max() <= 1e-10
+    assert st.proposals == nch * nsw * p.n_links
+    assert 0 < st.accepts < st.proposals
+    assert st.max_drift < 1e-9
+
+
+def test_fp32_chains_replayed_through_oracle():
+    p = gi.make_problem(3, gi.SU2, 2, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(np.ascontiguousarray(gi.cold_links(p, 3)), precision=1, refresh_every=16, seed=5, width=1.0)
+    obs = ctx.sample(4)
+    fin = ctx.chains_links()
+    st = ctx.chains_stats()
+    ctx.close()
+    W = weight.Weights(p)
+    want = np.array([W.log_norm(G) for G in fin])
+    assert np.abs(obs[-1, :, 1] - want).max() <= 1e-4
+    assert np.abs(np.linalg.norm(fin, axis=-1) - 1.0).max() <= 1e-12
+    assert st.max_drift < 1e-3
+
+
+def test_fermion_bilinears_and_rejected_options():
+    from paper_2412_01737_gb300 import GGFError
+    p = gi.make_problem(2, gi.SU2, 2, 2, bond_scale=0.3)
+    links = np.ascontiguousarray(gi.random_links(p, 2, seed=4))
+    ctx = ctx_for(p)
+    with pytest.raises(GGFError):
+        ctx.chains_init(links, precision=1, delay=8)
+    ctx.chains_init(links, precision=0)
+    site, link = ctx.chains_fermion()
+    fe = fermionic.Fermionic(p)
+    for c in range(2):
+        rs, rl = fe.bilinears(links[c])
+        assert np.abs(site[c] - rs).max() <= 1e-10
+        assert np.abs(link[c] - rl).max() <= 1e-10
+    with pytest.raises(GGFError):
+        ctx.chains_electric()
+    ctx.close()
