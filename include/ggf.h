@@ -204,15 +204,18 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
  *   U(1): f_E(G)_l = -d^2/dtheta'^2 of sum_nm lambda_n^* lambda_m
  *         <psi_n(G)|psi_m(theta'; G)> / N(G) at theta' = theta_l: the Casimir
  *         J_l^2 (J = -i d/dtheta), i.e. the twist charge Q_l = sum_j q_j n_j
- *         of the link's source-end modes squared, inserted on the ket.
+ *         of the link's source-end modes squared, inserted on the ket;
+ *   SU(2): the Casimir sum_a J_a J_a of right translations of the ket's link,
+ *         i.e. sum_a (Q^a)^2 = (3/4)(n_0 + n_1 - 2 n_0 n_1) on the source
+ *         doublet, inserted on the ket.
  * Computed from the cached inverses by Wick's theorem on the covariance
  * Gamma_O = i 1 - (1 + i D) W_nm (1 + i O Gamma_X O^T) restricted to the
- * source-end Majoranas S (Z2: (-1)^{n_v} Pf(Gamma_O[S, S]); U(1): <Q_l^2>
- * from Gamma_O[S, S]); only the 8 n_v x 4 n_v block of W between the source
+ * source-end Majoranas S (Z2: (-1)^{n_v} Pf(Gamma_O[S, S]); U(1), SU(2):
+ * occupations from Gamma_O[S, S]); only the 8 n_v x 4 n_v block of W between the source
  * site and the link is read.  Pending delayed updates are folded into W first.
  *   out [n_chains][2V][2] FP64 (re, im), caller-owned.  A single
  *   configuration's value is complex; its average over p(G) is real.
- * GGF_EINVAL for SU(2) chains (not built); GGF_ESTATE before ggf_chains_init. */
+ * GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream);
 
 /* Fermionic observables (Sec. 5.2): Majorana bilinears on the physical

@@ -1,5 +1,5 @@
-"""Electric-field observables of Sec. 5.3: the Z2 link flip and the U(1)
-Casimir J_l^2.
+"""Electric-field observables of Sec. 5.3: the Z2 link flip and the U(1) and
+SU(2) Casimirs J_l^2.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -22,11 +22,18 @@ frequencies |Q| <= n_v and
     f_E(G) = sum_nm lambda_n^* lambda_m <psi_n(G)| Q_l^2 |psi_m(G)>_ket / N(G),
 Q_l^2 inserted on the ket's source-end modes before the contraction.
 
+SU(2): J^2 = sum_a J_a J_a with J_a the generators of right translations
+g -> g exp(i eps sigma_a / 2) of the ket's link (the left and right Casimirs
+agree); the twist of g exp(i eps sigma_a / 2) is U(g) exp(i eps Q^a), so
+f_E inserts sum_a (Q^a)^2, Q^a = psi^dag (sigma_a / 2) psi on the source
+doublet, which is (3/4)(n_0 + n_1 - 2 n_0 n_1).
+
 Two routes:
 
 1. Fock (the definition, tiny lattices): explicit vectors.  Z2: psi(G^(l)).
    U(1): the single-link integral itself, by quadrature over theta' on a
-   grid of 8 angles, exact for frequencies |Q| <= 3.
+   grid of 8 angles, exact for frequencies |Q| <= 3.  SU(2): the Laplacian
+   along each generator, by quadrature over eps on 8 points of [0, 4 pi).
 2. Covariance: the insertion acts on the source-end Majoranas S of link l
    (the end that carries the twist).  Composing the sites' virtual state
    (covariance D_G, the virtual block of Gamma_{A(G)}) with the bond operator
@@ -35,6 +42,7 @@ Two routes:
        Gamma_O = i 1 - (1 + i D_G) W (1 + i Gamma_X),  W = (D_G + Gamma_X)^{-1},
    and Wick's theorem with <c_a c_b> = -i Gamma_O[a, b] (a != b) gives
      Z2:   R_nm = (-1)^{n_v} Pf(Gamma_O[S, S])   (the parity of the end),
+     SU(2): R_nm = (3/4) (<n_0> + <n_1> - 2 <n_0 n_1>),
      U(1): R_nm = <Q_l^2> = sum_j q_j^2 <n_j> + 2 sum_{j<k} q_j q_k <n_j n_k>,
            <n_j> = (1 + G_{2j,2j+1}) / 2,
            <n_j n_k> = (1 + G_{2j,2j+1} + G_{2k,2k+1} + Pf G[2j,2j+1,2k,2k+1]) / 4,
@@ -48,7 +56,8 @@ exhaustive <X_l> on the 1x1 torus against explicit vectors, and on the 2x2
 lattice real and at most 1 in modulus.  U(1): the covariance route against
 the quadrature of the definition (2x2, K = 1, 2; 1x1, n_v = 2); gauge
 invariance; <J_l^2> over p(G) on the 1x1 torus (exact product quadrature) is
-real and non-negative.
+real and non-negative.  SU(2): the covariance route against the quadrature
+of the definition (1x1, K = 1, 2); gauge invariance.
 """
 from __future__ import annotations
 
@@ -57,8 +66,10 @@ import numpy as np
 from . import fock, weight
 from .pfaffian import pfaffian
 
-Z2, U1 = 0, 1
+Z2, U1, SU2 = 0, 1, 2
 N_QUAD = 8
+_PAULI = [np.array([[0, 1], [1, 0]], dtype=complex), np.array([[0, -1j], [1j, 0]]),
+          np.array([[1, 0], [0, -1]], dtype=complex)]
 
 
 def flipped(links: np.ndarray, l: int) -> np.ndarray:
@@ -93,8 +104,34 @@ def f_electric_u1_fock(fp: fock.FockPEPS, links: np.ndarray, l: int) -> complex:
     return complex(np.sum(Q ** 2 * c * np.exp(1j * Q * links[l])) / np.vdot(v, v))
 
 
+def f_electric_su2_fock(fp: fock.FockPEPS, links: np.ndarray, l: int) -> complex:
+    """SU(2) f_E(G) for link l: the Casimir J^2 = sum_a J_a J_a, J_a the
+    generators of right translations g -> g exp(i eps sigma_a / 2) of the
+    ket's link, i.e. -sum_a d^2/d eps_a^2 of the overlap at eps = 0.  Along
+    each generator the overlap is a trigonometric polynomial in eps / 2 of
+    degree <= 2 (period 4 pi), so 8 points on [0, 4 pi) give it exactly."""
+    import scipy.linalg
+    from .weight import su2_matrix
+    p = fp.p
+    lam = p.lam
+    v = (lam[:, None] * fp.psi(links)).sum(axis=0)
+    u = su2_matrix(links[l])
+    k = np.fft.fftfreq(N_QUAD, 1.0 / N_QUAD)           # phi(e) = sum_k c_k e^{i k e / 2}
+    tot = 0.0 + 0.0j
+    for sig in _PAULI:
+        phi = np.zeros(N_QUAD, dtype=complex)
+        for j in range(N_QUAD):
+            w = u @ scipy.linalg.expm(0.5j * (4.0 * np.pi * j / N_QUAD) * sig)
+            g = np.array(links, dtype=float).copy()
+            g[l] = [w[0, 0].real, w[0, 1].imag, w[0, 1].real, w[0, 0].imag]
+            phi[j] = np.vdot(v, (lam[:, None] * fp.psi(g)).sum(axis=0))
+        c = np.fft.fft(phi) / N_QUAD
+        tot += np.sum((k / 2.0) ** 2 * c)
+    return complex(tot / np.vdot(v, v))
+
+
 class Electric:
-    """Covariance route to f_E(G) for every link (Z2 flip or U(1) J^2)."""
+    """Covariance route to f_E(G) for every link (Z2 flip, U(1) or SU(2) J^2)."""
 
     def __init__(self, p):
         self.p = p
@@ -130,6 +167,11 @@ class Electric:
         p = self.p
         if p.group == Z2:
             return (-1) ** p.n_v * pfaffian(G)
+        if p.group == SU2:
+            # sum_a (Q^a)^2 on one doublet = (3/4)(n_0 + n_1 - 2 n_0 n_1)
+            occ = [(1.0 + G[2 * j, 2 * j + 1]) / 2.0 for j in range(2)]
+            pair = (1.0 + G[0, 1] + G[2, 3] + pfaffian(G)) / 4.0
+            return 0.75 * (occ[0] + occ[1] - 2.0 * pair)
         q = p.q_src
         occ = [(1.0 + G[2 * j, 2 * j + 1]) / 2.0 for j in range(p.n_v)]
         val = sum(q[j] ** 2 * occ[j] for j in range(p.n_v))

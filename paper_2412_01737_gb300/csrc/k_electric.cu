@@ -9,13 +9,17 @@
 //   U(1): I_l = Q_l^2, Q_l = sum_j q_j n_j the twist charge of those modes: the
 //         ket depends on its link angle through exp(i theta Q_l), so the
 //         single-link integral with <G|J^2|g; G> (J = -i d/dtheta) is
-//         -d^2/dtheta^2 of the overlap, i.e. the insertion of Q_l^2.
+//         -d^2/dtheta^2 of the overlap, i.e. the insertion of Q_l^2;
+//   SU(2): I_l = sum_a (Q^a)^2 on the source doublet, Q^a = psi^dag (sigma_a / 2)
+//         psi (right translations of the link act on the twist as
+//         exp(i eps Q^a)), which is (3/4)(n_0 + n_1 - 2 n_0 n_1).
 // Wick's theorem on the Gaussian operator composed of the sites' virtual
 // state and the bond operator X_nm gives the insertion's normalised
 // expectation from the covariance of that operator on the end's 2 n_v
 // Majoranas S,
 //   Gamma_O = i 1 - (1 + i D) W_nm (1 + i Gamma_tw),   G = Gamma_O[S, S],
 //   Z2:   R_nm = (-1)^{n_v} Pf(G),
+//   SU(2): R_nm = (3/4)(<n_0> + <n_1> - 2 <n_0 n_1>),
 //   U(1): R_nm = sum_j q_j^2 <n_j> + 2 sum_{j<k} q_j q_k <n_j n_k>,
 //         <n_j> = (1 + G_{2j,2j+1}) / 2,
 //         <n_j n_k> = (1 + G_{2j,2j+1} + G_{2k,2k+1} + Pf G[2j, 2j+1, 2k, 2k+1]) / 4,
@@ -54,6 +58,16 @@ __device__ __forceinline__ cxd insertion(const Geometry& g, const cxd (&G)[H][H]
         const double sg = (H / 2) % 2 ? -1.0 : 1.0;    // (-1)^{n_v}
         return sg * small_pf<H>(G);
     }
+    if constexpr (H == 4) {
+        if (g.group == GGF_SU2) {
+            // sum_a (Q^a)^2 on the doublet = (3/4)(n_0 + n_1 - 2 n_0 n_1)
+            cxd o = G[0][1] + G[2][3];
+            o.x += 2.0;                                  // 2 (<n_0> + <n_1>)
+            cxd pr = G[0][1] + G[2][3] + small_pf<H>(G);
+            pr.x += 1.0;                                 // 4 <n_0 n_1>
+            return 0.375 * (o - pr);                     // (3/4)(o / 2 - 2 pr / 4)
+        }
+    }
     cxd val = {0.0, 0.0};
 #pragma unroll
     for (int j = 0; j < H / 2; ++j) {
@@ -62,7 +76,7 @@ __device__ __forceinline__ cxd insertion(const Geometry& g, const cxd (&G)[H][H]
         occ.x += 1.0;
         val += (0.5 * qj * qj) * occ;
     }
-    if (H == 4) {
+    if constexpr (H == 4) {
         cxd pr = G[0][1] + G[2][3] + small_pf<H>(G);
         pr.x += 1.0;
         val += (0.5 * g.q[0] * g.q[1]) * pr;            // 2 q_0 q_1 <n_0 n_1>
@@ -74,7 +88,7 @@ __device__ __forceinline__ cxd insertion(const Geometry& g, const cxd (&G)[H][H]
 // conjugates.  W points at the pair's N x N inverse (row-major).
 template <class T, int H>
 __device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* W, int l, double gval,
-                            double theta, cxd& Rf, cxd& Rr) {
+                            double theta, const double* Rsu2, cxd& Rf, cxd& Rr) {
     constexpr int R = 2 * H, B = 4 * H;
     const Geometry& g = dc.g;
     int a0, b0;
@@ -94,8 +108,13 @@ __device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* 
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             cxd gt;
-            if (cplx_pair) gt = twisted<cxd>(dc, p - dc.K, l, j, b, gval, theta);
-            else gt = cxd{twisted<double>(dc, p, l, j, b, gval, theta), 0.0};
+            if (Rsu2) {
+                if (cplx_pair) gt = twisted_su2<cxd>(dc, p - dc.K, l, j, b, Rsu2);
+                else gt = cxd{twisted_su2<double>(dc, p, l, j, b, Rsu2), 0.0};
+            } else {
+                if (cplx_pair) gt = twisted<cxd>(dc, p - dc.K, l, j, b, gval, theta);
+                else gt = cxd{twisted<double>(dc, p, l, j, b, gval, theta), 0.0};
+            }
             cf[j] = times_i(gt);
             cr[j] = times_i(conjg(gt));
             if (j == b) { cf[j].x += 1.0; cr[j].x += 1.0; }
@@ -141,8 +160,14 @@ __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_c
     const int l = (blockIdx.x - c * blocks_per_chain) * ETHREADS + threadIdx.x;
     if (c >= n_chains || l >= g.n_links) return;
     const size_t NN = (size_t)g.N * g.N;
-    double gval, theta;
-    link_value<double>(dc, links, c, l, gval, theta);
+    double gval = 1.0, theta = 0.0, Rq[16];
+    const double* Rsu2 = nullptr;
+    if (g.group == GGF_SU2) {
+        doublet_rotation(link_quat(g, links, c, l), Rq);
+        Rsu2 = Rq;
+    } else {
+        link_value<double>(dc, links, c, l, gval, theta);
+    }
     const cxd* el = ell + (size_t)c * dc.P;
     double amax = -INFINITY;
     for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
@@ -157,11 +182,11 @@ __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_c
         den += E.x;
         cxd Rf, Rr;
         if (cplx) {
-            flip_ratios<CW, H>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, theta, Rf, Rr);
+            flip_ratios<CW, H>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, theta, Rsu2, Rf, Rr);
             // w_p = 2 lambda_n^* lambda_m: the (n, m) term takes E / 2, the (m, n) term its conjugate
             num += 0.5 * (E * Rf) + 0.5 * (conjg(E) * Rr);
         } else {
-            flip_ratios<RW, H>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, theta, Rf, Rr);
+            flip_ratios<RW, H>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, theta, Rsu2, Rf, Rr);
             num += E * Rf;
         }
     }
@@ -177,8 +202,6 @@ ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
-    if (g.group == GGF_SU2)
-        return ggf_fail(ctx, GGF_EINVAL, "the SU(2) electric observable (the Casimir of the doublet twist) is not built");
     // pending delayed updates first, so that W is the inverse at the current links
     GGF_TRY(ggf_flush(ctx, st));
     const int bpc = (g.n_links + ETHREADS - 1) / ETHREADS;

@@ -47,6 +47,8 @@ def _kernel_ratio(p, D, W, Gtw, S, site, lk):
     G = 1j * np.eye(h2) - left @ W[np.ix_(site, lk)] @ right
     if p.group == gi.Z2:
         return (-1) ** p.n_v * pfaffian.pfaffian(G)
+    if p.group == gi.SU2:
+        return 0.75 * ((2 + G[0, 1] + G[2, 3]) / 2 - 2 * (1 + G[0, 1] + G[2, 3] + pfaffian.pfaffian(G)) / 4)
     q = p.q_src
     val = sum(q[j] ** 2 * (1 + G[2 * j, 2 * j + 1]) / 2 for j in range(p.n_v))
     if p.n_v == 2:
@@ -55,7 +57,7 @@ def _kernel_ratio(p, D, W, Gtw, S, site, lk):
 
 
 @pytest.mark.parametrize("L,grp,n_v,K", [(3, gi.Z2, 1, 2), (2, gi.Z2, 1, 3), (2, gi.Z2, 2, 2),
-                                         (3, gi.U1, 1, 2), (2, gi.U1, 2, 3)])
+                                         (3, gi.U1, 1, 2), (2, gi.U1, 2, 3), (2, gi.SU2, 2, 2)])
 def test_block_recipe_matches_oracle(L, grp, n_v, K):
     p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
     el, Wt = electric.Electric(p), weight.Weights(p)

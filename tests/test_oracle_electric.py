@@ -114,3 +114,26 @@ def test_u1_gauge_invariance_and_positive_casimir():
     x = electric.Electric(q).expectation_exhaustive(grid)
     assert np.abs(x.imag).max() <= 1e-12
     assert x.real.min() >= 0.0 and x.real.max() > 0.01
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_su2_casimir_matches_quadrature(K):
+    """SU(2): (3/4) <n_0 + n_1 - 2 n_0 n_1> of the source doublet from Gamma_O
+    against -sum_a d^2/d eps_a^2 of the overlap under right translations of
+    the ket's link, by exact quadrature on explicit vectors (1x1 torus)."""
+    p = gi.make_problem(1, gi.SU2, 2, K, bond_scale=0.3)
+    fp, el = fock.FockPEPS(p), electric.Electric(p)
+    for G in gi.random_links(p, 2, seed=7):
+        ref = np.array([electric.f_electric_su2_fock(fp, G, l) for l in range(p.n_links)])
+        assert np.abs(ref).max() > 0.1
+        assert np.abs(el.f_electric(G) - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_su2_casimir_gauge_invariance():
+    p = gi.make_problem(2, gi.SU2, 2, 2, bond_scale=0.3)
+    el = electric.Electric(p)
+    G = gi.random_links(p, 2, seed=9)
+    h = gi.random_links(p, 1, seed=10)[0][:p.V]
+    for a, b in zip(G, gi.gauge_transform(p, G, h)):
+        fa, fb = el.f_electric(a), el.f_electric(b)
+        assert np.abs(fa - fb).max() <= 1e-11 * np.abs(fa).max()

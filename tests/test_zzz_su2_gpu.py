@@ -67,7 +67,7 @@ def test_fp32_chains_replayed_through_oracle():
     assert st.max_drift < 1e-3
 
 
-def test_fermion_bilinears_and_rejected_options():
+def test_fermion_bilinears_and_rejected_delay():
     from paper_2412_01737_gb300 import GGFError
     p = gi.make_problem(2, gi.SU2, 2, 2, bond_scale=0.3)
     links = np.ascontiguousarray(gi.random_links(p, 2, seed=4))
@@ -81,6 +81,19 @@ def test_fermion_bilinears_and_rejected_options():
         rs, rl = fe.bilinears(links[c])
         assert np.abs(site[c] - rs).max() <= 1e-10
         assert np.abs(link[c] - rl).max() <= 1e-10
-    with pytest.raises(GGFError):
-        ctx.chains_electric()
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+def test_casimir_matches_oracle(precision, tol):
+    from oracle import electric
+    p = gi.make_problem(3, gi.SU2, 2, 2, bond_scale=0.3)
+    links = np.ascontiguousarray(gi.random_links(p, 2, seed=12))
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=precision)
+    got = ctx.chains_electric()
+    el = electric.Electric(p)
+    for c in range(2):
+        ref = el.f_electric(links[c])
+        assert np.abs(got[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
     ctx.close()
