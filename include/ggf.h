@@ -26,8 +26,8 @@
  *   a2 sigma_y + a3 sigma_z); the source-end doublet is twisted by
  *   psi^dag_j -> sum_k psi^dag_k u_kj (the right-regular action, App. A).
  *   The weight is then invariant under u_l -> h_t^dag u_l h_s, and the
- *   plaquette observable is (1/2) tr(u1^dag u2^dag u3 u4).  SU(2) chains use
- *   immediate updates (delay <= 1); the proposal is u -> r u with
+ *   plaquette observable is (1/2) tr(u1^dag u2^dag u3 u4).  The SU(2)
+ *   proposal is u -> r u with
  *   r = cos d + i sin d (n . sigma), d = width (u_prop - 1/2) and n uniform
  *   on the sphere from Philox words 2 and 3 (z = 2 u - 1, phi = 2 pi u).
  *

@@ -431,8 +431,6 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     if (opts->precision != GGF_FP64 && opts->precision != GGF_FP32)
         return ggf_fail(ctx, GGF_EINVAL, "precision must be GGF_FP64 or GGF_FP32");
     if (opts->refresh_every < 1) return ggf_fail(ctx, GGF_EINVAL, "refresh_every must be >= 1");
-    if (ctx->g.group == GGF_SU2 && opts->delay > 1)
-        return ggf_fail(ctx, GGF_EINVAL, "SU(2) chains use immediate updates (delay <= 1)");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     ggf_free_chains(ctx);

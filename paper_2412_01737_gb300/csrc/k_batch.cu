@@ -199,7 +199,9 @@ __device__ __forceinline__ void small_update(T* Gm, T* Xm, const typename Sc<T>:
 }
 
 // One CTA (NWARP warps) per chain runs the batch's kb link steps in order.
-template <class RW, class CW>
+// SU2: SU(2) links (quaternion proposal and doublet twist); the Z2 and U(1)
+// instantiations (SU2 = false) do not contain that code.
+template <class RW, class CW, bool SU2>
 __global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
     extern __shared__ cxd sm[];
     const Geometry& g = a.dc.g;
@@ -220,6 +222,7 @@ __global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
     int* Tl = (int*)(Zs + P * r * r);      // [kb r]
     __shared__ Proposal s_q;
     __shared__ double s_cs[8];
+    __shared__ double s_su2[36];          // SU2: new quaternion, old and new doublet rotations
     __shared__ int s_accept, s_any;
     typedef typename Sc<RW>::R RR;
     const size_t NK = panel_plane(N, KRM), SS = (size_t)KRM * KRM;
@@ -236,15 +239,24 @@ __global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
 
     for (int j = 0; j < a.kb; ++j) {
         const int l = a.l0 + j, jr = j * r;
-        if (threadIdx.x == 0) s_q = draw_proposal(g, a.links, c, l, sweep, a.seed, a.width);
+        if constexpr (SU2) {
+            if (threadIdx.x == 0) {
+                Proposal qq{};
+                qq.u_acc = draw_su2(g, a.links, c, l, sweep, a.seed, a.width, s_su2, s_su2 + 4, s_su2 + 20);
+                s_q = qq;
+            }
+        } else {
+            if (threadIdx.x == 0) s_q = draw_proposal(g, a.links, c, l, sweep, a.seed, a.width);
+        }
         __syncthreads();
         const Proposal q = s_q;
-        twist_table(g, q, s_cs);
+        if constexpr (!SU2) twist_table(g, q, s_cs);
         __syncthreads();
         for (int p = warp; p < P; p += NWARP) {
             cxd* D = Delta + p * r * r;
             cxd* Ws = Wss + p * r * r;
-            pair_delta(a.dc, p, l, q, s_cs, D);
+            if constexpr (SU2) pair_delta_su2(a.dc, p, l, s_su2 + 4, s_su2 + 20, D);
+            else pair_delta(a.dc, p, l, q, s_cs, D);
             for (int e = lane; e < r * r; e += 32) {
                 const size_t off = (size_t)(jr + e / r) * KRM + jr + e % r;
                 if (p < K) Ws[e] = loadc((const RW*)a.Sr + ((size_t)c * K + p) * 2 * SS + off);
@@ -267,8 +279,13 @@ __global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
                 atomicAdd(&a.counters[1], 1ULL);
                 a.since_refresh[c] += 1;
                 a.sweep_acc[c] += 1;
-                if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)q.g_new;
-                else ((double*)a.links)[(size_t)c * g.n_links + l] = q.th_new;
+                if constexpr (SU2) {
+                    double* dst = (double*)a.links + ((size_t)c * g.n_links + l) * 4;
+                    for (int k = 0; k < 4; ++k) dst[k] = s_su2[k];
+                } else {
+                    if (g.group == GGF_Z2) ((int8_t*)a.links)[(size_t)c * g.n_links + l] = (int8_t)q.g_new;
+                    else ((double*)a.links)[(size_t)c * g.n_links + l] = q.th_new;
+                }
             }
         }
         __syncthreads();
@@ -415,8 +432,10 @@ ggf_status ggf_prepare_batch(ggf_ctx* ctx) {
     GGF_TRY(cap((const void*)batch_gather<float>));
     GGF_TRY(cap((const void*)batch_gather<cxd>));
     GGF_TRY(cap((const void*)batch_gather<cxf>));
-    GGF_TRY(cap((const void*)batch_steps<double, cxd>));
-    GGF_TRY(cap((const void*)batch_steps<float, cxf>));
+    GGF_TRY(cap((const void*)batch_steps<double, cxd, false>));
+    GGF_TRY(cap((const void*)batch_steps<float, cxf, false>));
+    GGF_TRY(cap((const void*)batch_steps<double, cxd, true>));
+    GGF_TRY(cap((const void*)batch_steps<float, cxf, true>));
     GGF_TRY(cap((const void*)batch_apply<double, 4>));
     GGF_TRY(cap((const void*)batch_apply<float, 4>));
     GGF_TRY(cap((const void*)batch_apply<cxd, 4>));
@@ -496,8 +515,13 @@ ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st) {
         a.Sr = Sr;
         a.Sc_ = Sc_;
         const size_t smem = steps_smem(ctx->P, r, KRM, fp64 ? sizeof(cxd) : sizeof(cxf));
-        if (fp64) batch_steps<double, cxd><<<ch.n, NWARP * 32, smem, st>>>(a);
-        else batch_steps<float, cxf><<<ch.n, NWARP * 32, smem, st>>>(a);
+        if (g.group == GGF_SU2) {
+            if (fp64) batch_steps<double, cxd, true><<<ch.n, NWARP * 32, smem, st>>>(a);
+            else batch_steps<float, cxf, true><<<ch.n, NWARP * 32, smem, st>>>(a);
+        } else {
+            if (fp64) batch_steps<double, cxd, false><<<ch.n, NWARP * 32, smem, st>>>(a);
+            else batch_steps<float, cxf, false><<<ch.n, NWARP * 32, smem, st>>>(a);
+        }
         GGF_CK(cudaGetLastError());
     }
     const int ev2 = ctx->prof_mark(st);

@@ -1,7 +1,8 @@
 """GPU parity of the SU(2) path: log N(G) against the oracle's covariance
-route, plaquettes, gauge invariance, FP64 Metropolis decisions against the
-oracle's exact chain under the shared Philox stream, and FP32 chains
-replayed through the oracle.
+route, plaquettes, gauge invariance, FP64 Metropolis decisions (immediate
+and batched updates) against the oracle's exact chain under the shared
+Philox stream, FP32 chains replayed through the oracle, and the observables
+computed from the chains' inverses.
 """
 import numpy as np
 import pytest
@@ -30,12 +31,13 @@ def test_logweight_matches_oracle(L, K):
     ctx.close()
 
 
+@pytest.mark.parametrize("delay", [1, 4])
 @pytest.mark.parametrize("L,K,nch,nsw", [(2, 1, 3, 6), (2, 2, 2, 4), (3, 1, 2, 3)])
-def test_fp64_decisions_match_oracle(L, K, nch, nsw):
+def test_fp64_decisions_match_oracle(L, K, nch, nsw, delay):
     p = gi.make_problem(L, gi.SU2, 2, K, bond_scale=0.3)
     start = gi.random_links(p, nch, seed=9)
     ctx = ctx_for(p)
-    ctx.chains_init(np.ascontiguousarray(start), precision=0, refresh_every=8, seed=77, width=1.0)
+    ctx.chains_init(np.ascontiguousarray(start), precision=0, refresh_every=8, seed=77, width=1.0, delay=delay)
     obs = ctx.sample(nsw)
     fin = ctx.chains_links()
     st = ctx.chains_stats()
@@ -52,10 +54,12 @@ def test_fp64_decisions_match_oracle(L, K, nch, nsw):
     assert st.max_drift < 1e-9
 
 
-def test_fp32_chains_replayed_through_oracle():
+@pytest.mark.parametrize("delay", [1, 8])
+def test_fp32_chains_replayed_through_oracle(delay):
     p = gi.make_problem(3, gi.SU2, 2, 2, bond_scale=0.3)
     ctx = ctx_for(p)
-    ctx.chains_init(np.ascontiguousarray(gi.cold_links(p, 3)), precision=1, refresh_every=16, seed=5, width=1.0)
+    ctx.chains_init(np.ascontiguousarray(gi.cold_links(p, 3)), precision=1, refresh_every=16, seed=5, width=1.0,
+                    delay=delay)
     obs = ctx.sample(4)
     fin = ctx.chains_links()
     st = ctx.chains_stats()
@@ -67,13 +71,10 @@ def test_fp32_chains_replayed_through_oracle():
     assert st.max_drift < 1e-3
 
 
-def test_fermion_bilinears_and_rejected_delay():
-    from paper_2412_01737_gb300 import GGFError
+def test_fermion_bilinears():
     p = gi.make_problem(2, gi.SU2, 2, 2, bond_scale=0.3)
     links = np.ascontiguousarray(gi.random_links(p, 2, seed=4))
     ctx = ctx_for(p)
-    with pytest.raises(GGFError):
-        ctx.chains_init(links, precision=1, delay=8)
     ctx.chains_init(links, precision=0)
     site, link = ctx.chains_fermion()
     fe = fermionic.Fermionic(p)
