@@ -39,6 +39,9 @@ WORKLOADS = {
              "8x8 periodic Z2, K=1 (M 512x512), 1024 chains, FP32 rank-r updates, FP64 refresh every 64 accepts"),
     "cfg2_fp64": (8, 0, 1, 1, 1024, 0, 1024, 1,
                   "8x8 periodic Z2, K=1 (M 512x512), 1024 chains, plain FP64 local updates"),
+    "su2": (16, 2, 2, 2, 256, 1, 1 << 30, 16,
+            "16x16 periodic SU(2), n_v=2 (one doublet per link end, M 4096x4096), K=2, 256 chains, FP32 "
+            "batched updates (16 links per batch)"),
     "cfg4": (16, 1, 2, 4, 192, 1, 1 << 30, 32,
              "16x16 periodic U(1), n_v=2, K=4 with the learned 4x4-block proposal (BF16 conv net trained on "
              "plain-sampler configurations); step = 1 local sweep + 16 block moves; 192 resident chains"),
@@ -209,7 +212,7 @@ def unit_bytes(p, prec):
 # Largest lattice on which the oracle times a proposal directly; bigger
 # workloads are timed on this lattice with the same group, n_v and K and the
 # per-proposal time scaled by the cube of the Pfaffian size.
-CPU_PROXY_L = {"cfg3": 6, "cfg4": 6}
+CPU_PROXY_L = {"cfg3": 6, "cfg4": 6, "su2": 6}
 
 
 def cpu_sample(name, budget_s=15.0, workers=None):
@@ -243,7 +246,7 @@ def _cpu_worker(name, chain, budget_s, proxy_L=None):
     import ggf_inputs as gi
     from oracle import weight
     from oracle.mcmc import propose
-    from oracle.philox import draws
+    from oracle.philox import draws4
     p, *_ = problem_for(name)
     if proxy_L:
         p = gi.make_problem(proxy_L, p.group, p.n_v, p.K, seed=BASE_SEED)
@@ -254,9 +257,9 @@ def _cpu_worker(name, chain, budget_s, proxy_L=None):
     n = 0
     while time.time() - t0 < budget_s:
         l = n % p.n_links
-        u_acc, u_prop = draws(BASE_SEED, chain, n // p.n_links, l)
+        u_acc, u_prop, u_z, u_phi = draws4(BASE_SEED, chain, n // p.n_links, l)
         new = links.copy()
-        new[l] = propose(p.group, links[l], u_prop, 0.5)
+        new[l] = propose(p.group, links[l], u_prop, 0.5, u_z, u_phi)
         ln = W.log_norm(new)
         if np.isfinite(ln) and u_acc < np.exp(ln - logN):
             links, logN = new, ln
