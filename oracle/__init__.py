@@ -24,6 +24,8 @@ electric The Z2 electric (link-flip) observable of Sec. 5.3: f_E(G) from
 fermionic  Majorana expectations of Sec. 5.2 (densities, link bilinears,
          general monomials) from explicit vectors and from the physical
          covariance A + B W B^T of each pair.
+variational  Per-configuration K x K matrices of the observables (Hermitian
+         forms in lambda) and the generalised-eigenvector optimum of lambda.
 
 Parity status per function is listed in each module's docstring; every
 function is pinned by a `-m "not gpu"` test except where a docstring says

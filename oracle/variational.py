@@ -1,0 +1,117 @@
+"""Variational optimisation of the superposition weights lambda_n (Sec. 4,
+Sec. 5; the Ansatz's parameters are meant to be optimised against an energy
+built from the observables of Sec. 5).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+For fixed Gaussians every per-configuration quantity of Secs. 5.1-5.3 is a
+Hermitian form in lambda:
+    N(G)   = lambda^dag N(G) lambda,          N(G)_nm  = N_nm(G),
+    O(G)   = lambda^dag Ohat(G) lambda,       Ohat(G)_nm = N_nm(G) o_nm(G),
+with o_nm the per-pair normalised expectation: W(G) for a Wilson loop (the
+same for every pair), R_nm(G) for the electric term (oracle.electric), and
+-i Gamma_eff^nm[a, b] for a Majorana bilinear (oracle.fermionic).  Hence
+    <O>_lambda = lambda^dag Obar lambda / lambda^dag Nbar lambda,
+    Obar = sum_G Ohat(G),  Nbar = sum_G N(G)
+(integrals over the group for U(1)), and the lambda minimising an energy
+E = sum_k c_k <O_k> is the lowest generalised eigenvector of
+    (sum_k c_k Obar_k) lambda = E Nbar lambda.
+Samples G_i of p_lambda0 estimate both matrices up to the common factor
+1 / sum_G N_lambda0(G): Obar ~ mean_i Ohat(G_i) / N_lambda0(G_i).  Per
+configuration the local matrices are returned in that normalised form
+(Ohat(G) / N_lambda0(G), N(G) / N_lambda0(G)), which needs no absolute scale.
+
+Pinned (tests/test_oracle_variational.py): on the 2x2 Z2 lattice, for random
+lambda, the Hermitian forms built from exhaustive sums reproduce the direct
+exhaustive expectations of the plaquette, the link flip and the densities
+computed with that lambda; the generalised eigenvector minimises the energy
+over random lambda; the forms are Hermitian and Nbar positive definite.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.linalg
+
+from . import electric, fermionic, weight
+from .observables import plaquette_values
+
+
+class LocalMatrices:
+    """Per-configuration K x K matrices for the observables of Sec. 5."""
+
+    def __init__(self, p):
+        self.p = p
+        self.W = weight.Weights(p)
+        self.el = electric.Electric(p)
+        self.fe = fermionic.Fermionic(p)
+
+    def __call__(self, links):
+        """dict of K x K (or (n, K, K)) arrays divided by N_lambda0(G):
+        'norm' N(G); 'plaquette' mean plaquette; 'electric' per link;
+        'density' per site (the bilinear c_2s c_2s+1)."""
+        p = self.p
+        lnm = self.W.log_n_matrix(links)
+        logN = weight.combine(lnm, p.lam)
+        Nn = np.exp(lnm - logN)                                  # N(G) / N_lambda0(G)
+        out = {"norm": Nn}
+        out["plaquette"] = Nn * plaquette_values(p.group, p.L, links).mean()
+        R = self.el.ratios(links)                                # [n, m, l]
+        out["electric"] = np.moveaxis(Nn[:, :, None] * R, 2, 0)  # [l, n, m]
+        Ge = self.fe.gamma_eff(links)
+        dens = np.zeros((p.V, p.K, p.K), dtype=complex)
+        for (n, m), G in Ge.items():
+            for s in range(p.V):
+                dens[s, n, m] = Nn[n, m] * (-1j) * G[2 * s, 2 * s + 1]
+        out["density"] = dens
+        return out
+
+
+def exhaustive(p, configs, weights=None):
+    """Sums over an explicit list of configurations (optionally weighted, e.g.
+    quadrature weights) of the local matrices, all divided by the same
+    constant sum_G N_lambda0(G).  Returns the dict of summed matrices."""
+    lm = LocalMatrices(p)
+    W = lm.W
+    logs = np.array([W.log_norm(G) for G in configs])
+    wts = np.exp(logs - logs.max())
+    if weights is not None:
+        wts = wts * weights
+    wts = wts / wts.sum()                                        # p_lambda0 on the list
+    acc = None
+    for w, G in zip(wts, configs):
+        loc = lm(G)
+        if acc is None:
+            acc = {k: w * v for k, v in loc.items()}
+        else:
+            for k, v in loc.items():
+                acc[k] = acc[k] + w * v
+    return acc
+
+
+def expectation(Obar, Nbar, lam):
+    """lambda^dag Obar lambda / lambda^dag Nbar lambda (Obar may carry leading axes)."""
+    lam = np.asarray(lam)
+    num = np.einsum("n,...nm,m->...", np.conj(lam), Obar, lam)
+    den = np.einsum("n,nm,m->", np.conj(lam), Nbar, lam)
+    return num / den
+
+
+def linear_method(Hbar, Nbar):
+    """Lowest generalised eigenpair of (Hbar + Hbar^dag)/2 lambda = E Nbar lambda
+    (Nbar Hermitian positive definite); lambda normalised to unit 2-norm with
+    lambda_0 real positive."""
+    H = 0.5 * (Hbar + Hbar.conj().T)
+    Nm = 0.5 * (Nbar + Nbar.conj().T)
+    w, v = scipy.linalg.eigh(H, Nm)
+    lam = v[:, 0]
+    lam = lam / np.linalg.norm(lam)
+    if abs(lam[0]) > 0:
+        lam = lam * (abs(lam[0]) / lam[0])
+    return float(w[0]), lam
+
+
+def with_lambda(p, lam):
+    """The same problem with other superposition weights."""
+    return dataclasses.replace(p, lam=np.asarray(lam, dtype=np.complex128))

@@ -1,0 +1,87 @@
+"""Pins of the lambda optimisation in the oracle (oracle/variational.py).
+
+On the 2x2 Z2 lattice everything is exhaustive: the Hermitian forms built
+from summed local matrices must reproduce the direct expectations computed
+with any other lambda; the generalised eigenvector must minimise the energy;
+and independent samples of p_lambda0 must estimate the same energy.
+"""
+import numpy as np
+import pytest
+
+import ggf_inputs as gi
+from oracle import electric, fermionic, variational as va, weight
+from oracle.observables import plaquette_values
+
+
+@pytest.fixture(scope="module")
+def setup():
+    p = gi.make_problem(2, gi.Z2, 1, 3, bond_scale=0.3)
+    cfgs = gi.all_z2_configs(p)
+    return p, cfgs, va.exhaustive(p, cfgs)
+
+
+def test_forms_reproduce_direct_expectations(setup):
+    p, cfgs, S = setup
+    rng = np.random.default_rng(1)
+    pl = plaquette_values(gi.Z2, 2, cfgs).mean(axis=1)
+    for _ in range(2):
+        z = rng.normal(size=p.K) + 1j * rng.normal(size=p.K)
+        lam = z / np.linalg.norm(z)
+        q = va.with_lambda(p, lam)
+        W = weight.Weights(q)
+        logs = np.array([W.log_norm(G) for G in cfgs])
+        w = np.exp(logs - logs.max())
+        w /= w.sum()
+        assert abs(va.expectation(S["plaquette"], S["norm"], lam) - np.sum(w * pl)) <= 1e-13
+        ref_el = electric.Electric(q).expectation_exhaustive(cfgs)
+        assert np.abs(va.expectation(S["electric"], S["norm"], lam) - ref_el).max() <= 1e-13
+        fe = fermionic.Fermionic(q)
+        ref_d = sum(wi * fe.bilinears(G)[0] for wi, G in zip(w, cfgs))
+        assert np.abs(va.expectation(S["density"], S["norm"], lam) - ref_d).max() <= 1e-13
+
+
+def test_linear_method_minimises_the_energy(setup):
+    p, cfgs, S = setup
+    assert np.abs(S["norm"] - S["norm"].conj().T).max() <= 1e-14
+    assert np.linalg.eigvalsh(S["norm"]).min() > 0
+    H = -1.0 * S["plaquette"] + 0.5 * S["electric"].sum(axis=0)
+    assert np.abs(H - H.conj().T).max() <= 1e-12          # Hermitian once summed over G
+    E0, lam0 = va.linear_method(H, S["norm"])
+    assert abs(va.expectation(H, S["norm"], lam0) - E0) <= 1e-12
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        z = rng.normal(size=p.K) + 1j * rng.normal(size=p.K)
+        assert va.expectation(H, S["norm"], z).real >= E0 - 1e-12
+    # the sampling weights of the problem are not the optimum
+    assert va.expectation(H, S["norm"], p.lam).real > E0 + 1e-3
+
+
+def test_sampled_matrices_estimate_the_energy(setup):
+    """Independent samples of p_lambda0 (drawn from the exhaustive
+    distribution) estimate Hbar and Nbar, hence E(lambda), within errors."""
+    p, cfgs, S = setup
+    W = weight.Weights(p)
+    logs = np.array([W.log_norm(G) for G in cfgs])
+    w = np.exp(logs - logs.max())
+    w /= w.sum()
+    rng = np.random.default_rng(3)
+    idx = rng.choice(len(cfgs), size=4000, p=w)
+    lm = va.LocalMatrices(p)
+    cache = {}
+    Hs, Ns = [], []
+    for i in idx:
+        if i not in cache:
+            loc = lm(cfgs[i])
+            cache[i] = (-1.0 * loc["plaquette"] + 0.5 * loc["electric"].sum(axis=0), loc["norm"])
+        Hs.append(cache[i][0])
+        Ns.append(cache[i][1])
+    Hs, Ns = np.array(Hs), np.array(Ns)
+    H = -1.0 * S["plaquette"] + 0.5 * S["electric"].sum(axis=0)
+    _, lam0 = va.linear_method(H, S["norm"])
+    e_loc = np.einsum("n,inm,m->i", np.conj(lam0), Hs, lam0)
+    n_loc = np.einsum("n,inm,m->i", np.conj(lam0), Ns, lam0)
+    est = e_loc.mean() / n_loc.mean()
+    # delta-method error of a ratio of means
+    r = (e_loc - est * n_loc) / n_loc.mean()
+    err = np.sqrt(np.mean(np.abs(r) ** 2) / len(idx))
+    assert abs(est - va.expectation(H, S["norm"], lam0)) <= 5 * err
