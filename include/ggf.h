@@ -235,6 +235,28 @@ ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream)
  *   caller-owned; either may be NULL (not both). */
 ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem, void* stream);
 
+/* Per-pair parts of the per-configuration quantities, for optimising the
+ * superposition weights: every quantity of Secs. 5.1-5.3 is a Hermitian form
+ * in lambda, O(G) = sum_nm lambda_n^* lambda_m N_nm(G) o_nm(G), so
+ *   <O>_lambda = lambda^dag Obar lambda / lambda^dag Nbar lambda
+ * with Obar, Nbar the expectations over p(G) (the context's lambda) of the
+ * matrices below; the lambda minimising an energy built from them is the
+ * lowest generalised eigenvector.  out [n_chains][items][K][K][2] FP64 (re,
+ * im) of N_nm(G) o_nm(G) / N(G), every ordered pair (n, m):
+ *   GGF_PAIRS_NORM      items = 1: o_nm = 1 (Wilson loops: multiply by W(G));
+ *   GGF_PAIRS_ELECTRIC  items = 2V: the electric insertion per link
+ *                       (ggf_chains_electric's terms);
+ *   GGF_PAIRS_SITE      items = V: -i Gamma_eff^nm[2s, 2s+1];
+ *   GGF_PAIRS_LINK      items = 2V x 2 x 2: the link blocks of
+ *                       ggf_chains_fermion, per pair.
+ * Contracting with lambda_n^* lambda_m gives the combined quantity.  Pending
+ * delayed updates are folded into W first. */
+#define GGF_PAIRS_NORM 0
+#define GGF_PAIRS_ELECTRIC 1
+#define GGF_PAIRS_SITE 2
+#define GGF_PAIRS_LINK 3
+ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* stream);
+
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
  * L^2.  For tests and diagnostics. */

@@ -18,8 +18,10 @@ ggf_status ggf_prepare_batch(ggf_ctx* ctx);
 ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64);
 ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st);
 ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
-ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
-ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cudaStream_t st);
+ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st);
+ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cxd* d_pair_site, cxd* d_pair_link,
+                       cudaStream_t st);
+ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -762,12 +764,12 @@ ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream)
     if (mem == GGF_MEM_HOST) {
         DBuf d;
         GGF_TRY(dalloc(ctx, d, bytes));
-        GGF_TRY(ggf_electric(ctx, (cxd*)d.p, st));
+        GGF_TRY(ggf_electric(ctx, (cxd*)d.p, nullptr, st));
         GGF_CK(cudaMemcpyAsync(out, d.p, bytes, cudaMemcpyDeviceToHost, st));
         GGF_CK(cudaStreamSynchronize(st));
         return check_err_word(ctx);
     }
-    GGF_TRY(ggf_electric(ctx, (cxd*)out, st));
+    GGF_TRY(ggf_electric(ctx, (cxd*)out, nullptr, st));
     return GGF_OK;
 }
 
@@ -782,13 +784,47 @@ ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem,
         DBuf ds, dl;
         if (site) GGF_TRY(dalloc(ctx, ds, sb));
         if (link) GGF_TRY(dalloc(ctx, dl, lb));
-        GGF_TRY(ggf_fermion(ctx, (cxd*)ds.p, (cxd*)dl.p, st));
+        GGF_TRY(ggf_fermion(ctx, (cxd*)ds.p, (cxd*)dl.p, nullptr, nullptr, st));
         if (site) GGF_CK(cudaMemcpyAsync(site, ds.p, sb, cudaMemcpyDeviceToHost, st));
         if (link) GGF_CK(cudaMemcpyAsync(link, dl.p, lb, cudaMemcpyDeviceToHost, st));
         GGF_CK(cudaStreamSynchronize(st));
         return check_err_word(ctx);
     }
-    GGF_TRY(ggf_fermion(ctx, (cxd*)site, (cxd*)link, st));
+    GGF_TRY(ggf_fermion(ctx, (cxd*)site, (cxd*)link, nullptr, nullptr, st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!out) return ggf_fail(ctx, GGF_EINVAL, "null out");
+    const Geometry& g = ctx->g;
+    const size_t KK = (size_t)ctx->K * ctx->K, n = ctx->ch.n;
+    size_t items;
+    switch (what) {
+        case GGF_PAIRS_NORM: items = 1; break;
+        case GGF_PAIRS_ELECTRIC: items = g.n_links; break;
+        case GGF_PAIRS_SITE: items = g.V; break;
+        case GGF_PAIRS_LINK: items = (size_t)g.n_links * 4; break;
+        default: return ggf_fail(ctx, GGF_EINVAL, "unknown pair quantity");
+    }
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = n * items * KK * sizeof(cxd);
+    DBuf d;
+    cxd* dst = (cxd*)out;
+    if (mem == GGF_MEM_HOST) {
+        GGF_TRY(dalloc(ctx, d, bytes));
+        dst = (cxd*)d.p;
+    }
+    if (what == GGF_PAIRS_NORM) GGF_TRY(ggf_pair_norm(ctx, dst, st));
+    else if (what == GGF_PAIRS_ELECTRIC) GGF_TRY(ggf_electric(ctx, nullptr, dst, st));
+    else if (what == GGF_PAIRS_SITE) GGF_TRY(ggf_fermion(ctx, nullptr, nullptr, dst, nullptr, st));
+    else GGF_TRY(ggf_fermion(ctx, nullptr, nullptr, nullptr, dst, st));
+    if (mem == GGF_MEM_HOST) {
+        GGF_CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return check_err_word(ctx);
+    }
     return GGF_OK;
 }
 

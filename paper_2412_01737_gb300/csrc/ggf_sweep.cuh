@@ -256,6 +256,16 @@ __device__ __forceinline__ cxd bordered_ratio(const cxd* D, const cxd* Ws, cxd* 
     return warp_pfaffian(Bw, n2);
 }
 
+// Ordered Gaussian indices (n, m) of pair p: p < K is (p, p); the pairs n < m
+// follow in lexicographic order.
+__device__ __forceinline__ void pair_nm(int K, int p, int& n, int& m) {
+    if (p < K) { n = m = p; return; }
+    int k = p - K;
+    n = 0;
+    while (k >= K - 1 - n) { k -= K - 1 - n; ++n; }
+    m = n + 1 + k;
+}
+
 // Numerator and denominator of N(G')/N(G) = Re sum_p w_p e^{logc_p + ell_p} rho_p
 // / Re sum_p w_p e^{logc_p + ell_p}, scaled by the largest modulus (FP64).
 __device__ __forceinline__ void combine_pairs(const DevConst& dc, const cxd* ell_c, const cxd* rho, double& sn,

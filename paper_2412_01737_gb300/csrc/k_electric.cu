@@ -150,11 +150,12 @@ __device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* 
     Rr = insertion<H>(g, Xr);
 }
 
-// One thread per (chain, link); out[c][l] = f_E(G_c)_l.
+// One thread per (chain, link); out[c][l] = f_E(G_c)_l (if out is set) and
+// pair_out[c][l][n][m] = N_nm(G) R_nm / N(G) for every ordered pair (if set).
 template <class RW, class CW, int H>
 __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_chains, int blocks_per_chain,
                                                             const void* links, const RW* Wr, const CW* Wc,
-                                                            const cxd* ell, cxd* out) {
+                                                            const cxd* ell, cxd* out, cxd* pair_out) {
     const Geometry& g = dc.g;
     const int c = blockIdx.x / blocks_per_chain;
     const int l = (blockIdx.x - c * blocks_per_chain) * ETHREADS + threadIdx.x;
@@ -171,35 +172,88 @@ __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_c
     const cxd* el = ell + (size_t)c * dc.P;
     double amax = -INFINITY;
     for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
+    // N(G) (scaled by e^{-amax}) = Re sum_p w_p N_p
     double den = 0.0;
+    for (int p = 0; p < dc.P; ++p) {
+        cxd e = dc.logc[p] + el[p];
+        if (p < dc.K) e.y = 0.0;
+        e.x -= amax;
+        den += (dc.w[p] * cexp_(e)).x;
+    }
+    const double iden = 1.0 / den;
     cxd num = {0.0, 0.0};
     for (int p = 0; p < dc.P; ++p) {
         cxd e = dc.logc[p] + el[p];
         const bool cplx = p >= dc.K;
         if (!cplx) e.y = 0.0;
         e.x -= amax;
-        const cxd E = dc.w[p] * cexp_(e);        // w_p N_p, scaled
-        den += E.x;
+        const cxd Np = iden * cexp_(e);          // N_nm(G) / N(G)
+        const cxd E = dc.w[p] * Np;              // w_p N_p / N(G)
         cxd Rf, Rr;
+        int n, m;
+        pair_nm(dc.K, p, n, m);
+        cxd* po = pair_out ? pair_out + ((size_t)c * g.n_links + l) * dc.K * dc.K : nullptr;
         if (cplx) {
             flip_ratios<CW, H>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, theta, Rsu2, Rf, Rr);
             // w_p = 2 lambda_n^* lambda_m: the (n, m) term takes E / 2, the (m, n) term its conjugate
             num += 0.5 * (E * Rf) + 0.5 * (conjg(E) * Rr);
+            if (po) {
+                po[n * dc.K + m] = Np * Rf;
+                po[m * dc.K + n] = conjg(Np) * Rr;
+            }
         } else {
             flip_ratios<RW, H>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, theta, Rsu2, Rf, Rr);
             num += E * Rf;
+            if (po) po[n * dc.K + n] = Np * Rf;
         }
     }
-    out[(size_t)c * g.n_links + l] = cxd{num.x / den, num.y / den};
+    if (out) out[(size_t)c * g.n_links + l] = num;
+}
+
+// One thread per chain: out[c][n][m] = N_nm(G) / N(G) for every ordered pair.
+__global__ void pair_norm_kernel(DevConst dc, int n_chains, const cxd* ell, cxd* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    const int K = dc.K;
+    const cxd* el = ell + (size_t)c * dc.P;
+    double amax = -INFINITY;
+    for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
+    double den = 0.0;
+    for (int p = 0; p < dc.P; ++p) {
+        cxd e = dc.logc[p] + el[p];
+        if (p < K) e.y = 0.0;
+        e.x -= amax;
+        den += (dc.w[p] * cexp_(e)).x;
+    }
+    cxd* o = out + (size_t)c * K * K;
+    for (int p = 0; p < dc.P; ++p) {
+        cxd e = dc.logc[p] + el[p];
+        if (p < K) e.y = 0.0;
+        e.x -= amax;
+        const cxd Np = (1.0 / den) * cexp_(e);
+        int n, m;
+        pair_nm(K, p, n, m);
+        o[n * K + m] = Np;
+        if (n != m) o[m * K + n] = conjg(Np);
+    }
 }
 
 }  // namespace
 
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
 
-// f_E for every chain and link into d_out [n_chains][n_links] (device):
-// Z2 the flip, U(1) the Casimir J^2.
-ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
+// N_nm(G) / N(G) of every chain into d_out [n_chains][K][K] (device).
+ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    pair_norm_kernel<<<(ch.n + 127) / 128, 128, 0, st>>>(ctx->dc(), ch.n, ch.ell, d_out);
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}
+
+// f_E for every chain and link into d_out [n_chains][n_links] and/or its
+// per-pair parts into d_pairs [n_chains][n_links][K][K] (device; either may
+// be null): Z2 the flip, U(1) and SU(2) the Casimir J^2.
+ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
     // pending delayed updates first, so that W is the inverse at the current links
@@ -212,7 +266,7 @@ ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
 #define GGF_EL(RW, CW, H)                                                                                \
     electric_kernel<RW, CW, H><<<(unsigned)blocks, ETHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, lk,          \
                                                                       (const RW*)ch.Wr, (const CW*)ch.Wc, \
-                                                                      ch.ell, d_out)
+                                                                      ch.ell, d_out, d_pairs)
     if (g.h2 == 2) {
         if (fp64) GGF_EL(double, cxd, 2); else GGF_EL(float, cxf, 2);
     } else if (g.h2 == 4) {

@@ -49,11 +49,25 @@ __device__ void coupled_block(const DevConst& dc, const T* W, int s, int t, cxd 
     }
 }
 
+// Per-pair expectation -i (A + X)[alpha][beta] of entry (alpha, beta) of item
+// (s, t), with c_a c_a = 1 where both Majoranas coincide (self-links).
+__device__ __forceinline__ cxd pair_bilinear(const DevConst& dc, int s, int t, int a, int b, cxd x) {
+    if (s == t) {
+        if (a == b) return cxd{1.0, 0.0};
+        x.x += dc.Ap[(size_t)s * 4 + a * 2 + b];
+    }
+    return times_minus_i(x);
+}
+
 // One thread per (chain, item): items 0 .. V-1 are sites, V .. V + n_links - 1 links.
+// Combined outputs site_out / link_out and per-pair outputs
+// pair_site[c][s][n][m], pair_link[c][l][alpha][beta][n][m] =
+// N_nm(G) <c c>_nm / N(G) (each may be null).
 template <class RW, class CW, int BW>
 __global__ void __launch_bounds__(FTHREADS) fermion_kernel(DevConst dc, int n_chains, int blocks_per_chain,
                                                            const RW* Wr, const CW* Wc, const cxd* ell,
-                                                           cxd* site_out, cxd* link_out) {
+                                                           cxd* site_out, cxd* link_out, cxd* pair_site,
+                                                           cxd* pair_link) {
     const Geometry& g = dc.g;
     const int c = blockIdx.x / blocks_per_chain;
     const int it = (blockIdx.x - c * blocks_per_chain) * FTHREADS + threadIdx.x;
@@ -69,54 +83,77 @@ __global__ void __launch_bounds__(FTHREADS) fermion_kernel(DevConst dc, int n_ch
         s = a0 / g.B;
         t = b0 / g.B;
     }
-    if (is_site ? !site_out : !link_out) return;
+    cxd* out = is_site ? site_out : link_out;
+    cxd* pout = is_site ? pair_site : pair_link;
+    if (!out && !pout) return;
+    const int K = dc.K;
+    if (pout) pout += is_site ? ((size_t)c * g.V + s) * K * K : ((size_t)c * g.n_links + (it - g.V)) * 4 * K * K;
     const size_t NN = (size_t)g.N * g.N;
     const cxd* el = ell + (size_t)c * dc.P;
     double amax = -INFINITY;
     for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
+    // N(G) (scaled by e^{-amax}) = Re sum_p w_p N_p
     double den = 0.0;
+    for (int p = 0; p < dc.P; ++p) {
+        cxd e = dc.logc[p] + el[p];
+        if (p < K) e.y = 0.0;
+        e.x -= amax;
+        den += (dc.w[p] * cexp_(e)).x;
+    }
+    const double iden = 1.0 / den;
     cxd acc[2][2] = {{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}};
     for (int p = 0; p < dc.P; ++p) {
         cxd e = dc.logc[p] + el[p];
-        const bool cplx = p >= dc.K;
+        const bool cplx = p >= K;
         if (!cplx) e.y = 0.0;
         e.x -= amax;
-        const cxd E = dc.w[p] * cexp_(e);        // w_p N_p, scaled
-        den += E.x;
+        const cxd Np = iden * cexp_(e);          // N_nm(G) / N(G)
+        const cxd E = dc.w[p] * Np;              // w_p N_p / N(G)
+        int n, m;
+        pair_nm(K, p, n, m);
         cxd X[2][2];
         if (cplx) {
-            coupled_block<CW, BW>(dc, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, s, t, X);
+            coupled_block<CW, BW>(dc, Wc + ((size_t)c * dc.Kc + (p - K)) * NN, s, t, X);
             // (n, m) with weight E / 2 (w_p = 2 lambda_n^* lambda_m), (m, n) with
             // conj(E) / 2 and the conjugate product; A is added after the loop
             const cxd h = 0.5 * E, hc = conjg(h);
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) acc[a][b] += h * X[a][b] + hc * conjg(X[a][b]);
+                for (int b = 0; b < 2; ++b) {
+                    acc[a][b] += h * X[a][b] + hc * conjg(X[a][b]);
+                    if (pout && (!is_site || (a == 0 && b == 1))) {
+                        cxd* q = pout + (is_site ? 0 : (size_t)(a * 2 + b) * K * K);
+                        q[n * K + m] = Np * pair_bilinear(dc, s, t, a, b, X[a][b]);
+                        q[m * K + n] = conjg(Np) * pair_bilinear(dc, s, t, a, b, conjg(X[a][b]));
+                    }
+                }
         } else {
             coupled_block<RW, BW>(dc, Wr + ((size_t)c * dc.K + p) * NN, s, t, X);
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) acc[a][b] += E * X[a][b];
+                for (int b = 0; b < 2; ++b) {
+                    acc[a][b] += E * X[a][b];
+                    if (pout && (!is_site || (a == 0 && b == 1))) {
+                        cxd* q = pout + (is_site ? 0 : (size_t)(a * 2 + b) * K * K);
+                        q[n * K + n] = Np * pair_bilinear(dc, s, t, a, b, X[a][b]);
+                    }
+                }
         }
     }
-    // F = -i (A + sum_p weight_p X_p) / den; A enters with the total weight
-    // sum_nm lambda_n^* lambda_m N_nm = den (only where s == t)
+    if (!out) return;
+    // F = -i (A + sum_p weight_p X_p); A enters with the total weight
+    // sum_nm lambda_n^* lambda_m N_nm / N(G) = 1 (only where s == t)
     cxd F[2][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            cxd v = {acc[a][b].x / den, acc[a][b].y / den};
-            if (s == t) v.x += dc.Ap[(size_t)s * 4 + a * 2 + b];
-            F[a][b] = times_minus_i(v);
-        }
+        for (int b = 0; b < 2; ++b) F[a][b] = pair_bilinear(dc, s, t, a, b, acc[a][b]);
     if (is_site) {
-        site_out[(size_t)c * g.V + s] = F[0][1];
+        out[(size_t)c * g.V + s] = F[0][1];
     } else {
-        if (s == t) { F[0][0] = cxd{1.0, 0.0}; F[1][1] = cxd{1.0, 0.0}; }   // c_a c_a = 1
-        cxd* o = link_out + ((size_t)c * g.n_links + (it - g.V)) * 4;
+        cxd* o = out + ((size_t)c * g.n_links + (it - g.V)) * 4;
         o[0] = F[0][0]; o[1] = F[0][1]; o[2] = F[1][0]; o[3] = F[1][1];
     }
 }
@@ -126,8 +163,10 @@ __global__ void __launch_bounds__(FTHREADS) fermion_kernel(DevConst dc, int n_ch
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
 
 // Site and link bilinears of every chain into d_site [n][V] and d_link
-// [n][n_links][2][2] (device; either may be null).
-ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cudaStream_t st) {
+// [n][n_links][2][2], and their per-pair parts into d_pair_site [n][V][K][K]
+// and d_pair_link [n][n_links][2][2][K][K] (device; any may be null).
+ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cxd* d_pair_site, cxd* d_pair_link,
+                       cudaStream_t st) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
     GGF_TRY(ggf_flush(ctx, st));
@@ -138,7 +177,8 @@ ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cudaStream_t st) 
     const bool fp64 = ch.opts.precision == GGF_FP64;
 #define GGF_FE(RW, CW, BW)                                                                                 \
     fermion_kernel<RW, CW, BW><<<(unsigned)blocks, FTHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, (const RW*)ch.Wr, \
-                                                                      (const CW*)ch.Wc, ch.ell, d_site, d_link)
+                                                                      (const CW*)ch.Wc, ch.ell, d_site, d_link, \
+                                                                      d_pair_site, d_pair_link)
     if (g.B == 8) {
         if (fp64) GGF_FE(double, cxd, 8); else GGF_FE(float, cxf, 8);
     } else if (g.B == 16) {

@@ -13,6 +13,7 @@ import os
 import numpy as np
 
 Z2, U1, SU2 = 0, 1, 2
+PAIRS_NORM, PAIRS_ELECTRIC, PAIRS_SITE, PAIRS_LINK = 0, 1, 2, 3
 FP64, FP32 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 N_OBS = 3
@@ -48,7 +49,8 @@ class ChainStats(ctypes.Structure):
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
-           "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_stats", "ggf_checkpoint",
+           "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_stats",
+           "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
            "ggf_selftest_flush", "ggf_net_create", "ggf_net_destroy", "ggf_net_last_error", "ggf_net_get_params",
            "ggf_net_set_params", "ggf_net_logq", "ggf_net_loss_grad", "ggf_net_train", "ggf_sample_blocks"]
@@ -85,6 +87,7 @@ def load():
         "ggf_chains_inverse": ([P, I, I, P, I, P], I),
         "ggf_chains_electric": ([P, P, I, P], I),
         "ggf_chains_fermion": ([P, P, P, I, P], I),
+        "ggf_chains_pairs": ([P, I, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -182,6 +185,7 @@ class GGF:
         gb = np.ascontiguousarray(gamma_bond, dtype=np.float64)
         lm = np.ascontiguousarray(np.stack([np.real(lam), np.imag(lam)], axis=-1), dtype=np.float64)
         self._ck(self.lib.ggf_init_gaussians(self.h, gs.ctypes.data, int(K), gb.ctypes.data, lm.ctypes.data))
+        self.K = int(K)
 
     def init_problem(self, p):
         """Convenience: the three init calls for a ggf_inputs.Problem-like object."""
@@ -293,6 +297,21 @@ class GGF:
         self._ck(self.lib.ggf_chains_fermion(self.h, _ptr(site)[0], _ptr(link)[0], self._mem(site, link),
                                              _stream([site, link])))
         return site, link
+
+    def chains_pairs(self, what, out=None):
+        """Per-pair parts N_nm(G) o_nm(G) / N(G) of every chain (PAIRS_NORM,
+        PAIRS_ELECTRIC, PAIRS_SITE, PAIRS_LINK): complex numpy arrays of shape
+        (n_chains, [items...,] K, K), or fills `out` (float64 with a trailing
+        axis of 2, numpy or CUDA tensor) and returns it."""
+        if out is None:
+            K = self.K
+            nl = self.n_links()
+            items = {PAIRS_NORM: (), PAIRS_ELECTRIC: (nl,), PAIRS_SITE: (nl // 2,), PAIRS_LINK: (nl, 2, 2)}[what]
+            host = np.zeros((self.n_chains,) + items + (K, K, 2))
+            self._ck(self.lib.ggf_chains_pairs(self.h, int(what), host.ctypes.data, MEM_HOST, None))
+            return host[..., 0] + 1j * host[..., 1]
+        self._ck(self.lib.ggf_chains_pairs(self.h, int(what), _ptr(out)[0], self._mem(out), _stream([out])))
+        return out
 
     def chains_inverse(self, chain, pair, N):
         out = np.zeros((N, N, 2))

@@ -54,7 +54,9 @@ def test_binding_constants_match_header():
              "GGF_MEM_DEVICE": ggf.MEM_DEVICE, "GGF_MEM_HOST": ggf.MEM_HOST, "GGF_N_OBS": ggf.N_OBS,
              "GGF_OBS_PLAQUETTE": ggf.OBS_PLAQUETTE, "GGF_KT_RATIO": ggf.KT_RATIO,
              "GGF_KT_UPDATE": ggf.KT_UPDATE, "GGF_KT_REFRESH": ggf.KT_REFRESH, "GGF_KT_FLUSH": ggf.KT_FLUSH,
-             "GGF_KT_GATHER": ggf.KT_GATHER, "GGF_KT_APPLY": ggf.KT_APPLY, "GGF_NET_PARAMS": ggf.NET_PARAMS}
+             "GGF_KT_GATHER": ggf.KT_GATHER, "GGF_KT_APPLY": ggf.KT_APPLY, "GGF_NET_PARAMS": ggf.NET_PARAMS,
+             "GGF_PAIRS_NORM": ggf.PAIRS_NORM, "GGF_PAIRS_ELECTRIC": ggf.PAIRS_ELECTRIC,
+             "GGF_PAIRS_SITE": ggf.PAIRS_SITE, "GGF_PAIRS_LINK": ggf.PAIRS_LINK}
     for name, val in pairs.items():
         assert defs[name] == val, name
     assert len(enum) == len(ggf.STATUS)

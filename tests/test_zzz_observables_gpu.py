@@ -146,3 +146,50 @@ def test_fermion_site_only_and_device_buffers():
     d = ds.cpu().numpy()
     assert np.array_equal(d[..., 0] + 1j * d[..., 1], hs)
     ctx.close()
+
+
+@pytest.mark.parametrize("L,grp,n_v,K,prec,tol", [
+    (3, gi.Z2, 1, 3, 0, 1e-10),
+    (2, gi.U1, 2, 2, 0, 1e-10),
+    (4, gi.U1, 1, 2, 1, 1e-4),
+])
+def test_pair_parts_match_oracle(L, grp, n_v, K, prec, tol):
+    """ggf_chains_pairs against the oracle's local matrices, and contracting
+    them with lambda gives the combined observables."""
+    from oracle import variational
+    from paper_2412_01737_gb300.ggf import PAIRS_NORM, PAIRS_ELECTRIC, PAIRS_SITE, PAIRS_LINK
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=51)
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=prec, seed=2)
+    norm = ctx.chains_pairs(PAIRS_NORM)
+    elp = ctx.chains_pairs(PAIRS_ELECTRIC)
+    sitep = ctx.chains_pairs(PAIRS_SITE)
+    linkp = ctx.chains_pairs(PAIRS_LINK)
+    el = ctx.chains_electric()
+    site, link = ctx.chains_fermion()
+    lm = variational.LocalMatrices(p)
+    fe = fermionic.Fermionic(p)
+    lam = p.lam
+    for c in range(2):
+        ref = lm(links[c])
+        sc = max(1.0, np.abs(ref["norm"]).max())
+        assert np.abs(norm[c] - ref["norm"]).max() <= tol * sc
+        assert np.abs(elp[c] - ref["electric"]).max() <= tol * max(1.0, np.abs(ref["electric"]).max())
+        assert np.abs(sitep[c] - ref["density"]).max() <= tol * max(1.0, np.abs(ref["density"]).max())
+        Ge = fe.gamma_eff(links[c])
+        for l in range(p.n_links):
+            s_, t_ = fermionic._link_sites(p, l)
+            for a in range(2):
+                for b in range(2):
+                    want = np.zeros((K, K), dtype=complex)
+                    for (n, m), G in Ge.items():
+                        i, j = 2 * s_ + a, 2 * t_ + b
+                        want[n, m] = ref["norm"][n, m] * (1.0 if i == j else -1j * G[i, j])
+                    assert np.abs(linkp[c, l, a, b] - want).max() <= tol * max(1.0, np.abs(want).max())
+        contract = lambda X: np.einsum("n,...nm,m->...", np.conj(lam), X, lam)
+        assert abs(contract(norm[c]) - 1.0) <= tol
+        assert np.abs(contract(elp[c]) - el[c]).max() <= tol * max(1.0, np.abs(el[c]).max())
+        assert np.abs(contract(sitep[c]) - site[c]).max() <= tol
+        assert np.abs(contract(linkp[c]) - link[c]).max() <= tol
+    ctx.close()
