@@ -1,0 +1,79 @@
+"""Optimal superposition weights lambda for a given energy.
+
+For fixed Gaussians every per-configuration quantity of Secs. 5.1-5.3 is a
+Hermitian form in lambda, so with the per-pair parts that
+``GGF.chains_pairs`` returns (N_nm(G) o_nm(G) / N(G), expectations over the
+chains' p(G)),
+
+    <E>_lambda = lambda^dag Hbar lambda / lambda^dag Nbar lambda,
+
+and the lambda that minimises it is the lowest generalised eigenvector of
+Hbar lambda = E Nbar lambda.  ``accumulate`` samples with the context's
+current lambda and estimates Hbar and Nbar for an energy
+
+    E = c_plaquette <mean plaquette> + sum_l c_electric[l] <f_E,l>
+        + sum_s c_site[s] <c_2s c_2s+1> + sum_{l,a,b} c_link[l,a,b] <c_{2s+a} c_{2t+b}>
+
+(any coefficient may be omitted); the couplings, and thus the Hamiltonian,
+are the caller's.  ``linear_method`` solves for the new lambda, which
+``GGF.init_gaussians`` takes for the next round of sampling.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+from .ggf import PAIRS_ELECTRIC, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
+
+
+def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric=None, c_site=None,
+                 c_link=None) -> np.ndarray:
+    """(n_chains, K, K) local matrices of the energy from one sweep's per-pair
+    parts (dict with keys 'norm', 'electric', 'site', 'link' as returned by
+    GGF.chains_pairs) and the chains' mean plaquettes."""
+    H = c_plaquette * plaquette[:, None, None] * pairs["norm"]
+    if c_electric is not None:
+        H = H + np.einsum("l,clnm->cnm", np.asarray(c_electric, dtype=complex), pairs["electric"])
+    if c_site is not None:
+        H = H + np.einsum("s,csnm->cnm", np.asarray(c_site, dtype=complex), pairs["site"])
+    if c_link is not None:
+        H = H + np.einsum("lab,clabnm->cnm", np.asarray(c_link, dtype=complex), pairs["link"])
+    return H
+
+
+def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None):
+    """Run n_sweeps sweeps of ctx's chains and return (Hbar, Nbar), the means
+    over chains and sweeps of the energy's and the norm's per-pair parts."""
+    Hbar, Nbar, n = 0.0, 0.0, 0
+    for _ in range(n_sweeps):
+        obs = ctx.sample(1)
+        pairs = {"norm": ctx.chains_pairs(PAIRS_NORM)}
+        if c_electric is not None:
+            pairs["electric"] = ctx.chains_pairs(PAIRS_ELECTRIC)
+        if c_site is not None:
+            pairs["site"] = ctx.chains_pairs(PAIRS_SITE)
+        if c_link is not None:
+            pairs["link"] = ctx.chains_pairs(PAIRS_LINK)
+        H = local_energy(pairs, obs[0, :, 0], c_plaquette, c_electric, c_site, c_link)
+        Hbar = Hbar + H.sum(axis=0)
+        Nbar = Nbar + pairs["norm"].sum(axis=0)
+        n += H.shape[0]
+    return Hbar / n, Nbar / n
+
+
+def linear_method(Hbar: np.ndarray, Nbar: np.ndarray):
+    """(E, lambda): the lowest generalised eigenpair of the Hermitian parts of
+    Hbar and Nbar; lambda has unit 2-norm and lambda_0 real non-negative."""
+    H = 0.5 * (Hbar + Hbar.conj().T)
+    Nm = 0.5 * (Nbar + Nbar.conj().T)
+    w, v = scipy.linalg.eigh(H, Nm)
+    lam = v[:, 0] / np.linalg.norm(v[:, 0])
+    if abs(lam[0]) > 0:
+        lam = lam * (abs(lam[0]) / lam[0])
+    return float(w[0]), lam
+
+
+def energy(Hbar: np.ndarray, Nbar: np.ndarray, lam) -> float:
+    """lambda^dag Hbar lambda / lambda^dag Nbar lambda (real part)."""
+    lam = np.asarray(lam, dtype=complex)
+    return float((np.conj(lam) @ Hbar @ lam / (np.conj(lam) @ Nbar @ lam)).real)

@@ -1,0 +1,53 @@
+"""Host logic of the lambda optimiser (paper_2412_01737_gb300/optimize.py),
+on CPU: the generalised eigensolver against the oracle's, the local energy
+contraction against explicit sums, and the accumulation loop with a stand-in
+context that serves the oracle's local matrices."""
+import numpy as np
+
+import ggf_inputs as gi
+from oracle import variational
+from paper_2412_01737_gb300 import optimize
+from paper_2412_01737_gb300.ggf import PAIRS_ELECTRIC, PAIRS_NORM, PAIRS_SITE
+
+
+def test_linear_method_matches_oracle():
+    rng = np.random.default_rng(0)
+    A = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    B = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    H, N = A + A.conj().T, B @ B.conj().T + np.eye(4)
+    e1, l1 = optimize.linear_method(H, N)
+    e2, l2 = variational.linear_method(H, N)
+    assert abs(e1 - e2) <= 1e-12 and np.abs(l1 - l2).max() <= 1e-10
+    assert abs(optimize.energy(H, N, l1) - e1) <= 1e-12
+
+
+class _Stub:
+    """Serves per-pair parts of fixed configurations, one per chain."""
+
+    def __init__(self, p, configs):
+        self.p, self.cfgs = p, configs
+        self.lm = variational.LocalMatrices(p)
+        self.loc = [self.lm(G) for G in configs]
+
+    def sample(self, n):
+        from oracle.observables import plaquette_values
+        pl = plaquette_values(self.p.group, self.p.L, self.cfgs).mean(axis=1)
+        return np.stack([pl, np.zeros_like(pl), np.zeros_like(pl)], axis=-1)[None]
+
+    def chains_pairs(self, what):
+        key = {PAIRS_NORM: "norm", PAIRS_ELECTRIC: "electric", PAIRS_SITE: "density"}[what]
+        return np.array([d[key] for d in self.loc])
+
+
+def test_accumulate_contracts_the_energy():
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    cfgs = gi.random_links(p, 3, seed=2)
+    stub = _Stub(p, cfgs)
+    ce = np.linspace(0.1, 0.8, p.n_links)
+    cs = np.linspace(-0.3, 0.3, p.V)
+    H, N = optimize.accumulate(stub, 2, c_plaquette=-1.5, c_electric=ce, c_site=cs)
+    want_H = np.mean([-1.5 * stub.sample(1)[0, c, 0] * d["norm"] + np.einsum("l,lnm->nm", ce, d["electric"])
+                      + np.einsum("s,snm->nm", cs, d["density"]) for c, d in enumerate(stub.loc)], axis=0)
+    want_N = np.mean([d["norm"] for d in stub.loc], axis=0)
+    assert np.abs(H - want_H).max() <= 1e-13
+    assert np.abs(N - want_N).max() <= 1e-13

@@ -193,3 +193,25 @@ def test_pair_parts_match_oracle(L, grp, n_v, K, prec, tol):
         assert np.abs(contract(sitep[c]) - site[c]).max() <= tol
         assert np.abs(contract(linkp[c]) - link[c]).max() <= tol
     ctx.close()
+
+
+def test_lambda_optimisation_end_to_end():
+    """Sample with the problem's lambda, estimate the per-pair matrices of
+    E = -<plaquette> + 0.5 sum_l <X_l> on the GPU, solve for lambda, and
+    check with the exhaustive oracle that the new lambda is near the optimum."""
+    from oracle import variational
+    from paper_2412_01737_gb300 import optimize
+    p = gi.make_problem(2, gi.Z2, 1, 3, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 512, seed=61), precision=0, seed=8)
+    ctx.sample(3)
+    Hbar, Nbar = optimize.accumulate(ctx, 20, c_plaquette=-1.0, c_electric=0.5 * np.ones(p.n_links))
+    ctx.close()
+    _, lam = optimize.linear_method(Hbar, Nbar)
+    S = variational.exhaustive(p, gi.all_z2_configs(p))
+    H = -1.0 * S["plaquette"] + 0.5 * S["electric"].sum(axis=0)
+    E0, _ = variational.linear_method(H, S["norm"])
+    e_new = variational.expectation(H, S["norm"], lam).real
+    e_old = variational.expectation(H, S["norm"], p.lam).real
+    assert e_old - E0 > 3.0
+    assert e_new < E0 + 0.5
