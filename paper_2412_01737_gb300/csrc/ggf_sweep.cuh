@@ -266,6 +266,28 @@ __device__ __forceinline__ void pair_nm(int K, int p, int& n, int& m) {
     m = n + 1 + k;
 }
 
+// Scale of the pair terms of one configuration: amax = max_p Re(logc_p + ell_p)
+// and 1 / (N(G) e^{-amax}), N(G) = Re sum_p w_p e^{logc_p + ell_p}; then
+// pair_norm gives N_nm(G) / N(G) for pair p (diagonal pairs real).
+__device__ __forceinline__ void pair_scale(const DevConst& dc, const cxd* ell_c, double& amax, double& iden) {
+    amax = -INFINITY;
+    for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + ell_c[p].x);
+    double den = 0.0;
+    for (int p = 0; p < dc.P; ++p) {
+        cxd e = dc.logc[p] + ell_c[p];
+        if (p < dc.K) e.y = 0.0;
+        e.x -= amax;
+        den += (dc.w[p] * cexp_(e)).x;
+    }
+    iden = 1.0 / den;
+}
+__device__ __forceinline__ cxd pair_norm(const DevConst& dc, const cxd* ell_c, int p, double amax, double iden) {
+    cxd e = dc.logc[p] + ell_c[p];
+    if (p < dc.K) e.y = 0.0;
+    e.x -= amax;
+    return iden * cexp_(e);
+}
+
 // Numerator and denominator of N(G')/N(G) = Re sum_p w_p e^{logc_p + ell_p} rho_p
 // / Re sum_p w_p e^{logc_p + ell_p}, scaled by the largest modulus (FP64).
 __device__ __forceinline__ void combine_pairs(const DevConst& dc, const cxd* ell_c, const cxd* rho, double& sn,

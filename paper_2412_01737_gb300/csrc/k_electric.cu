@@ -170,24 +170,12 @@ __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_c
         link_value<double>(dc, links, c, l, gval, theta);
     }
     const cxd* el = ell + (size_t)c * dc.P;
-    double amax = -INFINITY;
-    for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
-    // N(G) (scaled by e^{-amax}) = Re sum_p w_p N_p
-    double den = 0.0;
-    for (int p = 0; p < dc.P; ++p) {
-        cxd e = dc.logc[p] + el[p];
-        if (p < dc.K) e.y = 0.0;
-        e.x -= amax;
-        den += (dc.w[p] * cexp_(e)).x;
-    }
-    const double iden = 1.0 / den;
+    double amax, iden;
+    pair_scale(dc, el, amax, iden);
     cxd num = {0.0, 0.0};
     for (int p = 0; p < dc.P; ++p) {
-        cxd e = dc.logc[p] + el[p];
         const bool cplx = p >= dc.K;
-        if (!cplx) e.y = 0.0;
-        e.x -= amax;
-        const cxd Np = iden * cexp_(e);          // N_nm(G) / N(G)
+        const cxd Np = pair_norm(dc, el, p, amax, iden);   // N_nm(G) / N(G)
         const cxd E = dc.w[p] * Np;              // w_p N_p / N(G)
         cxd Rf, Rr;
         int n, m;
@@ -216,21 +204,11 @@ __global__ void pair_norm_kernel(DevConst dc, int n_chains, const cxd* ell, cxd*
     if (c >= n_chains) return;
     const int K = dc.K;
     const cxd* el = ell + (size_t)c * dc.P;
-    double amax = -INFINITY;
-    for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
-    double den = 0.0;
-    for (int p = 0; p < dc.P; ++p) {
-        cxd e = dc.logc[p] + el[p];
-        if (p < K) e.y = 0.0;
-        e.x -= amax;
-        den += (dc.w[p] * cexp_(e)).x;
-    }
+    double amax, iden;
+    pair_scale(dc, el, amax, iden);
     cxd* o = out + (size_t)c * K * K;
     for (int p = 0; p < dc.P; ++p) {
-        cxd e = dc.logc[p] + el[p];
-        if (p < K) e.y = 0.0;
-        e.x -= amax;
-        const cxd Np = (1.0 / den) * cexp_(e);
+        const cxd Np = pair_norm(dc, el, p, amax, iden);
         int n, m;
         pair_nm(K, p, n, m);
         o[n * K + m] = Np;

@@ -90,24 +90,12 @@ __global__ void __launch_bounds__(FTHREADS) fermion_kernel(DevConst dc, int n_ch
     if (pout) pout += is_site ? ((size_t)c * g.V + s) * K * K : ((size_t)c * g.n_links + (it - g.V)) * 4 * K * K;
     const size_t NN = (size_t)g.N * g.N;
     const cxd* el = ell + (size_t)c * dc.P;
-    double amax = -INFINITY;
-    for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + el[p].x);
-    // N(G) (scaled by e^{-amax}) = Re sum_p w_p N_p
-    double den = 0.0;
-    for (int p = 0; p < dc.P; ++p) {
-        cxd e = dc.logc[p] + el[p];
-        if (p < K) e.y = 0.0;
-        e.x -= amax;
-        den += (dc.w[p] * cexp_(e)).x;
-    }
-    const double iden = 1.0 / den;
+    double amax, iden;
+    pair_scale(dc, el, amax, iden);
     cxd acc[2][2] = {{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}};
     for (int p = 0; p < dc.P; ++p) {
-        cxd e = dc.logc[p] + el[p];
         const bool cplx = p >= K;
-        if (!cplx) e.y = 0.0;
-        e.x -= amax;
-        const cxd Np = iden * cexp_(e);          // N_nm(G) / N(G)
+        const cxd Np = pair_norm(dc, el, p, amax, iden);   // N_nm(G) / N(G)
         const cxd E = dc.w[p] * Np;              // w_p N_p / N(G)
         int n, m;
         pair_nm(K, p, n, m);

@@ -98,3 +98,22 @@ def test_casimir_matches_oracle(precision, tol):
         ref = el.f_electric(links[c])
         assert np.abs(got[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
     ctx.close()
+
+
+def test_checkpoint_resume_bit_exact(tmp_path):
+    p = gi.make_problem(2, gi.SU2, 2, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(np.ascontiguousarray(gi.cold_links(p, 3)), refresh_every=4, seed=3, width=1.0, delay=4)
+    ctx.sample(2)
+    ck = tmp_path / "su2.ckpt"
+    ctx.checkpoint(ck)
+    a = ctx.sample(3)
+    la = ctx.chains_links()
+    ctx.close()
+    ctx2 = ctx_for(p)
+    ctx2.resume(ck)
+    b = ctx2.sample(3)
+    lb = ctx2.chains_links()
+    ctx2.close()
+    assert np.array_equal(la, lb)
+    assert np.array_equal(a[:, :, 2], b[:, :, 2])
