@@ -1,11 +1,12 @@
-// Device-side lattice geometry and the twisted link blocks O Gamma_X O^T
-// (Sec. 3.1, Sec. 5), shared by the assembly and the sampler kernels.
+// Lattice geometry and the twisted link blocks O Gamma_X O^T (Sec. 3.1,
+// Sec. 5), shared by the assembly, sampler and observable kernels (host and
+// device callable).
 #pragma once
 #include "ggf_ctx.h"
 
 namespace {
 // ---- geometry helpers -------------------------------------------------------
-__device__ __forceinline__ void link_of(const Geometry& g, int i, int& link, int& pos) {
+GGF_HD void link_of(const Geometry& g, int i, int& link, int& pos) {
     int s = i / g.B, li = i - s * g.B, e = li / g.h2, k = li - e * g.h2;
     int d = e >> 1;
     if (e & 1) {           // +d end: source of link (s, d)
@@ -20,7 +21,7 @@ __device__ __forceinline__ void link_of(const Geometry& g, int i, int& link, int
 }
 
 // Row of the twist O restricted to link position x: up to two (index, coef).
-__device__ __forceinline__ void twist_row(const Geometry& g, int x, double gval, double c, double s,
+GGF_HD void twist_row(const Geometry& g, int x, double gval, double c, double s,
                                           int& i0, double& c0, int& i1, double& c1) {
     if (x >= g.h2) { i0 = x; c0 = 1.0; i1 = x; c1 = 0.0; return; }
     if (g.group == GGF_Z2) { i0 = x; c0 = gval; i1 = x; c1 = 0.0; return; }
@@ -30,22 +31,22 @@ __device__ __forceinline__ void twist_row(const Geometry& g, int x, double gval,
 }
 
 template <class T>
-__device__ __forceinline__ T bond_elem(const DevConst& dc, int pair, int link, int x, int y);
+GGF_HD T bond_elem(const DevConst& dc, int pair, int link, int x, int y);
 template <>
-__device__ __forceinline__ double bond_elem<double>(const DevConst& dc, int pair, int link, int x, int y) {
+GGF_HD double bond_elem<double>(const DevConst& dc, int pair, int link, int x, int y) {
     return dc.Gr[((size_t)pair * dc.g.n_links + link) * dc.g.r * dc.g.r + x * dc.g.r + y];
 }
 template <>
-__device__ __forceinline__ cxd bond_elem<cxd>(const DevConst& dc, int pair, int link, int x, int y) {
+GGF_HD cxd bond_elem<cxd>(const DevConst& dc, int pair, int link, int x, int y) {
     return dc.Gc[((size_t)pair * dc.g.n_links + link) * dc.g.r * dc.g.r + x * dc.g.r + y];
 }
 
-__device__ __forceinline__ double mulc(double c, double v) { return c * v; }
-__device__ __forceinline__ cxd mulc(double c, cxd v) { return c * v; }
+GGF_HD double mulc(double c, double v) { return c * v; }
+GGF_HD cxd mulc(double c, cxd v) { return c * v; }
 
 // twisted link block element (O G O^T)[x][y] for link value (Z2 g / U(1) theta)
 template <class T>
-__device__ T twisted(const DevConst& dc, int pair, int link, int x, int y, double gval, double theta) {
+__host__ __device__ T twisted(const DevConst& dc, int pair, int link, int x, int y, double gval, double theta) {
     const Geometry& g = dc.g;
     double cx_ = 1, sx_ = 0, cy_ = 1, sy_ = 0;
     if (g.group == GGF_U1) {
@@ -68,7 +69,7 @@ __device__ T twisted(const DevConst& dc, int pair, int link, int x, int y, doubl
 // Same element with the twist's cos/sin precomputed: cs[2 j], cs[2 j + 1] =
 // cos, sin of q_j theta for source-end mode j (U(1); unused for Z2).
 template <class T>
-__device__ T twisted_tab(const DevConst& dc, int pair, int link, int x, int y, double gval, const double* cs) {
+__host__ __device__ T twisted_tab(const DevConst& dc, int pair, int link, int x, int y, double gval, const double* cs) {
     const Geometry& g = dc.g;
     double cx_ = 1, sx_ = 0, cy_ = 1, sy_ = 0;
     if (g.group == GGF_U1) {
@@ -89,7 +90,7 @@ __device__ T twisted_tab(const DevConst& dc, int pair, int link, int x, int y, d
 }
 
 template <class T>
-__device__ __forceinline__ void link_value(const DevConst& dc, const void* links, int cfg, int link,
+GGF_HD void link_value(const DevConst& dc, const void* links, int cfg, int link,
                                            double& gval, double& theta) {
     if (dc.g.group == GGF_Z2) {
         gval = (double)((const int8_t*)links)[(size_t)cfg * dc.g.n_links + link];
@@ -108,12 +109,12 @@ __device__ __forceinline__ void link_value(const DevConst& dc, const void* links
 //   c_2j   -> sum_k  Re u_kj c_2k + Im u_kj c_2k+1,
 //   c_2j+1 -> sum_k -Im u_kj c_2k + Re u_kj c_2k+1.
 
-__device__ __forceinline__ const double* link_quat(const Geometry& g, const void* links, int cfg, int link) {
+GGF_HD const double* link_quat(const Geometry& g, const void* links, int cfg, int link) {
     return (const double*)links + ((size_t)cfg * g.n_links + link) * 4;
 }
 
 // (a0 + i a.s)(b0 + i b.s) = a0 b0 - a.b + i (a0 b + b0 a - a x b).s
-__device__ __forceinline__ void quat_mul(const double* a, const double* b, double* o) {
+GGF_HD void quat_mul(const double* a, const double* b, double* o) {
     o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
     o[1] = a[0] * b[1] + b[0] * a[1] - (a[2] * b[3] - a[3] * b[2]);
     o[2] = a[0] * b[2] + b[0] * a[2] - (a[3] * b[1] - a[1] * b[3]);
@@ -123,7 +124,7 @@ __device__ __forceinline__ void quat_mul(const double* a, const double* b, doubl
 // (1/2) tr(u1^dag u2^dag u3 u4): the scalar part of conj(q1) conj(q2) q3 q4.
 // The weight is invariant under u_l -> h_t^dag u_l h_s, so the covariant link
 // matrix is u^dag and this is the oriented plaquette trace.
-__device__ __forceinline__ double plaquette_su2(const double* q1, const double* q2, const double* q3,
+GGF_HD double plaquette_su2(const double* q1, const double* q2, const double* q3,
                                                 const double* q4) {
     const double c1[4] = {q1[0], -q1[1], -q1[2], -q1[3]}, c2[4] = {q2[0], -q2[1], -q2[2], -q2[3]};
     double a[4], b[4];
@@ -132,7 +133,7 @@ __device__ __forceinline__ double plaquette_su2(const double* q1, const double* 
     return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
 
-__device__ __forceinline__ void doublet_rotation(const double* q, double* R) {
+GGF_HD void doublet_rotation(const double* q, double* R) {
     // u00 = a0 + i a3, u01 = a2 + i a1, u10 = -a2 + i a1, u11 = a0 - i a3
     const double ure[2][2] = {{q[0], q[2]}, {-q[2], q[0]}};
     const double uim[2][2] = {{q[3], q[1]}, {q[1], -q[3]}};
@@ -148,7 +149,7 @@ __device__ __forceinline__ void doublet_rotation(const double* q, double* R) {
 // (O G O^T)[x][y] on one link (n_v = 2: the source end is one doublet at link
 // positions 0..3, rotated by R; the target end 4..7 is untouched).
 template <class T>
-__device__ T twisted_su2(const DevConst& dc, int pair, int link, int x, int y, const double* R) {
+__host__ __device__ T twisted_su2(const DevConst& dc, int pair, int link, int x, int y, const double* R) {
     T v = T{};
     if (x < 4 && y < 4) {
         for (int a = 0; a < 4; ++a)

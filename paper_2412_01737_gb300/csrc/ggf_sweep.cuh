@@ -112,13 +112,13 @@ template <> __device__ __forceinline__ void PanelIO<cxf>::st(float* p, size_t pl
 // Majorana offsets of the two ends of link l = 2 s + d: the source end (+d
 // end of site s, which carries the twist) and the target end (-d end of the
 // neighbour t).  Majorana xi < h2 of the link is a0 + xi, the others b0 + xi - h2.
-__device__ __forceinline__ void link_ends(const Geometry& g, int l, int& a0, int& b0) {
+GGF_HD void link_ends(const Geometry& g, int l, int& a0, int& b0) {
     const int s = l >> 1, d = l & 1, x = s % g.L, y = s / g.L;
     const int t = d == 0 ? y * g.L + (x + 1) % g.L : ((y + 1) % g.L) * g.L + x;
     a0 = s * g.B + (2 * d + 1) * g.h2;
     b0 = t * g.B + (2 * d) * g.h2;
 }
-__device__ __forceinline__ int link_majorana(const Geometry& g, int a0, int b0, int xi) {
+GGF_HD int link_majorana(const Geometry& g, int a0, int b0, int xi) {
     return xi < g.h2 ? a0 + xi : b0 + xi - g.h2;
 }
 
@@ -178,7 +178,7 @@ __device__ __forceinline__ void pair_delta(const DevConst& dc, int p, int l, con
 // z = 2 u_z - 1, phi = 2 pi u_phi, renormalised to a unit quaternion.  r and
 // r^dag are equally likely (a Haar-symmetric move).  Writes the new
 // quaternion and the old and new doublet rotations; returns u_acc.
-__device__ __forceinline__ double draw_su2(const Geometry& g, const void* links, int c, int l,
+GGF_HD double draw_su2(const Geometry& g, const void* links, int c, int l,
                                            unsigned long long sweep, uint64_t seed, double width, double* qn,
                                            double* Rold, double* Rnew) {
     uint64_t ctr[4] = {(uint64_t)sweep, (uint64_t)l, 0, 0}, out[4];
@@ -258,7 +258,7 @@ __device__ __forceinline__ cxd bordered_ratio(const cxd* D, const cxd* Ws, cxd* 
 
 // Ordered Gaussian indices (n, m) of pair p: p < K is (p, p); the pairs n < m
 // follow in lexicographic order.
-__device__ __forceinline__ void pair_nm(int K, int p, int& n, int& m) {
+GGF_HD void pair_nm(int K, int p, int& n, int& m) {
     if (p < K) { n = m = p; return; }
     int k = p - K;
     n = 0;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void pair_nm(int K, int p, int& n, int& m) {
 // Scale of the pair terms of one configuration: amax = max_p Re(logc_p + ell_p)
 // and 1 / (N(G) e^{-amax}), N(G) = Re sum_p w_p e^{logc_p + ell_p}; then
 // pair_norm gives N_nm(G) / N(G) for pair p (diagonal pairs real).
-__device__ __forceinline__ void pair_scale(const DevConst& dc, const cxd* ell_c, double& amax, double& iden) {
+GGF_HD void pair_scale(const DevConst& dc, const cxd* ell_c, double& amax, double& iden) {
     amax = -INFINITY;
     for (int p = 0; p < dc.P; ++p) amax = fmax(amax, dc.logc[p].x + ell_c[p].x);
     double den = 0.0;
@@ -281,7 +281,7 @@ __device__ __forceinline__ void pair_scale(const DevConst& dc, const cxd* ell_c,
     }
     iden = 1.0 / den;
 }
-__device__ __forceinline__ cxd pair_norm(const DevConst& dc, const cxd* ell_c, int p, double amax, double iden) {
+GGF_HD cxd pair_norm(const DevConst& dc, const cxd* ell_c, int p, double amax, double iden) {
     cxd e = dc.logc[p] + ell_c[p];
     if (p < dc.K) e.y = 0.0;
     e.x -= amax;

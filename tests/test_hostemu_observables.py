@@ -1,0 +1,193 @@
+"""The observable kernels' per-thread code (csrc/ggf_obs.cuh) and the SU(2)
+proposal and twist helpers, built for the host by
+tests/hostemu/emu_observables.cu, against the oracle -- on CPU.
+
+The test lays out the device-side arrays as the library does (site blocks
+D, A, B; bond blocks Gamma_X per pair; the chains' inverses of the reduced
+matrix D + O Gamma_X O^T; log-weights per pair) and checks the electric
+observable, the fermionic bilinears and the per-pair parts item by item
+against oracle.electric, oracle.fermionic and oracle.variational.  This checks
+the kernels' index arithmetic and data layout before a GPU runs them; the
+GPU parity tests remain the parity claim.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import ggf_inputs as gi
+from oracle import electric, fermionic, variational, weight
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("emu") / "libemu.so")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-shared", "-Xcompiler", "-fPIC", "-gencode",
+                    "arch=compute_103a,code=sm_103a", "-o", out,
+                    os.path.join(HERE, "hostemu", "emu_observables.cu")], check=True, capture_output=True)
+    return ctypes.CDLL(out)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _cplx(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return np.ascontiguousarray(np.stack([a.real, a.imag], axis=-1))
+
+
+class Layout:
+    """Device-side arrays of one problem and a set of chain configurations."""
+
+    def __init__(self, p, links):
+        self.p = p
+        V, B, nl, K = p.V, 8 * p.n_v, p.n_links, p.K
+        self.q = np.array([int(p.q_src[0]), int(p.q_src[1]) if p.n_v > 1 else 1] if p.group == gi.U1 else [1, 1],
+                          dtype=np.int32)
+        self.D = np.ascontiguousarray(np.array([p.gamma_site[s][2:, 2:] for s in range(V)]))
+        self.Ap = np.ascontiguousarray(np.array([p.gamma_site[s][:2, :2] for s in range(V)]))
+        self.Bp = np.ascontiguousarray(np.array([p.gamma_site[s][:2, 2:] for s in range(V)]))
+        bd = weight.BondData(p)
+        pairs = [(n, n) for n in range(K)] + [(n, m) for n in range(K) for m in range(n + 1, K)]
+        self.pairs = pairs
+        self.Gr = np.ascontiguousarray(np.array([[bd.G[n, n, l].real for l in range(nl)] for n in range(K)]))
+        cp = pairs[K:]
+        self.Gc = _cplx(np.array([[bd.G[n, m, l] for l in range(nl)] for n, m in cp]) if cp
+                        else np.zeros((1, nl, p.r, p.r)))
+        lam = p.lam
+        self.w = _cplx([abs(lam[n]) ** 2 if n == m else 2 * np.conj(lam[n]) * lam[m] for n, m in pairs])
+        self.logc = _cplx(np.zeros(len(pairs)))
+        W = weight.Weights(p)
+        virt = np.array([i for i in range(p.m_s * V) if i % p.m_s >= 2])
+        Dfull = np.zeros((B * V, B * V))
+        for s in range(V):
+            Dfull[s * B:(s + 1) * B, s * B:(s + 1) * B] = self.D[s]
+        Wr, Wc, ell = [], [], []
+        for G in links:
+            Ov = weight.twist_matrix(p, G)[np.ix_(virt, virt)]
+            lnm = W.log_n_matrix(G)
+            inv = {nm: np.linalg.inv(Dfull + Ov @ W.GX[nm][np.ix_(virt, virt)] @ Ov.T) for nm in pairs}
+            Wr.append([inv[(n, n)].real for n in range(K)])
+            Wc.append([inv[nm] for nm in cp])
+            ell.append([lnm[n, m] for n, m in pairs])
+        self.Wr = np.ascontiguousarray(np.array(Wr))
+        self.Wc = _cplx(np.array(Wc)) if cp else np.zeros(2)
+        self.ell = _cplx(np.array(ell))
+        self.links = np.ascontiguousarray(links)
+        self.n = len(links)
+
+    def common(self):
+        p = self.p
+        return [ctypes.c_int(p.L), ctypes.c_int(p.group), ctypes.c_int(p.n_v), _ptr(self.q), ctypes.c_int(p.K),
+                _ptr(self.D), _ptr(self.Ap), _ptr(self.Bp), _ptr(self.Gr), _ptr(self.Gc), _ptr(self.logc),
+                _ptr(self.w), ctypes.c_int(self.n)]
+
+
+def _c(a):
+    return a[..., 0] + 1j * a[..., 1]
+
+
+CASES = [(3, gi.Z2, 1, 3), (2, gi.Z2, 2, 2), (3, gi.U1, 1, 2), (2, gi.U1, 2, 3), (2, gi.SU2, 2, 2),
+         (1, gi.U1, 1, 2)]
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", CASES)
+def test_electric_items_match_oracle(emu, L, grp, n_v, K):
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=13)
+    lay = Layout(p, links)
+    out = np.zeros((2, p.n_links, 2))
+    pairs = np.zeros((2, p.n_links, K, K, 2))
+    emu.emu_electric(*lay.common()[:-1], ctypes.c_int(2), _ptr(lay.links), _ptr(lay.Wr), _ptr(lay.Wc),
+                     _ptr(lay.ell), _ptr(out), _ptr(pairs))
+    el, lm = electric.Electric(p), variational.LocalMatrices(p)
+    for c in range(2):
+        ref = el.f_electric(links[c])
+        assert np.abs(_c(out)[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+        refp = lm(links[c])["electric"]
+        assert np.abs(_c(pairs)[c] - refp).max() <= 1e-11 * max(1.0, np.abs(refp).max())
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", CASES)
+def test_fermion_items_match_oracle(emu, L, grp, n_v, K):
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=14)
+    lay = Layout(p, links)
+    site = np.zeros((2, p.V, 2))
+    link = np.zeros((2, p.n_links, 2, 2, 2))
+    ps = np.zeros((2, p.V, K, K, 2))
+    pl = np.zeros((2, p.n_links, 2, 2, K, K, 2))
+    emu.emu_fermion(*lay.common(), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell), _ptr(site), _ptr(link),
+                    _ptr(ps), _ptr(pl))
+    fe, lm = fermionic.Fermionic(p), variational.LocalMatrices(p)
+    for c in range(2):
+        rs, rl = fe.bilinears(links[c])
+        assert np.abs(_c(site)[c] - rs).max() <= 1e-11
+        assert np.abs(_c(link)[c] - rl).max() <= 1e-11
+        ref = lm(links[c])
+        assert np.abs(_c(ps)[c] - ref["density"]).max() <= 1e-11 * max(1.0, np.abs(ref["density"]).max())
+        Ge = fe.gamma_eff(links[c])
+        for l in range(p.n_links):
+            s, t = fermionic._link_sites(p, l)
+            for a in range(2):
+                for b in range(2):
+                    i, j = 2 * s + a, 2 * t + b
+                    want = np.array([[ref["norm"][n, m] * (1.0 if i == j else -1j * Ge[n, m][i, j])
+                                      for m in range(K)] for n in range(K)])
+                    assert np.abs(_c(pl)[c, l, a, b] - want).max() <= 1e-11 * max(1.0, np.abs(want).max())
+
+
+def test_pair_norm_items_match_oracle(emu):
+    p = gi.make_problem(2, gi.U1, 1, 3, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=15)
+    lay = Layout(p, links)
+    out = np.zeros((2, 3, 3, 2))
+    emu.emu_pair_norm(ctypes.c_int(p.L), ctypes.c_int(p.group), ctypes.c_int(p.n_v), _ptr(lay.q),
+                      ctypes.c_int(p.K), _ptr(lay.logc), _ptr(lay.w), ctypes.c_int(2), _ptr(lay.ell), _ptr(out))
+    lm = variational.LocalMatrices(p)
+    for c in range(2):
+        assert np.abs(_c(out)[c] - lm(links[c])["norm"]).max() <= 1e-12
+
+
+def test_su2_proposal_and_twist_match_oracle(emu):
+    """The GPU's SU(2) move (Philox words -> quaternion) equals the oracle's
+    proposal to rounding, so FP64 decisions can agree bit for bit; the
+    doublet rotation and the twisted link block equal the oracle's."""
+    from oracle import mcmc
+    from oracle.philox import draws4
+    emu.emu_draw_su2.restype = ctypes.c_double
+    emu.emu_twisted_su2.restype = ctypes.c_double
+    p = gi.make_problem(1, gi.SU2, 2, 1)
+    rng = np.random.default_rng(4)
+    for k in range(20):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        c, sweep, seed, width = k % 3, 5 + k, 1234 + k, 0.5 + 0.1 * k
+        qn, Ro, Rn = np.zeros(4), np.zeros(16), np.zeros(16)
+        u = emu.emu_draw_su2(ctypes.c_ulonglong(sweep), ctypes.c_uint64(seed), ctypes.c_int(c),
+                             ctypes.c_double(width), _ptr(q), _ptr(qn), _ptr(Ro), _ptr(Rn))
+        ua, up, uz, uf = draws4(seed, c, sweep, 0)
+        assert u == ua
+        want = mcmc.propose(gi.SU2, q, up, width, uz, uf)
+        assert np.abs(qn - want).max() <= 4e-16
+        assert np.abs(Ro.reshape(4, 4) - weight.doublet_rotation(weight.su2_matrix(q))).max() <= 1e-15
+        assert np.abs(Rn.reshape(4, 4) - weight.doublet_rotation(weight.su2_matrix(want))).max() <= 1e-15
+    # twisted block of one link against O Gamma O^T with the oracle's twist
+    G = np.ascontiguousarray(p.gamma_bond[0, 0])
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    R = np.ascontiguousarray(weight.doublet_rotation(weight.su2_matrix(q)))
+    O = np.eye(8)
+    O[:4, :4] = R
+    want = O @ G @ O.T
+    got = np.array([[emu.emu_twisted_su2(_ptr(G), x, y, _ptr(R)) for y in range(8)] for x in range(8)])
+    assert np.abs(got - want).max() <= 1e-15
