@@ -39,8 +39,9 @@ contraction (oracle.fock) for Z2 and U(1), K = 1, 2, 3; invariants
 (N >= 0, Im N = 0, N_mn = conj N_nm, gauge invariance, lambda phase
 invariance, B_2 = B_1 => N = |lambda_1 + lambda_2|^2 N_11); exhaustive
 normalisation on the 2x2 Z2 lattice; for pure site covariances the
-full-space Pfaffian equals the virtual-only Pf(D_G + Gamma_X) (Z2, U(1),
-SU(2); it does not for a mixed one).
+full-space Pfaffian equals the virtual-only Pf(D_G + Gamma_X) times the fixed
+sign prod_s sign(Gamma_s[0, 1]) (Z2, U(1), SU(2), L = 1..4; not for a mixed
+one).
 SU(2) (tests/test_oracle_su2.py): the doublet rotation against explicit
 Fock operators, N_nm against the Fock contraction on the 1x1 torus, the U(1)
 code on the subgroup exp(i theta sigma_z), gauge invariance under

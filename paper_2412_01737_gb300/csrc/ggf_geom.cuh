@@ -164,4 +164,30 @@ __host__ __device__ T twisted_su2(const DevConst& dc, int pair, int link, int x,
     return v;
 }
 
+// Element (i, j) of M_p(G) = D + O(G) Gamma_X^p O(G)^T for configuration cfg
+// (T = double for the diagonal pairs, cxd for the pairs n < m, indexed within
+// their family).
+template <class T>
+__host__ __device__ T assemble_elem(const DevConst& dc, const void* links, int cfg, int pair, int i, int j) {
+    const Geometry& g = dc.g;
+    T v = Sc<T>::zero();
+    int si = i / g.B, sj = j / g.B;
+    if (si == sj) v = Sc<T>::from(Sc<double>::to(dc.D[((size_t)si * g.B + (i - si * g.B)) * g.B + (j - sj * g.B)]));
+    int li, pi, lj, pj;
+    link_of(g, i, li, pi);
+    link_of(g, j, lj, pj);
+    if (li == lj) {
+        if (g.group == GGF_SU2) {
+            double R[16];
+            doublet_rotation(link_quat(g, links, cfg, li), R);
+            v += twisted_su2<T>(dc, pair, li, pi, pj, R);
+        } else {
+            double gv, th;
+            link_value<T>(dc, links, cfg, li, gv, th);
+            v += twisted<T>(dc, pair, li, pi, pj, gv, th);
+        }
+    }
+    return v;
+}
+
 }  // namespace

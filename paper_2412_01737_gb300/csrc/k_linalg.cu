@@ -30,25 +30,7 @@ __global__ void assemble_kernel(DevConst dc, const int* item_cfg, const int* ite
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NN) return;
     int i = (int)(e / g.N), j = (int)(e - (size_t)i * g.N);
-    int cfg = item_cfg[item], pair = item_pair[item];
-    T v = Sc<T>::zero();
-    int si = i / g.B, sj = j / g.B;
-    if (si == sj) v = Sc<T>::from(Sc<double>::to(dc.D[((size_t)si * g.B + (i - si * g.B)) * g.B + (j - sj * g.B)]));
-    int li, pi, lj, pj;
-    link_of(g, i, li, pi);
-    link_of(g, j, lj, pj);
-    if (li == lj) {
-        if (g.group == GGF_SU2) {
-            double R[16];
-            doublet_rotation(link_quat(g, links, cfg, li), R);
-            v += twisted_su2<T>(dc, pair, li, pi, pj, R);
-        } else {
-            double gv, th;
-            link_value<T>(dc, links, cfg, li, gv, th);
-            v += twisted<T>(dc, pair, li, pi, pj, gv, th);
-        }
-    }
-    dst[(size_t)item * NN + e] = v;
+    dst[(size_t)item * NN + e] = assemble_elem<T>(dc, links, item_cfg[item], item_pair[item], i, j);
 }
 
 // ---- block reductions -----------------------------------------------------------

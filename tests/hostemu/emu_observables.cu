@@ -81,6 +81,19 @@ double emu_twisted_su2(const double* Gr, int x, int y, const double* R) {
     return twisted_su2<double>(dc, 0, 0, x, y, R);
 }
 
+// M_p of configuration 0 (links holds one configuration) into M [N][N]
+// (cplx: complex pair p of its family, complex out).
+void emu_assemble(int L, int group, int n_v, const int* q, int K, const double* D, const double* Gr,
+                  const double* Gc, const void* links, int pair, int cplx, double* M) {
+    DevConst dc = make_dc(L, group, n_v, q, K, D, nullptr, nullptr, Gr, Gc, nullptr, nullptr);
+    const int N = dc.g.N;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            if (cplx) ((cxd*)M)[(size_t)i * N + j] = assemble_elem<cxd>(dc, links, 0, pair, i, j);
+            else M[(size_t)i * N + j] = assemble_elem<double>(dc, links, 0, pair, i, j);
+        }
+}
+
 void emu_pair_norm(int L, int group, int n_v, const int* q, int K, const double* logc, const double* w,
                    int n_chains, const double* ell, double* out) {
     DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, logc, w);

@@ -191,3 +191,37 @@ def test_su2_proposal_and_twist_match_oracle(emu):
     want = O @ G @ O.T
     got = np.array([[emu.emu_twisted_su2(_ptr(G), x, y, _ptr(R)) for y in range(8)] for x in range(8)])
     assert np.abs(got - want).max() <= 1e-15
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", [(3, gi.Z2, 1, 2), (2, gi.U1, 2, 2), (2, gi.SU2, 2, 2), (1, gi.SU2, 2, 2)])
+def test_assembled_matrix_matches_reduced_matrix(emu, L, grp, n_v, K):
+    """assemble_elem builds D + O(G) Gamma_X O(G)^T on the virtual modes, whose
+    Pfaffian is the covariance route's full-space one up to a fixed sign."""
+    from oracle.pfaffian import log_pfaffian
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=16)
+    lay = Layout(p, links[:1])
+    W = weight.Weights(p)
+    virt = np.array([i for i in range(p.m_s * p.V) if i % p.m_s >= 2])
+    Ov = weight.twist_matrix(p, links[0])[np.ix_(virt, virt)]
+    N = 8 * p.n_v * p.V
+    Dfull = np.zeros((N, N))
+    B = 8 * p.n_v
+    for s in range(p.V):
+        Dfull[s * B:(s + 1) * B, s * B:(s + 1) * B] = lay.D[s]
+    for k, (n, m) in enumerate(lay.pairs):
+        cplx = k >= K
+        M = np.zeros((N, N, 2)) if cplx else np.zeros((N, N))
+        emu.emu_assemble(ctypes.c_int(p.L), ctypes.c_int(p.group), ctypes.c_int(p.n_v), _ptr(lay.q),
+                         ctypes.c_int(K), _ptr(lay.D), _ptr(lay.Gr), _ptr(lay.Gc), _ptr(lay.links),
+                         ctypes.c_int(k - K if cplx else k), ctypes.c_int(int(cplx)), _ptr(M))
+        got = _c(M) if cplx else M
+        want = Dfull + Ov @ W.GX[n, m][np.ix_(virt, virt)] @ Ov.T
+        assert np.abs(got - want).max() <= 1e-14
+        # and the full-space Pfaffian of the covariance route agrees with it up
+        # to the sites' fixed sign prod_s sign(Gamma_s[0, 1])
+        O = weight.twist_matrix(p, links[0])
+        la, ph = log_pfaffian(O.T @ W.GA @ O + W.GX[n, m])
+        lb, pb = log_pfaffian(got)
+        sign = np.prod([np.sign(p.gamma_site[s][0, 1]) for s in range(p.V)])
+        assert abs(np.exp((la + np.log(complex(ph))) - (lb + np.log(complex(pb)))) - sign) <= 1e-12

@@ -104,29 +104,31 @@ def test_transition_covariance_is_pure():
             assert np.allclose(G, -G.T, atol=1e-13)
 
 
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
 @pytest.mark.parametrize("grp,n_v", [(gi.Z2, 1), (gi.U1, 2), (gi.SU2, 2)])
-def test_reduced_virtual_matrix_identity(grp, n_v):
+def test_reduced_virtual_matrix_identity(grp, n_v, L):
     """The sampler works on the virtual-mode matrix D + O Gamma_X O^T only.
-    For pure site covariances its Pfaffian equals the full-space
-    Pf(Gamma_A(G) + 0 (+) Gamma_X) of the covariance route, for every pair
-    and configuration, although the physical-virtual coupling is non-zero;
-    for a mixed site covariance the two differ."""
+    For pure site covariances the full-space Pf(Gamma_A(G) + 0 (+) Gamma_X) of
+    the covariance route equals its Pfaffian times prod_s sign(Gamma_s[0, 1])
+    (the sites' physical blocks), for every pair and configuration, although
+    the physical-virtual coupling is non-zero; for a mixed site covariance
+    the ratio is not of modulus one."""
     from oracle.pfaffian import log_pfaffian
-    p = gi.make_problem(2, grp, n_v, 2, bond_scale=0.3)
+    p = gi.make_problem(L, grp, n_v, 2, bond_scale=0.3)
     W = weight.Weights(p)
     virt = np.array([i for i in range(p.m_s * p.V) if i % p.m_s >= 2])
+    sign = np.prod([np.sign(p.gamma_site[s][0, 1]) for s in range(p.V)])
 
-    def gap(GA, links, nm):
+    def ratio(GA, links, nm):
         O = weight.twist_matrix(p, links)
         la, ph = log_pfaffian(O.T @ GA @ O + W.GX[nm])
         Ov = O[np.ix_(virt, virt)]
         lb, pb = log_pfaffian(GA[np.ix_(virt, virt)] + Ov @ W.GX[nm][np.ix_(virt, virt)] @ Ov.T)
-        return (la + np.log(complex(ph))) - (lb + np.log(complex(pb)))
+        return np.exp((la + np.log(complex(ph))) - (lb + np.log(complex(pb))))
 
     for links in gi.random_links(p, 3, seed=3):
         for nm in [(0, 0), (0, 1), (1, 0)]:
-            d = gap(W.GA, links, nm)
-            assert abs(np.exp(d) - 1.0) <= 1e-12
+            assert abs(ratio(W.GA, links, nm) - sign) <= 1e-12
     if grp != gi.SU2:        # the SU(2) physical singlet does not couple
         assert np.abs(p.gamma_site[0][:2, 2:]).max() > 0.05
-    assert abs(np.exp(gap(0.8 * W.GA, links, (0, 1))) - 1.0) > 0.1
+    assert abs(abs(ratio(0.8 * W.GA, links, (0, 1))) - 1.0) > 0.1
