@@ -1,0 +1,36 @@
+"""Parity at the benchmark's full problem size and launch shapes: 16x16 U(1),
+n_v = 2 (M 4096 x 4096), K = 4, FP32 chains with batches of 16 links (one
+rank-128 tensor-core flush per batch), on 32 chains (the per-chain launch
+shapes of the 256-chain benchmark, a tenth of its memory).
+
+The oracle's full recomputation is too slow at N = 4096, so the checks are
+the ones that hold at any size: the per-sweep plaquettes against the oracle's
+plaquettes of the final links, and the tracked FP32 log-weights against a
+fresh FP64 factorisation of the same configurations.
+"""
+import numpy as np
+import pytest
+
+import ggf_inputs as gi
+from oracle.observables import plaquette_mean
+from tests.gpu_util import ctx_for
+
+pytestmark = pytest.mark.gpu
+
+
+def test_u1_16x16_k4_batched_fp32():
+    p = gi.make_problem(16, gi.U1, 2, 4, seed=20241202)
+    ctx = ctx_for(p)
+    n = 32
+    ctx.chains_init(gi.cold_links(p, n), precision=1, refresh_every=1 << 30, seed=20241202, delay=16)
+    obs = ctx.sample(2)
+    fin = ctx.chains_links()
+    st = ctx.chains_stats()
+    assert np.isfinite(obs).all()
+    assert np.abs(obs[-1, :, 0] - plaquette_mean(gi.U1, 16, fin)).max() <= 1e-12
+    assert 0 < st.accepts < st.proposals
+    sample = np.ascontiguousarray(fin[::8])
+    fresh = ctx.logweight(sample)
+    tracked = obs[-1, ::8, 1]
+    assert np.abs(tracked - fresh).max() <= 1e-5 * np.abs(fresh).max() + 1e-3
+    ctx.close()
