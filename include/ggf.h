@@ -169,11 +169,12 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links,
 
 /* Run n_sweeps Metropolis sweeps on every chain (Sec. 5.1).  A sweep
  * proposes links l = 0 .. 2V-1 in order (Z2 flip; U(1) theta += width (u -
- * 1/2) wrapped into [0, 2 pi)), scores each proposal by the low-rank Pfaffian
+ * 1/2) wrapped into [0, 2 pi); SU(2) the quaternion move described above),
+ * scores each proposal by the low-rank Pfaffian
  * ratio on the cached inverse, accepts iff u < N(G')/N(G) and applies the
  * rank-r Sherman-Morrison-Woodbury update.  Random numbers: Philox4x64-10 with
  * counter (sweep, link, 0, 0), key (seed, chain); word 0 -> u_accept, word 1
- * -> u_propose, u = (word >> 11) 2^-53.
+ * -> u_propose (SU(2): words 2 and 3 give the axis), u = (word >> 11) 2^-53.
  *   obs [n_sweeps][n_chains][GGF_N_OBS] (may be NULL) */
 ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* stream);
 
