@@ -258,6 +258,17 @@ ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem,
 #define GGF_PAIRS_LINK 3
 ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* stream);
 
+/* Score of the site blocks: out[c][s][i][j] = d log N(G_c) / d D_s[i][j]
+ * for every chain c and site s, D_s the site's virtual covariance block
+ * (B x B, B = 8 n_v, entries treated as independent), FP64.  For pure site
+ * states N_nm(G) is a constant times Pf(D + O Gamma_X O^T), so the score is
+ * Re sum_nm lambda_n^* lambda_m (N_nm(G) / N(G)) (1/2) W_nm[s, s]^T from the
+ * cached inverses.  A change of the site parameters changes log N(G) by
+ * sum_ij S_ij dD_ij; the gradient of a Wilson-loop energy is then the
+ * covariance E_p[(W(G) - E) sum_s tr(S_s^T dD_s)].  Pending delayed updates
+ * are folded into W first.  out [n_chains][V][B][B], caller-owned. */
+ggf_status ggf_chains_score(ggf_ctx* ctx, double* out, int mem, void* stream);
+
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
  * L^2.  For tests and diagnostics. */

@@ -21,10 +21,15 @@ Samples G_i of p_lambda0 estimate both matrices up to the common factor
 configuration the local matrices are returned in that normalised form
 (Ohat(G) / N_lambda0(G), N(G) / N_lambda0(G)), which needs no absolute scale.
 
-Pinned (tests/test_oracle_variational.py): on the 2x2 Z2 lattice, for random
-lambda, the Hermitian forms built from exhaustive sums reproduce the direct
-exhaustive expectations of the plaquette, the link flip and the densities
-computed with that lambda; the generalised eigenvector minimises the energy
+Also the score d log N(G) / d D_s of the site blocks (score_sites), which
+gives exact gradients of Wilson-loop energies with respect to the site
+parameters: dE = E_p[(W(G) - E) sum_s tr(S_s^T dD_s)].
+
+Pinned (tests/test_oracle_variational.py): the score against central finite
+differences of log N(G) along commutant generators of the site states (Z2,
+U(1), SU(2)); on the 2x2 Z2 lattice, for random lambda, the Hermitian forms
+built from exhaustive sums reproduce the direct exhaustive expectations of
+the plaquette, the link flip and the densities computed with that lambda; the generalised eigenvector minimises the energy
 over random lambda; the forms are Hermitian and Nbar positive definite.
 """
 from __future__ import annotations
@@ -110,6 +115,33 @@ def linear_method(Hbar, Nbar):
     if abs(lam[0]) > 0:
         lam = lam * (abs(lam[0]) / lam[0])
     return float(w[0]), lam
+
+
+def score_sites(p, links) -> np.ndarray:
+    """d log N(G) / d D_s[i][j] for every site s (V, B, B), B = 8 n_v, D_s the
+    site's virtual covariance block, entries treated as independent.  For
+    pure site states N_nm(G) is Pf(D + O Gamma_X O^T) times a constant, and
+    d log Pf(M) = (1/2) tr(M^{-1} dM), so
+        S_s = Re sum_nm lambda_n^* lambda_m (N_nm(G) / N(G)) (1/2) W_nm[s, s]^T
+    with W_nm[s, s] the site's diagonal block of (D + O Gamma_X^nm O^T)^{-1}.
+    A variation of the site parameters changes log N(G) by sum_ij S_ij dD_ij."""
+    W = weight.Weights(p)
+    lnm = W.log_n_matrix(links)
+    logN = weight.combine(lnm, p.lam)
+    B = 8 * p.n_v
+    virt = np.array([i for i in range(p.m_s * p.V) if i % p.m_s >= 2])
+    Ov = weight.twist_matrix(p, links)[np.ix_(virt, virt)]
+    D = np.zeros((B * p.V, B * p.V))
+    for s in range(p.V):
+        D[s * B:(s + 1) * B, s * B:(s + 1) * B] = p.gamma_site[s][2:, 2:]
+    S = np.zeros((p.V, B, B))
+    for n in range(p.K):
+        for m in range(p.K):
+            Wnm = np.linalg.inv(D + Ov @ W.GX[n, m][np.ix_(virt, virt)] @ Ov.T)
+            wt = np.conj(p.lam[n]) * p.lam[m] * np.exp(lnm[n, m] - logN)
+            for s in range(p.V):
+                S[s] += (wt * 0.5 * Wnm[s * B:(s + 1) * B, s * B:(s + 1) * B].T).real
+    return S
 
 
 def with_lambda(p, lam):

@@ -22,6 +22,7 @@ ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st)
 ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cxd* d_pair_site, cxd* d_pair_link,
                        cudaStream_t st);
 ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
+ggf_status ggf_score(ggf_ctx* ctx, double* d_out, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -825,6 +826,24 @@ ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* 
         GGF_CK(cudaStreamSynchronize(st));
         return check_err_word(ctx);
     }
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_score(ggf_ctx* ctx, double* out, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!out) return ggf_fail(ctx, GGF_EINVAL, "null out");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)ctx->ch.n * ctx->g.V * ctx->g.B * ctx->g.B * sizeof(double);
+    if (mem == GGF_MEM_HOST) {
+        DBuf d;
+        GGF_TRY(dalloc(ctx, d, bytes));
+        GGF_TRY(ggf_score(ctx, (double*)d.p, st));
+        GGF_CK(cudaMemcpyAsync(out, d.p, bytes, cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return check_err_word(ctx);
+    }
+    GGF_TRY(ggf_score(ctx, out, st));
     return GGF_OK;
 }
 

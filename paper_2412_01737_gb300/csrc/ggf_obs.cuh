@@ -301,4 +301,33 @@ __host__ __device__ void fermion_item(const DevConst& dc, int c, int it, const R
     }
 }
 
+// ---- score of the site blocks ------------------------------------------------
+// d log N(G) / d D_s[i][j] of chain c and site s into out[c][s][i][j] (B x B,
+// FP64, entries treated as independent).  For pure site states
+// N_nm(G) = const Pf(D + O Gamma_X O^T) and d log Pf(M) = (1/2) tr(M^{-1} dM),
+// so the score is Re sum_p w_p (N_p / N(G)) (1/2) W_p[s, s]^T (the (m, n)
+// order of a pair n < m is the conjugate term, hence the real part).
+template <class RW, class CW>
+__host__ __device__ void score_item(const DevConst& dc, int c, int s, const RW* Wr, const CW* Wc, const cxd* ell,
+                                    double* out) {
+    const Geometry& g = dc.g;
+    const int B = g.B, N = g.N;
+    const size_t NN = (size_t)N * N;
+    const cxd* el = ell + (size_t)c * dc.P;
+    double amax, iden;
+    pair_scale(dc, el, amax, iden);
+    double* o = out + ((size_t)c * g.V + s) * B * B;
+    for (int e = 0; e < B * B; ++e) o[e] = 0.0;
+    for (int p = 0; p < dc.P; ++p) {
+        const cxd E = dc.w[p] * pair_norm(dc, el, p, amax, iden);
+        for (int i = 0; i < B; ++i)
+            for (int j = 0; j < B; ++j) {
+                const size_t off = (size_t)(s * B + j) * N + (size_t)s * B + i;     // W_p[sB + j][sB + i]
+                const cxd wv = p < dc.K ? Sc<RW>::to(Wr[((size_t)c * dc.K + p) * NN + off])
+                                        : Sc<CW>::to(Wc[((size_t)c * dc.Kc + (p - dc.K)) * NN + off]);
+                o[i * B + j] += 0.5 * (E * wv).x;
+            }
+    }
+}
+
 }  // namespace

@@ -49,7 +49,8 @@ class ChainStats(ctypes.Structure):
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
-           "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_stats",
+           "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
+           "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
            "ggf_selftest_flush", "ggf_net_create", "ggf_net_destroy", "ggf_net_last_error", "ggf_net_get_params",
@@ -88,6 +89,7 @@ def load():
         "ggf_chains_electric": ([P, P, I, P], I),
         "ggf_chains_fermion": ([P, P, P, I, P], I),
         "ggf_chains_pairs": ([P, I, P, I, P], I),
+        "ggf_chains_score": ([P, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -177,6 +179,7 @@ class GGF:
 
     def init_group(self, group, n_v, q_src=None):
         self.group = int(group)
+        self.n_v = int(n_v)
         q = None if q_src is None else np.ascontiguousarray(q_src, dtype=np.int32)
         self._ck(self.lib.ggf_init_group(self.h, int(group), int(n_v), None if q is None else q.ctypes.data))
 
@@ -311,6 +314,17 @@ class GGF:
             self._ck(self.lib.ggf_chains_pairs(self.h, int(what), host.ctypes.data, MEM_HOST, None))
             return host[..., 0] + 1j * host[..., 1]
         self._ck(self.lib.ggf_chains_pairs(self.h, int(what), _ptr(out)[0], self._mem(out), _stream([out])))
+        return out
+
+    def chains_score(self, out=None):
+        """d log N(G) / d D_s of every chain and site: numpy array
+        (n_chains, V, B, B), or fills `out` (float64, numpy or CUDA tensor)."""
+        if out is None:
+            nv = self.n_v
+            host = np.zeros((self.n_chains, self.n_links() // 2, 8 * nv, 8 * nv))
+            self._ck(self.lib.ggf_chains_score(self.h, host.ctypes.data, MEM_HOST, None))
+            return host
+        self._ck(self.lib.ggf_chains_score(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
         return out
 
     def chains_inverse(self, chain, pair, N):

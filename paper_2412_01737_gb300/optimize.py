@@ -17,6 +17,12 @@ current lambda and estimates Hbar and Nbar for an energy
 (any coefficient may be omitted); the couplings, and thus the Hamiltonian,
 are the caller's.  ``linear_method`` solves for the new lambda, which
 ``GGF.init_gaussians`` takes for the next round of sampling.
+
+``wilson_score`` gives the gradient of a Wilson-loop energy with respect to
+the site blocks, as the covariance of the plaquette with the score
+d log N(G) / d D_s (``GGF.chains_score``); gradients of the electric and
+fermionic terms would also need the derivatives of their per-pair parts and
+are not provided.
 """
 from __future__ import annotations
 
@@ -59,6 +65,27 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
         Nbar = Nbar + pairs["norm"].sum(axis=0)
         n += H.shape[0]
     return Hbar / n, Nbar / n
+
+
+def wilson_score(ctx, n_sweeps: int):
+    """Run n_sweeps sweeps and return (<W>, C): the mean plaquette and, per
+    site, the covariance C_s = E_p[(W(G) - <W>) S_s(G)] of the chains' mean
+    plaquette with the site scores S_s = d log N(G) / d D_s
+    (GGF.chains_score).  A change dD_s of the site blocks (through the
+    site parameters, keeping the states pure) changes <W> by
+    sum_s sum_ij C_s[i, j] dD_s[i, j]: the exact gradient of a Wilson-loop
+    energy with respect to the site parameters."""
+    sw, ss, sws, n = 0.0, 0.0, 0.0, 0
+    for _ in range(n_sweeps):
+        obs = ctx.sample(1)
+        S = ctx.chains_score()
+        w = obs[0, :, 0]
+        sw = sw + w.sum()
+        ss = ss + S.sum(axis=0)
+        sws = sws + np.einsum("c,csij->sij", w, S)
+        n += w.shape[0]
+    mw = sw / n
+    return mw, sws / n - mw * ss / n
 
 
 def linear_method(Hbar: np.ndarray, Nbar: np.ndarray):

@@ -94,6 +94,13 @@ void emu_assemble(int L, int group, int n_v, const int* q, int K, const double* 
         }
 }
 
+void emu_score(int L, int group, int n_v, const int* q, int K, const double* logc, const double* w, int n_chains,
+               const double* Wr, const double* Wc, const double* ell, double* out) {
+    DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, logc, w);
+    for (int c = 0; c < n_chains; ++c)
+        for (int s = 0; s < dc.g.V; ++s) score_item<double, cxd>(dc, c, s, Wr, (const cxd*)Wc, (const cxd*)ell, out);
+}
+
 void emu_pair_norm(int L, int group, int n_v, const int* q, int K, const double* logc, const double* w,
                    int n_chains, const double* ell, double* out) {
     DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, logc, w);

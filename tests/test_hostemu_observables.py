@@ -225,3 +225,17 @@ def test_assembled_matrix_matches_reduced_matrix(emu, L, grp, n_v, K):
         lb, pb = log_pfaffian(got)
         sign = np.prod([np.sign(p.gamma_site[s][0, 1]) for s in range(p.V)])
         assert abs(np.exp((la + np.log(complex(ph))) - (lb + np.log(complex(pb)))) - sign) <= 1e-12
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", [(2, gi.Z2, 1, 2), (2, gi.U1, 2, 3), (2, gi.SU2, 2, 2)])
+def test_score_items_match_oracle(emu, L, grp, n_v, K):
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=17)
+    lay = Layout(p, links)
+    B = 8 * n_v
+    out = np.zeros((2, p.V, B, B))
+    emu.emu_score(ctypes.c_int(p.L), ctypes.c_int(p.group), ctypes.c_int(p.n_v), _ptr(lay.q), ctypes.c_int(K),
+                  _ptr(lay.logc), _ptr(lay.w), ctypes.c_int(2), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell), _ptr(out))
+    for c in range(2):
+        ref = variational.score_sites(p, links[c])
+        assert np.abs(out[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())

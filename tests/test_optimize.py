@@ -21,6 +21,30 @@ def test_linear_method_matches_oracle():
     assert abs(optimize.energy(H, N, l1) - e1) <= 1e-12
 
 
+class _ScoreStub:
+    """Serves oracle scores and plaquettes of fixed configurations."""
+
+    def __init__(self, p, configs):
+        from oracle.observables import plaquette_values
+        self.S = np.array([variational.score_sites(p, G) for G in configs])
+        self.w = plaquette_values(p.group, p.L, configs).mean(axis=1)
+
+    def sample(self, n):
+        return np.stack([self.w, np.zeros_like(self.w), np.zeros_like(self.w)], axis=-1)[None]
+
+    def chains_score(self):
+        return self.S
+
+
+def test_wilson_score_is_the_sample_covariance():
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    stub = _ScoreStub(p, gi.random_links(p, 5, seed=3))
+    mw, C = optimize.wilson_score(stub, 3)
+    assert abs(mw - stub.w.mean()) <= 1e-14
+    want = np.mean([(w - stub.w.mean()) * S for w, S in zip(stub.w, stub.S)], axis=0)
+    assert np.abs(C - want).max() <= 1e-13
+
+
 class _Stub:
     """Serves per-pair parts of fixed configurations, one per chain."""
 

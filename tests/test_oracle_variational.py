@@ -85,3 +85,73 @@ def test_sampled_matrices_estimate_the_energy(setup):
     r = (e_loc - est * n_loc) / n_loc.mean()
     err = np.sqrt(np.mean(np.abs(r) ** 2) / len(idx))
     assert abs(est - va.expectation(H, S["norm"], lam0)) <= 5 * err
+
+
+@pytest.mark.parametrize("grp,n_v,K", [(gi.Z2, 1, 2), (gi.U1, 1, 2), (gi.U1, 2, 1), (gi.SU2, 2, 2)])
+def test_site_score_matches_finite_differences(grp, n_v, K):
+    """d log N(G) along a rotation of one sublattice's site states by a
+    generator of their commutant equals sum_s tr(S_s^T dD_s)."""
+    import dataclasses
+    import scipy.linalg
+    p = gi.make_problem(2, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 1, seed=5)[0]
+    S = va.score_sites(p, links)
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    if grp == gi.U1:
+        A = gi._project_commutant(A, gi.site_charges(p.n_v, +1))
+    elif grp == gi.SU2:
+        A = gi._project_commutant_su2(A, gi._su2_generators(gi._site_slots_su2(p.n_v)))
+
+    def log_n(eps):
+        O = scipy.linalg.expm(eps * A)
+        gs = p.gamma_site.copy()
+        for s in range(p.V):
+            if p.q_phys[s] == 1:
+                gs[s] = O @ gs[s] @ O.T
+        return weight.Weights(dataclasses.replace(p, gamma_site=gs)).log_norm(links)
+
+    h = 1e-5
+    fd = (log_n(h) - log_n(-h)) / (2 * h)
+    an = sum(np.sum(S[s] * (A @ p.gamma_site[s] - p.gamma_site[s] @ A)[2:, 2:])
+             for s in range(p.V) if p.q_phys[s] == 1)
+    assert abs(an) > 1e-3
+    assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
+
+
+def test_wilson_energy_gradient_is_a_covariance_with_the_score():
+    """d<W>/d theta = E_p[(W(G) - <W>) sum_s tr(S_s^T dD_s/d theta)] for a
+    rotation theta of one sublattice's site states (exhaustive 2x2 Z2)."""
+    import dataclasses
+    import scipy.linalg
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    cfgs = gi.all_z2_configs(p)
+    pl = plaquette_values(gi.Z2, 2, cfgs).mean(axis=1)
+    rng = np.random.default_rng(6)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+
+    def mean_w(eps):
+        O = scipy.linalg.expm(eps * A)
+        gs = p.gamma_site.copy()
+        for s in range(p.V):
+            if p.q_phys[s] == 1:
+                gs[s] = O @ gs[s] @ O.T
+        W = weight.Weights(dataclasses.replace(p, gamma_site=gs))
+        logs = np.array([W.log_norm(G) for G in cfgs])
+        w = np.exp(logs - logs.max())
+        return np.sum(w * pl) / w.sum()
+
+    h = 1e-5
+    fd = (mean_w(h) - mean_w(-h)) / (2 * h)
+    W = weight.Weights(p)
+    logs = np.array([W.log_norm(G) for G in cfgs])
+    w = np.exp(logs - logs.max())
+    w /= w.sum()
+    dD = {s: (A @ p.gamma_site[s] - p.gamma_site[s] @ A)[2:, 2:] for s in range(p.V) if p.q_phys[s] == 1}
+    dlog = np.array([sum(np.sum(S[s] * dD[s]) for s in dD) for S in (va.score_sites(p, G) for G in cfgs)])
+    mw = np.sum(w * pl)
+    an = np.sum(w * (pl - mw) * dlog)
+    assert abs(an) > 1e-3
+    assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))

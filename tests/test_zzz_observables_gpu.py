@@ -215,3 +215,50 @@ def test_lambda_optimisation_end_to_end():
     e_old = variational.expectation(H, S["norm"], p.lam).real
     assert e_old - E0 > 3.0
     assert e_new < E0 + 0.5
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+def test_site_score_matches_oracle(precision, tol):
+    from oracle import variational
+    p = gi.make_problem(3, gi.U1, 2, 2, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=71)
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=precision, seed=3)
+    S = ctx.chains_score()
+    ctx.close()
+    for c in range(2):
+        ref = variational.score_sites(p, links[c])
+        assert np.abs(S[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
+
+
+def test_wilson_gradient_estimate_matches_exact():
+    """The sampled covariance of the plaquette with the site score against
+    the exact gradient of <W> along a rotation of one sublattice's sites
+    (exhaustive 2x2 Z2 through the oracle)."""
+    from oracle import variational, weight
+    from oracle.observables import plaquette_values
+    from paper_2412_01737_gb300 import optimize
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    rng = np.random.default_rng(6)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    dD = {s: (A @ p.gamma_site[s] - p.gamma_site[s] @ A)[2:, 2:] for s in range(p.V) if p.q_phys[s] == 1}
+    cfgs = gi.all_z2_configs(p)
+    W = weight.Weights(p)
+    logs = np.array([W.log_norm(G) for G in cfgs])
+    w = np.exp(logs - logs.max())
+    w /= w.sum()
+    pl = plaquette_values(gi.Z2, 2, cfgs).mean(axis=1)
+    dlog = np.array([sum(np.sum(S[s] * dD[s]) for s in dD) for S in (variational.score_sites(p, G) for G in cfgs)])
+    exact = np.sum(w * (pl - np.sum(w * pl)) * dlog)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 1024, seed=81), precision=0, seed=9)
+    ctx.sample(3)
+    ests = []
+    for _ in range(8):
+        _, C = optimize.wilson_score(ctx, 4)
+        ests.append(sum(np.sum(C[s] * dD[s]) for s in dD))
+    ctx.close()
+    ests = np.array(ests)
+    se = ests.std(ddof=1) / np.sqrt(len(ests))
+    assert abs(ests.mean() - exact) <= max(5 * se, 0.2 * abs(exact))
