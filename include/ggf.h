@@ -233,7 +233,8 @@ ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream)
  * between the two sites is read).  Pending delayed updates are folded into W
  * first.
  *   site [n_chains][V][2], link [n_chains][2V][2][2][2], FP64 (re, im),
- *   caller-owned; either may be NULL (not both). */
+ *   caller-owned; either may be NULL (not both: GGF_EINVAL).  GGF_ESTATE
+ *   before ggf_chains_init. */
 ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem, void* stream);
 
 /* Per-pair parts of the per-configuration quantities, for optimising the
@@ -251,7 +252,8 @@ ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem,
  *   GGF_PAIRS_LINK      items = 2V x 2 x 2: the link blocks of
  *                       ggf_chains_fermion, per pair.
  * Contracting with lambda_n^* lambda_m gives the combined quantity.  Pending
- * delayed updates are folded into W first. */
+ * delayed updates are folded into W first.  GGF_EINVAL for an unknown `what`
+ * or a null `out`, GGF_ESTATE before ggf_chains_init. */
 #define GGF_PAIRS_NORM 0
 #define GGF_PAIRS_ELECTRIC 1
 #define GGF_PAIRS_SITE 2
@@ -266,7 +268,8 @@ ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* 
  * cached inverses.  A change of the site parameters changes log N(G) by
  * sum_ij S_ij dD_ij; the gradient of a Wilson-loop energy is then the
  * covariance E_p[(W(G) - E) sum_s tr(S_s^T dD_s)].  Pending delayed updates
- * are folded into W first.  out [n_chains][V][B][B], caller-owned. */
+ * are folded into W first.  out [n_chains][V][B][B], caller-owned.
+ * GGF_EINVAL for a null `out`, GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_score(ggf_ctx* ctx, double* out, int mem, void* stream);
 
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
