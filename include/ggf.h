@@ -237,6 +237,17 @@ ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream)
  *   before ggf_chains_init. */
 ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem, void* stream);
 
+/* Nearest-neighbour four-point function (Sec. 5.2, a weight-four Majorana
+ * monomial): out[c][l] = sum_nm lambda_n^* lambda_m
+ * <psi_n|c_2s c_2s+1 c_2t c_2t+1|psi_m> / N(G) for link l = (s -> t), by
+ * Wick's theorem -Pf of the physical covariance A + B W_nm B^T on those four
+ * Majoranas (three 8 n_v x 8 n_v blocks of W per pair).  With the site
+ * bilinears it gives density-density correlations,
+ * <n_s n_t> = (1 + i site[s] + i site[t] - out) / 4.  A self-link gives -1.
+ *   out [n_chains][2V][2] FP64 (re, im), caller-owned.  GGF_EINVAL for a
+ *   null `out`, GGF_ESTATE before ggf_chains_init. */
+ggf_status ggf_chains_fermion4(ggf_ctx* ctx, double* out, int mem, void* stream);
+
 /* Per-pair parts of the per-configuration quantities, for optimising the
  * superposition weights: every quantity of Secs. 5.1-5.3 is a Hermitian form
  * in lambda, O(G) = sum_nm lambda_n^* lambda_m N_nm(G) o_nm(G), so

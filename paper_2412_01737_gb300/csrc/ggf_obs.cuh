@@ -301,6 +301,59 @@ __host__ __device__ void fermion_item(const DevConst& dc, int c, int it, const R
     }
 }
 
+// ---- nearest-neighbour four-point function ----------------------------------
+// <c_2s c_2s+1 c_2t c_2t+1> of link l = (s -> t) for chain c into out[c][l]:
+// per pair, Wick's theorem gives Pf(-i G4) = -Pf(G4) with G4 the physical
+// covariance A + B W B^T on those four Majoranas (blocks (s, s), (t, t) and
+// (s, t); (t, s) = -(s, t)^T), and the pairs combine with lambda_n^* lambda_m
+// N_nm / N(G) as for the bilinears.  A self-link (s = t) gives -1.
+template <class RW, class CW, int BW>
+__host__ __device__ void fermion4_item(const DevConst& dc, int c, int l, const RW* Wr, const CW* Wc,
+                                       const cxd* ell, cxd* out) {
+    const Geometry& g = dc.g;
+    int a0, b0;
+    link_ends(g, l, a0, b0);
+    const int s = a0 / g.B, t = b0 / g.B;
+    cxd* o = out + (size_t)c * g.n_links + l;
+    if (s == t) { *o = cxd{-1.0, 0.0}; return; }
+    const int K = dc.K;
+    const size_t NN = (size_t)g.N * g.N;
+    const cxd* el = ell + (size_t)c * dc.P;
+    double amax, iden;
+    pair_scale(dc, el, amax, iden);
+    const double* As = dc.Ap + (size_t)s * 4;
+    const double* At = dc.Ap + (size_t)t * 4;
+    cxd acc = {0.0, 0.0};
+    for (int p = 0; p < dc.P; ++p) {
+        const bool cplx = p >= K;
+        const cxd E = dc.w[p] * pair_norm(dc, el, p, amax, iden);
+        cxd Xss[2][2], Xtt[2][2], Xst[2][2];
+        if (cplx) {
+            const CW* W = Wc + ((size_t)c * dc.Kc + (p - K)) * NN;
+            coupled_block<CW, BW>(dc, W, s, s, Xss);
+            coupled_block<CW, BW>(dc, W, t, t, Xtt);
+            coupled_block<CW, BW>(dc, W, s, t, Xst);
+        } else {
+            const RW* W = Wr + ((size_t)c * K + p) * NN;
+            coupled_block<RW, BW>(dc, W, s, s, Xss);
+            coupled_block<RW, BW>(dc, W, t, t, Xtt);
+            coupled_block<RW, BW>(dc, W, s, t, Xst);
+        }
+        // both orders of a complex pair: (n, m) with E / 2 and X, (m, n) with
+        // conj(E) / 2 and conj(X); a diagonal pair once with E
+        for (int ord = 0; ord < (cplx ? 2 : 1); ++ord) {
+            auto cj = [&](cxd v) { return ord ? conjg(v) : v; };
+            const cxd g01 = cj(Xss[0][1]) + cxd{As[1], 0.0};
+            const cxd g23 = cj(Xtt[0][1]) + cxd{At[1], 0.0};
+            const cxd g02 = cj(Xst[0][0]), g03 = cj(Xst[0][1]), g12 = cj(Xst[1][0]), g13 = cj(Xst[1][1]);
+            const cxd pf = g01 * g23 - g02 * g13 + g03 * g12;
+            const cxd wgt = cplx ? (ord ? 0.5 * conjg(E) : 0.5 * E) : E;
+            acc -= wgt * pf;
+        }
+    }
+    *o = acc;
+}
+
 // ---- score of the site blocks ------------------------------------------------
 // d log N(G) / d D_s[i][j] of chain c and site s into out[c][s][i][j] (B x B,
 // FP64, entries treated as independent).  For pure site states

@@ -34,9 +34,43 @@ __global__ void __launch_bounds__(FTHREADS) fermion_kernel(DevConst dc, int n_ch
     fermion_item<RW, CW, BW>(dc, c, it, Wr, Wc, ell, site_out, link_out, pair_site, pair_link);
 }
 
+// One thread per (chain, link).
+template <class RW, class CW, int BW>
+__global__ void __launch_bounds__(FTHREADS) fermion4_kernel(DevConst dc, int n_chains, int blocks_per_chain,
+                                                            const RW* Wr, const CW* Wc, const cxd* ell, cxd* out) {
+    const int c = blockIdx.x / blocks_per_chain;
+    const int l = (blockIdx.x - c * blocks_per_chain) * FTHREADS + threadIdx.x;
+    if (c >= n_chains || l >= dc.g.n_links) return;
+    fermion4_item<RW, CW, BW>(dc, c, l, Wr, Wc, ell, out);
+}
+
 }  // namespace
 
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
+
+// <c_2s c_2s+1 c_2t c_2t+1> of every chain and link into d_out [n][n_links] (device).
+ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    GGF_TRY(ggf_flush(ctx, st));
+    const int bpc = (g.n_links + FTHREADS - 1) / FTHREADS;
+    const long long blocks = (long long)bpc * ch.n;
+    if (blocks > 0x7fffffffLL) return ggf_fail(ctx, GGF_EINVAL, "too many chains for one launch");
+    const bool fp64 = ch.opts.precision == GGF_FP64;
+#define GGF_F4(RW, CW, BW)                                                                                 \
+    fermion4_kernel<RW, CW, BW><<<(unsigned)blocks, FTHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, (const RW*)ch.Wr, \
+                                                                       (const CW*)ch.Wc, ch.ell, d_out)
+    if (g.B == 8) {
+        if (fp64) GGF_F4(double, cxd, 8); else GGF_F4(float, cxf, 8);
+    } else if (g.B == 16) {
+        if (fp64) GGF_F4(double, cxd, 16); else GGF_F4(float, cxf, 16);
+    } else {
+        return ggf_fail(ctx, GGF_EINVAL, "n_v must be 1 or 2");
+    }
+#undef GGF_F4
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}
 
 // Site and link bilinears of every chain into d_site [n][V] and d_link
 // [n][n_links][2][2], and their per-pair parts into d_pair_site [n][V][K][K]

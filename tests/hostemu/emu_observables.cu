@@ -101,6 +101,17 @@ void emu_score(int L, int group, int n_v, const int* q, int K, const double* log
         for (int s = 0; s < dc.g.V; ++s) score_item<double, cxd>(dc, c, s, Wr, (const cxd*)Wc, (const cxd*)ell, out);
 }
 
+void emu_fermion4(int L, int group, int n_v, const int* q, int K, const double* D, const double* Ap,
+                  const double* Bp, const double* Gr, const double* Gc, const double* logc, const double* w,
+                  int n_chains, const double* Wr, const double* Wc, const double* ell, double* out) {
+    DevConst dc = make_dc(L, group, n_v, q, K, D, Ap, Bp, Gr, Gc, logc, w);
+    for (int c = 0; c < n_chains; ++c)
+        for (int l = 0; l < dc.g.n_links; ++l) {
+            if (dc.g.B == 8) fermion4_item<double, cxd, 8>(dc, c, l, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out);
+            else fermion4_item<double, cxd, 16>(dc, c, l, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out);
+        }
+}
+
 void emu_pair_norm(int L, int group, int n_v, const int* q, int K, const double* logc, const double* w,
                    int n_chains, const double* ell, double* out) {
     DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, logc, w);

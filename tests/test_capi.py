@@ -19,7 +19,7 @@ def lib():
 
 def declared_symbols():
     txt = open(os.path.join(ROOT, "include", "ggf.h")).read()
-    return sorted(set(re.findall(r"\b(ggf_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(ggf_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_symbols_exported(lib):

@@ -239,3 +239,18 @@ def test_score_items_match_oracle(emu, L, grp, n_v, K):
     for c in range(2):
         ref = variational.score_sites(p, links[c])
         assert np.abs(out[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", [(3, gi.Z2, 1, 3), (2, gi.U1, 2, 2), (3, gi.U1, 1, 2), (1, gi.Z2, 1, 2)])
+def test_fermion4_items_match_oracle(emu, L, grp, n_v, K):
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=18)
+    lay = Layout(p, links)
+    out = np.zeros((2, p.n_links, 2))
+    emu.emu_fermion4(*lay.common(), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell), _ptr(out))
+    fe = fermionic.Fermionic(p)
+    for c in range(2):
+        for l in range(p.n_links):
+            s_, t_ = fermionic._link_sites(p, l)
+            want = -1.0 if s_ == t_ else fe.monomial(links[c], (2 * s_, 2 * s_ + 1, 2 * t_, 2 * t_ + 1))
+            assert abs(_c(out)[c, l] - want) <= 1e-11

@@ -262,3 +262,29 @@ def test_wilson_gradient_estimate_matches_exact():
     ests = np.array(ests)
     se = ests.std(ddof=1) / np.sqrt(len(ests))
     assert abs(ests.mean() - exact) <= max(5 * se, 0.2 * abs(exact))
+
+
+@pytest.mark.parametrize("L,grp,n_v,K,prec,tol", [
+    (3, gi.Z2, 1, 3, 0, 1e-10),
+    (2, gi.U1, 2, 2, 0, 1e-10),
+    (4, gi.U1, 1, 2, 1, 1e-4),
+])
+def test_four_point_matches_oracle(L, grp, n_v, K, prec, tol):
+    """<c_2s c_2s+1 c_2t c_2t+1> per link against the oracle's monomial, and
+    the density-density correlation it gives lies in [0, 1] (n_s n_t is a
+    projector)."""
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=91)
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=prec, seed=4)
+    f4 = ctx.chains_fermion4()
+    site, _ = ctx.chains_fermion()
+    ctx.close()
+    fe = fermionic.Fermionic(p)
+    for c in range(2):
+        for l in range(p.n_links):
+            s_, t_ = fermionic._link_sites(p, l)
+            want = fe.monomial(links[c], (2 * s_, 2 * s_ + 1, 2 * t_, 2 * t_ + 1))
+            assert abs(f4[c, l] - want) <= tol
+            nn = (1 + 1j * site[c, s_] + 1j * site[c, t_] - f4[c, l]) / 4
+            assert abs(nn.imag) <= 1e-6 and -1e-6 <= nn.real <= 1 + 1e-6
