@@ -112,6 +112,22 @@ void emu_fermion4(int L, int group, int n_v, const int* q, int K, const double* 
         }
 }
 
+// Mean SU(2) plaquette of one configuration (links [2V][4]) on an L x L lattice,
+// with the link order of the plaquette kernels.
+double emu_plaquette_su2(int L, const double* links) {
+    Geometry g{};
+    g.L = L; g.V = L * L; g.n_links = 2 * g.V;
+    double acc = 0.0;
+    for (int s = 0; s < g.V; ++s) {
+        int x = s % L, y = s / L;
+        int sx = y * L + (x + 1) % L, sy = ((y + 1) % L) * L + x;
+        int l1 = 2 * s, l2 = 2 * sx + 1, l3 = 2 * sy, l4 = 2 * s + 1;
+        acc += plaquette_su2(link_quat(g, links, 0, l1), link_quat(g, links, 0, l2), link_quat(g, links, 0, l3),
+                             link_quat(g, links, 0, l4));
+    }
+    return acc / g.V;
+}
+
 void emu_pair_norm(int L, int group, int n_v, const int* q, int K, const double* logc, const double* w,
                    int n_chains, const double* ell, double* out) {
     DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, logc, w);

@@ -254,3 +254,14 @@ def test_fermion4_items_match_oracle(emu, L, grp, n_v, K):
             s_, t_ = fermionic._link_sites(p, l)
             want = -1.0 if s_ == t_ else fe.monomial(links[c], (2 * s_, 2 * s_ + 1, 2 * t_, 2 * t_ + 1))
             assert abs(_c(out)[c, l] - want) <= 1e-11
+
+
+def test_su2_plaquette_matches_oracle(emu):
+    from oracle.observables import plaquette_mean
+    emu.emu_plaquette_su2.restype = ctypes.c_double
+    for L in (1, 2, 3):
+        p = gi.make_problem(L, gi.SU2, 2, 1)
+        for G in gi.random_links(p, 3, seed=19):
+            G = np.ascontiguousarray(G)
+            got = emu.emu_plaquette_su2(ctypes.c_int(L), _ptr(G))
+            assert abs(got - plaquette_mean(gi.SU2, L, G)[0]) <= 1e-14
