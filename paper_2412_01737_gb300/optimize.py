@@ -16,7 +16,7 @@ current lambda and estimates Hbar and Nbar for an energy
 
 (any coefficient may be omitted); the couplings, and thus the Hamiltonian,
 are the caller's.  ``linear_method`` solves for the new lambda, which
-``GGF.init_gaussians`` takes for the next round of sampling.
+``GGF.init_gaussians`` takes before sampling again.
 
 ``wilson_score`` gives the gradient of a Wilson-loop energy with respect to
 the site blocks, as the covariance of the plaquette with the score
