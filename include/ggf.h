@@ -237,6 +237,20 @@ ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream)
  *   before ggf_chains_init. */
 ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem, void* stream);
 
+/* Score of the link blocks, per pair: out[c][p][l] = (w_p N_p / N(G))
+ * (1/2) (O_l^T W_p[l, l] O_l)^T (r x r complex), w_p the pair weight
+ * (|lambda_n|^2, or 2 lambda_n^* lambda_m for n < m), W_p[l, l] the block of
+ * the pair's inverse on link l's r Majoranas and O_l the link's twist.  Since
+ * N_p = c_p Pf(D + O Gamma_X^p O^T),
+ *   d log N(G) = Re sum_p sum_l tr(U_p[l]^T dGamma_X^p[l]) + Re sum_p (w_p N_p / N(G)) d log c_p;
+ * for K = 1 (Gamma_X = Gamma_B, c constant) this is the gradient with respect
+ * to the bond covariances; for K > 1 the caller chains through the
+ * transition covariances Gamma_X^nm and the pair constants.  Pending delayed
+ * updates are folded into W first.
+ *   out [n_chains][P][2V][r][r][2] FP64 (re, im), caller-owned.  GGF_EINVAL
+ *   for a null `out`, GGF_ESTATE before ggf_chains_init. */
+ggf_status ggf_chains_link_score(ggf_ctx* ctx, double* out, int mem, void* stream);
+
 /* Nearest-neighbour four-point function (Sec. 5.2, a weight-four Majorana
  * monomial): out[c][l] = sum_nm lambda_n^* lambda_m
  * <psi_n|c_2s c_2s+1 c_2t c_2t+1|psi_m> / N(G) for link l = (s -> t), by

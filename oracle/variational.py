@@ -23,11 +23,12 @@ configuration the local matrices are returned in that normalised form
 
 Also the score d log N(G) / d D_s of the site blocks (score_sites), which
 gives exact gradients of Wilson-loop energies with respect to the site
-parameters: dE = E_p[(W(G) - E) sum_s tr(S_s^T dD_s)].
+parameters: dE = E_p[(W(G) - E) sum_s tr(S_s^T dD_s)], and its counterpart
+for the link blocks of every pair (score_links; for K = 1 the bond gradient).
 
-Pinned (tests/test_oracle_variational.py): the score against central finite
-differences of log N(G) along commutant generators of the site states (Z2,
-U(1), SU(2)); on the 2x2 Z2 lattice, for random lambda, the Hermitian forms
+Pinned (tests/test_oracle_variational.py): the site and (K = 1) link scores
+against central finite differences of log N(G) along commutant generators of
+the site and bond states (Z2, U(1), SU(2)); on the 2x2 Z2 lattice, for random lambda, the Hermitian forms
 built from exhaustive sums reproduce the direct exhaustive expectations of
 the plaquette, the link flip and the densities computed with that lambda; the generalised eigenvector minimises the energy
 over random lambda; the forms are Hermitian and Nbar positive definite.
@@ -142,6 +143,41 @@ def score_sites(p, links) -> np.ndarray:
             for s in range(p.V):
                 S[s] += (wt * 0.5 * Wnm[s * B:(s + 1) * B, s * B:(s + 1) * B].T).real
     return S
+
+
+def score_links(p, links) -> np.ndarray:
+    """Per pair p (diagonal pairs, then n < m) and link l, the r x r complex
+    block U_p[l] = (w_p N_p / N(G)) (1/2) (O_l^T W_p[l, l] O_l)^T, with w_p the
+    pair weight (|lambda_n|^2, or 2 lambda_n^* lambda_m), N_p = N_nm(G),
+    W_p[l, l] the block of (D + O Gamma_X^p O^T)^{-1} on the link's r
+    Majoranas and O_l the link's twist.  Since d log Pf(M) = (1/2) tr(W dM),
+        d log N(G) = Re sum_p sum_l tr(U_p[l]^T dGamma_X^p[l])
+                     + Re sum_p (w_p N_p / N(G)) d log c_p,
+    c_p the pair's G-independent constant (for K = 1 the second term
+    vanishes and Gamma_X = Gamma_B, so this is the bond gradient)."""
+    W = weight.Weights(p)
+    lnm = W.log_n_matrix(links)
+    logN = weight.combine(lnm, p.lam)
+    B = 8 * p.n_v
+    virt = np.array([i for i in range(p.m_s * p.V) if i % p.m_s >= 2])
+    pos = -np.ones(p.m_s * p.V, dtype=int)
+    pos[virt] = np.arange(virt.size)
+    idx = [pos[np.array(ix)] for ix in weight.link_majoranas(p)]
+    Ov = weight.twist_matrix(p, links)[np.ix_(virt, virt)]
+    D = np.zeros((B * p.V, B * p.V))
+    for s in range(p.V):
+        D[s * B:(s + 1) * B, s * B:(s + 1) * B] = p.gamma_site[s][2:, 2:]
+    pairs = [(n, n) for n in range(p.K)] + [(n, m) for n in range(p.K) for m in range(n + 1, p.K)]
+    out = np.zeros((len(pairs), p.n_links, p.r, p.r), dtype=complex)
+    for k, (n, m) in enumerate(pairs):
+        Wnm = np.linalg.inv(D + Ov @ W.GX[n, m][np.ix_(virt, virt)] @ Ov.T)
+        wp = abs(p.lam[n]) ** 2 if n == m else 2 * np.conj(p.lam[n]) * p.lam[m]
+        f = wp * np.exp(lnm[n, m] - logN)
+        for l in range(p.n_links):
+            ii = idx[l]
+            Ol = Ov[np.ix_(ii, ii)]
+            out[k, l] = f * 0.5 * (Ol.T @ Wnm[np.ix_(ii, ii)] @ Ol).T
+    return out
 
 
 def with_lambda(p, lam):

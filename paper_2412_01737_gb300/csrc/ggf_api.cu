@@ -24,6 +24,7 @@ ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cxd* d_pair_site,
 ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 ggf_status ggf_score(ggf_ctx* ctx, double* d_out, cudaStream_t st);
 ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
+ggf_status ggf_link_score(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -845,6 +846,24 @@ ggf_status ggf_chains_fermion4(ggf_ctx* ctx, double* out, int mem, void* stream)
         return check_err_word(ctx);
     }
     GGF_TRY(ggf_fermion4(ctx, (cxd*)out, st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_link_score(ggf_ctx* ctx, double* out, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!out) return ggf_fail(ctx, GGF_EINVAL, "null out");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)ctx->ch.n * ctx->P * ctx->g.n_links * ctx->g.r * ctx->g.r * sizeof(cxd);
+    if (mem == GGF_MEM_HOST) {
+        DBuf d;
+        GGF_TRY(dalloc(ctx, d, bytes));
+        GGF_TRY(ggf_link_score(ctx, (cxd*)d.p, st));
+        GGF_CK(cudaMemcpyAsync(out, d.p, bytes, cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return check_err_word(ctx);
+    }
+    GGF_TRY(ggf_link_score(ctx, (cxd*)out, st));
     return GGF_OK;
 }
 

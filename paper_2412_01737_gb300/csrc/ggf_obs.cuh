@@ -383,4 +383,72 @@ __host__ __device__ void score_item(const DevConst& dc, int c, int s, const RW* 
     }
 }
 
+// ---- score of the link blocks ------------------------------------------------
+// Pair p, link l of chain c: out[c][p][l] (R x R complex, R = r) =
+// (w_p N_p / N(G)) (1/2) (O_l^T W_p[l, l] O_l)^T with W_p[l, l] the block of the
+// pair's inverse on the link's Majoranas and O_l the link's twist, so that
+// d log N(G) = Re sum_p sum_l tr(U_p[l]^T dGamma_X^p[l]) + the pair constants'
+// terms (none for K = 1, where this is the gradient for the bond blocks).
+template <class RW, class CW, int R>
+__host__ __device__ void link_score_item(const DevConst& dc, int c, int p, int l, const void* links, const RW* Wr,
+                                         const CW* Wc, const cxd* ell, cxd* out) {
+    const Geometry& g = dc.g;
+    const size_t NN = (size_t)g.N * g.N;
+    const cxd* el = ell + (size_t)c * dc.P;
+    double amax, iden;
+    pair_scale(dc, el, amax, iden);
+    const cxd f = 0.5 * (dc.w[p] * pair_norm(dc, el, p, amax, iden));
+    // the link's twist O (rows), source end positions 0 .. h2 - 1
+    double O[R][R];
+    for (int x = 0; x < R; ++x)
+        for (int y = 0; y < R; ++y) O[x][y] = 0.0;
+    if (g.group == GGF_SU2) {
+        double Rq[16];
+        doublet_rotation(link_quat(g, links, c, l), Rq);
+        for (int x = 0; x < R; ++x) {
+            if (x < 4)
+                for (int a = 0; a < 4; ++a) O[x][a] = Rq[x * 4 + a];
+            else
+                O[x][x] = 1.0;
+        }
+    } else {
+        double gval, theta;
+        link_value<double>(dc, links, c, l, gval, theta);
+        for (int x = 0; x < R; ++x) {
+            double cs = 1.0, sn = 0.0;
+            if (g.group == GGF_U1 && x < g.h2) {
+                cs = cos(g.q[x >> 1] * theta);
+                sn = sin(g.q[x >> 1] * theta);
+            }
+            int i0, i1;
+            double c0, c1;
+            twist_row(g, x, gval, cs, sn, i0, c0, i1, c1);
+            O[x][i0] += c0;
+            if (i1 != i0) O[x][i1] += c1;
+        }
+    }
+    int a0, b0;
+    link_ends(g, l, a0, b0);
+    cxd Wl[R][R];
+    for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b) {
+            const size_t off = (size_t)link_majorana(g, a0, b0, a) * g.N + link_majorana(g, a0, b0, b);
+            Wl[a][b] = p < dc.K ? Sc<RW>::to(Wr[((size_t)c * dc.K + p) * NN + off])
+                                : Sc<CW>::to(Wc[((size_t)c * dc.Kc + (p - dc.K)) * NN + off]);
+        }
+    cxd* o = out + (((size_t)c * dc.P + p) * g.n_links + l) * R * R;
+    for (int x = 0; x < R; ++x)
+        for (int y = 0; y < R; ++y) {
+            // (O^T W O)[y][x] = sum_ab O[a][y] W[a][b] O[b][x]
+            cxd v = {0.0, 0.0};
+            for (int a = 0; a < R; ++a) {
+                if (O[a][y] == 0.0) continue;
+                cxd t = {0.0, 0.0};
+                for (int b = 0; b < R; ++b) t += O[b][x] * Wl[a][b];
+                v += O[a][y] * t;
+            }
+            o[x * R + y] = f * v;
+        }
+}
+
 }  // namespace

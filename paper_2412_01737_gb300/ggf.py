@@ -50,7 +50,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
-           "ggf_chains_fermion4",
+           "ggf_chains_fermion4", "ggf_chains_link_score",
            "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
@@ -92,6 +92,7 @@ def load():
         "ggf_chains_pairs": ([P, I, P, I, P], I),
         "ggf_chains_score": ([P, P, I, P], I),
         "ggf_chains_fermion4": ([P, P, I, P], I),
+        "ggf_chains_link_score": ([P, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -316,6 +317,18 @@ class GGF:
             self._ck(self.lib.ggf_chains_pairs(self.h, int(what), host.ctypes.data, MEM_HOST, None))
             return host[..., 0] + 1j * host[..., 1]
         self._ck(self.lib.ggf_chains_pairs(self.h, int(what), _ptr(out)[0], self._mem(out), _stream([out])))
+        return out
+
+    def chains_link_score(self, out=None):
+        """Per-pair link-block scores (n_chains, P, 2V, r, r) complex (see
+        ggf_chains_link_score), or fills `out` (float64 with a trailing 2)."""
+        if out is None:
+            P = self.K * (self.K + 1) // 2
+            r = 4 * self.n_v
+            host = np.zeros((self.n_chains, P, self.n_links(), r, r, 2))
+            self._ck(self.lib.ggf_chains_link_score(self.h, host.ctypes.data, MEM_HOST, None))
+            return host[..., 0] + 1j * host[..., 1]
+        self._ck(self.lib.ggf_chains_link_score(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
         return out
 
     def chains_fermion4(self, out=None):

@@ -20,9 +20,10 @@ are the caller's.  ``linear_method`` solves for the new lambda, which
 
 ``wilson_score`` gives the gradient of a Wilson-loop energy with respect to
 the site blocks, as the covariance of the plaquette with the score
-d log N(G) / d D_s (``GGF.chains_score``); gradients of the electric and
-fermionic terms would also need the derivatives of their per-pair parts and
-are not provided.
+d log N(G) / d D_s (``GGF.chains_score``); ``wilson_link_score`` does the same
+for the link blocks (for K = 1 the bond covariances).  Gradients of the
+electric and fermionic terms would also need the derivatives of their
+per-pair parts and are not provided.
 """
 from __future__ import annotations
 
@@ -86,6 +87,24 @@ def wilson_score(ctx, n_sweeps: int):
         n += w.shape[0]
     mw = sw / n
     return mw, sws / n - mw * ss / n
+
+
+def wilson_link_score(ctx, n_sweeps: int):
+    """As wilson_score for the link blocks: (<W>, C) with
+    C = E_p[(W(G) - <W>) U(G)] (P, 2V, r, r complex), U the per-pair link
+    scores of GGF.chains_link_score.  For K = 1 a change dGamma_B[l] of the
+    bond blocks changes <W> by Re sum_l tr(C[0, l]^T dGamma_B[l])."""
+    sw, su, swu, n = 0.0, 0.0, 0.0, 0
+    for _ in range(n_sweeps):
+        obs = ctx.sample(1)
+        U = ctx.chains_link_score()
+        w = obs[0, :, 0]
+        sw = sw + w.sum()
+        su = su + U.sum(axis=0)
+        swu = swu + np.einsum("c,cplij->plij", w, U)
+        n += w.shape[0]
+    mw = sw / n
+    return mw, swu / n - mw * su / n
 
 
 def linear_method(Hbar: np.ndarray, Nbar: np.ndarray):

@@ -128,6 +128,20 @@ double emu_plaquette_su2(int L, const double* links) {
     return acc / g.V;
 }
 
+void emu_link_score(int L, int group, int n_v, const int* q, int K, const double* D, const double* Gr,
+                    const double* Gc, const double* logc, const double* w, int n_chains, const void* links,
+                    const double* Wr, const double* Wc, const double* ell, double* out) {
+    DevConst dc = make_dc(L, group, n_v, q, K, D, nullptr, nullptr, Gr, Gc, logc, w);
+    for (int c = 0; c < n_chains; ++c)
+        for (int p = 0; p < dc.P; ++p)
+            for (int l = 0; l < dc.g.n_links; ++l) {
+                if (dc.g.r == 4)
+                    link_score_item<double, cxd, 4>(dc, c, p, l, links, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out);
+                else
+                    link_score_item<double, cxd, 8>(dc, c, p, l, links, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out);
+            }
+}
+
 void emu_pair_norm(int L, int group, int n_v, const int* q, int K, const double* logc, const double* w,
                    int n_chains, const double* ell, double* out) {
     DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, logc, w);

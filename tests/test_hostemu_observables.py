@@ -265,3 +265,18 @@ def test_su2_plaquette_matches_oracle(emu):
             G = np.ascontiguousarray(G)
             got = emu.emu_plaquette_su2(ctypes.c_int(L), _ptr(G))
             assert abs(got - plaquette_mean(gi.SU2, L, G)[0]) <= 1e-14
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", [(2, gi.Z2, 1, 2), (2, gi.U1, 2, 3), (3, gi.U1, 1, 2), (2, gi.SU2, 2, 2)])
+def test_link_score_items_match_oracle(emu, L, grp, n_v, K):
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=20)
+    lay = Layout(p, links)
+    P = K * (K + 1) // 2
+    out = np.zeros((2, P, p.n_links, p.r, p.r, 2))
+    emu.emu_link_score(ctypes.c_int(p.L), ctypes.c_int(p.group), ctypes.c_int(p.n_v), _ptr(lay.q), ctypes.c_int(K),
+                       _ptr(lay.D), _ptr(lay.Gr), _ptr(lay.Gc), _ptr(lay.logc), _ptr(lay.w), ctypes.c_int(2),
+                       _ptr(lay.links), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell), _ptr(out))
+    for c in range(2):
+        ref = variational.score_links(p, links[c])
+        assert np.abs(_c(out)[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())

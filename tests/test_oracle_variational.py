@@ -155,3 +155,32 @@ def test_wilson_energy_gradient_is_a_covariance_with_the_score():
     an = np.sum(w * (pl - mw) * dlog)
     assert abs(an) > 1e-3
     assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
+
+
+@pytest.mark.parametrize("grp,n_v", [(gi.Z2, 1), (gi.U1, 1), (gi.U1, 2), (gi.SU2, 2)])
+def test_link_score_matches_finite_differences_k1(grp, n_v):
+    """K = 1: d log N(G) along a rotation of every link's bond state by a
+    generator of the bond commutant equals Re sum_l tr(U[l]^T dGamma_B[l])."""
+    import dataclasses
+    import scipy.linalg
+    p = gi.make_problem(2, grp, n_v, 1, bond_scale=0.3)
+    links = gi.random_links(p, 1, seed=5)[0]
+    U = va.score_links(p, links)[0]
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(p.r, p.r))
+    A = A - A.T
+    if grp == gi.U1:
+        A = gi._project_commutant(A, np.concatenate([p.q_src, -p.q_src]))
+    elif grp == gi.SU2:
+        A = gi._project_commutant_su2(A, gi._su2_generators(gi._bond_slots_su2(p.n_v)))
+
+    def log_n(eps):
+        O = scipy.linalg.expm(eps * A)
+        gb = np.einsum("ij,nljk,mk->nlim", O, p.gamma_bond, O)
+        return weight.Weights(dataclasses.replace(p, gamma_bond=gb)).log_norm(links)
+
+    h = 1e-5
+    fd = (log_n(h) - log_n(-h)) / (2 * h)
+    an = sum(np.sum(U[l] * (A @ p.gamma_bond[0, l] - p.gamma_bond[0, l] @ A)).real for l in range(p.n_links))
+    assert abs(an) > 1e-3
+    assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))

@@ -288,3 +288,21 @@ def test_four_point_matches_oracle(L, grp, n_v, K, prec, tol):
             assert abs(f4[c, l] - want) <= tol
             nn = (1 + 1j * site[c, s_] + 1j * site[c, t_] - f4[c, l]) / 4
             assert abs(nn.imag) <= 1e-6 and -1e-6 <= nn.real <= 1 + 1e-6
+
+
+@pytest.mark.parametrize("L,grp,n_v,K,prec,tol", [
+    (2, gi.U1, 2, 2, 0, 1e-10),
+    (3, gi.Z2, 1, 3, 0, 1e-10),
+    (4, gi.U1, 1, 2, 1, 1e-4),
+])
+def test_link_score_matches_oracle(L, grp, n_v, K, prec, tol):
+    from oracle import variational
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=95)
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=prec, seed=6)
+    U = ctx.chains_link_score()
+    ctx.close()
+    for c in range(2):
+        ref = variational.score_links(p, links[c])
+        assert np.abs(U[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
