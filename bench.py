@@ -529,9 +529,12 @@ def observable_bytes(p, prec):
 
 
 def run_observables(args):
-    """Time the per-configuration observables of Secs. 5.2 and 5.3 on the
-    workload's chains (not part of the sampling step): K calls each after W
-    warm-up calls, CUDA events on the launching stream, device buffers."""
+    """Time the per-configuration observables of Secs. 5.2 and 5.3 and the
+    derivatives built from the chains' inverses on the workload's chains (not
+    part of the sampling step): K calls each after W warm-up calls, CUDA events
+    on the launching stream, device buffers; bytes are the W elements each
+    call reads (fermion4 reads three site-pair blocks per link and pair, the
+    site score the diagonal site blocks, the link score the link blocks)."""
     import torch
     import ggf_inputs as gi
     from paper_2412_01737_gb300 import GGF
@@ -543,12 +546,29 @@ def run_observables(args):
     ctx.chains_init(gi.random_links(p, chains, seed=BASE_SEED), precision=prec, refresh_every=refresh,
                     seed=BASE_SEED, delay=delay)
     ctx.sample(1 + args.burn)
-    el = torch.zeros((chains, p.n_links, 2), dtype=torch.float64, device="cuda")
-    fs = torch.zeros((chains, p.V, 2), dtype=torch.float64, device="cuda")
-    fl = torch.zeros((chains, p.n_links, 2, 2, 2), dtype=torch.float64, device="cuda")
+    from paper_2412_01737_gb300.ggf import PAIRS_ELECTRIC
+    dev = dict(dtype=torch.float64, device="cuda")
+    P, B, r = p.K * (p.K + 1) // 2, 8 * p.n_v, 4 * p.n_v
+    el = torch.zeros((chains, p.n_links, 2), **dev)
+    fs = torch.zeros((chains, p.V, 2), **dev)
+    fl = torch.zeros((chains, p.n_links, 2, 2, 2), **dev)
+    f4 = torch.zeros((chains, p.n_links, 2), **dev)
+    ep = torch.zeros((chains, p.n_links, p.K, p.K, 2), **dev)
+    sc = torch.zeros((chains, p.V, B, B), **dev)
+    ls = torch.zeros((chains, P, p.n_links, r, r, 2), **dev)
     calls = {"electric": lambda: ctx.chains_electric(out=el),
-             "fermion": lambda: ctx.chains_fermion(site=fs, link=fl)}
+             "fermion": lambda: ctx.chains_fermion(site=fs, link=fl),
+             "fermion4": lambda: ctx.chains_fermion4(out=f4),
+             "electric_pairs": lambda: ctx.chains_pairs(PAIRS_ELECTRIC, out=ep),
+             "site_score": lambda: ctx.chains_score(out=sc),
+             "link_score": lambda: ctx.chains_link_score(out=ls)}
     eb, fb = observable_bytes(p, prec)
+    esz = 8 if prec == 0 else 4
+    per_pair = p.K * esz + p.K * (p.K - 1) // 2 * 2 * esz
+    read_bytes = {"electric": eb, "electric_pairs": eb, "fermion": fb,
+                  "fermion4": p.n_links * 3 * B * B * per_pair,
+                  "site_score": p.V * B * B * per_pair,
+                  "link_score": p.n_links * r * r * per_pair}
     peak = load_peaks().get("hbm_gbs")
     out = {"metric": "observable_kernel_time", "unit": "ms per call (all chains)", "workload": args.workload,
            "config": {"workload": label, "chains": chains}, "steps": args.steps, "warmup": args.warmup}
@@ -564,7 +584,7 @@ def run_observables(args):
         t1.record(stream)
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1) / args.steps
-        byts = (eb if name == "electric" else fb) * chains
+        byts = read_bytes[name] * chains
         gbs = byts / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "bytes": byts, "achieved_gbs": gbs, "peak_gbs": peak,
                      "frac": gbs / peak if peak else None, "bound": "latency (scattered small blocks)"}
