@@ -539,8 +539,8 @@ def run_observables(args):
     import ggf_inputs as gi
     from paper_2412_01737_gb300 import GGF
     p, chains, prec, refresh, delay, label = problem_for(args.workload)
-    if args.chains:
-        chains = args.chains
+    # the output buffers come on top of the inverses: 64 chains unless asked
+    chains = args.chains or min(chains, 64)
     ctx = GGF(0)
     ctx.init_problem(p)
     ctx.chains_init(gi.random_links(p, chains, seed=BASE_SEED), precision=prec, refresh_every=refresh,
