@@ -137,6 +137,23 @@ ggf_status ggf_logweight_noalloc(ggf_ctx* ctx, int n_cfg, const void* links, dou
 ggf_status ggf_observable(ggf_ctx* ctx, int which, int n_cfg, const void* links,
                           double* out, int mem, void* stream);
 
+/* Wilson loops from links alone (Sec. 5.1: oriented products of link
+ * operators along closed paths, diagonal in G): out[n_cfg] = mean over the V
+ * lower-left corners of the trace of the oriented product around the R x T
+ * rectangle (R steps +x, T steps +y, back along -x and -y; 1 <= R, T <= L;
+ * R = T = 1 is the plaquette).  A forward step contributes the covariant
+ * link matrix (Z2 g; U(1) e^{i theta}, real part of the product; SU(2)
+ * u^dag), a backward step its inverse; SU(2) takes (1/2) tr.  GGF_EINVAL for
+ * R or T outside [1, L]. */
+ggf_status ggf_wilson_loop(ggf_ctx* ctx, int R, int T, int n_cfg, const void* links, double* out, int mem,
+                           void* stream);
+
+/* Loops winding once around the torus along y (Polyakov loops of the
+ * periodic lattice, closed through the boundary): out[n_cfg] = mean over the
+ * L columns x of the trace of the product of the y links at x, with the
+ * orientation rule of ggf_wilson_loop. */
+ggf_status ggf_polyakov_loop(ggf_ctx* ctx, int n_cfg, const void* links, double* out, int mem, void* stream);
+
 typedef struct {
     int precision;      /* GGF_FP64, or GGF_FP32 (inverse and updates in FP32,
                            ratios, log-weights and refresh in FP64) */

@@ -429,6 +429,38 @@ ggf_status ggf_observable(ggf_ctx* ctx, int which, int n_cfg, const void* links,
     return ggf_plaquette(ctx, n_cfg, links, out, st);
 }
 
+static ggf_status loops_entry(ggf_ctx* ctx, int R, int T, int mode, int n_cfg, const void* links, double* out, int mem,
+                       void* stream) {
+    GGF_TRY(require(ctx, false, false));
+    if (n_cfg < 0 || !links || !out) return ggf_fail(ctx, GGF_EINVAL, "bad loop arguments");
+    const Geometry& g = ctx->g;
+    if (!mode && (R < 1 || T < 1 || R > g.L || T > g.L)) return ggf_fail(ctx, GGF_EINVAL, "need 1 <= R, T <= L");
+    if (n_cfg == 0) return GGF_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mem == GGF_MEM_HOST) {
+        DBuf dl, dout;
+        const size_t lb = (size_t)n_cfg * g.n_links * link_bytes(g);
+        GGF_TRY(dalloc(ctx, dl, lb));
+        GGF_TRY(dalloc(ctx, dout, n_cfg * sizeof(double)));
+        GGF_CK(cudaMemcpyAsync(dl.p, links, lb, cudaMemcpyHostToDevice, st));
+        GGF_TRY(ggf_loops(ctx, n_cfg, R, T, mode, dl.p, (double*)dout.p, st));
+        GGF_CK(cudaMemcpyAsync(out, dout.p, n_cfg * sizeof(double), cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return GGF_OK;
+    }
+    return ggf_loops(ctx, n_cfg, R, T, mode, links, out, st);
+}
+
+ggf_status ggf_wilson_loop(ggf_ctx* ctx, int R, int T, int n_cfg, const void* links, double* out, int mem,
+                           void* stream) {
+    return loops_entry(ctx, R, T, 0, n_cfg, links, out, mem, stream);
+}
+
+ggf_status ggf_polyakov_loop(ggf_ctx* ctx, int n_cfg, const void* links, double* out, int mem, void* stream) {
+    return loops_entry(ctx, 0, 0, 1, n_cfg, links, out, mem, stream);
+}
+
 ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const ggf_chain_opts* opts, int mem,
                            void* stream) {
     GGF_TRY(require(ctx, true, false));

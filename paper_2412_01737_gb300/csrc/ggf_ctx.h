@@ -157,3 +157,6 @@ ggf_status ggf_invert_batched(ggf_ctx* ctx, bool cplx, int n, int batch, void* A
 // Combine per-config pair log-Pfaffians into log N (device, n_cfg items).
 ggf_status ggf_combine(ggf_ctx* ctx, int n_cfg, const cxd* d_ell, double* d_logN, cudaStream_t st);
 ggf_status ggf_plaquette(ggf_ctx* ctx, int n_cfg, const void* d_links, double* d_out, cudaStream_t st);
+// Mean Wilson loops (mode 0: R x T rectangles; mode 1: loops winding along y).
+ggf_status ggf_loops(ggf_ctx* ctx, int n_cfg, int R, int T, int mode, const void* d_links, double* d_out,
+                     cudaStream_t st);

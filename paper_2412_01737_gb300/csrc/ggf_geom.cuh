@@ -164,6 +164,55 @@ __host__ __device__ T twisted_su2(const DevConst& dc, int pair, int link, int x,
     return v;
 }
 
+// Trace of the oriented product of link matrices along a closed path
+// (Sec. 5.1): mode 0 the R x T rectangle with lower-left corner s (R steps +x,
+// T steps +y, R steps -x, T steps -y); mode 1 the loop winding once around
+// the torus along y at column x = s.  A forward step contributes the covariant
+// link matrix (Z2 g; U(1) e^{i theta}, real part at the end; SU(2) u^dag), a
+// backward step its inverse, multiplied in path order.
+GGF_HD double loop_value(const Geometry& g, const void* links, int cfg, int s, int R, int T, int mode) {
+    const int L = g.L, x = s % L, y = s / L;
+    const int n = mode ? L : 2 * (R + T);
+    int prod = 1;
+    double ang = 0.0;
+    double M[4] = {1.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < n; ++k) {
+        int l;
+        bool fw;
+        if (mode) {
+            l = 2 * (((y + k) % L) * L + x) + 1;
+            fw = true;
+        } else if (k < R) {
+            l = 2 * (y * L + (x + k) % L);
+            fw = true;
+        } else if (k < R + T) {
+            l = 2 * (((y + k - R) % L) * L + (x + R) % L) + 1;
+            fw = true;
+        } else if (k < 2 * R + T) {
+            l = 2 * (((y + T) % L) * L + (x + 2 * R + T - 1 - k) % L);
+            fw = false;
+        } else {
+            l = 2 * (((y + 2 * R + 2 * T - 1 - k) % L) * L + x) + 1;
+            fw = false;
+        }
+        if (g.group == GGF_Z2) {
+            prod *= ((const int8_t*)links)[(size_t)cfg * g.n_links + l];
+        } else if (g.group == GGF_U1) {
+            const double th = ((const double*)links)[(size_t)cfg * g.n_links + l];
+            ang += fw ? th : -th;
+        } else {
+            const double* q = link_quat(g, links, cfg, l);
+            const double st[4] = {q[0], fw ? -q[1] : q[1], fw ? -q[2] : q[2], fw ? -q[3] : q[3]};
+            double t[4];
+            quat_mul(M, st, t);
+            for (int i = 0; i < 4; ++i) M[i] = t[i];
+        }
+    }
+    if (g.group == GGF_Z2) return (double)prod;
+    if (g.group == GGF_U1) return cos(ang);
+    return M[0];                                     // (1/2) tr of the SU(2) product
+}
+
 // Element (i, j) of M_p(G) = D + O(G) Gamma_X^p O(G)^T for configuration cfg
 // (T = double for the diagonal pairs, cxd for the pairs n < m, indexed within
 // their family).

@@ -287,6 +287,23 @@ __global__ void plaquette_kernel(Geometry g, int n_cfg, const void* links, doubl
     if (threadIdx.x == 0) out[c] = red[0] / g.V;
 }
 
+// Mean of loop_value over the loop positions (mode 0: the V corners of R x T
+// rectangles; mode 1: the L winding loops); one block per configuration.
+__global__ void loop_kernel(Geometry g, int n_cfg, int R, int T, int mode, const void* links, double* out) {
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    const int items = mode ? g.L : g.V;
+    double acc = 0.0;
+    for (int s = threadIdx.x; s < items; s += blockDim.x) acc += loop_value(g, links, c, s, R, T, mode);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0] / items;
+}
+
 template <class T>
 ggf_status run_pfaffian(ggf_ctx* ctx, int n, int batch, T* A, cxd* logpf, cxd* phase, void* tmp,
                         cudaStream_t st) {
@@ -365,6 +382,13 @@ ggf_status ggf_invert_batched(ggf_ctx* ctx, bool cplx, int n, int batch, void* A
 ggf_status ggf_combine(ggf_ctx* ctx, int n_cfg, const cxd* d_ell, double* d_logN, cudaStream_t st) {
     if (n_cfg == 0) return GGF_OK;
     combine_kernel<<<(n_cfg + 127) / 128, 128, 0, st>>>(ctx->dc(), n_cfg, d_ell, d_logN);
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}
+
+ggf_status ggf_loops(ggf_ctx* ctx, int n_cfg, int R, int T, int mode, const void* d_links, double* d_out,
+                     cudaStream_t st) {
+    loop_kernel<<<n_cfg, 256, 0, st>>>(ctx->g, n_cfg, R, T, mode, d_links, d_out);
     GGF_CK(cudaGetLastError());
     return GGF_OK;
 }

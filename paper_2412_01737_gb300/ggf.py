@@ -50,7 +50,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_init_gaussians", "ggf_get_constants", "ggf_logweight", "ggf_observable", "ggf_chains_init",
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
-           "ggf_chains_fermion4", "ggf_chains_link_score",
+           "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
            "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
@@ -93,6 +93,8 @@ def load():
         "ggf_chains_score": ([P, P, I, P], I),
         "ggf_chains_fermion4": ([P, P, I, P], I),
         "ggf_chains_link_score": ([P, P, I, P], I),
+        "ggf_wilson_loop": ([P, I, I, I, P, P, I, P], I),
+        "ggf_polyakov_loop": ([P, I, P, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -234,6 +236,24 @@ class GGF:
         mem = self._mem(links, out)
         self._ck(self.lib.ggf_observable(self.h, which, n_cfg, _ptr(links)[0], _ptr(out)[0], mem,
                                          _stream([links, out])))
+        return out
+
+    def wilson_loop(self, links, R, T, out=None):
+        """Mean R x T Wilson loop of every configuration (Sec. 5.1)."""
+        n_cfg = int(links.shape[0])
+        if out is None:
+            out = np.zeros(n_cfg) if isinstance(links, np.ndarray) else _torch_like(links, (n_cfg,))
+        self._ck(self.lib.ggf_wilson_loop(self.h, int(R), int(T), n_cfg, _ptr(links)[0], _ptr(out)[0],
+                                          self._mem(links, out), _stream([links, out])))
+        return out
+
+    def polyakov_loop(self, links, out=None):
+        """Mean loop winding along y of every configuration."""
+        n_cfg = int(links.shape[0])
+        if out is None:
+            out = np.zeros(n_cfg) if isinstance(links, np.ndarray) else _torch_like(links, (n_cfg,))
+        self._ck(self.lib.ggf_polyakov_loop(self.h, n_cfg, _ptr(links)[0], _ptr(out)[0], self._mem(links, out),
+                                            _stream([links, out])))
         return out
 
     def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202, delay=1, graph=1):

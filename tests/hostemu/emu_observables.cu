@@ -142,6 +142,15 @@ void emu_link_score(int L, int group, int n_v, const int* q, int K, const double
             }
 }
 
+// loop_value of every loop position of configuration 0 into out (mode 0: V
+// rectangles; mode 1: L winding loops).
+void emu_loops(int L, int group, const void* links, int R, int T, int mode, double* out) {
+    Geometry g{};
+    g.L = L; g.V = L * L; g.n_links = 2 * g.V; g.group = group;
+    const int items = mode ? L : g.V;
+    for (int s = 0; s < items; ++s) out[s] = loop_value(g, links, 0, s, R, T, mode);
+}
+
 void emu_pair_norm(int L, int group, int n_v, const int* q, int K, const double* logc, const double* w,
                    int n_chains, const double* ell, double* out) {
     DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, logc, w);

@@ -280,3 +280,22 @@ def test_link_score_items_match_oracle(emu, L, grp, n_v, K):
     for c in range(2):
         ref = variational.score_links(p, links[c])
         assert np.abs(_c(out)[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("grp", [gi.Z2, gi.U1, gi.SU2])
+def test_loops_match_oracle(emu, grp):
+    from oracle.observables import polyakov_values, wilson_loop_values
+    for L in (1, 3, 4):
+        p = gi.make_problem(L, grp, 2 if grp == gi.SU2 else 1, 1)
+        G = np.ascontiguousarray(gi.random_links(p, 1, seed=21)[0])
+        for R, T in ((1, 1), (1, 2), (2, 3), (L, 1), (L, L)):
+            if R > L or T > L:
+                continue
+            out = np.zeros(p.V)
+            emu.emu_loops(ctypes.c_int(L), ctypes.c_int(grp), _ptr(G), ctypes.c_int(R), ctypes.c_int(T),
+                          ctypes.c_int(0), _ptr(out))
+            assert np.abs(out - wilson_loop_values(grp, L, G, R, T)[0]).max() <= 1e-14
+        out = np.zeros(L)
+        emu.emu_loops(ctypes.c_int(L), ctypes.c_int(grp), _ptr(G), ctypes.c_int(0), ctypes.c_int(0),
+                      ctypes.c_int(1), _ptr(out))
+        assert np.abs(out - polyakov_values(grp, L, G)[0]).max() <= 1e-14

@@ -306,3 +306,18 @@ def test_link_score_matches_oracle(L, grp, n_v, K, prec, tol):
     for c in range(2):
         ref = variational.score_links(p, links[c])
         assert np.abs(U[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("grp,n_v", [(gi.Z2, 1), (gi.U1, 1), (gi.SU2, 2)])
+def test_wilson_and_polyakov_loops_match_oracle(grp, n_v):
+    from oracle.observables import polyakov_values, wilson_loop_values
+    p = gi.make_problem(4, grp, n_v, 1)
+    links = np.ascontiguousarray(gi.random_links(p, 3, seed=97))
+    ctx = ctx_for(p)
+    for R, T in ((1, 1), (2, 1), (2, 3), (4, 4)):
+        got = ctx.wilson_loop(links, R, T)
+        assert np.abs(got - wilson_loop_values(grp, 4, links, R, T).mean(axis=1)).max() <= 1e-13
+    got = ctx.polyakov_loop(links)
+    assert np.abs(got - polyakov_values(grp, 4, links).mean(axis=1)).max() <= 1e-13
+    assert np.abs(ctx.wilson_loop(links, 1, 1) - ctx.observable(links)).max() <= 1e-14
+    ctx.close()
