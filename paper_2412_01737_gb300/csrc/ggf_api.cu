@@ -331,6 +331,7 @@ ggf_status ggf_get_constants(const ggf_ctx* cctx, int* n_pairs, double* log_c, i
 
 ggf_status ggf_logweight(ggf_ctx* ctx, int n_cfg, const void* links, double* logN, double* ell, int mem,
                          void* stream) {
+    NvtxRange range("ggf_logweight");
     GGF_TRY(require(ctx, true, false));
     if (n_cfg < 0 || !links || !logN) return ggf_fail(ctx, GGF_EINVAL, "bad logweight arguments");
     if (n_cfg == 0) return GGF_OK;
@@ -463,6 +464,7 @@ ggf_status ggf_polyakov_loop(ggf_ctx* ctx, int n_cfg, const void* links, double*
 
 ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const ggf_chain_opts* opts, int mem,
                            void* stream) {
+    NvtxRange range("ggf_chains_init");
     GGF_TRY(require(ctx, true, false));
     if (n_chains < 1 || !links || !opts) return ggf_fail(ctx, GGF_EINVAL, "bad chains_init arguments");
     if (opts->precision != GGF_FP64 && opts->precision != GGF_FP32)
@@ -689,6 +691,7 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
     // the graph) so that every launch is bracketed by events
     const bool use_graph = ch.opts.graph && !ctx->prof;
     for (int s = 0; s < n_sweeps; ++s) {
+        NvtxRange range("ggf_sample sweep");
         if (use_graph) {
             GGF_TRY(ensure_graph(ctx));
             GGF_CK(cudaGraphLaunch(ch.gexec, ch.cs));
@@ -708,6 +711,7 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
 
 ggf_status ggf_sample_group(ggf_ctx* const* ctxs, int n_ctx, int n_sweeps, double* const* obs, int mem,
                             void* stream) {
+    NvtxRange range("ggf_sample_group");
     if (!ctxs || n_ctx < 1 || n_sweeps < 0) return GGF_EINVAL;
     for (int k = 0; k < n_ctx; ++k) {
         GGF_TRY(require(ctxs[k], true, true));

@@ -3,6 +3,7 @@
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include "ggf_common.cuh"
 #include "../../include/ggf.h"
 
@@ -119,6 +120,14 @@ struct ggf_ctx {
         c.D = d_D; c.Ap = d_Ap; c.Bp = d_Bp; c.Gr = d_Gr; c.Gc = d_Gc; c.logc = d_logc; c.w = d_w;
         return c;
     }
+};
+
+// NVTX range for the lifetime of a scope (a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // status helpers
