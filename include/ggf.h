@@ -314,6 +314,14 @@ ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* 
  * GGF_EINVAL for a null `out`, GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_score(ggf_ctx* ctx, double* out, int mem, void* stream);
 
+/* Fault injection for tests: write NaN into element (i, j) (real part for a
+ * complex pair) of one chain's cached inverse W_pair.  The sampler rejects a
+ * proposal whose W_SS block is not finite (ratio 0), so the chain stalls
+ * without error until a refresh rebuilds W from its links.  Synchronises the
+ * device.  GGF_EINVAL for an index out of range, GGF_ESTATE before
+ * ggf_chains_init. */
+ggf_status ggf_debug_poison_inverse(ggf_ctx* ctx, int chain, int pair, int i, int j);
+
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
  * L^2.  For tests and diagnostics. */

@@ -1,5 +1,6 @@
 // C ABI entry points of libggf (see include/ggf.h for the contract).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -918,6 +919,27 @@ ggf_status ggf_chains_score(ggf_ctx* ctx, double* out, int mem, void* stream) {
         return check_err_word(ctx);
     }
     GGF_TRY(ggf_score(ctx, out, st));
+    return GGF_OK;
+}
+
+ggf_status ggf_debug_poison_inverse(ggf_ctx* ctx, int chain, int pair, int i, int j) {
+    GGF_TRY(require(ctx, true, true));
+    Chains& ch = ctx->ch;
+    const int N = ctx->g.N;
+    if (chain < 0 || chain >= ch.n || pair < 0 || pair >= ctx->P || i < 0 || i >= N || j < 0 || j >= N)
+        return ggf_fail(ctx, GGF_EINVAL, "bad debug_poison_inverse arguments");
+    cudaSetDevice(ctx->device);
+    const bool fp64 = ch.opts.precision == GGF_FP64;
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    const bool cplx = pair >= ctx->K;
+    const size_t esz = cplx ? 2 * rsz : rsz;
+    const size_t NN = (size_t)N * N, e = (size_t)i * N + j;
+    unsigned char* base = cplx ? (unsigned char*)ch.Wc + ((size_t)chain * ctx->Kc + (pair - ctx->K)) * NN * esz
+                               : (unsigned char*)ch.Wr + ((size_t)chain * ctx->K + pair) * NN * esz;
+    const double nd = NAN;
+    const float nf = NAN;
+    GGF_CK(cudaDeviceSynchronize());
+    GGF_CK(cudaMemcpy(base + e * esz, fp64 ? (const void*)&nd : (const void*)&nf, rsz, cudaMemcpyHostToDevice));
     return GGF_OK;
 }
 

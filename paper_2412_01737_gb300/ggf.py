@@ -51,6 +51,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
            "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
+           "ggf_debug_poison_inverse",
            "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
@@ -95,6 +96,7 @@ def load():
         "ggf_chains_link_score": ([P, P, I, P], I),
         "ggf_wilson_loop": ([P, I, I, I, P, P, I, P], I),
         "ggf_polyakov_loop": ([P, I, P, P, I, P], I),
+        "ggf_debug_poison_inverse": ([P, I, I, I, I], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -376,6 +378,10 @@ class GGF:
         out = np.zeros((N, N, 2))
         self._ck(self.lib.ggf_chains_inverse(self.h, int(chain), int(pair), out.ctypes.data, MEM_HOST, None))
         return out[..., 0] + 1j * out[..., 1]
+
+    def debug_poison_inverse(self, chain, pair, i, j):
+        """Fault injection for tests: NaN into W_pair[i][j] of one chain."""
+        self._ck(self.lib.ggf_debug_poison_inverse(self.h, int(chain), int(pair), int(i), int(j)))
 
     def chains_stats(self):
         s = ChainStats()

@@ -8,3 +8,5 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libggf")
+    config.addinivalue_line("markers", "gpu_fault: fault-injection runs on a GPU, selected only explicitly "
+                                       "(-m gpu_fault), not by -m gpu")
