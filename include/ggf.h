@@ -340,6 +340,22 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out);
 /* Write / read the chain state (links, sweep counter, options, log-weights,
  * counters).  Inverses are rebuilt on resume by a full refresh, so resumed
  * chains make the same decisions as uninterrupted ones. */
+/* Chain state in memory, for residency waves (more chains than fit in HBM,
+ * paged to host memory, e.g. the Grace CPU's over NVLink-C2C): the links,
+ * cached inverses, tracked log-weights, refresh counters, drift, options and
+ * sweep counter of the context's chains, after folding pending updates.
+ * Loading a state into a context whose chains have the same problem, count,
+ * precision and delay continues those chains bit for bit (no refactorisation);
+ * the loaded options (seed, width, refresh cadence) replace the context's and
+ * the captured sweep graph is rebuilt on the next ggf_sample.
+ *   state_size: bytes of the state; save_state/load_state: dst/src of that
+ *   size, host (GGF_MEM_HOST; pinned memory copies fastest) or device memory,
+ *   caller-owned.  GGF_EINVAL for a state of another problem or shape,
+ *   GGF_ESTATE before ggf_chains_init. */
+ggf_status ggf_chains_state_size(ggf_ctx* ctx, uint64_t* bytes);
+ggf_status ggf_chains_save_state(ggf_ctx* ctx, void* dst, int mem, void* stream);
+ggf_status ggf_chains_load_state(ggf_ctx* ctx, const void* src, int mem, void* stream);
+
 ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path);
 ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
 

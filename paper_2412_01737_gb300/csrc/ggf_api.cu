@@ -993,6 +993,108 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     return GGF_OK;
 }
 
+// In-memory chain state (residency waves): header, then the device arrays.
+struct StateHeader {
+    char magic[8];
+    int geo[8];                 // L, group, n_v, K, n, P, precision, kmax
+    ggf_chain_opts opts;
+    uint64_t sweep, block_moves;
+    unsigned long long counters[6];
+};
+
+struct StatePart {
+    void* dev;
+    size_t bytes;
+};
+
+static std::vector<StatePart> state_parts(ggf_ctx* ctx) {
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    const size_t rsz = ch.opts.precision == GGF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t NN = (size_t)g.N * g.N;
+    return {{ch.links, (size_t)ch.n * g.n_links * link_bytes(g)},
+            {ch.Wr, (size_t)ch.n * ctx->K * NN * rsz},
+            {ch.Wc, (size_t)ch.n * ctx->Kc * NN * 2 * rsz},
+            {ch.ell, (size_t)ch.n * ctx->P * sizeof(cxd)},
+            {ch.since_refresh, (size_t)ch.n * sizeof(int)},
+            {ch.drift, (size_t)ch.n * sizeof(double)}};
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+ggf_status ggf_chains_state_size(ggf_ctx* ctx, uint64_t* bytes) {
+    GGF_TRY(require(ctx, true, true));
+    if (!bytes) return ggf_fail(ctx, GGF_EINVAL, "null bytes");
+    size_t total = align_up(sizeof(StateHeader));
+    for (const StatePart& q : state_parts(ctx)) total += align_up(q.bytes);
+    *bytes = total;
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_save_state(ggf_ctx* ctx, void* dst, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!dst) return ggf_fail(ctx, GGF_EINVAL, "null dst");
+    cudaSetDevice(ctx->device);
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)stream;
+    GGF_TRY(ggf_flush(ctx, st));
+    GGF_CK(cudaStreamSynchronize(st));
+    GGF_CK(cudaStreamSynchronize(ch.cs));
+    StateHeader h{};
+    std::memcpy(h.magic, "GGFSTAT1", 8);
+    const int geo[8] = {g.L, g.group, g.n_v, ctx->K, ch.n, ctx->P, ch.opts.precision, ch.kmax};
+    std::memcpy(h.geo, geo, sizeof(geo));
+    h.opts = ch.opts;
+    h.sweep = ch.sweep;
+    h.block_moves = ch.block_moves;
+    GGF_CK(cudaMemcpy(h.counters, ch.counters, sizeof(h.counters), cudaMemcpyDeviceToHost));
+    const cudaMemcpyKind down = mem == GGF_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    unsigned char* out = (unsigned char*)dst;
+    GGF_CK(cudaMemcpy(out, &h, sizeof(h), mem == GGF_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
+    size_t off = align_up(sizeof(StateHeader));
+    for (const StatePart& q : state_parts(ctx)) {
+        if (q.bytes) GGF_CK(cudaMemcpyAsync(out + off, q.dev, q.bytes, down, st));
+        off += align_up(q.bytes);
+    }
+    GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_load_state(ggf_ctx* ctx, const void* src, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!src) return ggf_fail(ctx, GGF_EINVAL, "null src");
+    cudaSetDevice(ctx->device);
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    cudaStream_t st = (cudaStream_t)stream;
+    StateHeader h;
+    GGF_CK(cudaMemcpy(&h, src, sizeof(h), mem == GGF_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost));
+    const int geo[8] = {g.L, g.group, g.n_v, ctx->K, ch.n, ctx->P, ch.opts.precision, ch.kmax};
+    if (std::memcmp(h.magic, "GGFSTAT1", 8) != 0 || std::memcmp(h.geo, geo, sizeof(geo)) != 0)
+        return ggf_fail(ctx, GGF_EINVAL, "state does not match the context's problem, chains, precision or delay");
+    GGF_CK(cudaStreamSynchronize(st));
+    GGF_CK(cudaStreamSynchronize(ch.cs));
+    const cudaMemcpyKind up = mem == GGF_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const unsigned char* in = (const unsigned char*)src;
+    size_t off = align_up(sizeof(StateHeader));
+    for (const StatePart& q : state_parts(ctx)) {
+        if (q.bytes) GGF_CK(cudaMemcpyAsync(q.dev, in + off, q.bytes, up, st));
+        off += align_up(q.bytes);
+    }
+    GGF_CK(cudaMemcpyAsync(ch.counters, h.counters, sizeof(h.counters), cudaMemcpyHostToDevice, st));
+    unsigned long long sw = h.sweep;
+    GGF_CK(cudaMemcpyAsync(ch.d_sweep, &sw, sizeof(sw), cudaMemcpyHostToDevice, st));
+    GGF_CK(cudaMemsetAsync(ch.pend, 0, (size_t)ch.n * sizeof(int), st));
+    GGF_CK(cudaStreamSynchronize(st));
+    ch.opts = h.opts;              // seed, width, refresh cadence of the saved chains
+    ch.sweep = h.sweep;
+    ch.block_moves = h.block_moves;
+    ch.steps_since_flush = 0;
+    drop_graph(ch);                // the captured sweep holds the previous options
+    return GGF_OK;
+}
+
 ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path) {
     GGF_TRY(require(ctx, true, true));
     if (!path) return ggf_fail(ctx, GGF_EINVAL, "null path");

@@ -51,7 +51,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
            "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
-           "ggf_debug_poison_inverse",
+           "ggf_debug_poison_inverse", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
            "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
@@ -97,6 +97,9 @@ def load():
         "ggf_wilson_loop": ([P, I, I, I, P, P, I, P], I),
         "ggf_polyakov_loop": ([P, I, P, P, I, P], I),
         "ggf_debug_poison_inverse": ([P, I, I, I, I], I),
+        "ggf_chains_state_size": ([P, ctypes.POINTER(ctypes.c_uint64)], I),
+        "ggf_chains_save_state": ([P, P, I, P], I),
+        "ggf_chains_load_state": ([P, P, I, P], I),
         "ggf_chains_stats": ([P, ctypes.POINTER(ChainStats)], I),
         "ggf_checkpoint": ([P, ctypes.c_char_p], I),
         "ggf_resume": ([P, ctypes.c_char_p, P], I),
@@ -387,6 +390,24 @@ class GGF:
         s = ChainStats()
         self._ck(self.lib.ggf_chains_stats(self.h, ctypes.byref(s)))
         return s
+
+    def state_size(self):
+        """Bytes of the in-memory chain state (save_state / load_state)."""
+        n = ctypes.c_uint64()
+        self._ck(self.lib.ggf_chains_state_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def save_state(self, out=None):
+        """Copy the chains' state into `out` (uint8 numpy array or CUDA/pinned
+        torch tensor of state_size() bytes; a new numpy array if None)."""
+        if out is None:
+            out = np.zeros(self.state_size(), dtype=np.uint8)
+        self._ck(self.lib.ggf_chains_save_state(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
+        return out
+
+    def load_state(self, src):
+        """Replace the chains' state by a saved one of the same problem and shape."""
+        self._ck(self.lib.ggf_chains_load_state(self.h, _ptr(src)[0], self._mem(src), _stream([src])))
 
     def checkpoint(self, path):
         self._ck(self.lib.ggf_checkpoint(self.h, str(path).encode()))

@@ -321,3 +321,44 @@ def test_wilson_and_polyakov_loops_match_oracle(grp, n_v):
     assert np.abs(got - polyakov_values(grp, 4, links).mean(axis=1)).max() <= 1e-13
     assert np.abs(ctx.wilson_loop(links, 1, 1) - ctx.observable(links)).max() <= 1e-14
     ctx.close()
+
+
+def test_state_save_load_continues_bit_exact():
+    from paper_2412_01737_gb300 import GGFError
+    p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.cold_links(p, 3), precision=1, seed=5, delay=4)
+    ctx.sample(2)
+    state = ctx.save_state()
+    a = ctx.sample(3)
+    la = ctx.chains_links()
+    ctx.load_state(state)
+    b = ctx.sample(3)
+    lb = ctx.chains_links()
+    assert np.array_equal(a, b) and np.array_equal(la, lb)
+    bad = state.copy()
+    bad[:8] = 0
+    with pytest.raises(GGFError):
+        ctx.load_state(bad)
+    ctx.close()
+
+
+def test_waves_match_separate_contexts():
+    """Two waves paged through one context reproduce two resident contexts."""
+    from paper_2412_01737_gb300.waves import Waves
+    p = gi.make_problem(3, gi.Z2, 1, 2, bond_scale=0.3)
+    starts = [gi.random_links(p, 4, seed=s) for s in (1, 2)]
+    ctx = ctx_for(p)
+    wv = Waves(ctx, starts, seed=100, precision=0, delay=4)
+    obs = wv.sample(3)
+    obs2 = wv.sample(2)
+    links = wv.links()
+    ctx.close()
+    for w in range(2):
+        c = ctx_for(p)
+        c.chains_init(starts[w], precision=0, delay=4, seed=100 + 7919 * w)
+        ref = c.sample(3)
+        ref2 = c.sample(2)
+        assert np.array_equal(obs[w], ref) and np.array_equal(obs2[w], ref2)
+        assert np.array_equal(links[w], c.chains_links())
+        c.close()
