@@ -184,3 +184,31 @@ def test_link_score_matches_finite_differences_k1(grp, n_v):
     an = sum(np.sum(U[l] * (A @ p.gamma_bond[0, l] - p.gamma_bond[0, l] @ A)).real for l in range(p.n_links))
     assert abs(an) > 1e-3
     assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
+
+
+def test_energies_respect_the_variational_bounds(setup):
+    """H = -h sum_l X_l - J sum_p W_p acts on the 2^8 link states of the 2x2
+    Z2 torus (X_l flips link l, W_p is diagonal).  Every energy the per-pair
+    matrices give -- for random lambda and for the optimum -- is a genuine
+    quantum expectation, hence within H's spectrum."""
+    p, cfgs, S = setup
+    h, J = 0.7, 1.3
+    idx = {tuple(G): k for k, G in enumerate(cfgs)}
+    Hm = np.zeros((len(cfgs), len(cfgs)))
+    pl = plaquette_values(gi.Z2, 2, cfgs)
+    for k, G in enumerate(cfgs):
+        Hm[k, k] = -J * pl[k].sum()
+        for l in range(p.n_links):
+            g2 = G.copy()
+            g2[l] = -g2[l]
+            Hm[idx[tuple(g2)], k] += -h
+    ev = np.linalg.eigvalsh(Hm)
+    Hbar = -J * p.V * S["plaquette"] - h * S["electric"].sum(axis=0)
+    E0, lam0 = va.linear_method(Hbar, S["norm"])
+    assert ev[0] - 1e-9 <= E0 <= ev[-1] + 1e-9
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        z = rng.normal(size=p.K) + 1j * rng.normal(size=p.K)
+        e = va.expectation(Hbar, S["norm"], z).real
+        assert ev[0] - 1e-9 <= e <= ev[-1] + 1e-9
+        assert e >= E0 - 1e-9
