@@ -212,3 +212,48 @@ def test_energies_respect_the_variational_bounds(setup):
         e = va.expectation(Hbar, S["norm"], z).real
         assert ev[0] - 1e-9 <= e <= ev[-1] + 1e-9
         assert e >= E0 - 1e-9
+
+
+def test_site_gradient_step_lowers_a_wilson_energy():
+    """E = -<mean plaquette> on the 2x2 Z2 torus (exhaustive).  The gradient
+    with respect to a rotation exp(A) of the even-sublattice site states,
+    A = sum_k theta_k E_k over the antisymmetric basis, is the covariance of
+    the plaquette with sum_s tr(S_s^T dD_s/d theta_k); a small step against
+    it lowers E, by the amount the gradient predicts to first order."""
+    import dataclasses
+    import scipy.linalg
+    p = gi.make_problem(2, gi.Z2, 1, 1, bond_scale=0.3)
+    cfgs = gi.all_z2_configs(p)
+    pl = plaquette_values(gi.Z2, 2, cfgs).mean(axis=1)
+
+    def energy(q):
+        W = weight.Weights(q)
+        logs = np.array([W.log_norm(G) for G in cfgs])
+        w = np.exp(logs - logs.max())
+        return -np.sum(w * pl) / w.sum(), w / w.sum()
+
+    E, w = energy(p)
+    scores = [va.score_sites(p, G) for G in cfgs]
+    m = p.m_s
+    basis = []
+    for a in range(m):
+        for b in range(a + 1, m):
+            Ek = np.zeros((m, m))
+            Ek[a, b], Ek[b, a] = 1.0, -1.0
+            basis.append(Ek)
+    even = [s for s in range(p.V) if p.q_phys[s] == 1]
+    grad = np.zeros(len(basis))
+    for k, Ek in enumerate(basis):
+        dlog = np.array([sum(np.sum(S[s] * (Ek @ p.gamma_site[s] - p.gamma_site[s] @ Ek)[2:, 2:]) for s in even)
+                         for S in scores])
+        grad[k] = -np.sum(w * (pl - np.sum(w * pl)) * dlog)      # dE/dtheta_k
+    assert np.linalg.norm(grad) > 1e-3
+    eta = 0.05 / np.linalg.norm(grad)
+    O = scipy.linalg.expm(-eta * sum(g * Ek for g, Ek in zip(grad, basis)))
+    gs = p.gamma_site.copy()
+    for s in even:
+        gs[s] = O @ gs[s] @ O.T
+    E2, _ = energy(dataclasses.replace(p, gamma_site=gs))
+    predicted = -eta * np.dot(grad, grad)
+    assert E2 < E
+    assert abs((E2 - E) - predicted) <= 0.2 * abs(predicted)
