@@ -57,7 +57,10 @@ lattice real and at most 1 in modulus.  U(1): the covariance route against
 the quadrature of the definition (2x2, K = 1, 2; 1x1, n_v = 2); gauge
 invariance; <J_l^2> over p(G) on the 1x1 torus (exact product quadrature) is
 real and non-negative.  SU(2): the covariance route against the quadrature
-of the definition (1x1, K = 1, 2); gauge invariance.
+of the definition (1x1, K = 1, 2); gauge invariance.  U(1) field <J_l> (the
+insertion of Q_l, -i d/dtheta'): against the quadrature of the definition,
+and Gauss's law in every configuration, sum_out <J> - sum_in <J> + q_s <n_s>
+= 0 with the density from oracle.fermionic.
 """
 from __future__ import annotations
 
@@ -102,6 +105,24 @@ def f_electric_u1_fock(fp: fock.FockPEPS, links: np.ndarray, l: int) -> complex:
     Q = np.fft.fftfreq(N_QUAD, 1.0 / N_QUAD)           # integer frequencies
     c = np.fft.fft(phi) / N_QUAD                        # phi(t) = sum_Q c_Q e^{i Q t}
     return complex(np.sum(Q ** 2 * c * np.exp(1j * Q * links[l])) / np.vdot(v, v))
+
+
+def f_field_u1_fock(fp: fock.FockPEPS, links: np.ndarray, l: int) -> complex:
+    """U(1) electric field <J_l> for link l: -i d/dtheta' of the ket's overlap
+    at theta' = theta_l (the single-link integral with <G|J|g; G>), by the
+    same exact quadrature as f_electric_u1_fock."""
+    p = fp.p
+    lam = p.lam
+    v = (lam[:, None] * fp.psi(links)).sum(axis=0)
+    th = 2.0 * np.pi * np.arange(N_QUAD) / N_QUAD
+    phi = np.zeros(N_QUAD, dtype=complex)
+    for k, t in enumerate(th):
+        g = np.array(links, dtype=float).copy()
+        g[l] = t
+        phi[k] = np.vdot(v, (lam[:, None] * fp.psi(g)).sum(axis=0))
+    Q = np.fft.fftfreq(N_QUAD, 1.0 / N_QUAD)
+    c = np.fft.fft(phi) / N_QUAD
+    return complex(np.sum(Q * c * np.exp(1j * Q * links[l])) / np.vdot(v, v))
 
 
 def f_electric_su2_fock(fp: fock.FockPEPS, links: np.ndarray, l: int) -> complex:
@@ -181,6 +202,29 @@ class Electric:
                 pair = (1.0 + G[2 * j, 2 * j + 1] + G[2 * k, 2 * k + 1] + pfaffian(G[np.ix_(ix, ix)])) / 4.0
                 val = val + 2 * q[j] * q[k] * pair
         return val
+
+    def field(self, links: np.ndarray) -> np.ndarray:
+        """U(1) electric field <J_l> per link: the insertion of the twist
+        charge Q_l = sum_j q_j n_j, <Q_l> = sum_j q_j (1 + G_{2j,2j+1}) / 2 with
+        G = Gamma_O[S, S] (complex per configuration)."""
+        p = self.p
+        if p.group != U1:
+            raise ValueError("the electric field insertion is defined for U(1)")
+        O = weight.twist_matrix(p, links)
+        D = (O.T @ self.W.GA @ O)[np.ix_(self.virt, self.virt)]
+        one = np.eye(D.shape[0])
+        lnm = self.W.log_n_matrix(links)
+        Nnm = np.exp(lnm - lnm.real.max())
+        w = np.conj(p.lam)[:, None] * p.lam[None, :] * Nnm
+        out = np.zeros(p.n_links, dtype=complex)
+        for n in range(p.K):
+            for m in range(p.K):
+                GX = self.GX[n, m]
+                GO = 1j * one - (one + 1j * D) @ np.linalg.inv(D + GX) @ (one + 1j * GX)
+                for l in range(p.n_links):
+                    G = GO[np.ix_(self.S[l], self.S[l])]
+                    out[l] += w[n, m] * sum(p.q_src[j] * (1.0 + G[2 * j, 2 * j + 1]) / 2.0 for j in range(p.n_v))
+        return out / w.sum()
 
     def f_electric(self, links: np.ndarray) -> np.ndarray:
         """f_E(G) for every link (complex; its expectation over p(G) is real)."""

@@ -137,3 +137,36 @@ def test_su2_casimir_gauge_invariance():
     for a, b in zip(G, gi.gauge_transform(p, G, h)):
         fa, fb = el.f_electric(a), el.f_electric(b)
         assert np.abs(fa - fb).max() <= 1e-11 * np.abs(fa).max()
+
+
+@pytest.mark.parametrize("L,n_v,K", [(2, 1, 1), (2, 1, 2), (1, 2, 2)])
+def test_u1_field_matches_quadrature(L, n_v, K):
+    """<J_l> from Gamma_O against -i d/dtheta' of the overlap (explicit vectors)."""
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    fp, el = fock.FockPEPS(p), electric.Electric(p)
+    ls = [0, 3, 5, 6] if L == 2 else list(range(p.n_links))
+    for G in gi.random_links(p, 1 if L == 2 else 3, seed=5):
+        ref = np.array([electric.f_field_u1_fock(fp, G, l) for l in ls])
+        assert np.abs(ref).max() > 0.1
+        assert np.abs(el.field(G)[ls] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("L,n_v,K", [(2, 1, 2), (3, 1, 2), (3, 2, 2), (1, 2, 1)])
+def test_u1_gauss_law_per_configuration(L, n_v, K):
+    """Site tensors conserve the total charge and bond pairs are neutral, so in
+    every configuration sum_out <J> - sum_in <J> + q_s <n_s> = 0 at each site
+    (the field from oracle.electric, the density from oracle.fermionic)."""
+    from oracle import fermionic
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    el, fe = electric.Electric(p), fermionic.Fermionic(p)
+    for G in gi.random_links(p, 3, seed=9):
+        J = el.field(G)
+        site, _ = fe.bilinears(G)
+        n = (1 + 1j * site) / 2
+        assert np.abs(J).max() > 0.05
+        for s in range(p.V):
+            x, y = s % L, s // L
+            out_l = [2 * s, 2 * s + 1]
+            in_l = [2 * (y * L + (x - 1) % L), 2 * (((y - 1) % L) * L + x) + 1]
+            div = sum(J[l] for l in out_l) - sum(J[l] for l in in_l)
+            assert abs(div + p.q_phys[s] * n[s]) <= 1e-12
