@@ -236,6 +236,18 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
  * GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream);
 
+/* U(1) electric field (Sec. 5.3): out[c][l] = -i d/dtheta' of
+ * sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(theta'; G)> / N(G) at
+ * theta' = theta_l, i.e. the twist charge Q_l = sum_j q_j n_j of the link's
+ * source-end modes inserted on the ket, from the same Gamma_O[S, S] as
+ * ggf_chains_electric.  Site tensors conserve the total charge and bond
+ * pairs are neutral, so in every configuration
+ *   sum_{l out of s} out[c][l] - sum_{l into s} out[c][l] + q_s <n_s> = 0
+ * with <n_s> = (1 + i site[s]) / 2 from ggf_chains_fermion (Gauss's law).
+ *   out [n_chains][2V][2] FP64 (re, im), caller-owned.  GGF_EINVAL for
+ *   non-U(1) chains or a null `out`, GGF_ESTATE before ggf_chains_init. */
+ggf_status ggf_chains_electric_field(ggf_ctx* ctx, double* out, int mem, void* stream);
+
 /* Fermionic observables (Sec. 5.2): Majorana bilinears on the physical
  * modes (site s carries c_2s, c_2s+1) at the current configuration G of every
  * chain,

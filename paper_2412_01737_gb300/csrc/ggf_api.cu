@@ -19,7 +19,7 @@ ggf_status ggf_prepare_batch(ggf_ctx* ctx);
 ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64);
 ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st);
 ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
-ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st);
+ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st, bool field = false);
 ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cxd* d_pair_site, cxd* d_pair_link,
                        cudaStream_t st);
 ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
@@ -810,6 +810,25 @@ ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream)
         return check_err_word(ctx);
     }
     GGF_TRY(ggf_electric(ctx, (cxd*)out, nullptr, st));
+    return GGF_OK;
+}
+
+ggf_status ggf_chains_electric_field(ggf_ctx* ctx, double* out, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!out) return ggf_fail(ctx, GGF_EINVAL, "null out");
+    if (ctx->g.group != GGF_U1) return ggf_fail(ctx, GGF_EINVAL, "the electric field insertion is defined for U(1)");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)ctx->ch.n * ctx->g.n_links * sizeof(cxd);
+    if (mem == GGF_MEM_HOST) {
+        DBuf d;
+        GGF_TRY(dalloc(ctx, d, bytes));
+        GGF_TRY(ggf_electric(ctx, (cxd*)d.p, nullptr, st, true));
+        GGF_CK(cudaMemcpyAsync(out, d.p, bytes, cudaMemcpyDeviceToHost, st));
+        GGF_CK(cudaStreamSynchronize(st));
+        return check_err_word(ctx);
+    }
+    GGF_TRY(ggf_electric(ctx, (cxd*)out, nullptr, st, true));
     return GGF_OK;
 }
 

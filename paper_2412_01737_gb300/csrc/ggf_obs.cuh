@@ -21,9 +21,20 @@ GGF_HD cxd small_pf<4>(const cxd (&A)[4][4]) {
 
 GGF_HD cxd times_i(cxd v) { return {-v.y, v.x}; }
 
-// Normalised expectation of the insertion from G = Gamma_O[S, S].
-template <int H>
+// Normalised expectation of the insertion from G = Gamma_O[S, S]; FIELD: the
+// U(1) twist charge Q_l itself (the electric field) instead of Q_l^2.
+template <int H, bool FIELD = false>
 GGF_HD cxd insertion(const Geometry& g, const cxd (&G)[H][H]) {
+    if constexpr (FIELD) {
+        cxd val = {0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < H / 2; ++j) {
+            cxd occ = G[2 * j][2 * j + 1];
+            occ.x += 1.0;
+            val += (0.5 * (double)g.q[j]) * occ;       // q_j <n_j>
+        }
+        return val;
+    }
     if (g.group == GGF_Z2) {
         const double sg = (H / 2) % 2 ? -1.0 : 1.0;    // (-1)^{n_v}
         return sg * small_pf<H>(G);
@@ -56,7 +67,7 @@ GGF_HD cxd insertion(const Geometry& g, const cxd (&G)[H][H]) {
 
 // R for both orders of pair p at link l: Rf from (W, Gamma_tw), Rr from their
 // conjugates.  W points at the pair's N x N inverse (row-major).
-template <class T, int H>
+template <class T, int H, bool FIELD = false>
 __host__ __device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, const T* W, int l, double gval,
                             double theta, const double* Rsu2, cxd& Rf, cxd& Rr) {
     constexpr int R = 2 * H, B = 4 * H;
@@ -116,13 +127,13 @@ __host__ __device__ void flip_ratios(const DevConst& dc, int p, bool cplx_pair, 
             Xr[a][b] = -Xr[a][b];
             if (a == b) { Xf[a][b].y += 1.0; Xr[a][b].y += 1.0; }
         }
-    Rf = insertion<H>(g, Xf);
-    Rr = insertion<H>(g, Xr);
+    Rf = insertion<H, FIELD>(g, Xf);
+    Rr = insertion<H, FIELD>(g, Xr);
 }
 
 // f_E(G_c)_l into out[c][l] (if out is set) and N_nm(G) R_nm / N(G) into
 // pair_out[c][l][n][m] for every ordered pair (if set).
-template <class RW, class CW, int H>
+template <class RW, class CW, int H, bool FIELD = false>
 __host__ __device__ void electric_item(const DevConst& dc, int c, int l, const void* links, const RW* Wr,
                                        const CW* Wc, const cxd* ell, cxd* out, cxd* pair_out) {
     const Geometry& g = dc.g;
@@ -148,7 +159,8 @@ __host__ __device__ void electric_item(const DevConst& dc, int c, int l, const v
         pair_nm(dc.K, p, n, m);
         cxd* po = pair_out ? pair_out + ((size_t)c * g.n_links + l) * dc.K * dc.K : nullptr;
         if (cplx) {
-            flip_ratios<CW, H>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, theta, Rsu2, Rf, Rr);
+            flip_ratios<CW, H, FIELD>(dc, p, true, Wc + ((size_t)c * dc.Kc + (p - dc.K)) * NN, l, gval, theta, Rsu2,
+                                      Rf, Rr);
             // w_p = 2 lambda_n^* lambda_m: the (n, m) term takes E / 2, the (m, n) term its conjugate
             num += 0.5 * (E * Rf) + 0.5 * (conjg(E) * Rr);
             if (po) {
@@ -156,7 +168,7 @@ __host__ __device__ void electric_item(const DevConst& dc, int c, int l, const v
                 po[m * dc.K + n] = conjg(Np) * Rr;
             }
         } else {
-            flip_ratios<RW, H>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, theta, Rsu2, Rf, Rr);
+            flip_ratios<RW, H, FIELD>(dc, p, false, Wr + ((size_t)c * dc.K + p) * NN, l, gval, theta, Rsu2, Rf, Rr);
             num += E * Rf;
             if (po) po[n * dc.K + n] = Np * Rf;
         }

@@ -38,15 +38,15 @@ namespace {
 
 constexpr int ETHREADS = 128;
 
-// One thread per (chain, link).
-template <class RW, class CW, int H>
+// One thread per (chain, link); FIELD: the U(1) electric field instead of J^2.
+template <class RW, class CW, int H, bool FIELD>
 __global__ void __launch_bounds__(ETHREADS) electric_kernel(DevConst dc, int n_chains, int blocks_per_chain,
                                                             const void* links, const RW* Wr, const CW* Wc,
                                                             const cxd* ell, cxd* out, cxd* pair_out) {
     const int c = blockIdx.x / blocks_per_chain;
     const int l = (blockIdx.x - c * blocks_per_chain) * ETHREADS + threadIdx.x;
     if (c >= n_chains || l >= dc.g.n_links) return;
-    electric_item<RW, CW, H>(dc, c, l, links, Wr, Wc, ell, out, pair_out);
+    electric_item<RW, CW, H, FIELD>(dc, c, l, links, Wr, Wc, ell, out, pair_out);
 }
 
 // One thread per chain.
@@ -71,7 +71,7 @@ ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
 // f_E for every chain and link into d_out [n_chains][n_links] and/or its
 // per-pair parts into d_pairs [n_chains][n_links][K][K] (device; either may
 // be null): Z2 the flip, U(1) and SU(2) the Casimir J^2.
-ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st) {
+ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st, bool field) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
     // pending delayed updates first, so that W is the inverse at the current links
@@ -81,10 +81,16 @@ ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st)
     if (blocks > 0x7fffffffLL) return ggf_fail(ctx, GGF_EINVAL, "too many chains for one launch");
     const bool fp64 = ch.opts.precision == GGF_FP64;
     const void* lk = ch.links;
-#define GGF_EL(RW, CW, H)                                                                                \
-    electric_kernel<RW, CW, H><<<(unsigned)blocks, ETHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, lk,          \
-                                                                      (const RW*)ch.Wr, (const CW*)ch.Wc, \
-                                                                      ch.ell, d_out, d_pairs)
+#define GGF_EL2(RW, CW, H, F)                                                                            \
+    electric_kernel<RW, CW, H, F><<<(unsigned)blocks, ETHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, lk,       \
+                                                                         (const RW*)ch.Wr,                \
+                                                                         (const CW*)ch.Wc, ch.ell, d_out, \
+                                                                         d_pairs)
+#define GGF_EL(RW, CW, H)                  \
+    do {                                   \
+        if (field) GGF_EL2(RW, CW, H, true); \
+        else GGF_EL2(RW, CW, H, false);      \
+    } while (0)
     if (g.h2 == 2) {
         if (fp64) GGF_EL(double, cxd, 2); else GGF_EL(float, cxf, 2);
     } else if (g.h2 == 4) {
@@ -93,6 +99,7 @@ ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st)
         return ggf_fail(ctx, GGF_EINVAL, "n_v must be 1 or 2");
     }
 #undef GGF_EL
+#undef GGF_EL2
     GGF_CK(cudaGetLastError());
     return GGF_OK;
 }

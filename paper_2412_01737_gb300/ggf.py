@@ -52,6 +52,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
            "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
            "ggf_debug_poison_inverse", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
+           "ggf_chains_electric_field",
            "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
@@ -97,6 +98,7 @@ def load():
         "ggf_wilson_loop": ([P, I, I, I, P, P, I, P], I),
         "ggf_polyakov_loop": ([P, I, P, P, I, P], I),
         "ggf_debug_poison_inverse": ([P, I, I, I, I], I),
+        "ggf_chains_electric_field": ([P, P, I, P], I),
         "ggf_chains_state_size": ([P, ctypes.POINTER(ctypes.c_uint64)], I),
         "ggf_chains_save_state": ([P, P, I, P], I),
         "ggf_chains_load_state": ([P, P, I, P], I),
@@ -312,6 +314,16 @@ class GGF:
             self._ck(self.lib.ggf_chains_electric(self.h, host.ctypes.data, MEM_HOST, None))
             return host[..., 0] + 1j * host[..., 1]
         self._ck(self.lib.ggf_chains_electric(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
+        return out
+
+    def chains_electric_field(self, out=None):
+        """U(1) electric field <J_l> of every chain and link (Sec. 5.3):
+        complex numpy array (n_chains, 2V), or fills `out` (float64 [n][2V][2])."""
+        if out is None:
+            host = np.zeros((self.n_chains, self.n_links(), 2))
+            self._ck(self.lib.ggf_chains_electric_field(self.h, host.ctypes.data, MEM_HOST, None))
+            return host[..., 0] + 1j * host[..., 1]
+        self._ck(self.lib.ggf_chains_electric_field(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
         return out
 
     def chains_fermion(self, site=None, link=None):

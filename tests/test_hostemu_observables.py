@@ -299,3 +299,17 @@ def test_loops_match_oracle(emu, grp):
         emu.emu_loops(ctypes.c_int(L), ctypes.c_int(grp), _ptr(G), ctypes.c_int(0), ctypes.c_int(0),
                       ctypes.c_int(1), _ptr(out))
         assert np.abs(out - polyakov_values(grp, L, G)[0]).max() <= 1e-14
+
+
+@pytest.mark.parametrize("L,n_v,K", [(3, 1, 2), (2, 2, 3), (1, 2, 2)])
+def test_field_items_match_oracle(emu, L, n_v, K):
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=22)
+    lay = Layout(p, links)
+    out = np.zeros((2, p.n_links, 2))
+    emu.emu_field(*lay.common()[:-1], ctypes.c_int(2), _ptr(lay.links), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell),
+                  _ptr(out))
+    el = electric.Electric(p)
+    for c in range(2):
+        ref = el.field(links[c])
+        assert np.abs(_c(out)[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())

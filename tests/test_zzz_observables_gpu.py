@@ -362,3 +362,55 @@ def test_waves_match_separate_contexts():
         assert np.array_equal(obs[w], ref) and np.array_equal(obs2[w], ref2)
         assert np.array_equal(links[w], c.chains_links())
         c.close()
+
+
+def _divergence(L, J):
+    """(n, V) sum over the links leaving a site minus the links entering it."""
+    V = L * L
+    s = np.arange(V)
+    x, y = s % L, s // L
+    left = 2 * (y * L + (x - 1) % L)
+    down = 2 * (((y - 1) % L) * L + x) + 1
+    return J[:, 2 * s] + J[:, 2 * s + 1] - J[:, left] - J[:, down]
+
+
+@pytest.mark.parametrize("L,n_v,K,prec,tol", [(3, 1, 2, 0, 1e-10), (2, 2, 3, 0, 1e-10), (4, 1, 2, 1, 1e-4)])
+def test_u1_field_matches_oracle(L, n_v, K, prec, tol):
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=17), precision=prec, seed=7, delay=8 if prec else 1)
+    ctx.sample(2)
+    links = ctx.chains_links()
+    J = ctx.chains_electric_field()
+    el = electric.Electric(p)
+    for c in range(2):
+        ref = el.field(links[c])
+        assert np.abs(J[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
+    ctx.close()
+
+
+@pytest.mark.parametrize("L,n_v,K,prec,tol", [(8, 1, 2, 0, 1e-10), (16, 2, 2, 1, 1e-4)])
+def test_u1_gauss_law_from_gpu_outputs(L, n_v, K, prec, tol):
+    """Gauss's law holds in every configuration at any size: the divergence of
+    the field plus the physical charge density vanishes, both read from the
+    chains' inverses after sampling (the 16x16 case at the benchmark's n_v)."""
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 4, seed=23), precision=prec, seed=9, delay=16 if prec else 4)
+    ctx.sample(1)
+    J = ctx.chains_electric_field()
+    site, _ = ctx.chains_fermion()
+    n = (1 + 1j * site) / 2
+    resid = _divergence(L, J) + p.q_phys[None, :] * n
+    assert np.abs(J).max() > 0.01
+    assert np.abs(resid).max() <= tol, np.abs(resid).max()
+    ctx.close()
+
+
+def test_u1_field_rejects_other_groups():
+    p = gi.make_problem(2, gi.Z2, 1, 1)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 1, seed=1), precision=0, seed=1)
+    with pytest.raises(RuntimeError):
+        ctx.chains_electric_field()
+    ctx.close()
