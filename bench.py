@@ -562,10 +562,12 @@ def run_observables(args):
              "electric_pairs": lambda: ctx.chains_pairs(PAIRS_ELECTRIC, out=ep),
              "site_score": lambda: ctx.chains_score(out=sc),
              "link_score": lambda: ctx.chains_link_score(out=ls)}
+    if p.group == gi.U1:
+        calls["electric_field"] = lambda: ctx.chains_electric_field(out=el)
     eb, fb = observable_bytes(p, prec)
     esz = 8 if prec == 0 else 4
     per_pair = p.K * esz + p.K * (p.K - 1) // 2 * 2 * esz
-    read_bytes = {"electric": eb, "electric_pairs": eb, "fermion": fb,
+    read_bytes = {"electric": eb, "electric_pairs": eb, "electric_field": eb, "fermion": fb,
                   "fermion4": p.n_links * 3 * B * B * per_pair,
                   "site_score": p.V * B * B * per_pair,
                   "link_score": p.n_links * r * r * per_pair}

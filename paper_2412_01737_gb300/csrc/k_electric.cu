@@ -13,6 +13,9 @@
 //   SU(2): I_l = sum_a (Q^a)^2 on the source doublet, Q^a = psi^dag (sigma_a / 2)
 //         psi (right translations of the link act on the twist as
 //         exp(i eps Q^a)), which is (3/4)(n_0 + n_1 - 2 n_0 n_1).
+// The U(1) field <J_l> itself inserts I_l = Q_l (one derivative of the
+// overlap), R_nm = sum_j q_j <n_j>; with charge-conserving site tensors and
+// neutral bond pairs it obeys Gauss's law configuration by configuration.
 // Wick's theorem on the Gaussian operator composed of the sites' virtual
 // state and the bond operator X_nm gives the insertion's normalised
 // expectation from the covariance of that operator on the end's 2 n_v
