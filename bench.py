@@ -564,10 +564,13 @@ def run_observables(args):
              "link_score": lambda: ctx.chains_link_score(out=ls)}
     if p.group == gi.U1:
         calls["electric_field"] = lambda: ctx.chains_electric_field(out=el)
+    if p.group in (gi.Z2, gi.U1):
+        calls["link_terms"] = lambda: ctx.chains_link_terms(p.q_phys, out=el)
     eb, fb = observable_bytes(p, prec)
     esz = 8 if prec == 0 else 4
     per_pair = p.K * esz + p.K * (p.K - 1) // 2 * 2 * esz
     read_bytes = {"electric": eb, "electric_pairs": eb, "electric_field": eb, "fermion": fb,
+                  "link_terms": p.n_links * B * B * per_pair,
                   "fermion4": p.n_links * 3 * B * B * per_pair,
                   "site_score": p.V * B * B * per_pair,
                   "link_score": p.n_links * r * r * per_pair}

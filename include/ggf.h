@@ -236,6 +236,28 @@ ggf_status ggf_chains_ell(ggf_ctx* ctx, double* ell, int mem, void* stream);
  * GGF_ESTATE before ggf_chains_init. */
 ggf_status ggf_chains_electric(ggf_ctx* ctx, double* out, int mem, void* stream);
 
+/* Gauge-invariant link terms (Sec. 5.2 with the link operator of the
+ * observable): for link l = (s -> t),
+ *   out[c][l] = u_l(G) sum_nm lambda_n^* lambda_m <psi_n(G)| F_s F_t |psi_m(G)> / N(G),
+ * u_l = g_l (Z2) or e^{i theta_l} (U(1)), F_s = psi_s if charges[s] > 0 else
+ * psi_s^dag, F_t = psi_t^dag if charges[t] > 0 else psi_t, psi_s =
+ * (c_2s + i c_2s+1) / 2.  With the Gauss generator sum_out J - sum_in J +
+ * q_s n_s this operator is gauge invariant; for staggered charges it is the
+ * pair term, and T_l + T_l^dag the link's hopping term (its expectation is
+ * 2 Re of the mean of out).  For Z2 every bilinear times g_l is invariant
+ * and the same F are used.
+ *   charges   [V] host int32, the sites' physical charges (+1 or -1, as the
+ *             site states were built); 0 gives GGF_EINVAL.
+ *   out       [n_chains][2V][2] FP64 (re, im), or null.
+ *   pair_out  [n_chains][2V][K][K][2] FP64: the per-pair parts N_nm <F F>_nm
+ *             u_l / N(G) (lambda^dag X lambda gives out), or null.
+ * Both caller-owned, in the memory `mem` says; at least one non-null.
+ * Blocking: returns after the results are written (it allocates and frees
+ * scratch).  GGF_EINVAL for SU(2) chains, GGF_ESTATE before
+ * ggf_chains_init. */
+ggf_status ggf_chains_link_terms(ggf_ctx* ctx, const int* charges, double* out, double* pair_out, int mem,
+                                 void* stream);
+
 /* U(1) electric field (Sec. 5.3): out[c][l] = -i d/dtheta' of
  * sum_nm lambda_n^* lambda_m <psi_n(G)|psi_m(theta'; G)> / N(G) at
  * theta' = theta_l, i.e. the twist charge Q_l = sum_j q_j n_j of the link's

@@ -22,8 +22,8 @@ observables  Plaquette Wilson loops (Sec. 2.3) and integrated
 electric The Z2 electric (link-flip) observable of Sec. 5.3: f_E(G) from
          explicit vectors and from a Pfaffian of the composed covariance.
 fermionic  Majorana expectations of Sec. 5.2 (densities, link bilinears,
-         general monomials) from explicit vectors and from the physical
-         covariance A + B W B^T of each pair.
+         general monomials, gauge-invariant link terms) from explicit
+         vectors and from the physical covariance A + B W B^T of each pair.
 variational  Per-configuration K x K matrices of the observables (Hermitian
          forms in lambda) and the generalised-eigenvector optimum of lambda.
 

@@ -26,6 +26,8 @@ ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 ggf_status ggf_score(ggf_ctx* ctx, double* d_out, cudaStream_t st);
 ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 ggf_status ggf_link_score(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
+ggf_status ggf_link_terms(ggf_ctx* ctx, const int* d_q, cxd* d_blk, cxd* d_pair_blk, cxd* d_out, cxd* d_pair_out,
+                          cudaStream_t st);
 
 ggf_status ggf_fail(ggf_ctx* ctx, ggf_status st, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -851,6 +853,39 @@ ggf_status ggf_chains_fermion(ggf_ctx* ctx, double* site, double* link, int mem,
     }
     GGF_TRY(ggf_fermion(ctx, (cxd*)site, (cxd*)link, nullptr, nullptr, st));
     return GGF_OK;
+}
+
+ggf_status ggf_chains_link_terms(ggf_ctx* ctx, const int* charges, double* out, double* pair_out, int mem,
+                                 void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!charges || (!out && !pair_out)) return ggf_fail(ctx, GGF_EINVAL, "need charges and an output");
+    const Geometry& g = ctx->g;
+    if (g.group != GGF_Z2 && g.group != GGF_U1)
+        return ggf_fail(ctx, GGF_EINVAL, "link terms are defined for Z2 and U(1) chains");
+    for (int s = 0; s < g.V; ++s)
+        if (charges[s] == 0) return ggf_fail(ctx, GGF_EINVAL, "site charges must be nonzero");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ob = (size_t)ctx->ch.n * g.n_links * sizeof(cxd), pb = ob * ctx->K * ctx->K;
+    DBuf dq, blk, pblk, dout, dpout;
+    GGF_TRY(dalloc(ctx, dq, (size_t)g.V * sizeof(int)));
+    GGF_CK(cudaMemcpyAsync(dq.p, charges, (size_t)g.V * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (out) GGF_TRY(dalloc(ctx, blk, 4 * ob));
+    if (pair_out) GGF_TRY(dalloc(ctx, pblk, 4 * pb));
+    cxd* o = (cxd*)out;
+    cxd* po = (cxd*)pair_out;
+    if (mem == GGF_MEM_HOST) {
+        if (out) { GGF_TRY(dalloc(ctx, dout, ob)); o = (cxd*)dout.p; }
+        if (pair_out) { GGF_TRY(dalloc(ctx, dpout, pb)); po = (cxd*)dpout.p; }
+    }
+    GGF_TRY(ggf_link_terms(ctx, (const int*)dq.p, (cxd*)blk.p, (cxd*)pblk.p, o, po, st));
+    if (mem == GGF_MEM_HOST) {
+        if (out) GGF_CK(cudaMemcpyAsync(out, o, ob, cudaMemcpyDeviceToHost, st));
+        if (pair_out) GGF_CK(cudaMemcpyAsync(pair_out, po, pb, cudaMemcpyDeviceToHost, st));
+    }
+    // the scratch buffers are released on return
+    GGF_CK(cudaStreamSynchronize(st));
+    return check_err_word(ctx);
 }
 
 ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* stream) {

@@ -313,6 +313,49 @@ __host__ __device__ void fermion_item(const DevConst& dc, int c, int it, const R
     }
 }
 
+// ---- gauge-invariant link terms ------------------------------------------------
+// A physical bilinear across link l = (s -> t) is gauge invariant together with
+// the link operator u_l (Z2: g_l; U(1): e^{i theta_l}, diagonal in G) when it
+// carries the charge u_l removes: T_l = u_l F_s F_t with F_s = psi_s (q_s > 0)
+// or psi_s^dag (q_s < 0) and F_t = psi_t^dag (q_t > 0) or psi_t (q_t < 0); for
+// staggered charges that is the pair term, and T_l + T_l^dag the link's hopping
+// term.  With psi = (c_0 + i c_1) / 2 and the link block X[alpha][beta] =
+// <c_{2s+alpha} c_{2t+beta}> (entries `stride` apart),
+//   T_l = u_l (1/4) (X00 + i e_t X01 + i e_s X10 - e_s e_t X11),
+// e = +1 for psi, -1 for psi^dag.
+GGF_HD cxd link_term(const cxd* X, size_t stride, int e_s, int e_t, cxd u) {
+    const cxd v = X[0] + cxd{0.0, (double)e_t} * X[stride] + cxd{0.0, (double)e_s} * X[2 * stride] +
+                  (-(double)(e_s * e_t)) * X[3 * stride];
+    return u * (0.25 * v);
+}
+
+// Chain c, link l: T_l from the combined link block blk [n][n_links][2][2]
+// into out[c][l], and from the per-pair blocks pair_blk
+// [n][n_links][2][2][K][K] into pair_out[c][l][n][m] (either pair of pointers
+// may be null); q [V] the sites' physical charges.
+GGF_HD void link_term_item(const DevConst& dc, int c, int l, const void* links, const int* q, const cxd* blk,
+                           const cxd* pair_blk, cxd* out, cxd* pair_out) {
+    const Geometry& g = dc.g;
+    int a0, b0;
+    link_ends(g, l, a0, b0);
+    const int s = a0 / g.B, t = b0 / g.B;
+    const int e_s = q[s] > 0 ? 1 : -1, e_t = q[t] > 0 ? -1 : 1;
+    const size_t cl = (size_t)c * g.n_links + l;
+    cxd u;
+    if (g.group == GGF_Z2) {
+        u = cxd{(double)((const int8_t*)links)[cl], 0.0};
+    } else {
+        const double th = ((const double*)links)[cl];
+        u = cxd{cos(th), sin(th)};
+    }
+    if (blk && out) out[cl] = link_term(blk + cl * 4, 1, e_s, e_t, u);
+    if (pair_blk && pair_out) {
+        const int KK = dc.K * dc.K;
+        for (int nm = 0; nm < KK; ++nm)
+            pair_out[cl * KK + nm] = link_term(pair_blk + cl * 4 * KK + nm, (size_t)KK, e_s, e_t, u);
+    }
+}
+
 // ---- nearest-neighbour four-point function ----------------------------------
 // <c_2s c_2s+1 c_2t c_2t+1> of link l = (s -> t) for chain c into out[c][l]:
 // per pair, Wick's theorem gives Pf(-i G4) = -Pf(G4) with G4 the physical

@@ -44,9 +44,42 @@ __global__ void __launch_bounds__(FTHREADS) fermion4_kernel(DevConst dc, int n_c
     fermion4_item<RW, CW, BW>(dc, c, l, Wr, Wc, ell, out);
 }
 
+// One thread per (chain, link).
+__global__ void __launch_bounds__(FTHREADS) link_term_kernel(DevConst dc, int n_chains, const void* links,
+                                                             const int* q, const cxd* blk, const cxd* pair_blk,
+                                                             cxd* out, cxd* pair_out) {
+    const long long t = (long long)blockIdx.x * FTHREADS + threadIdx.x;
+    if (t >= (long long)n_chains * dc.g.n_links) return;
+    const int c = (int)(t / dc.g.n_links), l = (int)(t - (long long)c * dc.g.n_links);
+    link_term_item(dc, c, l, links, q, blk, pair_blk, out, pair_out);
+}
+
 }  // namespace
 
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
+ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cxd* d_pair_site, cxd* d_pair_link,
+                       cudaStream_t st);
+
+// Gauge-invariant link terms of every chain into d_out [n][n_links] and/or
+// their per-pair parts into d_pair_out [n][n_links][K][K] (device; either may
+// be null), through the link blocks written to the scratch buffers d_blk
+// [n][n_links][2][2] and d_pair_blk [n][n_links][2][2][K][K]; d_q [V] device.
+ggf_status ggf_link_terms(ggf_ctx* ctx, const int* d_q, cxd* d_blk, cxd* d_pair_blk, cxd* d_out, cxd* d_pair_out,
+                          cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    const Geometry& g = ctx->g;
+    if (!d_out) d_blk = nullptr;
+    if (!d_pair_out) d_pair_blk = nullptr;
+    if (!d_blk && !d_pair_blk) return GGF_OK;
+    GGF_TRY(ggf_fermion(ctx, nullptr, d_blk, nullptr, d_pair_blk, st));
+    const long long items = (long long)ch.n * g.n_links;
+    const long long blocks = (items + FTHREADS - 1) / FTHREADS;
+    if (blocks > 0x7fffffffLL) return ggf_fail(ctx, GGF_EINVAL, "too many chains for one launch");
+    link_term_kernel<<<(unsigned)blocks, FTHREADS, 0, st>>>(ctx->dc(), ch.n, ch.links, d_q, d_blk, d_pair_blk,
+                                                             d_out, d_pair_out);
+    GGF_CK(cudaGetLastError());
+    return GGF_OK;
+}
 
 // <c_2s c_2s+1 c_2t c_2t+1> of every chain and link into d_out [n][n_links] (device).
 ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {

@@ -52,7 +52,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
            "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
            "ggf_debug_poison_inverse", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
-           "ggf_chains_electric_field",
+           "ggf_chains_electric_field", "ggf_chains_link_terms",
            "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
@@ -99,6 +99,7 @@ def load():
         "ggf_polyakov_loop": ([P, I, P, P, I, P], I),
         "ggf_debug_poison_inverse": ([P, I, I, I, I], I),
         "ggf_chains_electric_field": ([P, P, I, P], I),
+        "ggf_chains_link_terms": ([P, P, P, P, I, P], I),
         "ggf_chains_state_size": ([P, ctypes.POINTER(ctypes.c_uint64)], I),
         "ggf_chains_save_state": ([P, P, I, P], I),
         "ggf_chains_load_state": ([P, P, I, P], I),
@@ -325,6 +326,28 @@ class GGF:
             return host[..., 0] + 1j * host[..., 1]
         self._ck(self.lib.ggf_chains_electric_field(self.h, _ptr(out)[0], self._mem(out), _stream([out])))
         return out
+
+    def chains_link_terms(self, charges, out=None, pair_out=None, pairs=False):
+        """Gauge-invariant link terms T_l = u_l <F_s F_t> of every chain and
+        link (charges: the sites' physical charges, +1 / -1).  Returns a
+        complex numpy array (n_chains, 2V), with pairs=True also the per-pair
+        parts (n_chains, 2V, K, K); or fills out [n][2V][2] and/or pair_out
+        [n][2V][K][K][2] (numpy or CUDA tensors) and returns them."""
+        q = np.ascontiguousarray(np.asarray(charges), dtype=np.int32)
+        if q.shape != (self.n_links() // 2,):
+            raise ValueError("charges must have one entry per site")
+        if out is None and pair_out is None:
+            host = np.zeros((self.n_chains, self.n_links(), 2))
+            hp = np.zeros((self.n_chains, self.n_links(), self.K, self.K, 2)) if pairs else None
+            self._ck(self.lib.ggf_chains_link_terms(self.h, q.ctypes.data, host.ctypes.data,
+                                                    None if hp is None else hp.ctypes.data, MEM_HOST, None))
+            T = host[..., 0] + 1j * host[..., 1]
+            return (T, hp[..., 0] + 1j * hp[..., 1]) if pairs else T
+        mem = self._mem(out, pair_out)
+        self._ck(self.lib.ggf_chains_link_terms(self.h, q.ctypes.data, None if out is None else _ptr(out)[0],
+                                                None if pair_out is None else _ptr(pair_out)[0], mem,
+                                                _stream([a for a in (out, pair_out) if a is not None])))
+        return out, pair_out
 
     def chains_fermion(self, site=None, link=None):
         """Physical Majorana bilinears of every chain (Sec. 5.2): complex numpy

@@ -13,9 +13,11 @@ current lambda and estimates Hbar and Nbar for an energy
 
     E = c_plaquette <mean plaquette> + sum_l c_electric[l] <f_E,l>
         + sum_s c_site[s] <c_2s c_2s+1> + sum_{l,a,b} c_link[l,a,b] <c_{2s+a} c_{2t+b}>
+        + sum_l c_hop[l] <T_l + T_l^dag>
 
-(any coefficient may be omitted); the couplings, and thus the Hamiltonian,
-are the caller's.  ``linear_method`` solves for the new lambda, which
+(any coefficient may be omitted; T_l the gauge-invariant link term of
+``GGF.chains_link_terms``, whose per-pair parts enter as T + T^H over the pair
+indices); the couplings, and thus the Hamiltonian, are the caller's.  ``linear_method`` solves for the new lambda, which
 ``GGF.init_gaussians`` takes before sampling again.
 
 ``wilson_score`` gives the gradient of a Wilson-loop energy with respect to
@@ -34,10 +36,11 @@ from .ggf import PAIRS_ELECTRIC, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
 
 
 def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric=None, c_site=None,
-                 c_link=None) -> np.ndarray:
+                 c_link=None, c_hop=None) -> np.ndarray:
     """(n_chains, K, K) local matrices of the energy from one sweep's per-pair
     parts (dict with keys 'norm', 'electric', 'site', 'link' as returned by
-    GGF.chains_pairs) and the chains' mean plaquettes."""
+    GGF.chains_pairs, 'hop' the per-pair link terms of GGF.chains_link_terms)
+    and the chains' mean plaquettes."""
     H = c_plaquette * plaquette[:, None, None] * pairs["norm"]
     if c_electric is not None:
         H = H + np.einsum("l,clnm->cnm", np.asarray(c_electric, dtype=complex), pairs["electric"])
@@ -45,12 +48,19 @@ def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric
         H = H + np.einsum("s,csnm->cnm", np.asarray(c_site, dtype=complex), pairs["site"])
     if c_link is not None:
         H = H + np.einsum("lab,clabnm->cnm", np.asarray(c_link, dtype=complex), pairs["link"])
+    if c_hop is not None:
+        T = np.einsum("l,clnm->cnm", np.asarray(c_hop, dtype=float), pairs["hop"])
+        H = H + T + np.conj(np.swapaxes(T, 1, 2))
     return H
 
 
-def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None):
+def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
+               charges=None):
     """Run n_sweeps sweeps of ctx's chains and return (Hbar, Nbar), the means
-    over chains and sweeps of the energy's and the norm's per-pair parts."""
+    over chains and sweeps of the energy's and the norm's per-pair parts
+    (c_hop needs the sites' physical charges)."""
+    if c_hop is not None and charges is None:
+        raise ValueError("c_hop needs the sites' physical charges")
     Hbar, Nbar, n = 0.0, 0.0, 0
     for _ in range(n_sweeps):
         obs = ctx.sample(1)
@@ -61,7 +71,9 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
             pairs["site"] = ctx.chains_pairs(PAIRS_SITE)
         if c_link is not None:
             pairs["link"] = ctx.chains_pairs(PAIRS_LINK)
-        H = local_energy(pairs, obs[0, :, 0], c_plaquette, c_electric, c_site, c_link)
+        if c_hop is not None:
+            pairs["hop"] = ctx.chains_link_terms(charges, pairs=True)[1]
+        H = local_energy(pairs, obs[0, :, 0], c_plaquette, c_electric, c_site, c_link, c_hop)
         Hbar = Hbar + H.sum(axis=0)
         Nbar = Nbar + pairs["norm"].sum(axis=0)
         n += H.shape[0]

@@ -59,6 +59,16 @@ void emu_field(int L, int group, int n_v, const int* q, int K, const double* D, 
         }
 }
 
+void emu_link_terms(int L, int group, int n_v, int K, int n_chains, const void* links, const int* q_phys,
+                    const double* blk, const double* pair_blk, double* out, double* pair_out) {
+    const int q[2] = {1, 1};
+    DevConst dc = make_dc(L, group, n_v, q, K, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    for (int c = 0; c < n_chains; ++c)
+        for (int l = 0; l < dc.g.n_links; ++l)
+            link_term_item(dc, c, l, links, q_phys, (const cxd*)blk, (const cxd*)pair_blk, (cxd*)out,
+                           (cxd*)pair_out);
+}
+
 void emu_fermion(int L, int group, int n_v, const int* q, int K, const double* D, const double* Ap,
                  const double* Bp, const double* Gr, const double* Gc, const double* logc, const double* w,
                  int n_chains, const double* Wr, const double* Wc, const double* ell, double* site,

@@ -313,3 +313,32 @@ def test_field_items_match_oracle(emu, L, n_v, K):
     for c in range(2):
         ref = el.field(links[c])
         assert np.abs(_c(out)[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("L,grp,n_v,K", [(2, gi.U1, 1, 2), (3, gi.U1, 1, 2), (2, gi.Z2, 2, 3), (1, gi.U1, 2, 2)])
+def test_link_term_items_match_oracle(emu, L, grp, n_v, K):
+    """The link-term item on the emulated fermion outputs (combined and per
+    pair) against oracle.fermionic's link terms."""
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    links = gi.random_links(p, 2, seed=24)
+    lay = Layout(p, links)
+    site = np.zeros((2, p.V, 2))
+    link = np.zeros((2, p.n_links, 2, 2, 2))
+    ps = np.zeros((2, p.V, K, K, 2))
+    pl = np.zeros((2, p.n_links, 2, 2, K, K, 2))
+    emu.emu_fermion(*lay.common(), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell), _ptr(site), _ptr(link),
+                    _ptr(ps), _ptr(pl))
+    q = np.ascontiguousarray(p.q_phys, dtype=np.int32)
+    out = np.zeros((2, p.n_links, 2))
+    pout = np.zeros((2, p.n_links, K, K, 2))
+    emu.emu_link_terms(ctypes.c_int(p.L), ctypes.c_int(p.group), ctypes.c_int(p.n_v), ctypes.c_int(K),
+                       ctypes.c_int(2), _ptr(lay.links), _ptr(q), _ptr(link), _ptr(pl), _ptr(out), _ptr(pout))
+    fe = fermionic.Fermionic(p)
+    for c in range(2):
+        ref = fe.link_terms(links[c])
+        assert np.abs(ref).max() > 1e-3
+        assert np.abs(_c(out)[c] - ref).max() <= 1e-11
+        want = fermionic.link_terms_from_block(p, links[c], _c(pl)[c])
+        assert np.abs(_c(pout)[c] - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+        lam = p.lam
+        assert np.abs(np.einsum("n,lnm,m->l", np.conj(lam), _c(pout)[c], lam) - ref).max() <= 1e-11

@@ -75,3 +75,30 @@ def test_accumulate_contracts_the_energy():
     want_N = np.mean([d["norm"] for d in stub.loc], axis=0)
     assert np.abs(H - want_H).max() <= 1e-13
     assert np.abs(N - want_N).max() <= 1e-13
+
+
+def test_hopping_energy_is_twice_the_real_part():
+    """local_energy's hopping term: lambda^dag (sum_l c_l (T_l + T_l^H)) lambda
+    equals sum_l c_l 2 Re T_l(G) per configuration, with the per-pair link
+    terms built from the oracle's per-pair blocks."""
+    from oracle import fermionic, variational
+    p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
+    fe, lm = fermionic.Fermionic(p), variational.LocalMatrices(p)
+    ch = np.linspace(-0.5, 0.7, p.n_links)
+    for G in gi.random_links(p, 2, seed=8):
+        Nn = lm(G)["norm"]
+        Ge = fe.gamma_eff(G)
+        blk = np.zeros((p.n_links, 2, 2, p.K, p.K), dtype=complex)
+        for l in range(p.n_links):
+            s, t = fermionic._link_sites(p, l)
+            for a in range(2):
+                for b in range(2):
+                    i, j = 2 * s + a, 2 * t + b
+                    for (n, m), Gm in Ge.items():
+                        blk[l, a, b, n, m] = Nn[n, m] * (1.0 if i == j else -1j * Gm[i, j])
+        hop = fermionic.link_terms_from_block(p, G, blk)
+        H = optimize.local_energy({"norm": Nn[None], "hop": hop[None]}, np.zeros(1), c_hop=ch)[0]
+        assert np.abs(H - H.conj().T).max() <= 1e-13
+        got = np.conj(p.lam) @ H @ p.lam
+        want = np.sum(ch * 2 * fe.link_terms(G).real)
+        assert abs(got - want) <= 1e-12

@@ -414,3 +414,67 @@ def test_u1_field_rejects_other_groups():
     with pytest.raises(RuntimeError):
         ctx.chains_electric_field()
     ctx.close()
+
+
+@pytest.mark.parametrize("L,grp,n_v,K,prec,tol", [
+    (2, gi.Z2, 1, 2, 0, 1e-10),
+    (3, gi.U1, 1, 2, 0, 1e-10),    # odd torus: wrap-around links join equal charges
+    (2, gi.U1, 2, 3, 0, 1e-10),
+    (4, gi.U1, 1, 2, 1, 1e-4),
+])
+def test_link_terms_match_oracle(L, grp, n_v, K, prec, tol):
+    """Gauge-invariant link terms and their per-pair parts against the
+    oracle; the parts contract with lambda to the combined terms."""
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=61), precision=prec, seed=4, delay=8 if prec else 1)
+    if prec:
+        ctx.sample(2)
+    links = ctx.chains_links()
+    T, Tp = ctx.chains_link_terms(p.q_phys, pairs=True)
+    fe = fermionic.Fermionic(p)
+    for c in range(2):
+        ref = fe.link_terms(links[c])
+        assert np.abs(T[c] - ref).max() <= tol, np.abs(T[c] - ref).max()
+        con = np.einsum("n,lnm,m->l", np.conj(p.lam), Tp[c], p.lam)
+        assert np.abs(con - T[c]).max() <= tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("grp", [gi.Z2, gi.U1])
+def test_link_terms_gauge_invariant_on_gpu(grp):
+    """Chains started at G and at a gauge transform of G give the same link
+    terms (each from its own inverse), at a size the oracle does not run."""
+    p = gi.make_problem(8, grp, 1, 2, bond_scale=0.3)
+    G = gi.random_links(p, 1, seed=63)
+    rng = np.random.default_rng(5)
+    h = rng.uniform(0, 2 * np.pi, p.V) if grp == gi.U1 else rng.choice([-1, 1], p.V)
+    Gh = gi.gauge_transform(p, G, h)
+    ctx = ctx_for(p)
+    ctx.chains_init(np.ascontiguousarray(np.concatenate([G, Gh])), precision=0, seed=1)
+    T = ctx.chains_link_terms(p.q_phys)
+    assert np.abs(T[0]).max() > 1e-3
+    assert np.abs(T[1] - T[0]).max() <= 1e-10
+    ctx.close()
+
+
+def test_link_terms_device_buffers_and_errors():
+    torch = pytest.importorskip("torch")
+    from paper_2412_01737_gb300 import GGFError
+    p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=6), precision=0, seed=1)
+    T = ctx.chains_link_terms(p.q_phys)
+    dev = torch.zeros((2, p.n_links, 2), dtype=torch.float64, device="cuda")
+    ctx.chains_link_terms(p.q_phys, out=dev)
+    d = dev.cpu().numpy()
+    assert np.array_equal(d[..., 0] + 1j * d[..., 1], T)
+    with pytest.raises(GGFError):
+        ctx.chains_link_terms(np.zeros(p.V, dtype=np.int32))
+    ctx.close()
+    s = gi.make_problem(1, gi.SU2, 2, 1)
+    cs = ctx_for(s)
+    cs.chains_init(gi.random_links(s, 1, seed=2), precision=0, seed=1)
+    with pytest.raises(GGFError):
+        cs.chains_link_terms(np.ones(s.V, dtype=np.int32))
+    cs.close()
