@@ -30,7 +30,7 @@ Pinned (tests/test_oracle_variational.py): the site and (K = 1) link scores
 against central finite differences of log N(G) along commutant generators of
 the site and bond states (Z2, U(1), SU(2)); on the 2x2 Z2 lattice, for random lambda, the Hermitian forms
 built from exhaustive sums reproduce the direct exhaustive expectations of
-the plaquette, the link flip and the densities computed with that lambda; the generalised eigenvector minimises the energy
+the plaquette, the link flip, the densities and the link terms computed with that lambda; the generalised eigenvector minimises the energy
 over random lambda; the forms are Hermitian and Nbar positive definite.
 """
 from __future__ import annotations
@@ -56,7 +56,9 @@ class LocalMatrices:
     def __call__(self, links):
         """dict of K x K (or (n, K, K)) arrays divided by N_lambda0(G):
         'norm' N(G); 'plaquette' mean plaquette; 'electric' per link;
-        'density' per site (the bilinear c_2s c_2s+1)."""
+        'density' per site (the bilinear c_2s c_2s+1); 'hopping' per link
+        (Z2 and U(1): the gauge-invariant link term T_l; T_l^dag has the
+        conjugate transpose over n, m)."""
         p = self.p
         lnm = self.W.log_n_matrix(links)
         logN = weight.combine(lnm, p.lam)
@@ -71,6 +73,17 @@ class LocalMatrices:
             for s in range(p.V):
                 dens[s, n, m] = Nn[n, m] * (-1j) * G[2 * s, 2 * s + 1]
         out["density"] = dens
+        if p.group == weight.SU2:      # link terms are defined for Z2 and U(1)
+            return out
+        blk = np.zeros((p.n_links, 2, 2, p.K, p.K), dtype=complex)
+        for l in range(p.n_links):
+            s, t = fermionic._link_sites(p, l)
+            for a in range(2):
+                for b in range(2):
+                    i, j = 2 * s + a, 2 * t + b
+                    for (n, m), G in Ge.items():
+                        blk[l, a, b, n, m] = Nn[n, m] * (1.0 if i == j else -1j * G[i, j])
+        out["hopping"] = fermionic.link_terms_from_block(p, links, blk)
         return out
 
 

@@ -12,8 +12,12 @@ Hbar lambda = E Nbar lambda.  ``accumulate`` samples with the context's
 current lambda and estimates Hbar and Nbar for an energy
 
     E = c_plaquette <mean plaquette> + sum_l c_electric[l] <f_E,l>
-        + sum_s c_site[s] <c_2s c_2s+1> + sum_{l,a,b} c_link[l,a,b] <c_{2s+a} c_{2t+b}>
+        + sum_s c_site[s] <n_s> + sum_{l,a,b} c_link[l,a,b] <i c_{2s+a} c_{2t+b}>
         + sum_l c_hop[l] <T_l + T_l^dag>
+
+with the Hermitian operators n_s = (1 + i c_2s c_2s+1) / 2 and i c c (the
+Majorana bilinears themselves are anti-Hermitian), so that for real
+coefficients every local matrix is Hermitian
 
 (any coefficient may be omitted; T_l the gauge-invariant link term of
 ``GGF.chains_link_terms``, whose per-pair parts enter as T + T^H over the pair
@@ -45,9 +49,10 @@ def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric
     if c_electric is not None:
         H = H + np.einsum("l,clnm->cnm", np.asarray(c_electric, dtype=complex), pairs["electric"])
     if c_site is not None:
-        H = H + np.einsum("s,csnm->cnm", np.asarray(c_site, dtype=complex), pairs["site"])
+        cs = np.asarray(c_site, dtype=complex)
+        H = H + 0.5 * (cs.sum() * pairs["norm"] + 1j * np.einsum("s,csnm->cnm", cs, pairs["site"]))
     if c_link is not None:
-        H = H + np.einsum("lab,clabnm->cnm", np.asarray(c_link, dtype=complex), pairs["link"])
+        H = H + 1j * np.einsum("lab,clabnm->cnm", np.asarray(c_link, dtype=complex), pairs["link"])
     if c_hop is not None:
         T = np.einsum("l,clnm->cnm", np.asarray(c_hop, dtype=float), pairs["hop"])
         H = H + T + np.conj(np.swapaxes(T, 1, 2))

@@ -62,6 +62,10 @@ class _Stub:
         key = {PAIRS_NORM: "norm", PAIRS_ELECTRIC: "electric", PAIRS_SITE: "density"}[what]
         return np.array([d[key] for d in self.loc])
 
+    def chains_link_terms(self, charges, pairs=False):
+        assert pairs and np.array_equal(charges, self.p.q_phys)
+        return None, np.array([d["hopping"] for d in self.loc])
+
 
 def test_accumulate_contracts_the_energy():
     p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
@@ -69,9 +73,13 @@ def test_accumulate_contracts_the_energy():
     stub = _Stub(p, cfgs)
     ce = np.linspace(0.1, 0.8, p.n_links)
     cs = np.linspace(-0.3, 0.3, p.V)
-    H, N = optimize.accumulate(stub, 2, c_plaquette=-1.5, c_electric=ce, c_site=cs)
+    ch = np.linspace(-0.2, 0.4, p.n_links)
+    H, N = optimize.accumulate(stub, 2, c_plaquette=-1.5, c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
+    hop = [np.einsum("l,lnm->nm", ch, d["hopping"]) for d in stub.loc]
     want_H = np.mean([-1.5 * stub.sample(1)[0, c, 0] * d["norm"] + np.einsum("l,lnm->nm", ce, d["electric"])
-                      + np.einsum("s,snm->nm", cs, d["density"]) for c, d in enumerate(stub.loc)], axis=0)
+                      + np.einsum("s,snm->nm", cs, 0.5 * (d["norm"] + 1j * d["density"]))
+                      + hop[c] + hop[c].conj().T
+                      for c, d in enumerate(stub.loc)], axis=0)
     want_N = np.mean([d["norm"] for d in stub.loc], axis=0)
     assert np.abs(H - want_H).max() <= 1e-13
     assert np.abs(N - want_N).max() <= 1e-13

@@ -38,6 +38,11 @@ def test_forms_reproduce_direct_expectations(setup):
         fe = fermionic.Fermionic(q)
         ref_d = sum(wi * fe.bilinears(G)[0] for wi, G in zip(w, cfgs))
         assert np.abs(va.expectation(S["density"], S["norm"], lam) - ref_d).max() <= 1e-13
+        ref_t = sum(wi * fe.link_terms(G) for wi, G in zip(w, cfgs))
+        assert np.abs(ref_t).max() > 1e-3
+        assert np.abs(va.expectation(S["hopping"], S["norm"], lam) - ref_t).max() <= 1e-13
+        hop = S["hopping"] + np.conj(np.swapaxes(S["hopping"], 1, 2))      # T + T^dag
+        assert np.abs(va.expectation(hop, S["norm"], lam) - 2 * ref_t.real).max() <= 1e-13
 
 
 def test_linear_method_minimises_the_energy(setup):
@@ -54,6 +59,18 @@ def test_linear_method_minimises_the_energy(setup):
         assert va.expectation(H, S["norm"], z).real >= E0 - 1e-12
     # the sampling weights of the problem are not the optimum
     assert va.expectation(H, S["norm"], p.lam).real > E0 + 1e-3
+    # a lattice-gauge energy with every term: magnetic, electric, staggered
+    # mass (n_s = (1 + i c_2s c_2s+1) / 2; the bilinear itself is
+    # anti-Hermitian) and hopping (T + T^dag)
+    hop = S["hopping"].sum(axis=0)
+    H2 = (-1.0 * S["plaquette"] + 0.5 * S["electric"].sum(axis=0)
+          + 0.4 * np.einsum("s,snm->nm", p.q_phys.astype(float), 0.5 * (S["norm"] + 1j * S["density"]))
+          + 0.3 * (hop + hop.conj().T))
+    assert np.abs(H2 - H2.conj().T).max() <= 1e-12
+    E2, lam2 = va.linear_method(H2, S["norm"])
+    for _ in range(200):
+        z = rng.normal(size=p.K) + 1j * rng.normal(size=p.K)
+        assert va.expectation(H2, S["norm"], z).real >= E2 - 1e-12
 
 
 def test_sampled_matrices_estimate_the_energy(setup):
