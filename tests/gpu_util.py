@@ -1,8 +1,6 @@
 """Helpers shared by the GPU tests."""
 import numpy as np
 
-import ggf_inputs as gi
-
 
 def ctx_for(p):
     from paper_2412_01737_gb300 import GGF

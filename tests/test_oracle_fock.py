@@ -3,7 +3,6 @@ fermionic reordering and contraction (App. C worked example)."""
 import os
 
 import numpy as np
-import pytest
 import scipy.linalg
 
 import ggf_inputs as gi

@@ -1,6 +1,4 @@
 """Pin the oracle Pfaffian to closed forms and to numpy's determinant."""
-import itertools
-
 import numpy as np
 import pytest
 
