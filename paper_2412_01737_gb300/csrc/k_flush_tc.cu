@@ -42,11 +42,10 @@
 // its MMAs in flight and the TMEM is freed.
 #include <cstring>
 #include "ggf_ctx.h"
+#include "ggf_flush_layout.cuh"
 
 namespace {
 
-constexpr int KC = 8;                         // rank columns per stage (one MMA K step)
-constexpr int SBO = KC / 4 * 128;             // bytes between 8-row core-matrix groups
 constexpr int STAGES = 3;                     // split (MMA operand) stages
 constexpr int RAWS = 4, PD = 3;               // raw cp.async slots; stages of loads in flight ahead
 constexpr int NPROD = 8, NEPI = 8;            // producer and epilogue warps (+ one MMA warp)
@@ -69,10 +68,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// byte offset of (row, k) inside a K-major no-swizzle operand plane (KC wide)
-__device__ __forceinline__ uint32_t cm_off(int row, int k) {
-    return (uint32_t)((row >> 3) * SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
@@ -194,8 +189,9 @@ __device__ __forceinline__ void copy_plane(const float* src, int NP, int row0, i
     constexpr int PER = NR * 2 / PGROUP;
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-        const int idx = (int)threadIdx.x + t * PGROUP, row = idx >> 1, k = k0 + 4 * (idx & 1);
-        const int gr = row0 + row;
+        int row, kq;
+        stage_elem((int)threadIdx.x + t * PGROUP, row, kq);
+        const int gr = row0 + row, k = k0 + kq;
         const bool in = gr < N && k < K;
         const float* p = in ? src + pidx(gr, k, NP) : src;
         cp_async16(raw + (uint32_t)((slot0 + t) * PGROUP + threadIdx.x) * 16u, p, in ? 16u : 0u);
@@ -229,7 +225,8 @@ __device__ __forceinline__ void split_plane(const unsigned char* raw, int slot0,
     constexpr int PER = NR * 2 / PGROUP;
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-        const int idx = (int)threadIdx.x + t * PGROUP, row = idx >> 1, kq = 4 * (idx & 1);
+        int row, kq;
+        stage_elem((int)threadIdx.x + t * PGROUP, row, kq);
         const float4 x = *(const float4*)(raw + ((slot0 + t) * PGROUP + threadIdx.x) * 16);
         const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
         const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
