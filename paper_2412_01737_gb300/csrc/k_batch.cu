@@ -322,8 +322,11 @@ size_t steps_smem(int P, int r, int KRM, size_t cw_bytes) {
 // Grid (ceil(N / RB), family pairs, chains) with RB = 16 RPT rows per CTA,
 // 256 threads as 16 x 16.  A CTA stages its RB rows of V^T in shared memory
 // and rewrites them in place; per 128-wide output chunk, thread (ty, tx)
-// accumulates rows ty RPT .. + RPT - 1 x outputs tx 8 .. tx 8 + 7 over the
-// rank, with X^T staged 16 columns at a time.
+// accumulates rows ty RPT .. + RPT - 1 x outputs tx + 16 t (t = 0 .. 7) over
+// the rank, with X^T staged 16 columns at a time.  Interleaved outputs make
+// the 16 threads of a row read 16 consecutive elements of a staged X^T row
+// (contiguous blocks of 8 per thread put them 8 elements apart: 4- to 16-way
+// bank conflicts) and write 8 consecutive rank columns of a panel chunk.
 constexpr int AP_LDX = 132;   // X^T stage row length (128 outputs + pad, 16-byte rows)
 
 template <class T, int RPT>
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(256) batch_apply(int N, int fam_pairs, int KRM
 #pragma unroll
                 for (int u = 0; u < RPT; ++u) v[u] = Vs[(ty * RPT + u) * ld + b0 + bb];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) x[t] = Xs[bb * AP_LDX + tx * 8 + t];
+                for (int t = 0; t < 8; ++t) x[t] = Xs[bb * AP_LDX + tx + 16 * t];
 #pragma unroll
                 for (int u = 0; u < RPT; ++u)
 #pragma unroll
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(256) batch_apply(int N, int fam_pairs, int KRM
             if (ii >= nb) continue;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const int aa = a0 + tx * 8 + t;
+                const int aa = a0 + tx + 16 * t;
                 if (aa < kr) PanelIO<T>::st(Vt, NK, pidx(i0 + ii, aa, NP), acc[u][t]);
             }
         }
