@@ -24,19 +24,31 @@ coefficients every local matrix is Hermitian
 indices); the couplings, and thus the Hamiltonian, are the caller's.  ``linear_method`` solves for the new lambda, which
 ``GGF.init_gaussians`` takes before sampling again.
 
+``energy_gradient`` gives the derivative of any such energy along directions
+in the space of site and bond parameters (``rotate_sites``, ``rotate_bonds``:
+orthogonal rotations, which keep the Gaussians pure), from configurations
+sampled at the current parameters: for a problem p' near p,
+    E(p') = sum_i r_i h'(G_i) / sum_i r_i,   r_i = N'(G_i) / N(G_i),
+exactly for samples of p (Sec. 5.1: p(G) = N(G) / sum_G N(G)), with h' the
+local energy of the configuration under p'; central differences of this
+reweighted energy on the same samples estimate the gradient (every term,
+including the electric and fermionic ones and the dependence of the pair
+weights, at O(delta^2) plus the sampling error).
+
 ``wilson_score`` gives the gradient of a Wilson-loop energy with respect to
 the site blocks, as the covariance of the plaquette with the score
 d log N(G) / d D_s (``GGF.chains_score``); ``wilson_link_score`` does the same
-for the link blocks (for K = 1 the bond covariances).  Gradients of the
-electric and fermionic terms would also need the derivatives of their
-per-pair parts and are not provided.
+for the link blocks (for K = 1 the bond covariances).  For the other terms
+use ``energy_gradient``.
 """
 from __future__ import annotations
 
 import numpy as np
 import scipy.linalg
 
-from .ggf import PAIRS_ELECTRIC, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
+import dataclasses
+
+from .ggf import FP64, PAIRS_ELECTRIC, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
 
 
 def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric=None, c_site=None,
@@ -140,3 +152,87 @@ def energy(Hbar: np.ndarray, Nbar: np.ndarray, lam) -> float:
     """lambda^dag Hbar lambda / lambda^dag Nbar lambda (real part)."""
     lam = np.asarray(lam, dtype=complex)
     return float((np.conj(lam) @ Hbar @ lam / (np.conj(lam) @ Nbar @ lam)).real)
+
+
+def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
+                   charges=None):
+    """(log N(G), h(G)) for every configuration in links under ctx's current
+    problem: h(G) the per-configuration value of the energy of
+    ``local_energy`` (complex; its mean over p is real).  The configurations
+    become FP64 chains of ctx (replacing any it holds)."""
+    links = np.ascontiguousarray(links)
+    logN = np.asarray(ctx.logweight(links), dtype=float)
+    h = c_plaquette * np.asarray(ctx.observable(links), dtype=complex)
+    if c_electric is None and c_site is None and c_link is None and c_hop is None:
+        return logN, h
+    ctx.chains_init(links, precision=FP64, refresh_every=1 << 30, delay=1)
+    if c_electric is not None:
+        h = h + ctx.chains_electric() @ np.asarray(c_electric, dtype=complex)
+    if c_site is not None or c_link is not None:
+        site, link = ctx.chains_fermion()
+        if c_site is not None:
+            h = h + (0.5 * (1.0 + 1j * site)) @ np.asarray(c_site, dtype=complex)
+        if c_link is not None:
+            h = h + 1j * np.einsum("lab,clab->c", np.asarray(c_link, dtype=complex), link)
+    if c_hop is not None:
+        if charges is None:
+            raise ValueError("c_hop needs the sites' physical charges")
+        T = ctx.chains_link_terms(charges)
+        h = h + 2.0 * T.real @ np.asarray(c_hop, dtype=float)
+    return logN, h
+
+
+def reweighted_energy(logN0, logN1, h1, weights=None) -> float:
+    """sum_i w_i r_i h1_i / sum_i w_i r_i (real part), r_i = exp(logN1_i - logN0_i):
+    the energy under the problem of (logN1, h1) from configurations sampled
+    under that of logN0 (w_i = 1 for samples; pass p0(G) for an explicit list)."""
+    d = np.asarray(logN1, dtype=float) - np.asarray(logN0, dtype=float)
+    r = np.exp(d - d.max())
+    if weights is not None:
+        r = r * np.asarray(weights, dtype=float)
+    return float((np.sum(r * np.asarray(h1)) / np.sum(r)).real)
+
+
+def rotate_sites(p, generator, t, sites=None):
+    """The problem with the site covariances rotated, Gamma_s -> O Gamma_s O^T,
+    O = expm(t A) for the antisymmetric m_s x m_s generator A (in the commutant
+    of the group action, so the symmetry is kept), on the given sites (all by
+    default).  A pure state stays pure."""
+    O = scipy.linalg.expm(t * np.asarray(generator, dtype=float))
+    gs = np.array(p.gamma_site, copy=True)
+    for s in (range(gs.shape[0]) if sites is None else sites):
+        gs[s] = O @ gs[s] @ O.T
+    return dataclasses.replace(p, gamma_site=gs)
+
+
+def rotate_bonds(p, n, generator, t):
+    """The problem with bond state n rotated on every link, Gamma_{B_n} ->
+    O Gamma_{B_n} O^T, O = expm(t A) for an antisymmetric r x r generator A."""
+    O = scipy.linalg.expm(t * np.asarray(generator, dtype=float))
+    gb = np.array(p.gamma_bond, copy=True)
+    for l in range(gb.shape[1]):
+        gb[n, l] = O @ gb[n, l] @ O.T
+    return dataclasses.replace(p, gamma_bond=gb)
+
+
+def energy_gradient(ctx, p, links, directions, delta=1e-3, weights=None, **couplings):
+    """dE/dt at t = 0 along each direction (a callable t -> problem, e.g.
+    ``lambda t: rotate_sites(p, A, t)``), by central differences of the
+    reweighted energy on the configurations `links` sampled under p (or an
+    explicit list with weights p(G)).  couplings as for ``local_energies``.
+    It re-initialises ctx for every offset, so use a context other than the
+    sampling one; ctx is left holding p (with FP64 chains at `links` if a
+    coupling needed them).  Returns (E(p), gradient)."""
+    ctx.init_problem(p)
+    logN0, h0 = local_energies(ctx, links, **couplings)
+    e0 = reweighted_energy(logN0, logN0, h0, weights)
+    grad = []
+    for d in directions:
+        e = []
+        for t in (delta, -delta):
+            ctx.init_problem(d(t))
+            logN, h = local_energies(ctx, links, **couplings)
+            e.append(reweighted_energy(logN0, logN, h, weights))
+        grad.append((e[0] - e[1]) / (2.0 * delta))
+    ctx.init_problem(p)
+    return e0, np.array(grad)

@@ -110,3 +110,99 @@ def test_hopping_energy_is_twice_the_real_part():
         got = np.conj(p.lam) @ H @ p.lam
         want = np.sum(ch * 2 * fe.link_terms(G).real)
         assert abs(got - want) <= 1e-12
+
+
+class _OracleCtx:
+    """The binding calls that energy_gradient makes, answered by the oracle."""
+
+    def init_problem(self, q):
+        from oracle import electric, fermionic, weight
+        self.p, self.W = q, weight.Weights(q)
+        self.el, self.fe = electric.Electric(q), fermionic.Fermionic(q)
+        self.links = None
+
+    def logweight(self, links):
+        return np.array([self.W.log_norm(G) for G in links])
+
+    def observable(self, links):
+        from oracle.observables import plaquette_mean
+        return plaquette_mean(self.p.group, self.p.L, links)
+
+    def chains_init(self, links, **kw):
+        self.links = links
+
+    def chains_electric(self):
+        return np.array([self.el.f_electric(G) for G in self.links])
+
+    def chains_fermion(self):
+        out = [self.fe.bilinears(G) for G in self.links]
+        return np.array([o[0] for o in out]), np.array([o[1] for o in out])
+
+    def chains_link_terms(self, charges):
+        assert np.array_equal(charges, self.p.q_phys)
+        return np.array([self.fe.link_terms(G) for G in self.links])
+
+
+def _exact_energy(q, cfgs, ce, cs, ch):
+    from oracle import variational as va
+    S = va.exhaustive(q, cfgs)
+    hop = np.einsum("l,lnm->nm", ch, S["hopping"])
+    H = (-1.0 * S["plaquette"] + np.einsum("l,lnm->nm", ce, S["electric"])
+         + np.einsum("s,snm->nm", cs, 0.5 * (S["norm"] + 1j * S["density"])) + hop + hop.conj().T)
+    return float(va.expectation(H, S["norm"], q.lam).real)
+
+
+def test_reweighted_gradient_matches_exact_finite_differences():
+    """On the 2x2 Z2 lattice with every configuration weighted by p(G), the
+    reweighted energies at p(+-delta) equal the exhaustive expectations of
+    the Hermitian forms at those parameters (another route), for a site and
+    a bond direction and an energy with every term."""
+    from oracle import weight
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    cfgs = gi.all_z2_configs(p)
+    W = weight.Weights(p)
+    logs = np.array([W.log_norm(G) for G in cfgs])
+    w0 = np.exp(logs - logs.max())
+    w0 /= w0.sum()
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    Bg = rng.normal(size=(p.r, p.r))
+    Bg = Bg - Bg.T
+    ce = np.linspace(0.2, 0.6, p.n_links)
+    cs = 0.4 * p.q_phys.astype(float)
+    ch = 0.3 * np.ones(p.n_links)
+    dirs = [lambda t: optimize.rotate_sites(p, A, t), lambda t: optimize.rotate_bonds(p, 1, Bg, t)]
+    delta = 1e-3
+    e0, g = optimize.energy_gradient(_OracleCtx(), p, cfgs, dirs, delta=delta, weights=w0, c_plaquette=-1.0,
+                                     c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
+    assert abs(e0 - _exact_energy(p, cfgs, ce, cs, ch)) <= 1e-12
+    for k, d in enumerate(dirs):
+        fd = (_exact_energy(d(delta), cfgs, ce, cs, ch) - _exact_energy(d(-delta), cfgs, ce, cs, ch)) / (2 * delta)
+        assert abs(fd) > 1e-3
+        assert abs(g[k] - fd) <= 1e-9 * max(1.0, abs(fd))
+
+
+def test_reweighted_gradient_of_a_wilson_energy_matches_the_score():
+    """For a plaquette energy the reweighted central difference along a site
+    rotation agrees with the analytic gradient sum_s tr(C_s^T dD_s/dt),
+    C_s = E_p[(W - <W>) S_s] with the site scores S_s (O(delta^2))."""
+    from oracle import variational as va, weight
+    from oracle.observables import plaquette_mean
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    cfgs = gi.all_z2_configs(p)
+    W = weight.Weights(p)
+    logs = np.array([W.log_norm(G) for G in cfgs])
+    w0 = np.exp(logs - logs.max())
+    w0 /= w0.sum()
+    A = np.random.default_rng(4).normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    _, g = optimize.energy_gradient(_OracleCtx(), p, cfgs, [lambda t: optimize.rotate_sites(p, A, t)],
+                                    delta=1e-4, weights=w0, c_plaquette=1.0)
+    pl = plaquette_mean(p.group, p.L, cfgs)
+    mw = np.sum(w0 * pl)
+    C = sum(wi * (x - mw) * va.score_sites(p, G) for wi, x, G in zip(w0, pl, cfgs))
+    dD = [(A @ p.gamma_site[s] - p.gamma_site[s] @ A)[2:, 2:] for s in range(p.V)]
+    want = sum(np.sum(C[s] * dD[s]) for s in range(p.V))
+    assert abs(want) > 1e-4
+    assert abs(g[0] - want) <= 1e-6

@@ -506,3 +506,45 @@ def test_link_terms_device_buffers_and_errors():
     with pytest.raises(GGFError):
         cs.chains_link_terms(np.ones(s.V, dtype=np.int32))
     cs.close()
+
+
+def test_reweighted_energy_gradient_on_gpu():
+    """energy_gradient through the GPU context (log-weights, Wilson loops,
+    electric, fermionic and link terms of every configuration), with the 256
+    configurations of the 2x2 Z2 lattice weighted by p(G): equals the
+    central difference of the oracle's exhaustive energies along a site and
+    a bond rotation."""
+    from oracle import variational as va, weight
+    from paper_2412_01737_gb300 import optimize
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    cfgs = np.ascontiguousarray(gi.all_z2_configs(p))
+    W = weight.Weights(p)
+    logs = np.array([W.log_norm(G) for G in cfgs])
+    w0 = np.exp(logs - logs.max())
+    w0 /= w0.sum()
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    Bg = rng.normal(size=(p.r, p.r))
+    Bg = Bg - Bg.T
+    ce = np.linspace(0.2, 0.6, p.n_links)
+    cs = 0.4 * p.q_phys.astype(float)
+    ch = 0.3 * np.ones(p.n_links)
+
+    def exact(q):
+        S = va.exhaustive(q, cfgs)
+        hop = np.einsum("l,lnm->nm", ch, S["hopping"])
+        H = (-1.0 * S["plaquette"] + np.einsum("l,lnm->nm", ce, S["electric"])
+             + np.einsum("s,snm->nm", cs, 0.5 * (S["norm"] + 1j * S["density"])) + hop + hop.conj().T)
+        return float(va.expectation(H, S["norm"], q.lam).real)
+
+    dirs = [lambda t: optimize.rotate_sites(p, A, t), lambda t: optimize.rotate_bonds(p, 1, Bg, t)]
+    delta = 1e-3
+    ctx = ctx_for(p)
+    e0, g = optimize.energy_gradient(ctx, p, cfgs, dirs, delta=delta, weights=w0, c_plaquette=-1.0,
+                                     c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
+    ctx.close()
+    assert abs(e0 - exact(p)) <= 1e-9
+    for k, d in enumerate(dirs):
+        fd = (exact(d(delta)) - exact(d(-delta))) / (2 * delta)
+        assert abs(g[k] - fd) <= 1e-6 * max(1.0, abs(fd)), (k, g[k], fd)
