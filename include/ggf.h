@@ -327,7 +327,8 @@ ggf_status ggf_chains_fermion4(ggf_ctx* ctx, double* out, int mem, void* stream)
  *   GGF_PAIRS_SITE      items = V: -i Gamma_eff^nm[2s, 2s+1];
  *   GGF_PAIRS_LINK      items = 2V x 2 x 2: the link blocks of
  *                       ggf_chains_fermion, per pair.
- * Contracting with lambda_n^* lambda_m gives the combined quantity.  Pending
+ * Contracting with lambda_n^* lambda_m gives the combined quantity (the
+ * gauge-invariant link terms' parts come from ggf_chains_link_terms).  Pending
  * delayed updates are folded into W first.  GGF_EINVAL for an unknown `what`
  * or a null `out`, GGF_ESTATE before ggf_chains_init. */
 #define GGF_PAIRS_NORM 0
