@@ -26,7 +26,8 @@ indices); the couplings, and thus the Hamiltonian, are the caller's.  ``linear_m
 
 ``energy_gradient`` gives the derivative of any such energy along directions
 in the space of site and bond parameters (``rotate_sites``, ``rotate_bonds``:
-orthogonal rotations, which keep the Gaussians pure), from configurations
+orthogonal rotations, which keep the Gaussians pure; ``u1_generator``
+projects a generator onto the U(1)-symmetric ones), from configurations
 sampled at the current parameters: for a problem p' near p,
     E(p') = sum_i r_i h'(G_i) / sum_i r_i,   r_i = N'(G_i) / N(G_i),
 exactly for samples of p (Sec. 5.1: p(G) = N(G) / sum_G N(G)), with h' the
@@ -191,6 +192,27 @@ def reweighted_energy(logN0, logN1, h1, weights=None) -> float:
     if weights is not None:
         r = r * np.asarray(weights, dtype=float)
     return float((np.sum(r * np.asarray(h1)) / np.sum(r)).real)
+
+
+def u1_generator(A, charges):
+    """The part of an antisymmetric generator A (Majorana basis, mode j on
+    Majoranas 2j, 2j+1) that commutes with the U(1) action, which turns the
+    Majorana pair of a mode of charge q by the angle q phi: the average of
+    R(phi)^T A R(phi) over phi.  Its entries are trigonometric polynomials of
+    degree at most 2 max|q|, so 4 max|q| + 2 equally spaced angles give the
+    average exactly.  Rotations it generates keep a symmetric state
+    symmetric (site charges: the physical mode, then the virtual modes)."""
+    q = np.asarray(charges, dtype=float)
+    n_phi = 4 * int(np.max(np.abs(q))) + 2
+    out = np.zeros_like(np.asarray(A, dtype=float))
+    for k in range(n_phi):
+        phi = 2.0 * np.pi * k / n_phi
+        R = np.zeros_like(out)
+        for j, qj in enumerate(q):
+            c, sn = np.cos(qj * phi), np.sin(qj * phi)
+            R[2 * j:2 * j + 2, 2 * j:2 * j + 2] = [[c, sn], [-sn, c]]
+        out += R.T @ A @ R
+    return out / n_phi
 
 
 def rotate_sites(p, generator, t, sites=None):

@@ -206,3 +206,32 @@ def test_reweighted_gradient_of_a_wilson_energy_matches_the_score():
     want = sum(np.sum(C[s] * dD[s]) for s in range(p.V))
     assert abs(want) > 1e-4
     assert abs(g[0] - want) <= 1e-6
+
+
+def test_u1_generator_keeps_the_symmetry():
+    """Rotating one sublattice's site covariance with a projected generator
+    keeps it invariant under the U(1) action and keeps log N(G) gauge
+    invariant; the unprojected generator breaks both."""
+    from oracle import weight
+    p = gi.make_problem(2, gi.U1, 1, 2, bond_scale=0.3)
+    plus = [s for s in range(p.V) if p.q_phys[s] > 0]
+    q = gi.site_charges(p.n_v, 1)
+    rng = np.random.default_rng(6)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    Ap = optimize.u1_generator(A, q)
+    assert np.abs(Ap + Ap.T).max() <= 1e-14
+    assert np.abs(optimize.u1_generator(Ap, q) - Ap).max() <= 1e-13       # a projection
+    G = gi.random_links(p, 1, seed=3)
+    h = rng.uniform(0, 2 * np.pi, p.V)
+    Gh = gi.gauge_transform(p, G, h)
+    for gen, symmetric in ((Ap, True), (A, False)):
+        r = optimize.rotate_sites(p, gen, 0.3, sites=plus)
+        R = gi._rotation(q, 0.7)
+        inv = np.abs(R @ r.gamma_site[plus[0]] @ R.T - r.gamma_site[plus[0]]).max()
+        W = weight.Weights(r)
+        gauge = abs(W.log_norm(G[0]) - W.log_norm(Gh[0]))
+        if symmetric:
+            assert inv <= 1e-12 and gauge <= 1e-10
+        else:
+            assert inv > 1e-3 and gauge > 1e-6
