@@ -36,6 +36,9 @@ reweighted energy on the same samples estimate the gradient (every term,
 including the electric and fermionic ones and the dependence of the pair
 weights, at O(delta^2) plus the sampling error).
 
+``descend`` alternates the exact lambda update with gradient steps along
+given parameter directions, from the configurations a sampler returns.
+
 ``wilson_score`` gives the gradient of a Wilson-loop energy with respect to
 the site blocks, as the covariance of the plaquette with the score
 d log N(G) / d D_s (``GGF.chains_score``); ``wilson_link_score`` does the same
@@ -96,6 +99,58 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
         Nbar = Nbar + pairs["norm"].sum(axis=0)
         n += H.shape[0]
     return Hbar / n, Nbar / n
+
+
+def forms(ctx, links, weights=None, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
+          charges=None):
+    """(Hbar, Nbar) as in ``accumulate``, from an explicit list of
+    configurations (samples of ctx's problem, or every configuration with
+    weights p(G)): they become FP64 chains of ctx, whose per-pair parts are
+    averaged."""
+    if c_hop is not None and charges is None:
+        raise ValueError("c_hop needs the sites' physical charges")
+    links = np.ascontiguousarray(links)
+    ctx.chains_init(links, precision=FP64, refresh_every=1 << 30, delay=1)
+    pairs = {"norm": ctx.chains_pairs(PAIRS_NORM)}
+    if c_electric is not None:
+        pairs["electric"] = ctx.chains_pairs(PAIRS_ELECTRIC)
+    if c_site is not None:
+        pairs["site"] = ctx.chains_pairs(PAIRS_SITE)
+    if c_link is not None:
+        pairs["link"] = ctx.chains_pairs(PAIRS_LINK)
+    if c_hop is not None:
+        pairs["hop"] = ctx.chains_link_terms(charges, pairs=True)[1]
+    pl = np.asarray(ctx.observable(links), dtype=float)
+    H = local_energy(pairs, pl, c_plaquette, c_electric, c_site, c_link, c_hop)
+    w = np.full(len(links), 1.0 / len(links)) if weights is None else np.asarray(weights, float) / np.sum(weights)
+    return np.einsum("c,cnm->nm", w, H), np.einsum("c,cnm->nm", w, pairs["norm"])
+
+
+def descend(ctx, p, sampler, directions, n_iter, lr, delta=1e-3, **couplings):
+    """Variational optimisation of lambda and of the site and bond parameters.
+    Per iteration: configurations from sampler(p) -> (links, weights or None);
+    lambda <- the lowest generalised eigenvector of their forms (exact for
+    the sampled Gaussians); fresh configurations for the new problem; one
+    gradient step t_k = -lr dE/dt_k along each direction (callables
+    (p, t) -> problem, e.g. ``lambda q, t: rotate_sites(q, A, t)``), applied
+    in order.  ctx is re-initialised throughout (not a sampling context).
+    Returns the final problem and the energies after each lambda update."""
+    energies = []
+    for _ in range(n_iter):
+        links, w = sampler(p)
+        ctx.init_problem(p)
+        H, N = forms(ctx, links, w, **couplings)
+        E, lam = linear_method(H, N)
+        energies.append(E)
+        p = dataclasses.replace(p, lam=np.asarray(lam, dtype=np.complex128))
+        if not directions:
+            continue
+        links, w = sampler(p)
+        dirs = [(lambda t, d=d, q=p: d(q, t)) for d in directions]
+        _, g = energy_gradient(ctx, p, links, dirs, delta=delta, weights=w, **couplings)
+        for d, gk in zip(directions, g):
+            p = d(p, -lr * gk)
+    return p, energies
 
 
 def wilson_score(ctx, n_sweeps: int):

@@ -138,9 +138,20 @@ class _OracleCtx:
         out = [self.fe.bilinears(G) for G in self.links]
         return np.array([o[0] for o in out]), np.array([o[1] for o in out])
 
-    def chains_link_terms(self, charges):
+    def chains_link_terms(self, charges, pairs=False):
         assert np.array_equal(charges, self.p.q_phys)
-        return np.array([self.fe.link_terms(G) for G in self.links])
+        T = np.array([self.fe.link_terms(G) for G in self.links])
+        if not pairs:
+            return T
+        from oracle import variational
+        lm = variational.LocalMatrices(self.p)
+        return T, np.array([lm(G)["hopping"] for G in self.links])
+
+    def chains_pairs(self, what):
+        from oracle import variational
+        lm = variational.LocalMatrices(self.p)
+        key = {PAIRS_NORM: "norm", PAIRS_ELECTRIC: "electric", PAIRS_SITE: "density"}[what]
+        return np.array([lm(G)[key] for G in self.links])
 
 
 def _exact_energy(q, cfgs, ce, cs, ch):
@@ -235,3 +246,45 @@ def test_u1_generator_keeps_the_symmetry():
             assert inv <= 1e-12 and gauge <= 1e-10
         else:
             assert inv > 1e-3 and gauge > 1e-6
+
+
+
+def test_descend_lowers_the_energy():
+    """Two iterations of lambda updates and gradient steps along a site and a
+    bond rotation on the 2x2 Z2 lattice (every configuration, weighted by
+    p(G)): each lambda update is the exact optimum for its Gaussians, and
+    the steps lower the exact energy further."""
+    from oracle import weight
+    p = gi.make_problem(2, gi.Z2, 1, 2, bond_scale=0.3)
+    cfgs = gi.all_z2_configs(p)
+
+    def sampler(q):
+        W = weight.Weights(q)
+        logs = np.array([W.log_norm(G) for G in cfgs])
+        w = np.exp(logs - logs.max())
+        return cfgs, w / w.sum()
+
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = 0.2 * (A - A.T)
+    Bg = rng.normal(size=(p.r, p.r))
+    Bg = 0.2 * (Bg - Bg.T)
+    ce = 0.5 * np.ones(p.n_links)
+    cs = 0.4 * p.q_phys.astype(float)
+    ch = 0.3 * np.ones(p.n_links)
+    kw = dict(c_plaquette=-1.0, c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
+    dirs = [lambda q, t: optimize.rotate_sites(q, A, t), lambda q, t: optimize.rotate_bonds(q, 1, Bg, t)]
+    e_start = _exact_energy(p, cfgs, ce, cs, ch)
+    q, hist = optimize.descend(_OracleCtx(), p, sampler, dirs, n_iter=2, lr=0.05, **kw)
+    # the first lambda update is the exact optimum for the starting Gaussians
+    from oracle import variational as va
+    S = va.exhaustive(p, cfgs)
+    hop = np.einsum("l,lnm->nm", ch, S["hopping"])
+    H = (-1.0 * S["plaquette"] + np.einsum("l,lnm->nm", ce, S["electric"])
+         + np.einsum("s,snm->nm", cs, 0.5 * (S["norm"] + 1j * S["density"])) + hop + hop.conj().T)
+    E0, _ = va.linear_method(H, S["norm"])
+    assert abs(hist[0] - E0) <= 1e-9
+    assert hist[0] < e_start - 1.0
+    e_final = _exact_energy(q, cfgs, ce, cs, ch)
+    assert hist[1] < hist[0] - 1e-4
+    assert e_final < hist[1] + 1e-9
