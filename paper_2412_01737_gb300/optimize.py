@@ -1,4 +1,5 @@
-"""Optimal superposition weights lambda for a given energy.
+"""Variational optimisation: the superposition weights lambda and the site
+and bond parameters for a given energy.
 
 For fixed Gaussians every per-configuration quantity of Secs. 5.1-5.3 is a
 Hermitian form in lambda, so with the per-pair parts that
@@ -17,12 +18,13 @@ current lambda and estimates Hbar and Nbar for an energy
 
 with the Hermitian operators n_s = (1 + i c_2s c_2s+1) / 2 and i c c (the
 Majorana bilinears themselves are anti-Hermitian), so that for real
-coefficients every local matrix is Hermitian
-
-(any coefficient may be omitted; T_l the gauge-invariant link term of
-``GGF.chains_link_terms``, whose per-pair parts enter as T + T^H over the pair
-indices); the couplings, and thus the Hamiltonian, are the caller's.  ``linear_method`` solves for the new lambda, which
-``GGF.init_gaussians`` takes before sampling again.
+coefficients every local matrix is Hermitian.  Any coefficient may be
+omitted; T_l is the gauge-invariant link term of ``GGF.chains_link_terms``,
+whose per-pair parts enter as T + T^H over the pair indices.  The couplings,
+and thus the Hamiltonian, are the caller's.  ``linear_method`` solves for the
+new lambda, which ``GGF.init_gaussians`` takes before sampling again;
+``forms`` does what ``accumulate`` does for an explicit list of
+configurations.
 
 ``energy_gradient`` gives the derivative of any such energy along directions
 in the space of site and bond parameters (``rotate_sites``, ``rotate_bonds``:
@@ -47,10 +49,10 @@ use ``energy_gradient``.
 """
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 import scipy.linalg
-
-import dataclasses
 
 from .ggf import FP64, PAIRS_ELECTRIC, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
 
