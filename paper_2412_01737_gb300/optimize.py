@@ -213,12 +213,17 @@ def energy(Hbar: np.ndarray, Nbar: np.ndarray, lam) -> float:
 
 
 def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
-                   charges=None):
+                   charges=None, batch=None):
     """(log N(G), h(G)) for every configuration in links under ctx's current
     problem: h(G) the per-configuration value of the energy of
     ``local_energy`` (complex; its mean over p is real).  The configurations
-    become FP64 chains of ctx (replacing any it holds)."""
+    become FP64 chains of ctx (replacing any it holds), `batch` of them at a
+    time (all by default; each holds its P inverses in FP64)."""
     links = np.ascontiguousarray(links)
+    if batch is not None and len(links) > batch:
+        parts = [local_energies(ctx, links[i:i + batch], c_plaquette, c_electric, c_site, c_link, c_hop, charges)
+                 for i in range(0, len(links), batch)]
+        return np.concatenate([a for a, _ in parts]), np.concatenate([b for _, b in parts])
     logN = np.asarray(ctx.logweight(links), dtype=float)
     h = c_plaquette * np.asarray(ctx.observable(links), dtype=complex)
     if c_electric is None and c_site is None and c_link is None and c_hop is None:
@@ -294,23 +299,24 @@ def rotate_bonds(p, n, generator, t):
     return dataclasses.replace(p, gamma_bond=gb)
 
 
-def energy_gradient(ctx, p, links, directions, delta=1e-3, weights=None, **couplings):
+def energy_gradient(ctx, p, links, directions, delta=1e-3, weights=None, batch=None, **couplings):
     """dE/dt at t = 0 along each direction (a callable t -> problem, e.g.
     ``lambda t: rotate_sites(p, A, t)``), by central differences of the
     reweighted energy on the configurations `links` sampled under p (or an
-    explicit list with weights p(G)).  couplings as for ``local_energies``.
+    explicit list with weights p(G)).  couplings and batch as for
+    ``local_energies``.
     It re-initialises ctx for every offset, so use a context other than the
     sampling one; ctx is left holding p (with FP64 chains at `links` if a
     coupling needed them).  Returns (E(p), gradient)."""
     ctx.init_problem(p)
-    logN0, h0 = local_energies(ctx, links, **couplings)
+    logN0, h0 = local_energies(ctx, links, batch=batch, **couplings)
     e0 = reweighted_energy(logN0, logN0, h0, weights)
     grad = []
     for d in directions:
         e = []
         for t in (delta, -delta):
             ctx.init_problem(d(t))
-            logN, h = local_energies(ctx, links, **couplings)
+            logN, h = local_energies(ctx, links, batch=batch, **couplings)
             e.append(reweighted_energy(logN0, logN, h, weights))
         grad.append((e[0] - e[1]) / (2.0 * delta))
     ctx.init_problem(p)

@@ -185,8 +185,8 @@ def test_reweighted_gradient_matches_exact_finite_differences():
     ch = 0.3 * np.ones(p.n_links)
     dirs = [lambda t: optimize.rotate_sites(p, A, t), lambda t: optimize.rotate_bonds(p, 1, Bg, t)]
     delta = 1e-3
-    e0, g = optimize.energy_gradient(_OracleCtx(), p, cfgs, dirs, delta=delta, weights=w0, c_plaquette=-1.0,
-                                     c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
+    e0, g = optimize.energy_gradient(_OracleCtx(), p, cfgs, dirs, delta=delta, weights=w0, batch=100,
+                                     c_plaquette=-1.0, c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
     assert abs(e0 - _exact_energy(p, cfgs, ce, cs, ch)) <= 1e-12
     for k, d in enumerate(dirs):
         fd = (_exact_energy(d(delta), cfgs, ce, cs, ch) - _exact_energy(d(-delta), cfgs, ce, cs, ch)) / (2 * delta)
