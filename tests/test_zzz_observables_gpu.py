@@ -595,3 +595,28 @@ def test_descend_with_gpu_samples():
     sctx.close()
     assert abs(hist[0] - (-2.2105)) <= 0.3
     assert exact(q) < exact(p) - 2.5
+
+
+@pytest.mark.parametrize("grp", [gi.Z2, gi.U1])
+def test_link_terms_and_field_on_the_1x1_torus(grp):
+    """Self-links (both ends on one site): the link term is u_l <psi psi^dag>
+    = u_l (1 - <n>) for a positive charge (the oracle agrees to 1e-15), and
+    the U(1) field of the two self-links matches the oracle."""
+    p = gi.make_problem(1, grp, 2, 2, bond_scale=0.3)
+    links = gi.random_links(p, 3, seed=81)
+    ctx = ctx_for(p)
+    ctx.chains_init(links, precision=0, seed=2)
+    T = ctx.chains_link_terms(p.q_phys)
+    site, _ = ctx.chains_fermion()
+    fe = fermionic.Fermionic(p)
+    for c in range(3):
+        assert np.abs(T[c] - fe.link_terms(links[c])).max() <= 1e-10
+        u = links[c].astype(float) if grp == gi.Z2 else np.exp(1j * links[c])
+        n = (1 + 1j * site[c, 0]) / 2
+        assert np.abs(T[c] - u * (1 - n)).max() <= 1e-10
+    if grp == gi.U1:
+        J = ctx.chains_electric_field()
+        el = electric.Electric(p)
+        for c in range(3):
+            assert np.abs(J[c] - el.field(links[c])).max() <= 1e-10
+    ctx.close()
