@@ -34,3 +34,22 @@ def test_u1_16x16_k4_batched_fp32():
     tracked = obs[-1, ::8, 1]
     assert np.abs(tracked - fresh).max() <= 1e-5 * np.abs(fresh).max() + 1e-3
     ctx.close()
+
+
+def test_u1_16x16_fermion_properties_fp32():
+    """At the benchmark's lattice and n_v, properties that hold in every
+    configuration whatever the size: the Majorana bilinears of a Hermitian
+    state are imaginary (i <c_a c_b> real), the densities lie in [0, 1], and
+    the staggered charge sum_s q_s <n_s> vanishes (charge-conserving site
+    tensors, neutral bond pairs)."""
+    p = gi.make_problem(16, gi.U1, 2, 2, seed=20241202, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 4, seed=5), precision=1, refresh_every=1 << 30, seed=3, delay=16)
+    ctx.sample(1)
+    site, link = ctx.chains_fermion()
+    n = (1 + 1j * site) / 2
+    assert np.abs(site.real).max() <= 1e-4
+    assert np.abs(link.real).max() <= 1e-4
+    assert n.real.min() >= -1e-4 and n.real.max() <= 1 + 1e-4
+    assert np.abs(n @ p.q_phys).max() <= 1e-3
+    ctx.close()
