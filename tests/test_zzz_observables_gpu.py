@@ -620,3 +620,24 @@ def test_link_terms_and_field_on_the_1x1_torus(grp):
         for c in range(3):
             assert np.abs(J[c] - el.field(links[c])).max() <= 1e-10
     ctx.close()
+
+
+def test_loop_and_pair_argument_errors():
+    """Rejected arguments come back as errors with the context still usable:
+    loops larger than the lattice, an unknown per-pair quantity; an empty
+    batch of configurations is a no-op."""
+    from paper_2412_01737_gb300 import GGFError
+    p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
+    links = np.ascontiguousarray(gi.random_links(p, 2, seed=7))
+    ctx = ctx_for(p)
+    with pytest.raises(GGFError):
+        ctx.wilson_loop(links, 4, 1)
+    with pytest.raises(GGFError):
+        ctx.wilson_loop(links, 1, 0)
+    assert ctx.wilson_loop(np.ascontiguousarray(links[:0]), 1, 1).shape == (0,)
+    ctx.chains_init(links, precision=0, seed=1)
+    with pytest.raises(GGFError):
+        ctx.chains_pairs(7, out=np.zeros((2, p.K, p.K, 2)))
+    from oracle.observables import wilson_loop_values
+    assert np.abs(ctx.wilson_loop(links, 3, 3) - wilson_loop_values(gi.U1, 3, links, 3, 3).mean(axis=1)).max() <= 1e-13
+    ctx.close()
