@@ -641,3 +641,33 @@ def test_loop_and_pair_argument_errors():
     from oracle.observables import wilson_loop_values
     assert np.abs(ctx.wilson_loop(links, 3, 3) - wilson_loop_values(gi.U1, 3, links, 3, 3).mean(axis=1)).max() <= 1e-13
     ctx.close()
+
+
+def test_u1_gradient_on_gpu_matches_oracle_on_the_same_samples():
+    """The reweighted gradient along a U(1)-symmetric site rotation from the
+    GPU (log-weights, Wilson loops, electric, fermionic and link terms of
+    every sample under the offset parameters) against the same estimator
+    evaluated by the oracle on the same sampled configurations (3x3 torus,
+    K = 2): equal up to rounding."""
+    from paper_2412_01737_gb300 import optimize
+    from tests.test_optimize import _OracleCtx
+    p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
+    sctx = ctx_for(p)
+    sctx.chains_init(gi.random_links(p, 64, seed=5), precision=0, seed=4)
+    sctx.sample(3)
+    links = np.ascontiguousarray(sctx.chains_links())
+    sctx.close()
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    plus = [s for s in range(p.V) if p.q_phys[s] > 0]
+    Ap = optimize.u1_generator(A, gi.site_charges(p.n_v, 1))
+    dirs = [lambda t: optimize.rotate_sites(p, Ap, t, sites=plus)]
+    kw = dict(c_plaquette=-1.0, c_electric=0.5 * np.ones(p.n_links), c_site=0.4 * p.q_phys.astype(float),
+              c_hop=0.3 * np.ones(p.n_links), charges=p.q_phys)
+    gctx = ctx_for(p)
+    e_gpu, g_gpu = optimize.energy_gradient(gctx, p, links, dirs, **kw)
+    gctx.close()
+    e_ref, g_ref = optimize.energy_gradient(_OracleCtx(), p, links, dirs, **kw)
+    assert abs(e_gpu - e_ref) <= 1e-10 * max(1.0, abs(e_ref))
+    assert abs(g_gpu[0] - g_ref[0]) <= 1e-6 * max(1.0, abs(g_ref[0]))
