@@ -29,7 +29,8 @@ configurations.
 ``energy_gradient`` gives the derivative of any such energy along directions
 in the space of site and bond parameters (``rotate_sites``, ``rotate_bonds``:
 orthogonal rotations, which keep the Gaussians pure; ``u1_generator``
-projects a generator onto the U(1)-symmetric ones), from configurations
+projects a generator onto the U(1)-symmetric ones, ``commutant_generator``
+onto those of any group given its generators), from configurations
 sampled at the current parameters: for a problem p' near p,
     E(p') = sum_i r_i h'(G_i) / sum_i r_i,   r_i = N'(G_i) / N(G_i),
 exactly for samples of p (Sec. 5.1: p(G) = N(G) / sum_G N(G)), with h' the
@@ -275,6 +276,35 @@ def u1_generator(A, charges):
             R[2 * j:2 * j + 2, 2 * j:2 * j + 2] = [[c, sn], [-sn, c]]
         out += R.T @ A @ R
     return out / n_phi
+
+
+def commutant_generator(A, generators, tol=1e-10):
+    """Orthogonal (Frobenius) projection of an antisymmetric A onto the
+    antisymmetric matrices that commute with every given generator of a
+    group action (so(m) matrices, e.g. the SU(2) action on a site's
+    doublets).  C(X) = sum_a [T_a, [T_a, X]] maps antisymmetric matrices to
+    antisymmetric ones, is symmetric and negative semi-definite, and vanishes
+    exactly on that commutant, so the projection is onto C's null space."""
+    A = np.asarray(A, dtype=float)
+    n = A.shape[0]
+    iu = np.triu_indices(n, 1)
+    basis = np.zeros((len(iu[0]), n, n))
+    for k, (a, b) in enumerate(zip(*iu)):
+        basis[k, a, b], basis[k, b, a] = 2 ** -0.5, -(2 ** -0.5)
+    Ts = [np.asarray(T, dtype=float) for T in generators]
+
+    def C(X):
+        out = np.zeros_like(X)
+        for T in Ts:
+            Y = T @ X - X @ T
+            out += T @ Y - Y @ T
+        return out
+
+    Cm = np.array([[np.sum(Bi * C(Bj)) for Bj in basis] for Bi in basis])
+    w, v = np.linalg.eigh(0.5 * (Cm + Cm.T))
+    null = v[:, np.abs(w) <= tol * max(1.0, np.abs(w).max())]
+    coef = np.einsum("kab,ab->k", basis, A)
+    return np.einsum("k,kab->ab", null @ (null.T @ coef), basis)
 
 
 def rotate_sites(p, generator, t, sites=None):

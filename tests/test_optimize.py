@@ -288,3 +288,38 @@ def test_descend_lowers_the_energy():
     e_final = _exact_energy(q, cfgs, ce, cs, ch)
     assert hist[1] < hist[0] - 1e-4
     assert e_final < hist[1] + 1e-9
+
+
+def test_commutant_generator_for_su2_keeps_gauge_invariance():
+    """Projected onto the commutant of the SU(2) action on a site's doublets,
+    a generator commutes with that action (and the projection is
+    idempotent); rotating the site covariances with it keeps log N(G)
+    invariant under SU(2) gauge transformations, which the unprojected
+    generator breaks.  For a U(1) action it agrees with u1_generator."""
+    from oracle import weight
+    p = gi.make_problem(1, gi.SU2, 2, 1, bond_scale=0.3)
+    gens = gi._su2_generators(gi._site_slots_su2(p.n_v))
+    rng = np.random.default_rng(12)
+    A = rng.normal(size=(p.m_s, p.m_s))
+    A = A - A.T
+    X = optimize.commutant_generator(A, gens)
+    assert np.abs(X + X.T).max() <= 1e-13
+    assert max(np.abs(T @ X - X @ T).max() for T in gens) <= 1e-10
+    assert np.abs(optimize.commutant_generator(X, gens) - X).max() <= 1e-10
+    assert np.abs(X).max() > 1e-2
+    G = gi.random_links(p, 1, seed=4)
+    h = np.array([gi._quat_of(gi.su2(q)) for q in rng.normal(size=(p.V, 4))])
+    h = h / np.linalg.norm(h, axis=1, keepdims=True)
+    Gh = gi.gauge_transform(p, G, h)
+    for gen, symmetric in ((X, True), (A, False)):
+        W = weight.Weights(optimize.rotate_sites(p, gen, 0.3))
+        d = abs(W.log_norm(G[0]) - W.log_norm(Gh[0]))
+        assert (d <= 1e-10) if symmetric else (d > 1e-6)
+    # U(1): the same projection as the exact group average
+    q = gi.site_charges(1, 1)
+    T = np.zeros((len(q) * 2, len(q) * 2))
+    for j, qj in enumerate(q):
+        T[2 * j, 2 * j + 1], T[2 * j + 1, 2 * j] = qj, -qj
+    B = rng.normal(size=T.shape)
+    B = B - B.T
+    assert np.abs(optimize.commutant_generator(B, [T]) - optimize.u1_generator(B, q)).max() <= 1e-10
