@@ -117,3 +117,29 @@ def test_checkpoint_resume_bit_exact(tmp_path):
     ctx2.close()
     assert np.array_equal(la, lb)
     assert np.array_equal(a[:, :, 2], b[:, :, 2])
+
+
+def test_su2_gradient_on_gpu_matches_oracle_on_the_same_samples():
+    """The reweighted gradient along an SU(2)-symmetric site rotation
+    (magnetic, Casimir and density terms) from the GPU against the same
+    estimator evaluated by the oracle on the same sampled configurations."""
+    from paper_2412_01737_gb300 import optimize
+    from tests.test_optimize import _OracleCtx
+    p = gi.make_problem(2, gi.SU2, 2, 2, bond_scale=0.3)
+    sctx = ctx_for(p)
+    sctx.chains_init(gi.random_links(p, 32, seed=5), precision=0, seed=4)
+    sctx.sample(2)
+    links = np.ascontiguousarray(sctx.chains_links())
+    sctx.close()
+    gens = gi._su2_generators(gi._site_slots_su2(p.n_v))
+    A = np.random.default_rng(3).normal(size=(p.m_s, p.m_s))
+    X = optimize.commutant_generator(A - A.T, gens)
+    dirs = [lambda t: optimize.rotate_sites(p, X, t)]
+    kw = dict(c_plaquette=-1.0, c_electric=0.5 * np.ones(p.n_links), c_site=0.4 * np.ones(p.V))
+    gctx = ctx_for(p)
+    e_gpu, g_gpu = optimize.energy_gradient(gctx, p, links, dirs, **kw)
+    gctx.close()
+    e_ref, g_ref = optimize.energy_gradient(_OracleCtx(), p, links, dirs, **kw)
+    assert abs(g_ref[0]) > 1e-4
+    assert abs(e_gpu - e_ref) <= 1e-10 * max(1.0, abs(e_ref))
+    assert abs(g_gpu[0] - g_ref[0]) <= 1e-6 * max(1.0, abs(g_ref[0]))
