@@ -15,7 +15,8 @@
 //   site[s]           = sum_nm lambda_n^* lambda_m <psi_n|c_2s c_2s+1|psi_m> / N(G)
 //   link[l][alpha][beta] = same for c_{2s+alpha} c_{2t+beta}, link l = (s -> t)
 // (densities n_s = (1 + i site[s]) / 2; hoppings and pairings are linear in
-// the link block; the gauge string of the operator multiplies them).
+// the link block, and link_term_kernel forms the gauge-invariant one with the
+// link operator, u_l F_s F_t, from it).
 #include "ggf_obs.cuh"
 
 namespace {
