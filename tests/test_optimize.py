@@ -323,3 +323,37 @@ def test_commutant_generator_for_su2_keeps_gauge_invariance():
     B = rng.normal(size=T.shape)
     B = B - B.T
     assert np.abs(optimize.commutant_generator(B, [T]) - optimize.u1_generator(B, q)).max() <= 1e-10
+
+
+def test_reweighted_gradient_u1_on_an_exact_grid():
+    """U(1) on the 1x1 torus, every configuration of an 8 x 8 angle grid
+    weighted by N(G) (a grid that integrates the energy's terms exactly): the
+    reweighted central difference along a U(1)-symmetric site rotation
+    equals the finite difference of the grid expectations of the Hermitian
+    forms (magnetic, Casimir, density and link terms)."""
+    from oracle import variational as va, weight
+    p = gi.make_problem(1, gi.U1, 1, 2, bond_scale=0.4)
+    th = 2 * np.pi * np.arange(8) / 8
+    grid = np.array([[a, b] for a in th for b in th])
+    W = weight.Weights(p)
+    logs = np.array([W.log_norm(G) for G in grid])
+    w0 = np.exp(logs - logs.max())
+    w0 /= w0.sum()
+    A = np.random.default_rng(8).normal(size=(p.m_s, p.m_s))
+    Ap = optimize.u1_generator(A - A.T, gi.site_charges(p.n_v, int(p.q_phys[0])))
+    ce, cs, ch = np.array([0.5, 0.7]), np.array([0.4]), np.array([0.3, -0.2])
+
+    def exact(q):
+        S = va.exhaustive(q, grid)
+        hop = np.einsum("l,lnm->nm", ch, S["hopping"])
+        H = (-1.0 * S["plaquette"] + np.einsum("l,lnm->nm", ce, S["electric"])
+             + np.einsum("s,snm->nm", cs, 0.5 * (S["norm"] + 1j * S["density"])) + hop + hop.conj().T)
+        return float(va.expectation(H, S["norm"], q.lam).real)
+
+    d = lambda t: optimize.rotate_sites(p, Ap, t)
+    e0, g = optimize.energy_gradient(_OracleCtx(), p, grid, [d], delta=1e-3, weights=w0, c_plaquette=-1.0,
+                                     c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
+    fd = (exact(d(1e-3)) - exact(d(-1e-3))) / 2e-3
+    assert abs(e0 - exact(p)) <= 1e-12
+    assert abs(fd) > 1e-3
+    assert abs(g[0] - fd) <= 1e-9 * max(1.0, abs(fd))
