@@ -1,7 +1,9 @@
-"""Host logic of the lambda optimiser (paper_2412_01737_gb300/optimize.py),
+"""Host logic of the variational optimiser (paper_2412_01737_gb300/optimize.py),
 on CPU: the generalised eigensolver against the oracle's, the local energy
-contraction against explicit sums, and the accumulation loop with a stand-in
-context that serves the oracle's local matrices."""
+contraction against explicit sums, the accumulation loop with a stand-in
+context that serves the oracle's local matrices, the reweighted gradients
+against exhaustive finite differences (Z2, and U(1) on an exact angle grid)
+and the site score, the descent loop, and the symmetric generators."""
 import numpy as np
 
 import ggf_inputs as gi
