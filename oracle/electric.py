@@ -203,28 +203,34 @@ class Electric:
                 val = val + 2 * q[j] * q[k] * pair
         return val
 
-    def field(self, links: np.ndarray) -> np.ndarray:
-        """U(1) electric field <J_l> per link: the insertion of the twist
-        charge Q_l = sum_j q_j n_j, <Q_l> = sum_j q_j (1 + G_{2j,2j+1}) / 2 with
-        G = Gamma_O[S, S] (complex per configuration)."""
+    def field_ratios(self, links: np.ndarray) -> np.ndarray:
+        """F[n, m, l]: the normalised expectation of the twist charge
+        Q_l = sum_j q_j n_j inserted on the ket for pair (n, m),
+        <Q_l> = sum_j q_j (1 + G_{2j,2j+1}) / 2 with G = Gamma_O[S, S]."""
         p = self.p
         if p.group != U1:
             raise ValueError("the electric field insertion is defined for U(1)")
         O = weight.twist_matrix(p, links)
         D = (O.T @ self.W.GA @ O)[np.ix_(self.virt, self.virt)]
         one = np.eye(D.shape[0])
-        lnm = self.W.log_n_matrix(links)
-        Nnm = np.exp(lnm - lnm.real.max())
-        w = np.conj(p.lam)[:, None] * p.lam[None, :] * Nnm
-        out = np.zeros(p.n_links, dtype=complex)
+        out = np.zeros((p.K, p.K, p.n_links), dtype=complex)
         for n in range(p.K):
             for m in range(p.K):
                 GX = self.GX[n, m]
                 GO = 1j * one - (one + 1j * D) @ np.linalg.inv(D + GX) @ (one + 1j * GX)
                 for l in range(p.n_links):
                     G = GO[np.ix_(self.S[l], self.S[l])]
-                    out[l] += w[n, m] * sum(p.q_src[j] * (1.0 + G[2 * j, 2 * j + 1]) / 2.0 for j in range(p.n_v))
-        return out / w.sum()
+                    out[n, m, l] = sum(p.q_src[j] * (1.0 + G[2 * j, 2 * j + 1]) / 2.0 for j in range(p.n_v))
+        return out
+
+    def field(self, links: np.ndarray) -> np.ndarray:
+        """U(1) electric field <J_l> per link (complex per configuration): the
+        pairs' field_ratios combined with lambda_n^* lambda_m N_nm(G) / N(G)."""
+        p = self.p
+        lnm = self.W.log_n_matrix(links)
+        Nnm = np.exp(lnm - lnm.real.max())
+        w = np.conj(p.lam)[:, None] * p.lam[None, :] * Nnm
+        return np.einsum("nm,nml->l", w, self.field_ratios(links)) / w.sum()
 
     def f_electric(self, links: np.ndarray) -> np.ndarray:
         """f_E(G) for every link (complex; its expectation over p(G) is real)."""

@@ -56,6 +56,7 @@ class LocalMatrices:
     def __call__(self, links):
         """dict of K x K (or (n, K, K)) arrays divided by N_lambda0(G):
         'norm' N(G); 'plaquette' mean plaquette; 'electric' per link;
+        'field' per link (U(1): the electric field <J_l>);
         'density' per site (the bilinear c_2s c_2s+1); 'hopping' per link
         (Z2 and U(1): the gauge-invariant link term T_l; T_l^dag has the
         conjugate transpose over n, m)."""
@@ -67,6 +68,8 @@ class LocalMatrices:
         out["plaquette"] = Nn * plaquette_values(p.group, p.L, links).mean()
         R = self.el.ratios(links)                                # [n, m, l]
         out["electric"] = np.moveaxis(Nn[:, :, None] * R, 2, 0)  # [l, n, m]
+        if p.group == weight.U1:
+            out["field"] = np.moveaxis(Nn[:, :, None] * self.el.field_ratios(links), 2, 0)
         Ge = self.fe.gamma_eff(links)
         dens = np.zeros((p.V, p.K, p.K), dtype=complex)
         for (n, m), G in Ge.items():

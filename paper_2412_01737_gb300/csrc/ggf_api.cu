@@ -899,6 +899,10 @@ ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* 
         case GGF_PAIRS_ELECTRIC: items = g.n_links; break;
         case GGF_PAIRS_SITE: items = g.V; break;
         case GGF_PAIRS_LINK: items = (size_t)g.n_links * 4; break;
+        case GGF_PAIRS_FIELD:
+            if (g.group != GGF_U1) return ggf_fail(ctx, GGF_EINVAL, "the field's pair parts are defined for U(1)");
+            items = g.n_links;
+            break;
         default: return ggf_fail(ctx, GGF_EINVAL, "unknown pair quantity");
     }
     cudaSetDevice(ctx->device);
@@ -912,6 +916,7 @@ ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* 
     }
     if (what == GGF_PAIRS_NORM) GGF_TRY(ggf_pair_norm(ctx, dst, st));
     else if (what == GGF_PAIRS_ELECTRIC) GGF_TRY(ggf_electric(ctx, nullptr, dst, st));
+    else if (what == GGF_PAIRS_FIELD) GGF_TRY(ggf_electric(ctx, nullptr, dst, st, true));
     else if (what == GGF_PAIRS_SITE) GGF_TRY(ggf_fermion(ctx, nullptr, nullptr, dst, nullptr, st));
     else GGF_TRY(ggf_fermion(ctx, nullptr, nullptr, nullptr, dst, st));
     if (mem == GGF_MEM_HOST) {

@@ -14,7 +14,7 @@ current lambda and estimates Hbar and Nbar for an energy
 
     E = c_plaquette <mean plaquette> + sum_l c_electric[l] <f_E,l>
         + sum_s c_site[s] <n_s> + sum_{l,a,b} c_link[l,a,b] <i c_{2s+a} c_{2t+b}>
-        + sum_l c_hop[l] <T_l + T_l^dag>
+        + sum_l c_hop[l] <T_l + T_l^dag> + sum_l c_field[l] <J_l>   (U(1))
 
 with the Hermitian operators n_s = (1 + i c_2s c_2s+1) / 2 and i c c (the
 Majorana bilinears themselves are anti-Hermitian), so that for real
@@ -55,14 +55,15 @@ import dataclasses
 import numpy as np
 import scipy.linalg
 
-from .ggf import FP64, PAIRS_ELECTRIC, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
+from .ggf import FP64, PAIRS_ELECTRIC, PAIRS_FIELD, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
 
 
 def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric=None, c_site=None,
-                 c_link=None, c_hop=None) -> np.ndarray:
+                 c_link=None, c_hop=None, c_field=None) -> np.ndarray:
     """(n_chains, K, K) local matrices of the energy from one sweep's per-pair
     parts (dict with keys 'norm', 'electric', 'site', 'link' as returned by
-    GGF.chains_pairs, 'hop' the per-pair link terms of GGF.chains_link_terms)
+    GGF.chains_pairs, 'hop' the per-pair link terms of GGF.chains_link_terms,
+    'field' the PAIRS_FIELD parts)
     and the chains' mean plaquettes."""
     H = c_plaquette * plaquette[:, None, None] * pairs["norm"]
     if c_electric is not None:
@@ -75,11 +76,13 @@ def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric
     if c_hop is not None:
         T = np.einsum("l,clnm->cnm", np.asarray(c_hop, dtype=float), pairs["hop"])
         H = H + T + np.conj(np.swapaxes(T, 1, 2))
+    if c_field is not None:
+        H = H + np.einsum("l,clnm->cnm", np.asarray(c_field, dtype=complex), pairs["field"])
     return H
 
 
 def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
-               charges=None):
+               charges=None, c_field=None):
     """Run n_sweeps sweeps of ctx's chains and return (Hbar, Nbar), the means
     over chains and sweeps of the energy's and the norm's per-pair parts
     (c_hop needs the sites' physical charges)."""
@@ -97,7 +100,9 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
             pairs["link"] = ctx.chains_pairs(PAIRS_LINK)
         if c_hop is not None:
             pairs["hop"] = ctx.chains_link_terms(charges, pairs=True)[1]
-        H = local_energy(pairs, obs[0, :, 0], c_plaquette, c_electric, c_site, c_link, c_hop)
+        if c_field is not None:
+            pairs["field"] = ctx.chains_pairs(PAIRS_FIELD)
+        H = local_energy(pairs, obs[0, :, 0], c_plaquette, c_electric, c_site, c_link, c_hop, c_field)
         Hbar = Hbar + H.sum(axis=0)
         Nbar = Nbar + pairs["norm"].sum(axis=0)
         n += H.shape[0]
@@ -105,7 +110,7 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
 
 
 def forms(ctx, links, weights=None, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
-          charges=None):
+          charges=None, c_field=None):
     """(Hbar, Nbar) as in ``accumulate``, from an explicit list of
     configurations (samples of ctx's problem, or every configuration with
     weights p(G)): they become FP64 chains of ctx, whose per-pair parts are
@@ -123,8 +128,10 @@ def forms(ctx, links, weights=None, c_plaquette=0.0, c_electric=None, c_site=Non
         pairs["link"] = ctx.chains_pairs(PAIRS_LINK)
     if c_hop is not None:
         pairs["hop"] = ctx.chains_link_terms(charges, pairs=True)[1]
+    if c_field is not None:
+        pairs["field"] = ctx.chains_pairs(PAIRS_FIELD)
     pl = np.asarray(ctx.observable(links), dtype=float)
-    H = local_energy(pairs, pl, c_plaquette, c_electric, c_site, c_link, c_hop)
+    H = local_energy(pairs, pl, c_plaquette, c_electric, c_site, c_link, c_hop, c_field)
     w = np.full(len(links), 1.0 / len(links)) if weights is None else np.asarray(weights, float) / np.sum(weights)
     return np.einsum("c,cnm->nm", w, H), np.einsum("c,cnm->nm", w, pairs["norm"])
 
@@ -214,7 +221,7 @@ def energy(Hbar: np.ndarray, Nbar: np.ndarray, lam) -> float:
 
 
 def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
-                   charges=None, batch=None):
+                   charges=None, batch=None, c_field=None):
     """(log N(G), h(G)) for every configuration in links under ctx's current
     problem: h(G) the per-configuration value of the energy of
     ``local_energy`` (complex; its mean over p is real).  The configurations
@@ -222,12 +229,12 @@ def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_
     time (all by default; each holds its P inverses in FP64)."""
     links = np.ascontiguousarray(links)
     if batch is not None and len(links) > batch:
-        parts = [local_energies(ctx, links[i:i + batch], c_plaquette, c_electric, c_site, c_link, c_hop, charges)
-                 for i in range(0, len(links), batch)]
+        parts = [local_energies(ctx, links[i:i + batch], c_plaquette, c_electric, c_site, c_link, c_hop, charges,
+                                c_field=c_field) for i in range(0, len(links), batch)]
         return np.concatenate([a for a, _ in parts]), np.concatenate([b for _, b in parts])
     logN = np.asarray(ctx.logweight(links), dtype=float)
     h = c_plaquette * np.asarray(ctx.observable(links), dtype=complex)
-    if c_electric is None and c_site is None and c_link is None and c_hop is None:
+    if c_electric is None and c_site is None and c_link is None and c_hop is None and c_field is None:
         return logN, h
     ctx.chains_init(links, precision=FP64, refresh_every=1 << 30, delay=1)
     if c_electric is not None:
@@ -243,6 +250,8 @@ def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_
             raise ValueError("c_hop needs the sites' physical charges")
         T = ctx.chains_link_terms(charges)
         h = h + 2.0 * T.real @ np.asarray(c_hop, dtype=float)
+    if c_field is not None:
+        h = h + ctx.chains_electric_field() @ np.asarray(c_field, dtype=complex)
     return logN, h
 
 

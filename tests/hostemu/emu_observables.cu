@@ -46,16 +46,17 @@ void emu_electric(int L, int group, int n_v, const int* q, int K, const double* 
 
 void emu_field(int L, int group, int n_v, const int* q, int K, const double* D, const double* Ap,
                const double* Bp, const double* Gr, const double* Gc, const double* logc, const double* w,
-               int n_chains, const void* links, const double* Wr, const double* Wc, const double* ell, double* out) {
+               int n_chains, const void* links, const double* Wr, const double* Wc, const double* ell, double* out,
+               double* pairs) {
     DevConst dc = make_dc(L, group, n_v, q, K, D, Ap, Bp, Gr, Gc, logc, w);
     for (int c = 0; c < n_chains; ++c)
         for (int l = 0; l < dc.g.n_links; ++l) {
             if (dc.g.h2 == 2)
                 electric_item<double, cxd, 2, true>(dc, c, l, links, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out,
-                                                    nullptr);
+                                                    (cxd*)pairs);
             else
                 electric_item<double, cxd, 4, true>(dc, c, l, links, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out,
-                                                    nullptr);
+                                                    (cxd*)pairs);
         }
 }
 

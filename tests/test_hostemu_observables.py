@@ -307,12 +307,16 @@ def test_field_items_match_oracle(emu, L, n_v, K):
     links = gi.random_links(p, 2, seed=22)
     lay = Layout(p, links)
     out = np.zeros((2, p.n_links, 2))
+    pairs = np.zeros((2, p.n_links, K, K, 2))
     emu.emu_field(*lay.common()[:-1], ctypes.c_int(2), _ptr(lay.links), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell),
-                  _ptr(out))
+                  _ptr(out), _ptr(pairs))
     el = electric.Electric(p)
+    lm = variational.LocalMatrices(p)
     for c in range(2):
         ref = el.field(links[c])
         assert np.abs(_c(out)[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+        rp = lm(links[c])["field"]
+        assert np.abs(_c(pairs)[c] - rp).max() <= 1e-11 * max(1.0, np.abs(rp).max())
 
 
 @pytest.mark.parametrize("L,grp,n_v,K", [(2, gi.U1, 1, 2), (3, gi.U1, 1, 2), (2, gi.Z2, 2, 3), (1, gi.U1, 2, 2)])

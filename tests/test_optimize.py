@@ -9,7 +9,7 @@ import numpy as np
 import ggf_inputs as gi
 from oracle import variational
 from paper_2412_01737_gb300 import optimize
-from paper_2412_01737_gb300.ggf import PAIRS_ELECTRIC, PAIRS_NORM, PAIRS_SITE
+from paper_2412_01737_gb300.ggf import PAIRS_ELECTRIC, PAIRS_FIELD, PAIRS_NORM, PAIRS_SITE
 
 
 def test_linear_method_matches_oracle():
@@ -152,8 +152,17 @@ class _OracleCtx:
     def chains_pairs(self, what):
         from oracle import variational
         lm = variational.LocalMatrices(self.p)
-        key = {PAIRS_NORM: "norm", PAIRS_ELECTRIC: "electric", PAIRS_SITE: "density"}[what]
+        key = {PAIRS_NORM: "norm", PAIRS_ELECTRIC: "electric", PAIRS_SITE: "density", PAIRS_FIELD: "field"}[what]
         return np.array([lm(G)[key] for G in self.links])
+
+    def chains_electric_field(self):
+        return np.array([self.el.field(G) for G in self.links])
+
+
+def _OracleCtx_at(q):
+    ctx = _OracleCtx()
+    ctx.init_problem(q)
+    return ctx
 
 
 def _exact_energy(q, cfgs, ce, cs, ch):
@@ -332,7 +341,8 @@ def test_reweighted_gradient_u1_on_an_exact_grid():
     weighted by N(G) (a grid that integrates the energy's terms exactly): the
     reweighted central difference along a U(1)-symmetric site rotation
     equals the finite difference of the grid expectations of the Hermitian
-    forms (magnetic, Casimir, density and link terms)."""
+    forms (magnetic, Casimir, density, link and field terms); the forms of an
+    explicit weighted list give the same energy."""
     from oracle import variational as va, weight
     p = gi.make_problem(1, gi.U1, 1, 2, bond_scale=0.4)
     th = 2 * np.pi * np.arange(8) / 8
@@ -343,18 +353,21 @@ def test_reweighted_gradient_u1_on_an_exact_grid():
     w0 /= w0.sum()
     A = np.random.default_rng(8).normal(size=(p.m_s, p.m_s))
     Ap = optimize.u1_generator(A - A.T, gi.site_charges(p.n_v, int(p.q_phys[0])))
-    ce, cs, ch = np.array([0.5, 0.7]), np.array([0.4]), np.array([0.3, -0.2])
+    ce, cs, ch, cf = np.array([0.5, 0.7]), np.array([0.4]), np.array([0.3, -0.2]), np.array([0.25, -0.6])
 
     def exact(q):
         S = va.exhaustive(q, grid)
         hop = np.einsum("l,lnm->nm", ch, S["hopping"])
         H = (-1.0 * S["plaquette"] + np.einsum("l,lnm->nm", ce, S["electric"])
-             + np.einsum("s,snm->nm", cs, 0.5 * (S["norm"] + 1j * S["density"])) + hop + hop.conj().T)
+             + np.einsum("s,snm->nm", cs, 0.5 * (S["norm"] + 1j * S["density"])) + hop + hop.conj().T
+             + np.einsum("l,lnm->nm", cf, S["field"]))
         return float(va.expectation(H, S["norm"], q.lam).real)
 
     d = lambda t: optimize.rotate_sites(p, Ap, t)
-    e0, g = optimize.energy_gradient(_OracleCtx(), p, grid, [d], delta=1e-3, weights=w0, c_plaquette=-1.0,
-                                     c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
+    kw = dict(c_plaquette=-1.0, c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys, c_field=cf)
+    e0, g = optimize.energy_gradient(_OracleCtx(), p, grid, [d], delta=1e-3, weights=w0, **kw)
+    H, N = optimize.forms(_OracleCtx_at(p), grid, w0, **kw)
+    assert abs(optimize.energy(H, N, p.lam) - exact(p)) <= 1e-12
     fd = (exact(d(1e-3)) - exact(d(-1e-3))) / 2e-3
     assert abs(e0 - exact(p)) <= 1e-12
     assert abs(fd) > 1e-3

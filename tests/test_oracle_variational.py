@@ -274,3 +274,28 @@ def test_site_gradient_step_lowers_a_wilson_energy():
     predicted = -eta * np.dot(grad, grad)
     assert E2 < E
     assert abs((E2 - E) - predicted) <= 0.2 * abs(predicted)
+
+
+def test_u1_field_forms_reproduce_direct_expectations():
+    """U(1) on the 1x1 torus, on an 8 x 8 angle grid that integrates the
+    terms exactly: the per-pair field forms, contracted with another lambda,
+    give the grid expectation of <J_l> computed directly with that lambda."""
+    from oracle import electric
+    p = gi.make_problem(1, gi.U1, 1, 2, bond_scale=0.4)
+    th = 2 * np.pi * np.arange(8) / 8
+    grid = np.array([[a, b] for a in th for b in th])
+    S = va.exhaustive(p, grid)
+    rng = np.random.default_rng(4)
+    for _ in range(2):
+        z = rng.normal(size=p.K) + 1j * rng.normal(size=p.K)
+        lam = z / np.linalg.norm(z)
+        q = va.with_lambda(p, lam)
+        W = weight.Weights(q)
+        logs = np.array([W.log_norm(G) for G in grid])
+        w = np.exp(logs - logs.max())
+        w /= w.sum()
+        el = electric.Electric(q)
+        direct = sum(wi * el.field(G) for wi, G in zip(w, grid))
+        got = va.expectation(S["field"], S["norm"], lam)
+        assert np.abs(direct).max() > 1e-3
+        assert np.abs(got - direct).max() <= 1e-12

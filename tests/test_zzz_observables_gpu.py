@@ -671,3 +671,33 @@ def test_u1_gradient_on_gpu_matches_oracle_on_the_same_samples():
     e_ref, g_ref = optimize.energy_gradient(_OracleCtx(), p, links, dirs, **kw)
     assert abs(e_gpu - e_ref) <= 1e-10 * max(1.0, abs(e_ref))
     assert abs(g_gpu[0] - g_ref[0]) <= 1e-6 * max(1.0, abs(g_ref[0]))
+
+
+@pytest.mark.parametrize("L,n_v,K,prec,tol", [(3, 1, 2, 0, 1e-10), (2, 2, 3, 0, 1e-10), (4, 1, 2, 1, 1e-4)])
+def test_field_pair_parts_match_oracle(L, n_v, K, prec, tol):
+    """PAIRS_FIELD against the oracle's per-pair field forms; contracted with
+    lambda they give ggf_chains_electric_field.  Rejected for Z2 chains."""
+    from oracle import variational
+    from paper_2412_01737_gb300 import GGFError
+    from paper_2412_01737_gb300.ggf import PAIRS_FIELD
+    p = gi.make_problem(L, gi.U1, n_v, K, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=19), precision=prec, seed=3, delay=8 if prec else 1)
+    if prec:
+        ctx.sample(2)
+    links = ctx.chains_links()
+    fp = ctx.chains_pairs(PAIRS_FIELD)
+    J = ctx.chains_electric_field()
+    ctx.close()
+    lm = variational.LocalMatrices(p)
+    for c in range(2):
+        ref = lm(links[c])["field"]
+        assert np.abs(fp[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
+        con = np.einsum("n,lnm,m->l", np.conj(p.lam), fp[c], p.lam)
+        assert np.abs(con - J[c]).max() <= tol * max(1.0, np.abs(J[c]).max())
+    z = gi.make_problem(2, gi.Z2, 1, 2)
+    zc = ctx_for(z)
+    zc.chains_init(gi.random_links(z, 1, seed=1), precision=0, seed=1)
+    with pytest.raises(GGFError):
+        zc.chains_pairs(PAIRS_FIELD, out=np.zeros((1, z.n_links, 2, 2, 2)))
+    zc.close()
