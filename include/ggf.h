@@ -328,7 +328,9 @@ ggf_status ggf_chains_fermion4(ggf_ctx* ctx, double* out, int mem, void* stream)
  *   GGF_PAIRS_LINK      items = 2V x 2 x 2: the link blocks of
  *                       ggf_chains_fermion, per pair;
  *   GGF_PAIRS_FIELD     items = 2V (U(1) chains only): the electric field
- *                       of ggf_chains_electric_field, per pair.
+ *                       of ggf_chains_electric_field, per pair;
+ *   GGF_PAIRS_FOUR      items = 2V: the four-point function of
+ *                       ggf_chains_fermion4, per pair.
  * Contracting with lambda_n^* lambda_m gives the combined quantity (the
  * gauge-invariant link terms' parts come from ggf_chains_link_terms).  Pending
  * delayed updates are folded into W first.  GGF_EINVAL for an unknown `what`
@@ -338,6 +340,7 @@ ggf_status ggf_chains_fermion4(ggf_ctx* ctx, double* out, int mem, void* stream)
 #define GGF_PAIRS_SITE 2
 #define GGF_PAIRS_LINK 3
 #define GGF_PAIRS_FIELD 4
+#define GGF_PAIRS_FOUR 5
 ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* stream);
 
 /* Score of the site blocks: out[c][s][i][j] = d log N(G_c) / d D_s[i][j]

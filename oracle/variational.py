@@ -41,6 +41,7 @@ import numpy as np
 import scipy.linalg
 
 from . import electric, fermionic, weight
+from .pfaffian import pfaffian
 from .observables import plaquette_values
 
 
@@ -56,7 +57,8 @@ class LocalMatrices:
     def __call__(self, links):
         """dict of K x K (or (n, K, K)) arrays divided by N_lambda0(G):
         'norm' N(G); 'plaquette' mean plaquette; 'electric' per link;
-        'field' per link (U(1): the electric field <J_l>);
+        'field' per link (U(1): the electric field <J_l>); 'four' per link
+        (<c_2s c_2s+1 c_2t c_2t+1>, the density-density part);
         'density' per site (the bilinear c_2s c_2s+1); 'hopping' per link
         (Z2 and U(1): the gauge-invariant link term T_l; T_l^dag has the
         conjugate transpose over n, m)."""
@@ -76,6 +78,13 @@ class LocalMatrices:
             for s in range(p.V):
                 dens[s, n, m] = Nn[n, m] * (-1j) * G[2 * s, 2 * s + 1]
         out["density"] = dens
+        four = np.zeros((p.n_links, p.K, p.K), dtype=complex)
+        for l in range(p.n_links):
+            s, t = fermionic._link_sites(p, l)
+            ix = [2 * s, 2 * s + 1, 2 * t, 2 * t + 1]
+            for (n, m), G in Ge.items():
+                four[l, n, m] = Nn[n, m] * (-1.0 if s == t else pfaffian(-1j * G[np.ix_(ix, ix)]))
+        out["four"] = four
         if p.group == weight.SU2:      # link terms are defined for Z2 and U(1)
             return out
         blk = np.zeros((p.n_links, 2, 2, p.K, p.K), dtype=complex)

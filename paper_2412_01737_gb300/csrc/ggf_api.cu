@@ -24,7 +24,7 @@ ggf_status ggf_fermion(ggf_ctx* ctx, cxd* d_site, cxd* d_link, cxd* d_pair_site,
                        cudaStream_t st);
 ggf_status ggf_pair_norm(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 ggf_status ggf_score(ggf_ctx* ctx, double* d_out, cudaStream_t st);
-ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
+ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st, cxd* d_pairs = nullptr);
 ggf_status ggf_link_score(ggf_ctx* ctx, cxd* d_out, cudaStream_t st);
 ggf_status ggf_link_terms(ggf_ctx* ctx, const int* d_q, cxd* d_blk, cxd* d_pair_blk, cxd* d_out, cxd* d_pair_out,
                           cudaStream_t st);
@@ -899,6 +899,7 @@ ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* 
         case GGF_PAIRS_ELECTRIC: items = g.n_links; break;
         case GGF_PAIRS_SITE: items = g.V; break;
         case GGF_PAIRS_LINK: items = (size_t)g.n_links * 4; break;
+        case GGF_PAIRS_FOUR: items = g.n_links; break;
         case GGF_PAIRS_FIELD:
             if (g.group != GGF_U1) return ggf_fail(ctx, GGF_EINVAL, "the field's pair parts are defined for U(1)");
             items = g.n_links;
@@ -917,6 +918,7 @@ ggf_status ggf_chains_pairs(ggf_ctx* ctx, int what, double* out, int mem, void* 
     if (what == GGF_PAIRS_NORM) GGF_TRY(ggf_pair_norm(ctx, dst, st));
     else if (what == GGF_PAIRS_ELECTRIC) GGF_TRY(ggf_electric(ctx, nullptr, dst, st));
     else if (what == GGF_PAIRS_FIELD) GGF_TRY(ggf_electric(ctx, nullptr, dst, st, true));
+    else if (what == GGF_PAIRS_FOUR) GGF_TRY(ggf_fermion4(ctx, nullptr, st, dst));
     else if (what == GGF_PAIRS_SITE) GGF_TRY(ggf_fermion(ctx, nullptr, nullptr, dst, nullptr, st));
     else GGF_TRY(ggf_fermion(ctx, nullptr, nullptr, nullptr, dst, st));
     if (mem == GGF_MEM_HOST) {

@@ -364,24 +364,39 @@ GGF_HD void link_term_item(const DevConst& dc, int c, int l, const void* links, 
 // N_nm / N(G) as for the bilinears.  A self-link (s = t) gives -1.
 template <class RW, class CW, int BW>
 __host__ __device__ void fermion4_item(const DevConst& dc, int c, int l, const RW* Wr, const CW* Wc,
-                                       const cxd* ell, cxd* out) {
+                                       const cxd* ell, cxd* out, cxd* pair_out = nullptr) {
     const Geometry& g = dc.g;
     int a0, b0;
     link_ends(g, l, a0, b0);
     const int s = a0 / g.B, t = b0 / g.B;
-    cxd* o = out + (size_t)c * g.n_links + l;
-    if (s == t) { *o = cxd{-1.0, 0.0}; return; }
     const int K = dc.K;
-    const size_t NN = (size_t)g.N * g.N;
     const cxd* el = ell + (size_t)c * dc.P;
     double amax, iden;
     pair_scale(dc, el, amax, iden);
+    // per-pair parts pair_out[c][l][n][m] = N_nm(G) <c c c c>_nm / N(G)
+    cxd* q = pair_out ? pair_out + ((size_t)c * g.n_links + l) * K * K : nullptr;
+    if (s == t) {   // c_2s c_2s+1 c_2s c_2s+1 = -1
+        if (out) out[(size_t)c * g.n_links + l] = cxd{-1.0, 0.0};
+        if (q)
+            for (int p = 0; p < dc.P; ++p) {
+                int n, m;
+                pair_nm(K, p, n, m);
+                const cxd Np = pair_norm(dc, el, p, amax, iden);
+                q[n * K + m] = -1.0 * Np;
+                if (p >= K) q[m * K + n] = -1.0 * conjg(Np);
+            }
+        return;
+    }
+    const size_t NN = (size_t)g.N * g.N;
     const double* As = dc.Ap + (size_t)s * 4;
     const double* At = dc.Ap + (size_t)t * 4;
     cxd acc = {0.0, 0.0};
     for (int p = 0; p < dc.P; ++p) {
         const bool cplx = p >= K;
-        const cxd E = dc.w[p] * pair_norm(dc, el, p, amax, iden);
+        const cxd Np = pair_norm(dc, el, p, amax, iden);
+        const cxd E = dc.w[p] * Np;
+        int n, m;
+        pair_nm(K, p, n, m);
         cxd Xss[2][2], Xtt[2][2], Xst[2][2];
         if (cplx) {
             const CW* W = Wc + ((size_t)c * dc.Kc + (p - K)) * NN;
@@ -404,9 +419,13 @@ __host__ __device__ void fermion4_item(const DevConst& dc, int c, int l, const R
             const cxd pf = g01 * g23 - g02 * g13 + g03 * g12;
             const cxd wgt = cplx ? (ord ? 0.5 * conjg(E) : 0.5 * E) : E;
             acc -= wgt * pf;
+            if (q) {
+                if (ord) q[m * K + n] = -1.0 * (conjg(Np) * pf);
+                else q[n * K + m] = -1.0 * (Np * pf);
+            }
         }
     }
-    *o = acc;
+    if (out) out[(size_t)c * g.n_links + l] = acc;
 }
 
 // ---- score of the site blocks ------------------------------------------------

@@ -38,11 +38,12 @@ __global__ void __launch_bounds__(FTHREADS) fermion_kernel(DevConst dc, int n_ch
 // One thread per (chain, link).
 template <class RW, class CW, int BW>
 __global__ void __launch_bounds__(FTHREADS) fermion4_kernel(DevConst dc, int n_chains, int blocks_per_chain,
-                                                            const RW* Wr, const CW* Wc, const cxd* ell, cxd* out) {
+                                                            const RW* Wr, const CW* Wc, const cxd* ell, cxd* out,
+                                                            cxd* pair_out) {
     const int c = blockIdx.x / blocks_per_chain;
     const int l = (blockIdx.x - c * blocks_per_chain) * FTHREADS + threadIdx.x;
     if (c >= n_chains || l >= dc.g.n_links) return;
-    fermion4_item<RW, CW, BW>(dc, c, l, Wr, Wc, ell, out);
+    fermion4_item<RW, CW, BW>(dc, c, l, Wr, Wc, ell, out, pair_out);
 }
 
 // One thread per (chain, link).
@@ -82,8 +83,10 @@ ggf_status ggf_link_terms(ggf_ctx* ctx, const int* d_q, cxd* d_blk, cxd* d_pair_
     return GGF_OK;
 }
 
-// <c_2s c_2s+1 c_2t c_2t+1> of every chain and link into d_out [n][n_links] (device).
-ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
+// <c_2s c_2s+1 c_2t c_2t+1> of every chain and link into d_out [n][n_links]
+// and/or its per-pair parts into d_pairs [n][n_links][K][K] (device; either
+// may be null).
+ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st, cxd* d_pairs) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
     GGF_TRY(ggf_flush(ctx, st));
@@ -93,7 +96,7 @@ ggf_status ggf_fermion4(ggf_ctx* ctx, cxd* d_out, cudaStream_t st) {
     const bool fp64 = ch.opts.precision == GGF_FP64;
 #define GGF_F4(RW, CW, BW)                                                                                 \
     fermion4_kernel<RW, CW, BW><<<(unsigned)blocks, FTHREADS, 0, st>>>(ctx->dc(), ch.n, bpc, (const RW*)ch.Wr, \
-                                                                       (const CW*)ch.Wc, ch.ell, d_out)
+                                                                       (const CW*)ch.Wc, ch.ell, d_out, d_pairs)
     if (g.B == 8) {
         if (fp64) GGF_F4(double, cxd, 8); else GGF_F4(float, cxf, 8);
     } else if (g.B == 16) {

@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 Z2, U1, SU2 = 0, 1, 2
-PAIRS_NORM, PAIRS_ELECTRIC, PAIRS_SITE, PAIRS_LINK, PAIRS_FIELD = 0, 1, 2, 3, 4
+PAIRS_NORM, PAIRS_ELECTRIC, PAIRS_SITE, PAIRS_LINK, PAIRS_FIELD, PAIRS_FOUR = 0, 1, 2, 3, 4, 5
 FP64, FP32 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 N_OBS = 3
@@ -366,14 +366,14 @@ class GGF:
 
     def chains_pairs(self, what, out=None):
         """Per-pair parts N_nm(G) o_nm(G) / N(G) of every chain (PAIRS_NORM,
-        PAIRS_ELECTRIC, PAIRS_SITE, PAIRS_LINK, PAIRS_FIELD): complex numpy arrays of shape
+        PAIRS_ELECTRIC, PAIRS_SITE, PAIRS_LINK, PAIRS_FIELD, PAIRS_FOUR): complex arrays of shape
         (n_chains, [items...,] K, K), or fills `out` (float64 with a trailing
         axis of 2, numpy or CUDA tensor) and returns it."""
         if out is None:
             K = self.K
             nl = self.n_links()
             items = {PAIRS_NORM: (), PAIRS_ELECTRIC: (nl,), PAIRS_SITE: (nl // 2,), PAIRS_LINK: (nl, 2, 2),
-                     PAIRS_FIELD: (nl,)}.get(what, ())
+                     PAIRS_FIELD: (nl,), PAIRS_FOUR: (nl,)}.get(what, ())
             host = np.zeros((self.n_chains,) + items + (K, K, 2))
             self._ck(self.lib.ggf_chains_pairs(self.h, int(what), host.ctypes.data, MEM_HOST, None))
             return host[..., 0] + 1j * host[..., 1]

@@ -15,6 +15,7 @@ current lambda and estimates Hbar and Nbar for an energy
     E = c_plaquette <mean plaquette> + sum_l c_electric[l] <f_E,l>
         + sum_s c_site[s] <n_s> + sum_{l,a,b} c_link[l,a,b] <i c_{2s+a} c_{2t+b}>
         + sum_l c_hop[l] <T_l + T_l^dag> + sum_l c_field[l] <J_l>   (U(1))
+        + sum_l c_nn[l] <n_s n_t>   (l = (s -> t), density-density)
 
 with the Hermitian operators n_s = (1 + i c_2s c_2s+1) / 2 and i c c (the
 Majorana bilinears themselves are anti-Hermitian), so that for real
@@ -55,15 +56,16 @@ import dataclasses
 import numpy as np
 import scipy.linalg
 
-from .ggf import FP64, PAIRS_ELECTRIC, PAIRS_FIELD, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
+from .ggf import FP64, PAIRS_ELECTRIC, PAIRS_FIELD, PAIRS_FOUR, PAIRS_LINK, PAIRS_NORM, PAIRS_SITE
 
 
 def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric=None, c_site=None,
-                 c_link=None, c_hop=None, c_field=None) -> np.ndarray:
+                 c_link=None, c_hop=None, c_field=None, c_nn=None) -> np.ndarray:
     """(n_chains, K, K) local matrices of the energy from one sweep's per-pair
     parts (dict with keys 'norm', 'electric', 'site', 'link' as returned by
     GGF.chains_pairs, 'hop' the per-pair link terms of GGF.chains_link_terms,
-    'field' the PAIRS_FIELD parts)
+    'field' the PAIRS_FIELD parts, 'four' the PAIRS_FOUR parts; c_nn needs
+    'site' and 'four')
     and the chains' mean plaquettes."""
     H = c_plaquette * plaquette[:, None, None] * pairs["norm"]
     if c_electric is not None:
@@ -78,11 +80,28 @@ def local_energy(pairs: dict, plaquette: np.ndarray, c_plaquette=0.0, c_electric
         H = H + T + np.conj(np.swapaxes(T, 1, 2))
     if c_field is not None:
         H = H + np.einsum("l,clnm->cnm", np.asarray(c_field, dtype=complex), pairs["field"])
+    if c_nn is not None:
+        # n_s n_t = (1 + i A_s + i A_t - A_s A_t) / 4, A_s = c_2s c_2s+1
+        cn = np.asarray(c_nn, dtype=complex)
+        V = pairs["site"].shape[1]
+        src = np.arange(cn.size) // 2
+        dst = np.array([_link_target(l, int(round(np.sqrt(V)))) for l in range(cn.size)])
+        site = pairs["site"]
+        H = H + 0.25 * (cn.sum() * pairs["norm"] + 1j * np.einsum("l,clnm->cnm", cn, site[:, src])
+                        + 1j * np.einsum("l,clnm->cnm", cn, site[:, dst])
+                        - np.einsum("l,clnm->cnm", cn, pairs["four"]))
     return H
 
 
+def _link_target(l, L):
+    """Site t of link l = (s -> t): s + e_x for even l, s + e_y for odd l."""
+    s, d = l // 2, l % 2
+    x, y = s % L, s // L
+    return y * L + (x + 1) % L if d == 0 else ((y + 1) % L) * L + x
+
+
 def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
-               charges=None, c_field=None):
+               charges=None, c_field=None, c_nn=None):
     """Run n_sweeps sweeps of ctx's chains and return (Hbar, Nbar), the means
     over chains and sweeps of the energy's and the norm's per-pair parts
     (c_hop needs the sites' physical charges)."""
@@ -94,7 +113,7 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
         pairs = {"norm": ctx.chains_pairs(PAIRS_NORM)}
         if c_electric is not None:
             pairs["electric"] = ctx.chains_pairs(PAIRS_ELECTRIC)
-        if c_site is not None:
+        if c_site is not None or c_nn is not None:
             pairs["site"] = ctx.chains_pairs(PAIRS_SITE)
         if c_link is not None:
             pairs["link"] = ctx.chains_pairs(PAIRS_LINK)
@@ -102,7 +121,9 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
             pairs["hop"] = ctx.chains_link_terms(charges, pairs=True)[1]
         if c_field is not None:
             pairs["field"] = ctx.chains_pairs(PAIRS_FIELD)
-        H = local_energy(pairs, obs[0, :, 0], c_plaquette, c_electric, c_site, c_link, c_hop, c_field)
+        if c_nn is not None:
+            pairs["four"] = ctx.chains_pairs(PAIRS_FOUR)
+        H = local_energy(pairs, obs[0, :, 0], c_plaquette, c_electric, c_site, c_link, c_hop, c_field, c_nn)
         Hbar = Hbar + H.sum(axis=0)
         Nbar = Nbar + pairs["norm"].sum(axis=0)
         n += H.shape[0]
@@ -110,7 +131,7 @@ def accumulate(ctx, n_sweeps: int, c_plaquette=0.0, c_electric=None, c_site=None
 
 
 def forms(ctx, links, weights=None, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
-          charges=None, c_field=None):
+          charges=None, c_field=None, c_nn=None):
     """(Hbar, Nbar) as in ``accumulate``, from an explicit list of
     configurations (samples of ctx's problem, or every configuration with
     weights p(G)): they become FP64 chains of ctx, whose per-pair parts are
@@ -122,7 +143,7 @@ def forms(ctx, links, weights=None, c_plaquette=0.0, c_electric=None, c_site=Non
     pairs = {"norm": ctx.chains_pairs(PAIRS_NORM)}
     if c_electric is not None:
         pairs["electric"] = ctx.chains_pairs(PAIRS_ELECTRIC)
-    if c_site is not None:
+    if c_site is not None or c_nn is not None:
         pairs["site"] = ctx.chains_pairs(PAIRS_SITE)
     if c_link is not None:
         pairs["link"] = ctx.chains_pairs(PAIRS_LINK)
@@ -130,8 +151,10 @@ def forms(ctx, links, weights=None, c_plaquette=0.0, c_electric=None, c_site=Non
         pairs["hop"] = ctx.chains_link_terms(charges, pairs=True)[1]
     if c_field is not None:
         pairs["field"] = ctx.chains_pairs(PAIRS_FIELD)
+    if c_nn is not None:
+        pairs["four"] = ctx.chains_pairs(PAIRS_FOUR)
     pl = np.asarray(ctx.observable(links), dtype=float)
-    H = local_energy(pairs, pl, c_plaquette, c_electric, c_site, c_link, c_hop, c_field)
+    H = local_energy(pairs, pl, c_plaquette, c_electric, c_site, c_link, c_hop, c_field, c_nn)
     w = np.full(len(links), 1.0 / len(links)) if weights is None else np.asarray(weights, float) / np.sum(weights)
     return np.einsum("c,cnm->nm", w, H), np.einsum("c,cnm->nm", w, pairs["norm"])
 
@@ -221,7 +244,7 @@ def energy(Hbar: np.ndarray, Nbar: np.ndarray, lam) -> float:
 
 
 def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_link=None, c_hop=None,
-                   charges=None, batch=None, c_field=None):
+                   charges=None, batch=None, c_field=None, c_nn=None):
     """(log N(G), h(G)) for every configuration in links under ctx's current
     problem: h(G) the per-configuration value of the energy of
     ``local_energy`` (complex; its mean over p is real).  The configurations
@@ -230,16 +253,16 @@ def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_
     links = np.ascontiguousarray(links)
     if batch is not None and len(links) > batch:
         parts = [local_energies(ctx, links[i:i + batch], c_plaquette, c_electric, c_site, c_link, c_hop, charges,
-                                c_field=c_field) for i in range(0, len(links), batch)]
+                                c_field=c_field, c_nn=c_nn) for i in range(0, len(links), batch)]
         return np.concatenate([a for a, _ in parts]), np.concatenate([b for _, b in parts])
     logN = np.asarray(ctx.logweight(links), dtype=float)
     h = c_plaquette * np.asarray(ctx.observable(links), dtype=complex)
-    if c_electric is None and c_site is None and c_link is None and c_hop is None and c_field is None:
+    if all(c is None for c in (c_electric, c_site, c_link, c_hop, c_field, c_nn)):
         return logN, h
     ctx.chains_init(links, precision=FP64, refresh_every=1 << 30, delay=1)
     if c_electric is not None:
         h = h + ctx.chains_electric() @ np.asarray(c_electric, dtype=complex)
-    if c_site is not None or c_link is not None:
+    if c_site is not None or c_link is not None or c_nn is not None:
         site, link = ctx.chains_fermion()
         if c_site is not None:
             h = h + (0.5 * (1.0 + 1j * site)) @ np.asarray(c_site, dtype=complex)
@@ -252,6 +275,14 @@ def local_energies(ctx, links, c_plaquette=0.0, c_electric=None, c_site=None, c_
         h = h + 2.0 * T.real @ np.asarray(c_hop, dtype=float)
     if c_field is not None:
         h = h + ctx.chains_electric_field() @ np.asarray(c_field, dtype=complex)
+    if c_nn is not None:
+        cn = np.asarray(c_nn, dtype=complex)
+        L = int(round(np.sqrt(site.shape[1])))
+        src = np.arange(cn.size) // 2
+        dst = np.array([_link_target(l, L) for l in range(cn.size)])
+        four = ctx.chains_fermion4()
+        nn = 0.25 * (1.0 + 1j * site[:, src] + 1j * site[:, dst] - four)
+        h = h + nn @ cn
     return logN, h
 
 

@@ -129,12 +129,15 @@ void emu_score(int L, int group, int n_v, const int* q, int K, const double* log
 
 void emu_fermion4(int L, int group, int n_v, const int* q, int K, const double* D, const double* Ap,
                   const double* Bp, const double* Gr, const double* Gc, const double* logc, const double* w,
-                  int n_chains, const double* Wr, const double* Wc, const double* ell, double* out) {
+                  int n_chains, const double* Wr, const double* Wc, const double* ell, double* out,
+                  double* pairs) {
     DevConst dc = make_dc(L, group, n_v, q, K, D, Ap, Bp, Gr, Gc, logc, w);
     for (int c = 0; c < n_chains; ++c)
         for (int l = 0; l < dc.g.n_links; ++l) {
-            if (dc.g.B == 8) fermion4_item<double, cxd, 8>(dc, c, l, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out);
-            else fermion4_item<double, cxd, 16>(dc, c, l, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out);
+            if (dc.g.B == 8)
+                fermion4_item<double, cxd, 8>(dc, c, l, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out, (cxd*)pairs);
+            else
+                fermion4_item<double, cxd, 16>(dc, c, l, Wr, (const cxd*)Wc, (const cxd*)ell, (cxd*)out, (cxd*)pairs);
         }
 }
 

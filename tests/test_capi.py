@@ -57,7 +57,7 @@ def test_binding_constants_match_header():
              "GGF_KT_GATHER": ggf.KT_GATHER, "GGF_KT_APPLY": ggf.KT_APPLY, "GGF_NET_PARAMS": ggf.NET_PARAMS,
              "GGF_PAIRS_NORM": ggf.PAIRS_NORM, "GGF_PAIRS_ELECTRIC": ggf.PAIRS_ELECTRIC,
              "GGF_PAIRS_SITE": ggf.PAIRS_SITE, "GGF_PAIRS_LINK": ggf.PAIRS_LINK,
-             "GGF_PAIRS_FIELD": ggf.PAIRS_FIELD}
+             "GGF_PAIRS_FIELD": ggf.PAIRS_FIELD, "GGF_PAIRS_FOUR": ggf.PAIRS_FOUR}
     for name, val in pairs.items():
         assert defs[name] == val, name
     assert len(enum) == len(ggf.STATUS)

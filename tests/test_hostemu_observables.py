@@ -247,13 +247,18 @@ def test_fermion4_items_match_oracle(emu, L, grp, n_v, K):
     links = gi.random_links(p, 2, seed=18)
     lay = Layout(p, links)
     out = np.zeros((2, p.n_links, 2))
-    emu.emu_fermion4(*lay.common(), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell), _ptr(out))
+    pairs = np.zeros((2, p.n_links, K, K, 2))
+    emu.emu_fermion4(*lay.common(), _ptr(lay.Wr), _ptr(lay.Wc), _ptr(lay.ell), _ptr(out), _ptr(pairs))
     fe = fermionic.Fermionic(p)
+    lm = variational.LocalMatrices(p)
     for c in range(2):
         for l in range(p.n_links):
             s_, t_ = fermionic._link_sites(p, l)
             want = -1.0 if s_ == t_ else fe.monomial(links[c], (2 * s_, 2 * s_ + 1, 2 * t_, 2 * t_ + 1))
             assert abs(_c(out)[c, l] - want) <= 1e-11
+        ref = lm(links[c])["four"]
+        assert np.abs(_c(pairs)[c] - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+        assert np.abs(np.einsum("n,lnm,m->l", np.conj(p.lam), ref, p.lam) - _c(out)[c]).max() <= 1e-11
 
 
 def test_su2_plaquette_matches_oracle(emu):

@@ -9,7 +9,7 @@ import numpy as np
 import ggf_inputs as gi
 from oracle import variational
 from paper_2412_01737_gb300 import optimize
-from paper_2412_01737_gb300.ggf import PAIRS_ELECTRIC, PAIRS_FIELD, PAIRS_NORM, PAIRS_SITE
+from paper_2412_01737_gb300.ggf import PAIRS_ELECTRIC, PAIRS_FIELD, PAIRS_FOUR, PAIRS_NORM, PAIRS_SITE
 
 
 def test_linear_method_matches_oracle():
@@ -152,11 +152,24 @@ class _OracleCtx:
     def chains_pairs(self, what):
         from oracle import variational
         lm = variational.LocalMatrices(self.p)
-        key = {PAIRS_NORM: "norm", PAIRS_ELECTRIC: "electric", PAIRS_SITE: "density", PAIRS_FIELD: "field"}[what]
+        key = {PAIRS_NORM: "norm", PAIRS_ELECTRIC: "electric", PAIRS_SITE: "density", PAIRS_FIELD: "field",
+               PAIRS_FOUR: "four"}[what]
         return np.array([lm(G)[key] for G in self.links])
 
     def chains_electric_field(self):
         return np.array([self.el.field(G) for G in self.links])
+
+    def chains_fermion4(self):
+        from oracle import fermionic
+        p = self.p
+        out = []
+        for G in self.links:
+            row = []
+            for l in range(p.n_links):
+                s, t = fermionic._link_sites(p, l)
+                row.append(-1.0 if s == t else self.fe.monomial(G, [2 * s, 2 * s + 1, 2 * t, 2 * t + 1]))
+            out.append(row)
+        return np.array(out, dtype=complex)
 
 
 def _OracleCtx_at(q):
@@ -165,12 +178,16 @@ def _OracleCtx_at(q):
     return ctx
 
 
-def _exact_energy(q, cfgs, ce, cs, ch):
-    from oracle import variational as va
+def _exact_energy(q, cfgs, ce, cs, ch, cn=None):
+    from oracle import fermionic, variational as va
     S = va.exhaustive(q, cfgs)
     hop = np.einsum("l,lnm->nm", ch, S["hopping"])
     H = (-1.0 * S["plaquette"] + np.einsum("l,lnm->nm", ce, S["electric"])
          + np.einsum("s,snm->nm", cs, 0.5 * (S["norm"] + 1j * S["density"])) + hop + hop.conj().T)
+    if cn is not None:
+        for l in range(q.n_links):
+            s, t = fermionic._link_sites(q, l)
+            H = H + cn[l] * 0.25 * (S["norm"] + 1j * S["density"][s] + 1j * S["density"][t] - S["four"][l])
     return float(va.expectation(H, S["norm"], q.lam).real)
 
 
@@ -194,13 +211,16 @@ def test_reweighted_gradient_matches_exact_finite_differences():
     ce = np.linspace(0.2, 0.6, p.n_links)
     cs = 0.4 * p.q_phys.astype(float)
     ch = 0.3 * np.ones(p.n_links)
+    cn = np.linspace(-0.5, 0.5, p.n_links)
     dirs = [lambda t: optimize.rotate_sites(p, A, t), lambda t: optimize.rotate_bonds(p, 1, Bg, t)]
     delta = 1e-3
-    e0, g = optimize.energy_gradient(_OracleCtx(), p, cfgs, dirs, delta=delta, weights=w0, batch=100,
-                                     c_plaquette=-1.0, c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys)
-    assert abs(e0 - _exact_energy(p, cfgs, ce, cs, ch)) <= 1e-12
+    kw = dict(c_plaquette=-1.0, c_electric=ce, c_site=cs, c_hop=ch, charges=p.q_phys, c_nn=cn)
+    e0, g = optimize.energy_gradient(_OracleCtx(), p, cfgs, dirs, delta=delta, weights=w0, batch=100, **kw)
+    assert abs(e0 - _exact_energy(p, cfgs, ce, cs, ch, cn)) <= 1e-12
+    H, N = optimize.forms(_OracleCtx_at(p), cfgs, w0, **kw)
+    assert abs(optimize.energy(H, N, p.lam) - e0) <= 1e-12
     for k, d in enumerate(dirs):
-        fd = (_exact_energy(d(delta), cfgs, ce, cs, ch) - _exact_energy(d(-delta), cfgs, ce, cs, ch)) / (2 * delta)
+        fd = (_exact_energy(d(delta), cfgs, ce, cs, ch, cn) - _exact_energy(d(-delta), cfgs, ce, cs, ch, cn)) / (2 * delta)
         assert abs(fd) > 1e-3
         assert abs(g[k] - fd) <= 1e-9 * max(1.0, abs(fd))
 

@@ -38,6 +38,12 @@ def test_forms_reproduce_direct_expectations(setup):
         fe = fermionic.Fermionic(q)
         ref_d = sum(wi * fe.bilinears(G)[0] for wi, G in zip(w, cfgs))
         assert np.abs(va.expectation(S["density"], S["norm"], lam) - ref_d).max() <= 1e-13
+        four = lambda G: np.array([fe.monomial(G, [2 * (l // 2), 2 * (l // 2) + 1,
+                                                   2 * fermionic._link_sites(q, l)[1],
+                                                   2 * fermionic._link_sites(q, l)[1] + 1])
+                                   for l in range(q.n_links)])
+        ref_f = sum(wi * four(G) for wi, G in zip(w, cfgs))
+        assert np.abs(va.expectation(S["four"], S["norm"], lam) - ref_f).max() <= 1e-13
         ref_t = sum(wi * fe.link_terms(G) for wi, G in zip(w, cfgs))
         assert np.abs(ref_t).max() > 1e-3
         assert np.abs(va.expectation(S["hopping"], S["norm"], lam) - ref_t).max() <= 1e-13

@@ -701,3 +701,31 @@ def test_field_pair_parts_match_oracle(L, n_v, K, prec, tol):
     with pytest.raises(GGFError):
         zc.chains_pairs(PAIRS_FIELD, out=np.zeros((1, z.n_links, 2, 2, 2)))
     zc.close()
+
+
+@pytest.mark.parametrize("L,grp,n_v,K,prec,tol", [
+    (3, gi.Z2, 1, 3, 0, 1e-10),
+    (2, gi.U1, 2, 2, 0, 1e-10),
+    (1, gi.U1, 1, 2, 0, 1e-10),     # self-links: -N_nm / N(G)
+    (4, gi.U1, 1, 2, 1, 1e-4),
+])
+def test_four_point_pair_parts_match_oracle(L, grp, n_v, K, prec, tol):
+    """PAIRS_FOUR against the oracle's per-pair four-point forms; contracted
+    with lambda they give ggf_chains_fermion4."""
+    from oracle import variational
+    from paper_2412_01737_gb300.ggf import PAIRS_FOUR
+    p = gi.make_problem(L, grp, n_v, K, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 2, seed=29), precision=prec, seed=3, delay=8 if prec else 1)
+    if prec:
+        ctx.sample(2)
+    links = ctx.chains_links()
+    fp = ctx.chains_pairs(PAIRS_FOUR)
+    f4 = ctx.chains_fermion4()
+    ctx.close()
+    lm = variational.LocalMatrices(p)
+    for c in range(2):
+        ref = lm(links[c])["four"]
+        assert np.abs(fp[c] - ref).max() <= tol * max(1.0, np.abs(ref).max())
+        con = np.einsum("n,lnm,m->l", np.conj(p.lam), fp[c], p.lam)
+        assert np.abs(con - f4[c]).max() <= tol
