@@ -562,14 +562,19 @@ def run_observables(args):
              "electric_pairs": lambda: ctx.chains_pairs(PAIRS_ELECTRIC, out=ep),
              "site_score": lambda: ctx.chains_score(out=sc),
              "link_score": lambda: ctx.chains_link_score(out=ls)}
+    from paper_2412_01737_gb300.ggf import PAIRS_FIELD, PAIRS_FOUR
+    fp4 = torch.zeros((chains, p.n_links, p.K, p.K, 2), **dev)
+    calls["four_pairs"] = lambda: ctx.chains_pairs(PAIRS_FOUR, out=fp4)
     if p.group == gi.U1:
         calls["electric_field"] = lambda: ctx.chains_electric_field(out=el)
+        calls["field_pairs"] = lambda: ctx.chains_pairs(PAIRS_FIELD, out=ep)
     if p.group in (gi.Z2, gi.U1):
         calls["link_terms"] = lambda: ctx.chains_link_terms(p.q_phys, out=el)
     eb, fb = observable_bytes(p, prec)
     esz = 8 if prec == 0 else 4
     per_pair = p.K * esz + p.K * (p.K - 1) // 2 * 2 * esz
-    read_bytes = {"electric": eb, "electric_pairs": eb, "electric_field": eb, "fermion": fb,
+    read_bytes = {"electric": eb, "electric_pairs": eb, "electric_field": eb, "field_pairs": eb, "fermion": fb,
+                  "four_pairs": p.n_links * 3 * B * B * per_pair,
                   "link_terms": p.n_links * B * B * per_pair,
                   "fermion4": p.n_links * 3 * B * B * per_pair,
                   "site_score": p.V * B * B * per_pair,
