@@ -324,7 +324,8 @@ def test_field_items_match_oracle(emu, L, n_v, K):
         assert np.abs(_c(pairs)[c] - rp).max() <= 1e-11 * max(1.0, np.abs(rp).max())
 
 
-@pytest.mark.parametrize("L,grp,n_v,K", [(2, gi.U1, 1, 2), (3, gi.U1, 1, 2), (2, gi.Z2, 2, 3), (1, gi.U1, 2, 2)])
+@pytest.mark.parametrize("L,grp,n_v,K", [(2, gi.U1, 1, 2), (3, gi.U1, 1, 2), (2, gi.Z2, 2, 3), (1, gi.U1, 2, 2),
+                                         (1, gi.Z2, 2, 1)])
 def test_link_term_items_match_oracle(emu, L, grp, n_v, K):
     """The link-term item on the emulated fermion outputs (combined and per
     pair) against oracle.fermionic's link terms."""
