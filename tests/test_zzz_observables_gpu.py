@@ -1,9 +1,12 @@
 """GPU parity of the per-configuration observables computed from the chains'
 cached inverses: the electric observables of Sec. 5.3 (Z2 link flip, U(1)
-Casimir; ggf_chains_electric) and the fermionic bilinears of Sec. 5.2
-(ggf_chains_fermion).  The oracle evaluates both by the full covariance route
-(itself pinned to explicit Fock vectors).  FP64 chains agree to 1e-10
-relative, FP32 chains to 1e-4.
+Casimir and field, Gauss's law), the fermionic ones of Sec. 5.2 (bilinears,
+four-point function, gauge-invariant link terms), their per-pair parts, the
+scores, Wilson and Polyakov loops, in-memory chain states, and the
+variational helpers built on them (lambda optimisation, reweighted
+gradients, descent).  The oracle evaluates the observables by the full
+covariance route (itself pinned to explicit Fock vectors).  FP64 chains agree
+to 1e-10 relative, FP32 chains to 1e-4.
 """
 import numpy as np
 import pytest
