@@ -115,19 +115,22 @@ ggf_status ggf_get_constants(const ggf_ctx* ctx, int* n_pairs, double* log_c, in
 ggf_status ggf_logweight(ggf_ctx* ctx, int n_cfg, const void* links, double* logN,
                          double* ell, int mem, void* stream);
 
-/* Allocation-free log N(G): the same result as ggf_logweight (Sec. 5 has no
- * counterpart for this call; it exists for callers that cannot allocate
- * device memory when they need the weights, such as code running under
- * stream capture or hosts whose GPU memory is budgeted once at start-up).
- * It calls no cudaMalloc/cudaFree or allocating library routine: all scratch
- * lives in one fixed 32 MiB device array inside the library (held by every
- * GPU that loads the library until the process exits), so M_nm must be at
- * most 1024 x 1024 (N = 8 n_v L^2 <= 1024); larger lattices return
- * GGF_EINVAL.  links [n_cfg][2V] and logN [n_cfg] are DEVICE pointers.  The
- * first call on a device looks up the array's device address (do that first
- * call before any stream capture).  Every call on a device shares the array:
- * calls whose GPU work overlaps race and must be serialised by the caller.
- * Work is enqueued on `stream`; the call does not synchronise. */
+/* Allocation-free log N(G): the same result as ggf_logweight.  The paper has
+ * no counterpart for this call; it exists for callers that cannot allocate
+ * device memory when they need the weights, such as code running while a
+ * stream is captured (where cudaMalloc is not allowed) or hosts whose GPU
+ * memory is budgeted once at start-up.  It calls no cudaMalloc/cudaFree or
+ * allocating library routine: all scratch lives in one fixed 32 MiB device
+ * array inside the library (held by every GPU that loads the library until
+ * the process exits).  The (configuration, pair) factorisations are done in
+ * groups that fit the array, one at a time at the largest size, so any K is
+ * accepted while M_nm is at most 1024 x 1024 (N = 8 n_v L^2 <= 1024); larger
+ * lattices return GGF_EINVAL.  links [n_cfg][2V] and logN [n_cfg] are DEVICE
+ * pointers.  The first call on a device looks up the array's device address
+ * (make that first call before any stream capture).  Every call on a device
+ * shares the array and it keeps the last call's contents: calls whose GPU
+ * work overlaps race and must be serialised by the caller.  Work is enqueued
+ * on `stream`; the call does not synchronise. */
 ggf_status ggf_logweight_noalloc(ggf_ctx* ctx, int n_cfg, const void* links, double* logN, void* stream);
 
 /* Wilson-loop observables from links alone (Sec. 2.3, Sec. 5.1).

@@ -42,16 +42,18 @@ ggf_status scratch_for(ggf_ctx* ctx, void** out) {
     return GGF_OK;
 }
 
-__global__ void na_items(int n_items, int npf, int* cfg, int* pair) {
+// Items i0 .. i0 + n_items - 1 of one family, item = cfg * npf + pair (cfg
+// counted from the start of the current chunk of configurations).
+__global__ void na_items(int i0, int n_items, int npf, int* cfg, int* pair) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_items) { cfg[i] = i / npf; pair[i] = i % npf; }
+    if (i < n_items) { cfg[i] = (i0 + i) / npf; pair[i] = (i0 + i) % npf; }
 }
 
-__global__ void na_write_ell(int n_items, int npf, int pair_off, int P, bool cplx, const cxd* logpf,
+__global__ void na_write_ell(int i0, int n_items, int npf, int pair_off, int P, bool cplx, const cxd* logpf,
                              const cxd* phase, cxd* ell) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n_items) return;
-    int c = it / npf, p = it % npf;
+    int c = (i0 + it) / npf, p = (i0 + it) % npf;
     cxd v = {logpf[it].x, 0.0};
     if (cplx) v.y = atan2(phase[it].y, phase[it].x);
     ell[(size_t)c * P + pair_off + p] = v;
@@ -81,51 +83,57 @@ extern "C" ggf_status ggf_logweight_noalloc(ggf_ctx* ctx, int n_cfg, const void*
     void* base = nullptr;
     GGF_TRY(scratch_for(ctx, &base));
     const size_t NN = (size_t)N * N;
-    // configurations per chunk: their pair log-Pfaffians plus one family's
-    // matrices, factor scratch and item tables must fit in the scratch
-    const int npf_max = std::max(ctx->K, ctx->Kc);
-    int cfg_chunk = 0;
-    for (int c = n_cfg; c >= 1; c = c > 1 ? c / 2 : 0) {
-        int items = c * npf_max;
-        size_t need = align256((size_t)c * P * sizeof(cxd)) + align256(NN * sizeof(cxd) * items) +
-                      align256(ggf_factor_tmp_bytes(N, items)) + 2 * align256((size_t)items * sizeof(int)) +
-                      2 * align256((size_t)items * sizeof(cxd));
-        if (need <= kScratchBytes) { cfg_chunk = c; break; }
-    }
-    if (cfg_chunk == 0) return ggf_fail(ctx, GGF_EINVAL, "ggf_logweight_noalloc: one configuration does not fit the scratch");
+    // Configurations are taken in chunks whose log-Pfaffians (P per
+    // configuration) stay in the scratch until they are combined; within a
+    // chunk each family's (configuration, pair) items are factored in groups
+    // sized to the rest of the scratch (real items at 8 B per entry, complex
+    // at 16 B), so a single item of the largest M (N = kMaxN) always fits.
+    const int cfg_chunk = std::min(n_cfg, 4096);
+    const size_t ell_bytes = align256((size_t)cfg_chunk * P * sizeof(cxd));
+    auto item_bytes = [&](int items, size_t elem) {
+        return align256(NN * elem * items) + align256(ggf_factor_tmp_bytes(N, items)) +
+               2 * align256((size_t)items * sizeof(int)) + 2 * align256((size_t)items * sizeof(cxd));
+    };
     unsigned char* s0 = (unsigned char*)base;
     const size_t lrow = (size_t)g.n_links * (g.group == GGF_Z2 ? 1 : g.group == GGF_SU2 ? 4 * sizeof(double) : sizeof(double));
     for (int c0 = 0; c0 < n_cfg; c0 += cfg_chunk) {
         const int nc = std::min(cfg_chunk, n_cfg - c0);
         const void* lk = (const unsigned char*)links + (size_t)c0 * lrow;
-        unsigned char* q = s0;
-        cxd* ell = (cxd*)q;
-        q += align256((size_t)nc * P * sizeof(cxd));
-        unsigned char* fam_base = q;
+        cxd* ell = (cxd*)s0;
+        unsigned char* fam_base = s0 + ell_bytes;
         for (int fam = 0; fam < 2; ++fam) {
             const bool cplx = fam == 1;
             const int npf = cplx ? ctx->Kc : ctx->K;
             if (npf == 0) continue;
-            const int items = nc * npf;
-            q = fam_base;
-            void* A = q;
-            q += align256(NN * (cplx ? sizeof(cxd) : sizeof(double)) * items);
-            void* ftmp = q;
-            q += align256(ggf_factor_tmp_bytes(N, items));
-            int* d_cfg = (int*)q;
-            q += align256((size_t)items * sizeof(int));
-            int* d_pair = (int*)q;
-            q += align256((size_t)items * sizeof(int));
-            cxd* d_logpf = (cxd*)q;
-            q += align256((size_t)items * sizeof(cxd));
-            cxd* d_phase = (cxd*)q;
-            na_items<<<(items + 127) / 128, 128, 0, st>>>(items, npf, d_cfg, d_pair);
-            GGF_CK(cudaGetLastError());
-            GGF_TRY(ggf_assemble(ctx, !cplx, items, d_cfg, d_pair, lk, A, st));
-            GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, items, A, d_logpf, d_phase, ftmp, st));
-            na_write_ell<<<(items + 127) / 128, 128, 0, st>>>(items, npf, cplx ? ctx->K : 0, P, cplx, d_logpf,
-                                                              d_phase, ell);
-            GGF_CK(cudaGetLastError());
+            const size_t elem = cplx ? sizeof(cxd) : sizeof(double);
+            const int total = nc * npf;
+            int group = 0;
+            for (int it = total; it >= 1; it = it > 1 ? it / 2 : 0)
+                if (ell_bytes + item_bytes(it, elem) <= kScratchBytes) { group = it; break; }
+            if (group == 0)
+                return ggf_fail(ctx, GGF_EINVAL, "ggf_logweight_noalloc: one item does not fit the scratch");
+            for (int i0 = 0; i0 < total; i0 += group) {
+                const int items = std::min(group, total - i0);
+                unsigned char* q = fam_base;
+                void* A = q;
+                q += align256(NN * elem * items);
+                void* ftmp = q;
+                q += align256(ggf_factor_tmp_bytes(N, items));
+                int* d_cfg = (int*)q;
+                q += align256((size_t)items * sizeof(int));
+                int* d_pair = (int*)q;
+                q += align256((size_t)items * sizeof(int));
+                cxd* d_logpf = (cxd*)q;
+                q += align256((size_t)items * sizeof(cxd));
+                cxd* d_phase = (cxd*)q;
+                na_items<<<(items + 127) / 128, 128, 0, st>>>(i0, items, npf, d_cfg, d_pair);
+                GGF_CK(cudaGetLastError());
+                GGF_TRY(ggf_assemble(ctx, !cplx, items, d_cfg, d_pair, lk, A, st));
+                GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, items, A, d_logpf, d_phase, ftmp, st));
+                na_write_ell<<<(items + 127) / 128, 128, 0, st>>>(i0, items, npf, cplx ? ctx->K : 0, P, cplx,
+                                                                  d_logpf, d_phase, ell);
+                GGF_CK(cudaGetLastError());
+            }
         }
         GGF_TRY(ggf_combine(ctx, nc, ell, logN + c0, st));
     }
