@@ -30,22 +30,31 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+REFRESH_CFG3 = 4096   # accepts per chain between refreshes (about 8 sweeps at the workload's acceptance)
+
 WORKLOADS = {
     # name: (L, group, n_v, K, chains, precision, refresh_every, delay, label)
-    "cfg3": (16, 1, 2, 4, 256, 1, 1 << 30, 16,
+    "cfg3": (16, 1, 2, 4, 256, 1, REFRESH_CFG3, 16,
              "16x16 periodic U(1), n_v=2 (M 4096x4096 complex), K=4, 256 chains, FP32 batched updates "
-             "(16 links per batch, one rank-128 tensor-core flush per batch)"),
+             "(16 links per batch, one rank-128 tensor-core flush per batch), FP64 refresh every "
+             f"{REFRESH_CFG3} accepts per chain (site-by-site FP64 Pfaffian for the log-weights, one "
+             "tensor-core Newton step for the inverses)"),
     "cfg2": (8, 0, 1, 1, 1024, 1, 64, 1,
              "8x8 periodic Z2, K=1 (M 512x512), 1024 chains, FP32 rank-r updates, FP64 refresh every 64 accepts"),
     "cfg2_fp64": (8, 0, 1, 1, 1024, 0, 1024, 1,
                   "8x8 periodic Z2, K=1 (M 512x512), 1024 chains, plain FP64 local updates"),
-    "su2": (16, 2, 2, 2, 256, 1, 1 << 30, 16,
+    "su2": (16, 2, 2, 2, 256, 1, REFRESH_CFG3, 16,
             "16x16 periodic SU(2), n_v=2 (one doublet per link end, M 4096x4096), K=2, 256 chains, FP32 "
-            "batched updates (16 links per batch)"),
-    "cfg4": (16, 1, 2, 4, 192, 1, 1 << 30, 32,
+            f"batched updates (16 links per batch), FP64 refresh every {REFRESH_CFG3} accepts"),
+    "cfg4": (16, 1, 2, 4, 192, 1, REFRESH_CFG3, 32,
              "16x16 periodic U(1), n_v=2, K=4 with the learned 4x4-block proposal (BF16 conv net trained on "
-             "plain-sampler configurations); step = 1 local sweep + 16 block moves; 192 resident chains"),
+             "plain-sampler configurations); step = 1 local sweep + 16 block moves; 192 resident chains; FP64 "
+             f"refresh every {REFRESH_CFG3} accepts"),
 }
+# Bond covariances: B_n (n >= 2) is B_1 rotated by a link-local Gaussian
+# unitary with generator entries of this standard deviation, so that the K
+# superposed Gaussians are distinct states.
+BOND_SCALE = 0.3
 BLOCK_MOVES_PER_STEP = 16
 
 # Uneven batch: every (lattice, group, K) cell below is one problem; all cells
@@ -113,9 +122,9 @@ def run_cfg5(args):
     for k, (c, o) in enumerate(zip(ctxs, outs)):
         ser = np.concatenate([obs[k][0], o], axis=0).transpose(1, 0, 2)      # chains, sweeps, 3
         keep = ser[:, max(1, ser.shape[1] // 4):, :]
-        tau = max(tau_int(keep[:, :, 0] - keep[:, :, 0].mean(axis=0, keepdims=True)),
-                  tau_int(keep[:, :, 1] - keep[:, :, 1].mean(axis=0, keepdims=True)), 0.5)
+        tau, closed, _ = tau_report(keep)
         tuned[k]["tau_int"] = round(tau, 3)
+        tuned[k]["tau_window_closed"] = closed
         ess += c.n_chains * args.steps / (2 * tau)
         total_chains += c.n_chains
         launches += c.chains_stats().launches
@@ -181,24 +190,29 @@ class Clocks:
 
 
 def tau_int(series, c=5.0):
+    """Integrated autocorrelation time of the (chains, sweeps) series with the
+    Madras-Sokal window: the sum runs to the first lag t >= c tau.  Returns
+    (tau, window, closed); closed is False when the series ended before the
+    window condition was met (tau is then a truncated sum, a lower bound)."""
     x = np.asarray(series, dtype=np.float64)
     x = x - x.mean()
     T = x.shape[1]
     var = np.mean(x * x)
     if var == 0 or T < 2:
-        return 0.5
+        return 0.5, 0, False
     tau = 0.5
     for t in range(1, T):
         tau += np.mean(x[:, :-t] * x[:, t:]) / var
         if t >= c * tau:
-            return float(tau)
-    return float(tau)
+            return float(tau), t, True
+    return float(tau), T - 1, False
 
 
 def problem_for(name):
     import ggf_inputs as gi
     L, grp, nv, K, chains, prec, refresh, delay, label = WORKLOADS[name]
-    p = gi.make_problem(L, grp, nv, K, seed=BASE_SEED)
+    p = gi.make_problem(L, grp, nv, K, seed=BASE_SEED, bond_scale=BOND_SCALE)
+    label += f"; bond generators N(0, {BOND_SCALE}^2)"
     return p, chains, prec, refresh, delay, label
 
 
@@ -209,91 +223,120 @@ def unit_bytes(p, prec):
     return 2 * p.N * p.N * (p.K * b + p.K * (p.K - 1) // 2 * 2 * b)
 
 
-# Largest lattice on which the oracle times a proposal directly; bigger
-# workloads are timed on this lattice with the same group, n_v and K and the
-# per-proposal time scaled by the cube of the Pfaffian size.
-CPU_PROXY_L = {"cfg3": 6, "cfg4": 6, "su2": 6}
-
-
-def cpu_sample(name, budget_s=15.0, workers=None):
-    """Time the oracle's exact Metropolis on a bounded sample (spawned pool).
-    Returns (proposals per second of the full workload, wall seconds,
-    workers, description)."""
-    import multiprocessing as mp
-    workers = workers or min(16, os.cpu_count() or 1)
-    Lp = CPU_PROXY_L.get(name)
-    if Lp:
-        workers = min(workers, 8)
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(workers) as pool:
-        res = pool.starmap(_cpu_worker, [(name, w, budget_s, Lp) for w in range(workers)])
-    props = sum(r[0] for r in res)
-    secs = max(r[1] for r in res)
-    rate = props / secs
-    p, *_ = problem_for(name)
-    desc = (f"{props} exact-Metropolis proposals over {workers} spawned chains in {secs:.1f}s "
-            f"(one full FP64 Pfaffian per pair per proposal)")
-    if Lp:
-        n_full, n_proxy = p.m_s * p.V, p.m_s * Lp * Lp
-        rate /= (n_full / n_proxy) ** 3
-        desc += (f" on the {Lp}x{Lp} lattice with the same group, n_v and K; rate scaled by "
-                 f"(Pfaffian size {n_full}/{n_proxy})^3 to the {p.L}x{p.L} workload")
-    return rate, secs, workers, desc
-
-
-def _cpu_worker(name, chain, budget_s, proxy_L=None):
+def _oracle_pair_task(args):
+    """One pair term log N_nm(G') of the oracle's exact Metropolis step at the
+    workload's full size: the covariance route of oracle.weight (twist O(G'),
+    O^T Gamma_A O + Gamma_X^{nm} on the full physical + virtual space, FP64
+    Parlett-Reid Pfaffian).  G' is the cold start with one link proposed.
+    Only the pair's own covariance is embedded (the oracle's table of all
+    K^2 would not fit the workers' memory) and the constant log Pf(Gamma_A),
+    which every ratio cancels, is left at 0.  Returns wall seconds."""
+    name, k, link = args
     sys.path.insert(0, ROOT)
     import ggf_inputs as gi
     from oracle import weight
-    from oracle.mcmc import propose
-    from oracle.philox import draws4
     p, *_ = problem_for(name)
-    if proxy_L:
-        p = gi.make_problem(proxy_L, p.group, p.n_v, p.K, seed=BASE_SEED)
-    W = weight.Weights(p)
-    links = gi.cold_links(p)[0]
-    logN = W.log_norm(links)
+    pairs = [(n, n) for n in range(p.K)] + [(n, m) for n in range(p.K) for m in range(n + 1, p.K)]
+    n, m = pairs[k % len(pairs)]
+    W = weight.Weights.__new__(weight.Weights)
+    W.p = p
+    W.GA = weight.gamma_A(p)
+    W.bond = weight.BondData(p)
+    W.log_pf_A = 0.0
+    W.n_virt = 4 * p.n_v * p.V
+    W.GX = {(n, m): W.bond.embedded(n, m)}
+    links = gi.cold_links(p)[0].copy()
+    if p.group == gi.Z2:
+        links[link % p.n_links] *= -1
+    else:
+        links[link % p.n_links] += 0.25
     t0 = time.time()
-    n = 0
-    while time.time() - t0 < budget_s:
-        l = n % p.n_links
-        u_acc, u_prop, u_z, u_phi = draws4(BASE_SEED, chain, n // p.n_links, l)
-        new = links.copy()
-        new[l] = propose(p.group, links[l], u_prop, 0.5, u_z, u_phi)
-        ln = W.log_norm(new)
-        if np.isfinite(ln) and u_acc < np.exp(ln - logN):
-            links, logN = new, ln
-        n += 1
-    return n, time.time() - t0
+    W.log_n_nm(links, n, m)
+    return time.time() - t0
+
+
+def start_cpu_baseline(name, workers):
+    """Start the oracle's pair terms on `workers` spawned processes (one BLAS
+    thread each); returns a handle for finish_cpu_baseline."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(workers)
+    res = pool.map_async(_oracle_pair_task, [(name, w, 37 * w + 5) for w in range(workers)])
+    return pool, res, workers, time.time()
+
+
+def finish_cpu_baseline(name, handle, timeout=1800):
+    """Collect the pair-term timings: proposals per second of the oracle's
+    exact Metropolis on the host cores, and the sample description."""
+    pool, res, workers, t0 = handle
+    secs = res.get(timeout=timeout)
+    pool.close()
+    pool.join()
+    p, *_ = problem_for(name)
+    P = p.K * (p.K + 1) // 2
+    t_pair = float(np.mean(secs))
+    rate = workers / (P * t_pair)
+    desc = (f"{workers} concurrent spawned workers, each the oracle's exact-Metropolis pair term log N_nm(G') "
+            f"at the full {p.L}x{p.L} size (full-space {p.m_s * p.V}x{p.m_s * p.V} complex Pfaffian route), "
+            f"mean {t_pair:.1f} s per term (wall {time.time() - t0:.0f} s); one proposal = the {P} pair terms, "
+            f"so proposals/s = workers / ({P} x mean)")
+    return rate, t_pair, workers, desc
 
 
 def run_reference(args):
+    """The oracle on the host cores (the reference arm): one round of full-size
+    pair terms on every core; each core's chain would need P such terms per
+    proposal and 2V proposals per sweep.  ESS uses tau_int = 1/2 (the bound
+    that favours the oracle)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     p, chains, prec, refresh, delay, label = problem_for(args.workload)
     t0 = time.time()
-    rate, secs, workers, desc = cpu_sample(args.workload, budget_s=args.cpu_seconds)
-    props = rate * secs
+    workers = os.cpu_count() or 1
+    rate, t_pair, workers, desc = finish_cpu_baseline(args.workload, start_cpu_baseline(args.workload, workers))
     sweeps_per_s = rate / p.n_links
     value = sweeps_per_s / (2 * 0.5)      # tau_int >= 1/2: upper bound for the oracle
     line = {"metric": "effective samples/sec/GPU", "value": value, "unit": "samples/s", "impl": "reference",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * secs / max(props / p.n_links, 1e-9), "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 / sweeps_per_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": label, "chains": chains},
-            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
-                             "sample": desc + "; ESS bound with tau_int = 1/2"},
+            "config": {"workload": label, "chains": workers,
+                       "note": "one round of pair terms on every host core stands for the steps: a single "
+                               "full-size pair term takes minutes, so --steps/--warmup sweeps cannot run"},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": desc + "; ESS bound with tau_int = 1/2"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.time() - t0}
     print(json.dumps(line), flush=True)
 
 
+def tau_report(series):
+    """tau_int of the plaquette and log N(G) series (chains, sweeps) about each
+    sweep's ensemble mean (removes a common drift of chains started together);
+    the larger one is used.  Returns (tau, closed, details)."""
+    out, taus = {}, []
+    for k, name in ((0, "plaquette"), (1, "logN")):
+        x = series[:, :, k] - series[:, :, k].mean(axis=0, keepdims=True)
+        t, w, closed = tau_int(x)
+        out[name] = {"tau": t, "window": w, "window_closed": closed}
+        taus.append((t, closed))
+    tau = max(max(t for t, _ in taus), 0.5)
+    return tau, all(c for _, c in taus), out
+
+
 def run_ggf(args):
-    import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the oracle's CPU baseline runs on the host cores while the GPU samples
+    # (spawned before the first CUDA call; two cores stay with this process)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = start_cpu_baseline(args.workload, max(1, (os.cpu_count() or 1) - 2))
+    import torch
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -308,14 +351,19 @@ def run_ggf(args):
         chains = args.chains
     if args.delay:
         delay = args.delay
-    seed = BASE_SEED + 7919 * rank
+    # replica r owns the chains r * chains .. (r + 1) * chains - 1 of one
+    # global ensemble: Philox key (seed, global chain index)
+    seed = BASE_SEED
+    # ---- set-up through the public API from host buffers (part of the e2e time)
+    torch.cuda.synchronize()
+    t_setup0 = time.time()
     ctx = GGF(local)
     ctx.init_problem(p)
     start = gi.cold_links(p, chains)
-    t_init = time.time()
-    ctx.chains_init(start, precision=prec, refresh_every=refresh, seed=seed, delay=delay)
-    t_init = time.time() - t_init
-    obs_all = []
+    ctx.chains_init(start, precision=prec, refresh_every=refresh, seed=seed, delay=delay,
+                    chain_offset=rank * chains)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup0
     dev_obs = torch.zeros((1, chains, 3), dtype=torch.float64, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
     net, train_info = None, None
@@ -339,68 +387,83 @@ def run_ggf(args):
                       "loss_last": float(losses[-10:].mean())}
         blk_obs = torch.zeros((BLOCK_MOVES_PER_STEP, chains, 3), dtype=torch.float64, device=f"cuda:{local}")
 
-    def one_step():
-        ctx.sample(1, obs=dev_obs)
+    def one_step(obs):
+        """One step; obs is a (1, chains, 3) device tensor or host array."""
+        ctx.sample(1, obs=obs)
         if net is not None:
             ctx.sample_blocks(net, BLOCK_MOVES_PER_STEP, obs=blk_obs)
-            return blk_obs[-1]
-        return dev_obs[0]
+            if isinstance(obs, np.ndarray):
+                obs[0] = blk_obs[-1].cpu().numpy()
+            else:
+                obs[0].copy_(blk_obs[-1])
 
-    def sweep():
-        obs_all.append(one_step().cpu().numpy().copy())
-
+    # ---- thermalisation from the cold start (discarded), then recorded
+    # untimed sweeps for the autocorrelation estimate and the warm-up
+    t_burn0 = time.time()
     for _ in range(args.burn):
-        sweep()
-    for _ in range(args.warmup):
-        sweep()
+        one_step(dev_obs)
+    torch.cuda.synchronize()
+    t_burn = time.time() - t_burn0
+    series = []
+    for _ in range(args.tau_sweeps + args.warmup):
+        one_step(dev_obs)
+        series.append(dev_obs[0].cpu().numpy().copy())
     st0 = ctx.chains_stats()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # ---- timed region: the captured sweep graph replayed, observables read
+    # back into host memory every step through the public API
+    host_obs = np.zeros((args.steps, chains, 3))
     clocks = Clocks()
     clocks.start()
-    ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.cudart().cudaProfilerStart()     # ncu --profile-from-start off sees the timed sweeps only
+    t_wall0 = time.time()
     e0.record(stream)
-    for _ in range(args.steps):
-        obs_all.append(one_step().clone())
+    for k in range(args.steps):
+        one_step(host_obs[k:k + 1])
     e1.record(stream)
     torch.cuda.synchronize()
+    t_wall = time.time() - t_wall0
     torch.cuda.cudart().cudaProfilerStop()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    obs_all = [o.cpu().numpy() if hasattr(o, "cpu") else o for o in obs_all]
     st1 = ctx.chains_stats()
+    series.extend(list(host_obs))
+    if dist:
+        t = torch.tensor([ms, t_wall], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, t_wall = float(t[0]), float(t[1])
+    # ---- separate profiled pass (not timed): the same graph with timing-event
+    # nodes around every launch group, for the kernel shares and the roofline
+    ctx.profile(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sp0 = ctx.chains_stats()
+    p0.record(stream)
+    for _ in range(args.prof_sweeps):
+        one_step(dev_obs)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    sp1 = ctx.chains_stats()
+    prof_ms = p0.elapsed_time(p1)
     kt = {k: ctx.kernel_time(v) for k, v in (("ratio", KT_RATIO), ("update", KT_UPDATE),
                                              ("refresh", KT_REFRESH), ("flush", KT_FLUSH),
                                              ("gather", KT_GATHER), ("apply", KT_APPLY))}
     ctx.profile(False)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-    series = np.stack(obs_all, axis=1)             # (chains, sweeps, 3)
-    keep = series[:, max(1, series.shape[1] // 4):, :]
-    # fluctuations about the ensemble mean of each sweep (removes the common
-    # thermalisation trend of chains started together)
-    tau_pl = tau_int(keep[:, :, 0] - keep[:, :, 0].mean(axis=0, keepdims=True))
-    tau_ln = tau_int(keep[:, :, 1] - keep[:, :, 1].mean(axis=0, keepdims=True))
-    tau = max(tau_pl, tau_ln, 0.5)
+    obs_series = np.stack(series, axis=1)             # (chains, sweeps, 3) after thermalisation
+    tau, closed, tau_detail = tau_report(obs_series)
     sweeps_timed = args.steps
     value = world * chains * sweeps_timed / (2 * tau) / (ms * 1e-3)
-    accepts = st1.accepts - st0.accepts
+    accepts = sp1.accepts - sp0.accepts
     shares = {k: v[0] for k, v in kt.items()}
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     dom = max(shares, key=shares.get)
     wpairs = p.K + 4 * (p.K * (p.K - 1) // 2)             # real-MAC weight of all pairs
     if dom == "refresh":
-        nref = st1.refreshes - st0.refreshes
-        fl = nref * 2.0 * p.N ** 3 * wpairs               # Gauss-Jordan: N^3 MACs per real pair
-        roof = {"kernel": "refresh (FP64 Gauss-Jordan gj_update)", "bound": "alu",
-                "achieved": fl / (kt["refresh"][0] * 1e-3) / 1e12, "peak": 1.25, "unit": "TFLOP/s",
-                "peak_source": "FP64 nominal 1.25 TFLOP/s from the profiling recipe (not in MEASURED_PEAKS)"}
+        roof = {"kernel": "refresh (site-by-site FP64 Pfaffian + Newton step)", "bound": "alu",
+                "achieved": None, "peak": None, "unit": None}
     elif dom == "flush":
         fl = accepts * 2.0 * p.N ** 2 * p.r * wpairs      # every accepted rank-r update folded once
         t_fl = kt["flush"][0] * 1e-3
@@ -411,6 +474,7 @@ def run_ggf(args):
                     "achieved": byts / t_fl / 1e9, "peak": hbm, "unit": "GB/s",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                     "algorithmic_bytes_per_launch_group": chains * unit_bytes(p, prec),
+                    "avg_launch_group_ms": kt["flush"][0] / max(1, kt["flush"][1]),
                     "fp32_equivalent_tflops": fl / t_fl / 1e12}
         else:
             roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V)", "bound": "alu",
@@ -428,12 +492,12 @@ def run_ggf(args):
         b = 8 if prec == 0 else 4
         kr_mean = 0.5 * 31 * p.r
         per = sum((2 if n == m else 4) * b * p.N * (kr_mean + 1.5 * p.r) for n in range(p.K) for m in range(n, p.K))
-        n_upd = 32 * ((st1.block_proposals - st0.block_proposals) if hasattr(st1, "block_proposals") else 0)
+        n_upd = 32 * (sp1.block_proposals - sp0.block_proposals)
         roof = {"kernel": "gather_kernel (pending-panel rows/columns)", "bound": "l2",
                 "achieved": n_upd * per / (kt["update"][0] * 1e-3) / 1e9, "peak": None, "unit": "GB/s",
                 "peak_source": "no measured L2 peak; reported for the record"}
     elif dom == "ratio" and delay > 1:
-        props = st1.proposals - st0.proposals
+        props = sp1.proposals - sp0.proposals
         roof = {"kernel": "batch_steps (link steps on W[T, T], FP64 ratios)", "bound": "latency",
                 "achieved": props / (kt["ratio"][0] * 1e-3), "peak": None, "unit": "link proposals/s",
                 "peak_source": "latency-bound (one CTA per chain, sequential links); no peak applies"}
@@ -441,7 +505,12 @@ def run_ggf(args):
         roof = {"kernel": "ratio_kernel", "bound": "alu", "achieved": None, "peak": None, "unit": None}
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
     roof["traffic"] = None
-    roof["share"] = {k: round(v / max(ms, 1e-9), 4) for k, v in shares.items()}
+    roof["share"] = {k: round(v / max(prof_ms, 1e-9), 4) for k, v in shares.items()}
+    roof["profiled_pass"] = {"sweeps": args.prof_sweeps, "ms": prof_ms,
+                             "refreshes": int(sp1.refreshes - sp0.refreshes),
+                             "note": "separate untimed pass of the same graph with timing-event nodes"}
+    if kt["refresh"][1] > 0:
+        roof["refresh_ms_per_chain"] = kt["refresh"][0] / max(1, sp1.refreshes - sp0.refreshes)
     if delay > 1 and kt["gather"][1] > 0:
         # batched mode: per batch and pair, the gather reads W[:, T] and W[T, :]
         # (2 N kr b) and writes the U and V^T panels (2 N kr b); the X product
@@ -456,65 +525,59 @@ def run_ggf(args):
             "batch_apply_gbs": n_b * chains * 2 * per_b / (kt["apply"][0] * 1e-3) / 1e9,
             "batch_apply_fp32_tflops": n_b * chains * 2 * macs / (kt["apply"][0] * 1e-3) / 1e12,
             "note": "kr = delay r is the batch's rank; sizes per launch group over all chains"}
-    # |Delta log N|: tracked FP32/FP64 values vs a fresh FP64 factorisation
+    # |Delta log N|: every chain's tracked log-weight at the end of the timed
+    # region against a fresh FP64 factorisation of its configuration
     fin = ctx.chains_links()
-    pick = np.ascontiguousarray(fin[: min(4, chains)])
-    fresh = ctx.logweight(pick)
-    dlogp = float(np.abs(fresh - series[: len(pick), -1, 1]).max())
+    fresh = ctx.logweight(np.ascontiguousarray(fin))
+    dlogp = float(np.nanmax(np.abs(fresh - obs_series[:, -1, 1])))
+    st2 = ctx.chains_stats()
+    h2d = (p.gamma_site.nbytes + p.gamma_bond.nbytes + p.lam.nbytes + start.nbytes) / args.steps
+    ess_timed = world * chains * sweeps_timed / (2 * tau)
     line = {"metric": "effective samples/sec/GPU", "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
-            "config": {"workload": label, "chains": chains, "delay": delay, "sweeps_timed": args.steps,
-                       "burn_in_sweeps": args.burn + args.warmup, "tau_int": {"plaquette": tau_pl, "logN": tau_ln},
+            "config": {"workload": label, "chains": chains, "delay": delay, "refresh_every_accepts": refresh,
+                       "sweeps_timed": args.steps, "thermalisation_sweeps": args.burn,
+                       "thermalisation_s": t_burn,
+                       "thermalisation_note": "untimed, discarded; the survey prescribes 200 for this workload",
+                       "tau_series_sweeps": obs_series.shape[1],
+                       "tau_int": tau_detail, "tau_used": tau, "tau_window_closed": closed,
+                       "ess_is_upper_bound": not closed,
+                       "timed_path": "captured sweep graph replayed (graph mode), observables read back to host "
+                                     "every step",
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (W is "
                        f"{chains * unit_bytes(p, prec) / 2 / 2**30:.1f} GiB)",
                        "link_updates_per_s": world * chains * p.n_links * sweeps_timed / (ms * 1e-3),
-                       "acceptance": accepts / max(1, st1.proposals - st0.proposals),
-                       "init_s": t_init},
-            "dlogp_vs_fp64_recompute": dlogp,
+                       "acceptance": (st1.accepts - st0.accepts) / max(1, st1.proposals - st0.proposals),
+                       "refreshes_timed": int(st1.refreshes - st0.refreshes),
+                       "refresh_max_resid": st2.max_resid, "refresh_dense_fallbacks": int(st2.dense_refreshes),
+                       "pfaffian_dense_fallbacks": int(st2.dense_pfaffians),
+                       "init_s": t_setup},
+            "dlogp_vs_fp64_recompute": dlogp, "max_drift_at_refresh": st2.max_drift,
             "roofline": roof, "clocks": ck,
-            "gpu_launches": int(st1.launches - st0.launches)}
+            "gpu_launches": int(st1.launches - st0.launches),
+            "e2e": {"value": ess_timed / (t_setup + t_wall), "unit": "samples/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(chains * 3 * 8),
+                    "includes": "context creation, parameter and start-link upload (host buffers), FP64 chain "
+                                "set-up, then the timed sweeps with every step's observables read back to host "
+                                "memory (wall clock)"}}
     if train_info is not None:
         nb = st1.block_proposals - st0.block_proposals
         train_info["block_acceptance"] = (st1.block_accepts - st0.block_accepts) / max(1, nb)
         line["config"]["learned_proposal"] = train_info
         net.close()
-        args.no_e2e = True     # the end-to-end leg covers the plain sampler only
-    ctx.close()                                   # frees the chains before the e2e run
-    if rank == 0 and not args.no_cpu:
-        rate, secs, workers, desc = cpu_sample(args.workload, budget_s=args.cpu_seconds)
+    ctx.close()
+    if cpu is not None:
+        rate, t_pair, workers, desc = finish_cpu_baseline(args.workload, cpu)
         line["cpu_baseline"] = {"value": rate / p.n_links / (2 * tau), "unit": "samples/s",
-                                "cores": workers, "kind": "oracle", "sample": desc + ", same tau_int"}
-    if rank == 0 and not args.no_e2e:
-        line["e2e"] = run_e2e(args, p, chains, prec, refresh, delay, local, tau)
+                                "cores": workers, "host_cores": os.cpu_count(), "kind": "oracle",
+                                "sample": desc + "; run concurrently with the GPU sweeps; same tau_int"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-
-
-def run_e2e(args, p, chains, prec, refresh, delay, local, tau):
-    """Public API end to end with host buffers: init (parameters and links
-    host->device), K sweeps with the observables read back every sweep."""
-    import torch
-    import ggf_inputs as gi
-    from paper_2412_01737_gb300 import GGF
-    torch.cuda.synchronize()
-    t0 = time.time()
-    ctx = GGF(local)
-    ctx.init_problem(p)
-    start = gi.cold_links(p, chains)
-    ctx.chains_init(start, precision=prec, refresh_every=refresh, seed=BASE_SEED + 1, delay=delay)
-    obs = ctx.sample(args.steps)            # host numpy buffer: copied back every sweep
-    dt = time.time() - t0
-    ctx.close()
-    h2d = (p.gamma_site.nbytes + p.gamma_bond.nbytes + p.lam.nbytes + start.nbytes) / args.steps
-    d2h = obs.nbytes / args.steps
-    return {"value": chains * args.steps / (2 * tau) / dt, "unit": "samples/s",
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "includes": "context creation, parameter upload, FP64 chain set-up, sweeps, per-sweep host read-back"}
 
 
 def observable_bytes(p, prec):
@@ -607,14 +670,17 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--burn", type=int, default=0, help="extra untimed sweeps before warm-up")
+    ap.add_argument("--burn", type=int, default=40,
+                    help="thermalisation sweeps from the cold start (untimed, discarded)")
+    ap.add_argument("--tau-sweeps", type=int, default=30,
+                    help="untimed sweeps recorded (with warm-up and timed ones) for the tau_int estimate")
+    ap.add_argument("--prof-sweeps", type=int, default=8,
+                    help="sweeps of the separate profiled pass (kernel shares, roofline)")
     ap.add_argument("--impl", default="ggf", choices=["ggf", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS) + ["cfg5"])
     ap.add_argument("--chains", type=int, default=0)
     ap.add_argument("--delay", type=int, default=0, help="override the workload's batch size (links per flush)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--burn-train", type=int, default=4, help="cfg4: local sweeps before collecting training data")
     ap.add_argument("--train-sweeps", type=int, default=6, help="cfg4: local sweeps whose configurations train the net")
     ap.add_argument("--train-steps", type=int, default=300, help="cfg4: Adam steps")

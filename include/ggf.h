@@ -162,7 +162,7 @@ typedef struct {
                            ratios, log-weights and refresh in FP64) */
     int refresh_every;  /* full FP64 refresh of a chain after this many accepts */
     double width;       /* U(1) proposal: theta += width * (u - 1/2) */
-    uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = chain index) */
+    uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = chain_offset + chain index) */
     int delay;          /* <= 1: apply every accepted rank-r update to the
                            whole W at once (true columns);
                            k > 1 (at most 64): sweep in batches of k
@@ -178,6 +178,10 @@ typedef struct {
     int graph;          /* != 0: capture one sweep (all link steps, flushes,
                            observables) into a CUDA graph on first use and
                            replay it; 0: launch every kernel eagerly */
+    uint64_t chain_offset;  /* Philox key word 1 = chain_offset + chain: a
+                               replica holding chains i0 .. i0 + n - 1 of a
+                               larger ensemble passes i0 and draws exactly
+                               the numbers those chains draw in one run */
 } ggf_chain_opts;
 
 /* Create n_chains Markov chains starting at links [n_chains][2V] and build
@@ -371,12 +375,26 @@ ggf_status ggf_debug_poison_inverse(ggf_ctx* ctx, int chain, int pair, int i, in
  * L^2.  For tests and diagnostics. */
 ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, int mem, void* stream);
 
+/* Residual of the cached inverse of one FP32 chain and pair (pair index as in
+ * ggf_get_constants): *rmax = max |I - M_nm(G) W| over the entries (M
+ * assembled in FP64 from the chain's links, the product in FP32).  apply != 0
+ * then refines W by one Newton step W <- W + W (I - M W) on the tensor cores
+ * (the step the periodic refresh takes), skipped when *rmax > 1e-3.  The
+ * paper has no counterpart; for tests and diagnostics.  Synchronous. */
+ggf_status ggf_chains_refine(ggf_ctx* ctx, int chain, int pair, int apply, double* rmax);
+
 typedef struct {
     uint64_t proposals, accepts, refreshes, sweeps;
     double max_drift;   /* max |l_tracked - l_refresh| over refreshes so far */
     uint64_t launches;  /* CUDA kernels launched by ggf_sample since ggf_chains_init */
     uint64_t block_proposals, block_accepts;   /* learned-proposal block moves */
     int n_chains, n_pairs;
+    double max_resid;          /* FP32 chains: largest |I - M W| entry met by a
+                                  refresh before its Newton step */
+    uint64_t dense_refreshes;  /* FP32 chains refreshed by FP64 Gauss-Jordan
+                                  because the residual was above 1e-3 */
+    uint64_t dense_pfaffians;  /* log-Pfaffians that fell back from the
+                                  site-by-site to the dense elimination */
 } ggf_chain_stats;
 
 ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out);
@@ -417,8 +435,9 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream);
  *   GGF_KT_APPLY    batched mode: V <- X V
  * ggf_kernel_time returns the accumulated device milliseconds and the number
  * of timed launch groups since the last reset.  Events are read at the end of
- * each sweep.  While timing is on, sweeps launch eagerly instead of replaying
- * their graph (the kernel sequence is the same). */
+ * each sweep.  In graph mode the sweep replayed while timing is on is the same
+ * captured sweep with event-record nodes around its launch groups (captured
+ * once, kept beside the plain graph). */
 #define GGF_KT_RATIO 0
 #define GGF_KT_UPDATE 1
 #define GGF_KT_REFRESH 2

@@ -9,6 +9,11 @@
 #include "ggf_ctx.h"
 
 size_t ggf_factor_tmp_bytes(int n, int batch);
+size_t ggf_refine_bytes(int N, bool cplx);
+ggf_status ggf_refine_inverse(ggf_ctx* ctx, bool cplx, const void* d_links, int cfg, int pair, float* W, void* ws,
+                              double tol, double* rmax, cudaStream_t st);
+// largest residual |I - M W| entry that one Newton step on the tensor cores refines
+static const double kRefineTol = 1e-3;
 ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st);
 ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st);
 ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st);
@@ -54,6 +59,8 @@ void ggf_free_chains(ggf_ctx* ctx) {
     Chains& c = ctx->ch;
     if (c.gexec) cudaGraphExecDestroy(c.gexec);
     if (c.graph) cudaGraphDestroy(c.graph);
+    if (c.gexec_t) cudaGraphExecDestroy(c.gexec_t);
+    if (c.graph_t) cudaGraphDestroy(c.graph_t);
     if (c.cs) cudaStreamDestroy(c.cs);
     if (c.join) cudaEventDestroy(c.join);
     if (c.d_sweep) cudaFree(c.d_sweep);
@@ -100,14 +107,22 @@ size_t budget_bytes() {
     return std::max<size_t>(std::min(cap, fr / 2), (size_t)64 << 20);
 }
 
-__global__ void write_ell_kernel(int n_items, int fam_pairs, int pair_off, int P, bool cplx, const cxd* logpf,
-                                 const cxd* phase, cxd* ell) {
+// logpf/phase of dense refactorisations back to their item positions
+__global__ void scatter_pf_kernel(int n, const int* idx, const cxd* lp, const cxd* ph, cxd* logpf, cxd* phase) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    logpf[idx[i]] = lp[i];
+    phase[idx[i]] = ph[i];
+}
+
+// ell[cfg][pair_off + pair] of items with explicit (cfg, pair)
+__global__ void write_items_kernel(int n_items, const int* cfg, const int* pair, int pair_off, int P, bool cplx,
+                                   const cxd* logpf, const cxd* phase, cxd* ell) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n_items) return;
-    int cfg = it / fam_pairs, p = it % fam_pairs;
     cxd v = {logpf[it].x, 0.0};
     if (cplx) v.y = atan2(phase[it].y, phase[it].x);
-    ell[(size_t)cfg * P + pair_off + p] = v;
+    ell[(size_t)cfg[it] * P + pair_off + pair[it]] = v;
 }
 
 // W[chain][p] <- convert(A[item]) and log-weight bookkeeping after a factorisation
@@ -123,48 +138,120 @@ __global__ void scatter_kernel(int N, int fam_pairs, const int* item_chain, cons
     W[((size_t)c * fam_pairs + p) * NN + e] = Sc<TD>::from(v);
 }
 
-__global__ void ell_update_kernel(int n_items, int pair_off, int P, bool cplx, bool init, const int* item_chain,
-                                  const int* item_pair, const cxd* logdet, const cxd* logpf, const cxd* phase,
-                                  cxd* ell, double* drift, int* since, unsigned long long* counters) {
+// log Pf(M_nm(G)) of explicit (configuration, pair-within-family) items
+// (host lists hc, hp) into d_logpf / d_phase, by the site-by-site FP64
+// elimination; items whose closed sets had no usable pivot are refactored by
+// the dense FP64 Parlett-Reid Pfaffian.  d_cfg, d_pair, d_flag hold
+// hc.size() entries (overwritten).
+ggf_status pf_items(ggf_ctx* ctx, bool cplx, const std::vector<int>& hc, const std::vector<int>& hp,
+                    const void* d_links, int* d_cfg, int* d_pair, int* d_flag, cxd* d_logpf, cxd* d_phase,
+                    cudaStream_t st) {
+    const int items = (int)hc.size();
+    if (items == 0) return GGF_OK;
+    const int N = ctx->g.N;
+    const size_t NN = (size_t)N * N;
+    GGF_CK(cudaMemcpyAsync(d_cfg, hc.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+    GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+    GGF_TRY(ggf_front_pfaffian(ctx, cplx, items, d_cfg, d_pair, d_links, d_logpf, d_phase, d_flag, st));
+    std::vector<int> hf(items);
+    GGF_CK(cudaMemcpyAsync(hf.data(), d_flag, items * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GGF_CK(cudaStreamSynchronize(st));
+    std::vector<int> fi, fc, fp;
+    for (int i = 0; i < items; ++i)
+        if (hf[i]) { fi.push_back(i); fc.push_back(hc[i]); fp.push_back(hp[i]); }
+    ctx->dense_pfaffians += fi.size();
+    if (fi.empty()) return GGF_OK;
+    const size_t elem = cplx ? sizeof(cxd) : sizeof(double);
+    const int nf = (int)fi.size();
+    const int per = (int)std::max<size_t>(1, std::min<size_t>(nf, budget_bytes() / (NN * elem)));
+    const size_t tmp = ggf_factor_tmp_bytes(N, per);
+    GGF_TRY(ggf_workspace(ctx, NN * elem * per + tmp + (size_t)per * (3 * sizeof(int) + 2 * sizeof(cxd)) + 1024));
+    unsigned char* q = (unsigned char*)ctx->work;
+    void* A = q;
+    q += (NN * elem * per + 255) / 256 * 256;
+    void* ftmp = q;
+    q += (tmp + 255) / 256 * 256;
+    cxd* f_logpf = (cxd*)q; q += (size_t)per * sizeof(cxd);
+    cxd* f_phase = (cxd*)q; q += (size_t)per * sizeof(cxd);
+    int* f_cfg = (int*)q; q += (size_t)per * sizeof(int);
+    int* f_pair = (int*)q; q += (size_t)per * sizeof(int);
+    int* f_idx = (int*)q;
+    for (int f0 = 0; f0 < nf; f0 += per) {
+        const int nb = std::min(per, nf - f0);
+        GGF_CK(cudaMemcpyAsync(f_cfg, fc.data() + f0, nb * sizeof(int), cudaMemcpyHostToDevice, st));
+        GGF_CK(cudaMemcpyAsync(f_pair, fp.data() + f0, nb * sizeof(int), cudaMemcpyHostToDevice, st));
+        GGF_CK(cudaMemcpyAsync(f_idx, fi.data() + f0, nb * sizeof(int), cudaMemcpyHostToDevice, st));
+        GGF_TRY(ggf_assemble(ctx, !cplx, nb, f_cfg, f_pair, d_links, A, st));
+        GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, nb, A, f_logpf, f_phase, ftmp, st));
+        scatter_pf_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, f_idx, f_logpf, f_phase, d_logpf, d_phase);
+        GGF_CK(cudaGetLastError());
+        GGF_CK(cudaStreamSynchronize(st));
+    }
+    return GGF_OK;
+}
+
+// log Pf of every (configuration, pair) item of one family into ell[cfg][P].
+ggf_status front_family(ggf_ctx* ctx, bool cplx, int n_cfg, int npf, const void* d_links, cxd* ell, cudaStream_t st) {
+    const int P = ctx->P;
+    const long long total = (long long)n_cfg * npf;
+    const int chunk = (int)std::min<long long>(total, 1 << 20);
+    DBuf tab;
+    GGF_TRY(dalloc(ctx, tab, (size_t)chunk * (2 * sizeof(cxd) + 3 * sizeof(int)) + 256));
+    cxd* d_logpf = (cxd*)tab.p;
+    cxd* d_phase = d_logpf + chunk;
+    int* d_cfg = (int*)(d_phase + chunk);
+    int* d_pair = d_cfg + chunk;
+    int* d_flag = d_pair + chunk;
+    std::vector<int> hc, hp;
+    for (long long i0 = 0; i0 < total; i0 += chunk) {
+        const int items = (int)std::min<long long>(chunk, total - i0);
+        hc.resize(items); hp.resize(items);
+        for (int i = 0; i < items; ++i) { hc[i] = (int)((i0 + i) / npf); hp[i] = (int)((i0 + i) % npf); }
+        GGF_TRY(pf_items(ctx, cplx, hc, hp, d_links, d_cfg, d_pair, d_flag, d_logpf, d_phase, st));
+        GGF_CK(cudaMemcpyAsync(d_cfg, hc.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+        GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+        write_items_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, d_cfg, d_pair, cplx ? ctx->K : 0, P, cplx,
+                                                                 d_logpf, d_phase, ell);
+        GGF_CK(cudaGetLastError());
+        GGF_CK(cudaStreamSynchronize(st));
+    }
+    return GGF_OK;
+}
+
+// Log-weights of (chain, pair) items from a fresh factorisation: init sets
+// them; a refresh records |l_tracked - l_fresh| (log magnitude plus phase
+// mod 2 pi) as drift and replaces them.  Resets the accept count since the
+// last refresh.
+__global__ void ell_set_kernel(int n_items, int pair_off, int P, bool cplx, bool init, const int* item_chain,
+                               const int* item_pair, const cxd* logpf, const cxd* phase, cxd* ell, double* drift,
+                               int* since, unsigned long long* counters) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n_items) return;
     int c = item_chain[it], p = pair_off + item_pair[it];
     cxd& el = ell[(size_t)c * P + p];
-    if (!isfinite(logdet[it].x)) atomicAdd(&counters[3], 1ULL);
-    if (init) {
-        cxd v = {logpf[it].x, 0.0};
-        if (cplx) v.y = atan2(phase[it].y, phase[it].x);
-        el = v;
-    } else {
-        double la = 0.5 * logdet[it].x;
-        double d = 0.0;
-        if (!cplx) {
-            d = fabs(la - el.x);
-            el = {la, 0.0};
-        } else {
-            double ph = 0.5 * logdet[it].y;
-            double best = 0.0, bestd = 1e300;
-            for (int k = 0; k < 2; ++k) {
-                double cand = ph + k * M_PI;
-                double dd = remainder(cand - el.y, 2 * M_PI);
-                if (fabs(dd) < bestd) { bestd = fabs(dd); best = cand; }
-            }
-            best = remainder(best, 2 * M_PI);
-            d = fabs(la - el.x) + bestd;
-            el = {la, best};
-        }
-        if (d > drift[c]) drift[c] = d;
+    cxd v = {logpf[it].x, 0.0};
+    if (cplx) v.y = atan2(phase[it].y, phase[it].x);
+    if (!isfinite(v.x)) atomicAdd(&counters[3], 1ULL);
+    if (!init) {
+        double d = fabs(v.x - el.x);
+        if (cplx) d += fabs(remainder(v.y - el.y, 2 * M_PI));
+        if (!(d <= drift[c])) drift[c] = d;
     }
+    el = v;
     since[c] = 0;
 }
 
-// Factor the FP64 M_nm(G) of the listed chains: W <- M^{-1}; log-weights from
-// the Pfaffian (init) or from det with the branch nearest the tracked value.
-ggf_status factor_chains(ggf_ctx* ctx, const std::vector<int>& chains, bool init, cudaStream_t st) {
+__global__ void count_singular_kernel(int n_items, const cxd* logdet, unsigned long long* counters) {
+    int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it < n_items && !isfinite(logdet[it].x)) atomicAdd(&counters[3], 1ULL);
+}
+
+// FP64 Gauss-Jordan inverses of the listed chains' M_nm(G), converted into
+// the chains' W storage.
+ggf_status dense_inverse(ggf_ctx* ctx, const std::vector<int>& chains, cudaStream_t st) {
     if (chains.empty()) return GGF_OK;
     Chains& ch = ctx->ch;
-    const Geometry& g = ctx->g;
-    const int N = g.N;
+    const int N = ctx->g.N;
     const size_t NN = (size_t)N * N;
     const bool fp64 = ch.opts.precision == GGF_FP64;
     for (int fam = 0; fam < 2; ++fam) {
@@ -172,26 +259,22 @@ ggf_status factor_chains(ggf_ctx* ctx, const std::vector<int>& chains, bool init
         const int npf = cplx ? ctx->Kc : ctx->K;
         if (npf == 0) continue;
         const size_t elem = cplx ? sizeof(cxd) : sizeof(double);
-        const size_t per_item = NN * elem * (init ? 2 : 1);
-        size_t budget = budget_bytes();
-        int chunk_chains = (int)std::max<size_t>(1, budget / (per_item * npf));
+        const size_t per_item = NN * elem;
+        int chunk_chains = (int)std::max<size_t>(1, budget_bytes() / (per_item * npf));
         chunk_chains = std::min<int>(chunk_chains, (int)chains.size());
         const int max_items = chunk_chains * npf;
         const size_t tmp = ggf_factor_tmp_bytes(N, max_items);
-        const size_t small = (size_t)max_items * (2 * sizeof(int) + 3 * sizeof(cxd)) + 256;
+        const size_t small = (size_t)max_items * (2 * sizeof(int) + sizeof(cxd)) + 256;
         GGF_TRY(ggf_workspace(ctx, per_item * max_items + tmp + small + 1024));
         unsigned char* base = (unsigned char*)ctx->work;
         void* A = base;
-        void* A2 = init ? base + NN * elem * max_items : nullptr;
         unsigned char* q = base + per_item * max_items;
         void* ftmp = q;
         q += (tmp + 255) / 256 * 256;
         int* d_chain = (int*)q; q += (size_t)max_items * sizeof(int);
         int* d_pair = (int*)q; q += (size_t)max_items * sizeof(int);
         q = (unsigned char*)(((uintptr_t)q + 15) / 16 * 16);
-        cxd* d_logdet = (cxd*)q; q += (size_t)max_items * sizeof(cxd);
-        cxd* d_logpf = (cxd*)q; q += (size_t)max_items * sizeof(cxd);
-        cxd* d_phase = (cxd*)q;
+        cxd* d_logdet = (cxd*)q;
         std::vector<int> hc, hp;
         for (size_t c0 = 0; c0 < chains.size(); c0 += chunk_chains) {
             int nc = (int)std::min<size_t>(chunk_chains, chains.size() - c0);
@@ -202,10 +285,6 @@ ggf_status factor_chains(ggf_ctx* ctx, const std::vector<int>& chains, bool init
             GGF_CK(cudaMemcpyAsync(d_chain, hc.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
             GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
             GGF_TRY(ggf_assemble(ctx, !cplx, items, d_chain, d_pair, ch.links, A, st));
-            if (init) {
-                GGF_CK(cudaMemcpyAsync(A2, A, NN * elem * items, cudaMemcpyDeviceToDevice, st));
-                GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, items, A2, d_logpf, d_phase, ftmp, st));
-            }
             GGF_TRY(ggf_invert_batched(ctx, cplx, N, items, A, d_logdet, ftmp, st));
             dim3 grid((unsigned)((NN + 255) / 256), items);
             if (!cplx) {
@@ -215,15 +294,87 @@ ggf_status factor_chains(ggf_ctx* ctx, const std::vector<int>& chains, bool init
                 if (fp64) scatter_kernel<cxd><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxd*)ch.Wc);
                 else scatter_kernel<cxf><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxf*)ch.Wc);
             }
+            count_singular_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, d_logdet, ch.counters);
             ctx->launches += 2;
-            ell_update_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, cplx ? ctx->K : 0, ctx->P, cplx, init,
-                                                                   d_chain, d_pair, d_logdet, d_logpf, d_phase,
-                                                                   ch.ell, ch.drift, ch.since_refresh, ch.counters);
             GGF_CK(cudaGetLastError());
             GGF_CK(cudaStreamSynchronize(st));  // hc/hp are reused by the next chunk
         }
     }
     return GGF_OK;
+}
+
+// Newton refinement of the listed FP32 chains' inverses (k_refine.cu); the
+// chains whose residual is too large for it are returned in `dense`.
+ggf_status newton_inverse(ggf_ctx* ctx, const std::vector<int>& chains, std::vector<int>& dense, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    const int N = ctx->g.N;
+    const size_t NN = (size_t)N * N;
+    const size_t need = ggf_refine_bytes(N, ctx->Kc > 0);
+    GGF_TRY(ggf_workspace(ctx, need));
+    for (int c : chains) {
+        bool ok = true;
+        for (int fam = 0; fam < 2 && ok; ++fam) {
+            const bool cplx = fam == 1;
+            const int npf = cplx ? ctx->Kc : ctx->K;
+            for (int p = 0; p < npf && ok; ++p) {
+                float* W = cplx ? (float*)ch.Wc + ((size_t)c * ctx->Kc + p) * NN * 2
+                                : (float*)ch.Wr + ((size_t)c * ctx->K + p) * NN;
+                double rmax = 0.0;
+                GGF_TRY(ggf_refine_inverse(ctx, cplx, ch.links, c, p, W, ctx->work, kRefineTol, &rmax, st));
+                if (!(rmax <= kRefineTol)) ok = false;
+                ctx->refine_rmax = std::max(ctx->refine_rmax, rmax);
+            }
+        }
+        if (!ok) dense.push_back(c);
+    }
+    GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
+// Log-weights of the listed chains from the site-by-site FP64 Pfaffian
+// (dense fallback for items without a usable pivot).
+ggf_status chain_ell(ggf_ctx* ctx, const std::vector<int>& chains, bool init, cudaStream_t st) {
+    Chains& ch = ctx->ch;
+    for (int fam = 0; fam < 2; ++fam) {
+        const bool cplx = fam == 1;
+        const int npf = cplx ? ctx->Kc : ctx->K;
+        if (npf == 0) continue;
+        const int items = (int)chains.size() * npf;
+        std::vector<int> hc(items), hp(items);
+        for (size_t i = 0; i < chains.size(); ++i)
+            for (int p = 0; p < npf; ++p) { hc[i * npf + p] = chains[i]; hp[i * npf + p] = p; }
+        DBuf tab;
+        GGF_TRY(dalloc(ctx, tab, (size_t)items * (2 * sizeof(cxd) + 3 * sizeof(int)) + 256));
+        cxd* d_logpf = (cxd*)tab.p;
+        cxd* d_phase = d_logpf + items;
+        int* d_chain = (int*)(d_phase + items);
+        int* d_pair = d_chain + items;
+        int* d_flag = d_pair + items;
+        GGF_TRY(pf_items(ctx, cplx, hc, hp, ch.links, d_chain, d_pair, d_flag, d_logpf, d_phase, st));
+        GGF_CK(cudaMemcpyAsync(d_chain, hc.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+        GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
+        ell_set_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, cplx ? ctx->K : 0, ctx->P, cplx, init, d_chain,
+                                                            d_pair, d_logpf, d_phase, ch.ell, ch.drift,
+                                                            ch.since_refresh, ch.counters);
+        GGF_CK(cudaGetLastError());
+        GGF_CK(cudaStreamSynchronize(st));
+    }
+    return GGF_OK;
+}
+
+// Factor the listed chains: log-weights from the site-by-site FP64 Pfaffian
+// (init: set; refresh: drift recorded), inverses by FP64 Gauss-Jordan at the
+// start and for FP64 chains, by a Newton step on the tensor cores for FP32
+// chains (Gauss-Jordan where the residual is too large for it).
+ggf_status factor_chains(ggf_ctx* ctx, const std::vector<int>& chains, bool init, cudaStream_t st) {
+    if (chains.empty()) return GGF_OK;
+    GGF_TRY(chain_ell(ctx, chains, init, st));
+    const bool newton = !init && ctx->ch.opts.precision == GGF_FP32 && ctx->use_tc && ctx->g.N % 8 == 0;
+    if (!newton) return dense_inverse(ctx, chains, st);
+    std::vector<int> dense;
+    GGF_TRY(newton_inverse(ctx, chains, dense, st));
+    ctx->dense_refreshes += dense.size();
+    return dense_inverse(ctx, dense, st);
 }
 
 ggf_status require(ggf_ctx* ctx, bool gauss, bool chains) {
@@ -265,6 +416,7 @@ void ggf_destroy(ggf_ctx* ctx) {
     cudaSetDevice(ctx->device);
     ggf_free_chains(ctx);
     ggf_free_consts(ctx);
+    ggf_front_free(ctx);
     if (ctx->work) cudaFree(ctx->work);
     if (ctx->d_err) cudaFree(ctx->d_err);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -356,42 +508,7 @@ ggf_status ggf_logweight(ggf_ctx* ctx, int n_cfg, const void* links, double* log
         const bool cplx = fam == 1;
         const int npf = cplx ? ctx->Kc : ctx->K;
         if (npf == 0) continue;
-        const size_t elem = cplx ? sizeof(cxd) : sizeof(double);
-        size_t budget = budget_bytes();
-        int max_items = (int)std::max<size_t>(1, budget / (NN * elem));
-        max_items = std::min(max_items, n_cfg * npf);
-        max_items = std::min(max_items, 65535);
-        max_items = std::max(npf, max_items / npf * npf);  // whole configurations per chunk
-        const size_t tmp = ggf_factor_tmp_bytes(N, max_items);
-        const size_t small = (size_t)max_items * (2 * sizeof(int) + 2 * sizeof(cxd)) + 256;
-        GGF_TRY(ggf_workspace(ctx, NN * elem * max_items + tmp + small + 1024));
-        unsigned char* q = (unsigned char*)ctx->work;
-        void* A = q;
-        q += NN * elem * max_items;
-        void* ftmp = q;
-        q += (tmp + 255) / 256 * 256;
-        int* d_cfg = (int*)q; q += (size_t)max_items * sizeof(int);
-        int* d_pair = (int*)q; q += (size_t)max_items * sizeof(int);
-        q = (unsigned char*)(((uintptr_t)q + 15) / 16 * 16);
-        cxd* d_logpf = (cxd*)q; q += (size_t)max_items * sizeof(cxd);
-        cxd* d_phase = (cxd*)q;
-        const int total = n_cfg * npf;
-        std::vector<int> hc, hp;
-        for (int i0 = 0; i0 < total; i0 += max_items) {
-            int items = std::min(max_items, total - i0);
-            hc.resize(items); hp.resize(items);
-            for (int i = 0; i < items; ++i) { hc[i] = (i0 + i) / npf; hp[i] = (i0 + i) % npf; }
-            GGF_CK(cudaMemcpyAsync(d_cfg, hc.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
-            GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
-            GGF_TRY(ggf_assemble(ctx, !cplx, items, d_cfg, d_pair, d_links, A, st));
-            GGF_TRY(ggf_pfaffian_batched(ctx, cplx, N, items, A, d_logpf, d_phase, ftmp, st));
-            // items are consecutive (cfg, pair) in this family: offset by i0
-            write_ell_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, npf, cplx ? ctx->K : 0, P, cplx, d_logpf,
-                                                                   d_phase, (cxd*)dell.p + (size_t)(i0 / npf) * P);
-            GGF_CK(cudaGetLastError());
-            // hc/hp are reused by the next chunk: wait for their copies
-            GGF_CK(cudaStreamSynchronize(st));
-        }
+        GGF_TRY(front_family(ctx, cplx, n_cfg, npf, d_links, (cxd*)dell.p, st));
     }
     double* d_logN = logN;
     if (mem == GGF_MEM_HOST) {
@@ -476,6 +593,8 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     ggf_free_chains(ctx);
+    ctx->refine_rmax = 0.0;
+    ctx->dense_refreshes = ctx->dense_pfaffians = 0;
     Chains& ch = ctx->ch;
     ch.opts = *opts;
     ch.n = n_chains;
@@ -586,32 +705,62 @@ ggf_status sweep_body(ggf_ctx* ctx, cudaStream_t st) {
 void drop_graph(Chains& ch) {
     if (ch.gexec) cudaGraphExecDestroy(ch.gexec);
     if (ch.graph) cudaGraphDestroy(ch.graph);
+    if (ch.gexec_t) cudaGraphExecDestroy(ch.gexec_t);
+    if (ch.graph_t) cudaGraphDestroy(ch.graph_t);
     ch.gexec = nullptr;
     ch.graph = nullptr;
+    ch.gexec_t = nullptr;
+    ch.graph_t = nullptr;
+    ch.gev_cat.clear();
+    ch.gev_n = 0;
 }
 
-ggf_status ensure_graph(ggf_ctx* ctx) {
+// Capture one sweep into a CUDA graph: the plain graph, or (timed = true) the
+// same sweep with timing-event record nodes around its launch groups.
+ggf_status ensure_graph(ggf_ctx* ctx, bool timed = false) {
     Chains& ch = ctx->ch;
-    if (ch.gexec) return GGF_OK;
-    drop_graph(ch);
+    if (timed ? ch.gexec_t : ch.gexec) return GGF_OK;
     const bool prof = ctx->prof;
-    ctx->prof = false;   // captured graphs hold no timing events
+    if (timed) {
+        // events are created before the capture: a sweep marks at most a few
+        // events per link batch, link step or flush
+        const size_t want = (size_t)8 * ctx->g.n_links + 64;
+        while (ctx->ev.size() < want) {
+            cudaEvent_t ev;
+            GGF_CK(cudaEventCreate(&ev));
+            ctx->ev.push_back(ev);
+        }
+    }
+    ctx->prof = timed;
     ctx->ev_used = 0;
     ctx->ev_cat.clear();
     const unsigned long long l0 = ctx->launches;
+    ctx->capturing = true;
     cudaError_t eb = cudaStreamBeginCapture(ch.cs, cudaStreamCaptureModeThreadLocal);
-    if (eb != cudaSuccess) { ctx->prof = prof; return ggf_cuda(ctx, eb, "cudaStreamBeginCapture"); }
+    if (eb != cudaSuccess) {
+        ctx->prof = prof;
+        ctx->capturing = false;
+        return ggf_cuda(ctx, eb, "cudaStreamBeginCapture");
+    }
     ggf_status s = sweep_body(ctx, ch.cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(ch.cs, &g);
+    ctx->capturing = false;
     ctx->prof = prof;
     if (s != GGF_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
     }
     if (e != cudaSuccess) return ggf_cuda(ctx, e, "cudaStreamEndCapture");
-    ch.graph = g;
-    GGF_CK(cudaGraphInstantiate(&ch.gexec, g, 0));
+    if (timed) {
+        ch.graph_t = g;
+        GGF_CK(cudaGraphInstantiate(&ch.gexec_t, g, 0));
+        ch.gev_cat = ctx->ev_cat;
+        ch.gev_n = ctx->ev_used;
+    } else {
+        ch.graph = g;
+        GGF_CK(cudaGraphInstantiate(&ch.gexec, g, 0));
+    }
     ch.graph_launches = ctx->launches - l0;
     ctx->launches = l0;
     ctx->ev_cat.clear();
@@ -630,7 +779,11 @@ ggf_status accumulate_events(ggf_ctx* ctx, const std::vector<int>& cat, const st
 }
 
 // After a sweep's kernels: observables out, refresh of the marked chains.
-ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem, bool graph_launched) {
+// With timing on, the events of the sweep (eager launch, or the timed graph's
+// record nodes) are accumulated before the refresh records its own.
+// launched: 0 eager sweep, 1 plain graph (no timing events), 2 timed graph.
+ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem, int launched) {
+    const bool graph_launched = launched != 0;
     Chains& ch = ctx->ch;
     cudaStream_t cs = ch.cs;
     if (obs_dst)
@@ -643,9 +796,16 @@ ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem, bool graph_launc
     // a bounded device wait that ran out ends the call after this sweep
     if (derr) return ggf_fail(ctx, GGF_ETIMEOUT, "a bounded device wait ran out (tensor-core flush)");
     if (ctx->prof) {
-        if (!graph_launched) GGF_TRY(accumulate_events(ctx, ctx->ev_cat, ctx->ev));
+        if (launched == 2) {
+            GGF_TRY(accumulate_events(ctx, ch.gev_cat, ctx->ev));
+            ctx->ev_used = ch.gev_n;     // the graph's events stay reserved for its next replay
+        } else if (launched == 1) {
+            ctx->ev_used = ch.gev_n;     // a plain replay records nothing
+        } else {
+            GGF_TRY(accumulate_events(ctx, ctx->ev_cat, ctx->ev));
+            ctx->ev_used = 0;
+        }
         ctx->ev_cat.clear();
-        ctx->ev_used = 0;
     }
     if (cnt > 0) {
         std::vector<int> list(cnt);
@@ -659,7 +819,7 @@ ggf_status finish_sweep(ggf_ctx* ctx, double* obs_dst, int mem, bool graph_launc
         if (ctx->prof) {
             GGF_TRY(accumulate_events(ctx, ctx->ev_cat, ctx->ev));
             ctx->ev_cat.clear();
-            ctx->ev_used = 0;
+            ctx->ev_used = graph_launched ? ch.gev_n : 0;
         }
         unsigned long long h[4];
         GGF_CK(cudaMemcpy(h, ch.counters, sizeof(h), cudaMemcpyDeviceToHost));
@@ -690,21 +850,22 @@ ggf_status ggf_sample(ggf_ctx* ctx, int n_sweeps, double* obs, int mem, void* st
     // the library stream waits for the caller's stream, and the caller's stream for it at the end
     GGF_CK(cudaEventRecord(ch.join, st));
     GGF_CK(cudaStreamWaitEvent(ch.cs, ch.join, 0));
-    // with per-kernel timing on, sweeps launch eagerly (same kernel sequence as
-    // the graph) so that every launch is bracketed by events
-    const bool use_graph = ch.opts.graph && !ctx->prof;
+    // graph mode replays the captured sweep; with per-kernel timing on, the
+    // replayed graph is the same sweep with timing-event record nodes
+    const bool use_graph = ch.opts.graph != 0;
     for (int s = 0; s < n_sweeps; ++s) {
         NvtxRange range("ggf_sample sweep");
         if (use_graph) {
-            GGF_TRY(ensure_graph(ctx));
-            GGF_CK(cudaGraphLaunch(ch.gexec, ch.cs));
+            GGF_TRY(ensure_graph(ctx, ctx->prof));
+            GGF_CK(cudaGraphLaunch(ctx->prof ? ch.gexec_t : ch.gexec, ch.cs));
             ctx->launches += ch.graph_launches;
         } else {
             ctx->ev_used = 0;
             ctx->ev_cat.clear();
             GGF_TRY(sweep_body(ctx, ch.cs));
         }
-        GGF_TRY(finish_sweep(ctx, obs ? obs + (size_t)s * ch.n * GGF_N_OBS : nullptr, mem, use_graph));
+        GGF_TRY(finish_sweep(ctx, obs ? obs + (size_t)s * ch.n * GGF_N_OBS : nullptr, mem,
+                             use_graph ? (ctx->prof ? 2 : 1) : 0));
     }
     GGF_CK(cudaEventRecord(ch.join, ch.cs));
     GGF_CK(cudaStreamWaitEvent(st, ch.join, 0));
@@ -755,7 +916,7 @@ ggf_status ggf_sample_group(ggf_ctx* const* ctxs, int n_ctx, int n_sweeps, doubl
                 c->launches += c->ch.graph_launches;
                 if (k > 0) cudaStreamWaitEvent(c->ch.cs, ctx->ch.join, 0);
                 double* dst = (obs && obs[k]) ? obs[k] + (size_t)s * c->ch.n * GGF_N_OBS : nullptr;
-                rc = finish_sweep(c, dst, mem, true);   // no per-kernel timing in group mode
+                rc = finish_sweep(c, dst, mem, 1);   // no per-kernel timing in group mode
             }
         }
         if (rc == GGF_OK) {
@@ -1004,6 +1165,26 @@ ggf_status ggf_debug_poison_inverse(ggf_ctx* ctx, int chain, int pair, int i, in
     return GGF_OK;
 }
 
+ggf_status ggf_chains_refine(ggf_ctx* ctx, int chain, int pair, int apply, double* rmax) {
+    GGF_TRY(require(ctx, true, true));
+    Chains& ch = ctx->ch;
+    if (chain < 0 || chain >= ch.n || pair < 0 || pair >= ctx->P || !rmax)
+        return ggf_fail(ctx, GGF_EINVAL, "bad chains_refine arguments");
+    if (ch.opts.precision != GGF_FP32) return ggf_fail(ctx, GGF_EINVAL, "chains_refine: FP32 chains only");
+    cudaSetDevice(ctx->device);
+    const int N = ctx->g.N;
+    const size_t NN = (size_t)N * N;
+    const bool cplx = pair >= ctx->K;
+    const int p = cplx ? pair - ctx->K : pair;
+    float* W = cplx ? (float*)ch.Wc + ((size_t)chain * ctx->Kc + p) * NN * 2
+                    : (float*)ch.Wr + ((size_t)chain * ctx->K + p) * NN;
+    GGF_CK(cudaDeviceSynchronize());
+    GGF_TRY(ggf_workspace(ctx, ggf_refine_bytes(N, cplx)));
+    GGF_TRY(ggf_refine_inverse(ctx, cplx, ch.links, chain, p, W, ctx->work, apply ? kRefineTol : -1.0, rmax, 0));
+    GGF_CK(cudaDeviceSynchronize());
+    return GGF_OK;
+}
+
 ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, int mem, void* stream) {
     GGF_TRY(require(ctx, true, true));
     Chains& ch = ctx->ch;
@@ -1050,6 +1231,9 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     out->block_proposals = h[4];
     out->block_accepts = h[5];
     out->n_pairs = ctx->P;
+    out->max_resid = ctx->refine_rmax;
+    out->dense_refreshes = ctx->dense_refreshes;
+    out->dense_pfaffians = ctx->dense_pfaffians;
     if (h[3]) return ggf_fail(ctx, GGF_ESINGULAR, "a refresh met a singular M(G)");
     return GGF_OK;
 }
@@ -1103,7 +1287,7 @@ ggf_status ggf_chains_save_state(ggf_ctx* ctx, void* dst, int mem, void* stream)
     GGF_CK(cudaStreamSynchronize(st));
     GGF_CK(cudaStreamSynchronize(ch.cs));
     StateHeader h{};
-    std::memcpy(h.magic, "GGFSTAT1", 8);
+    std::memcpy(h.magic, "GGFSTAT2", 8);
     const int geo[8] = {g.L, g.group, g.n_v, ctx->K, ch.n, ctx->P, ch.opts.precision, ch.kmax};
     std::memcpy(h.geo, geo, sizeof(geo));
     h.opts = ch.opts;
@@ -1132,7 +1316,7 @@ ggf_status ggf_chains_load_state(ggf_ctx* ctx, const void* src, int mem, void* s
     StateHeader h;
     GGF_CK(cudaMemcpy(&h, src, sizeof(h), mem == GGF_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost));
     const int geo[8] = {g.L, g.group, g.n_v, ctx->K, ch.n, ctx->P, ch.opts.precision, ch.kmax};
-    if (std::memcmp(h.magic, "GGFSTAT1", 8) != 0 || std::memcmp(h.geo, geo, sizeof(geo)) != 0)
+    if (std::memcmp(h.magic, "GGFSTAT2", 8) != 0 || std::memcmp(h.geo, geo, sizeof(geo)) != 0)
         return ggf_fail(ctx, GGF_EINVAL, "state does not match the context's problem, chains, precision or delay");
     GGF_CK(cudaStreamSynchronize(st));
     GGF_CK(cudaStreamSynchronize(ch.cs));
@@ -1174,7 +1358,7 @@ ggf_status ggf_checkpoint(ggf_ctx* ctx, const char* path) {
     GGF_CK(cudaMemcpy(cnt, ch.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
     FILE* f = fopen(path, "wb");
     if (!f) return ggf_fail(ctx, GGF_EIO, std::string("cannot open ") + path);
-    const char magic[8] = {'G', 'G', 'F', 'C', 'K', 'P', 'T', '2'};
+    const char magic[8] = {'G', 'G', 'F', 'C', 'K', 'P', 'T', '3'};
     int hdr[8] = {g.L, g.group, g.n_v, ctx->K, ch.n, ctx->P, 0, 0};
     bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               fwrite(&ch.opts, sizeof(ch.opts), 1, f) == 1 && fwrite(&ch.sweep, sizeof(ch.sweep), 1, f) == 1 &&
@@ -1196,7 +1380,7 @@ ggf_status ggf_resume(ggf_ctx* ctx, const char* path, void* stream) {
     ggf_chain_opts o;
     uint64_t sweep;
     unsigned long long cnt[4];
-    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GGFCKPT2", 8) == 0 &&
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "GGFCKPT3", 8) == 0 &&
               fread(hdr, sizeof(hdr), 1, f) == 1 && fread(&o, sizeof(o), 1, f) == 1 &&
               fread(&sweep, sizeof(sweep), 1, f) == 1 && fread(cnt, sizeof(cnt), 1, f) == 1;
     const Geometry& g = ctx->g;

@@ -66,6 +66,13 @@ struct Chains {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     unsigned long long graph_launches = 0;   // kernels per replay
+    // the same sweep captured with timing-event record nodes around its launch
+    // groups (per-kernel timing on, ggf_profile): events ev[0 .. gev_n) of the
+    // context's pool and their (category, start, end) triples
+    cudaGraph_t graph_t = nullptr;
+    cudaGraphExec_t gexec_t = nullptr;
+    std::vector<int> gev_cat;
+    int gev_n = 0;
 };
 
 struct ggf_net;
@@ -90,22 +97,37 @@ struct ggf_ctx {
     Chains ch;
     void* work = nullptr;
     size_t work_bytes = 0;
+    // site-by-site Pfaffian (k_front.cu): schedule [slot N | eoff V+1 | elim N]
+    // for the lattice it was built for, and a global front workspace for
+    // fronts too large for shared memory
+    int* d_front = nullptr;
+    int front_F = 0, front_L = -1, front_B = -1;
+    void* front_ws = nullptr;
+    size_t front_ws_bytes = 0;
+    // refresh bookkeeping since ggf_chains_init: largest Newton residual
+    // |I - M W| seen, chains refreshed by dense Gauss-Jordan instead, and
+    // Pfaffian items that fell back to the dense elimination
+    double refine_rmax = 0.0;
+    unsigned long long dense_refreshes = 0, dense_pfaffians = 0;
     // event timing (ggf_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev;            // event pool
     std::vector<int> ev_cat;                // category of each recorded (start, end) pair
     int ev_used = 0;                        // events recorded this sweep
+    bool capturing = false;                 // a sweep is being captured into a graph
     double kt_ms[GGF_KT_N] = {0, 0, 0, 0, 0, 0};
     unsigned long long kt_n[GGF_KT_N] = {0, 0, 0, 0, 0, 0};
     // record one event (returns its index, or -1 when profiling is off)
     int prof_mark(cudaStream_t st) {
         if (!prof) return -1;
         if (ev_used == (int)ev.size()) {
+            if (capturing) return -1;    // the pool is grown before a capture
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return -1;
             ev.push_back(e);
         }
-        cudaEventRecord(ev[ev_used], st);
+        // inside a capture the record becomes an event-record node of the graph
+        cudaEventRecordWithFlags(ev[ev_used], st, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
         return ev_used++;
     }
     void prof_pair(int cat, int a, int b) {
@@ -163,6 +185,12 @@ ggf_status ggf_pfaffian_batched(ggf_ctx* ctx, bool cplx, int n, int batch, void*
 // Batched Gauss-Jordan inverse in place: logdet (log|det|, arg) per item.
 ggf_status ggf_invert_batched(ggf_ctx* ctx, bool cplx, int n, int batch, void* A, cxd* d_logdet,
                               void* d_tmp, cudaStream_t st);
+// log Pf(M_nm(G)) by site-by-site elimination along the lattice (FP64):
+// (log|Pf|, 0) and the unit phase per item; flag[item] = 1 where no pivot was
+// usable inside a closed set (refactor those items densely).
+ggf_status ggf_front_pfaffian(ggf_ctx* ctx, bool cplx, int n_items, const int* d_item_cfg, const int* d_item_pair,
+                              const void* d_links, cxd* d_logpf, cxd* d_phase, int* d_flag, cudaStream_t st);
+void ggf_front_free(ggf_ctx* ctx);
 // Combine per-config pair log-Pfaffians into log N (device, n_cfg items).
 ggf_status ggf_combine(ggf_ctx* ctx, int n_cfg, const cxd* d_ell, double* d_logN, cudaStream_t st);
 ggf_status ggf_plaquette(ggf_ctx* ctx, int n_cfg, const void* d_links, double* d_out, cudaStream_t st);

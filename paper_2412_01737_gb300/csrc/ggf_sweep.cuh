@@ -131,9 +131,10 @@ struct Proposal {
 // word 0 -> u_accept, word 1 -> u_propose.  Z2 flips the link; U(1) moves
 // theta by width (u - 1/2) and wraps into [0, 2 pi).
 __device__ __forceinline__ Proposal draw_proposal(const Geometry& g, const void* links, int c, int l,
-                                                  unsigned long long sweep, uint64_t seed, double width) {
+                                                  unsigned long long sweep, uint64_t seed, double width,
+                                                  uint64_t coff = 0) {
     uint64_t ctr[4] = {(uint64_t)sweep, (uint64_t)l, 0, 0}, out[4];
-    philox4x64_10(ctr, seed, (uint64_t)c, out);
+    philox4x64_10(ctr, seed, coff + (uint64_t)c, out);
     Proposal q;
     q.u_acc = u53(out[0]);
     const double u_prop = u53(out[1]);
@@ -180,9 +181,9 @@ __device__ __forceinline__ void pair_delta(const DevConst& dc, int p, int l, con
 // quaternion and the old and new doublet rotations; returns u_acc.
 GGF_HD double draw_su2(const Geometry& g, const void* links, int c, int l,
                                            unsigned long long sweep, uint64_t seed, double width, double* qn,
-                                           double* Rold, double* Rnew) {
+                                           double* Rold, double* Rnew, uint64_t coff = 0) {
     uint64_t ctr[4] = {(uint64_t)sweep, (uint64_t)l, 0, 0}, out[4];
-    philox4x64_10(ctr, seed, (uint64_t)c, out);
+    philox4x64_10(ctr, seed, coff + (uint64_t)c, out);
     const double d = width * (u53(out[1]) - 0.5);
     const double z = 2.0 * u53(out[2]) - 1.0;
     const double rho = sqrt(fmax(0.0, 1.0 - z * z));

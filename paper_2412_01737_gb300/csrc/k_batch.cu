@@ -93,6 +93,7 @@ struct BatchArgs {
     const unsigned long long* d_sweep;
     int l0, kb, KRM;
     uint64_t seed;
+    uint64_t coff;         // Philox key word 1 = coff + chain
     double width;
     void* links;
     cxd* ell;
@@ -242,11 +243,12 @@ __global__ void __launch_bounds__(NWARP * 32, 2) batch_steps(BatchArgs a) {
         if constexpr (SU2) {
             if (threadIdx.x == 0) {
                 Proposal qq{};
-                qq.u_acc = draw_su2(g, a.links, c, l, sweep, a.seed, a.width, s_su2, s_su2 + 4, s_su2 + 20);
+                qq.u_acc = draw_su2(g, a.links, c, l, sweep, a.seed, a.width, s_su2, s_su2 + 4, s_su2 + 20,
+                                   a.coff);
                 s_q = qq;
             }
         } else {
-            if (threadIdx.x == 0) s_q = draw_proposal(g, a.links, c, l, sweep, a.seed, a.width);
+            if (threadIdx.x == 0) s_q = draw_proposal(g, a.links, c, l, sweep, a.seed, a.width, a.coff);
         }
         __syncthreads();
         const Proposal q = s_q;
@@ -506,6 +508,7 @@ ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st) {
         a.kb = kb;
         a.KRM = KRM;
         a.seed = ch.opts.seed;
+        a.coff = ch.opts.chain_offset;
         a.width = ch.opts.width;
         a.links = ch.links;
         a.ell = ch.ell;

@@ -24,11 +24,11 @@ ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st);
 
 namespace {
 
-__global__ void block_origin(int n, int L, uint64_t seed, uint64_t move, int* blocks) {
+__global__ void block_origin(int n, int L, uint64_t seed, uint64_t koff, uint64_t move, int* blocks) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     uint64_t c4[4] = {move, 0, 21, 0}, o4[4];
-    philox4x64_10(c4, seed, (uint64_t)c, o4);
+    philox4x64_10(c4, seed, koff + (uint64_t)c, o4);
     blocks[2 * c] = min(L - 1, (int)(u53(o4[0]) * L));
     blocks[2 * c + 1] = min(L - 1, (int)(u53(o4[1]) * L));
 }
@@ -66,7 +66,7 @@ __device__ double combine_log(const DevConst& dc, const cxd* ell, double amax, b
 __global__ void block_decide(DevConst dc, int n, const int* link_k, const double* lq, const double* old_links,
                              const cxd* ell_save, cxd* ell, double* links, int* pend, const int* dead,
                              int* since_refresh, int* sweep_acc, unsigned long long* counters, uint64_t seed,
-                             uint64_t move) {
+                             uint64_t koff, uint64_t move) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     const int P = dc.P, nl = dc.g.n_links;
@@ -77,7 +77,7 @@ __global__ void block_decide(DevConst dc, int n, const int* link_k, const double
     bool ok0, ok1;
     double l0 = combine_log(dc, e0, amax, &ok0), l1 = combine_log(dc, e1, amax, &ok1);
     uint64_t c4[4] = {move, 0, 23, 0}, o4[4];
-    philox4x64_10(c4, seed, (uint64_t)c, o4);
+    philox4x64_10(c4, seed, koff + (uint64_t)c, o4);
     double u = u53(o4[0]);
     double logR = l1 - l0 - lq[c];
     bool acc = !dead[c] && ok0 && ok1 && (logR >= 0.0 || u < exp(logR));
@@ -128,18 +128,20 @@ extern "C" ggf_status ggf_sample_blocks(ggf_ctx* ctx, ggf_net* net, int n_moves,
     for (int mv = 0; mv < n_moves && rc == GGF_OK; ++mv) {
         const uint64_t move = ch.block_moves;
         if ((rc = ggf_flush(ctx, st)) != GGF_OK) break;
-        block_origin<<<(n + 127) / 128, 128, 0, st>>>(n, g.L, ch.opts.seed, move, blocks);
+        block_origin<<<(n + 127) / 128, 128, 0, st>>>(n, g.L, ch.opts.seed, ch.opts.chain_offset, move, blocks);
         block_prepare<<<n, 32, 0, st>>>(n, g.L, P, blocks, (const double*)ch.links, ch.ell, link_k, old_links,
                                         ell_save, dead);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail_cuda(e, "block_prepare"); break; }
-        rc = ggf_net_head(net, n, 2, (const double*)ch.links, nullptr, blocks, lq, prop, ch.opts.seed, move, st);
+        rc = ggf_net_head(net, n, 2, (const double*)ch.links, nullptr, blocks, lq, prop, ch.opts.seed, move, st,
+                          ch.opts.chain_offset);
         if (rc != GGF_OK) { ctx->err = ggf_net_last_error(net); break; }
         for (int k = 0; k < 32 && rc == GGF_OK; ++k)
             rc = ggf_link_step_ex(ctx, -1, st, link_k + (size_t)k * n, prop, k, dead);
         if (rc != GGF_OK) break;
         block_decide<<<(n + 127) / 128, 128, 0, st>>>(ctx->dc(), n, link_k, lq, old_links, ell_save, ch.ell,
                                                       (double*)ch.links, ch.pend, dead, ch.since_refresh,
-                                                      ch.sweep_acc, ch.counters, ch.opts.seed, move);
+                                                      ch.sweep_acc, ch.counters, ch.opts.seed, ch.opts.chain_offset,
+                                                      move);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail_cuda(e, "block_decide"); break; }
         if ((rc = ggf_flush(ctx, st)) != GGF_OK) break;
         ctx->launches += 4;

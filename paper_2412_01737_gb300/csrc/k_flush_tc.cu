@@ -609,6 +609,15 @@ ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st) {
     return GGF_OK;
 }
 
+// W -= U V for one N x N matrix with rank-K panels (K = pend[0] * R, panel
+// column count KRM), FP32-accurate (TF32 three-product split).  Used by the
+// Newton refinement of the inverses (k_refine.cu).
+ggf_status ggf_flush_tc_one(ggf_ctx* ctx, bool cplx, int N, float* W, const float* Pan, const int* pend, int R,
+                            int KRM, int nprod, cudaStream_t st) {
+    (void)nprod;
+    return launch_flush_tc(ctx, cplx, N, 1, 1, W, Pan, pend, R, KRM, false, ctx->d_err, st);
+}
+
 extern "C" ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank, double* max_rel_err) {
     if (!ctx || !max_rel_err || N < 1 || N > 8192 || rank < 4 || rank > 512 || rank % 4)
         return ggf_fail(ctx, GGF_EINVAL, "selftest_flush: N in [1, 8192], rank in {4, 8, ..., 512}");

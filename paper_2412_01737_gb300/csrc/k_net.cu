@@ -197,7 +197,7 @@ __global__ void conv_bwd_weight(int n, int L, int ci, int co, const bf16* X, con
 // into logq[b].
 __global__ void head_kernel(int n, int L, int mode, const float* out, const double* theta, const int* cfg,
                             const int* blocks, double* logq, float* dOut, double* loss, double* prop,
-                            uint64_t seed, uint64_t counter) {
+                            uint64_t seed, uint64_t counter, uint64_t koff) {
     const int b = blockIdx.x;
     if (b >= n) return;
     const int V = L * L, nl = 2 * V;
@@ -233,7 +233,7 @@ __global__ void head_kernel(int n, int L, int mode, const float* out, const doub
             db_[(3 * d + 2) * V + s] = (float)(-(drho * RHO_MAX * sig * (1.0 - sig)) / n);
         } else {
             uint64_t c4[4] = {counter, (uint64_t)k, 7, 0}, o4[4];
-            philox4x64_10(c4, seed, (uint64_t)b, o4);
+            philox4x64_10(c4, seed, koff + (uint64_t)b, o4);
             double u = u53(o4[0]);
             double t = mu - log(rho) * tan(M_PI * (u - 0.5));
             t = fmod(t, GGF_TWO_PI);
@@ -401,7 +401,8 @@ static ggf_status net_backward(ggf_net* net, int n, cudaStream_t st) {
 
 // log q / loss+grad / proposal for n samples (theta on the device)
 ggf_status ggf_net_head(ggf_net* net, int n, int mode, const double* theta, const int* cfg, const int* blocks,
-                        double* logq, double* prop, uint64_t seed, uint64_t counter, cudaStream_t st) {
+                        double* logq, double* prop, uint64_t seed, uint64_t counter, cudaStream_t st,
+                        uint64_t koff) {
     GGF_TRY(net_ws(net, n));
     const int L = net->L, V = L * L;
     features_kernel<<<n, px_threads(L), 0, st>>>(n, L, theta, cfg, blocks, net->X[0]);
@@ -412,7 +413,7 @@ ggf_status ggf_net_head(ggf_net* net, int n, int mode, const double* theta, cons
         NET_CK(cudaMemsetAsync(net->scal, 0, sizeof(double), st));
     }
     head_kernel<<<n, 32, 0, st>>>(n, L, mode, net->out, theta, cfg, blocks, logq, net->dA, net->scal, prop, seed,
-                                  counter);
+                                  counter, koff);
     NET_CK(cudaGetLastError());
     if (mode == 1) GGF_TRY(net_backward(net, n, st));
     return GGF_OK;

@@ -29,6 +29,7 @@ struct SweepArgs {
     const unsigned long long* d_sweep;   // sweep index (device, so captured sweeps replay)
     int link;
     uint64_t seed;
+    uint64_t coff;         // Philox key word 1 = coff + chain
     double width;
     void* links;
     const void* Wr;
@@ -79,13 +80,14 @@ __global__ void __launch_bounds__(NWARP * 32) ratio_kernel(SweepArgs a) {
     if constexpr (SU2) {
         if (threadIdx.x == 0) {
             Proposal q{};
-            q.u_acc = draw_su2(g, a.links, c, l, *a.d_sweep, a.seed, a.width, s_su2, s_su2 + 4, s_su2 + 20);
+            q.u_acc = draw_su2(g, a.links, c, l, *a.d_sweep, a.seed, a.width, s_su2, s_su2 + 4, s_su2 + 20,
+                                   a.coff);
             s_q = q;
         }
         __syncthreads();
     } else {
         if (threadIdx.x == 0) {
-            Proposal q = draw_proposal(g, a.links, c, l, *a.d_sweep, a.seed, a.width);
+            Proposal q = draw_proposal(g, a.links, c, l, *a.d_sweep, a.seed, a.width, a.coff);
             if (a.forced && g.group == GGF_U1) q.th_new = a.forced[(size_t)c * 32 + a.forced_k];   // block move
             s_q = q;
         }
@@ -470,6 +472,7 @@ ggf_status ggf_link_step_ex(ggf_ctx* ctx, int link, cudaStream_t st, const int* 
     a.d_sweep = ch.d_sweep;
     a.link = link;
     a.seed = ch.opts.seed;
+    a.coff = ch.opts.chain_offset;
     a.width = ch.opts.width;
     a.links = ch.links;
     a.Wr = ch.Wr;

@@ -36,14 +36,16 @@ class GGFError(RuntimeError):
 
 class ChainOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refresh_every", ctypes.c_int), ("width", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("delay", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("delay", ctypes.c_int), ("graph", ctypes.c_int),
+                ("chain_offset", ctypes.c_uint64)]
 
 
 class ChainStats(ctypes.Structure):
     _fields_ = [("proposals", ctypes.c_uint64), ("accepts", ctypes.c_uint64), ("refreshes", ctypes.c_uint64),
                 ("sweeps", ctypes.c_uint64), ("max_drift", ctypes.c_double), ("launches", ctypes.c_uint64),
                 ("block_proposals", ctypes.c_uint64), ("block_accepts", ctypes.c_uint64),
-                ("n_chains", ctypes.c_int), ("n_pairs", ctypes.c_int)]
+                ("n_chains", ctypes.c_int), ("n_pairs", ctypes.c_int), ("max_resid", ctypes.c_double),
+                ("dense_refreshes", ctypes.c_uint64), ("dense_pfaffians", ctypes.c_uint64)]
 
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
@@ -51,7 +53,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
            "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
-           "ggf_debug_poison_inverse", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
+           "ggf_debug_poison_inverse", "ggf_chains_refine", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
            "ggf_chains_electric_field", "ggf_chains_link_terms",
            "ggf_chains_stats",
            "ggf_checkpoint",
@@ -98,6 +100,7 @@ def load():
         "ggf_wilson_loop": ([P, I, I, I, P, P, I, P], I),
         "ggf_polyakov_loop": ([P, I, P, P, I, P], I),
         "ggf_debug_poison_inverse": ([P, I, I, I, I], I),
+        "ggf_chains_refine": ([P, I, I, I, ctypes.POINTER(ctypes.c_double)], I),
         "ggf_chains_electric_field": ([P, P, I, P], I),
         "ggf_chains_link_terms": ([P, P, P, P, I, P], I),
         "ggf_chains_state_size": ([P, ctypes.POINTER(ctypes.c_uint64)], I),
@@ -264,8 +267,10 @@ class GGF:
                                             _stream([links, out])))
         return out
 
-    def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202, delay=1, graph=1):
-        o = ChainOpts(int(precision), int(refresh_every), float(width), int(seed), int(delay), int(graph))
+    def chains_init(self, links, precision=FP64, refresh_every=64, width=0.5, seed=20241202, delay=1, graph=1,
+                    chain_offset=0):
+        o = ChainOpts(int(precision), int(refresh_every), float(width), int(seed), int(delay), int(graph),
+                      int(chain_offset))
         mem = self._mem(links)
         self.n_chains = int(links.shape[0])
         self.link_dtype = links.dtype
@@ -417,6 +422,13 @@ class GGF:
         out = np.zeros((N, N, 2))
         self._ck(self.lib.ggf_chains_inverse(self.h, int(chain), int(pair), out.ctypes.data, MEM_HOST, None))
         return out[..., 0] + 1j * out[..., 1]
+
+    def chains_refine(self, chain, pair, apply=True):
+        """max |I - M W| of one FP32 chain's cached inverse; with apply, one
+        Newton step on the tensor cores follows (skipped above 1e-3)."""
+        r = ctypes.c_double()
+        self._ck(self.lib.ggf_chains_refine(self.h, int(chain), int(pair), 1 if apply else 0, ctypes.byref(r)))
+        return r.value
 
     def debug_poison_inverse(self, chain, pair, i, j):
         """Fault injection for tests: NaN into W_pair[i][j] of one chain."""

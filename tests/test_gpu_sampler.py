@@ -110,3 +110,21 @@ def test_corrupt_checkpoint_rejected(tmp_path):
     with pytest.raises(GGFError):
         ctx.resume(bad)
     ctx.close()
+
+
+@pytest.mark.parametrize("delay", [1, 4])
+def test_chain_offset_reproduces_global_chains(delay):
+    """A replica holding global chains 2 and 3 (chain_offset = 2) makes the
+    decisions those chains make in one run of chains 0..3 (the replica split
+    of bench.py)."""
+    p = gi.make_problem(2, gi.U1, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.cold_links(p, 4), refresh_every=8, seed=41, delay=delay)
+    a = ctx.sample(3)
+    la = ctx.chains_links()
+    ctx.chains_init(gi.cold_links(p, 2), refresh_every=8, seed=41, delay=delay, chain_offset=2)
+    b = ctx.sample(3)
+    lb = ctx.chains_links()
+    ctx.close()
+    assert np.array_equal(la[2:], lb)
+    assert np.array_equal(a[:, 2:, 2], b[:, :, 2])

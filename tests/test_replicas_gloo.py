@@ -1,9 +1,13 @@
 """Multi-GPU is replicas only: chains are independent and their random
 numbers are keyed by the global chain index, so splitting chains over ranks
 and merging the per-rank observables on the host reproduces a single run.
-Checked with two gloo ranks on the CPU (the oracle sampler stands in for the
-per-rank GPU work; no collective is used in the data path, only to gather
-results and to take the max of the ranks' times)."""
+The split is the one bench.py uses: rank r holds the contiguous global
+chains r n .. r n + n - 1 and passes chain_offset = r n to the library, whose
+Philox key is (seed, chain_offset + local chain).  Checked with two gloo
+ranks on the CPU (the oracle sampler stands in for the per-rank GPU work; no
+collective is used in the data path, only to gather results and to take the
+max of the ranks' times); tests/test_gpu_sampler.py checks on the GPU that
+chain_offset reproduces the same chains of a single run."""
 import os
 import socket
 
@@ -38,7 +42,8 @@ def _rank(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     p = gi.make_problem(2, gi.U1, 1, 2, bond_scale=0.3)
-    mine = [c for c in range(4) if c % world == rank]           # global chain ids of this replica
+    n = 4 // world
+    mine = list(range(rank * n, (rank + 1) * n))                 # global chain ids of this replica
     obs = torch.from_numpy(_chains(p, mine, 3, 99))
     gathered = [torch.zeros_like(obs) for _ in range(world)]
     dist.all_gather(gathered, obs)
@@ -46,9 +51,9 @@ def _rank(rank, world, port, q):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     if rank == 0:
         merged = np.zeros((4,) + tuple(obs.shape[1:]))
+        n = 4 // world
         for r in range(world):
-            ids = [c for c in range(4) if c % world == r]
-            merged[ids] = gathered[r].numpy()
+            merged[r * n:(r + 1) * n] = gathered[r].numpy()
         q.put((merged, float(t[0])))
     dist.barrier()
     dist.destroy_process_group()
