@@ -52,9 +52,8 @@ WORKLOADS = {
              f"refresh every {REFRESH_CFG3} accepts"),
 }
 # Bond covariances: B_n (n >= 2) is B_1 rotated by a link-local Gaussian
-# unitary with generator entries of this standard deviation, so that the K
-# superposed Gaussians are distinct states.
-BOND_SCALE = 0.3
+# unitary with generator entries of this standard deviation.
+BOND_SCALE = 0.05
 BLOCK_MOVES_PER_STEP = 16
 
 # Uneven batch: every (lattice, group, K) cell below is one problem; all cells
@@ -351,6 +350,8 @@ def run_ggf(args):
         chains = args.chains
     if args.delay:
         delay = args.delay
+    if args.refresh:
+        refresh = args.refresh
     # replica r owns the chains r * chains .. (r + 1) * chains - 1 of one
     # global ensemble: Philox key (seed, global chain index)
     seed = BASE_SEED
@@ -445,6 +446,7 @@ def run_ggf(args):
         one_step(dev_obs)
     p1.record(stream)
     torch.cuda.synchronize()
+    last_tracked = dev_obs[0, :, 1].cpu().numpy().copy()     # log N tracked at the last sweep run
     sp1 = ctx.chains_stats()
     prof_ms = p0.elapsed_time(p1)
     kt = {k: ctx.kernel_time(v) for k, v in (("ratio", KT_RATIO), ("update", KT_UPDATE),
@@ -529,7 +531,7 @@ def run_ggf(args):
     # region against a fresh FP64 factorisation of its configuration
     fin = ctx.chains_links()
     fresh = ctx.logweight(np.ascontiguousarray(fin))
-    dlogp = float(np.nanmax(np.abs(fresh - obs_series[:, -1, 1])))
+    dlogp = float(np.nanmax(np.abs(fresh - last_tracked)))
     st2 = ctx.chains_stats()
     h2d = (p.gamma_site.nbytes + p.gamma_bond.nbytes + p.lam.nbytes + start.nbytes) / args.steps
     ess_timed = world * chains * sweeps_timed / (2 * tau)
@@ -552,6 +554,7 @@ def run_ggf(args):
                        "acceptance": (st1.accepts - st0.accepts) / max(1, st1.proposals - st0.proposals),
                        "refreshes_timed": int(st1.refreshes - st0.refreshes),
                        "refresh_max_resid": st2.max_resid, "refresh_dense_fallbacks": int(st2.dense_refreshes),
+                       "refresh_newton_steps": int(st2.refine_steps),
                        "pfaffian_dense_fallbacks": int(st2.dense_pfaffians),
                        "init_s": t_setup},
             "dlogp_vs_fp64_recompute": dlogp, "max_drift_at_refresh": st2.max_drift,
@@ -670,16 +673,17 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--burn", type=int, default=40,
+    ap.add_argument("--burn", type=int, default=30,
                     help="thermalisation sweeps from the cold start (untimed, discarded)")
-    ap.add_argument("--tau-sweeps", type=int, default=30,
+    ap.add_argument("--tau-sweeps", type=int, default=25,
                     help="untimed sweeps recorded (with warm-up and timed ones) for the tau_int estimate")
-    ap.add_argument("--prof-sweeps", type=int, default=8,
+    ap.add_argument("--prof-sweeps", type=int, default=9,
                     help="sweeps of the separate profiled pass (kernel shares, roofline)")
     ap.add_argument("--impl", default="ggf", choices=["ggf", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=sorted(WORKLOADS) + ["cfg5"])
     ap.add_argument("--chains", type=int, default=0)
     ap.add_argument("--delay", type=int, default=0, help="override the workload's batch size (links per flush)")
+    ap.add_argument("--refresh", type=int, default=0, help="override the workload's refresh cadence (accepts)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--burn-train", type=int, default=4, help="cfg4: local sweeps before collecting training data")
     ap.add_argument("--train-sweeps", type=int, default=6, help="cfg4: local sweeps whose configurations train the net")

@@ -369,6 +369,10 @@ ggf_status ggf_chains_score(ggf_ctx* ctx, double* out, int mem, void* stream);
  * device.  GGF_EINVAL for an index out of range, GGF_ESTATE before
  * ggf_chains_init. */
 ggf_status ggf_debug_poison_inverse(ggf_ctx* ctx, int chain, int pair, int i, int j);
+/* Test hook (no counterpart in the paper): multiply the cached FP32 inverse
+ * of one chain and pair by `factor`, an error of known size for the refresh
+ * to repair.  Synchronous. */
+ggf_status ggf_debug_scale_inverse(ggf_ctx* ctx, int chain, int pair, double factor);
 
 /* Copy the cached inverse W_nm = M_nm(G)^{-1} of one chain and pair (pair
  * index as in ggf_get_constants) into out [N][N][2] as FP64 (re, im), N = 8 n_v
@@ -379,7 +383,10 @@ ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, in
  * ggf_get_constants): *rmax = max |I - M_nm(G) W| over the entries (M
  * assembled in FP64 from the chain's links, the product in FP32).  apply != 0
  * then refines W by one Newton step W <- W + W (I - M W) on the tensor cores
- * (the step the periodic refresh takes), skipped when *rmax > 1e-3.  The
+ * (one TF32 product when *rmax <= 1e-4, else the FP32-accurate three-product
+ * split; skipped when *rmax > 5e-2).  The periodic refresh skips the step at
+ * the FP32 floor (*rmax <= 4e-6) and repeats it, at most three times, while
+ * the residual shrinks.  The
  * paper has no counterpart; for tests and diagnostics.  Synchronous. */
 ggf_status ggf_chains_refine(ggf_ctx* ctx, int chain, int pair, int apply, double* rmax);
 
@@ -392,7 +399,9 @@ typedef struct {
     double max_resid;          /* FP32 chains: largest |I - M W| entry met by a
                                   refresh before its Newton step */
     uint64_t dense_refreshes;  /* FP32 chains refreshed by FP64 Gauss-Jordan
-                                  because the residual was above 1e-3 */
+                                  because the Newton steps could not bring
+                                  the residual to the FP32 floor */
+    uint64_t refine_steps;     /* Newton steps taken by refreshes */
     uint64_t dense_pfaffians;  /* log-Pfaffians that fell back from the
                                   site-by-site to the dense elimination */
 } ggf_chain_stats;

@@ -11,9 +11,14 @@
 size_t ggf_factor_tmp_bytes(int n, int batch);
 size_t ggf_refine_bytes(int N, bool cplx);
 ggf_status ggf_refine_inverse(ggf_ctx* ctx, bool cplx, const void* d_links, int cfg, int pair, float* W, void* ws,
-                              double tol, double* rmax, cudaStream_t st);
-// largest residual |I - M W| entry that one Newton step on the tensor cores refines
-static const double kRefineTol = 1e-3;
+                              int terms, double* rmax, cudaStream_t st);
+// Newton refinement policy for FP32 inverses (largest |I - M W| entry r):
+// r <= kRefineFloor is the FP32 floor (no step); r <= kRefineOne takes one
+// step with one TF32 product; r <= kRefineTol takes three-product steps.
+// Steps repeat (at most three) while each halves r; the inverse is kept when
+// r ends at most kRefineOne (a matrix whose FP32 floor lies above
+// kRefineFloor stalls there), else the chain is refactored by Gauss-Jordan.
+static const double kRefineFloor = 4e-6, kRefineOne = 1e-4, kRefineTol = 5e-2;
 ggf_status ggf_link_step(ggf_ctx* ctx, int link, cudaStream_t st);
 ggf_status ggf_observe(ggf_ctx* ctx, double* d_obs, cudaStream_t st);
 ggf_status ggf_mark_refresh(ggf_ctx* ctx, cudaStream_t st);
@@ -303,14 +308,35 @@ ggf_status dense_inverse(ggf_ctx* ctx, const std::vector<int>& chains, cudaStrea
     return GGF_OK;
 }
 
+// Newton refinement of one FP32 inverse by the policy above; false when the
+// residual is too large (or does not shrink) and the chain needs refactoring.
+ggf_status refine_one(ggf_ctx* ctx, bool cplx, int c, int p, float* W, bool* ok, cudaStream_t st) {
+    double r = 0.0;
+    GGF_TRY(ggf_refine_inverse(ctx, cplx, ctx->ch.links, c, p, W, ctx->work, 0, &r, st));
+    ctx->refine_rmax = std::max(ctx->refine_rmax, r);
+    for (int step = 0; step < 3; ++step) {
+        if (r <= kRefineFloor) { *ok = true; return GGF_OK; }
+        if (!(r <= kRefineTol)) break;
+        double unused = 0.0, after = 0.0;
+        GGF_TRY(ggf_refine_inverse(ctx, cplx, ctx->ch.links, c, p, W, ctx->work, r <= kRefineOne ? 1 : 3, &unused, st));
+        GGF_TRY(ggf_refine_inverse(ctx, cplx, ctx->ch.links, c, p, W, ctx->work, 0, &after, st));
+        ctx->refine_steps += 1;
+        // a step that no longer shrinks the residual has met this matrix's
+        // FP32 floor (the rounded exact inverse has the same residual)
+        if (!(after < 0.5 * r)) { r = std::min(r, after); *ok = r <= kRefineOne; return GGF_OK; }
+        r = after;
+    }
+    *ok = r <= kRefineOne;
+    return GGF_OK;
+}
+
 // Newton refinement of the listed FP32 chains' inverses (k_refine.cu); the
 // chains whose residual is too large for it are returned in `dense`.
 ggf_status newton_inverse(ggf_ctx* ctx, const std::vector<int>& chains, std::vector<int>& dense, cudaStream_t st) {
     Chains& ch = ctx->ch;
     const int N = ctx->g.N;
     const size_t NN = (size_t)N * N;
-    const size_t need = ggf_refine_bytes(N, ctx->Kc > 0);
-    GGF_TRY(ggf_workspace(ctx, need));
+    GGF_TRY(ggf_workspace(ctx, ggf_refine_bytes(N, ctx->Kc > 0)));
     for (int c : chains) {
         bool ok = true;
         for (int fam = 0; fam < 2 && ok; ++fam) {
@@ -319,10 +345,7 @@ ggf_status newton_inverse(ggf_ctx* ctx, const std::vector<int>& chains, std::vec
             for (int p = 0; p < npf && ok; ++p) {
                 float* W = cplx ? (float*)ch.Wc + ((size_t)c * ctx->Kc + p) * NN * 2
                                 : (float*)ch.Wr + ((size_t)c * ctx->K + p) * NN;
-                double rmax = 0.0;
-                GGF_TRY(ggf_refine_inverse(ctx, cplx, ch.links, c, p, W, ctx->work, kRefineTol, &rmax, st));
-                if (!(rmax <= kRefineTol)) ok = false;
-                ctx->refine_rmax = std::max(ctx->refine_rmax, rmax);
+                GGF_TRY(refine_one(ctx, cplx, c, p, W, &ok, st));
             }
         }
         if (!ok) dense.push_back(c);
@@ -594,7 +617,7 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     cudaStream_t st = (cudaStream_t)stream;
     ggf_free_chains(ctx);
     ctx->refine_rmax = 0.0;
-    ctx->dense_refreshes = ctx->dense_pfaffians = 0;
+    ctx->dense_refreshes = ctx->dense_pfaffians = ctx->refine_steps = 0;
     Chains& ch = ctx->ch;
     ch.opts = *opts;
     ch.n = n_chains;
@@ -1165,6 +1188,37 @@ ggf_status ggf_debug_poison_inverse(ggf_ctx* ctx, int chain, int pair, int i, in
     return GGF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+__global__ void scale_kernel(float* W, size_t n, float f) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) W[i] *= f;
+}
+}  // namespace
+
+extern "C" {
+
+ggf_status ggf_debug_scale_inverse(ggf_ctx* ctx, int chain, int pair, double factor) {
+    GGF_TRY(require(ctx, true, true));
+    Chains& ch = ctx->ch;
+    if (chain < 0 || chain >= ch.n || pair < 0 || pair >= ctx->P)
+        return ggf_fail(ctx, GGF_EINVAL, "bad debug_scale_inverse arguments");
+    if (ch.opts.precision != GGF_FP32) return ggf_fail(ctx, GGF_EINVAL, "debug_scale_inverse: FP32 chains only");
+    cudaSetDevice(ctx->device);
+    const size_t NN = (size_t)ctx->g.N * ctx->g.N;
+    const bool cplx = pair >= ctx->K;
+    const int p = cplx ? pair - ctx->K : pair;
+    float* W = cplx ? (float*)ch.Wc + ((size_t)chain * ctx->Kc + p) * NN * 2
+                    : (float*)ch.Wr + ((size_t)chain * ctx->K + p) * NN;
+    const size_t n = NN * (cplx ? 2 : 1);
+    GGF_CK(cudaDeviceSynchronize());
+    scale_kernel<<<(unsigned)((n + 255) / 256), 256>>>(W, n, (float)factor);
+    GGF_CK(cudaGetLastError());
+    GGF_CK(cudaDeviceSynchronize());
+    return GGF_OK;
+}
+
 ggf_status ggf_chains_refine(ggf_ctx* ctx, int chain, int pair, int apply, double* rmax) {
     GGF_TRY(require(ctx, true, true));
     Chains& ch = ctx->ch;
@@ -1180,7 +1234,11 @@ ggf_status ggf_chains_refine(ggf_ctx* ctx, int chain, int pair, int apply, doubl
                     : (float*)ch.Wr + ((size_t)chain * ctx->K + p) * NN;
     GGF_CK(cudaDeviceSynchronize());
     GGF_TRY(ggf_workspace(ctx, ggf_refine_bytes(N, cplx)));
-    GGF_TRY(ggf_refine_inverse(ctx, cplx, ch.links, chain, p, W, ctx->work, apply ? kRefineTol : -1.0, rmax, 0));
+    GGF_TRY(ggf_refine_inverse(ctx, cplx, ch.links, chain, p, W, ctx->work, 0, rmax, 0));
+    if (apply && *rmax <= kRefineTol) {
+        double unused = 0.0;
+        GGF_TRY(ggf_refine_inverse(ctx, cplx, ch.links, chain, p, W, ctx->work, *rmax <= kRefineOne ? 1 : 3, &unused, 0));
+    }
     GGF_CK(cudaDeviceSynchronize());
     return GGF_OK;
 }
@@ -1233,6 +1291,7 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     out->n_pairs = ctx->P;
     out->max_resid = ctx->refine_rmax;
     out->dense_refreshes = ctx->dense_refreshes;
+    out->refine_steps = ctx->refine_steps;
     out->dense_pfaffians = ctx->dense_pfaffians;
     if (h[3]) return ggf_fail(ctx, GGF_ESINGULAR, "a refresh met a singular M(G)");
     return GGF_OK;

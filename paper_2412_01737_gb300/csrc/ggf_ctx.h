@@ -108,7 +108,7 @@ struct ggf_ctx {
     // |I - M W| seen, chains refreshed by dense Gauss-Jordan instead, and
     // Pfaffian items that fell back to the dense elimination
     double refine_rmax = 0.0;
-    unsigned long long dense_refreshes = 0, dense_pfaffians = 0;
+    unsigned long long dense_refreshes = 0, dense_pfaffians = 0, refine_steps = 0;
     // event timing (ggf_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev;            // event pool

@@ -218,7 +218,7 @@ __device__ __forceinline__ void copy_stage(const float* Pan, size_t NK, int fam_
 
 // Split this thread's raw values of one plane into tf32 hi/lo and write them
 // at core-matrix row offset dst_row (and negated at dst_row2 when hi2 is given).
-template <int NR>
+template <int NR, bool LO>
 __device__ __forceinline__ void split_plane(const unsigned char* raw, int slot0, unsigned char* hi, unsigned char* lo,
                                             int dst_row, unsigned char* hi2 = nullptr, unsigned char* lo2 = nullptr,
                                             int dst_row2 = 0) {
@@ -232,28 +232,31 @@ __device__ __forceinline__ void split_plane(const unsigned char* raw, int slot0,
         const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
         const uint32_t o = cm_off(dst_row + row, kq);
         *(float4*)(hi + o) = h;
-        *(float4*)(lo + o) = l;
+        if (LO) *(float4*)(lo + o) = l;
         if (hi2) {
             const uint32_t o2 = cm_off(dst_row2 + row, kq);
             *(float4*)(hi2 + o2) = make_float4(-h.x, -h.y, -h.z, -h.w);
-            *(float4*)(lo2 + o2) = make_float4(-l.x, -l.y, -l.z, -l.w);
+            if (LO) *(float4*)(lo2 + o2) = make_float4(-l.x, -l.y, -l.z, -l.w);
         }
     }
 }
 
-template <bool CPLX>
+// LO = false: the hi planes only (one TF32 product per term), for Newton
+// corrections small enough that the tf32 rounding of the operands is far below
+// the FP32 rounding of W.
+template <bool CPLX, bool LO>
 __device__ __forceinline__ void split_stage(const unsigned char* raw, unsigned char* sb) {
     constexpr int S1 = 256 / PGROUP;   // float4 slots per thread of a 128-row plane
     if (!CPLX) {
-        split_plane<128>(raw, 0, sb, sb + PLANE_A, 0);
-        split_plane<256>(raw, S1, sb + 2 * PLANE_A, sb + 2 * PLANE_A + 256 * KC * 4, 0);
+        split_plane<128, LO>(raw, 0, sb, sb + PLANE_A, 0);
+        split_plane<256, LO>(raw, S1, sb + 2 * PLANE_A, sb + 2 * PLANE_A + 256 * KC * 4, 0);
     } else {
         unsigned char* bh = sb + 4 * PLANE_A;
         unsigned char* bl = bh + 384 * KC * 4;
-        split_plane<128>(raw, 0, sb, sb + PLANE_A, 0);                        // V_r
-        split_plane<128>(raw, S1, sb + 2 * PLANE_A, sb + 3 * PLANE_A, 0);     // V_i
-        split_plane<128>(raw, 2 * S1, bh, bl, 128);                           // U_r
-        split_plane<128>(raw, 3 * S1, bh, bl, 256, bh, bl, 0);                // U_i and -U_i
+        split_plane<128, LO>(raw, 0, sb, sb + PLANE_A, 0);                        // V_r
+        split_plane<128, LO>(raw, S1, sb + 2 * PLANE_A, sb + 3 * PLANE_A, 0);     // V_i
+        split_plane<128, LO>(raw, 2 * S1, bh, bl, 128);                           // U_r
+        split_plane<128, LO>(raw, 3 * S1, bh, bl, 256, bh, bl, 0);                // U_i and -U_i
     }
 }
 
@@ -287,7 +290,8 @@ __device__ __forceinline__ void stage_next(StageIter& it, long long total, int t
     }
 }
 
-template <bool CPLX>
+// TERMS = 3: FP32-accurate TF32 split; TERMS = 1: one TF32 product.
+template <bool CPLX, int TERMS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, const int* pend, int R, int KRM,
                 int upper, int* err) {
@@ -357,7 +361,7 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
             stage_next<ROWS>(ahead, total, tiles_i, tiles_j, fam_pairs, pend, R, upper);
             asm volatile("cp.async.wait_group %0;" ::"n"(PD) : "memory");
             if (!mbar_wait_bounded(smem_u32(&bar_empty[st]), ph ^ 1u, &s_fail)) { raise_fail(&s_fail, err); break; }
-            split_stage<CPLX>(raw + (size_t)(sidx % RAWS) * RAW_BYTES, base + st * SB);
+            split_stage<CPLX, TERMS == 3>(raw + (size_t)(sidx % RAWS) * RAW_BYTES, base + st * SB);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&bar_full[st]));
             if (++st == STAGES) { st = 0; ph ^= 1u; }
@@ -481,19 +485,25 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
                 if (!CPLX) {
                     const uint32_t ah = sb, al = sb + PLANE_A, bh = sb + 2 * PLANE_A, bl = bh + 256 * KC * 4;
                     mma_tf32(d, smem_desc(ah), smem_desc(bh), id, first);
-                    mma_tf32(d, smem_desc(ah), smem_desc(bl), id, 1u);
-                    mma_tf32(d, smem_desc(al), smem_desc(bh), id, 1u);
+                    if (TERMS == 3) {
+                        mma_tf32(d, smem_desc(ah), smem_desc(bl), id, 1u);
+                        mma_tf32(d, smem_desc(al), smem_desc(bh), id, 1u);
+                    }
                 } else {
                     const uint32_t arh = sb, arl = sb + PLANE_A, aih = sb + 2 * PLANE_A, ail = sb + 3 * PLANE_A;
                     const uint32_t bh = sb + 4 * PLANE_A, bl = bh + 384 * KC * 4;
                     const uint32_t o1 = (128 / 8) * SBO;    // rows 128..383: [U_r ; U_i]
                     // rows 0..255: [-U_i ; U_r]
                     mma_tf32(d, smem_desc(arh), smem_desc(bh + o1), id, first);
-                    mma_tf32(d, smem_desc(arh), smem_desc(bl + o1), id, 1u);
-                    mma_tf32(d, smem_desc(arl), smem_desc(bh + o1), id, 1u);
+                    if (TERMS == 3) {
+                        mma_tf32(d, smem_desc(arh), smem_desc(bl + o1), id, 1u);
+                        mma_tf32(d, smem_desc(arl), smem_desc(bh + o1), id, 1u);
+                    }
                     mma_tf32(d, smem_desc(aih), smem_desc(bh), id, 1u);
-                    mma_tf32(d, smem_desc(aih), smem_desc(bl), id, 1u);
-                    mma_tf32(d, smem_desc(ail), smem_desc(bh), id, 1u);
+                    if (TERMS == 3) {
+                        mma_tf32(d, smem_desc(aih), smem_desc(bl), id, 1u);
+                        mma_tf32(d, smem_desc(ail), smem_desc(bh), id, 1u);
+                    }
                 }
                 mma_commit(smem_u32(&bar_empty[st]));
                 if (++st == STAGES) { st = 0; ph ^= 1u; }
@@ -523,8 +533,10 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
 ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx) {
     static bool done[64] = {false};
     if (ctx->device >= 0 && ctx->device < 64 && done[ctx->device]) return GGF_OK;
-    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(true)));
-    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false)));
+    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(true)));
+    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false)));
+    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(true)));
+    GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false)));
     if (ctx->device >= 0 && ctx->device < 64) done[ctx->device] = true;
     return GGF_OK;
 }
@@ -532,7 +544,7 @@ ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx) {
 namespace {
 
 ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_chains, float* W, const float* Pan,
-                           const int* pend, int R, int KRM, bool upper, int* err, cudaStream_t st) {
+                           const int* pend, int R, int KRM, bool upper, int* err, cudaStream_t st, int terms = 3) {
     if (fam_pairs == 0 || n_chains == 0) return GGF_OK;
     if (KRM < 1) return ggf_fail(ctx, GGF_EINVAL, "tensor-core flush: empty panel");
     const int rows = cplx ? 128 : 256;
@@ -540,13 +552,19 @@ ggf_status launch_flush_tc(ggf_ctx* ctx, bool cplx, int N, int fam_pairs, int n_
     int sms = ctx->n_sms > 0 ? ctx->n_sms : 152;
     const long long grid = std::min<long long>(total, (long long)sms);
     GGF_TRY(ggf_prepare_flush_tc(ctx));
-    if (cplx) {
-        flush_tc_kernel<true><<<(unsigned)grid, TC_THREADS, smem_bytes(true), st>>>(N, fam_pairs, n_chains, W, Pan,
-                                                                                    pend, R, KRM, upper ? 1 : 0, err);
-    } else {
-        flush_tc_kernel<false><<<(unsigned)grid, TC_THREADS, smem_bytes(false), st>>>(N, fam_pairs, n_chains, W, Pan,
-                                                                                      pend, R, KRM, upper ? 1 : 0, err);
-    }
+    const int up = upper ? 1 : 0;
+    if (cplx && terms == 1)
+        flush_tc_kernel<true, 1><<<(unsigned)grid, TC_THREADS, smem_bytes(true), st>>>(N, fam_pairs, n_chains, W, Pan,
+                                                                                       pend, R, KRM, up, err);
+    else if (cplx)
+        flush_tc_kernel<true, 3><<<(unsigned)grid, TC_THREADS, smem_bytes(true), st>>>(N, fam_pairs, n_chains, W, Pan,
+                                                                                       pend, R, KRM, up, err);
+    else if (terms == 1)
+        flush_tc_kernel<false, 1><<<(unsigned)grid, TC_THREADS, smem_bytes(false), st>>>(N, fam_pairs, n_chains, W, Pan,
+                                                                                         pend, R, KRM, up, err);
+    else
+        flush_tc_kernel<false, 3><<<(unsigned)grid, TC_THREADS, smem_bytes(false), st>>>(N, fam_pairs, n_chains, W, Pan,
+                                                                                         pend, R, KRM, up, err);
     GGF_CK(cudaGetLastError());
     return GGF_OK;
 }
@@ -610,12 +628,11 @@ ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st) {
 }
 
 // W -= U V for one N x N matrix with rank-K panels (K = pend[0] * R, panel
-// column count KRM), FP32-accurate (TF32 three-product split).  Used by the
-// Newton refinement of the inverses (k_refine.cu).
+// column count KRM), terms = 3 (FP32-accurate TF32 split) or 1 (one TF32
+// product).  Used by the Newton refinement of the inverses (k_refine.cu).
 ggf_status ggf_flush_tc_one(ggf_ctx* ctx, bool cplx, int N, float* W, const float* Pan, const int* pend, int R,
-                            int KRM, int nprod, cudaStream_t st) {
-    (void)nprod;
-    return launch_flush_tc(ctx, cplx, N, 1, 1, W, Pan, pend, R, KRM, false, ctx->d_err, st);
+                            int KRM, int terms, cudaStream_t st) {
+    return launch_flush_tc(ctx, cplx, N, 1, 1, W, Pan, pend, R, KRM, false, ctx->d_err, st, terms == 1 ? 1 : 3);
 }
 
 extern "C" ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank, double* max_rel_err) {

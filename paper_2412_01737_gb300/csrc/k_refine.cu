@@ -5,8 +5,10 @@
 // the partner end of its link, <= B + 2 n_v entries), so R costs O(N^2 B)
 // FP32 work assembled from the links; the dense product W R runs on the
 // tcgen05 tensor cores through the flush kernel (W -= U V with U = W and
-// V = -R, rank N, FP32-accurate TF32 three-product split).  The error of W
-// after the step is about ||R||^2 plus the FP32 floor of computing R.
+// V = -R, rank N).  The error of W after a step is about ||R||^2 plus the
+// FP32 floor of computing R; for a residual below 1e-4 one TF32 product per
+// term suffices (its 2^-11 rounding of a correction that small is below the
+// FP32 rounding of W), larger residuals take the three-product split.
 #include <algorithm>
 #include <cstring>
 #include "ggf_ctx.h"
@@ -176,12 +178,15 @@ size_t ggf_refine_bytes(int N, bool cplx) {
     return panel_plane(N, N) * (cplx ? 4 : 2) * sizeof(float) + 256;
 }
 
-// One Newton step on W (FP32, N x N, real or interleaved complex) for the
-// matrix M of (cfg, pair-within-family).  ws holds ggf_refine_bytes(N, cplx)
-// bytes.  Returns in *rmax the largest |R| entry before the step; when it is
-// above tol the step is not applied (the caller refactors densely).
+// Newton refinement of W (FP32, N x N, real or interleaved complex) for the
+// matrix M of (cfg, pair-within-family), in two calls:
+//   terms = 0: measure, *rmax = max |I - M W| over the entries, and keep
+//              -R = M W - I in the workspace (synchronises the stream);
+//   terms = 1 or 3: apply W <- W + W R with the R the last measure left (one
+//              TF32 product, or the FP32-accurate three-product split).
+// ws holds ggf_refine_bytes(N, cplx) bytes and must not change in between.
 ggf_status ggf_refine_inverse(ggf_ctx* ctx, bool cplx, const void* d_links, int cfg, int pair, float* W, void* ws,
-                              double tol, double* rmax, cudaStream_t st) {
+                              int terms, double* rmax, cudaStream_t st) {
     const Geometry& g = ctx->g;
     const int N = g.N, NP = panel_rows(N);
     if (N % 8) return ggf_fail(ctx, GGF_EINVAL, "refinement needs N divisible by 8");
@@ -191,6 +196,15 @@ ggf_status ggf_refine_inverse(ggf_ctx* ctx, bool cplx, const void* d_links, int 
     float* Vt = Pan + (cplx ? 2 : 1) * NK;
     unsigned* d_rmax = (unsigned*)(Pan + (cplx ? 4 : 2) * NK);
     int* d_pend = (int*)(d_rmax + 1);
+    if (terms != 0) {
+        dim3 ug((N + 255) / 256, N / 8);
+        if (cplx) upanel_kernel<true><<<ug, 256, 0, st>>>(N, W, U, NK, NP);
+        else upanel_kernel<false><<<ug, 256, 0, st>>>(N, W, U, NK, NP);
+        set_int<<<1, 1, 0, st>>>(d_pend, N / 8);
+        GGF_CK(cudaGetLastError());
+        ctx->launches += 3;
+        return ggf_flush_tc_one(ctx, cplx, N, W, Pan, d_pend, 8, N, terms, st);
+    }
     GGF_CK(cudaMemsetAsync(d_rmax, 0, sizeof(unsigned), st));
     dim3 grid((N + RT - 1) / RT, (N + RB - 1) / RB);
     if (cplx)
@@ -198,19 +212,12 @@ ggf_status ggf_refine_inverse(ggf_ctx* ctx, bool cplx, const void* d_links, int 
     else
         resid_kernel<double><<<grid, RT, 0, st>>>(ctx->dc(), d_links, cfg, pair, W, Vt, NK, NP, d_rmax);
     GGF_CK(cudaGetLastError());
+    ctx->launches += 1;
     unsigned hb = 0;
     GGF_CK(cudaMemcpyAsync(&hb, d_rmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     GGF_CK(cudaStreamSynchronize(st));
     float hr;
     std::memcpy(&hr, &hb, sizeof(float));
     *rmax = hr;
-    ctx->launches += 1;
-    if (!(hr <= tol)) return GGF_OK;
-    dim3 ug((N + 255) / 256, N / 8);
-    if (cplx) upanel_kernel<true><<<ug, 256, 0, st>>>(N, W, U, NK, NP);
-    else upanel_kernel<false><<<ug, 256, 0, st>>>(N, W, U, NK, NP);
-    set_int<<<1, 1, 0, st>>>(d_pend, N / 8);
-    GGF_CK(cudaGetLastError());
-    ctx->launches += 3;
-    return ggf_flush_tc_one(ctx, cplx, N, W, Pan, d_pend, 8, N, 3, st);
+    return GGF_OK;
 }

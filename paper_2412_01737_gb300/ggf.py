@@ -45,7 +45,8 @@ class ChainStats(ctypes.Structure):
                 ("sweeps", ctypes.c_uint64), ("max_drift", ctypes.c_double), ("launches", ctypes.c_uint64),
                 ("block_proposals", ctypes.c_uint64), ("block_accepts", ctypes.c_uint64),
                 ("n_chains", ctypes.c_int), ("n_pairs", ctypes.c_int), ("max_resid", ctypes.c_double),
-                ("dense_refreshes", ctypes.c_uint64), ("dense_pfaffians", ctypes.c_uint64)]
+                ("dense_refreshes", ctypes.c_uint64), ("refine_steps", ctypes.c_uint64),
+                ("dense_pfaffians", ctypes.c_uint64)]
 
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",
@@ -53,7 +54,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
            "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
-           "ggf_debug_poison_inverse", "ggf_chains_refine", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
+           "ggf_debug_poison_inverse", "ggf_chains_refine", "ggf_debug_scale_inverse", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
            "ggf_chains_electric_field", "ggf_chains_link_terms",
            "ggf_chains_stats",
            "ggf_checkpoint",
@@ -101,6 +102,7 @@ def load():
         "ggf_polyakov_loop": ([P, I, P, P, I, P], I),
         "ggf_debug_poison_inverse": ([P, I, I, I, I], I),
         "ggf_chains_refine": ([P, I, I, I, ctypes.POINTER(ctypes.c_double)], I),
+        "ggf_debug_scale_inverse": ([P, I, I, ctypes.c_double], I),
         "ggf_chains_electric_field": ([P, P, I, P], I),
         "ggf_chains_link_terms": ([P, P, P, P, I, P], I),
         "ggf_chains_state_size": ([P, ctypes.POINTER(ctypes.c_uint64)], I),
@@ -429,6 +431,10 @@ class GGF:
         r = ctypes.c_double()
         self._ck(self.lib.ggf_chains_refine(self.h, int(chain), int(pair), 1 if apply else 0, ctypes.byref(r)))
         return r.value
+
+    def debug_scale_inverse(self, chain, pair, factor):
+        """Test hook: multiply one FP32 chain's cached inverse by `factor`."""
+        self._ck(self.lib.ggf_debug_scale_inverse(self.h, int(chain), int(pair), float(factor)))
 
     def debug_poison_inverse(self, chain, pair, i, j):
         """Fault injection for tests: NaN into W_pair[i][j] of one chain."""

@@ -51,11 +51,9 @@ def test_newton_step_on_fresh_inverse(L, grp, nv, K):
         want = np.linalg.inv(reduced_matrix(p, links[1], n, m))
         got = ctx.chains_inverse(1, k, N)
         got = got.real if n == m else got
-        print("pair", (n, m), "W err", np.abs(got - want).max() / np.abs(want).max())
         r0 = ctx.chains_refine(1, k, apply=False)
         r1 = ctx.chains_refine(1, k, apply=True)
         r2 = ctx.chains_refine(1, k, apply=False)
-        print("pair", (n, m), "resid", r0, r1, r2)
         assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
         assert r0 < 1e-5 and r1 == r0 and r2 < 1e-5
         got = ctx.chains_inverse(1, k, N)
@@ -78,7 +76,7 @@ def test_fp32_refresh_every_sweep(L, grp, nv, K, delay):
     st = ctx.chains_stats()
     assert st.refreshes > 0
     assert st.dense_refreshes == 0
-    assert 0.0 < st.max_resid < 1e-3
+    assert 0.0 < st.max_resid < 1e-4
     links = ctx.chains_links()
     ell = ctx.chains_ell()
     lc, pr = ctx.get_constants()
@@ -142,4 +140,31 @@ def test_logweight_16x16_u1_k2_golden():
         assert abs(g.real - o.real) <= 1e-10 * max(1.0, abs(o.real))
         if n != m:
             assert phase_dist(np.array([g.imag]), np.array([o.imag])).max() <= 1e-9
+    ctx.close()
+
+
+def test_newton_step_repairs_a_perturbed_inverse():
+    """A Newton step (three-product split for a residual of 1e-3, one product
+    below 1e-4) brings an inverse with a perturbed entry back to the FP32
+    floor: the perturbation is planted in W on the device through the
+    diagnostic hook, and the refined W matches numpy's inverse again."""
+    from paper_2412_01737_gb300 import FP32
+    p = gi.make_problem(4, gi.U1, 2, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    links = gi.random_links(p, 1, seed=12)
+    ctx.chains_init(links, precision=FP32, refresh_every=10**9, seed=9, delay=4)
+    N = 8 * 2 * 16
+    lc, pr = ctx.get_constants()
+    for k, (n, m) in enumerate(pr):
+        want = np.linalg.inv(reduced_matrix(p, links[0], n, m))
+        ctx.debug_scale_inverse(0, k, 1.0 + 1e-3)
+        r0 = ctx.chains_refine(0, k, apply=True)
+        assert 5e-4 < r0 < 5e-2
+        r1 = ctx.chains_refine(0, k, apply=True)
+        assert r1 < 1e-5 < r0
+        r2 = ctx.chains_refine(0, k, apply=False)
+        assert r2 < 1e-5
+        got = ctx.chains_inverse(0, k, N)
+        got = got.real if n == m else got
+        assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
     ctx.close()
