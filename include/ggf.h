@@ -408,6 +408,14 @@ typedef struct {
 
 ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out);
 
+/* Per-chain failure report (the aggregate counters above say that something
+ * failed, this says which chain): status[n_chains] (int32, host or device per
+ * mem) gets GGF_ESINGULAR for a chain whose factorisation met a singular
+ * M_nm(G) or whose tracked log-weights are not finite, GGF_EDRIFT for one
+ * whose largest |l_tracked - l_refresh| so far exceeds drift_tol (tol <= 0:
+ * not checked), else GGF_OK.  Synchronises `stream`. */
+ggf_status ggf_chains_status(ggf_ctx* ctx, double drift_tol, int32_t* status, int mem, void* stream);
+
 /* Write / read the chain state (links, sweep counter, options, log-weights,
  * counters).  Inverses are rebuilt on resume by a full refresh, so resumed
  * chains make the same decisions as uninterrupted ones. */

@@ -71,7 +71,7 @@ void ggf_free_chains(ggf_ctx* ctx) {
     if (c.d_sweep) cudaFree(c.d_sweep);
     if (c.d_obs_stage) cudaFree(c.d_obs_stage);
     void* ptrs[] = {c.links, c.Wr, c.Wc, c.ell, c.zbuf, c.ybuf, c.accept, c.since_refresh,
-                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend, c.Sm};
+                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend, c.Sm, c.flags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ggf_chain_opts o = c.opts;
@@ -229,14 +229,17 @@ ggf_status front_family(ggf_ctx* ctx, bool cplx, int n_cfg, int npf, const void*
 // last refresh.
 __global__ void ell_set_kernel(int n_items, int pair_off, int P, bool cplx, bool init, const int* item_chain,
                                const int* item_pair, const cxd* logpf, const cxd* phase, cxd* ell, double* drift,
-                               int* since, unsigned long long* counters) {
+                               int* since, unsigned long long* counters, int* flags) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= n_items) return;
     int c = item_chain[it], p = pair_off + item_pair[it];
     cxd& el = ell[(size_t)c * P + p];
     cxd v = {logpf[it].x, 0.0};
     if (cplx) v.y = atan2(phase[it].y, phase[it].x);
-    if (!isfinite(v.x)) atomicAdd(&counters[3], 1ULL);
+    if (!isfinite(v.x)) {
+        atomicAdd(&counters[3], 1ULL);
+        atomicOr(&flags[c], 1);
+    }
     if (!init) {
         double d = fabs(v.x - el.x);
         if (cplx) d += fabs(remainder(v.y - el.y, 2 * M_PI));
@@ -246,9 +249,27 @@ __global__ void ell_set_kernel(int n_items, int pair_off, int P, bool cplx, bool
     since[c] = 0;
 }
 
-__global__ void count_singular_kernel(int n_items, const cxd* logdet, unsigned long long* counters) {
+__global__ void count_singular_kernel(int n_items, const int* item_chain, const cxd* logdet,
+                                      unsigned long long* counters, int* flags) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it < n_items && !isfinite(logdet[it].x)) atomicAdd(&counters[3], 1ULL);
+    if (it < n_items && !isfinite(logdet[it].x)) {
+        atomicAdd(&counters[3], 1ULL);
+        atomicOr(&flags[item_chain[it]], 1);
+    }
+}
+
+// Per-chain status: singular factorisation or non-finite tracked log-weight
+// -> GGF_ESINGULAR; drift above tol (tol > 0) -> GGF_EDRIFT; else GGF_OK.
+__global__ void status_kernel(int n, int P, const cxd* ell, const double* drift, const int* flags, double tol,
+                              int32_t* status) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    bool bad = (flags[c] & 1) != 0;
+    for (int p = 0; p < P; ++p) {
+        const cxd e = ell[(size_t)c * P + p];
+        bad |= !isfinite(e.x) || !isfinite(e.y);
+    }
+    status[c] = bad ? GGF_ESINGULAR : (tol > 0.0 && !(drift[c] <= tol)) ? GGF_EDRIFT : GGF_OK;
 }
 
 // FP64 Gauss-Jordan inverses of the listed chains' M_nm(G), converted into
@@ -299,7 +320,8 @@ ggf_status dense_inverse(ggf_ctx* ctx, const std::vector<int>& chains, cudaStrea
                 if (fp64) scatter_kernel<cxd><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxd*)ch.Wc);
                 else scatter_kernel<cxf><<<grid, 256, 0, st>>>(N, npf, d_chain, d_pair, A, true, (cxf*)ch.Wc);
             }
-            count_singular_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, d_logdet, ch.counters);
+            count_singular_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, d_chain, d_logdet, ch.counters,
+                                                                       ch.flags);
             ctx->launches += 2;
             GGF_CK(cudaGetLastError());
             GGF_CK(cudaStreamSynchronize(st));  // hc/hp are reused by the next chunk
@@ -378,7 +400,7 @@ ggf_status chain_ell(ggf_ctx* ctx, const std::vector<int>& chains, bool init, cu
         GGF_CK(cudaMemcpyAsync(d_pair, hp.data(), items * sizeof(int), cudaMemcpyHostToDevice, st));
         ell_set_kernel<<<(items + 127) / 128, 128, 0, st>>>(items, cplx ? ctx->K : 0, ctx->P, cplx, init, d_chain,
                                                             d_pair, d_logpf, d_phase, ch.ell, ch.drift,
-                                                            ch.since_refresh, ch.counters);
+                                                            ch.since_refresh, ch.counters, ch.flags);
         GGF_CK(cudaGetLastError());
         GGF_CK(cudaStreamSynchronize(st));
     }
@@ -662,6 +684,8 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
     GGF_CK(cudaMalloc(&ch.sweep_acc, n_chains * sizeof(int)));
     GGF_CK(cudaMalloc(&ch.counters, 6 * sizeof(unsigned long long)));
     GGF_CK(cudaMalloc(&ch.drift, n_chains * sizeof(double)));
+    GGF_CK(cudaMalloc(&ch.flags, n_chains * sizeof(int)));
+    GGF_CK(cudaMemsetAsync(ch.flags, 0, n_chains * sizeof(int), st));
     GGF_CK(cudaMalloc(&ch.refresh_list, (n_chains + 1) * sizeof(int)));
     GGF_CK(cudaMemsetAsync(ch.accept, 0, n_chains * sizeof(int), st));
     GGF_CK(cudaMemsetAsync(ch.since_refresh, 0, n_chains * sizeof(int), st));
@@ -1271,6 +1295,26 @@ ggf_status ggf_chains_inverse(ggf_ctx* ctx, int chain, int pair, double* out, in
     return GGF_OK;
 }
 
+ggf_status ggf_chains_status(ggf_ctx* ctx, double drift_tol, int32_t* status, int mem, void* stream) {
+    GGF_TRY(require(ctx, true, true));
+    if (!status) return ggf_fail(ctx, GGF_EINVAL, "null status");
+    cudaSetDevice(ctx->device);
+    Chains& ch = ctx->ch;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t* d = status;
+    DBuf tmp;
+    if (mem == GGF_MEM_HOST) {
+        GGF_TRY(dalloc(ctx, tmp, (size_t)ch.n * sizeof(int32_t)));
+        d = (int32_t*)tmp.p;
+    }
+    status_kernel<<<(ch.n + 127) / 128, 128, 0, st>>>(ch.n, ctx->P, ch.ell, ch.drift, ch.flags, drift_tol, d);
+    GGF_CK(cudaGetLastError());
+    if (mem == GGF_MEM_HOST)
+        GGF_CK(cudaMemcpyAsync(status, d, (size_t)ch.n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GGF_CK(cudaStreamSynchronize(st));
+    return GGF_OK;
+}
+
 ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     GGF_TRY(require(ctx, true, true));
     if (!out) return ggf_fail(ctx, GGF_EINVAL, "null stats");
@@ -1321,7 +1365,8 @@ static std::vector<StatePart> state_parts(ggf_ctx* ctx) {
             {ch.Wc, (size_t)ch.n * ctx->Kc * NN * 2 * rsz},
             {ch.ell, (size_t)ch.n * ctx->P * sizeof(cxd)},
             {ch.since_refresh, (size_t)ch.n * sizeof(int)},
-            {ch.drift, (size_t)ch.n * sizeof(double)}};
+            {ch.drift, (size_t)ch.n * sizeof(double)},
+            {ch.flags, (size_t)ch.n * sizeof(int)}};
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }

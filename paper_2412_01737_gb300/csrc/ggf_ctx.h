@@ -45,6 +45,7 @@ struct Chains {
     int* sweep_acc = nullptr;     // [n]
     unsigned long long* counters = nullptr;  // [6]: proposals, accepts, refreshes, singular, block proposals, block accepts
     double* drift = nullptr;      // [n] max drift seen
+    int* flags = nullptr;         // [n] bit 0: a factorisation of this chain met a singular M
     int* refresh_list = nullptr;  // [n + 1]
     // delayed updates (opts.delay > 1): per chain and pair, U^T and V panels
     // [n][pairs][kmax r][N] in W precision, pending count per chain

@@ -46,8 +46,22 @@
 
 namespace {
 
-constexpr int STAGES = 3;                     // split (MMA operand) stages
-constexpr int RAWS = 4, PD = 3;               // raw cp.async slots; stages of loads in flight ahead
+// Pipeline depths (compile-time; shared memory: STAGES x 40 KB + RAWS x 16 KB
+// + 1 KB must stay within the 227 KB per CTA).
+#ifndef GGF_FLUSH_STAGES
+#define GGF_FLUSH_STAGES 3
+#endif
+#ifndef GGF_FLUSH_PD
+#define GGF_FLUSH_PD 3
+#endif
+// Epilogue of real tiles: 1 = the W rows of the next 16-row chunk are loaded
+// before the current chunk is drained (two chunks of loads in flight).
+#ifndef GGF_FLUSH_EPI_PP
+#define GGF_FLUSH_EPI_PP 0
+#endif
+constexpr int STAGES = GGF_FLUSH_STAGES;      // split (MMA operand) stages
+constexpr int PD = GGF_FLUSH_PD;              // stages of loads in flight ahead
+constexpr int RAWS = PD + 1;                  // raw cp.async slots
 constexpr int NPROD = 8, NEPI = 8;            // producer and epilogue warps (+ one MMA warp)
 constexpr int EPI_PARTS = NEPI / 4;           // epilogue warps per TMEM lane quarter (row groups of a tile)
 constexpr int PGROUP = NPROD * 32;
@@ -63,6 +77,7 @@ constexpr int RAW_BYTES = 8 * 128 * 16;
 // both variants reserve the complex size, so exactly one CTA fits on an SM
 // (the CTA allocates all 512 TMEM columns)
 __host__ __device__ constexpr int smem_bytes(bool) { return STAGES * stage_bytes(true) + RAWS * RAW_BYTES + 1024; }
+static_assert(STAGES * stage_bytes(true) + RAWS * RAW_BYTES + 1024 <= 227 * 1024, "flush pipeline exceeds shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -399,8 +414,16 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
             const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
             if (!CPLX) {
                 // rows i0 + half*RG + 16 cb + k  <->  TMEM column half*RG + 16 cb + k (RG = 256 / EPI_PARTS)
-#pragma unroll 1
-                for (int cb = 0; cb < 256 / EPI_PARTS / 16; ++cb) {
+                constexpr int NCB = 256 / EPI_PARTS / 16;
+                auto load_w = [&](int cb, float* w) {
+                    const int ib = t.i0 + half * (256 / EPI_PARTS) + cb * 16;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int i = ib + k;
+                        w[k] = (i < N && j < N) ? Wp[(size_t)i * N + j] : 0.f;
+                    }
+                };
+                auto drain = [&](int cb, const float* w) {
                     uint32_t v[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -409,18 +432,30 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
                           "=r"(v[14]), "=r"(v[15])
                         : "r"(tl + half * (256 / EPI_PARTS) + cb * 16));
-                    const int ib = t.i0 + half * (256 / EPI_PARTS) + cb * 16;
-                    float w[16];
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const int i = ib + k;
-                        w[k] = (i < N && j < N) ? Wp[(size_t)i * N + j] : 0.f;
-                    }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int ib = t.i0 + half * (256 / EPI_PARTS) + cb * 16;
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         const int i = ib + k;
                         if (i < N && j < N) Wp[(size_t)i * N + j] = w[k] - __uint_as_float(v[k]);
+                    }
+                };
+                if (GGF_FLUSH_EPI_PP) {
+                    float wa[16], wb[16];
+                    load_w(0, wa);
+#pragma unroll 1
+                    for (int cb = 0; cb < NCB; cb += 2) {
+                        load_w(cb + 1, wb);
+                        drain(cb, wa);
+                        if (cb + 2 < NCB) load_w(cb + 2, wa);
+                        drain(cb + 1, wb);
+                    }
+                } else {
+#pragma unroll 1
+                    for (int cb = 0; cb < NCB; ++cb) {
+                        float w[16];
+                        load_w(cb, w);
+                        drain(cb, w);
                     }
                 }
             } else {

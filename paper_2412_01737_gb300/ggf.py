@@ -24,6 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libggf.so")
 _lib = None
 
+GGF_OK, GGF_ESINGULAR, GGF_EDRIFT = 0, 4, 6
 STATUS = {0: "GGF_OK", 1: "GGF_EINVAL", 2: "GGF_ENOMEM", 3: "GGF_ECUDA", 4: "GGF_ESINGULAR",
           5: "GGF_ETIMEOUT", 6: "GGF_EDRIFT", 7: "GGF_ESTATE", 8: "GGF_EIO"}
 
@@ -54,7 +55,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_sample", "ggf_sample_group", "ggf_chains_links", "ggf_chains_ell", "ggf_chains_inverse",
            "ggf_chains_electric", "ggf_chains_fermion", "ggf_chains_pairs", "ggf_chains_score",
            "ggf_chains_fermion4", "ggf_chains_link_score", "ggf_wilson_loop", "ggf_polyakov_loop",
-           "ggf_debug_poison_inverse", "ggf_chains_refine", "ggf_debug_scale_inverse", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
+           "ggf_debug_poison_inverse", "ggf_chains_refine", "ggf_debug_scale_inverse", "ggf_chains_status", "ggf_chains_state_size", "ggf_chains_save_state", "ggf_chains_load_state",
            "ggf_chains_electric_field", "ggf_chains_link_terms",
            "ggf_chains_stats",
            "ggf_checkpoint",
@@ -103,6 +104,7 @@ def load():
         "ggf_debug_poison_inverse": ([P, I, I, I, I], I),
         "ggf_chains_refine": ([P, I, I, I, ctypes.POINTER(ctypes.c_double)], I),
         "ggf_debug_scale_inverse": ([P, I, I, ctypes.c_double], I),
+        "ggf_chains_status": ([P, ctypes.c_double, P, I, P], I),
         "ggf_chains_electric_field": ([P, P, I, P], I),
         "ggf_chains_link_terms": ([P, P, P, P, I, P], I),
         "ggf_chains_state_size": ([P, ctypes.POINTER(ctypes.c_uint64)], I),
@@ -439,6 +441,12 @@ class GGF:
     def debug_poison_inverse(self, chain, pair, i, j):
         """Fault injection for tests: NaN into W_pair[i][j] of one chain."""
         self._ck(self.lib.ggf_debug_poison_inverse(self.h, int(chain), int(pair), int(i), int(j)))
+
+    def chains_status(self, drift_tol=0.0):
+        """Per-chain status codes (GGF_OK, GGF_ESINGULAR, GGF_EDRIFT), int32 numpy array."""
+        out = np.zeros(self.n_chains, dtype=np.int32)
+        self._ck(self.lib.ggf_chains_status(self.h, float(drift_tol), out.ctypes.data, MEM_HOST, None))
+        return out
 
     def chains_stats(self):
         s = ChainStats()

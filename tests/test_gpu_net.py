@@ -48,11 +48,17 @@ def test_gradient_matches_oracle():
     lo, go = onet.loss_and_grad(params, th, [tuple(b) for b in bl], L, quant=onet.bf16)
     assert abs(loss - lo) <= 1e-3 * abs(lo)
     assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
-    # per layer as well
+    # per layer, in norm and element by element: each entry within 5 % of its
+    # oracle value plus 0.5 % of the layer's largest entry (FP32 accumulation
+    # order moves activations across BF16 rounding boundaries now and then)
     k = 0
     for ci, co in onet.LAYERS:
         m = co * ci * 9 + co
-        assert np.linalg.norm(g[k:k + m] - go[k:k + m]) <= 2e-2 * np.linalg.norm(go[k:k + m]) + 1e-6, (ci, co)
+        gl, ol = g[k:k + m], go[k:k + m]
+        assert np.linalg.norm(gl - ol) <= 2e-2 * np.linalg.norm(ol) + 1e-6, (ci, co)
+        bound = 5e-2 * np.abs(ol) + 5e-3 * np.abs(ol).max() + 1e-7
+        bad = np.abs(gl - ol) > bound
+        assert not bad.any(), (ci, co, int(bad.sum()), float((np.abs(gl - ol) / bound).max()))
         k += m
     # against the unrounded FP64 network: the BF16 format's own error
     le, ge = onet.loss_and_grad(params, th, [tuple(b) for b in bl], L)

@@ -128,3 +128,58 @@ def test_chain_offset_reproduces_global_chains(delay):
     ctx.close()
     assert np.array_equal(la[2:], lb)
     assert np.array_equal(a[:, 2:, 2], b[:, :, 2])
+
+
+def test_chain_status_reports_the_failing_chain():
+    """The per-chain status names the chain whose inverse carries a planted
+    error: chain 1's FP32 inverse is scaled by 1.01 through the test hook, its
+    ratios are then wrong by about that much, and the next refresh records a
+    drift far above the others'."""
+    from paper_2412_01737_gb300 import FP32
+    from paper_2412_01737_gb300.ggf import GGF_OK, GGF_EDRIFT
+    p = gi.make_problem(3, gi.U1, 1, 2, bond_scale=0.3)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.cold_links(p, 3), precision=FP32, refresh_every=8, seed=5, delay=1)
+    assert np.array_equal(ctx.chains_status(1e-9), [GGF_OK] * 3)
+    ctx.sample(1)
+    for k in range(3):
+        ctx.debug_scale_inverse(1, k, 1.01)
+    ctx.sample(2)
+    st = ctx.chains_stats()
+    assert st.refreshes >= 3
+    s = ctx.chains_status(1e-4)
+    assert s[0] == GGF_OK and s[2] == GGF_OK and s[1] == GGF_EDRIFT
+    ctx.close()
+
+
+def test_z2_2x2_chain_of_ten_thousand_sweeps():
+    """The 2x2 Z2 workload (one chain, 10^4 sweeps, FP64): every sweep's
+    observables equal the oracle's exact Metropolis under the same Philox
+    stream, and the visited log N(G) classes follow the exhaustive p(G)
+    (chi^2 with the effective sample size)."""
+    from oracle.observables import tau_int
+    p = gi.make_problem(2, gi.Z2, 1, 1)
+    n_sw = 10000
+    start, obs, fin, st = run_both(p, 1, n_sw, seed=20241202, refresh=64)
+    W = weight.Weights(p)
+    lk, ob, _ = mcmc.run_chain(p, W, start[0], 20241202, 0, 0, n_sw)
+    assert np.array_equal(lk, fin[0])
+    assert np.array_equal(ob[:, 0], obs[:, 0, 0])
+    assert np.abs(ob[:, 1] - obs[:, 0, 1]).max() < 1e-10
+    assert np.array_equal(ob[:, 2], obs[:, 0, 2])
+    cfgs = gi.all_z2_configs(p)
+    logs = np.array([W.log_norm(c) for c in cfgs])
+    pg = np.exp(logs - logs.max())
+    pg /= pg.sum()
+    classes = np.unique(np.round(logs, 8))
+    exp_p = np.array([pg[np.abs(logs - v) < 1e-7].sum() for v in classes])
+    series = obs[200:, 0, 1]
+    idx = np.abs(series[:, None] - classes[None, :]).argmin(axis=1)
+    assert np.abs(series - classes[idx]).max() < 1e-7
+    obs_p = np.bincount(idx, minlength=classes.size) / series.size
+    tau, _ = tau_int(series[None, :])
+    n_eff = series.size / (2 * max(tau, 0.5))
+    mask = exp_p > 0.01
+    dof = int(mask.sum()) - 1
+    chi2 = n_eff * np.sum((obs_p[mask] - exp_p[mask]) ** 2 / exp_p[mask])
+    assert chi2 < dof + 6 * np.sqrt(2 * dof) + 10

@@ -3,10 +3,14 @@ n_v = 2 (M 4096 x 4096), K = 4, FP32 chains with batches of 16 links (one
 rank-128 tensor-core flush per batch), on 32 chains (the per-chain launch
 shapes of the 256-chain benchmark, a tenth of its memory).
 
-The oracle's full recomputation is too slow at N = 4096, so the checks are
-the ones that hold at any size: the per-sweep plaquettes against the oracle's
-plaquettes of the final links, and the tracked FP32 log-weights against a
-fresh FP64 factorisation of the same configurations.
+The oracle's exact Metropolis is too slow at N = 4096 (minutes per pair
+term), so the checks are: the per-sweep plaquettes against the oracle's
+plaquettes of the final links, and the tracked FP32 log-weights against the
+FP64 log N(G) of the same configurations at an absolute 1e-4.  The FP64 value
+comes from ggf_logweight (the site-by-site Pfaffian), which
+tests/test_gpu_refresh.py pins to the oracle at this lattice size
+(16 x 16, n_v = 2, against values the oracle wrote into tests/golden/) and
+per pair at 8 x 8 with K = 4.
 """
 import numpy as np
 import pytest
@@ -29,10 +33,9 @@ def test_u1_16x16_k4_batched_fp32():
     assert np.isfinite(obs).all()
     assert np.abs(obs[-1, :, 0] - plaquette_mean(gi.U1, 16, fin)).max() <= 1e-12
     assert 0 < st.accepts < st.proposals
-    sample = np.ascontiguousarray(fin[::8])
-    fresh = ctx.logweight(sample)
-    tracked = obs[-1, ::8, 1]
-    assert np.abs(tracked - fresh).max() <= 1e-5 * np.abs(fresh).max() + 1e-3
+    fresh = ctx.logweight(np.ascontiguousarray(fin))
+    tracked = obs[-1, :, 1]
+    assert np.abs(tracked - fresh).max() <= 1e-4
     ctx.close()
 
 
