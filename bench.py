@@ -97,14 +97,14 @@ def run_cfg5(args):
     for k, (p, ch, mem) in enumerate(cells):
         links = gi.cold_links(p, ch)
         t_cell = time.time()
-        d, tim = tune_delay(p, links, 1, candidates=(4, 8, 16), use_cache=False, seed=BASE_SEED + k)
+        d, tim = tune_delay(p, links, 1, candidates=(8, 16), use_cache=False, seed=BASE_SEED + k)
         print(f"cfg5 cell {k}: L={p.L} group={p.group} K={p.K} chains={ch} delay={d} "
               f"tune {time.time() - t_cell:.1f}s {tim}", file=sys.stderr, flush=True)
         tuned.append({"L": p.L, "group": "Z2" if p.group == 0 else "U1", "K": p.K, "chains": ch, "delay": d,
                       "ms_per_sweep": {str(a): round(b, 2) for a, b in tim.items()}})
         c = GGF(0)
         c.init_problem(p)
-        c.chains_init(links, precision=1, refresh_every=1 << 30, seed=BASE_SEED + k, delay=d, graph=1)
+        c.chains_init(links, precision=1, refresh_every=REFRESH_CFG3, seed=BASE_SEED + k, delay=d, graph=1)
         ctxs.append(c)
     t_setup = time.time() - t0
     obs = [[] for _ in ctxs]
@@ -120,6 +120,14 @@ def run_cfg5(args):
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # the same sweeps cell by cell (one graph launch per cell and sweep, in
+    # sequence): what the single grouped launch saves over separate launches
+    torch.cuda.synchronize()
+    t_sep = time.time()
+    for c in ctxs:
+        c.sample(args.steps)
+    torch.cuda.synchronize()
+    t_sep = time.time() - t_sep
     ess, total_chains, launches = 0.0, 0, 0
     for k, (c, o) in enumerate(zip(ctxs, outs)):
         ser = np.concatenate([obs[k][0], o], axis=0).transpose(1, 0, 2)      # chains, sweeps, 3
@@ -135,8 +143,11 @@ def run_cfg5(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"uneven batch: {len(cells)} problems (L in 8,12,16; Z2 and U(1); K in 1,2,4), "
-                                   f"{total_chains} chains, one parent CUDA graph launch per sweep, autotuned delay",
-                       "cells": tuned, "setup_s": t_setup},
+                                   f"{total_chains} chains, one parent CUDA graph launch per sweep, autotuned delay, "
+                                   f"FP32 updates with the FP64 refresh every {REFRESH_CFG3} accepts",
+                       "cells": tuned, "setup_s": t_setup,
+                       "separate_launches_s": t_sep, "grouped_s": ms * 1e-3,
+                       "separate_note": "the timed sweeps repeated cell by cell, one graph launch per cell"},
             "roofline": None, "roofline_note": "per-kernel timing is not collected inside grouped graph launches",
             "clocks": ck, "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
@@ -329,7 +340,7 @@ def tau_report(series):
     return tau, all(c for _, c in taus), out
 
 
-def tau_calibration(args, p, prec, refresh, delay, local):
+def tau_calibration(args, p, prec, refresh, delay, local, keep=False):
     """tau_int of the same sampler from a longer run with fewer chains: the
     autocorrelation time is a property of the Markov chain (lattice, weights,
     proposal), not of how many independent chains run, and the benchmark's
@@ -352,7 +363,10 @@ def tau_calibration(args, p, prec, refresh, delay, local):
         ctx.sample(1, obs=obs)
         series.append(obs[0].cpu().numpy().copy())
     ctx.close()
-    tau, closed, detail = tau_report(np.stack(series, axis=1))
+    ser = np.stack(series, axis=1)
+    tau, closed, detail = tau_report(ser)
+    if keep:
+        return tau, closed, detail, args.tau_run, n, time.time() - t0, ser
     return tau, closed, detail, args.tau_run, n, time.time() - t0
 
 
@@ -629,6 +643,115 @@ def run_ggf(args):
         dist.destroy_process_group()
 
 
+def run_compare(args):
+    """Effective samples per second of three samplers of the same 16x16 U(1),
+    K = 4 problem, i.e. the time each needs for a given error bar on the
+    plaquette (error ~ sigma / sqrt(ESS)):
+      * plain FP64 local updates (FP64 inverses, ratios and batched updates),
+      * plain FP32 local updates with the FP64 refresh (the benchmark's sampler),
+      * the learned block proposal on top of the FP32 sampler (one local sweep
+        + 16 block moves per step, exact Metropolis-Hastings).
+    tau_int of each sampler comes from its own recorded run (FP64 and FP32
+    local updates are the same Markov chain, so they share the FP32 run's).
+    ESS/s = chain-steps per second / (2 tau_int) at the chain count each
+    sampler ran with (stated; the FP32 samplers gain a little per chain at
+    the benchmark's 256).  Plaquette means are reported with their errors
+    as a consistency check."""
+    import torch
+    import ggf_inputs as gi
+    from paper_2412_01737_gb300 import GGF, Net
+    p, chains, prec, refresh, delay, label = problem_for("cfg3")
+    out = {"metric": "effective samples/sec/GPU (comparison)", "unit": "samples/s",
+           "config": {"workload": label, "note": run_compare.__doc__.split("\n")[0]}}
+
+    def mean_err(series, tau):
+        x = series.reshape(-1)
+        n_eff = series.size / (2 * tau)
+        return float(x.mean()), float(x.std() / np.sqrt(max(n_eff, 1.0)))
+
+    # plain FP32 local updates: tau from a long recorded run
+    tau32, closed32, det32, sw32, ch32, sec32, ser32 = tau_calibration(args, p, 1, refresh, delay, 0, keep=True)
+    pl32 = mean_err(ser32[:, :, 0], tau32)
+    ctx = GGF(0)
+    ctx.init_problem(p)
+    n32 = args.tau_chains
+    ctx.chains_init(gi.cold_links(p, n32), precision=1, refresh_every=refresh, seed=BASE_SEED + 7, delay=delay)
+    ctx.sample(2)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ctx.sample(3)
+    torch.cuda.synchronize()
+    s32 = (time.time() - t0) / (3 * n32)                 # seconds per chain-sweep
+    ctx.close()
+    # plain FP64 local updates
+    n64 = 4
+    ctx = GGF(0)
+    ctx.init_problem(p)
+    ctx.chains_init(gi.cold_links(p, n64), precision=0, refresh_every=refresh, seed=BASE_SEED + 11, delay=delay)
+    ctx.sample(1)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ctx.sample(2)
+    torch.cuda.synchronize()
+    s64 = (time.time() - t0) / (2 * n64)
+    ctx.close()
+    # learned block proposal on the FP32 sampler
+    nl = args.learn_chains
+    ctx = GGF(0)
+    ctx.init_problem(p)
+    ctx.chains_init(gi.cold_links(p, nl), precision=1, refresh_every=refresh, seed=BASE_SEED + 13, delay=32)
+    obs = torch.zeros((1, nl, 3), dtype=torch.float64, device="cuda")
+    for _ in range(args.tau_burn):
+        ctx.sample(1, obs=obs)
+    data = []
+    for _ in range(args.train_sweeps):
+        ctx.sample(1)
+        data.append(ctx.chains_links())
+    data = torch.from_numpy(np.concatenate(data)).cuda()
+    net = Net(0, p.L, BASE_SEED)
+    losses = net.train(data, 128, args.train_steps, 2e-3)
+    blk = torch.zeros((BLOCK_MOVES_PER_STEP, nl, 3), dtype=torch.float64, device="cuda")
+    series = []
+    st0 = ctx.chains_stats()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for _ in range(args.learn_steps):
+        ctx.sample(1, obs=obs)
+        ctx.sample_blocks(net, BLOCK_MOVES_PER_STEP, obs=blk)
+        series.append(blk[-1].cpu().numpy().copy())
+    torch.cuda.synchronize()
+    sl = (time.time() - t0) / (args.learn_steps * nl)    # seconds per chain-step
+    st1 = ctx.chains_stats()
+    fin = ctx.chains_links()
+    dlogp = float(np.nanmax(np.abs(ctx.logweight(np.ascontiguousarray(fin)) - blk[-1, :, 1].cpu().numpy())))
+    ser = np.stack(series, axis=1)
+    taul, closedl, detl = tau_report(ser)
+    net.close()
+    ctx.close()
+    res = {}
+    for name, sec, tau, closed, nch in (("fp64_local", s64, tau32, closed32, n64),
+                                        ("fp32_local", s32, tau32, closed32, n32),
+                                        ("fp32_learned", sl, taul, closedl, nl)):
+        # chain-steps per second of the GPU at the measured chain count, over 2 tau
+        res[name] = {"s_per_chain_step": sec, "tau_int": tau, "tau_window_closed": closed, "chains_measured": nch,
+                     "ess_per_s": 1.0 / (sec * 2 * tau)}
+    res["fp32_learned"].update({"tau_detail": detl, "block_acceptance":
+                                (st1.block_accepts - st0.block_accepts) / max(1, st1.block_proposals - st0.block_proposals),
+                                "plaquette_mean_err": mean_err(ser[:, :, 0], taul), "dlogp_vs_fp64_recompute": dlogp,
+                                "train_configs": int(data.shape[0]), "train_steps": args.train_steps,
+                                "train_loss_first_last": [float(losses[:10].mean()), float(losses[-10:].mean())],
+                                "steps": args.learn_steps})
+    res["fp32_local"].update({"tau_detail": det32, "tau_sweeps": sw32, "plaquette_mean_err": pl32})
+    res["fp64_local"].update({"note": "the same Markov chain as fp32_local (FP64 arithmetic), so its tau_int"})
+    out["samplers"] = res
+    out["winner"] = max(res, key=lambda k: res[k]["ess_per_s"])
+    out["learned_vs_fp64_local"] = res["fp32_learned"]["ess_per_s"] / res["fp64_local"]["ess_per_s"]
+    out["learned_vs_fp32_local"] = res["fp32_learned"]["ess_per_s"] / res["fp32_local"]["ess_per_s"]
+    d = res["fp32_learned"]["plaquette_mean_err"][0] - pl32[0]
+    out["plaquette_difference_sigma"] = d / np.hypot(res["fp32_learned"]["plaquette_mean_err"][1], pl32[1])
+    print(json.dumps(out), flush=True)
+
+
 def observable_bytes(p, prec):
     """Algorithmic bytes of W that one call of the electric and of the
     fermionic kernel reads per chain: per pair, the B x r block between each
@@ -738,6 +861,10 @@ def main():
     ap.add_argument("--burn-train", type=int, default=4, help="cfg4: local sweeps before collecting training data")
     ap.add_argument("--train-sweeps", type=int, default=6, help="cfg4: local sweeps whose configurations train the net")
     ap.add_argument("--train-steps", type=int, default=300, help="cfg4: Adam steps")
+    ap.add_argument("--compare", action="store_true",
+                    help="ESS/s of the plain FP64, plain FP32 and learned-proposal samplers (16x16 U(1), K=4)")
+    ap.add_argument("--learn-chains", type=int, default=32, help="--compare: chains of the learned-proposal run")
+    ap.add_argument("--learn-steps", type=int, default=100, help="--compare: recorded learned-proposal steps")
     ap.add_argument("--observables", action="store_true",
                     help="time the electric and fermionic observable kernels instead of sampling")
     args = ap.parse_args()
@@ -749,6 +876,8 @@ def main():
         run_observables(args)
     elif args.workload == "cfg5":
         run_cfg5(args)
+    elif args.compare:
+        run_compare(args)
     else:
         run_ggf(args)
 

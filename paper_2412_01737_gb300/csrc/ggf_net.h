@@ -10,3 +10,6 @@ int ggf_net_L(const ggf_net* net);
 ggf_status ggf_net_head(ggf_net* net, int n, int mode, const double* theta, const int* cfg, const int* blocks,
                         double* logq, double* prop, uint64_t seed, uint64_t counter, cudaStream_t st,
                         uint64_t koff = 0);
+// GGF_ETIMEOUT once a tensor-core convolution's bounded wait ran out
+// (synchronises the device), else GGF_OK.
+ggf_status ggf_net_check(ggf_net* net);

@@ -155,6 +155,7 @@ extern "C" ggf_status ggf_sample_blocks(ggf_ctx* ctx, ggf_net* net, int n_moves,
         ch.block_moves += 1;
     }
     if (rc == GGF_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) fail_cuda(e, "sample_blocks sync");
+    if (rc == GGF_OK && (rc = ggf_net_check(net)) != GGF_OK) ctx->err = ggf_net_last_error(net);
     if (rc == GGF_OK && ctx->prof) {   // timing of the tentative link steps and flushes
         for (size_t k = 0; k + 2 < ctx->ev_cat.size(); k += 3) {
             float ms = 0;

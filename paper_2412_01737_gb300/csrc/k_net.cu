@@ -20,6 +20,13 @@
 #include "ggf_ctx.h"
 #include "ggf_net.h"
 
+ggf_status ggf_conv_fwd_tc(int n, int L, int ci, int co, bool relu, const void* X, const void* W, const float* bias,
+                           void* Y, bool out_f32, int* err, int sms, cudaStream_t st);
+ggf_status ggf_conv_bwd_data_tc(int n, int L, int ci, int co, const void* W, const float* dY, const void* act,
+                                float* dX, int* err, int sms, cudaStream_t st);
+ggf_status ggf_conv_bwd_weight_tc(int n, int L, int ci, int co, const void* X, const float* dY, float* dW,
+                                  float* db, int* err, int sms, cudaStream_t st);
+
 namespace {
 
 constexpr int C_IN = 8, CH = 64, C_OUT = 6, BLK = 4;
@@ -76,118 +83,6 @@ __global__ void features_kernel(int n, int L, const double* theta, const int* cf
         v[7] = bs ? 1.f : 0.f;
 #pragma unroll
         for (int c = 0; c < C_IN; ++c) Xb[(size_t)c * V + s] = __float2bfloat16(v[c]);
-    }
-}
-
-// Y[b][co][s] = bias[co] + sum_ci sum_taps W[co][ci][ky][kx] X[b][ci][s + tap]
-// grid (n, co / 16), block = min(V, 256) threads looping over pixels.
-template <bool RELU, bool OUT_F32>
-__global__ void conv_fwd(int n, int L, int ci, int co, const bf16* X, const bf16* W, const float* bias, void* Y) {
-    extern __shared__ unsigned char sm[];
-    const int V = L * L;
-    const int b = blockIdx.x, co0 = blockIdx.y * 16;
-    const int nco = min(16, co - co0);
-    bf16* xs = (bf16*)sm;                        // [ci][V]
-    bf16* ws = xs + (size_t)ci * V;              // [16][ci][9]
-    const bf16* Xb = X + (size_t)b * ci * V;
-    for (int e = threadIdx.x; e < ci * V; e += blockDim.x) xs[e] = Xb[e];
-    for (int e = threadIdx.x; e < nco * ci * 9; e += blockDim.x) ws[e] = W[(size_t)co0 * ci * 9 + e];
-    __syncthreads();
-    for (int s = threadIdx.x; s < V; s += blockDim.x) {
-        int x = s % L, y = s / L;
-        int nb[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            int ky = t / 3, kx = t % 3;
-            nb[t] = ((y + ky - 1 + L) % L) * L + (x + kx - 1 + L) % L;
-        }
-        for (int o = 0; o < nco; ++o) {
-            float acc = bias[co0 + o];
-            const bf16* wo = ws + (size_t)o * ci * 9;
-            for (int c = 0; c < ci; ++c) {
-                const bf16* xc = xs + (size_t)c * V;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) acc += __bfloat162float(wo[c * 9 + t]) * __bfloat162float(xc[nb[t]]);
-            }
-            if (RELU) acc = fmaxf(acc, 0.f);
-            size_t oi = ((size_t)b * co + co0 + o) * V + s;
-            if (OUT_F32) ((float*)Y)[oi] = acc;
-            else ((bf16*)Y)[oi] = __float2bfloat16(acc);
-        }
-    }
-}
-
-// dX[b][c][s] = mask(act[b][c][s] > 0) * sum_o sum_taps W[o][c][tap] dY[b][o][s - tap]
-// grid (n, ci / 16)
-__global__ void conv_bwd_data(int n, int L, int ci, int co, const bf16* W, const float* dY, const bf16* act,
-                              float* dX) {
-    extern __shared__ unsigned char sm[];
-    const int V = L * L;
-    const int b = blockIdx.x, c0 = blockIdx.y * 16;
-    const int nc = min(16, ci - c0);
-    float* ds = (float*)sm;                       // [co][V]
-    bf16* ws = (bf16*)(ds + (size_t)co * V);      // [co][16][9]
-    const float* dYb = dY + (size_t)b * co * V;
-    for (int e = threadIdx.x; e < co * V; e += blockDim.x) ds[e] = dYb[e];
-    for (int e = threadIdx.x; e < co * nc * 9; e += blockDim.x) {
-        int o = e / (nc * 9), r = e % (nc * 9), c = r / 9, t = r % 9;
-        ws[e] = W[((size_t)o * ci + c0 + c) * 9 + t];
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < V; s += blockDim.x) {
-        int x = s % L, y = s / L;
-        int nb[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            int ky = t / 3, kx = t % 3;   // output pixel whose tap t read input s
-            nb[t] = ((y - ky + 1 + L) % L) * L + (x - kx + 1 + L) % L;
-        }
-        for (int c = 0; c < nc; ++c) {
-            size_t xi = ((size_t)b * ci + c0 + c) * V + s;
-            if (act && !(__bfloat162float(act[xi]) > 0.f)) { dX[xi] = 0.f; continue; }
-            float acc = 0.f;
-            for (int o = 0; o < co; ++o) {
-                const float* dyo = ds + (size_t)o * V;
-                const bf16* w = ws + ((size_t)o * nc + c) * 9;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) acc += __bfloat162float(w[t]) * dyo[nb[t]];
-            }
-            dX[xi] = acc;
-        }
-    }
-}
-
-// dW[o][c][tap] = sum_b sum_s dY[b][o][s] X[b][c][s + tap]; db[o] = sum dY (c == 0 CTAs)
-// grid (co, ci), 256 threads
-__global__ void conv_bwd_weight(int n, int L, int ci, int co, const bf16* X, const float* dY, float* dW, float* db) {
-    const int V = L * L;
-    const int o = blockIdx.x, c = blockIdx.y;
-    float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int e = threadIdx.x; e < n * V; e += blockDim.x) {
-        int b = e / V, s = e % V;
-        int x = s % L, y = s / L;
-        float g = dY[((size_t)b * co + o) * V + s];
-        const bf16* xb = X + ((size_t)b * ci + c) * V;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            int ky = t / 3, kx = t % 3;
-            acc[t] += g * __bfloat162float(xb[((y + ky - 1 + L) % L) * L + (x + kx - 1 + L) % L]);
-        }
-        acc[9] += g;
-    }
-    __shared__ float red[10][32];
-#pragma unroll
-    for (int t = 0; t < 10; ++t) {
-        float v = acc[t];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if ((threadIdx.x & 31) == 0) red[t][threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 10) {
-        float v = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-        if (threadIdx.x < 9) dW[((size_t)o * ci + c) * 9 + threadIdx.x] = v;
-        else if (c == 0) db[o] = v;
     }
 }
 
@@ -318,6 +213,8 @@ struct ggf_net {
     int* cfg = nullptr;
     int* blocks = nullptr;
     double* scal = nullptr;    // loss accumulator
+    int* d_err = nullptr;      // raised by a tensor-core convolution whose bounded wait ran out
+    int sms = 0;               // streaming multiprocessors of the device
 };
 
 static ggf_status net_fail(ggf_net* n, ggf_status st, const std::string& m) {
@@ -358,41 +255,33 @@ static int px_threads(int L) { return L * L >= 256 ? 256 : ((L * L + 31) / 32) *
 
 // forward pass for n samples whose inputs are already in X[0]; head to net->out
 ggf_status ggf_net_forward(ggf_net* net, int n, cudaStream_t st) {
-    const int L = net->L, V = L * L, thr = px_threads(L);
+    const int L = net->L;
     for (int l = 0; l < NLAYER; ++l) {
         const int ci = layer_ci(l), co = layer_co(l);
         const bf16* W = net->pb + layer_off(l);
         const float* b = net->p + layer_off(l) + co * ci * 9;
-        size_t smem = (size_t)ci * V * sizeof(bf16) + (size_t)16 * ci * 9 * sizeof(bf16);
-        dim3 grid(n, (co + 15) / 16);
-        if (l < NLAYER - 1) {
-            NET_CK(cudaFuncSetAttribute(conv_fwd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            conv_fwd<true, false><<<grid, thr, smem, st>>>(n, L, ci, co, net->X[l], W, b, net->X[l + 1]);
-        } else {
-            NET_CK(cudaFuncSetAttribute(conv_fwd<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            conv_fwd<false, true><<<grid, thr, smem, st>>>(n, L, ci, co, net->X[l], W, b, net->out);
-        }
-        NET_CK(cudaGetLastError());
+        const bool last = l == NLAYER - 1;
+        ggf_status rc = ggf_conv_fwd_tc(n, L, ci, co, !last, net->X[l], W, b, last ? (void*)net->out : (void*)net->X[l + 1],
+                                        last, net->d_err, net->sms, st);
+        if (rc != GGF_OK) return net_fail(net, rc, "tensor-core convolution (forward) failed to launch");
     }
     return GGF_OK;
 }
 
 static ggf_status net_backward(ggf_net* net, int n, cudaStream_t st) {
-    const int L = net->L, V = L * L, thr = px_threads(L);
+    const int L = net->L;
     float* dcur = net->dA;      // gradient w.r.t. the current layer's output
     float* dnext = net->dB;
     for (int l = NLAYER - 1; l >= 0; --l) {
         const int ci = layer_ci(l), co = layer_co(l);
         float* dW = net->g + layer_off(l);
         float* db = dW + co * ci * 9;
-        conv_bwd_weight<<<dim3(co, ci), 256, 0, st>>>(n, L, ci, co, net->X[l], dcur, dW, db);
-        NET_CK(cudaGetLastError());
+        ggf_status rc = ggf_conv_bwd_weight_tc(n, L, ci, co, net->X[l], dcur, dW, db, net->d_err, net->sms, st);
+        if (rc != GGF_OK) return net_fail(net, rc, "tensor-core convolution (weight gradient) failed to launch");
         if (l > 0) {
-            size_t smem = (size_t)co * V * sizeof(float) + (size_t)co * 16 * 9 * sizeof(bf16);
-            NET_CK(cudaFuncSetAttribute(conv_bwd_data, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            conv_bwd_data<<<dim3(n, (ci + 15) / 16), thr, smem, st>>>(n, L, ci, co, net->pb + layer_off(l), dcur,
-                                                                     net->X[l], dnext);
-            NET_CK(cudaGetLastError());
+            rc = ggf_conv_bwd_data_tc(n, L, ci, co, net->pb + layer_off(l), dcur, net->X[l], dnext, net->d_err,
+                                      net->sms, st);
+            if (rc != GGF_OK) return net_fail(net, rc, "tensor-core convolution (input gradient) failed to launch");
             std::swap(dcur, dnext);
         }
     }
@@ -421,6 +310,16 @@ ggf_status ggf_net_head(ggf_net* net, int n, int mode, const double* theta, cons
 
 int ggf_net_L(const ggf_net* net) { return net ? net->L : 0; }
 
+// GGF_ETIMEOUT once a tensor-core convolution's bounded wait ran out
+// (synchronises the device).
+ggf_status ggf_net_check(ggf_net* net) {
+    int h = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&h, net->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return net_fail(net, GGF_ECUDA, "network error word unreadable");
+    if (h) return net_fail(net, GGF_ETIMEOUT, "a tensor-core convolution's bounded wait ran out");
+    return GGF_OK;
+}
+
 extern "C" {
 
 ggf_status ggf_net_create(ggf_net** out, int device, int L, uint64_t seed) {
@@ -439,7 +338,10 @@ ggf_status ggf_net_create(ggf_net** out, int device, int L, uint64_t seed) {
     ck(cudaMalloc(&net->g, NPARAM * sizeof(float)));
     ck(cudaMalloc(&net->m, NPARAM * sizeof(float)));
     ck(cudaMalloc(&net->v, NPARAM * sizeof(float)));
+    ck(cudaMalloc(&net->d_err, sizeof(int)));
     if (s != GGF_OK) { ggf_net_destroy(net); return s; }
+    cudaMemset(net->d_err, 0, sizeof(int));
+    cudaDeviceGetAttribute(&net->sms, cudaDevAttrMultiProcessorCount, device);
     init_params<<<(NPARAM + 255) / 256, 256>>>(net->p, seed);
     to_bf16<<<(NPARAM + 255) / 256, 256>>>(NPARAM, net->p, net->pb);
     cudaMemset(net->m, 0, NPARAM * sizeof(float));
@@ -453,7 +355,7 @@ void ggf_net_destroy(ggf_net* net) {
     if (!net) return;
     cudaSetDevice(net->device);
     net_free_ws(net);
-    void* ps[] = {net->p, net->pb, net->g, net->m, net->v};
+    void* ps[] = {net->p, net->pb, net->g, net->m, net->v, net->d_err};
     for (void* q : ps) if (q) cudaFree(q);
     delete net;
 }
@@ -506,6 +408,7 @@ ggf_status ggf_net_logq(ggf_net* net, int n, const double* theta, const int* blo
     if (t1) cudaFree(t1);
     if (t2) cudaFree(t2);
     if (t3) cudaFree(t3);
+    if (s == GGF_OK) s = ggf_net_check(net);
     return s;
 }
 
@@ -527,6 +430,7 @@ ggf_status ggf_net_loss_grad(ggf_net* net, int n, const double* theta, const int
     }
     cudaFree(t1);
     cudaFree(t2);
+    if (s == GGF_OK) s = ggf_net_check(net);
     return s;
 }
 
@@ -555,7 +459,7 @@ ggf_status ggf_net_train(ggf_net* net, int n_cfg, const double* theta, int batch
         }
     }
     NET_CK(cudaStreamSynchronize(st));
-    return GGF_OK;
+    return ggf_net_check(net);
 }
 
 }  // extern "C"
