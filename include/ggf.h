@@ -107,7 +107,9 @@ ggf_status ggf_init_gaussians(ggf_ctx* ctx, const double* gamma_site, int K,
 ggf_status ggf_get_constants(const ggf_ctx* ctx, int* n_pairs, double* log_c, int* pairs);
 
 /* log N(G) for n_cfg configurations (Sec. 5): assemble M_nm(G) for every
- * pair, factor it (FP64 Parlett-Reid Pfaffian on the GPU) and combine.
+ * pair, take log Pf(M_nm(G)) in FP64 on the GPU (site-by-site elimination
+ * along the lattice; the dense Parlett-Reid Pfaffian for an item whose
+ * pivot falls below 1e-8) and combine.
  *   links  [n_cfg][2V]  int8 (Z2) or double (U(1))
  *   logN   [n_cfg]      log N(G) (unnormalised; -inf if N(G) <= 0)
  *   ell    [n_cfg][P][2] optional (NULL): log Pf(M_nm(G)) as (log|Pf|, arg);
@@ -117,9 +119,11 @@ ggf_status ggf_logweight(ggf_ctx* ctx, int n_cfg, const void* links, double* log
 
 /* Allocation-free log N(G): the same result as ggf_logweight.  The paper has
  * no counterpart for this call; it exists for callers that cannot allocate
- * device memory when they need the weights, such as code running while a
- * stream is captured (where cudaMalloc is not allowed) or hosts whose GPU
- * memory is budgeted once at start-up.  It calls no cudaMalloc/cudaFree or
+ * device memory when they need the weights: hosts whose GPU memory is
+ * budgeted once at start-up, processes that share the GPU under an
+ * allocator that refuses further cudaMalloc calls, and loops that cannot
+ * pay the implicit device synchronisation of cudaFree.  It calls no
+ * cudaMalloc/cudaFree or
  * allocating library routine: all scratch lives in one fixed 32 MiB device
  * array inside the library (held by every GPU that loads the library until
  * the process exits).  The (configuration, pair) factorisations are done in
@@ -127,7 +131,7 @@ ggf_status ggf_logweight(ggf_ctx* ctx, int n_cfg, const void* links, double* log
  * accepted while M_nm is at most 1024 x 1024 (N = 8 n_v L^2 <= 1024); larger
  * lattices return GGF_EINVAL.  links [n_cfg][2V] and logN [n_cfg] are DEVICE
  * pointers.  The first call on a device looks up the array's device address
- * (make that first call before any stream capture).  Every call on a device
+ * (a runtime query that allocates nothing).  Every call on a device
  * shares the array and it keeps the last call's contents: calls whose GPU
  * work overlaps race and must be serialised by the caller.  Work is enqueued
  * on `stream`; the call does not synchronise. */

@@ -1,10 +1,10 @@
 // Allocation-free variant of ggf_logweight.
 //
 // Some callers cannot allocate device memory at the point where they need
-// log N(G): code that runs while a CUDA stream is being captured into a
-// graph, real-time or embedded hosts whose memory is budgeted once at start,
-// or a process that shares the GPU under an allocator that forbids further
-// cudaMalloc calls.  ggf_logweight itself grows a workspace with cudaMalloc,
+// log N(G): real-time or embedded hosts whose memory is budgeted once at
+// start, a process that shares the GPU under an allocator that forbids
+// further cudaMalloc calls, or a loop that cannot pay the implicit device
+// synchronisation of cudaFree.  ggf_logweight itself grows a workspace with cudaMalloc,
 // so this entry point instead works in one fixed scratch array that lives in
 // the library image (a file-scope __device__ array, 32 MiB, held by every GPU
 // that loads the library until the process exits).
