@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 REFRESH_CFG3 = 2048   # accepts per chain between refreshes (about 4 sweeps at the workload's acceptance)
+REFRESH_Z2 = 64       # Z2 cells of the uneven batch (as the 8x8 Z2 workload)
 
 WORKLOADS = {
     # name: (L, group, n_v, K, chains, precision, refresh_every, delay, label)
@@ -102,9 +103,13 @@ def run_cfg5(args):
               f"tune {time.time() - t_cell:.1f}s {tim}", file=sys.stderr, flush=True)
         tuned.append({"L": p.L, "group": "Z2" if p.group == 0 else "U1", "K": p.K, "chains": ch, "delay": d,
                       "ms_per_sweep": {str(a): round(b, 2) for a, b in tim.items()}})
+        # Z2 flips are large moves: their FP32 tracked log-weight drifts ~1.5e-6
+        # per accept, so Z2 cells refresh every REFRESH_Z2 accepts
+        refresh = REFRESH_Z2 if p.group == gi.Z2 else REFRESH_CFG3
+        tuned[-1]["refresh_every_accepts"] = refresh
         c = GGF(0)
         c.init_problem(p)
-        c.chains_init(links, precision=1, refresh_every=REFRESH_CFG3, seed=BASE_SEED + k, delay=d, graph=1)
+        c.chains_init(links, precision=1, refresh_every=refresh, seed=BASE_SEED + k, delay=d, graph=1)
         ctxs.append(c)
     t_setup = time.time() - t0
     obs = [[] for _ in ctxs]
@@ -124,10 +129,13 @@ def run_cfg5(args):
     # sequence): what the single grouped launch saves over separate launches
     torch.cuda.synchronize()
     t_sep = time.time()
-    for c in ctxs:
-        c.sample(args.steps)
+    last = [c.sample(args.steps)[-1] for c in ctxs]
     torch.cuda.synchronize()
     t_sep = time.time() - t_sep
+    # tracked log N at the last sweep against a fresh FP64 evaluation
+    for k, (c, o) in enumerate(zip(ctxs, last)):
+        fresh = c.logweight(np.ascontiguousarray(c.chains_links()))
+        tuned[k]["dlogp_vs_fp64_recompute"] = float(np.nanmax(np.abs(fresh - o[:, 1])))
     ess, total_chains, launches = 0.0, 0, 0
     for k, (c, o) in enumerate(zip(ctxs, outs)):
         ser = np.concatenate([obs[k][0], o], axis=0).transpose(1, 0, 2)      # chains, sweeps, 3
@@ -144,7 +152,8 @@ def run_cfg5(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"uneven batch: {len(cells)} problems (L in 8,12,16; Z2 and U(1); K in 1,2,4), "
                                    f"{total_chains} chains, one parent CUDA graph launch per sweep, autotuned delay, "
-                                   f"FP32 updates with the FP64 refresh every {REFRESH_CFG3} accepts",
+                                   f"FP32 updates with the FP64 refresh every {REFRESH_CFG3} accepts (U(1) cells) or "
+                                   f"{REFRESH_Z2} accepts (Z2 cells)",
                        "cells": tuned, "setup_s": t_setup,
                        "separate_launches_s": t_sep, "grouped_s": ms * 1e-3,
                        "separate_note": "the timed sweeps repeated cell by cell, one graph launch per cell"},

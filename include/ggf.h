@@ -473,8 +473,10 @@ ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launch
  * FP32 data on tcgen05 TF32 tensor cores, three-product split): runs it on
  * one N x N (cplx = 0) or complex N x N (cplx = 1) matrix with seeded data
  * and a rank-`rank` panel (rank a multiple of 4, <= 512) and reports the
- * largest error relative to the largest entry of an FP64 reference.  Needs
- * only a context (allocates its own buffers).  Not part of the method. */
+ * largest error relative to the largest entry of an FP64 reference, over both
+ * flush kernels: the per-tile split (Newton step of the refresh) and the
+ * pre-split one the sweeps use.  Needs only a context (allocates its own
+ * buffers).  Not part of the method. */
 ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank, double* max_rel_err);
 
 /* ---- Learned block proposal ------------------------------------------------

@@ -27,6 +27,7 @@ ggf_status ggf_prepare_sampler(ggf_ctx* ctx);
 ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx);
 ggf_status ggf_prepare_batch(ggf_ctx* ctx);
 ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64);
+size_t ggf_flush_ps_chain_bytes(ggf_ctx* ctx, int KRM);
 ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st);
 ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st, bool field = false);
@@ -71,7 +72,7 @@ void ggf_free_chains(ggf_ctx* ctx) {
     if (c.d_sweep) cudaFree(c.d_sweep);
     if (c.d_obs_stage) cudaFree(c.d_obs_stage);
     void* ptrs[] = {c.links, c.Wr, c.Wc, c.ell, c.zbuf, c.ybuf, c.accept, c.since_refresh,
-                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend, c.Sm, c.flags};
+                    c.sweep_acc, c.counters, c.drift, c.refresh_list, c.Pr, c.Pc, c.pend, c.Sm, c.flags, c.ps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ggf_chain_opts o = c.opts;
@@ -719,6 +720,16 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
                                    ctx->Kc * NN * 2 * rsz, cudaMemcpyDeviceToDevice, st));
         GGF_CK(cudaMemcpyAsync(ch.ell + (size_t)c * ctx->P, ch.ell + (size_t)r0 * ctx->P, ctx->P * sizeof(cxd),
                                cudaMemcpyDeviceToDevice, st));
+    }
+    // pre-split scratch of the tensor-core flush, after the set-up's own
+    // workspace: waves of up to 2 GiB and a quarter of the free memory
+    if (!fp64 && ch.kmax > 1 && ctx->use_tc) {
+        const size_t per = ggf_flush_ps_chain_bytes(ctx, ch.kmax * g.r);
+        size_t free_b = 0, total_b = 0;
+        GGF_CK(cudaMemGetInfo(&free_b, &total_b));
+        const size_t budget = std::min<size_t>((size_t)2 << 30, free_b / 4);
+        ch.ps_wave = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_chains, budget / std::max<size_t>(per, 1)));
+        GGF_CK(cudaMalloc(&ch.ps, (size_t)ch.ps_wave * per));
     }
     GGF_CK(cudaMemsetAsync(ch.counters, 0, 6 * sizeof(unsigned long long), st));
     GGF_CK(cudaStreamSynchronize(st));

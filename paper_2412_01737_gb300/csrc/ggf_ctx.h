@@ -58,6 +58,10 @@ struct Chains {
     void* Sm = nullptr;
     int kmax = 1;
     int steps_since_flush = 0;
+    // pre-split operand scratch of the tensor-core flush (FP32 delayed
+    // modes): the flush runs in waves of ps_wave chains
+    unsigned char* ps = nullptr;
+    int ps_wave = 0;
     unsigned long long block_moves = 0;      // learned-proposal moves made (Philox counter)
     // one sweep captured as a CUDA graph (opts.graph != 0)
     unsigned long long* d_sweep = nullptr;   // device copy of the sweep counter

@@ -446,7 +446,7 @@ __global__ void mark_refresh(int n_chains, int R, const int* since, int* list) {
 }  // namespace
 
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
-ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st);
+ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st, int* launches);
 
 size_t ggf_ratio_smem(int P, int r) {
     return (size_t)(2 * P * r * r + NWARP * 4 * r * r + P + NWARP * r) * sizeof(cxd);
@@ -577,8 +577,10 @@ ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st) {
     dim3 gr(tiles * tiles, ctx->K, ch.n), gc(tiles * tiles, ctx->Kc, ch.n);
 #define GGF_FL(T, R_, grid, fam, Wp, Pp) \
     flush_kernel<T, R_><<<grid, 256, 0, st>>>(N, fam, (T*)(Wp), (const typename Sc<T>::R*)(Pp), ch.pend, ch.kmax, tiles)
+    int nl = 1 + (ctx->Kc ? 1 : 0);
     if (!fp64 && ctx->use_tc) {
-        GGF_TRY(ggf_flush_tc(ctx, st));
+        nl = 0;
+        GGF_TRY(ggf_flush_tc(ctx, st, &nl));
     } else if (g.r == 4) {
         if (fp64) { GGF_FL(double, 4, gr, ctx->K, ch.Wr, ch.Pr); if (ctx->Kc) GGF_FL(cxd, 4, gc, ctx->Kc, ch.Wc, ch.Pc); }
         else { GGF_FL(float, 4, gr, ctx->K, ch.Wr, ch.Pr); if (ctx->Kc) GGF_FL(cxf, 4, gc, ctx->Kc, ch.Wc, ch.Pc); }
@@ -589,7 +591,7 @@ ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st) {
 #undef GGF_FL
     ctx->prof_pair(GGF_KT_FLUSH, ev0, ctx->prof_mark(st));
     reset_pend<<<(ch.n + 127) / 128, 128, 0, st>>>(ch.n, ch.pend);
-    ctx->launches += 2 + (ctx->Kc ? 1 : 0);
+    ctx->launches += nl + 1;
     GGF_CK(cudaGetLastError());
     ch.steps_since_flush = 0;
     return GGF_OK;

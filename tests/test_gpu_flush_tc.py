@@ -1,5 +1,9 @@
 """The tcgen05 tensor-core flush of the delayed updates (TF32 three-product
-split) reproduces W - U V^T at FP32 accuracy against an FP64 reference.
+split) reproduces W - U V^T at FP32 accuracy against an FP64 reference.  The
+self-test runs both flush kernels on the same input and reports the larger
+error: the one whose producer warps split the operands per tile (used by the
+Newton step of the refresh) and the sweep's one, which splits them once per
+chain wave and fills its stages with bulk copies.
 
 The tensor core accumulates the rank-K sum in FP32 in TMEM, so the error
 grows with K: the bound is 2.5e-6 of the largest entry up to K = 128 and

@@ -71,3 +71,66 @@ def test_panel_reads_are_coalesced(lay, NR):
         byte = pan[w0:w0 + 32].astype(np.int64) * 4
         assert len({int(b) // 128 for b in byte}) == 4
         assert len(set(byte.tolist())) == 32
+
+
+# ---- pre-split operand blocks (flush in chain waves) -------------------------
+
+def _cm(row, k):
+    """Core-matrix byte offset of (row, k) in a KC = 8 wide plane: 8-row x
+    16-byte core matrices, 128 bytes apart along k, 256 bytes between 8-row
+    groups (the layout the MMA descriptors of the flush read)."""
+    return (row // 8) * 256 + (k // 4) * 128 + (row % 8) * 16 + (k % 4) * 4
+
+
+@pytest.mark.parametrize("cplx,N,KRM,pairs,n", [(0, 300, 12, 2, 3), (1, 300, 12, 3, 2), (0, 512, 16, 1, 1),
+                                                (1, 128, 8, 1, 2)])
+def test_presplit_blocks_tile_the_scratch(lay, cplx, N, KRM, pairs, n):
+    """Every 16-byte hi/lo piece the split pass writes has its own place, all
+    inside the scratch, and together they fill it: the two bulk copies of a
+    stage then read only bytes the split pass wrote."""
+    NP = (N + 255) // 256 * 256
+    KP = (KRM + 7) // 8 * 8
+    cap = n * pairs * 2 * (2 if cplx else 1) * NP * (KP // 4)
+    rec = np.zeros((cap, 10), dtype=np.uint64)
+    m = lay.emu_ps_layout(ctypes.c_int(cplx), ctypes.c_int(N), ctypes.c_int(KRM), ctypes.c_int(pairs),
+                          ctypes.c_int(n), rec.ctypes.data_as(ctypes.c_void_p), ctypes.c_longlong(cap))
+    assert m == cap
+    lay.emu_ps_bytes.restype = ctypes.c_ulonglong
+    total = lay.emu_ps_bytes(ctypes.c_int(cplx), ctypes.c_int(N), ctypes.c_int(KRM), ctypes.c_int(pairs),
+                             ctypes.c_int(n))
+    none = np.uint64(2**64 - 1)
+    offs = np.concatenate([rec[:, 6], rec[:, 7], rec[:, 8][rec[:, 8] != none], rec[:, 9][rec[:, 9] != none]])
+    assert np.all(offs % 16 == 0)
+    assert len(np.unique(offs)) == len(offs)
+    assert offs.max() + 16 <= total and len(offs) * 16 == total
+
+
+@pytest.mark.parametrize("cplx", [0, 1])
+def test_presplit_blocks_hold_the_stage_layout(lay, cplx):
+    """Inside each block the pieces sit where the per-tile producers of the
+    other flush kernel put them in a stage: V (A operand) hi/lo planes of 128
+    rows, then the U (B operand) hi and lo parts -- 256 rows for real pairs,
+    the composite [-U_i ; U_r ; U_i] for complex pairs."""
+    N, KRM, pairs, n = 300, 12, 2, 2
+    NP = 512
+    KP = 16
+    cap = n * pairs * 2 * (2 if cplx else 1) * NP * (KP // 4)
+    rec = np.zeros((cap, 10), dtype=np.uint64)
+    lay.emu_ps_layout(ctypes.c_int(cplx), ctypes.c_int(N), ctypes.c_int(KRM), ctypes.c_int(pairs), ctypes.c_int(n),
+                      rec.ctypes.data_as(ctypes.c_void_p), ctypes.c_longlong(cap))
+    lay.emu_ps_off.restype = ctypes.c_ulonglong
+    plane = 128 * 8 * 4
+    for c, p, uv, pl, row, k, hi, lo, hi2, lo2 in rec.astype(object):
+        ur = 128 if (uv == 0 or cplx) else 256
+        blk = lay.emu_ps_off(ctypes.c_int(cplx), ctypes.c_int(N), ctypes.c_int(KRM), ctypes.c_int(pairs),
+                             ctypes.c_int(n), ctypes.c_int(uv), ctypes.c_int(c), ctypes.c_int(p),
+                             ctypes.c_int(row // ur), ctypes.c_int(k // 8))
+        r, kk = row % ur, k % 8
+        if uv == 0:
+            assert hi - blk == 2 * pl * plane + _cm(r, kk) and lo == hi + plane
+        elif not cplx:
+            assert hi - blk == _cm(r, kk) and lo == hi + 2 * plane
+        else:
+            assert hi - blk == _cm((128 if pl == 0 else 256) + r, kk) and lo == hi + 3 * plane
+            if pl == 1:
+                assert hi2 - blk == _cm(r, kk) and lo2 == hi2 + 3 * plane

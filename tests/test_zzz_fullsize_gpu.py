@@ -56,3 +56,41 @@ def test_u1_16x16_fermion_properties_fp32():
     assert n.real.min() >= -1e-4 and n.real.max() <= 1 + 1e-4
     assert np.abs(n @ p.q_phys).max() <= 1e-3
     ctx.close()
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_z2_16x16_batched_fp32(K):
+    """16x16 Z2, n_v = 1 (M 2048 x 2048), the largest Z2 cell of the uneven
+    batch: FP32 chains with batches of 16 links, from the cold start.
+
+    Without a refresh, every accepted flip adds the FP32 error of the cached
+    inverse to the tracked log-weight; a Z2 flip is a large change (a sign, not
+    a small angle), so over three sweeps (~1.4e3 accepts per chain) the
+    tracked value drifts by ~1.5e-6 per accept.  The test bounds that at
+    3e-6 per accept.  With a refresh every 32 accepts each chain is refreshed
+    at the end of every sweep (the fresh FP64 log-weight resets the tracked
+    one, the Newton step refines the inverse), so the drift, both at the
+    refreshes and at the last sweep, is that of one sweep's accepts only:
+    the refresh does not let the error accumulate."""
+    p = gi.make_problem(16, gi.Z2, 1, K, seed=20241202 + K)
+    n = 8
+    for refresh in (1 << 30, 32):
+        ctx = ctx_for(p)
+        ctx.chains_init(gi.cold_links(p, n), precision=1, refresh_every=refresh, seed=77 + K, delay=16)
+        obs = ctx.sample(3)
+        fin = ctx.chains_links()
+        st = ctx.chains_stats()
+        assert np.isfinite(obs).all()
+        assert np.abs(obs[-1, :, 0] - plaquette_mean(gi.Z2, 16, fin)).max() <= 1e-12
+        assert 0 < st.accepts < st.proposals
+        fresh = ctx.logweight(np.ascontiguousarray(fin))
+        err = np.abs(obs[-1, :, 1] - fresh).max()
+        per_chain = st.accepts / n
+        if refresh > st.accepts:
+            assert st.refreshes == 0
+            assert err <= 3e-6 * per_chain, (err, per_chain)
+        else:
+            assert st.refreshes == 3 * n
+            assert err <= 1.5 * 3e-6 * per_chain / 3, (err, per_chain)
+            assert st.max_drift <= 1.5 * 3e-6 * per_chain / 3, (st.max_drift, per_chain)
+        ctx.close()
