@@ -561,6 +561,9 @@ def run_ggf(args):
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
     roof["traffic"] = None
     roof["share"] = {k: round(v / max(prof_ms, 1e-9), 4) for k, v in shares.items()}
+    # time between the graph's kernel groups (launch gaps, host work between
+    # sweeps): what a single persistent kernel could at most remove
+    roof["kernel_time_fraction"] = round(sum(shares.values()) / max(prof_ms, 1e-9), 4)
     roof["profiled_pass"] = {"sweeps": args.prof_sweeps, "ms": prof_ms,
                              "refreshes": int(sp1.refreshes - sp0.refreshes),
                              "note": "separate untimed pass of the same graph with timing-event nodes"}
@@ -609,6 +612,7 @@ def run_ggf(args):
                        "refresh_max_resid": st2.max_resid, "refresh_dense_fallbacks": int(st2.dense_refreshes),
                        "refresh_newton_steps": int(st2.refine_steps),
                        "pfaffian_dense_fallbacks": int(st2.dense_pfaffians),
+                       "flush_wave_chains": int(st2.flush_wave),
                        "init_s": t_setup},
             "dlogp_vs_fp64_recompute": dlogp, "max_drift_at_refresh": st2.max_drift,
             "roofline": roof, "clocks": ck,

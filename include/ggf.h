@@ -408,6 +408,8 @@ typedef struct {
     uint64_t refine_steps;     /* Newton steps taken by refreshes */
     uint64_t dense_pfaffians;  /* log-Pfaffians that fell back from the
                                   site-by-site to the dense elimination */
+    uint64_t flush_wave;       /* FP32 delayed modes: chains per wave of the
+                                  tensor-core flush (0 otherwise) */
 } ggf_chain_stats;
 
 ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out);

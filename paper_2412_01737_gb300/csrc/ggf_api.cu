@@ -1348,6 +1348,7 @@ ggf_status ggf_chains_stats(ggf_ctx* ctx, ggf_chain_stats* out) {
     out->dense_refreshes = ctx->dense_refreshes;
     out->refine_steps = ctx->refine_steps;
     out->dense_pfaffians = ctx->dense_pfaffians;
+    out->flush_wave = ctx->ch.ps ? (uint64_t)ctx->ch.ps_wave : 0;
     if (h[3]) return ggf_fail(ctx, GGF_ESINGULAR, "a refresh met a singular M(G)");
     return GGF_OK;
 }

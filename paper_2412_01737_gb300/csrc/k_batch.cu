@@ -27,6 +27,11 @@
 // pass over W.
 #include "ggf_sweep.cuh"
 
+// 1: the X product of FP32 batches runs on the tensor cores (k_apply_tc.cu)
+#ifndef GGF_APPLY_TC
+#define GGF_APPLY_TC 1
+#endif
+
 namespace {
 
 // ---- gather -------------------------------------------------------------------
@@ -419,6 +424,7 @@ int gather_rows(int kr, size_t tb) {
 }  // namespace
 
 ggf_status ggf_flush(ggf_ctx* ctx, cudaStream_t st);
+ggf_status ggf_apply_tc(ggf_ctx* ctx, bool cplx, int fam_pairs, int kr, float* Pan, const float* Sm, cudaStream_t st);
 
 // Shared-memory caps of the batch kernels (once per device, like the other
 // sampler kernels), and the largest batch that fits.
@@ -542,7 +548,11 @@ ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st) {
         const size_t sr = apply_smem(rpt_r, kr, rsz), sc = apply_smem(rpt_c, kr, 2 * rsz);
 #define GGF_APPLY(T, RPT, grid, smem, fam, Pp, Sp) \
     batch_apply<T, RPT><<<grid, 256, smem, st>>>(N, fam, KRM, kr, (typename Sc<T>::R*)(Pp), (const T*)(Sp), ch.pend)
-        if (fp64) {
+        if (GGF_APPLY_TC && !fp64 && ctx->use_tc && kr <= 256) {
+            // FP32 chains: the X product on the tensor cores (TF32 split)
+            GGF_TRY(ggf_apply_tc(ctx, false, ctx->K, kr, (float*)ch.Pr, (const float*)Sr, st));
+            GGF_TRY(ggf_apply_tc(ctx, true, ctx->Kc, kr, (float*)ch.Pc, (const float*)Sc_, st));
+        } else if (fp64) {
             if (rpt_r == 4) GGF_APPLY(double, 4, gr, sr, ctx->K, ch.Pr, Sr); else GGF_APPLY(double, 2, gr, sr, ctx->K, ch.Pr, Sr);
             if (ctx->Kc) {
                 if (rpt_c == 4) GGF_APPLY(cxd, 4, gc, sc, ctx->Kc, ch.Pc, Sc_); else GGF_APPLY(cxd, 2, gc, sc, ctx->Kc, ch.Pc, Sc_);

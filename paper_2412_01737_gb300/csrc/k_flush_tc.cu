@@ -59,6 +59,14 @@ namespace {
 #ifndef GGF_FLUSH_EPI_PP
 #define GGF_FLUSH_EPI_PP 0
 #endif
+// 1: the lo part of the operand split is rounded to TF32 (else the MMA drops
+// its low 13 bits)
+#ifndef GGF_SPLIT_LO_RNA
+#define GGF_SPLIT_LO_RNA 0
+#endif
+#ifndef GGF_FLUSH_PS_STAGES
+#define GGF_FLUSH_PS_STAGES 5
+#endif
 constexpr int STAGES = GGF_FLUSH_STAGES;      // split (MMA operand) stages
 constexpr int PD = GGF_FLUSH_PD;              // stages of loads in flight ahead
 constexpr int RAWS = PD + 1;                  // raw cp.async slots
@@ -392,8 +400,16 @@ __device__ __forceinline__ void epilogue_tiles(int warp, int ew, int lane, long 
         } else {
             // rows i0 + half*RG + 16 cb + k  <->  re column half*RG + 16 cb + k, im column + 128
             // (RG = 128 / EPI_PARTS)
-#pragma unroll 1
-            for (int cb = 0; cb < 128 / EPI_PARTS / 16; ++cb) {
+            constexpr int NCBC = 128 / EPI_PARTS / 16;
+            auto load_wc = [&](int cb, float2* w) {
+                const int ib = t.i0 + half * (128 / EPI_PARTS) + cb * 16;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int i = ib + k;
+                    w[k] = (i < N && j < N) ? *(const float2*)(Wp + (size_t)i * rowW + 2 * j) : make_float2(0.f, 0.f);
+                }
+            };
+            auto drain_c = [&](int cb, const float2* w) {
                 uint32_t v[16], vi[16];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -409,20 +425,33 @@ __device__ __forceinline__ void epilogue_tiles(int warp, int ew, int lane, long 
                       "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]),
                       "=r"(vi[13]), "=r"(vi[14]), "=r"(vi[15])
                     : "r"(tl + 128 + half * (128 / EPI_PARTS) + cb * 16));
-                const int ib = t.i0 + half * (128 / EPI_PARTS) + cb * 16;
-                float2 w[16];
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const int i = ib + k;
-                    w[k] = (i < N && j < N) ? *(const float2*)(Wp + (size_t)i * rowW + 2 * j) : make_float2(0.f, 0.f);
-                }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int ib = t.i0 + half * (128 / EPI_PARTS) + cb * 16;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int i = ib + k;
                     if (i < N && j < N)
                         *(float2*)(Wp + (size_t)i * rowW + 2 * j) =
                             make_float2(w[k].x - __uint_as_float(v[k]), w[k].y - __uint_as_float(vi[k]));
+                }
+            };
+            if (GGF_FLUSH_EPI_PP) {
+                static_assert(NCBC % 2 == 0, "ping-pong epilogue drains chunk pairs");
+                float2 wa[16], wb[16];
+                load_wc(0, wa);
+#pragma unroll 1
+                for (int cb = 0; cb < NCBC; cb += 2) {
+                    load_wc(cb + 1, wb);
+                    drain_c(cb, wa);
+                    if (cb + 2 < NCBC) load_wc(cb + 2, wa);
+                    drain_c(cb + 1, wb);
+                }
+            } else {
+#pragma unroll 1
+                for (int cb = 0; cb < NCBC; ++cb) {
+                    float2 w[16];
+                    load_wc(cb, w);
+                    drain_c(cb, w);
                 }
             }
         }
@@ -601,7 +630,7 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
 // operands once per tile.  The MMA issuer and the epilogue are those of
 // flush_tc_kernel; with the producer warps gone, the CTA is 8 epilogue warps
 // (0-7), one copy warp (8) and one MMA warp (9), and holds PS_STAGES stages.
-constexpr int PS_STAGES = 5;
+constexpr int PS_STAGES = GGF_FLUSH_PS_STAGES;
 constexpr int PS_COPY_WARP = NEPI, PS_MMA_WARP = NEPI + 1;
 constexpr int PS_THREADS = (NEPI + 2) * 32;
 __host__ __device__ constexpr int ps_smem_bytes() { return PS_STAGES * stage_bytes(true) + 1024; }
@@ -656,8 +685,10 @@ __global__ void __launch_bounds__(256) ps_split_kernel(int N, int fam_pairs, int
         };
         auto put = [&](size_t hi, size_t lo, float4 x, float sgn) {
             const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+            if (GGF_SPLIT_LO_RNA) l = make_float4(tf32_hi(l.x), tf32_hi(l.y), tf32_hi(l.z), tf32_hi(l.w));
             *(float4*)(ps + hi) = make_float4(sgn * h.x, sgn * h.y, sgn * h.z, sgn * h.w);
-            *(float4*)(ps + lo) = make_float4(sgn * (x.x - h.x), sgn * (x.y - h.y), sgn * (x.z - h.z), sgn * (x.w - h.w));
+            *(float4*)(ps + lo) = make_float4(sgn * l.x, sgn * l.y, sgn * l.z, sgn * l.w);
         };
         const float* U0 = Pan + blk;
         const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;

@@ -47,7 +47,7 @@ class ChainStats(ctypes.Structure):
                 ("block_proposals", ctypes.c_uint64), ("block_accepts", ctypes.c_uint64),
                 ("n_chains", ctypes.c_int), ("n_pairs", ctypes.c_int), ("max_resid", ctypes.c_double),
                 ("dense_refreshes", ctypes.c_uint64), ("refine_steps", ctypes.c_uint64),
-                ("dense_pfaffians", ctypes.c_uint64)]
+                ("dense_pfaffians", ctypes.c_uint64), ("flush_wave", ctypes.c_uint64)]
 
 
 EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "ggf_init_group",

@@ -183,3 +183,23 @@ def test_z2_2x2_chain_of_ten_thousand_sweeps():
     dof = int(mask.sum()) - 1
     chi2 = n_eff * np.sum((obs_p[mask] - exp_p[mask]) ** 2 / exp_p[mask])
     assert chi2 < dof + 6 * np.sqrt(2 * dof) + 10
+
+
+@pytest.mark.parametrize("delay", [16, 32])
+def test_fp32_batched_inverse_residual(delay):
+    """FP32 chains with batched updates (the X product on the tensor cores --
+    one 128-column output block at 16 links of r = 8, two at 32 -- and the
+    flush from pre-split operands): after two sweeps every cached inverse
+    still satisfies |I - M W| <= 1e-4 entrywise, M from the chain's links."""
+    from paper_2412_01737_gb300 import FP32
+    p = gi.make_problem(8, gi.U1, 2, 3, bond_scale=0.05)
+    ctx = ctx_for(p)
+    n = 3
+    ctx.chains_init(gi.cold_links(p, n), precision=FP32, refresh_every=1 << 30, seed=11, delay=delay)
+    ctx.sample(2)
+    st = ctx.chains_stats()
+    assert st.accepts > 0.9 * st.proposals
+    for c in range(n):
+        for pr in range(p.K * (p.K + 1) // 2):
+            assert ctx.chains_refine(c, pr, apply=False) <= 1e-4, (c, pr)
+    ctx.close()
