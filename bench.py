@@ -63,7 +63,8 @@ BLOCK_MOVES_PER_STEP = 16
 # Uneven batch: every (lattice, group, K) cell below is one problem; all cells
 # sweep together, one parent CUDA graph launch per sweep.  Chains are spread
 # so that every cell holds about the same inverse memory (at least one chain).
-CFG5_CELLS = [(L, grp, K) for L in (8, 12, 16) for grp in (0, 1) for K in (1, 2, 4)]
+CFG5_CELLS = [(L, grp, K) for L in (8, 12, 16, 24) for grp in (0, 1) for K in (1, 2, 4, 8)]
+CFG5_TUNE_MAX = 2 * 2**30      # cells whose chains hold more inverse memory run at delay 16 untuned
 CFG5_CHAINS = 4096
 CFG5_BUDGET = 120 * 2**30
 
@@ -94,23 +95,31 @@ def run_cfg5(args):
     from paper_2412_01737_gb300.ggf import sample_group
     from paper_2412_01737_gb300.tune import tune_delay
     cells = cfg5_cells()
-    ctxs, tuned, t0 = [], [], time.time()
-    for k, (p, ch, mem) in enumerate(cells):
+    ctxs, tuned, t0 = [None] * len(cells), [None] * len(cells), time.time()
+    # the largest cells are set up first, while the most memory is free
+    order = sorted(range(len(cells)), key=lambda k: -cells[k][1] * cells[k][2])
+    for k in order:
+        p, ch, mem = cells[k]
         links = gi.cold_links(p, ch)
         t_cell = time.time()
-        d, tim = tune_delay(p, links, 1, candidates=(8, 16), use_cache=False, seed=BASE_SEED + k)
+        if mem <= CFG5_TUNE_MAX:
+            d, tim = tune_delay(p, links, 1, candidates=(8, 16), use_cache=False, seed=BASE_SEED + k)
+        else:
+            d, tim = 16, {}       # the tuner would set these chains up once per candidate
         print(f"cfg5 cell {k}: L={p.L} group={p.group} K={p.K} chains={ch} delay={d} "
               f"tune {time.time() - t_cell:.1f}s {tim}", file=sys.stderr, flush=True)
-        tuned.append({"L": p.L, "group": "Z2" if p.group == 0 else "U1", "K": p.K, "chains": ch, "delay": d,
-                      "ms_per_sweep": {str(a): round(b, 2) for a, b in tim.items()}})
+        tuned[k] = {"L": p.L, "group": "Z2" if p.group == 0 else "U1", "K": p.K, "chains": ch, "delay": d,
+                    "tuned": bool(tim), "ms_per_sweep": {str(a): round(b, 2) for a, b in tim.items()}}
         # Z2 flips are large moves: their FP32 tracked log-weight drifts ~1.5e-6
         # per accept, so Z2 cells refresh every REFRESH_Z2 accepts
         refresh = REFRESH_Z2 if p.group == gi.Z2 else REFRESH_CFG3
-        tuned[-1]["refresh_every_accepts"] = refresh
+        tuned[k]["refresh_every_accepts"] = refresh
+        t_init = time.time()
         c = GGF(0)
         c.init_problem(p)
         c.chains_init(links, precision=1, refresh_every=refresh, seed=BASE_SEED + k, delay=d, graph=1)
-        ctxs.append(c)
+        tuned[k]["init_s"] = round(time.time() - t_init, 2)
+        ctxs[k] = c
     t_setup = time.time() - t0
     obs = [[] for _ in ctxs]
     for o, s in zip(sample_group(ctxs, args.warmup), obs):
@@ -150,7 +159,7 @@ def run_cfg5(args):
     line = {"metric": "effective samples/sec/GPU", "value": ess / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"uneven batch: {len(cells)} problems (L in 8,12,16; Z2 and U(1); K in 1,2,4), "
+            "config": {"workload": f"uneven batch: {len(cells)} problems (L in 8,12,16,24; Z2 and U(1); K in 1,2,4,8), "
                                    f"{total_chains} chains, one parent CUDA graph launch per sweep, autotuned delay, "
                                    f"FP32 updates with the FP64 refresh every {REFRESH_CFG3} accepts (U(1) cells) or "
                                    f"{REFRESH_Z2} accepts (Z2 cells)",

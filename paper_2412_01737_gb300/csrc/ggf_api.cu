@@ -721,6 +721,14 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
         GGF_CK(cudaMemcpyAsync(ch.ell + (size_t)c * ctx->P, ch.ell + (size_t)r0 * ctx->P, ctx->P * sizeof(cxd),
                                cudaMemcpyDeviceToDevice, st));
     }
+    // the set-up's dense factorisation workspace can be large (up to 8 GiB);
+    // a refresh grows its own again when it needs one
+    if (ctx->work_bytes > ((size_t)1 << 30)) {
+        GGF_CK(cudaStreamSynchronize(st));
+        cudaFree(ctx->work);
+        ctx->work = nullptr;
+        ctx->work_bytes = 0;
+    }
     // pre-split scratch of the tensor-core flush, after the set-up's own
     // workspace: waves of up to 2 GiB and a quarter of the free memory
     if (!fp64 && ch.kmax > 1 && ctx->use_tc) {

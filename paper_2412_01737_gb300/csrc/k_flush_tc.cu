@@ -656,54 +656,71 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 // Only the rank chunks below the chain's pending rank are written (the flush
 // reads no others); inside them, rows past N and columns past the rank are 0.
 template <bool CPLX>
-__global__ void __launch_bounds__(256) ps_split_kernel(int N, int fam_pairs, int c0, int n, const float* Pan,
-                                                       const int* pend, int R, int KRM, unsigned char* ps) {
+__global__ void __launch_bounds__(256) ps_split_kernel(int N, int fam_pairs, int c0, int n,
+                                                       const float* __restrict__ Pan, const int* __restrict__ pend,
+                                                       int R, int KRM, unsigned char* __restrict__ ps) {
+    constexpr int PL = CPLX ? 4 : 2;              // planes read per item: V (re, im), U (re, im)
+    constexpr int UN = 2;                         // items per thread and loop trip, loads issued first
     const size_t NK = panel_plane(N, KRM);
     const int NP = panel_rows(N);
     const int nq = panel_cols(KRM) / 4;
     const long long total = (long long)n * fam_pairs * NP * nq;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(e % nq);
-        long long rest = e / nq;
-        const int row = (int)(rest % NP);
-        rest /= NP;
-        const int p = (int)(rest % fam_pairs);
-        const int cw = (int)(rest / fam_pairs);
-        const int K = pend[c0 + cw] * R;
-        const int k = 4 * q;
-        if (k >= ((K + KC - 1) / KC) * KC) continue;
-        const size_t blk = ((size_t)(c0 + cw) * fam_pairs + p) * (CPLX ? 4 : 2) * NK;
-        auto load = [&](const float* plane) {
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row < N) x = *(const float4*)(plane + pidx(row, k, NP));
-            if (k + 0 >= K) x.x = 0.f;
-            if (k + 1 >= K) x.y = 0.f;
-            if (k + 2 >= K) x.z = 0.f;
-            if (k + 3 >= K) x.w = 0.f;
-            return x;
-        };
-        auto put = [&](size_t hi, size_t lo, float4 x, float sgn) {
-            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-            float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += UN * stride) {
+        float4 x[UN][PL];
+        int row[UN], k[UN], p[UN], cw[UN];
+        bool live[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const long long e = e0 + u * stride;
+            live[u] = e < total;
+            const long long ee = live[u] ? e : 0;
+            const int q = (int)(ee % nq);
+            long long rest = ee / nq;
+            row[u] = (int)(rest % NP);
+            rest /= NP;
+            p[u] = (int)(rest % fam_pairs);
+            cw[u] = (int)(rest / fam_pairs);
+            k[u] = 4 * q;
+            const int K = pend[c0 + cw[u]] * R;
+            live[u] = live[u] && k[u] < ((K + KC - 1) / KC) * KC;
+            const size_t blk = ((size_t)(c0 + cw[u]) * fam_pairs + p[u]) * PL * NK;
+            // planes in panel order: U re, (U im), V re, (V im)
+#pragma unroll
+            for (int pl = 0; pl < PL; ++pl) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (live[u] && row[u] < N) v = *(const float4*)(Pan + blk + pl * NK + pidx(row[u], k[u], NP));
+                if (k[u] + 0 >= K) v.x = 0.f;
+                if (k[u] + 1 >= K) v.y = 0.f;
+                if (k[u] + 2 >= K) v.z = 0.f;
+                if (k[u] + 3 >= K) v.w = 0.f;
+                x[u][pl] = v;
+            }
+        }
+        auto put = [&](size_t hi, size_t lo, float4 v, float sgn) {
+            const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+            float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
             if (GGF_SPLIT_LO_RNA) l = make_float4(tf32_hi(l.x), tf32_hi(l.y), tf32_hi(l.z), tf32_hi(l.w));
             *(float4*)(ps + hi) = make_float4(sgn * h.x, sgn * h.y, sgn * h.z, sgn * h.w);
             *(float4*)(ps + lo) = make_float4(sgn * l.x, sgn * l.y, sgn * l.z, sgn * l.w);
         };
-        const float* U0 = Pan + blk;
-        const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;
-        size_t hi, lo, hi2, lo2;
-        ps_vdst(CPLX, N, KRM, fam_pairs, cw, p, 0, row, k, hi, lo);
-        put(hi, lo, load(V0), 1.f);
-        ps_udst(CPLX, N, KRM, fam_pairs, n, cw, p, 0, row, k, hi, lo, hi2, lo2);
-        put(hi, lo, load(U0), 1.f);
-        if (CPLX) {
-            ps_vdst(CPLX, N, KRM, fam_pairs, cw, p, 1, row, k, hi, lo);
-            put(hi, lo, load(V0 + NK), 1.f);
-            const float4 ui = load(U0 + NK);
-            ps_udst(CPLX, N, KRM, fam_pairs, n, cw, p, 1, row, k, hi, lo, hi2, lo2);
-            put(hi, lo, ui, 1.f);
-            put(hi2, lo2, ui, -1.f);
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            if (!live[u]) continue;
+            const float4 ur = x[u][0], vr = x[u][CPLX ? 2 : 1];
+            size_t hi, lo, hi2, lo2;
+            ps_vdst(CPLX, N, KRM, fam_pairs, cw[u], p[u], 0, row[u], k[u], hi, lo);
+            put(hi, lo, vr, 1.f);
+            ps_udst(CPLX, N, KRM, fam_pairs, n, cw[u], p[u], 0, row[u], k[u], hi, lo, hi2, lo2);
+            put(hi, lo, ur, 1.f);
+            if (CPLX) {
+                const float4 ui = x[u][1], vi = x[u][3];
+                ps_vdst(CPLX, N, KRM, fam_pairs, cw[u], p[u], 1, row[u], k[u], hi, lo);
+                put(hi, lo, vi, 1.f);
+                ps_udst(CPLX, N, KRM, fam_pairs, n, cw[u], p[u], 1, row[u], k[u], hi, lo, hi2, lo2);
+                put(hi, lo, ui, 1.f);
+                put(hi2, lo2, ui, -1.f);
+            }
         }
     }
 }
