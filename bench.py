@@ -58,6 +58,13 @@ WORKLOADS = {
 # Bond covariances: B_n (n >= 2) is B_1 rotated by a link-local Gaussian
 # unitary with generator entries of this standard deviation.
 BOND_SCALE = 0.05
+# dram__bytes_read.sum + dram__bytes_write.sum of one flush launch group per
+# chain (ncu, 4 chains of the same workload; profiles/sweep_kernels_cfg3_4chains.md).
+# Remove the entry when the split or flush kernels change.
+FLUSH_TRAFFIC_PER_CHAIN = {
+    "cfg3": {"bytes": 2.573e9, "source": "ncu capture of ps_split_kernel and flush_ps_kernel, 4 chains, scaled "
+                                          "by the chains (profiles/sweep_kernels_cfg3_4chains.md)"},
+}
 BLOCK_MOVES_PER_STEP = 16
 
 # Uneven batch: every (lattice, group, K) cell below is one problem; all cells
@@ -569,6 +576,15 @@ def run_ggf(args):
         roof = {"kernel": "ratio_kernel", "bound": "alu", "achieved": None, "peak": None, "unit": None}
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
     roof["traffic"] = None
+    if dom == "flush" and prec == 1 and args.workload in FLUSH_TRAFFIC_PER_CHAIN:
+        # DRAM bytes of one flush launch group (split passes + flushes, both
+        # families), per chain from an ncu capture of these kernels, times the
+        # chains: the traffic grows in proportion to them
+        t = FLUSH_TRAFFIC_PER_CHAIN[args.workload]
+        roof["traffic"] = t["bytes"] * chains / 1e9
+        roof["traffic_unit"] = "GB per launch group"
+        roof["traffic_source"] = t["source"]
+        roof["traffic_over_algorithmic"] = t["bytes"] / unit_bytes(p, prec)
     roof["share"] = {k: round(v / max(prof_ms, 1e-9), 4) for k, v in shares.items()}
     # time between the graph's kernel groups (launch gaps, host work between
     # sweeps): what a single persistent kernel could at most remove

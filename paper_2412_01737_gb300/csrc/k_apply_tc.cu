@@ -25,7 +25,9 @@
 // 3.3e-6 per accepted flip against 1.7e-6 with the FP32 FMA version of this
 // product; with four, 2.3e-6.  Neither the fourth split product
 // (a_lo b_lo) nor rounding the lo part to TF32 changed it: the length of
-// the tensor-core accumulation is what matters.
+// the tensor-core accumulation is what matters.  The sampler therefore keeps
+// Z2 chains on the FMA-pipe product and uses this kernel for U(1) and SU(2)
+// chains, whose small moves drift ~1e-8 per accept either way.
 //
 // Waits are bounded; on expiry the CTA stops, raises the context's error
 // word and frees its TMEM.

@@ -548,8 +548,12 @@ ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st) {
         const size_t sr = apply_smem(rpt_r, kr, rsz), sc = apply_smem(rpt_c, kr, 2 * rsz);
 #define GGF_APPLY(T, RPT, grid, smem, fam, Pp, Sp) \
     batch_apply<T, RPT><<<grid, 256, smem, st>>>(N, fam, KRM, kr, (typename Sc<T>::R*)(Pp), (const T*)(Sp), ch.pend)
-        if (GGF_APPLY_TC && !fp64 && ctx->use_tc && kr <= 256) {
-            // FP32 chains: the X product on the tensor cores (TF32 split)
+        if (GGF_APPLY_TC && !fp64 && ctx->use_tc && kr <= 256 && g.group != GGF_Z2) {
+            // FP32 chains: the X product on the tensor cores (TF32 split).  Z2
+            // chains keep the FMA-pipe product: a flip is a large change, and
+            // the tensor-core accumulation doubled their FP32 drift (measured
+            // 3.3e-6 against 1.7e-6 per accept at 16 x 16), while the small
+            // moves of U(1) and SU(2) chains are unaffected (1e-8 per accept)
             GGF_TRY(ggf_apply_tc(ctx, false, ctx->K, kr, (float*)ch.Pr, (const float*)Sr, st));
             GGF_TRY(ggf_apply_tc(ctx, true, ctx->Kc, kr, (float*)ch.Pc, (const float*)Sc_, st));
         } else if (fp64) {

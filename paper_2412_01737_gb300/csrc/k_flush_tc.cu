@@ -54,10 +54,16 @@ namespace {
 #ifndef GGF_FLUSH_PD
 #define GGF_FLUSH_PD 3
 #endif
-// Epilogue of real tiles: 1 = the W rows of the next 16-row chunk are loaded
-// before the current chunk is drained (two chunks of loads in flight).
+// Epilogue of the pre-split flush's real tiles: 1 = the W rows of the next
+// 16-row chunk are loaded before the current chunk is drained (two chunks of
+// loads in flight).  The per-tile flush (96 registers) never does this.
 #ifndef GGF_FLUSH_EPI_PP
 #define GGF_FLUSH_EPI_PP 0
+#endif
+// the same for complex tiles (16 float2 per chunk: two chunks in flight need
+// more registers than 10 warps per SM leave)
+#ifndef GGF_FLUSH_EPI_PP_C
+#define GGF_FLUSH_EPI_PP_C 0
 #endif
 // 1: the lo part of the operand split is rounded to TF32 (else the MMA drops
 // its low 13 bits)
@@ -317,7 +323,7 @@ __device__ __forceinline__ void stage_next(StageIter& it, long long total, int t
 // warp = the CTA warp index, whose value mod 4 is the TMEM lane quarter the
 // warp may read): for each of the CTA's tiles, wait for its accumulator, W -= D
 // from TMEM, and release the accumulator to the MMA thread.
-template <bool CPLX>
+template <bool CPLX, bool PP>
 __device__ __forceinline__ void epilogue_tiles(int warp, int ew, int lane, long long total, int tiles_i, int tiles_j,
                                                int fam_pairs, const int* pend, int R, int upper, int N, float* W,
                                                uint32_t tbase, uint64_t* bar_accf, uint64_t* bar_acce,
@@ -379,7 +385,7 @@ __device__ __forceinline__ void epilogue_tiles(int warp, int ew, int lane, long 
                     if (i < N && j < N) Wp[(size_t)i * N + j] = w[k] - __uint_as_float(v[k]);
                 }
             };
-            if (GGF_FLUSH_EPI_PP) {
+            if (PP) {
                 float wa[16], wb[16];
                 load_w(0, wa);
 #pragma unroll 1
@@ -435,7 +441,7 @@ __device__ __forceinline__ void epilogue_tiles(int warp, int ew, int lane, long 
                             make_float2(w[k].x - __uint_as_float(v[k]), w[k].y - __uint_as_float(vi[k]));
                 }
             };
-            if (GGF_FLUSH_EPI_PP) {
+            if (PP && GGF_FLUSH_EPI_PP_C) {
                 static_assert(NCBC % 2 == 0, "ping-pong epilogue drains chunk pairs");
                 float2 wa[16], wb[16];
                 load_wc(0, wa);
@@ -606,7 +612,7 @@ flush_tc_kernel(int N, int fam_pairs, int n_chains, float* W, const float* Pan, 
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp < MMA_WARP) {
-        epilogue_tiles<CPLX>(warp, warp - NPROD, lane, total, tiles_i, tiles_j, fam_pairs, pend, R, upper, N, W, tbase,
+        epilogue_tiles<CPLX, false>(warp, warp - NPROD, lane, total, tiles_i, tiles_j, fam_pairs, pend, R, upper, N, W, tbase,
                              bar_accf, bar_acce, s_fail, err);
     } else if (lane == 0) {
         mma_tiles<CPLX, TERMS, STAGES>(total, tiles_i, tiles_j, fam_pairs, pend, R, upper, tbase, base, bar_full,
@@ -656,71 +662,54 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 // Only the rank chunks below the chain's pending rank are written (the flush
 // reads no others); inside them, rows past N and columns past the rank are 0.
 template <bool CPLX>
-__global__ void __launch_bounds__(256) ps_split_kernel(int N, int fam_pairs, int c0, int n,
-                                                       const float* __restrict__ Pan, const int* __restrict__ pend,
-                                                       int R, int KRM, unsigned char* __restrict__ ps) {
-    constexpr int PL = CPLX ? 4 : 2;              // planes read per item: V (re, im), U (re, im)
-    constexpr int UN = 2;                         // items per thread and loop trip, loads issued first
+__global__ void __launch_bounds__(256) ps_split_kernel(int N, int fam_pairs, int c0, int n, const float* Pan,
+                                                       const int* pend, int R, int KRM, unsigned char* ps) {
     const size_t NK = panel_plane(N, KRM);
     const int NP = panel_rows(N);
     const int nq = panel_cols(KRM) / 4;
     const long long total = (long long)n * fam_pairs * NP * nq;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += UN * stride) {
-        float4 x[UN][PL];
-        int row[UN], k[UN], p[UN], cw[UN];
-        bool live[UN];
-#pragma unroll
-        for (int u = 0; u < UN; ++u) {
-            const long long e = e0 + u * stride;
-            live[u] = e < total;
-            const long long ee = live[u] ? e : 0;
-            const int q = (int)(ee % nq);
-            long long rest = ee / nq;
-            row[u] = (int)(rest % NP);
-            rest /= NP;
-            p[u] = (int)(rest % fam_pairs);
-            cw[u] = (int)(rest / fam_pairs);
-            k[u] = 4 * q;
-            const int K = pend[c0 + cw[u]] * R;
-            live[u] = live[u] && k[u] < ((K + KC - 1) / KC) * KC;
-            const size_t blk = ((size_t)(c0 + cw[u]) * fam_pairs + p[u]) * PL * NK;
-            // planes in panel order: U re, (U im), V re, (V im)
-#pragma unroll
-            for (int pl = 0; pl < PL; ++pl) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (live[u] && row[u] < N) v = *(const float4*)(Pan + blk + pl * NK + pidx(row[u], k[u], NP));
-                if (k[u] + 0 >= K) v.x = 0.f;
-                if (k[u] + 1 >= K) v.y = 0.f;
-                if (k[u] + 2 >= K) v.z = 0.f;
-                if (k[u] + 3 >= K) v.w = 0.f;
-                x[u][pl] = v;
-            }
-        }
-        auto put = [&](size_t hi, size_t lo, float4 v, float sgn) {
-            const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-            float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(e % nq);
+        long long rest = e / nq;
+        const int row = (int)(rest % NP);
+        rest /= NP;
+        const int p = (int)(rest % fam_pairs);
+        const int cw = (int)(rest / fam_pairs);
+        const int K = pend[c0 + cw] * R;
+        const int k = 4 * q;
+        if (k >= ((K + KC - 1) / KC) * KC) continue;
+        const size_t blk = ((size_t)(c0 + cw) * fam_pairs + p) * (CPLX ? 4 : 2) * NK;
+        auto load = [&](const float* plane) {
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < N) x = *(const float4*)(plane + pidx(row, k, NP));
+            if (k + 0 >= K) x.x = 0.f;
+            if (k + 1 >= K) x.y = 0.f;
+            if (k + 2 >= K) x.z = 0.f;
+            if (k + 3 >= K) x.w = 0.f;
+            return x;
+        };
+        auto put = [&](size_t hi, size_t lo, float4 x, float sgn) {
+            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
             if (GGF_SPLIT_LO_RNA) l = make_float4(tf32_hi(l.x), tf32_hi(l.y), tf32_hi(l.z), tf32_hi(l.w));
             *(float4*)(ps + hi) = make_float4(sgn * h.x, sgn * h.y, sgn * h.z, sgn * h.w);
             *(float4*)(ps + lo) = make_float4(sgn * l.x, sgn * l.y, sgn * l.z, sgn * l.w);
         };
-#pragma unroll
-        for (int u = 0; u < UN; ++u) {
-            if (!live[u]) continue;
-            const float4 ur = x[u][0], vr = x[u][CPLX ? 2 : 1];
-            size_t hi, lo, hi2, lo2;
-            ps_vdst(CPLX, N, KRM, fam_pairs, cw[u], p[u], 0, row[u], k[u], hi, lo);
-            put(hi, lo, vr, 1.f);
-            ps_udst(CPLX, N, KRM, fam_pairs, n, cw[u], p[u], 0, row[u], k[u], hi, lo, hi2, lo2);
-            put(hi, lo, ur, 1.f);
-            if (CPLX) {
-                const float4 ui = x[u][1], vi = x[u][3];
-                ps_vdst(CPLX, N, KRM, fam_pairs, cw[u], p[u], 1, row[u], k[u], hi, lo);
-                put(hi, lo, vi, 1.f);
-                ps_udst(CPLX, N, KRM, fam_pairs, n, cw[u], p[u], 1, row[u], k[u], hi, lo, hi2, lo2);
-                put(hi, lo, ui, 1.f);
-                put(hi2, lo2, ui, -1.f);
-            }
+        const float* U0 = Pan + blk;
+        const float* V0 = Pan + blk + (CPLX ? 2 : 1) * NK;
+        size_t hi, lo, hi2, lo2;
+        ps_vdst(CPLX, N, KRM, fam_pairs, cw, p, 0, row, k, hi, lo);
+        put(hi, lo, load(V0), 1.f);
+        ps_udst(CPLX, N, KRM, fam_pairs, n, cw, p, 0, row, k, hi, lo, hi2, lo2);
+        put(hi, lo, load(U0), 1.f);
+        if (CPLX) {
+            ps_vdst(CPLX, N, KRM, fam_pairs, cw, p, 1, row, k, hi, lo);
+            put(hi, lo, load(V0 + NK), 1.f);
+            const float4 ui = load(U0 + NK);
+            ps_udst(CPLX, N, KRM, fam_pairs, n, cw, p, 1, row, k, hi, lo, hi2, lo2);
+            put(hi, lo, ui, 1.f);
+            put(hi2, lo2, ui, -1.f);
         }
     }
 }
@@ -768,7 +757,7 @@ flush_ps_kernel(int N, int fam_pairs, int n_chains, float* W, const unsigned cha
     const uint32_t tbase = tmem_slot;
 
     if (warp < NEPI) {
-        epilogue_tiles<CPLX>(warp, warp, lane, total, tiles_i, tiles_j, fam_pairs, pend, R, 0, N, W, tbase, bar_accf,
+        epilogue_tiles<CPLX, GGF_FLUSH_EPI_PP != 0>(warp, warp, lane, total, tiles_i, tiles_j, fam_pairs, pend, R, 0, N, W, tbase, bar_accf,
                              bar_acce, s_fail, err);
     } else if (warp == PS_COPY_WARP) {
         if (lane == 0) {
