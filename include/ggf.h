@@ -481,6 +481,20 @@ ggf_status ggf_kernel_time(ggf_ctx* ctx, int which, double* ms, uint64_t* launch
  * buffers).  Not part of the method. */
 ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank, double* max_rel_err);
 
+/* The same seeded case with its data, for a reference computed outside the
+ * library: which = 0 runs the per-tile-split flush, 1 the pre-split one.
+ * Host outputs (caller-owned):
+ *   w0, w1  [N][N] floats (cplx = 0) or [N][N][2] (re, im), the input and
+ *           output W;
+ *   pan     the panels: planes U, V^T (cplx = 0) or U re, U im, V^T re,
+ *           V^T im, each NP x KP floats with NP = N rounded up to 256 and
+ *           KP = rank rounded up to 8, element (row, q) of a plane at
+ *           ((q / 8) NP + row) 8 + q % 8.  Only rows < N and q < rank enter:
+ *           w1 = w0 - U (V^T)^T over them.
+ * Not part of the method. */
+ggf_status ggf_selftest_flush_data(ggf_ctx* ctx, int cplx, int N, int rank, int which, float* w0, float* pan,
+                                   float* w1);
+
 /* ---- Learned block proposal ------------------------------------------------
  * A small convolutional network proposes new angles for the 32 links of a
  * 4 x 4 block of sites (U(1) only) from the links outside the block; block

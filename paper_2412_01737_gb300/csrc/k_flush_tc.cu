@@ -1023,3 +1023,55 @@ extern "C" ggf_status ggf_selftest_flush(ggf_ctx* ctx, int cplx, int N, int rank
     cleanup();
     return rc;
 }
+
+// The self-test's seeded case with its data copied to host memory, so that a
+// reference independent of the library can be computed: which = 0 runs the
+// per-tile-split flush, 1 the pre-split one.
+extern "C" ggf_status ggf_selftest_flush_data(ggf_ctx* ctx, int cplx, int N, int rank, int which, float* w0,
+                                              float* pan, float* w1) {
+    if (!ctx || !w0 || !pan || !w1 || N < 1 || N > 8192 || rank < 4 || rank > 512 || rank % 4 || which < 0 ||
+        which > 1)
+        return ggf_fail(ctx, GGF_EINVAL, "selftest_flush_data: N in [1, 8192], rank in {4, 8, ..., 512}, which 0 or 1");
+    cudaSetDevice(ctx->device);
+    const int R = 4, KRM = rank;
+    const int rowW = cplx ? 2 * N : N;
+    const size_t NK = panel_plane(N, KRM), nW = (size_t)N * rowW, nP = (cplx ? 4 : 2) * NK;
+    float *W = nullptr, *Pan = nullptr;
+    unsigned char* ps = nullptr;
+    int* pend = nullptr;
+    ggf_status rc = GGF_OK;
+    auto cleanup = [&]() {
+        if (W) cudaFree(W);
+        if (Pan) cudaFree(Pan);
+        if (pend) cudaFree(pend);
+        if (ps) cudaFree(ps);
+    };
+    if (cudaMalloc(&W, nW * 4) != cudaSuccess || cudaMalloc(&Pan, nP * 4) != cudaSuccess ||
+        cudaMalloc(&pend, 4) != cudaSuccess ||
+        (which == 1 && cudaMalloc(&ps, ps_bytes(cplx != 0, N, KRM, 1, 1)) != cudaSuccess)) {
+        cleanup();
+        return ggf_fail(ctx, GGF_ENOMEM, "selftest_flush_data allocation failed");
+    }
+    const int pv = rank / R;
+    cudaMemcpy(pend, &pv, 4, cudaMemcpyHostToDevice);
+    st_fill<<<(unsigned)((nW + 255) / 256), 256>>>(W, nW, 1, 1.0f);
+    st_fill<<<(unsigned)((nP + 255) / 256), 256>>>(Pan, nP, 2, 0.3f);
+    if (cudaMemcpy(w0, W, nW * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pan, Pan, nP * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = ggf_cuda(ctx, cudaGetLastError(), "selftest_flush_data");
+    } else if ((rc = ggf_prepare_flush_tc(ctx)) == GGF_OK) {
+        if (which == 0) rc = launch_flush_tc(ctx, cplx != 0, N, 1, 1, W, Pan, pend, R, KRM, false, ctx->d_err, 0);
+        else rc = cplx ? flush_wave<true>(ctx, N, R, 1, 0, 1, W, Pan, pend, KRM, ps, 0)
+                       : flush_wave<false>(ctx, N, R, 1, 0, 1, W, Pan, pend, KRM, ps, 0);
+        int herr = 0;
+        if (rc == GGF_OK) {
+            if (cudaMemcpy(w1, W, nW * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(&herr, ctx->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+                rc = ggf_cuda(ctx, cudaGetLastError(), "selftest_flush_data");
+            else if (herr)
+                rc = ggf_fail(ctx, GGF_ETIMEOUT, "tensor-core flush: mbarrier wait ran out");
+        }
+    }
+    cleanup();
+    return rc;
+}

@@ -60,7 +60,7 @@ EXPORTS = ["ggf_create", "ggf_destroy", "ggf_last_error", "ggf_init_lattice", "g
            "ggf_chains_stats",
            "ggf_checkpoint",
            "ggf_resume", "ggf_profile", "ggf_kernel_time", "ggf_sync", "ggf_logweight_noalloc",
-           "ggf_selftest_flush", "ggf_net_create", "ggf_net_destroy", "ggf_net_last_error", "ggf_net_get_params",
+           "ggf_selftest_flush", "ggf_selftest_flush_data", "ggf_net_create", "ggf_net_destroy", "ggf_net_last_error", "ggf_net_get_params",
            "ggf_net_set_params", "ggf_net_logq", "ggf_net_loss_grad", "ggf_net_train", "ggf_sample_blocks"]
 
 
@@ -118,6 +118,7 @@ def load():
         "ggf_sync": ([P, P], I),
         "ggf_logweight_noalloc": ([P, I, P, P, P], I),
         "ggf_selftest_flush": ([P, I, I, I, ctypes.POINTER(ctypes.c_double)], I),
+        "ggf_selftest_flush_data": ([P, I, I, I, I, P, P, P], I),
         "ggf_net_create": ([ctypes.POINTER(P), I, I, ctypes.c_uint64], I),
         "ggf_net_destroy": ([P], V),
         "ggf_net_last_error": ([P], ctypes.c_char_p),
@@ -483,6 +484,19 @@ class GGF:
         e = ctypes.c_double()
         self._ck(self.lib.ggf_selftest_flush(self.h, int(cplx), int(N), int(rank), ctypes.byref(e)))
         return e.value
+
+    def selftest_flush_data(self, cplx, N, rank, which):
+        """(w0, panels, w1) of the flush self-test case as host arrays (see
+        ggf_selftest_flush_data for the layouts)."""
+        NP = (N + 255) // 256 * 256
+        KP = (rank + 7) // 8 * 8
+        nW = N * N * (2 if cplx else 1)
+        w0 = np.zeros(nW, dtype=np.float32)
+        w1 = np.zeros(nW, dtype=np.float32)
+        pan = np.zeros((4 if cplx else 2) * NP * KP, dtype=np.float32)
+        self._ck(self.lib.ggf_selftest_flush_data(self.h, int(cplx), int(N), int(rank), int(which),
+                                                  w0.ctypes.data, pan.ctypes.data, w1.ctypes.data))
+        return w0, pan, w1
 
     def profile(self, enable=True):
         self._ck(self.lib.ggf_profile(self.h, 1 if enable else 0))

@@ -9,6 +9,7 @@ The tensor core accumulates the rank-K sum in FP32 in TMEM, so the error
 grows with K: the bound is 2.5e-6 of the largest entry up to K = 128 and
 scales linearly beyond (measured: 2.0e-6 at K = 128 and 3.3e-6 at K = 256,
 complex, with N = 4096)."""
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -23,3 +24,40 @@ def test_flush_tc_accuracy(cplx, N, rank):
     err = ctx.selftest_flush(cplx, N, rank)
     ctx.close()
     assert err < 2.5e-6 * max(1.0, rank / 128), err
+
+
+def _plane(pan, k, NP, KP, N, rank):
+    """Dense N x rank view of panel plane k (chunk-major: element (row, q) at
+    ((q / 8) NP + row) 8 + q % 8)."""
+    P = pan[k * NP * KP:(k + 1) * NP * KP].astype(np.float64).reshape(KP // 8, NP, 8)
+    return P.transpose(1, 0, 2).reshape(NP, KP)[:N, :rank]
+
+
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("cplx", [0, 1])
+@pytest.mark.parametrize("N,rank", [(200, 36), (1000, 132), (4096, 128)])
+def test_flush_tc_against_host_reference(which, cplx, N, rank):
+    """Both flush kernels against W0 - U V computed here in FP64 from the
+    same inputs, element by element: each entry within 2.5e-6 of the largest
+    |entry| (scaled with the rank above 128), the FP32 accuracy the TF32
+    three-product split is built for."""
+    from paper_2412_01737_gb300 import GGF
+    ctx = GGF(0)
+    w0, pan, w1 = ctx.selftest_flush_data(cplx, N, rank, which)
+    ctx.close()
+    NP = (N + 255) // 256 * 256
+    KP = (rank + 7) // 8 * 8
+    if not cplx:
+        U, Vt = _plane(pan, 0, NP, KP, N, rank), _plane(pan, 1, NP, KP, N, rank)
+        ref = w0.astype(np.float64).reshape(N, N) - U @ Vt.T
+        got = w1.astype(np.float64).reshape(N, N)
+    else:
+        U = _plane(pan, 0, NP, KP, N, rank) + 1j * _plane(pan, 1, NP, KP, N, rank)
+        Vt = _plane(pan, 2, NP, KP, N, rank) + 1j * _plane(pan, 3, NP, KP, N, rank)
+        W0 = w0.astype(np.float64).reshape(N, N, 2)
+        ref = (W0[..., 0] + 1j * W0[..., 1]) - U @ Vt.T
+        W1 = w1.astype(np.float64).reshape(N, N, 2)
+        got = W1[..., 0] + 1j * W1[..., 1]
+    bound = 2.5e-6 * max(1.0, rank / 128) * np.abs(ref).max()
+    err = np.abs(got - ref)
+    assert err.max() <= bound, (err.max(), bound)
