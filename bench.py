@@ -547,6 +547,13 @@ def run_ggf(args):
                     "algorithmic_bytes_per_launch_group": chains * unit_bytes(p, prec),
                     "avg_launch_group_ms": kt["flush"][0] / max(1, kt["flush"][1]),
                     "fp32_equivalent_tflops": fl / t_fl / 1e12}
+            # the complex-pair tiles are tensor-bound (three TF32 products per
+            # FP32 MAC): the same time against the tensor roofline, TF32 peak =
+            # measured BF16 burst x the nominal TF32/BF16 ratio (1.1 / 2.25)
+            tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+            roof["tensor"] = {"achieved": 3 * fl / t_fl / 1e12, "peak": tf32_peak, "unit": "TFLOP/s (TF32)",
+                              "frac": 3 * fl / t_fl / 1e12 / tf32_peak,
+                              "peak_source": "MEASURED_PEAKS.json bf16_tflops x 1.1/2.25 (nominal TF32/BF16 ratio)"}
         else:
             roof = {"kernel": "flush_kernel (FP64 SIMT, W -= U V)", "bound": "alu",
                     "achieved": fl / t_fl / 1e12, "peak": 1.25, "unit": "TFLOP/s",
