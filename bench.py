@@ -12,7 +12,8 @@ from all sweeps run after burn-in.
 
 --impl reference times the FP64 CPU oracle (exact Metropolis, full Pfaffian
 recompute per proposal) on the host cores on a bounded sample.
-Multi-GPU: independent replicas (different chain seeds), no data-path
+Multi-GPU: independent replicas (rank k runs the global chains k*chains .. ,
+the Philox key of each chain is its global index), no data-path
 collective; the timing is the max over ranks.
 """
 from __future__ import annotations

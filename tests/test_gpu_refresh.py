@@ -168,3 +168,25 @@ def test_newton_step_repairs_a_perturbed_inverse():
         got = got.real if n == m else got
         assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
     ctx.close()
+
+
+def test_newton_step_at_full_size():
+    """At the benchmark's matrix order (16x16 U(1), n_v = 2, K = 2: N = 4096,
+    real and complex pairs) a planted 1e-3 scaling of each pair's FP32
+    inverse is repaired by the tensor-core Newton steps (a three-product step
+    for the 1e-3 residual, then the residual at the level of the freshly
+    factored inverse)."""
+    from paper_2412_01737_gb300 import FP32
+    p = gi.make_problem(16, gi.U1, 2, 2, seed=20241202)
+    ctx = ctx_for(p)
+    ctx.chains_init(gi.random_links(p, 1, seed=3), precision=FP32, refresh_every=10**9, seed=9, delay=16)
+    for k in range(3):
+        fresh = ctx.chains_refine(0, k, apply=False)
+        assert fresh < 1e-5
+        ctx.debug_scale_inverse(0, k, 1.0 + 1e-3)
+        r0 = ctx.chains_refine(0, k, apply=True)
+        assert 5e-4 < r0 < 5e-2
+        ctx.chains_refine(0, k, apply=True)
+        r2 = ctx.chains_refine(0, k, apply=False)
+        assert r2 <= max(2 * fresh, 1e-5), (k, fresh, r2)
+    ctx.close()
