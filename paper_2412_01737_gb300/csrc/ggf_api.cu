@@ -28,6 +28,7 @@ ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx);
 ggf_status ggf_prepare_batch(ggf_ctx* ctx);
 ggf_status ggf_check_batch(ggf_ctx* ctx, int kmax, bool fp64);
 size_t ggf_flush_ps_chain_bytes(ggf_ctx* ctx, int KRM);
+size_t ggf_flush_ps_newton_bytes(ggf_ctx* ctx);
 ggf_status ggf_batch(ggf_ctx* ctx, int l0, int kb, cudaStream_t st);
 ggf_status ggf_bump_sweep(ggf_ctx* ctx, cudaStream_t st);
 ggf_status ggf_electric(ggf_ctx* ctx, cxd* d_out, cxd* d_pairs, cudaStream_t st, bool field = false);
@@ -730,14 +731,19 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
         ctx->work_bytes = 0;
     }
     // pre-split scratch of the tensor-core flush, after the set-up's own
-    // workspace: waves of up to 2 GiB and a quarter of the free memory
+    // workspace: waves of up to 2 GiB and a quarter of the free memory; within
+    // that budget at least what the refresh's Newton product (rank N, one
+    // pair) needs, so that it runs through the scratch too
     if (!fp64 && ch.kmax > 1 && ctx->use_tc) {
         const size_t per = ggf_flush_ps_chain_bytes(ctx, ch.kmax * g.r);
         size_t free_b = 0, total_b = 0;
         GGF_CK(cudaMemGetInfo(&free_b, &total_b));
         const size_t budget = std::min<size_t>((size_t)2 << 30, free_b / 4);
         ch.ps_wave = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_chains, budget / std::max<size_t>(per, 1)));
-        GGF_CK(cudaMalloc(&ch.ps, (size_t)ch.ps_wave * per));
+        ch.ps_bytes = (size_t)ch.ps_wave * per;
+        const size_t newton = ggf_flush_ps_newton_bytes(ctx);
+        if (newton > ch.ps_bytes && newton <= budget) ch.ps_bytes = newton;
+        GGF_CK(cudaMalloc(&ch.ps, ch.ps_bytes));
     }
     GGF_CK(cudaMemsetAsync(ch.counters, 0, 6 * sizeof(unsigned long long), st));
     GGF_CK(cudaStreamSynchronize(st));

@@ -62,6 +62,7 @@ struct Chains {
     // modes): the flush runs in waves of ps_wave chains
     unsigned char* ps = nullptr;
     int ps_wave = 0;
+    size_t ps_bytes = 0;
     unsigned long long block_moves = 0;      // learned-proposal moves made (Philox counter)
     // one sweep captured as a CUDA graph (opts.graph != 0)
     unsigned long long* d_sweep = nullptr;   // device copy of the sweep counter

@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(256) ps_split_kernel(int N, int fam_pairs, int
 
 // W -= U V for chains 0 .. n_chains - 1 of W and pend (the caller offsets
 // them to the wave), operands from the wave's pre-split blocks ps.
-template <bool CPLX>
+template <bool CPLX, int TERMS>
 __global__ void __launch_bounds__(PS_THREADS, 1)
 flush_ps_kernel(int N, int fam_pairs, int n_chains, float* W, const unsigned char* ps, const int* pend, int R, int KRM,
                 int* err) {
@@ -775,9 +775,18 @@ flush_ps_kernel(int N, int fam_pairs, int n_chains, float* W, const unsigned cha
                 const unsigned char* usrc =
                     ps + ps_uoff(CPLX, N, KRM, fam_pairs, n_chains, it.t.c, it.t.p, it.t.i0 / ROWS, kc);
                 const uint32_t sb = smem_u32(base + st * SB), bar = smem_u32(&bar_full[st]);
-                mbar_expect_tx(bar, VB + UB);
-                bulk_to_smem(sb, vsrc, VB, bar);
-                bulk_to_smem(sb + VB, usrc, UB, bar);
+                if (TERMS == 3) {
+                    mbar_expect_tx(bar, VB + UB);
+                    bulk_to_smem(sb, vsrc, VB, bar);
+                    bulk_to_smem(sb + VB, usrc, UB, bar);
+                } else {
+                    // one product: the hi planes only (V hi at the start of
+                    // each plane pair, U hi the first half of its block)
+                    mbar_expect_tx(bar, VB / 2 + UB / 2);
+                    bulk_to_smem(sb, vsrc, PS_PLANE, bar);
+                    if (CPLX) bulk_to_smem(sb + 2 * PS_PLANE, vsrc + 2 * PS_PLANE, PS_PLANE, bar);
+                    bulk_to_smem(sb + VB, usrc, UB / 2, bar);
+                }
                 ++issued;
                 if (++st == PS_STAGES) { st = 0; ph ^= 1u; }
                 stage_next<ROWS>(it, total, tiles_i, tiles_j, fam_pairs, pend, R, 0);
@@ -791,7 +800,7 @@ flush_ps_kernel(int N, int fam_pairs, int n_chains, float* W, const unsigned cha
             }
         }
     } else if (lane == 0) {
-        mma_tiles<CPLX, 3, PS_STAGES>(total, tiles_i, tiles_j, fam_pairs, pend, R, 0, tbase, base, bar_full, bar_empty,
+        mma_tiles<CPLX, TERMS, PS_STAGES>(total, tiles_i, tiles_j, fam_pairs, pend, R, 0, tbase, base, bar_full, bar_empty,
                                       bar_accf, bar_acce, &bar_done, s_fail, err);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -813,8 +822,10 @@ ggf_status ggf_prepare_flush_tc(ggf_ctx* ctx) {
     GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false)));
     GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(true)));
     GGF_CK(cudaFuncSetAttribute(flush_tc_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false)));
-    GGF_CK(cudaFuncSetAttribute(flush_ps_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps_smem_bytes()));
-    GGF_CK(cudaFuncSetAttribute(flush_ps_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps_smem_bytes()));
+    GGF_CK(cudaFuncSetAttribute(flush_ps_kernel<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps_smem_bytes()));
+    GGF_CK(cudaFuncSetAttribute(flush_ps_kernel<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps_smem_bytes()));
+    GGF_CK(cudaFuncSetAttribute(flush_ps_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps_smem_bytes()));
+    GGF_CK(cudaFuncSetAttribute(flush_ps_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps_smem_bytes()));
     if (ctx->device >= 0 && ctx->device < 64) done[ctx->device] = true;
     return GGF_OK;
 }
@@ -894,6 +905,13 @@ __global__ void st_maxerr(size_t n, const float* got, const double* ref, unsigne
 
 }  // namespace
 
+// Bytes of pre-split scratch of one rank-N product (the Newton step of the
+// refresh) of the larger family.
+size_t ggf_flush_ps_newton_bytes(ggf_ctx* ctx) {
+    const int N = ctx->g.N;
+    return ps_bytes(ctx->Kc > 0, N, N, 1, 1);
+}
+
 // Bytes of pre-split scratch per chain (the larger of the two families).
 size_t ggf_flush_ps_chain_bytes(ggf_ctx* ctx, int KRM) {
     const int N = ctx->g.N;
@@ -903,7 +921,7 @@ size_t ggf_flush_ps_chain_bytes(ggf_ctx* ctx, int KRM) {
 namespace {
 
 // One wave (chains c0 .. c0 + n - 1 of W, Pan and pend): split, then flush.
-template <bool CPLX>
+template <bool CPLX, int TERMS = 3>
 ggf_status flush_wave(ggf_ctx* ctx, int N, int R, int fam_pairs, int c0, int n, float* W, const float* Pan,
                       const int* pend, int KRM, unsigned char* ps, cudaStream_t st) {
     const int sms = ctx->n_sms > 0 ? ctx->n_sms : 152;
@@ -913,7 +931,7 @@ ggf_status flush_wave(ggf_ctx* ctx, int N, int R, int fam_pairs, int c0, int n, 
     const int rows = CPLX ? 128 : 256;
     const long long total = (long long)n * fam_pairs * ((N + rows - 1) / rows) * ((N + 127) / 128);
     const size_t wsz = (size_t)N * N * (CPLX ? 2 : 1);
-    flush_ps_kernel<CPLX><<<(unsigned)std::min<long long>(total, sms), PS_THREADS, ps_smem_bytes(), st>>>(
+    flush_ps_kernel<CPLX, TERMS><<<(unsigned)std::min<long long>(total, sms), PS_THREADS, ps_smem_bytes(), st>>>(
         N, fam_pairs, n, W + (size_t)c0 * fam_pairs * wsz, ps, pend + c0, R, KRM, ctx->d_err);
     GGF_CK(cudaGetLastError());
     return GGF_OK;
@@ -950,6 +968,16 @@ ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st, int* launches) {
 // product).  Used by the Newton refinement of the inverses (k_refine.cu).
 ggf_status ggf_flush_tc_one(ggf_ctx* ctx, bool cplx, int N, float* W, const float* Pan, const int* pend, int R,
                             int KRM, int terms, cudaStream_t st) {
+    // through the chains' pre-split scratch when it holds this product's
+    // operands (outside a sweep it is free), else splitting per tile
+    const Chains& ch = ctx->ch;
+    if (ch.ps && ps_bytes(cplx, N, KRM, 1, 1) <= ch.ps_bytes) {
+        GGF_TRY(ggf_prepare_flush_tc(ctx));
+        if (cplx) return terms == 1 ? flush_wave<true, 1>(ctx, N, R, 1, 0, 1, W, Pan, pend, KRM, ch.ps, st)
+                                    : flush_wave<true, 3>(ctx, N, R, 1, 0, 1, W, Pan, pend, KRM, ch.ps, st);
+        return terms == 1 ? flush_wave<false, 1>(ctx, N, R, 1, 0, 1, W, Pan, pend, KRM, ch.ps, st)
+                          : flush_wave<false, 3>(ctx, N, R, 1, 0, 1, W, Pan, pend, KRM, ch.ps, st);
+    }
     return launch_flush_tc(ctx, cplx, N, 1, 1, W, Pan, pend, R, KRM, false, ctx->d_err, st, terms == 1 ? 1 : 3);
 }
 
