@@ -631,7 +631,7 @@ def run_ggf(args):
             "config": {"workload": label, "chains": chains, "delay": delay, "refresh_every_accepts": refresh,
                        "sweeps_timed": args.steps, "thermalisation_sweeps": args.burn,
                        "thermalisation_s": t_burn,
-                       "thermalisation_note": "untimed, discarded; the survey prescribes 200 for this workload",
+                       "thermalisation_note": "untimed, discarded; 200 sweeps of this workload would take about 25 min",
                        "tau_series_sweeps": obs_series.shape[1],
                        "tau_int": tau_detail, "tau_used": tau, "tau_window_closed": closed,
                        "ess_is_upper_bound": not closed,
