@@ -19,7 +19,15 @@
 //   D[:, 0:256] += V_r [U_r ; U_i]^T + V_i [-U_i ; U_r]^T
 // holds re(D^T) in TMEM columns 0..127 and im(D^T) in 128..255.
 //
-// One persistent CTA per SM, warp-specialised:
+// Two kernels share the MMA issuer and the epilogue below.  The sweep's
+// flush (and the refresh's Newton product, when the scratch holds it) is
+// flush_ps_kernel: the operands are split once per chain wave by
+// ps_split_kernel into pre-split stage blocks, which one thread bulk-copies
+// into the stages (further down).  flush_tc_kernel, laid out here, splits the
+// operands per tile; it serves the Newton product when the scratch is too
+// small, and the self-test.
+//
+// flush_tc_kernel: one persistent CTA per SM, warp-specialised:
 //   warps 0-7   producers: copy an 8-wide rank chunk of the operands into
 //               a private raw shared-memory slot with cp.async (16 bytes
 //               per copy, zero-filled outside the matrix; PD stages of
