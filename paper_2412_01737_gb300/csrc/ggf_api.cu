@@ -743,7 +743,13 @@ ggf_status ggf_chains_init(ggf_ctx* ctx, int n_chains, const void* links, const 
         ch.ps_bytes = (size_t)ch.ps_wave * per;
         const size_t newton = ggf_flush_ps_newton_bytes(ctx);
         if (newton > ch.ps_bytes && newton <= budget) ch.ps_bytes = newton;
-        GGF_CK(cudaMalloc(&ch.ps, ch.ps_bytes));
+        if (cudaMalloc(&ch.ps, ch.ps_bytes) != cudaSuccess) {
+            // memory is full: the flush splits its operands per tile instead
+            cudaGetLastError();
+            ch.ps = nullptr;
+            ch.ps_wave = 0;
+            ch.ps_bytes = 0;
+        }
     }
     GGF_CK(cudaMemsetAsync(ch.counters, 0, 6 * sizeof(unsigned long long), st));
     GGF_CK(cudaStreamSynchronize(st));

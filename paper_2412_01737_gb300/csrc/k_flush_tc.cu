@@ -949,12 +949,21 @@ ggf_status flush_wave(ggf_ctx* ctx, int N, int R, int fam_pairs, int c0, int n, 
 
 // The sweep's flush of every chain's pending panels: chain waves of
 // ch.ps_wave chains, each split once into pre-split blocks and flushed from
-// them (two launches per family and wave; the count is added to *launches).
+// them (two launches per family and wave; the count is added to *launches);
+// without a scratch, the per-tile-split kernel over all chains.
 ggf_status ggf_flush_tc(ggf_ctx* ctx, cudaStream_t st, int* launches) {
     Chains& ch = ctx->ch;
     const Geometry& g = ctx->g;
     const int KRM = ch.kmax * g.r;
-    if (!ch.ps || ch.ps_wave < 1) return ggf_fail(ctx, GGF_ESTATE, "tensor-core flush: no pre-split scratch");
+    if (!ch.ps || ch.ps_wave < 1) {
+        // no scratch (the chains left no room for one): split per tile
+        GGF_TRY(launch_flush_tc(ctx, false, g.N, ctx->K, ch.n, (float*)ch.Wr, (const float*)ch.Pr, ch.pend, g.r, KRM,
+                                false, ctx->d_err, st));
+        GGF_TRY(launch_flush_tc(ctx, true, g.N, ctx->Kc, ch.n, (float*)ch.Wc, (const float*)ch.Pc, ch.pend, g.r, KRM,
+                                false, ctx->d_err, st));
+        *launches += 1 + (ctx->Kc ? 1 : 0);
+        return GGF_OK;
+    }
     for (int c0 = 0; c0 < ch.n; c0 += ch.ps_wave) {
         const int n = std::min(ch.ps_wave, ch.n - c0);
         if (ctx->K) {
